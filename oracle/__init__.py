@@ -1,0 +1,219 @@
+"""FP64 CPU oracle for the statically condensed GL-DGSEM Newton solve.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The product
+library never links, imports or calls it, and it imports nothing from the product
+package: the only module both sides share is ``sc_inputs`` (seeded inputs).
+
+Layers:
+  * ``oracle/sc_oracle.cpp`` (compiled to ``oracle/_build/liboracle.so``): Gauss-Lobatto
+    basis, weak-form residual (Sec. 2.1, eq. DGSEMsystem), dual-number Jacobian
+    (eq. NewtonLinSys1) and Jacobian-vector products.
+  * ``oracle/linalg.py``: the static condensation of Sec. 2.2 / 3.2 (eqs. StaticCondBlock,
+    SC_step1, SC_step2) and a right-preconditioned restarted GMRES, on numpy/scipy.
+
+Parity status of each function is recorded in the design doc (all pinned by tests in
+``tests/test_oracle_*.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle/sc_oracle.cpp with g++ (-O3 -fopenmp) into oracle/_build."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    src = os.path.join(_HERE, "sc_oracle.cpp")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c++17", "-o", tmp, src]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int), ("N", ctypes.c_int), ("L", ctypes.c_double), ("dt", ctypes.c_double),
+        ("bdf", ctypes.c_int), ("gamma", ctypes.c_double), ("Pr", ctypes.c_double),
+        ("Re", ctypes.c_double), ("Ma", ctypes.c_double), ("Ts", ctypes.c_double),
+        ("sutherland", ctypes.c_int), ("model", ctypes.c_int), ("viscous", ctypes.c_int),
+        ("adv", ctypes.c_double * 3), ("nu", ctypes.c_double), ("roe_delta", ctypes.c_double),
+        ("with_time", ctypes.c_int),
+    ]
+
+
+@dataclass
+class Params:
+    """Problem definition: mesh, order, physics and time step."""
+    n: int
+    N: int
+    dt: float = 1.0
+    L: float = 2.0 * np.pi
+    bdf: int = 1
+    gamma: float = 1.4
+    Pr: float = 0.72
+    Re: float = 1600.0
+    Ma: float = 0.1
+    Ts: float = 110.4 / 288.15
+    sutherland: bool = True
+    model: int = 0          # 0 Navier-Stokes, 1 linear advection-diffusion (5 copies)
+    viscous: bool = True
+    adv: tuple = (1.0, 0.0, 0.0)
+    nu: float = 0.0
+    roe_delta: float = 0.05
+    with_time: bool = True
+
+    @property
+    def K(self) -> int:
+        return self.n ** 3
+
+    @property
+    def nn(self) -> int:
+        return (self.N + 1) ** 3
+
+    @property
+    def ndof(self) -> int:
+        return self.K * self.nn * 5
+
+    def c(self) -> _Params:
+        p = _Params()
+        p.n, p.N, p.L, p.dt, p.bdf = self.n, self.N, self.L, self.dt, self.bdf
+        p.gamma, p.Pr, p.Re, p.Ma, p.Ts = self.gamma, self.Pr, self.Re, self.Ma, self.Ts
+        p.sutherland, p.model, p.viscous = int(self.sutherland), self.model, int(self.viscous)
+        p.adv = (ctypes.c_double * 3)(*self.adv)
+        p.nu, p.roe_delta, p.with_time = self.nu, self.roe_delta, int(self.with_time)
+        return p
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.POINTER(_Params)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.or_gl.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.or_lagrange.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+        L.or_lifting.argtypes = [P, dp, dp]
+        L.or_residual.argtypes = [P, dp, dp, dp, dp]
+        L.or_jvp.argtypes = [P, dp, dp, dp]
+        L.or_jacobian_coo.argtypes = [P, dp, ctypes.c_long, ip, ip, dp]
+        L.or_jacobian_coo.restype = ctypes.c_long
+        L.or_jacobian_elem_rows.argtypes = [P, dp, ctypes.c_int, ip, dp]
+        L.or_num_flux.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp]
+        L.or_phys_flux.argtypes = [P, dp, dp, ctypes.c_int, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def gl(N: int):
+    """Gauss-Lobatto nodes, weights and derivative matrix D[a, i] = l_i'(xi_a)."""
+    xi = np.zeros(N + 1); w = np.zeros(N + 1); D = np.zeros((N + 1, N + 1))
+    if lib().or_gl(N, _dp(xi), _dp(w), _dp(D)) != 0:
+        raise ValueError("bad N")
+    return xi, w, D
+
+
+def lagrange(N: int, i: int, x: float):
+    v = ctypes.c_double(); d = ctypes.c_double()
+    lib().or_lagrange(N, i, x, ctypes.byref(v), ctypes.byref(d))
+    return v.value, d.value
+
+
+def lifting(p: Params, Q: np.ndarray) -> np.ndarray:
+    Q = _f64(Q)
+    g = np.zeros((p.K, p.nn, 3, 5))
+    lib().or_lifting(ctypes.byref(p.c()), _dp(Q), _dp(g))
+    return g
+
+
+def residual(p: Params, Q: np.ndarray, Qs: np.ndarray | None = None, Qsm1: np.ndarray | None = None) -> np.ndarray:
+    """R(Q) of eq. NeqtonEq, shape [K, nn, 5]."""
+    Q = _f64(Q)
+    Qs = Q if Qs is None else _f64(Qs)
+    Qsm1 = Qs if Qsm1 is None else _f64(Qsm1)
+    R = np.zeros((p.K, p.nn, 5))
+    lib().or_residual(ctypes.byref(p.c()), _dp(Q), _dp(Qs), _dp(Qsm1), _dp(R))
+    return R
+
+
+def jvp(p: Params, Q: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """(dR/dQ)(Q) x, shape [K, nn, 5]."""
+    Q = _f64(Q); x = _f64(x)
+    y = np.zeros((p.K, p.nn, 5))
+    lib().or_jvp(ctypes.byref(p.c()), _dp(Q), _dp(x), _dp(y))
+    return y
+
+
+def jacobian(p: Params, Q: np.ndarray):
+    """Global Jacobian A = dR/dQ as a scipy CSR matrix (global dof order)."""
+    import scipy.sparse as sp
+    Q = _f64(Q)
+    ne = p.nn * 5
+    cap = int(p.K * 27 * ne * ne * 0.6) + 1024
+    while True:
+        rows = np.zeros(cap, np.int32); cols = np.zeros(cap, np.int32); vals = np.zeros(cap)
+        nnz = lib().or_jacobian_coo(ctypes.byref(p.c()), _dp(Q), cap, _ip(rows), _ip(cols), _dp(vals))
+        if nnz <= cap:
+            break
+        cap = int(nnz)
+    A = sp.csr_matrix((vals[:nnz], (rows[:nnz], cols[:nnz])), shape=(p.ndof, p.ndof))
+    A.sum_duplicates()
+    return A
+
+
+def jacobian_element_rows(p: Params, Q: np.ndarray, e: int):
+    """Rows of element e: dict {column element c: dense block [nn*5, nn*5]} (natural order)."""
+    Q = _f64(Q)
+    ne = p.nn * 5
+    elems = np.zeros(27, np.int32)
+    blocks = np.zeros((27, ne, ne))
+    cnt = lib().or_jacobian_elem_rows(ctypes.byref(p.c()), _dp(Q), e, _ip(elems), _dp(blocks))
+    return {int(elems[i]): blocks[i].copy() for i in range(cnt)}
+
+
+def num_flux(p: Params, qL, qR, d: int, s: int) -> np.ndarray:
+    f = np.zeros(5)
+    lib().or_num_flux(ctypes.byref(p.c()), _dp(_f64(qL)), _dp(_f64(qR)), d, s, _dp(f))
+    return f
+
+
+def phys_flux(p: Params, q, g, d: int):
+    fa = np.zeros(5); fv = np.zeros(5)
+    lib().or_phys_flux(ctypes.byref(p.c()), _dp(_f64(q)), _dp(_f64(g)), d, _dp(fa), _dp(fv))
+    return fa, fv
+
+
+from .linalg import (  # noqa: E402
+    boundary_interior_split, condensed_operator, condensed_solve, global_solve, gmres,
+    ratio_formula,
+)

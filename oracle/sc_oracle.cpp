@@ -1,0 +1,712 @@
+// FP64 CPU oracle for the statically condensed GL-DGSEM Newton system.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product library links or calls this
+// file; only the tests, the smoke check and the CPU-baseline leg of the benchmark
+// load it.  It shares no code, header or table with the CUDA path.
+//
+// What it computes (all in double precision, straight from the paper's equations):
+//   * Gauss-Lobatto nodes and weights and the Lagrange basis (App. C, eqs. mapping,
+//     quadRule; discrete orthogonality l_i(xi_j) = delta_ij).
+//   * The weak-form GL-DGSEM residual of Sec. 2.1, eq. DGSEMsystem:
+//       lifting   J_m w_m g_m = - sum_n J w_n q_n grad phi_m(x_n) + int phi_m qhat n dS
+//       outer eq  R_j = J_j w_j dQ/dt - sum_m J w_m F(q_m, g_m) . grad phi_j(x_m)
+//                       + int fhat phi_j dS
+//     with F = f^a - f^nu (App. B), fhat = Roe(q+, q-, n) - BR1 average of f^nu . n,
+//     qhat = (q+ + q-)/2 (BR1), and a BDF1/BDF2 time term (eqs. ImplicitDisc,
+//     NeqtonEq).
+//   * The Jacobian A = dR/dQ of eq. NewtonLinSys1 by forward-mode dual numbers
+//     (exact to rounding), column node by column node, and the Jacobian-vector
+//     product A x with a one-direction dual.
+// The condensation itself (Sec. 2.2 eqs. StaticCondBlock, SC_step1, SC_step2) lives
+// in oracle/linalg.py on top of these matrices.
+//
+// Readings of the paper used here:
+//   * nondimensionalisation rho_inf = V_inf = L_inf = T_inf = 1, p_inf = 1/(gamma Ma^2),
+//     T = gamma Ma^2 p / rho, kappa = mu / ((gamma-1) Pr Ma^2)  (App. B, kappa);
+//   * Stokes stress tau = mu (grad v + grad v^T) - (2/3) mu (div v) I (App. B);
+//   * Sutherland mu = (1+S)/(T+S) T^(3/2), S = T_suth / T_inf (App. B);
+//   * Roe flux with Roe averages and Harten's entropy fix on every wave,
+//     |lambda| -> (lambda^2 + delta^2)/(2 delta) for |lambda| < delta,
+//     delta = roe_delta * c_roe (the paper names Roe without details).
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------- dual numbers
+template <int ND>
+struct Dual {
+  double v;
+  double d[ND];
+  Dual() : v(0.0) { for (int i = 0; i < ND; ++i) d[i] = 0.0; }
+  Dual(double x) : v(x) { for (int i = 0; i < ND; ++i) d[i] = 0.0; }
+};
+
+template <int ND> inline Dual<ND> operator+(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r; r.v = a.v + b.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int ND> inline Dual<ND> operator-(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r; r.v = a.v - b.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+template <int ND> inline Dual<ND> operator-(const Dual<ND>& a) {
+  Dual<ND> r; r.v = -a.v; for (int i = 0; i < ND; ++i) r.d[i] = -a.d[i]; return r; }
+template <int ND> inline Dual<ND> operator*(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r; r.v = a.v * b.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+template <int ND> inline Dual<ND> operator/(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r; r.v = a.v / b.v; const double ib = 1.0 / (b.v * b.v);
+  for (int i = 0; i < ND; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) * ib;
+  return r; }
+template <int ND> inline Dual<ND> operator+(const Dual<ND>& a, double b) { Dual<ND> r = a; r.v += b; return r; }
+template <int ND> inline Dual<ND> operator+(double b, const Dual<ND>& a) { return a + b; }
+template <int ND> inline Dual<ND> operator-(const Dual<ND>& a, double b) { Dual<ND> r = a; r.v -= b; return r; }
+template <int ND> inline Dual<ND> operator-(double b, const Dual<ND>& a) { return (-a) + b; }
+template <int ND> inline Dual<ND> operator*(const Dual<ND>& a, double b) {
+  Dual<ND> r; r.v = a.v * b; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b; return r; }
+template <int ND> inline Dual<ND> operator*(double b, const Dual<ND>& a) { return a * b; }
+template <int ND> inline Dual<ND> operator/(const Dual<ND>& a, double b) { return a * (1.0 / b); }
+template <int ND> inline Dual<ND> operator/(double a, const Dual<ND>& b) { return Dual<ND>(a) / b; }
+template <int ND> inline Dual<ND>& operator+=(Dual<ND>& a, const Dual<ND>& b) { a = a + b; return a; }
+template <int ND> inline Dual<ND>& operator-=(Dual<ND>& a, const Dual<ND>& b) { a = a - b; return a; }
+template <int ND> inline Dual<ND> sqrt(const Dual<ND>& a) {
+  Dual<ND> r; r.v = std::sqrt(a.v); const double s = 0.5 / r.v;
+  for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * s;
+  return r; }
+
+inline double val(double x) { return x; }
+template <int ND> inline double val(const Dual<ND>& x) { return x.v; }
+using std::sqrt;
+
+}  // namespace
+
+extern "C" {
+struct or_params {
+  int n;            // elements per direction (periodic n^3 mesh)
+  int N;            // polynomial order
+  double L;         // box side
+  double dt;        // time step
+  int bdf;          // 1 or 2
+  double gamma, Pr, Re, Ma, Ts;  // Ts = T_sutherland / T_inf
+  int sutherland;   // 1: Sutherland viscosity, 0: mu = 1
+  int model;        // 0: Navier-Stokes; 1: five copies of linear advection-diffusion
+  int viscous;      // 0 drops the viscous flux (Euler / pure advection)
+  double adv[3];    // advection speed of model 1
+  double nu;        // diffusivity of model 1
+  double roe_delta; // entropy-fix width as a fraction of the Roe sound speed
+  int with_time;    // 0 drops the time term (spatial operator H only)
+};
+}
+
+namespace {
+
+constexpr int NV = 5;
+
+// Gauss-Lobatto nodes/weights by Newton iteration on P_N' (App. C), Lagrange basis
+// values and derivatives from the product formula.
+struct Basis {
+  int N = 0, p = 0;
+  std::vector<double> xi, w;
+  std::vector<double> ell;   // ell[i*p + a] = l_i(xi_a)
+  std::vector<double> dell;  // dell[i*p + a] = l_i'(xi_a)
+  std::vector<double> eL, eR;  // l_i(-1), l_i(+1)
+};
+
+void legendre(int N, double x, double& P, double& dP, double& d2P) {
+  // Three-term recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}; the derivatives
+  // follow from P'_{k+1} = P'_{k-1} + (2k+1) P_k and its derivative.
+  double p0 = 1.0, p1 = x, dp0 = 0.0, dp1 = 1.0, d2p0 = 0.0, d2p1 = 0.0;
+  if (N == 0) { P = 1.0; dP = 0.0; d2P = 0.0; return; }
+  for (int k = 1; k < N; ++k) {
+    double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    double dp2 = dp0 + (2 * k + 1) * p1;
+    double d2p2 = d2p0 + (2 * k + 1) * dp1;
+    p0 = p1; p1 = p2; dp0 = dp1; dp1 = dp2; d2p0 = d2p1; d2p1 = d2p2;
+  }
+  P = p1; dP = dp1; d2P = d2p1;
+}
+
+double lagrange(const std::vector<double>& xi, int i, double x) {
+  double r = 1.0;
+  for (size_t m = 0; m < xi.size(); ++m)
+    if ((int)m != i) r *= (x - xi[m]) / (xi[i] - xi[m]);
+  return r;
+}
+
+double lagrange_deriv(const std::vector<double>& xi, int i, double x) {
+  // d/dx prod_{m != i} (x - xi_m)/(xi_i - xi_m) by the product rule.
+  double s = 0.0;
+  for (size_t k = 0; k < xi.size(); ++k) {
+    if ((int)k == i) continue;
+    double t = 1.0 / (xi[i] - xi[k]);
+    for (size_t m = 0; m < xi.size(); ++m)
+      if ((int)m != i && m != k) t *= (x - xi[m]) / (xi[i] - xi[m]);
+    s += t;
+  }
+  return s;
+}
+
+Basis make_basis(int N) {
+  Basis b; b.N = N; b.p = N + 1;
+  b.xi.assign(N + 1, 0.0); b.w.assign(N + 1, 0.0);
+  b.xi[0] = -1.0; b.xi[N] = 1.0;
+  const double pi = 3.14159265358979323846;
+  for (int k = 1; k < N; ++k) {
+    double x = -std::cos(pi * k / N);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP, d2P; legendre(N, x, P, dP, d2P);
+      double dx = dP / d2P;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    b.xi[k] = x;
+  }
+  for (int k = 0; k <= N / 2; ++k) {  // symmetrise
+    double a = 0.5 * (b.xi[N - k] - b.xi[k]);
+    b.xi[k] = -a; b.xi[N - k] = a;
+  }
+  if (N % 2 == 0) b.xi[N / 2] = 0.0;
+  for (int k = 0; k <= N; ++k) {
+    double P, dP, d2P; legendre(N, b.xi[k], P, dP, d2P);
+    b.w[k] = 2.0 / (N * (N + 1) * P * P);
+  }
+  const int p = b.p;
+  b.ell.resize(p * p); b.dell.resize(p * p); b.eL.resize(p); b.eR.resize(p);
+  for (int i = 0; i < p; ++i) {
+    for (int a = 0; a < p; ++a) {
+      b.ell[i * p + a] = lagrange(b.xi, i, b.xi[a]);
+      b.dell[i * p + a] = lagrange_deriv(b.xi, i, b.xi[a]);
+    }
+    b.eL[i] = lagrange(b.xi, i, -1.0);
+    b.eR[i] = lagrange(b.xi, i, 1.0);
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------- physics (App. B)
+template <class T>
+void adv_flux(const or_params& P, const T* q, int d, T* f) {
+  if (P.model == 1) {
+    for (int k = 0; k < NV; ++k) f[k] = q[k] * P.adv[d];
+    return;
+  }
+  const double g = P.gamma;
+  T rho = q[0];
+  T vel[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  T p = (g - 1.0) * (q[4] - 0.5 * rho * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]));
+  f[0] = q[1 + d];
+  for (int i = 0; i < 3; ++i) f[1 + i] = q[1 + i] * vel[d];
+  f[1 + d] += p;
+  f[4] = vel[d] * (q[4] + p);
+}
+
+template <class T>
+T viscosity(const or_params& P, const T& Tmp) {
+  if (!P.sutherland) return T(1.0);
+  const double S = P.Ts;
+  return (1.0 + S) / (Tmp + S) * Tmp * sqrt(Tmp);
+}
+
+// Viscous flux f^nu_d(q, g), g[a*NV + k] = d q_k / d x_a.
+template <class T>
+void visc_flux(const or_params& P, const T* q, const T* g, int d, T* f) {
+  if (!P.viscous) { for (int k = 0; k < NV; ++k) f[k] = T(0.0); return; }
+  if (P.model == 1) {
+    for (int k = 0; k < NV; ++k) f[k] = P.nu * g[d * NV + k];
+    return;
+  }
+  const double gm = P.gamma;
+  T rho = q[0];
+  T vel[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  T E = q[4] / rho;
+  // gradients of primitive quantities from gradients of conserved ones
+  T dv[3][3];  // dv[a][i] = d u_i / d x_a
+  T dE[3];
+  for (int a = 0; a < 3; ++a) {
+    for (int i = 0; i < 3; ++i) dv[a][i] = (g[a * NV + 1 + i] - vel[i] * g[a * NV + 0]) / rho;
+    dE[a] = (g[a * NV + 4] - E * g[a * NV + 0]) / rho;
+  }
+  T e = E - 0.5 * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+  // T = gamma Ma^2 p / rho with p = (gamma-1) rho e
+  T Tmp = gm * (gm - 1.0) * P.Ma * P.Ma * e;
+  T mu = viscosity(P, Tmp);
+  T dT[3];
+  for (int a = 0; a < 3; ++a) {
+    T de = dE[a] - (vel[0] * dv[a][0] + vel[1] * dv[a][1] + vel[2] * dv[a][2]);
+    dT[a] = gm * (gm - 1.0) * P.Ma * P.Ma * de;
+  }
+  T kappa = mu / ((gm - 1.0) * P.Pr * P.Ma * P.Ma);
+  T div = dv[0][0] + dv[1][1] + dv[2][2];
+  T tau[3];  // tau_{d i}
+  for (int i = 0; i < 3; ++i) {
+    tau[i] = mu * (dv[d][i] + dv[i][d]);
+    if (i == d) tau[i] = tau[i] - (2.0 / 3.0) * mu * div;
+  }
+  const double iRe = 1.0 / P.Re;
+  f[0] = T(0.0);
+  for (int i = 0; i < 3; ++i) f[1 + i] = iRe * tau[i];
+  f[4] = iRe * (vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kappa * dT[d]);
+}
+
+template <class T>
+T abs_fixed(const T& lam, const T& delta) {
+  // Harten's entropy fix: |lambda| below delta is replaced by a parabola.
+  if (std::fabs(val(lam)) >= val(delta)) return val(lam) >= 0 ? lam : -lam;
+  return (lam * lam + delta * delta) / (2.0 * delta);
+}
+
+// Advective numerical flux fhat^a(q+, q-, n) . n with n = s e_d (outward for q+).
+template <class T>
+void num_flux_adv(const or_params& P, const T* qL, const T* qR, int d, int s, T* fh) {
+  T fL[NV], fR[NV];
+  adv_flux(P, qL, d, fL);
+  adv_flux(P, qR, d, fR);
+  if (P.model == 1) {
+    double an = P.adv[d] * s;
+    for (int k = 0; k < NV; ++k)
+      fh[k] = 0.5 * (double)s * (fL[k] + fR[k]) - 0.5 * std::fabs(an) * (qR[k] - qL[k]);
+    return;
+  }
+  const double g = P.gamma;
+  T rL = qL[0], rR = qR[0];
+  T uL[3] = {qL[1] / rL, qL[2] / rL, qL[3] / rL};
+  T uR[3] = {qR[1] / rR, qR[2] / rR, qR[3] / rR};
+  T pL = (g - 1.0) * (qL[4] - 0.5 * rL * (uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2]));
+  T pR = (g - 1.0) * (qR[4] - 0.5 * rR * (uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2]));
+  T HL = (qL[4] + pL) / rL, HR = (qR[4] + pR) / rR;
+  T sL = sqrt(rL), sR = sqrt(rR);
+  T den = sL + sR;
+  T ut[3];
+  for (int i = 0; i < 3; ++i) ut[i] = (sL * uL[i] + sR * uR[i]) / den;
+  T Ht = (sL * HL + sR * HR) / den;
+  T q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  T ct = sqrt((g - 1.0) * (Ht - 0.5 * q2));
+  T rt = sL * sR;
+  T unt = ut[d] * (double)s;
+  T drho = rR - rL, dp = pR - pL;
+  T du[3] = {uR[0] - uL[0], uR[1] - uL[1], uR[2] - uL[2]};
+  T dun = du[d] * (double)s;
+  T c2 = ct * ct;
+  T a1 = (dp - rt * ct * dun) / (2.0 * c2);
+  T a2 = drho - dp / c2;
+  T a5 = (dp + rt * ct * dun) / (2.0 * c2);
+  T delta = P.roe_delta * ct;
+  T l1 = abs_fixed(unt - ct, delta);
+  T l2 = abs_fixed(unt, delta);
+  T l5 = abs_fixed(unt + ct, delta);
+  double n[3] = {0.0, 0.0, 0.0}; n[d] = (double)s;
+  T dut[3];  // tangential velocity jump
+  for (int i = 0; i < 3; ++i) dut[i] = du[i] - dun * n[i];
+  T utdut = ut[0] * dut[0] + ut[1] * dut[1] + ut[2] * dut[2];
+  T diss[NV];
+  // acoustic wave u - c
+  diss[0] = l1 * a1;
+  for (int i = 0; i < 3; ++i) diss[1 + i] = l1 * a1 * (ut[i] - ct * n[i]);
+  diss[4] = l1 * a1 * (Ht - ct * unt);
+  // entropy wave
+  diss[0] += l2 * a2;
+  for (int i = 0; i < 3; ++i) diss[1 + i] += l2 * a2 * ut[i];
+  diss[4] += l2 * a2 * (0.5 * q2);
+  // shear waves
+  for (int i = 0; i < 3; ++i) diss[1 + i] += l2 * rt * dut[i];
+  diss[4] += l2 * rt * utdut;
+  // acoustic wave u + c
+  diss[0] += l5 * a5;
+  for (int i = 0; i < 3; ++i) diss[1 + i] += l5 * a5 * (ut[i] + ct * n[i]);
+  diss[4] += l5 * a5 * (Ht + ct * unt);
+  for (int k = 0; k < NV; ++k) fh[k] = 0.5 * (double)s * (fL[k] + fR[k]) - 0.5 * diss[k];
+}
+
+// ---------------------------------------------------------------- mesh + discretisation
+struct Disc {
+  or_params P;
+  Basis B;
+  int n, N, p, nn, K;
+  double h, J, Jf, dx;  // J = (h/2)^3 volume Jacobian, Jf = (h/2)^2 face Jacobian, dx = 2/h metric
+  explicit Disc(const or_params& pp) : P(pp) {
+    n = P.n; N = P.N; p = N + 1; nn = p * p * p; K = n * n * n;
+    B = make_basis(N);
+    h = P.L / n; J = std::pow(0.5 * h, 3); Jf = std::pow(0.5 * h, 2); dx = 2.0 / h;
+  }
+  int node(int i, int j, int k) const { return i + p * (j + p * k); }
+  void coords(int m, int c[3]) const { c[0] = m % p; c[1] = (m / p) % p; c[2] = m / (p * p); }
+  int elem(int ex, int ey, int ez) const {
+    ex = ((ex % n) + n) % n; ey = ((ey % n) + n) % n; ez = ((ez % n) + n) % n;
+    return ex + n * (ey + n * ez);
+  }
+  void ecoords(int e, int c[3]) const { c[0] = e % n; c[1] = (e / n) % n; c[2] = e / (n * n); }
+  int neighbor(int e, int d, int s) const {
+    int c[3]; ecoords(e, c); c[d] += s; return elem(c[0], c[1], c[2]);
+  }
+};
+
+// State accessor: the global double-precision state, with the five variables of one
+// node seeded as the dual directions (Jacobian columns) or a direction vector (JVP).
+template <class T>
+struct Access {
+  const Disc* D; const double* Q; int se = -1, sn = -1;
+  T get(int e, int m, int k) const { return T(Q[((size_t)e * D->nn + m) * NV + k]); }
+};
+template <int ND>
+struct Access<Dual<ND>> {
+  const Disc* D; const double* Q; int se = -1, sn = -1; const double* dir = nullptr;
+  Dual<ND> get(int e, int m, int k) const {
+    Dual<ND> t(Q[((size_t)e * D->nn + m) * NV + k]);
+    if (dir) { t.d[0] = dir[((size_t)e * D->nn + m) * NV + k]; }
+    else if (e == se && m == sn && k < ND) t.d[k] = 1.0;
+    return t;
+  }
+};
+
+// Value of the element's polynomial at a face point (face d, side s, in-face node
+// indices fb, fc): sum over nodes of q_n phi_n(x), reduced with l_i(xi_j) = delta_ij
+// in the two in-face directions.
+template <class T, class A>
+void trace(const Disc& D, const A& acc, int e, int d, int s, int fb, int fc, T* out) {
+  const std::vector<double>& edge = (s > 0) ? D.B.eR : D.B.eL;
+  for (int k = 0; k < NV; ++k) out[k] = T(0.0);
+  int db = (d + 1) % 3, dc = (d + 2) % 3;
+  for (int a = 0; a < D.p; ++a) {
+    double phi = edge[a];
+    if (phi == 0.0) continue;
+    int c[3]; c[d] = a; c[db] = fb; c[dc] = fc;
+    int m = D.node(c[0], c[1], c[2]);
+    for (int k = 0; k < NV; ++k) out[k] += phi * acc.get(e, m, k);
+  }
+}
+
+// Weak-form lifting (eq. DGSEMsystem:2): g[m][a][k] for every node m of element e.
+template <class T, class A>
+void lifting(const Disc& D, const A& acc, int e, T* g /* nn*3*NV */) {
+  const Basis& B = D.B;
+  const int p = D.p;
+  for (int m = 0; m < D.nn; ++m) {
+    int cm[3]; D.coords(m, cm);
+    T s3[3][NV];
+    for (int a = 0; a < 3; ++a) for (int k = 0; k < NV; ++k) s3[a][k] = T(0.0);
+    // volume: - sum_n J w_n q_n d_a phi_m(x_n)
+    for (int nidx = 0; nidx < D.nn; ++nidx) {
+      int cn[3]; D.coords(nidx, cn);
+      double wn = B.w[cn[0]] * B.w[cn[1]] * B.w[cn[2]];
+      double e0 = B.ell[cm[0] * p + cn[0]], e1 = B.ell[cm[1] * p + cn[1]], e2 = B.ell[cm[2] * p + cn[2]];
+      double d0 = B.dell[cm[0] * p + cn[0]], d1 = B.dell[cm[1] * p + cn[1]], d2 = B.dell[cm[2] * p + cn[2]];
+      double gp[3] = {D.dx * d0 * e1 * e2, D.dx * e0 * d1 * e2, D.dx * e0 * e1 * d2};
+      if (gp[0] == 0.0 && gp[1] == 0.0 && gp[2] == 0.0) continue;
+      for (int k = 0; k < NV; ++k) {
+        T qn = acc.get(e, nidx, k);
+        for (int a = 0; a < 3; ++a)
+          if (gp[a] != 0.0) s3[a][k] -= (D.J * wn * gp[a]) * qn;
+      }
+    }
+    // surface: int phi_m qhat n dS over the six faces
+    for (int d = 0; d < 3; ++d) {
+      int db = (d + 1) % 3, dc = (d + 2) % 3;
+      for (int s = -1; s <= 1; s += 2) {
+        const std::vector<double>& edge = (s > 0) ? B.eR : B.eL;
+        double phin = edge[cm[d]];
+        if (phin == 0.0) continue;
+        int fb = cm[db], fc = cm[dc];  // face point co-located with m in-face
+        double wf = B.w[fb] * B.w[fc];
+        T qp[NV], qm[NV];
+        trace(D, acc, e, d, s, fb, fc, qp);
+        int nb = D.neighbor(e, d, s);
+        trace(D, acc, nb, d, -s, fb, fc, qm);
+        for (int k = 0; k < NV; ++k) {
+          T qhat = 0.5 * (qp[k] + qm[k]);
+          s3[d][k] += (D.Jf * wf * phin * (double)s) * qhat;
+        }
+      }
+    }
+    double wm = B.w[cm[0]] * B.w[cm[1]] * B.w[cm[2]];
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < NV; ++k) g[((size_t)m * 3 + a) * NV + k] = s3[a][k] / (D.J * wm);
+  }
+}
+
+// Residual rows of element e (eq. DGSEMsystem:1 plus the time term).  gsrc(e') must
+// return the lifted gradient array of element e'.
+template <class T, class A, class G>
+void elem_residual(const Disc& D, const A& acc, int e, const G& gsrc,
+                   const double* Qs, const double* Qsm1, T* R /* nn*NV */) {
+  const Basis& B = D.B;
+  const int p = D.p;
+  const size_t gsz = (size_t)D.nn * 3 * NV;
+  std::vector<T> g(gsz);
+  { const T* gp = gsrc(e); for (size_t x = 0; x < gsz; ++x) g[x] = gp[x]; }
+  // fluxes F_d = f^a_d - f^nu_d at every node
+  std::vector<T> F((size_t)D.nn * 3 * NV);
+  for (int m = 0; m < D.nn; ++m) {
+    T q[NV];
+    for (int k = 0; k < NV; ++k) q[k] = acc.get(e, m, k);
+    for (int d = 0; d < 3; ++d) {
+      T fa[NV], fv[NV];
+      adv_flux(D.P, q, d, fa);
+      visc_flux(D.P, q, &g[(size_t)m * 3 * NV], d, fv);
+      for (int k = 0; k < NV; ++k) F[((size_t)m * 3 + d) * NV + k] = fa[k] - fv[k];
+    }
+  }
+  for (int j = 0; j < D.nn; ++j) {
+    int cj[3]; D.coords(j, cj);
+    double wj = B.w[cj[0]] * B.w[cj[1]] * B.w[cj[2]];
+    T r[NV];
+    for (int k = 0; k < NV; ++k) r[k] = T(0.0);
+    if (D.P.with_time) {
+      for (int k = 0; k < NV; ++k) {
+        size_t idx = ((size_t)e * D.nn + j) * NV + k;
+        T qj = acc.get(e, j, k);
+        if (D.P.bdf == 2)
+          r[k] = (D.J * wj / D.P.dt) * (1.5 * qj - 2.0 * Qs[idx] + 0.5 * Qsm1[idx]);
+        else
+          r[k] = (D.J * wj / D.P.dt) * (qj - Qs[idx]);
+      }
+    }
+    // volume: - sum_m J w_m F(m) . grad phi_j(x_m)
+    for (int m = 0; m < D.nn; ++m) {
+      int cm[3]; D.coords(m, cm);
+      double e0 = B.ell[cj[0] * p + cm[0]], e1 = B.ell[cj[1] * p + cm[1]], e2 = B.ell[cj[2] * p + cm[2]];
+      double d0 = B.dell[cj[0] * p + cm[0]], d1 = B.dell[cj[1] * p + cm[1]], d2 = B.dell[cj[2] * p + cm[2]];
+      double gp[3] = {D.dx * d0 * e1 * e2, D.dx * e0 * d1 * e2, D.dx * e0 * e1 * d2};
+      if (gp[0] == 0.0 && gp[1] == 0.0 && gp[2] == 0.0) continue;
+      double wm = B.w[cm[0]] * B.w[cm[1]] * B.w[cm[2]];
+      for (int d = 0; d < 3; ++d) {
+        if (gp[d] == 0.0) continue;
+        for (int k = 0; k < NV; ++k) r[k] -= (D.J * wm * gp[d]) * F[((size_t)m * 3 + d) * NV + k];
+      }
+    }
+    // surface: int fhat phi_j dS
+    for (int d = 0; d < 3; ++d) {
+      int db = (d + 1) % 3, dc = (d + 2) % 3;
+      for (int s = -1; s <= 1; s += 2) {
+        const std::vector<double>& edge = (s > 0) ? B.eR : B.eL;
+        const std::vector<double>& edgeo = (s > 0) ? B.eL : B.eR;
+        double phin = edge[cj[d]];
+        if (phin == 0.0) continue;
+        int fb = cj[db], fc = cj[dc];
+        double wf = B.w[fb] * B.w[fc];
+        int nb = D.neighbor(e, d, s);
+        T qp[NV], qm[NV];
+        trace(D, acc, e, d, s, fb, fc, qp);
+        trace(D, acc, nb, d, -s, fb, fc, qm);
+        // lifted gradients are nodal polynomials too; trace them the same way
+        T gpl[3 * NV], gmi[3 * NV];
+        for (int x = 0; x < 3 * NV; ++x) { gpl[x] = T(0.0); gmi[x] = T(0.0); }
+        const T* gn = gsrc(nb);
+        for (int a = 0; a < p; ++a) {
+          int c[3]; c[db] = fb; c[dc] = fc; c[d] = a;
+          int m = D.node(c[0], c[1], c[2]);
+          if (edge[a] != 0.0)
+            for (int x = 0; x < 3 * NV; ++x) gpl[x] += edge[a] * g[(size_t)m * 3 * NV + x];
+          if (edgeo[a] != 0.0)
+            for (int x = 0; x < 3 * NV; ++x) gmi[x] += edgeo[a] * gn[(size_t)m * 3 * NV + x];
+        }
+        T fa[NV], fvp[NV], fvm[NV];
+        num_flux_adv(D.P, qp, qm, d, s, fa);
+        visc_flux(D.P, qp, gpl, d, fvp);
+        visc_flux(D.P, qm, gmi, d, fvm);
+        for (int k = 0; k < NV; ++k) {
+          T fhat = fa[k] - 0.5 * (double)s * (fvp[k] + fvm[k]);
+          r[k] += (D.Jf * wf * phin) * fhat;
+        }
+      }
+    }
+    for (int k = 0; k < NV; ++k) R[(size_t)j * NV + k] = r[k];
+  }
+}
+
+// Distinct elements of the 3x3x3 block of elements around e (periodic wrap).
+int neighborhood(const Disc& D, int e, int* out) {
+  int c[3]; D.ecoords(e, c); int cnt = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dxx = -1; dxx <= 1; ++dxx) {
+        int x = D.elem(c[0] + dxx, c[1] + dy, c[2] + dz);
+        bool seen = false;
+        for (int i = 0; i < cnt; ++i) seen |= (out[i] == x);
+        if (!seen) out[cnt++] = x;
+      }
+  return cnt;
+}
+
+// Derivatives of the rows of the elements rows_e[0..nrow) with respect to the five
+// variables of node r of element c: out[i] holds dR_{rows_e[i]}/dq_{c,r} as duals.
+void column_node(const Disc& D, const double* Q, const std::vector<double>& g0,
+                 int c, int r, const int* rows_e, int nrow,
+                 std::vector<std::vector<Dual<5>>>& out) {
+  using T = Dual<5>;
+  Access<T> acc{&D, Q}; acc.se = c; acc.sn = r;
+  // Lifted gradients depend on the seed only in c and its face neighbours.
+  int N1[7]; int cnt = 0; N1[cnt++] = c;
+  for (int d = 0; d < 3; ++d)
+    for (int s = -1; s <= 1; s += 2) {
+      int nb = D.neighbor(c, d, s); bool seen = false;
+      for (int i = 0; i < cnt; ++i) seen |= (N1[i] == nb);
+      if (!seen) N1[cnt++] = nb;
+    }
+  const size_t gsz = (size_t)D.nn * 3 * NV;
+  std::vector<T> gseed((size_t)cnt * gsz);
+  for (int i = 0; i < cnt; ++i) lifting<T>(D, acc, N1[i], gseed.data() + (size_t)i * gsz);
+  // Unseeded elements carry the base gradients with zero derivative.  elem_residual
+  // copies its own element's gradients first and then asks for one neighbour at a
+  // time, so one promotion buffer suffices.
+  std::vector<T> slot(gsz);
+  auto gsrc = [&](int ee) -> const T* {
+    for (int t = 0; t < cnt; ++t) if (N1[t] == ee) return gseed.data() + (size_t)t * gsz;
+    for (size_t x = 0; x < gsz; ++x) slot[x] = T(g0[(size_t)ee * gsz + x]);
+    return slot.data();
+  };
+  out.resize(nrow);
+  for (int i = 0; i < nrow; ++i) {
+    out[i].resize((size_t)D.nn * NV);
+    elem_residual<T>(D, acc, rows_e[i], gsrc, Q, Q, out[i].data());
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int or_gl(int N, double* xi, double* w, double* Dm) {
+  if (N < 1 || N > 16) return 1;
+  Basis b = make_basis(N);
+  int p = N + 1;
+  for (int i = 0; i < p; ++i) { xi[i] = b.xi[i]; w[i] = b.w[i]; }
+  if (Dm)
+    for (int a = 0; a < p; ++a)
+      for (int i = 0; i < p; ++i) Dm[a * p + i] = b.dell[i * p + a];  // D[a][i] = l_i'(xi_a)
+  return 0;
+}
+
+int or_lagrange(int N, int i, double x, double* value, double* deriv) {
+  if (N < 1 || i < 0 || i > N) return 1;
+  Basis b = make_basis(N);
+  *value = lagrange(b.xi, i, x);
+  *deriv = lagrange_deriv(b.xi, i, x);
+  return 0;
+}
+
+// Lifted gradients of every element: g[K][nn][3][5].
+int or_lifting(const or_params* P, const double* Q, double* g) {
+  Disc D(*P);
+  Access<double> acc{&D, Q};
+#pragma omp parallel for schedule(dynamic)
+  for (int e = 0; e < D.K; ++e) lifting<double>(D, acc, e, g + (size_t)e * D.nn * 3 * NV);
+  return 0;
+}
+
+// Residual R(Q) of every element: R[K][nn][5].
+int or_residual(const or_params* P, const double* Q, const double* Qs, const double* Qsm1, double* R) {
+  Disc D(*P);
+  Access<double> acc{&D, Q};
+  std::vector<double> g((size_t)D.K * D.nn * 3 * NV);
+#pragma omp parallel for schedule(dynamic)
+  for (int e = 0; e < D.K; ++e) lifting<double>(D, acc, e, g.data() + (size_t)e * D.nn * 3 * NV);
+  auto gsrc = [&](int ee) { return (const double*)(g.data() + (size_t)ee * D.nn * 3 * NV); };
+#pragma omp parallel for schedule(dynamic)
+  for (int e = 0; e < D.K; ++e)
+    elem_residual<double>(D, acc, e, gsrc, Qs, Qsm1 ? Qsm1 : Qs, R + (size_t)e * D.nn * NV);
+  return 0;
+}
+
+// Jacobian-vector product y = (dR/dQ) x with a one-direction dual.
+int or_jvp(const or_params* P, const double* Q, const double* x, double* y) {
+  Disc D(*P);
+  using T = Dual<1>;
+  Access<T> acc{&D, Q}; acc.dir = x;
+  std::vector<T> g((size_t)D.K * D.nn * 3 * NV);
+#pragma omp parallel for schedule(dynamic)
+  for (int e = 0; e < D.K; ++e) lifting<T>(D, acc, e, g.data() + (size_t)e * D.nn * 3 * NV);
+  auto gsrc = [&](int ee) { return (const T*)(g.data() + (size_t)ee * D.nn * 3 * NV); };
+#pragma omp parallel for schedule(dynamic)
+  for (int e = 0; e < D.K; ++e) {
+    std::vector<T> R((size_t)D.nn * NV);
+    elem_residual<T>(D, acc, e, gsrc, Q, Q, R.data());
+    for (size_t i = 0; i < R.size(); ++i) y[(size_t)e * D.nn * NV + i] = R[i].d[0];
+  }
+  return 0;
+}
+
+// Full Jacobian in COO form: rows/cols are global dof indices (e*nn + node)*5 + var.
+// Returns the number of non-zeros; nothing beyond cap is written.
+long or_jacobian_coo(const or_params* P, const double* Q, long cap, int* rows, int* cols, double* vals) {
+  Disc D(*P);
+  std::vector<double> g0((size_t)D.K * D.nn * 3 * NV);
+  or_lifting(P, Q, g0.data());
+  std::vector<std::vector<long>> R_(D.K), C_(D.K);
+  std::vector<std::vector<double>> V_(D.K);
+#pragma omp parallel for schedule(dynamic)
+  for (int c = 0; c < D.K; ++c) {
+    int nbh[27]; int cnt = neighborhood(D, c, nbh);
+    std::vector<std::vector<Dual<5>>> Rr;
+    for (int r = 0; r < D.nn; ++r) {
+      column_node(D, Q, g0, c, r, nbh, cnt, Rr);
+      for (int i = 0; i < cnt; ++i) {
+        int e = nbh[i];
+        for (int j = 0; j < D.nn; ++j)
+          for (int v = 0; v < NV; ++v)
+            for (int k = 0; k < NV; ++k) {
+              double a = Rr[i][(size_t)j * NV + v].d[k];
+              if (a == 0.0) continue;
+              R_[c].push_back(((long)e * D.nn + j) * NV + v);
+              C_[c].push_back(((long)c * D.nn + r) * NV + k);
+              V_[c].push_back(a);
+            }
+      }
+    }
+  }
+  long total = 0;
+  for (int c = 0; c < D.K; ++c)
+    for (size_t i = 0; i < R_[c].size(); ++i) {
+      if (total < cap) { rows[total] = (int)R_[c][i]; cols[total] = (int)C_[c][i]; vals[total] = V_[c][i]; }
+      ++total;
+    }
+  return total;
+}
+
+// Rows of element e only: for each distinct element c of the 3x3x3 neighbourhood,
+// the dense block dR_e/dQ_c (nn*5 x nn*5, natural order, row-major).
+// Returns the number of blocks written (<= 27); col_elems receives their elements.
+int or_jacobian_elem_rows(const or_params* P, const double* Q, int e, int* col_elems, double* blocks) {
+  Disc D(*P);
+  std::vector<double> g0((size_t)D.K * D.nn * 3 * NV);
+  or_lifting(P, Q, g0.data());
+  int nbh[27]; int cnt = neighborhood(D, e, nbh);
+  const int ne = D.nn * NV;
+#pragma omp parallel for schedule(dynamic)
+  for (int i = 0; i < cnt; ++i) {
+    int c = nbh[i];
+    col_elems[i] = c;
+    double* blk = blocks + (size_t)i * ne * ne;
+    std::vector<std::vector<Dual<5>>> Rr;
+    for (int r = 0; r < D.nn; ++r) {
+      column_node(D, Q, g0, c, r, &e, 1, Rr);
+      for (int j = 0; j < D.nn; ++j)
+        for (int v = 0; v < NV; ++v)
+          for (int k = 0; k < NV; ++k)
+            blk[(size_t)(j * NV + v) * ne + r * NV + k] = Rr[0][(size_t)j * NV + v].d[k];
+    }
+  }
+  return cnt;
+}
+
+// The fluxes on their own, for the flux pins.
+int or_num_flux(const or_params* P, const double* qL, const double* qR, int d, int s, double* fa) {
+  num_flux_adv<double>(*P, qL, qR, d, s, fa);
+  return 0;
+}
+int or_phys_flux(const or_params* P, const double* q, const double* g, int d, double* fa, double* fv) {
+  adv_flux<double>(*P, q, d, fa);
+  visc_flux<double>(*P, q, g, d, fv);
+  return 0;
+}
+int or_num_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+}  // extern "C"

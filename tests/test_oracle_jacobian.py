@@ -1,0 +1,106 @@
+"""Pins of the oracle Jacobian A = dR/dQ (eq. NewtonLinSys1) and its structure (Sec. 3.1)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import sc_inputs as I
+
+
+@pytest.fixture(scope="module")
+def tgv_small():
+    n, N = 3, 2
+    Q, dt = I.tgv_state(n, N, eps=1e-2)
+    p = O.Params(n=n, N=N, dt=dt)
+    return p, Q, O.jacobian(p, Q)
+
+
+def test_jacobian_matches_central_differences(tgv_small):
+    p, Q, A = tgv_small
+    rng = np.random.default_rng(1)
+    for _ in range(2):
+        x = rng.standard_normal(Q.shape)
+        y = (A @ x.reshape(-1)).reshape(Q.shape)
+        h = 1e-5
+        fd = (O.residual(p, Q + h * x, Q) - O.residual(p, Q - h * x, Q)) / (2 * h)
+        assert np.abs(y - fd).max() / np.abs(y).max() < 1e-8
+
+
+def test_jvp_equals_matrix(tgv_small):
+    p, Q, A = tgv_small
+    x = np.random.default_rng(2).standard_normal(Q.shape)
+    y = (A @ x.reshape(-1)).reshape(Q.shape)
+    np.testing.assert_allclose(O.jvp(p, Q, x), y, rtol=0, atol=1e-12 * np.abs(y).max())
+
+
+def test_time_term_is_the_mass_matrix(tgv_small):
+    p, Q, A = tgv_small
+    ps = O.Params(**{**p.__dict__, "with_time": False})
+    As = O.jacobian(ps, Q)
+    _, w, _ = O.gl(p.N)
+    h = p.L / p.n
+    W = np.einsum("i,j,k->kji", w, w, w).reshape(-1)
+    Mdiag = np.repeat(np.tile((h / 2) ** 3 * W, p.K), 5) / p.dt
+    D = (A - As).toarray()
+    np.testing.assert_allclose(np.diag(D), Mdiag, rtol=1e-12)
+    assert np.abs(D - np.diag(np.diag(D))).max() < 1e-12 * Mdiag.max()
+    p2 = O.Params(**{**p.__dict__, "bdf": 2})
+    A2 = O.jacobian(p2, Q)
+    np.testing.assert_allclose(np.diag((A2 - As).toarray()), 1.5 * Mdiag, rtol=1e-12)
+
+
+def test_conservation_of_column_sums(tgv_small):
+    # sum over all rows of one variable of dH/dq_r vanishes (H's rows sum to zero for
+    # every state on a periodic mesh, so do their derivatives).
+    p, Q, _ = tgv_small
+    ps = O.Params(**{**p.__dict__, "with_time": False})
+    H = O.jacobian(ps, Q)
+    cs = np.zeros((5, H.shape[1]))
+    Hc = H.tocoo()
+    np.add.at(cs, (Hc.row % 5, Hc.col), Hc.data)
+    assert np.abs(cs).max() < 1e-11 * np.abs(H.data).max()
+
+
+def _classify(n, N):
+    In, Bn, I_, B_ = O.boundary_interior_split(n, N)
+    K = n ** 3
+    nn = (N + 1) ** 3
+    is_b = np.zeros(K * nn * 5, bool)
+    is_b[B_.reshape(-1)] = True
+    elem = np.arange(K * nn * 5) // (nn * 5)
+    return is_b, elem
+
+
+@pytest.mark.parametrize("viscous", [True, False])
+def test_sparsity_structure(viscous):
+    # Sec. 3.1 summary: off-diagonal (element-to-element) entries need j AND r on the
+    # boundary (advective case) or j OR r on the boundary (diffusive case), so A_ii is
+    # block diagonal.  The corner neighbours never couple (stencil of Roe + BR1).
+    n, N = 3, 3
+    Q, dt = I.tgv_state(n, N, eps=1e-2)
+    p = O.Params(n=n, N=N, dt=dt, viscous=viscous)
+    A = O.jacobian(p, Q).tocoo()
+    is_b, elem = _classify(n, N)
+    off = elem[A.row] != elem[A.col]
+    rb, cb = is_b[A.row[off]], is_b[A.col[off]]
+    assert off.sum() > 0
+    assert np.all(rb | cb)                      # never interior-interior across elements
+    if not viscous:
+        assert np.all(rb & cb)                  # advective: boundary-boundary only
+    else:
+        assert np.any(rb & ~cb) and np.any(~rb & cb)
+    # element-level stencil: face and edge neighbours only
+    def ec(e):
+        return np.stack([e % n, (e // n) % n, e // (n * n)], -1)
+    d = np.abs(ec(elem[A.row[off]]) - ec(elem[A.col[off]]))
+    d = np.minimum(d, n - d)
+    hops = d.sum(-1)
+    assert hops.max() == (2 if viscous else 1)
+
+
+def test_linear_model_jacobian_is_state_independent():
+    n, N = 2, 2
+    p = O.Params(n=n, N=N, model=1, adv=(0.7, -0.3, 0.2), nu=0.05, dt=0.3)
+    rng = np.random.default_rng(4)
+    A1 = O.jacobian(p, rng.standard_normal((n ** 3, (N + 1) ** 3, 5)))
+    A2 = O.jacobian(p, rng.standard_normal((n ** 3, (N + 1) ** 3, 5)))
+    assert abs(A1 - A2).max() < 1e-13 * abs(A1).max()
