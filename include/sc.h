@@ -1,0 +1,148 @@
+/*
+ * sc.h -- C ABI of the GB300 statically condensed GL-DGSEM Newton solver.
+ *
+ * One Newton linear system of the time-implicit GL-DGSEM discretisation of the 3D
+ * compressible Navier-Stokes equations (Roe advective flux, BR1 viscous flux) on a
+ * periodic Cartesian mesh, solved by static condensation on one GPU:
+ *
+ *   A dQ = B,  A = dR/dQ,  B = -R(Q)                       (Sec. 2.1, eq. NewtonLinSys1)
+ *   [A_bb A_bi; A_ib A_ii] [Q_b; Q_i] = [B_b; B_i]          (Sec. 3.1, eq. StaticDGSEM_QbQiSystem)
+ *   (A_bb - A_bi A_ii^-1 A_ib) Q_b = B_b - A_bi A_ii^-1 B_i (Sec. 2.2, eq. SC_step1)
+ *   Q_i = A_ii^-1 (B_i - A_ib Q_b)                          (Sec. 2.2, eq. SC_step2)
+ *
+ * Index convention ("row-column"): A_bi has rows on element boundaries and columns
+ * in element interiors; A_ib the reverse.  (The paper's names swap the two.)
+ *
+ * Global dof order of every vector crossing this ABI: element-major
+ * (e = ex + n*(ey + n*ez)), then node (i + (N+1)*(j + (N+1)*k), i fastest), then the
+ * conserved variable (rho, rho u, rho v, rho w, rho E) innermost.  All vectors are
+ * double precision.  The boundary/interior permutation is internal.
+ *
+ * Ownership: the caller owns every array it passes; the library owns all device
+ * storage it allocates (Jacobian blocks, factors, Krylov space) and frees it in
+ * sc_destroy.  Every call returns an sc_status and never aborts; on failure
+ * sc_last_error() describes the cause.  All device work is enqueued on the stream
+ * given to sc_create; calls return after that stream has finished the call's work
+ * unless stated otherwise.  A context is not thread safe.
+ */
+#ifndef SC_H
+#define SC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sc_ctx sc_ctx;
+
+typedef enum {
+  SC_OK = 0,
+  SC_ERR_ARG = 1,            /* invalid argument (null pointer, size out of range) */
+  SC_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  SC_ERR_OOM = 3,            /* device allocation failed */
+  SC_ERR_STATE = 4,          /* calls made out of order (e.g. solve before condense) */
+  SC_ERR_SINGULAR_BLOCK = 5, /* a zero pivot in an element block factorisation */
+  SC_ERR_NONFINITE = 6,      /* a NaN/Inf appeared in a result */
+  SC_ERR_NOT_CONVERGED = 7   /* GMRES / refinement did not reach the tolerance */
+} sc_status;
+
+enum { SC_PREC_FP64 = 0, SC_PREC_MIXED = 1 };
+enum { SC_PC_BLOCK_JACOBI = 0, SC_PC_NONE = 1 };
+
+/* Physics and solver settings (App. B parameters; solver choices of the build). */
+typedef struct {
+  double gamma;          /* heat capacity ratio (1.4) */
+  double Pr;             /* Prandtl number (0.72) */
+  double Re;             /* reference Reynolds number */
+  double Ma;             /* reference Mach number */
+  double Ts;             /* Sutherland temperature / reference temperature (110.4/288.15) */
+  int sutherland;        /* 1: Sutherland viscosity law, 0: mu = 1 */
+  double roe_delta;      /* Harten entropy-fix width as a fraction of the Roe sound speed (0.05) */
+  int precision;         /* SC_PREC_FP64 or SC_PREC_MIXED */
+  int precond;           /* SC_PC_BLOCK_JACOBI or SC_PC_NONE */
+  int gmres_restart;     /* Krylov dimension per cycle (e.g. 30) */
+  int gmres_max_iters;   /* total iteration cap */
+  int max_refine;        /* mixed arm: cap on FP64 refinement sweeps */
+  double rel_tol;        /* target ||B - A dQ||_2 / ||B||_2 on the global system (1e-8) */
+  double inner_tol;      /* mixed arm: relative tolerance of each inner condensed solve */
+} sc_config;
+
+/* Per-solve statistics filled by sc_solve. */
+typedef struct {
+  int gmres_iters;          /* total GMRES iterations */
+  int refinements;          /* FP64 refinement sweeps (mixed arm), 0 for FP64 */
+  double rel_residual;      /* ||B - A dQ||_2 / ||B||_2 recomputed in FP64 after the solve */
+  double cond_rel_residual; /* last condensed residual estimate / ||B||_2 */
+  double ms_rhs, ms_gmres, ms_backsub, ms_refine;  /* device time per phase */
+  int first_bad_element;    /* first element with a singular block, or -1 */
+} sc_solve_stats;
+
+/* Fill *cfg with the defaults listed above (Re = 1600, Ma = 0.1, FP64, block Jacobi,
+   GMRES(30), 4000 iterations, rel_tol 1e-8).  Never fails for a non-null cfg. */
+sc_status sc_default_config(sc_config* cfg);
+
+/* Create a context that enqueues all work on `cuda_stream` (a cudaStream_t, or NULL
+   for the legacy default stream) of the current device.  *out receives the handle. */
+sc_status sc_create(const sc_config* cfg, void* cuda_stream, sc_ctx** out);
+
+/* Release every device and host resource of the context.  Null is ignored. */
+void sc_destroy(sc_ctx* ctx);
+
+/* Human-readable description of the last failure of this context ("" if none). */
+const char* sc_last_error(const sc_ctx* ctx);
+
+/* Mesh and order (App. C): periodic n x n x n Cartesian hexahedra on [0, L]^3,
+   polynomial order N in every element (2 <= N <= 4 and 1 <= n <= 32 in this build).  Allocates
+   all per-mesh device storage; invalidates any previous state and Jacobian. */
+sc_status sc_set_mesh(sc_ctx* ctx, int n, double L, int N);
+
+/* Physical coordinates [K][(N+1)^3][3] of the Gauss-Lobatto nodes (host array). */
+sc_status sc_node_coords(sc_ctx* ctx, double* xyz);
+
+/* Newton iterate Q and the time history (eq. ImplicitDisc): Qs = Q at time level s,
+   Qsm1 = level s-1 (only read for BDF2; may be NULL for BDF1).  Arrays hold
+   K*(N+1)^3*5 doubles in global dof order; on_device != 0 means device pointers. */
+sc_status sc_set_state(sc_ctx* ctx, const double* Q, const double* Qs, const double* Qsm1,
+                       int on_device);
+
+/* Time step and scheme: bdf = 1 (backward Euler) or 2 (BDF2, needs Qsm1). */
+sc_status sc_set_timestep(sc_ctx* ctx, double dt, int bdf);
+
+/* Residual B = -R(Q) (eq. NeqtonEq) and the Jacobian A = dR/dQ (Sec. 2.1.1-2.1.2):
+   dense per-element blocks plus the structured neighbour couplings. */
+sc_status sc_assemble(sc_ctx* ctx);
+
+/* Static condensation set-up (Sec. 3.2): A_ii^-1 per element, the element Schur
+   blocks S_ee = A_bb,ee - A_bi,ee A_ii^-1 A_ib,ee and their LU factors (the block-Jacobi
+   preconditioner of the condensed solve). */
+sc_status sc_condense(sc_ctx* ctx);
+
+/* Solve A dQ = B: condensed right-hand side (eq. SC_step1), right-preconditioned
+   restarted GMRES on S, back-substitution (eq. SC_step2), then the FP64 global residual
+   ||B - A dQ|| / ||B||.  The mixed arm wraps this in FP64 iterative refinement.
+   dQ receives K*(N+1)^3*5 doubles (device pointer if on_device).  stats may be NULL.
+   Returns SC_ERR_NOT_CONVERGED (dQ still written) if rel_tol is not met. */
+sc_status sc_solve(sc_ctx* ctx, double* dQ, int on_device, sc_solve_stats* stats);
+
+/* B = -R(Q) from the last sc_assemble (copy out). */
+sc_status sc_get_rhs(sc_ctx* ctx, double* B, int on_device);
+
+/* y = A x with the assembled FP64 Jacobian (global dof order). */
+sc_status sc_apply_jacobian(sc_ctx* ctx, const double* x, double* y, int on_device);
+
+/* Element e's rows of A restricted to the columns of element c (natural node order,
+   row-major (N+1)^3*5 square, host array).  c must be e or a face/edge neighbour of e;
+   the block sums every coupling between the two elements.  Test hook. */
+sc_status sc_get_jacobian_block(sc_ctx* ctx, int e, int c, double* block);
+
+/* y_b = S x_b with the condensed operator (boundary dof vectors of length
+   K * 5 * (number of boundary nodes), ordered element-major, then boundary node in
+   natural order, then variable).  Device pointers.  Test hook. */
+sc_status sc_condensed_matvec(sc_ctx* ctx, const double* xb, double* yb);
+
+/* Sizes: number of elements, dofs per element, interior and boundary dofs per element. */
+sc_status sc_sizes(const sc_ctx* ctx, int* K, int* ne, int* ni, int* nb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SC_H */

@@ -1,0 +1,541 @@
+// C-ABI entry points (include/sc.h) and host orchestration of the condensed solve.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <tuple>
+
+#include "sc_internal.cuh"
+
+namespace sc {
+cudaError_t launch_history(sc_ctx* c, const double* Qs, const double* Qsm1);
+}
+
+namespace {
+
+#define SC_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t _e = (call);                                                            \
+    if (_e != cudaSuccess) return fail(c, SC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+sc_status fail(sc_ctx* c, sc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+// Gauss-Lobatto nodes: interior nodes are the roots of q(x) = P_{N+1}(x) - P_{N-1}(x)
+// found by Newton's method; weights 2 / (N (N+1) P_N(x)^2).
+void legendre_q(int N, double x, double& q, double& dq, double& LN) {
+  double l0 = 1.0, l1 = x, d0 = 0.0, d1 = 1.0;
+  double lm1 = 1.0, dm1 = 0.0;  // P_{N-1}, P'_{N-1}
+  for (int k = 1; k <= N; ++k) {
+    const double l2 = ((2 * k + 1) * x * l1 - k * l0) / (k + 1);
+    const double d2 = d0 + (2 * k + 1) * l1;
+    if (k == N - 1) { lm1 = l1; dm1 = d1; }
+    l0 = l1; l1 = l2; d0 = d1; d1 = d2;
+  }
+  // now l1 = P_{N+1}, l0 = P_N
+  if (N == 1) { lm1 = 1.0; dm1 = 0.0; }
+  q = l1 - lm1;
+  dq = d1 - dm1;
+  LN = l0;
+}
+
+void gauss_lobatto(int N, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(N + 1, 0.0); w.assign(N + 1, 0.0);
+  x[0] = -1.0; x[N] = 1.0;
+  const double pi = 3.14159265358979323846;
+  // Newton from the left half only (a right-half start can fall onto the root x = 1
+  // of q); the right half follows by symmetry.
+  for (int j = 1; j <= N / 2; ++j) {
+    double xx = -std::cos((j + 0.25) * pi / N - 3.0 / (8.0 * N * pi * (j + 0.25)));
+    for (int it = 0; it < 60; ++it) {
+      double q, dq, LN; legendre_q(N, xx, q, dq, LN);
+      const double dx = q / dq;
+      xx -= dx;
+      if (std::fabs(dx) < 1e-16 * std::max(1.0, std::fabs(xx))) break;
+    }
+    x[j] = xx;
+    x[N - j] = -xx;
+  }
+  if (N % 2 == 0) x[N / 2] = 0.0;
+  for (int j = 0; j <= N; ++j) {
+    double q, dq, LN; legendre_q(N, x[j], q, dq, LN);
+    w[j] = 2.0 / (N * (N + 1) * LN * LN);
+  }
+}
+
+// Differentiation matrix from barycentric weights: D_ij = (b_j/b_i)/(x_i - x_j),
+// D_ii = -sum_{j != i} D_ij.
+void diff_matrix(const std::vector<double>& x, double D[SC_MAXP][SC_MAXP]) {
+  const int p = (int)x.size();
+  std::vector<double> b(p, 1.0);
+  for (int j = 0; j < p; ++j)
+    for (int k = 0; k < p; ++k)
+      if (k != j) b[j] /= (x[j] - x[k]);
+  for (int i = 0; i < p; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < p; ++j) {
+      if (j == i) continue;
+      D[i][j] = (b[j] / b[i]) / (x[i] - x[j]);
+      s += D[i][j];
+    }
+    D[i][i] = -s;
+  }
+}
+
+void free_all(sc_ctx* c) {
+  double** dps[] = {&c->Q, &c->Qh, &c->grad, &c->F, &c->B, &c->NJ, &c->RJ, &c->Aown, &c->X, &c->Ainv,
+                    &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
+                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull};
+  for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
+  int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
+                 &c->d_pids, &c->piv, &c->d_status};
+  for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) { return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)); }
+
+void build_pattern(sc_ctx* c) {
+  const Geo& G = c->G;
+  const int p = G.p, N = G.N, nn = G.nn;
+  auto idx = [&](int i, int j, int k) { return i + p * (j + p * k); };
+  auto crd = [&](int m, int cc[3]) { cc[0] = m % p; cc[1] = (m / p) % p; cc[2] = m / (p * p); };
+  std::set<std::tuple<int, int, int>> S;  // (row node, slot, col node)
+  for (int d = 0; d < 3; ++d)
+    for (int s = -1; s <= 1; s += 2) {
+      const int slot = face_slot(d, s), jend = s > 0 ? N : 0, nend = N - jend;
+      for (int m = 0; m < nn; ++m) {
+        int cm[3]; crd(m, cm);
+        if (cm[d] != jend) continue;
+        int cr[3] = {cm[0], cm[1], cm[2]}; cr[d] = nend;
+        const int r = idx(cr[0], cr[1], cr[2]);
+        // e's rows reaching face node m through their grid lines (own lifting)
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < p; ++b) {
+            int cj[3] = {cm[0], cm[1], cm[2]}; cj[a] = b;
+            S.insert({idx(cj[0], cj[1], cj[2]), slot, r});
+          }
+        // face row m: neighbour nodes on the grid lines through its partner r
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < p; ++b) {
+            int cx[3] = {cr[0], cr[1], cr[2]}; cx[a] = b;
+            S.insert({m, slot, idx(cx[0], cx[1], cx[2])});
+          }
+      }
+    }
+  for (int pi = 0; pi < 3; ++pi) {
+    const int d1 = pi == 2 ? 1 : 0, d2 = pi == 0 ? 1 : 2, d3 = 3 - d1 - d2;
+    for (int q = 0; q < 4; ++q) {
+      const int s1 = (q & 2) ? 1 : -1, s2 = (q & 1) ? 1 : -1;
+      const int slot = 6 + 4 * pi + q;
+      for (int b = 0; b < p; ++b) {
+        int cj[3]; cj[d1] = s1 > 0 ? N : 0; cj[d2] = s2 > 0 ? N : 0; cj[d3] = b;
+        int cr[3] = {cj[0], cj[1], cj[2]}; cr[d1] = N - cj[d1]; cr[d2] = N - cj[d2];
+        S.insert({idx(cj[0], cj[1], cj[2]), slot, idx(cr[0], cr[1], cr[2])});
+      }
+    }
+  }
+  Pattern& P = c->pat;
+  P.row.clear(); P.slot.clear(); P.col.clear();
+  for (auto& t : S) { P.row.push_back(std::get<0>(t)); P.slot.push_back(std::get<1>(t)); P.col.push_back(std::get<2>(t)); }
+  const int np = (int)P.row.size();
+  P.ptr.assign(nn + 1, 0);
+  for (int i = 0; i < np; ++i) P.ptr[P.row[i] + 1]++;
+  for (int i = 0; i < nn; ++i) P.ptr[i + 1] += P.ptr[i];
+  P.ids.assign(np, 0);
+  std::vector<int> fill(P.ptr.begin(), P.ptr.end() - 1);
+  for (int i = 0; i < np; ++i) P.ids[fill[P.row[i]]++] = i;
+  c->G.NP = np;
+}
+
+sc_status check(sc_ctx* c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, SC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, SC_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  return SC_OK;
+}
+
+double dnorm2(sc_ctx* c, const double* v, size_t n, double* hd_slot) {
+  sc::multidot(c, v, 1, n, v, hd_slot);
+  double h = 0.0;
+  cudaMemcpyAsync(&h, hd_slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return std::sqrt(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sc_default_config(sc_config* cfg) {
+  if (!cfg) return SC_ERR_ARG;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->gamma = 1.4; cfg->Pr = 0.72; cfg->Re = 1600.0; cfg->Ma = 0.1;
+  cfg->Ts = 110.4 / 288.15; cfg->sutherland = 1; cfg->roe_delta = 0.05;
+  cfg->precision = SC_PREC_FP64; cfg->precond = SC_PC_BLOCK_JACOBI;
+  cfg->gmres_restart = 30; cfg->gmres_max_iters = 4000; cfg->max_refine = 10;
+  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4;
+  return SC_OK;
+}
+
+sc_status sc_create(const sc_config* cfg, void* cuda_stream, sc_ctx** out) {
+  if (!cfg || !out) return SC_ERR_ARG;
+  if (cfg->gmres_restart < 1 || cfg->gmres_restart > 60 || cfg->gmres_max_iters < 1 || !(cfg->rel_tol > 0) ||
+      !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->gamma > 1) || !(cfg->Pr > 0))
+    return SC_ERR_ARG;
+  if (cfg->precision != SC_PREC_FP64 && cfg->precision != SC_PREC_MIXED) return SC_ERR_ARG;
+  sc_ctx* c = new sc_ctx();
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)cuda_stream;
+  for (auto& e : c->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) { delete c; return SC_ERR_CUDA; }
+  }
+  *out = c;
+  return SC_OK;
+}
+
+void sc_destroy(sc_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  for (auto& e : c->ev) if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* sc_last_error(const sc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
+  if (!c) return SC_ERR_ARG;
+  if (n < 1 || n > 32 || N < 2 || N > 4 || !(L > 0)) return fail(c, SC_ERR_ARG, "mesh: need n in [1,32], N in [2,4], L > 0");
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  c->has_mesh = c->has_state = c->assembled = c->condensed = false;
+  Geo& G = c->G;
+  G = Geo{};
+  G.n = n; G.N = N; G.p = N + 1; G.nn = G.p * G.p * G.p; G.K = n * n * n;
+  G.nin = (N - 1) * (N - 1) * (N - 1); G.nbn = G.nn - G.nin;
+  G.ne = 5 * G.nn; G.ni = 5 * G.nin; G.nb = 5 * G.nbn;
+  c->L = L;
+  G.h = L / n; G.Jf = 0.25 * G.h * G.h; G.dx = 2.0 / G.h;
+  std::vector<double> w;
+  gauss_lobatto(N, c->xi, w);
+  for (int i = 0; i <= N; ++i) G.w[i] = w[i];
+  diff_matrix(c->xi, G.D);
+  G.inv_hw = 1.0 / (G.h * w[N]);
+  G.gamma = c->cfg.gamma; G.Pr = c->cfg.Pr; G.Re = c->cfg.Re; G.Ma = c->cfg.Ma; G.Ts = c->cfg.Ts;
+  G.roe_delta = c->cfg.roe_delta; G.sutherland = c->cfg.sutherland;
+  G.dt = 1.0; G.c0 = 1.0;
+  // node permutation: interior nodes first, then boundary nodes, each in natural order
+  const int p = G.p;
+  c->perm.assign(G.nn, 0); c->iperm.assign(G.nn, 0);
+  int ii = 0, bb = G.nin;
+  for (int m = 0; m < G.nn; ++m) {
+    const int i = m % p, j = (m / p) % p, k = m / (p * p);
+    const bool inner = i > 0 && i < N && j > 0 && j < N && k > 0 && k < N;
+    c->perm[m] = inner ? ii++ : bb++;
+  }
+  for (int m = 0; m < G.nn; ++m) c->iperm[c->perm[m]] = m;
+  // neighbour table
+  c->nbr.assign((size_t)G.K * 18, 0);
+  auto E = [&](int x, int y, int z) { x = (x % n + n) % n; y = (y % n + n) % n; z = (z % n + n) % n; return x + n * (y + n * z); };
+  for (int e = 0; e < G.K; ++e) {
+    const int ex = e % n, ey = (e / n) % n, ez = e / (n * n);
+    const int ce[3] = {ex, ey, ez};
+    for (int d = 0; d < 3; ++d)
+      for (int s = -1; s <= 1; s += 2) {
+        int cc[3] = {ce[0], ce[1], ce[2]}; cc[d] += s;
+        c->nbr[(size_t)e * 18 + face_slot(d, s)] = E(cc[0], cc[1], cc[2]);
+      }
+    for (int pi = 0; pi < 3; ++pi) {
+      const int d1 = pi == 2 ? 1 : 0, d2 = pi == 0 ? 1 : 2;
+      for (int q = 0; q < 4; ++q) {
+        int cc[3] = {ce[0], ce[1], ce[2]};
+        cc[d1] += (q & 2) ? 1 : -1; cc[d2] += (q & 1) ? 1 : -1;
+        c->nbr[(size_t)e * 18 + 6 + 4 * pi + q] = E(cc[0], cc[1], cc[2]);
+      }
+    }
+  }
+  build_pattern(c);
+  const size_t nodes = (size_t)G.K * G.nn, dofs = nodes * 5;
+  const size_t n1 = (size_t)G.K * G.nb;
+  const int m = c->cfg.gmres_restart;
+  c->restart_alloc = m;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(dalloc(&c->Q, dofs)); A(dalloc(&c->Qh, dofs)); A(dalloc(&c->B, dofs));
+  A(dalloc(&c->Xfull, dofs)); A(dalloc(&c->Rfull, dofs));
+  A(dalloc(&c->grad, nodes * 15)); A(dalloc(&c->F, nodes * 15));
+  A(dalloc(&c->NJ, nodes * 375)); A(dalloc(&c->RJ, (size_t)G.K * 6 * 50 * G.p * G.p));
+  A(dalloc(&c->Aown, (size_t)G.K * G.ne * G.ne)); A(dalloc(&c->X, (size_t)G.K * G.NP * 25));
+  A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ni)); A(dalloc(&c->Ytmp, (size_t)G.K * G.ni * G.nb));
+  A(dalloc(&c->See, (size_t)G.K * G.nb * G.nb)); A(dalloc(&c->piv, (size_t)G.K * G.nb));
+  A(dalloc(&c->V, n1 * (m + 1))); A(dalloc(&c->Wv, n1)); A(dalloc(&c->Zv, n1)); A(dalloc(&c->Xb, n1));
+  A(dalloc(&c->Gb, n1)); A(dalloc(&c->Rb, n1)); A(dalloc(&c->Tb, n1));
+  A(dalloc(&c->Ui, (size_t)G.K * G.ni)); A(dalloc(&c->Hd, 256)); A(dalloc(&c->partial, 608 * 64));
+  A(dalloc(&c->d_status, 1));
+  A(dalloc(&c->d_nbr, c->nbr.size())); A(dalloc(&c->d_perm, G.nn)); A(dalloc(&c->d_iperm, G.nn));
+  const int np = G.NP;
+  A(dalloc(&c->d_prow, np)); A(dalloc(&c->d_pslot, np)); A(dalloc(&c->d_pcol, np));
+  A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pids, np));
+  if (e != cudaSuccess) { free_all(c); cudaGetLastError(); return fail(c, SC_ERR_OOM, std::string("allocation: ") + cudaGetErrorString(e)); }
+  SC_CUDA(cudaMemcpy(c->d_nbr, c->nbr.data(), c->nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_perm, c->perm.data(), G.nn * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_iperm, c->iperm.data(), G.nn * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_prow, c->pat.row.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_pslot, c->pat.slot.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_pcol, c->pat.col.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_pptr, c->pat.ptr.data(), (G.nn + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_pids, c->pat.ids.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  c->has_mesh = true;
+  return SC_OK;
+}
+
+sc_status sc_sizes(const sc_ctx* c, int* K, int* ne, int* ni, int* nb) {
+  if (!c || !c->has_mesh) return SC_ERR_STATE;
+  if (K) *K = c->G.K;
+  if (ne) *ne = c->G.ne;
+  if (ni) *ni = c->G.ni;
+  if (nb) *nb = c->G.nb;
+  return SC_OK;
+}
+
+sc_status sc_node_coords(sc_ctx* c, double* xyz) {
+  if (!c || !xyz) return SC_ERR_ARG;
+  if (!c->has_mesh) return fail(c, SC_ERR_STATE, "node_coords before set_mesh");
+  const Geo& G = c->G;
+  for (int e = 0; e < G.K; ++e) {
+    const int ce[3] = {e % G.n, (e / G.n) % G.n, e / (G.n * G.n)};
+    for (int m = 0; m < G.nn; ++m) {
+      const int cm[3] = {m % G.p, (m / G.p) % G.p, m / (G.p * G.p)};
+      for (int a = 0; a < 3; ++a)
+        xyz[((size_t)e * G.nn + m) * 3 + a] = G.h * ce[a] + 0.5 * G.h * (1.0 + c->xi[cm[a]]);
+    }
+  }
+  return SC_OK;
+}
+
+sc_status sc_set_timestep(sc_ctx* c, double dt, int bdf) {
+  if (!c) return SC_ERR_ARG;
+  if (!(dt > 0) || (bdf != 1 && bdf != 2)) return fail(c, SC_ERR_ARG, "timestep: dt > 0, bdf in {1,2}");
+  c->G.dt = dt; c->bdf = bdf; c->G.c0 = bdf == 2 ? 1.5 : 1.0;
+  c->has_dt = true; c->assembled = c->condensed = false;
+  return SC_OK;
+}
+
+sc_status sc_set_state(sc_ctx* c, const double* Q, const double* Qs, const double* Qsm1, int on_device) {
+  if (!c || !Q || !Qs) return fail(c, SC_ERR_ARG, "set_state: Q and Qs required");
+  if (!c->has_mesh) return fail(c, SC_ERR_STATE, "set_state before set_mesh");
+  if (c->bdf == 2 && !Qsm1) return fail(c, SC_ERR_ARG, "set_state: BDF2 needs Qsm1");
+  const size_t n = (size_t)c->G.K * c->G.nn * 5, bytes = n * sizeof(double);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  SC_CUDA(cudaMemcpyAsync(c->Q, Q, bytes, kind, c->stream));
+  // the history combination is formed in Rfull/Xfull as scratch
+  SC_CUDA(cudaMemcpyAsync(c->Rfull, Qs, bytes, kind, c->stream));
+  if (Qsm1) SC_CUDA(cudaMemcpyAsync(c->Xfull, Qsm1, bytes, kind, c->stream));
+  SC_CUDA(sc::launch_history(c, c->Rfull, Qsm1 ? c->Xfull : c->Rfull));
+  sc_status s = check(c);
+  if (s != SC_OK) return s;
+  c->has_state = true; c->assembled = c->condensed = false;
+  return SC_OK;
+}
+
+sc_status sc_assemble(sc_ctx* c) {
+  if (!c) return SC_ERR_ARG;
+  if (!c->has_mesh || !c->has_state || !c->has_dt) return fail(c, SC_ERR_STATE, "assemble needs mesh, state and timestep");
+  SC_CUDA(sc::launch_residual(c));
+  SC_CUDA(sc::launch_assembly(c));
+  sc_status s = check(c);
+  if (s != SC_OK) return s;
+  c->assembled = true; c->condensed = false;
+  return SC_OK;
+}
+
+sc_status sc_condense(sc_ctx* c) {
+  if (!c) return SC_ERR_ARG;
+  if (!c->assembled) return fail(c, SC_ERR_STATE, "condense before assemble");
+  const int minus1 = -1;
+  SC_CUDA(cudaMemcpyAsync(c->d_status, &minus1, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  SC_CUDA(sc::launch_condense(c));
+  int bad = -1;
+  SC_CUDA(cudaMemcpyAsync(&bad, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  sc_status s = check(c);
+  if (s != SC_OK) return s;
+  if (bad >= 0) return fail(c, SC_ERR_SINGULAR_BLOCK, "singular element block in element " + std::to_string(bad));
+  c->condensed = true;
+  return SC_OK;
+}
+
+sc_status sc_get_rhs(sc_ctx* c, double* Bout, int on_device) {
+  if (!c || !Bout) return SC_ERR_ARG;
+  if (!c->assembled) return fail(c, SC_ERR_STATE, "get_rhs before assemble");
+  const size_t bytes = (size_t)c->G.K * c->G.ne * sizeof(double);
+  SC_CUDA(cudaMemcpyAsync(Bout, c->B, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  return check(c);
+}
+
+sc_status sc_apply_jacobian(sc_ctx* c, const double* x, double* y, int on_device) {
+  if (!c || !x || !y) return SC_ERR_ARG;
+  if (!c->assembled) return fail(c, SC_ERR_STATE, "apply_jacobian before assemble");
+  const size_t bytes = (size_t)c->G.K * c->G.ne * sizeof(double);
+  const double* xd = x;
+  if (!on_device) { SC_CUDA(cudaMemcpyAsync(c->Xfull, x, bytes, cudaMemcpyHostToDevice, c->stream)); xd = c->Xfull; }
+  double* yd = on_device ? y : c->Rfull;
+  SC_CUDA(sc::global_apply(c, xd, yd));
+  if (!on_device) SC_CUDA(cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, c->stream));
+  return check(c);
+}
+
+sc_status sc_get_jacobian_block(sc_ctx* c, int e, int col, double* block) {
+  if (!c || !block) return SC_ERR_ARG;
+  if (!c->assembled) return fail(c, SC_ERR_STATE, "get_jacobian_block before assemble");
+  const Geo& G = c->G;
+  if (e < 0 || e >= G.K || col < 0 || col >= G.K) return fail(c, SC_ERR_ARG, "element index out of range");
+  const int ne = G.ne;
+  std::vector<double> own((size_t)ne * ne), X((size_t)G.NP * 25);
+  SC_CUDA(cudaMemcpyAsync(own.data(), c->Aown + (size_t)e * ne * ne, own.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SC_CUDA(cudaMemcpyAsync(X.data(), c->X + (size_t)e * G.NP * 25, X.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  sc_status s = check(c);
+  if (s != SC_OK) return s;
+  std::fill(block, block + (size_t)ne * ne, 0.0);
+  if (col == e)
+    for (int j = 0; j < G.nn; ++j)
+      for (int r = 0; r < G.nn; ++r)
+        for (int k = 0; k < 5; ++k)
+          for (int l = 0; l < 5; ++l)
+            block[(size_t)(5 * j + k) * ne + 5 * r + l] = own[(size_t)(5 * c->perm[j] + k) * ne + 5 * c->perm[r] + l];
+  bool any = col == e;
+  for (int pr = 0; pr < G.NP; ++pr) {
+    if (c->nbr[(size_t)e * 18 + c->pat.slot[pr]] != col) continue;
+    any = true;
+    const int j = c->pat.row[pr], r = c->pat.col[pr];
+    for (int k = 0; k < 5; ++k)
+      for (int l = 0; l < 5; ++l) block[(size_t)(5 * j + k) * ne + 5 * r + l] += X[(size_t)pr * 25 + k * 5 + l];
+  }
+  if (!any) return fail(c, SC_ERR_ARG, "element c is not in the stencil of e");
+  return SC_OK;
+}
+
+sc_status sc_condensed_matvec(sc_ctx* c, const double* xb, double* yb) {
+  if (!c || !xb || !yb) return SC_ERR_ARG;
+  if (!c->condensed) return fail(c, SC_ERR_STATE, "condensed_matvec before condense");
+  SC_CUDA(sc::cond_interior(c, xb, 1.0, nullptr, 0.0, c->Ui));
+  SC_CUDA(sc::cond_boundary(c, xb, 1.0, nullptr, 0.0, c->Ui, yb));
+  return check(c);
+}
+
+sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
+  if (!c || !dQ) return SC_ERR_ARG;
+  if (!c->condensed) return fail(c, SC_ERR_STATE, "solve before condense");
+  const Geo& G = c->G;
+  const size_t n1 = (size_t)G.K * G.nb, dofs = (size_t)G.K * G.ne;
+  const int m = c->restart_alloc;
+  sc_solve_stats S{};
+  S.first_bad_element = -1;
+  cudaEvent_t* ev = c->ev;
+  SC_CUDA(cudaEventRecord(ev[0], c->stream));
+  // condensed right-hand side g = B_b - A_bi A_ii^-1 B_i   (eq. SC_step1)
+  SC_CUDA(sc::cond_interior(c, nullptr, 0.0, c->B, 1.0, c->Ui));
+  SC_CUDA(sc::cond_boundary(c, nullptr, 0.0, c->B, 1.0, c->Ui, c->Gb));
+  SC_CUDA(cudaEventRecord(ev[1], c->stream));
+  const double bnorm = dnorm2(c, c->B, dofs, c->Hd + 200);
+  const double target = c->cfg.rel_tol * bnorm;
+  // right-preconditioned restarted GMRES, x0 = 0
+  SC_CUDA(cudaMemsetAsync(c->Xb, 0, n1 * sizeof(double), c->stream));
+  SC_CUDA(cudaMemcpyAsync(c->Rb, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  double beta = dnorm2(c, c->Rb, n1, c->Hd + 200);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(160), y(m);
+  int iters = 0;
+  double resid = beta;
+  bool ok = beta <= target || bnorm == 0.0;
+  while (!ok && iters < c->cfg.gmres_max_iters) {
+    SC_CUDA(sc::vec_axpby(c, c->V, 1.0 / beta, c->Rb, 0.0, n1));
+    std::fill(gv.begin(), gv.end(), 0.0); gv[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m && iters < c->cfg.gmres_max_iters; ++j) {
+      double* Vj = c->V + (size_t)j * n1;
+      SC_CUDA(sc::precond_apply(c, Vj, c->Zv));
+      SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
+      SC_CUDA(sc::cond_boundary(c, c->Zv, 1.0, nullptr, 0.0, c->Ui, c->Wv));
+      // classical Gram-Schmidt, twice
+      SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, c->Hd));
+      SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, c->Hd, -1.0));
+      SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, c->Hd + 64));
+      SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, c->Hd + 64, -1.0));
+      SC_CUDA(sc::multidot(c, c->Wv, 1, n1, c->Wv, c->Hd + 128));
+      SC_CUDA(cudaMemcpyAsync(hbuf.data(), c->Hd, 129 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      SC_CUDA(cudaStreamSynchronize(c->stream));
+      double* Hc = &H[(size_t)j];  // column j, row stride m
+      for (int i = 0; i <= j; ++i) Hc[(size_t)i * m] = hbuf[i] + hbuf[64 + i];
+      const double hn = std::sqrt(std::max(hbuf[128], 0.0));
+      Hc[(size_t)(j + 1) * m] = hn;
+      if (!std::isfinite(hn)) return fail(c, SC_ERR_NONFINITE, "non-finite value in GMRES");
+      if (hn > 0) SC_CUDA(sc::vec_axpby(c, c->V + (size_t)(j + 1) * n1, 1.0 / hn, c->Wv, 0.0, n1));
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hc[(size_t)i * m] + sn[i] * Hc[(size_t)(i + 1) * m];
+        Hc[(size_t)(i + 1) * m] = -sn[i] * Hc[(size_t)i * m] + cs[i] * Hc[(size_t)(i + 1) * m];
+        Hc[(size_t)i * m] = t;
+      }
+      const double den = std::hypot(Hc[(size_t)j * m], Hc[(size_t)(j + 1) * m]);
+      cs[j] = Hc[(size_t)j * m] / den; sn[j] = Hc[(size_t)(j + 1) * m] / den;
+      Hc[(size_t)j * m] = den; Hc[(size_t)(j + 1) * m] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++iters; k = j + 1;
+      resid = std::fabs(gv[j + 1]);
+      if (resid <= target || hn == 0.0) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double s = gv[i];
+      for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    SC_CUDA(cudaMemcpyAsync(c->Hd, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    SC_CUDA(cudaMemsetAsync(c->Tb, 0, n1 * sizeof(double), c->stream));
+    SC_CUDA(sc::vec_update(c, c->Tb, c->V, k, n1, c->Hd, 1.0));
+    SC_CUDA(sc::precond_apply(c, c->Tb, c->Zv));
+    SC_CUDA(sc::vec_axpby(c, c->Xb, 1.0, c->Zv, 1.0, n1));
+    // true condensed residual r = g - S x
+    SC_CUDA(sc::cond_interior(c, c->Xb, 1.0, nullptr, 0.0, c->Ui));
+    SC_CUDA(sc::cond_boundary(c, c->Xb, 1.0, nullptr, 0.0, c->Ui, c->Wv));
+    SC_CUDA(cudaMemcpyAsync(c->Rb, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    SC_CUDA(sc::vec_axpby(c, c->Rb, -1.0, c->Wv, 1.0, n1));
+    beta = dnorm2(c, c->Rb, n1, c->Hd + 200);
+    resid = beta;
+    if (!std::isfinite(beta)) return fail(c, SC_ERR_NONFINITE, "non-finite condensed residual");
+    if (beta <= target) ok = true;
+  }
+  SC_CUDA(cudaEventRecord(ev[2], c->stream));
+  // back-substitution Q_i = A_ii^-1 (B_i - A_ib Q_b)   (eq. SC_step2)
+  SC_CUDA(sc::cond_interior(c, c->Xb, -1.0, c->B, 1.0, c->Ui));
+  double* xout = on_device ? dQ : c->Xfull;
+  SC_CUDA(sc::scatter_solution(c, c->Xb, c->Ui, xout));
+  SC_CUDA(cudaEventRecord(ev[3], c->stream));
+  // FP64 global residual ||B - A x|| / ||B||
+  SC_CUDA(sc::global_apply(c, xout, c->Rfull));
+  SC_CUDA(sc::vec_axpby(c, c->Rfull, 1.0, c->B, -1.0, dofs));
+  const double rn = dnorm2(c, c->Rfull, dofs, c->Hd + 200);
+  if (!on_device) SC_CUDA(cudaMemcpyAsync(dQ, xout, dofs * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  sc_status s = check(c);
+  if (s != SC_OK) return s;
+  float t01 = 0, t12 = 0, t23 = 0;
+  cudaEventElapsedTime(&t01, ev[0], ev[1]);
+  cudaEventElapsedTime(&t12, ev[1], ev[2]);
+  cudaEventElapsedTime(&t23, ev[2], ev[3]);
+  S.ms_rhs = t01; S.ms_gmres = t12; S.ms_backsub = t23;
+  S.gmres_iters = iters;
+  S.cond_rel_residual = bnorm > 0 ? resid / bnorm : 0.0;
+  S.rel_residual = bnorm > 0 ? rn / bnorm : 0.0;
+  if (st) *st = S;
+  if (!std::isfinite(S.rel_residual)) return fail(c, SC_ERR_NONFINITE, "non-finite solution");
+  if (S.rel_residual > c->cfg.rel_tol * 1.0000001 && !(bnorm == 0.0))
+    return fail(c, SC_ERR_NOT_CONVERGED, "relative residual " + std::to_string(S.rel_residual) + " above tolerance");
+  return SC_OK;
+}
+
+}  // extern "C"

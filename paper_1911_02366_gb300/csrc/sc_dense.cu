@@ -1,0 +1,366 @@
+// Batched dense linear algebra on the element blocks of the condensation
+// (Sec. 3.2, "Analysis and Implementation": dense A_ii blocks inverted element by
+// element, Schur products by matrix-matrix multiplication).
+//
+//   k_gj_inv    A_ii^-1 by Gauss-Jordan elimination with partial pivoting, one block
+//               per CTA held in shared memory.
+//   k_gemm      C = alpha A B + beta C for a batch of row-major blocks (SIMT, 64x64
+//               tiles, 4x4 register micro-tiles).
+//   k_lu        right-looking blocked LU with partial pivoting of a batch of blocks
+//               in global memory (32-column panels factorised in shared memory).
+//   k_lu_solve  z = (P^T L U)^-1 v for every element (one warp per element).
+#include "sc_internal.cuh"
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+// Warp argmax of |v| (ties: smallest index).
+__device__ __forceinline__ void warp_argmax(double& v, int& idx) {
+  for (int off = 16; off > 0; off >>= 1) {
+    double ov = __shfl_down_sync(0xffffffffu, v, off);
+    int oi = __shfl_down_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+}
+
+template <class T>
+__global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int lda,
+                         T* __restrict__ Ainv, long long strideO, int* __restrict__ status) {
+  extern __shared__ unsigned char smem_raw[];
+  const int ld = n + 1;
+  T* M = reinterpret_cast<T*>(smem_raw);
+  T* colk = M + (size_t)n * ld;
+  int* piv = reinterpret_cast<int*>(colk + n);
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  const int e = blockIdx.x;
+  const T* Ae = A + (long long)e * strideA;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t % n;
+    M[i * ld + j] = Ae[(long long)i * lda + j];
+  }
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x < 32) {
+      double best = -1.0; int bi = k;
+      for (int i = k + threadIdx.x; i < n; i += 32) {
+        const double v = (double)tabs(M[i * ld + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+      warp_argmax(best, bi);
+      if (threadIdx.x == 0) {
+        s_p = bi;
+        piv[k] = bi;
+        if (!(best > 0.0)) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        T t = M[k * ld + j]; M[k * ld + j] = M[p * ld + j]; M[p * ld + j] = t;
+      }
+    __syncthreads();
+    const T pinv = s_bad ? T(0) : T(1) / M[k * ld + k];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = M[i * ld + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) M[k * ld + j] = (j == k) ? pinv : M[k * ld + j] * pinv;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int i = t / n, j = t % n;
+      if (i == k) continue;
+      const T f = colk[i];
+      if (j == k) M[i * ld + j] = -f * pinv;
+      else M[i * ld + j] -= f * M[k * ld + j];
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        T t = M[i * ld + k]; M[i * ld + k] = M[i * ld + p]; M[i * ld + p] = t;
+      }
+    __syncthreads();
+  }
+  T* Oe = Ainv + (long long)e * strideO;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Oe[t] = M[(t / n) * ld + (t % n)];
+  if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
+}
+
+// C = alpha * A * B + beta * C, all row-major, one batch entry per blockIdx.z.
+template <class T>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, T alpha,
+                                              const T* __restrict__ A, long long sA, int lda,
+                                              const T* __restrict__ B, long long sB, int ldb, T beta,
+                                              T* __restrict__ C, long long sC, int ldc) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN];
+  const int z = blockIdx.z;
+  A += (long long)z * sA; B += (long long)z * sB; C += (long long)z * sC;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int t = threadIdx.x; t < BM * BK; t += 256) {
+      const int r = t / BK, c = t % BK;
+      const int gr = m0 + r, gc = k0 + c;
+      As[c][r] = (gr < M && gc < K) ? A[(long long)gr * lda + gc] : T(0);
+    }
+    for (int t = threadIdx.x; t < BK * BN; t += 256) {
+      const int r = t / BN, c = t % BN;
+      const int gr = k0 + r, gc = n0 + c;
+      Bs[r][c] = (gr < K && gc < N) ? B[(long long)gr * ldb + gc] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = m0 + ty + 16 * i;
+    if (gr >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = n0 + tx + 16 * j;
+      if (gc >= N) continue;
+      T* cp = C + (long long)gr * ldc + gc;
+      *cp = (beta == T(0)) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *cp;
+    }
+  }
+}
+
+// Copy a sub-block (rows x cols) of a batch of row-major matrices.
+template <class T>
+__global__ void k_copy_block(int rows, int cols, const T* __restrict__ src, long long sS, int lds,
+                             T* __restrict__ dst, long long sD, int ldd) {
+  const int z = blockIdx.y;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rows * cols; t += gridDim.x * blockDim.x) {
+    const int i = t / cols, j = t % cols;
+    dst[(long long)z * sD + (long long)i * ldd + j] = src[(long long)z * sS + (long long)i * lds + j];
+  }
+}
+
+constexpr int PW = 32;  // LU panel width
+
+template <class T>
+__global__ void __launch_bounds__(256) k_lu(int n, T* __restrict__ A, long long stride, int lda,
+                                            int* __restrict__ piv_all, int* __restrict__ status) {
+  extern __shared__ unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);  // panel [n][PW+1]
+  constexpr int pld = PW + 1;
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  const int e = blockIdx.x;
+  T* Mx = A + (long long)e * stride;
+  int* piv = piv_all + (long long)e * n;
+  if (threadIdx.x == 0) s_bad = 0;
+  for (int k0 = 0; k0 < n; k0 += PW) {
+    const int bw = min(PW, n - k0), rows = n - k0;
+    for (int t = threadIdx.x; t < rows * bw; t += blockDim.x) {
+      const int i = t / bw, c = t % bw;
+      P[i * pld + c] = Mx[(long long)(k0 + i) * lda + k0 + c];
+    }
+    __syncthreads();
+    for (int c = 0; c < bw; ++c) {
+      if (threadIdx.x < 32) {
+        double best = -1.0; int bi = c;
+        for (int i = c + threadIdx.x; i < rows; i += 32) {
+          const double v = (double)tabs(P[i * pld + c]);
+          if (v > best) { best = v; bi = i; }
+        }
+        warp_argmax(best, bi);
+        if (threadIdx.x == 0) {
+          s_p = bi;
+          piv[k0 + c] = k0 + bi;
+          if (!(best > 0.0)) s_bad = 1;
+        }
+      }
+      __syncthreads();
+      const int pr = s_p;
+      if (pr != c)
+        for (int j = threadIdx.x; j < bw; j += blockDim.x) {
+          T t = P[c * pld + j]; P[c * pld + j] = P[pr * pld + j]; P[pr * pld + j] = t;
+        }
+      __syncthreads();
+      const T d = P[c * pld + c];
+      const T dinv = (d == T(0)) ? T(0) : T(1) / d;
+      for (int i = c + 1 + threadIdx.x; i < rows; i += blockDim.x) P[i * pld + c] *= dinv;
+      __syncthreads();
+      const int w = bw - c - 1;
+      if (w > 0)
+        for (int t = threadIdx.x; t < (rows - c - 1) * w; t += blockDim.x) {
+          const int i = c + 1 + t / w, j = c + 1 + t % w;
+          P[i * pld + j] -= P[i * pld + c] * P[c * pld + j];
+        }
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < rows * bw; t += blockDim.x) {
+      const int i = t / bw, c = t % bw;
+      Mx[(long long)(k0 + i) * lda + k0 + c] = P[i * pld + c];
+    }
+    // row interchanges of this panel applied to the columns outside it
+    for (int c = 0; c < bw; ++c) {
+      const int r1 = k0 + c, r2 = piv[k0 + c];
+      if (r2 != r1)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+          if (j >= k0 && j < k0 + bw) continue;
+          T t = Mx[(long long)r1 * lda + j]; Mx[(long long)r1 * lda + j] = Mx[(long long)r2 * lda + j];
+          Mx[(long long)r2 * lda + j] = t;
+        }
+      __syncthreads();
+    }
+    const int rest = n - k0 - bw;
+    if (rest > 0) {
+      // U12 = L11^-1 A12, one column per thread
+      for (int j = k0 + bw + threadIdx.x; j < n; j += blockDim.x) {
+        T col[PW];
+        for (int c = 0; c < bw; ++c) col[c] = Mx[(long long)(k0 + c) * lda + j];
+        for (int c = 0; c < bw; ++c)
+          for (int i = c + 1; i < bw; ++i) col[i] -= P[i * pld + c] * col[c];
+        for (int c = 0; c < bw; ++c) Mx[(long long)(k0 + c) * lda + j] = col[c];
+      }
+      __syncthreads();
+      // A22 -= L21 U12, 4x4 register tiles
+      const int tr = (rest + 3) / 4, tcn = (rest + 3) / 4;
+      for (int t = threadIdx.x; t < tr * tcn; t += blockDim.x) {
+        const int bi = (t / tcn) * 4, bj = (t % tcn) * 4;
+        T acc[4][4];
+        for (int a = 0; a < 4; ++a) for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+        for (int c = 0; c < bw; ++c) {
+          T l[4], u[4];
+          for (int a = 0; a < 4; ++a) l[a] = (bi + a < rest) ? P[(bw + bi + a) * pld + c] : T(0);
+          for (int b = 0; b < 4; ++b)
+            u[b] = (bj + b < rest) ? Mx[(long long)(k0 + c) * lda + k0 + bw + bj + b] : T(0);
+          for (int a = 0; a < 4; ++a) for (int b = 0; b < 4; ++b) acc[a][b] = fma(l[a], u[b], acc[a][b]);
+        }
+        for (int a = 0; a < 4; ++a) {
+          if (bi + a >= rest) continue;
+          for (int b = 0; b < 4; ++b) {
+            if (bj + b >= rest) continue;
+            Mx[(long long)(k0 + bw + bi + a) * lda + k0 + bw + bj + b] -= acc[a][b];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
+}
+
+// z = A^-1 v with the LU factors and pivots of k_lu; one warp per element.
+template <class T>
+__global__ void k_lu_solve(int n, const T* __restrict__ LU, long long stride, int lda,
+                           const int* __restrict__ piv_all, const double* __restrict__ v,
+                           double* __restrict__ z, int nelem) {
+  extern __shared__ unsigned char smem_raw[];
+  double* x = reinterpret_cast<double*>(smem_raw) + (size_t)(threadIdx.x / 32) * n;
+  const int lane = threadIdx.x % 32;
+  const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (e >= nelem) return;
+  const T* M = LU + (long long)e * stride;
+  const int* piv = piv_all + (long long)e * n;
+  for (int i = lane; i < n; i += 32) x[i] = v[(long long)e * n + i];
+  __syncwarp();
+  if (lane == 0)
+    for (int k = 0; k < n; ++k) {
+      const int p = piv[k];
+      if (p != k) { double t = x[k]; x[k] = x[p]; x[p] = t; }
+    }
+  __syncwarp();
+  for (int i = 1; i < n; ++i) {  // unit lower triangle
+    double s = 0.0;
+    for (int k = lane; k < i; k += 32) s = fma((double)M[(long long)i * lda + k], x[k], s);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) x[i] -= s;
+    __syncwarp();
+  }
+  for (int i = n - 1; i >= 0; --i) {  // upper triangle
+    double s = 0.0;
+    for (int k = i + 1 + lane; k < n; k += 32) s = fma((double)M[(long long)i * lda + k], x[k], s);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) x[i] = (x[i] - s) / (double)M[(long long)i * lda + i];
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) z[(long long)e * n + i] = x[i];
+}
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+
+namespace sc {
+
+// Condensation set-up (FP64): A_ii^-1, Y = A_ii^-1 A_ib,ee, S_ee = A_bb,ee - A_bi,ee Y,
+// LU(S_ee).
+cudaError_t launch_condense(sc_ctx* c) {
+  const Geo& G = c->G;
+  const int ni = G.ni, nb = G.nb, ne = G.ne, K = G.K;
+  cudaError_t err;
+  if (ni > 0) {
+    const size_t smem = (size_t)ni * (ni + 1) * sizeof(double) + ni * sizeof(double) + ni * sizeof(int);
+    err = cudaFuncSetAttribute(k_gj_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_gj_inv<double><<<K, 256, smem, c->stream>>>(ni, c->Aown, (long long)ne * ne, ne, c->Ainv,
+                                                  (long long)ni * ni, c->d_status);
+    // Y = A_ii^-1 * A_ib,ee  (ni x nb)
+    dim3 g1(cdiv(nb, 64), cdiv(ni, 64), K);
+    k_gemm<double><<<g1, 256, 0, c->stream>>>(ni, nb, ni, 1.0, c->Ainv, (long long)ni * ni, ni,
+                                              c->Aown + ni, (long long)ne * ne, ne, 0.0,
+                                              c->Ytmp, (long long)ni * nb, nb);
+  }
+  // S_ee = A_bb,ee - A_bi,ee * Y
+  dim3 gc(cdiv((long long)nb * nb, 256 * 8), K);
+  k_copy_block<double><<<gc, 256, 0, c->stream>>>(nb, nb, c->Aown + (size_t)ni * ne + ni, (long long)ne * ne, ne,
+                                                  c->See, (long long)nb * nb, nb);
+  if (ni > 0) {
+    dim3 g2(cdiv(nb, 64), cdiv(nb, 64), K);
+    k_gemm<double><<<g2, 256, 0, c->stream>>>(nb, nb, ni, -1.0, c->Aown + (size_t)ni * ne, (long long)ne * ne, ne,
+                                              c->Ytmp, (long long)ni * nb, nb, 1.0,
+                                              c->See, (long long)nb * nb, nb);
+  }
+  if (c->cfg.precond == SC_PC_BLOCK_JACOBI) {
+    const size_t smem = (size_t)nb * (PW + 1) * sizeof(double);
+    err = cudaFuncSetAttribute(k_lu<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_lu<double><<<K, 256, smem, c->stream>>>(nb, c->See, (long long)nb * nb, nb, c->piv, c->d_status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
+  const Geo& G = c->G;
+  const size_t n1 = (size_t)G.K * G.nb;
+  if (c->cfg.precond != SC_PC_BLOCK_JACOBI) {
+    return cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  }
+  const int wpb = 4;
+  const size_t smem = (size_t)wpb * G.nb * sizeof(double);
+  cudaError_t err = cudaFuncSetAttribute(k_lu_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_lu_solve<double><<<cdiv(G.K, wpb), 32 * wpb, smem, c->stream>>>(G.nb, c->See, (long long)G.nb * G.nb, G.nb,
+                                                                    c->piv, v, z, G.K);
+  return cudaGetLastError();
+}
+
+}  // namespace sc

@@ -1,0 +1,270 @@
+// Internal declarations of the GB300 condensed GL-DGSEM library.
+//
+// Shared by the CUDA translation units of paper_1911_02366_gb300/csrc only.  The
+// public ABI is include/sc.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sc.h"
+
+#define SC_MAXP 8  // N + 1 <= 8
+#define SC_HD __host__ __device__
+
+// Geometry, basis and physics, passed by value to every kernel.
+struct Geo {
+  int n, N, p, nn, K;     // elements per direction, order, N+1, nodes/element, elements
+  int ne, nin, nbn, ni, nb;  // dofs/element, interior nodes, boundary nodes, interior dofs, boundary dofs
+  int NP;                 // neighbour-coupling pairs per element
+  double h, Jf, dx, inv_hw;  // element size, (h/2)^2, 2/h, 1/(h w_N)
+  double dt, c0;          // time step, BDF leading coefficient (1 or 3/2)
+  double gamma, Pr, Re, Ma, Ts, roe_delta;
+  int sutherland;
+  double D[SC_MAXP][SC_MAXP];  // D[a][b] = l_b'(xi_a)
+  double w[SC_MAXP];           // Gauss-Lobatto weights
+};
+
+// Slot numbering of an element's neighbours: faces 0..5 = (d, s) -> 2d + (s > 0);
+// edges 6..17 = 6 + 4*pairIndex(d1 < d2) + 2*(s1 > 0) + (s2 > 0).
+SC_HD inline int face_slot(int d, int s) { return 2 * d + (s > 0); }
+SC_HD inline int edge_pair_index(int d1, int d2) {  // d1 < d2
+  return d1 == 0 ? (d2 == 1 ? 0 : 1) : 2;
+}
+
+// ------------------------------------------------------------------ dual numbers
+// Five-direction forward-mode dual used to differentiate the point fluxes.
+struct D5 {
+  double v, d[5];
+  __host__ __device__ D5() : v(0.0) { for (int i = 0; i < 5; ++i) d[i] = 0.0; }
+  __host__ __device__ D5(double x) : v(x) { for (int i = 0; i < 5; ++i) d[i] = 0.0; }
+};
+SC_HD inline D5 operator+(const D5& a, const D5& b) { D5 r; r.v = a.v + b.v;
+  for (int i = 0; i < 5; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+SC_HD inline D5 operator-(const D5& a, const D5& b) { D5 r; r.v = a.v - b.v;
+  for (int i = 0; i < 5; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+SC_HD inline D5 operator-(const D5& a) { D5 r; r.v = -a.v;
+  for (int i = 0; i < 5; ++i) r.d[i] = -a.d[i]; return r; }
+SC_HD inline D5 operator*(const D5& a, const D5& b) { D5 r; r.v = a.v * b.v;
+  for (int i = 0; i < 5; ++i) r.d[i] = fma(a.d[i], b.v, a.v * b.d[i]); return r; }
+SC_HD inline D5 operator*(const D5& a, double b) { D5 r; r.v = a.v * b;
+  for (int i = 0; i < 5; ++i) r.d[i] = a.d[i] * b; return r; }
+SC_HD inline D5 operator*(double b, const D5& a) { return a * b; }
+SC_HD inline D5 operator+(const D5& a, double b) { D5 r = a; r.v += b; return r; }
+SC_HD inline D5 operator+(double b, const D5& a) { D5 r = a; r.v += b; return r; }
+SC_HD inline D5 operator-(const D5& a, double b) { D5 r = a; r.v -= b; return r; }
+SC_HD inline D5 operator-(double b, const D5& a) { D5 r = -a; r.v += b; return r; }
+SC_HD inline D5 recip(const D5& a) { D5 r; r.v = 1.0 / a.v; const double s = -r.v * r.v;
+  for (int i = 0; i < 5; ++i) r.d[i] = a.d[i] * s; return r; }
+SC_HD inline D5 operator/(const D5& a, const D5& b) { return a * recip(b); }
+SC_HD inline D5 operator/(const D5& a, double b) { return a * (1.0 / b); }
+SC_HD inline D5 operator/(double a, const D5& b) { return recip(b) * a; }
+SC_HD inline D5 dsqrt(const D5& a) { D5 r; r.v = sqrt(a.v); const double s = 0.5 / r.v;
+  for (int i = 0; i < 5; ++i) r.d[i] = a.d[i] * s; return r; }
+SC_HD inline double dsqrt(double a) { return sqrt(a); }
+SC_HD inline double vval(double a) { return a; }
+SC_HD inline double vval(const D5& a) { return a.v; }
+SC_HD inline double recip(double a) { return 1.0 / a; }
+
+// ------------------------------------------------------------------ point physics
+// Inviscid flux of the compressible Euler equations along x_d (App. B).
+template <class T>
+SC_HD inline void flux_inviscid(const Geo& G, const T q[5], int d, T f[5]) {
+  const T ir = recip(q[0]);
+  const T ux = q[1] * ir, uy = q[2] * ir, uz = q[3] * ir;
+  const T ud = d == 0 ? ux : (d == 1 ? uy : uz);
+  const T kin = 0.5 * (q[1] * ux + q[2] * uy + q[3] * uz);
+  const T pr = (G.gamma - 1.0) * (q[4] - kin);
+  f[0] = q[1 + d];
+  f[1] = q[1] * ud;
+  f[2] = q[2] * ud;
+  f[3] = q[3] * ud;
+  f[1 + d] = f[1 + d] + pr;
+  f[4] = (q[4] + pr) * ud;
+}
+
+// Viscous flux along x_d from the state and the gradients of the conserved
+// variables g[a][k] = d q_k / d x_a (App. B).  The heat flux is written through the
+// specific internal energy: kappa dT/dx = (mu gamma / Pr) de/dx.
+template <class T, class TG>
+SC_HD inline void flux_viscous(const Geo& G, const T q[5], const TG g[3][5], int d, T f[5]) {
+  const T ir = recip(q[0]);
+  const T u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const T Et = q[4] * ir;
+  T grad_u[3][3];  // grad_u[a][i] = d u_i / d x_a
+  T grad_e[3];
+  for (int a = 0; a < 3; ++a) {
+    T su = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      grad_u[a][i] = (g[a][1 + i] - u[i] * g[a][0]) * ir;
+      su = su + u[i] * grad_u[a][i];
+    }
+    grad_e[a] = (g[a][4] - Et * g[a][0]) * ir - su;
+  }
+  const T eint = Et - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  T mu;
+  if (G.sutherland) {
+    const T Tt = (G.gamma * (G.gamma - 1.0) * G.Ma * G.Ma) * eint;
+    mu = (1.0 + G.Ts) * Tt * dsqrt(Tt) * recip(Tt + G.Ts);
+  } else {
+    mu = T(1.0);
+  }
+  const T divu = grad_u[0][0] + grad_u[1][1] + grad_u[2][2];
+  const double iRe = 1.0 / G.Re;
+  T tau[3];
+  for (int i = 0; i < 3; ++i) tau[i] = mu * (grad_u[d][i] + grad_u[i][d]);
+  tau[d] = tau[d] - (2.0 / 3.0) * mu * divu;
+  f[0] = T(0.0);
+  for (int i = 0; i < 3; ++i) f[1 + i] = iRe * tau[i];
+  f[4] = iRe * (u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2] + (G.gamma / G.Pr) * mu * grad_e[d]);
+}
+
+// Viscous fluxes along all three directions at once, f[d][k], with every array
+// index a compile-time constant after unrolling (used for the dual-number Jacobians).
+template <class T>
+SC_HD inline void flux_viscous_all(const Geo& G, const T q[5], const T g[3][5], T f[3][5]) {
+  const T ir = recip(q[0]);
+  const T u0 = q[1] * ir, u1 = q[2] * ir, u2 = q[3] * ir;
+  const T Et = q[4] * ir;
+  // velocity gradients du_i/dx_a
+  const T a00 = (g[0][1] - u0 * g[0][0]) * ir, a01 = (g[0][2] - u1 * g[0][0]) * ir, a02 = (g[0][3] - u2 * g[0][0]) * ir;
+  const T a10 = (g[1][1] - u0 * g[1][0]) * ir, a11 = (g[1][2] - u1 * g[1][0]) * ir, a12 = (g[1][3] - u2 * g[1][0]) * ir;
+  const T a20 = (g[2][1] - u0 * g[2][0]) * ir, a21 = (g[2][2] - u1 * g[2][0]) * ir, a22 = (g[2][3] - u2 * g[2][0]) * ir;
+  const T e0 = (g[0][4] - Et * g[0][0]) * ir - (u0 * a00 + u1 * a01 + u2 * a02);
+  const T e1 = (g[1][4] - Et * g[1][0]) * ir - (u0 * a10 + u1 * a11 + u2 * a12);
+  const T e2 = (g[2][4] - Et * g[2][0]) * ir - (u0 * a20 + u1 * a21 + u2 * a22);
+  const T eint = Et - 0.5 * (u0 * u0 + u1 * u1 + u2 * u2);
+  T mu;
+  if (G.sutherland) {
+    const T Tt = (G.gamma * (G.gamma - 1.0) * G.Ma * G.Ma) * eint;
+    mu = (1.0 + G.Ts) * Tt * dsqrt(Tt) * recip(Tt + G.Ts);
+  } else {
+    mu = T(1.0);
+  }
+  const double iRe = 1.0 / G.Re;
+  const T mR = iRe * mu;
+  const T lam = (2.0 / 3.0) * (a00 + a11 + a22);
+  const T t00 = mR * (2.0 * a00 - lam), t11 = mR * (2.0 * a11 - lam), t22 = mR * (2.0 * a22 - lam);
+  const T t01 = mR * (a01 + a10), t02 = mR * (a02 + a20), t12 = mR * (a12 + a21);
+  const T kq = (iRe * G.gamma / G.Pr) * mu;
+  f[0][0] = T(0.0); f[0][1] = t00; f[0][2] = t01; f[0][3] = t02;
+  f[0][4] = u0 * t00 + u1 * t01 + u2 * t02 + kq * e0;
+  f[1][0] = T(0.0); f[1][1] = t01; f[1][2] = t11; f[1][3] = t12;
+  f[1][4] = u0 * t01 + u1 * t11 + u2 * t12 + kq * e1;
+  f[2][0] = T(0.0); f[2][1] = t02; f[2][2] = t12; f[2][3] = t22;
+  f[2][4] = u0 * t02 + u1 * t12 + u2 * t22 + kq * e2;
+}
+
+template <class T>
+SC_HD inline T abs_harten(const T& lam, const T& del) {
+  const double l = vval(lam);
+  if (fabs(l) >= vval(del)) return l < 0.0 ? -lam : lam;
+  return (lam * lam + del * del) * recip(2.0 * del);
+}
+
+// Roe numerical flux fhat(qa, qb, n) . n, n = s e_d outward from qa's element,
+// with Roe-averaged wave decomposition and Harten's entropy fix on every wave.
+template <class T>
+SC_HD inline void flux_roe(const Geo& G, const T qa[5], const T qb[5], int d, int s, T fh[5]) {
+  const double gm1 = G.gamma - 1.0;
+  T fa[5], fb[5];
+  flux_inviscid(G, qa, d, fa);
+  flux_inviscid(G, qb, d, fb);
+  const T ira = recip(qa[0]), irb = recip(qb[0]);
+  T ua[3], ub[3];
+  for (int i = 0; i < 3; ++i) { ua[i] = qa[1 + i] * ira; ub[i] = qb[1 + i] * irb; }
+  const T pa = gm1 * (qa[4] - 0.5 * (qa[1] * ua[0] + qa[2] * ua[1] + qa[3] * ua[2]));
+  const T pb = gm1 * (qb[4] - 0.5 * (qb[1] * ub[0] + qb[2] * ub[1] + qb[3] * ub[2]));
+  const T ra = dsqrt(qa[0]), rb = dsqrt(qb[0]);
+  const T iw = recip(ra + rb);
+  T um[3];
+  for (int i = 0; i < 3; ++i) um[i] = (ra * ua[i] + rb * ub[i]) * iw;
+  const T Hm = (ra * (qa[4] + pa) * ira + rb * (qb[4] + pb) * irb) * iw;
+  const T vsq = um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+  const T cm = dsqrt(gm1 * (Hm - 0.5 * vsq));
+  const T rhom = ra * rb;
+  const double sd = (double)s;
+  const T un = um[d] * sd;
+  const T jr = qb[0] - qa[0];
+  const T jp = pb - pa;
+  T ju[3];
+  for (int i = 0; i < 3; ++i) ju[i] = ub[i] - ua[i];
+  const T jun = ju[d] * sd;
+  const T ic2 = recip(cm * cm);
+  const T wm = 0.5 * (jp - rhom * cm * jun) * ic2;  // strength of the u - c wave
+  const T wp = 0.5 * (jp + rhom * cm * jun) * ic2;  // strength of the u + c wave
+  const T we = jr - jp * ic2;                        // entropy wave
+  const T del = G.roe_delta * cm;
+  const T am = abs_harten(un - cm, del) * wm;
+  const T ap = abs_harten(un + cm, del) * wp;
+  const T a0 = abs_harten(un, del);
+  // shear: tangential velocity jump
+  T jt[3];
+  for (int i = 0; i < 3; ++i) jt[i] = ju[i];
+  jt[d] = T(0.0);
+  const T umjt = um[0] * jt[0] + um[1] * jt[1] + um[2] * jt[2];
+  T diss[5];
+  diss[0] = am + ap + a0 * we;
+  for (int i = 0; i < 3; ++i) diss[1 + i] = (am + ap) * um[i] + a0 * (we * um[i] + rhom * jt[i]);
+  diss[1 + d] = diss[1 + d] + (ap - am) * cm * sd;
+  diss[4] = (am + ap) * Hm + (ap - am) * cm * un + a0 * (0.5 * we * vsq + rhom * umjt);
+  for (int k = 0; k < 5; ++k) fh[k] = 0.5 * sd * (fa[k] + fb[k]) - 0.5 * diss[k];
+}
+
+// ------------------------------------------------------------------ host context
+struct Pattern {
+  // Neighbour couplings of one element (identical for all elements): pair p couples
+  // row node row[p] of the element to node col[p] of the neighbour in slot slot[p].
+  std::vector<int> row, slot, col;
+  // Row-grouped lists (CSR over the element's nodes in natural order).
+  std::vector<int> ptr;  // size nn+1
+  std::vector<int> ids;  // pair ids
+};
+
+struct sc_ctx {
+  sc_config cfg{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool has_mesh = false, has_state = false, has_dt = false, assembled = false, condensed = false;
+  int bdf = 1;
+  Geo G{};
+  double L = 0.0;
+  std::vector<double> xi;          // Gauss-Lobatto nodes
+  std::vector<int> perm, iperm;    // natural node -> position (interior first), inverse
+  std::vector<int> nbr;            // [K][18] neighbour element per slot
+  Pattern pat;
+  // device memory
+  double *Q = nullptr, *Qh = nullptr, *grad = nullptr, *F = nullptr, *B = nullptr;
+  double *NJ = nullptr, *RJ = nullptr, *Aown = nullptr, *X = nullptr;
+  int *d_nbr = nullptr, *d_perm = nullptr, *d_iperm = nullptr;
+  int *d_prow = nullptr, *d_pslot = nullptr, *d_pcol = nullptr, *d_pptr = nullptr, *d_pids = nullptr;
+  double *Ainv = nullptr, *Ytmp = nullptr, *See = nullptr;
+  int *piv = nullptr, *d_status = nullptr;
+  // Krylov workspace (boundary space of size n1 = K*nb)
+  double *V = nullptr, *Wv = nullptr, *Zv = nullptr, *Xb = nullptr, *Gb = nullptr, *Rb = nullptr;
+  double *Ui = nullptr, *Tb = nullptr, *Hd = nullptr, *partial = nullptr, *Xfull = nullptr, *Rfull = nullptr;
+  int restart_alloc = 0;
+  cudaEvent_t ev[8] = {};
+};
+
+// kernels launchers (defined in the .cu files)
+namespace sc {
+cudaError_t launch_residual(sc_ctx* c);
+cudaError_t launch_assembly(sc_ctx* c);
+cudaError_t launch_condense(sc_ctx* c);
+cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double* Bfull, double alpha,
+                          double* u);
+cudaError_t cond_boundary(sc_ctx* c, const double* xb, double delta, const double* Bfull, double gamma_,
+                          const double* u, double* y);
+cudaError_t precond_apply(sc_ctx* c, const double* v, double* z);
+cudaError_t global_apply(sc_ctx* c, const double* x, double* y);
+cudaError_t scatter_solution(sc_ctx* c, const double* xb, const double* xi, double* x);
+cudaError_t multidot(sc_ctx* c, const double* V, int nvec, size_t n, const double* w, double* out_dev);
+cudaError_t vec_update(sc_ctx* c, double* w, const double* V, int nvec, size_t n, const double* coef_dev,
+                       double sign);
+cudaError_t vec_scale_copy(sc_ctx* c, double* dst, const double* src, size_t n, const double* scal_dev,
+                           int invert);
+cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b, size_t n);
+}  // namespace sc

@@ -1,0 +1,205 @@
+"""ctypes binding of the C ABI in include/sc.h (argument marshalling only).
+
+Every function here forwards to the CUDA library of the same name; all arithmetic of
+the Newton solve runs in the library's kernels.  Arrays are numpy (host) or torch CUDA
+tensors (device); device tensors are passed by their data pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SC_OK, SC_ERR_ARG, SC_ERR_CUDA, SC_ERR_OOM, SC_ERR_STATE = 0, 1, 2, 3, 4
+SC_ERR_SINGULAR_BLOCK, SC_ERR_NONFINITE, SC_ERR_NOT_CONVERGED = 5, 6, 7
+SC_PREC_FP64, SC_PREC_MIXED = 0, 1
+SC_PC_BLOCK_JACOBI, SC_PC_NONE = 0, 1
+
+_lib = None
+
+
+class SCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"sc status {status}: {msg}")
+        self.status = status
+
+
+class sc_config(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
+                ("Ma", ctypes.c_double), ("Ts", ctypes.c_double), ("sutherland", ctypes.c_int),
+                ("roe_delta", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("gmres_max_iters", ctypes.c_int),
+                ("max_refine", ctypes.c_int), ("rel_tol", ctypes.c_double), ("inner_tol", ctypes.c_double)]
+
+
+class sc_solve_stats(ctypes.Structure):
+    _fields_ = [("gmres_iters", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("cond_rel_residual", ctypes.c_double),
+                ("ms_rhs", ctypes.c_double), ("ms_gmres", ctypes.c_double),
+                ("ms_backsub", ctypes.c_double), ("ms_refine", ctypes.c_double),
+                ("first_bad_element", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_set_mesh", "sc_node_coords",
+           "sc_set_state", "sc_set_timestep", "sc_assemble", "sc_condense", "sc_solve", "sc_get_rhs",
+           "sc_apply_jacobian", "sc_get_jacobian_block", "sc_condensed_matvec", "sc_sizes"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libsc.so (building it first if it is missing).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)
+    L.sc_default_config.argtypes = [ctypes.POINTER(sc_config)]
+    L.sc_create.argtypes = [ctypes.POINTER(sc_config), vp, ctypes.POINTER(vp)]
+    L.sc_destroy.argtypes = [vp]; L.sc_destroy.restype = None
+    L.sc_last_error.argtypes = [vp]; L.sc_last_error.restype = ctypes.c_char_p
+    L.sc_set_mesh.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    L.sc_node_coords.argtypes = [vp, dp]
+    L.sc_set_state.argtypes = [vp, dp, dp, dp, ctypes.c_int]
+    L.sc_set_timestep.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.sc_assemble.argtypes = [vp]
+    L.sc_condense.argtypes = [vp]
+    L.sc_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(sc_solve_stats)]
+    L.sc_get_rhs.argtypes = [vp, dp, ctypes.c_int]
+    L.sc_apply_jacobian.argtypes = [vp, dp, dp, ctypes.c_int]
+    L.sc_get_jacobian_block.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
+    L.sc_condensed_matvec.argtypes = [vp, dp, dp]
+    L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
+    for f in EXPORTS:
+        if f not in ("sc_destroy", "sc_last_error"):
+            getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """(pointer, on_device) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+def default_config(**kw) -> sc_config:
+    cfg = sc_config()
+    lib().sc_default_config(ctypes.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Context:
+    """One solver context (wraps sc_create / sc_destroy)."""
+
+    def __init__(self, cfg: sc_config | None = None, stream: int | None = None, **kw):
+        self._L = lib()
+        self.cfg = cfg if cfg is not None else default_config(**kw)
+        h = ctypes.c_void_p()
+        self._check(self._L.sc_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h)), None)
+        self.h = h
+
+    def _check(self, status, h=...):
+        if status != SC_OK:
+            hh = self.h if h is ... else h
+            msg = self._L.sc_last_error(hh).decode() if hh else ""
+            raise SCError(status, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.sc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sc_set_mesh(self, n: int, L: float, N: int):
+        self._check(self._L.sc_set_mesh(self.h, n, L, N))
+
+    def sc_sizes(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(self._L.sc_sizes(self.h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def sc_node_coords(self) -> np.ndarray:
+        K, ne, _, _ = self.sc_sizes()
+        out = np.zeros((K, ne // 5, 3))
+        self._check(self._L.sc_node_coords(self.h, out.ctypes.data))
+        return out
+
+    def sc_set_timestep(self, dt: float, bdf: int = 1):
+        self._check(self._L.sc_set_timestep(self.h, dt, bdf))
+
+    def sc_set_state(self, Q, Qs=None, Qsm1=None):
+        Qs = Q if Qs is None else Qs
+        (pq, dq), (ps, ds), (pm, dm) = _ptr(Q), _ptr(Qs), _ptr(Qsm1)
+        if Qsm1 is not None and dm != dq:
+            raise ValueError("all state arrays must live on the same side")
+        if ds != dq:
+            raise ValueError("all state arrays must live on the same side")
+        self._check(self._L.sc_set_state(self.h, pq, ps, pm, dq))
+
+    def sc_assemble(self):
+        self._check(self._L.sc_assemble(self.h))
+
+    def sc_condense(self):
+        self._check(self._L.sc_condense(self.h))
+
+    def sc_solve(self, dQ, raise_on_not_converged: bool = True):
+        st = sc_solve_stats()
+        p, dev = _ptr(dQ)
+        s = self._L.sc_solve(self.h, p, dev, ctypes.byref(st))
+        if s != SC_OK and not (s == SC_ERR_NOT_CONVERGED and not raise_on_not_converged):
+            self._check(s)
+        return st.as_dict() | {"status": s}
+
+    def sc_get_rhs(self, B):
+        p, dev = _ptr(B)
+        self._check(self._L.sc_get_rhs(self.h, p, dev))
+        return B
+
+    def sc_apply_jacobian(self, x, y):
+        (px, dx), (py, dy) = _ptr(x), _ptr(y)
+        if dx != dy:
+            raise ValueError("x and y must live on the same side")
+        self._check(self._L.sc_apply_jacobian(self.h, px, py, dx))
+        return y
+
+    def sc_get_jacobian_block(self, e: int, c: int) -> np.ndarray:
+        _, ne, _, _ = self.sc_sizes()
+        out = np.zeros((ne, ne))
+        self._check(self._L.sc_get_jacobian_block(self.h, e, c, out.ctypes.data))
+        return out
+
+    def sc_condensed_matvec(self, xb, yb):
+        (px, dx), (py, dy) = _ptr(xb), _ptr(yb)
+        if not (dx and dy):
+            raise ValueError("condensed_matvec takes device tensors")
+        self._check(self._L.sc_condensed_matvec(self.h, px, py))
+        return yb

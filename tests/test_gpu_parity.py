@@ -1,0 +1,107 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import sc_inputs as I
+from gpu_common import case, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = [(1, 2), (2, 3), (3, 2), (3, 3), (2, 4)]
+
+
+@pytest.mark.parametrize("n,N", SMALL)
+def test_node_coordinates_match_inputs(n, N):
+    _, _, _, ctx = case(n, N)
+    np.testing.assert_allclose(ctx.sc_node_coords(), I.node_coordinates(n, N), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("n,N", SMALL)
+@pytest.mark.parametrize("bdf", [1, 2])
+def test_residual_matches_oracle(n, N, bdf):
+    Q, dt, p, ctx = case(n, N, eps=1e-2, bdf=bdf)
+    rng = np.random.default_rng(5)
+    Qs = Q * (1 + 1e-3 * rng.standard_normal(Q.shape))
+    Qsm1 = Q * (1 + 1e-3 * rng.standard_normal(Q.shape))
+    ctx.sc_set_state(Q, Qs, Qsm1 if bdf == 2 else None)
+    ctx.sc_assemble()
+    B = ctx.sc_get_rhs(np.zeros(Q.size)).reshape(Q.shape)
+    R = O.residual(p, Q, Qs, Qsm1)
+    assert rel(B, -R) < 1e-12
+
+
+@pytest.mark.parametrize("n,N", SMALL)
+def test_jacobian_blocks_match_oracle(n, N):
+    Q, dt, p, ctx = case(n, N, eps=1e-2)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    A = O.jacobian(p, Q).tocsr()
+    ne = p.nn * 5
+    scale = abs(A).max()
+    for e in range(p.K):
+        rows = A[e * ne:(e + 1) * ne]
+        cols_present = set(np.unique(rows.indices // ne).tolist())
+        for c in sorted(cols_present):
+            ref = rows[:, c * ne:(c + 1) * ne].toarray()
+            got = ctx.sc_get_jacobian_block(e, c)
+            err = np.abs(got - ref).max() / scale
+            assert err < 1e-11, (e, c, err)
+
+
+@pytest.mark.parametrize("n,N", [(3, 2), (2, 4)])
+def test_apply_jacobian_matches_oracle_jvp(n, N):
+    Q, dt, p, ctx = case(n, N, eps=1e-2)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    x = np.random.default_rng(6).standard_normal(Q.size)
+    y = ctx.sc_apply_jacobian(x, np.zeros(Q.size))
+    ref = O.jvp(p, Q, x.reshape(Q.shape)).reshape(-1)
+    assert rel(y, ref) < 1e-12
+
+
+@pytest.mark.parametrize("n,N", [(2, 3), (3, 2), (1, 4)])
+def test_condensed_operator_matches_oracle(n, N):
+    Q, dt, p, ctx = case(n, N)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    cs = O.condensed_operator(O.jacobian(p, Q), n, N)
+    S = cs.dense_S()
+    xb = np.random.default_rng(7).standard_normal(S.shape[0])
+    yb = torch.zeros(S.shape[0], dtype=torch.float64, device="cuda")
+    ctx.sc_condensed_matvec(torch.tensor(xb, device="cuda"), yb)
+    torch.cuda.synchronize()
+    assert rel(yb.cpu().numpy(), S @ xb) < 1e-11
+
+
+@pytest.mark.parametrize("n,N,cfl", [(2, 3, 10.0), (3, 2, 10.0), (1, 3, 10.0), (2, 4, 10.0)])
+def test_solve_matches_oracle_global_solve(n, N, cfl):
+    Q, dt, p, ctx = case(n, N, cfl=cfl, rel_tol=1e-13, gmres_restart=60, gmres_max_iters=3000)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    dQ = np.zeros(Q.size)
+    st = ctx.sc_solve(dQ)
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    x = O.global_solve(A, B)
+    assert np.linalg.norm(B - A @ dQ) / np.linalg.norm(B) < 1e-12
+    assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < 1e-10, st
+
+
+def test_tgv_4x4x4_N3_cfl50_reaches_1e8():
+    # Full size of the 4^3, N = 3 workload: the oracle's Jacobian-vector product
+    # checks the global residual of the GPU solution.
+    n, N = 4, 3
+    Q, dt, p, ctx = case(n, N, cfl=50.0, gmres_restart=60, gmres_max_iters=6000)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    dQ = np.zeros(Q.size)
+    st = ctx.sc_solve(dQ)
+    B = -O.residual(p, Q).reshape(-1)
+    r = B - O.jvp(p, Q, dQ.reshape(Q.shape)).reshape(-1)
+    assert np.linalg.norm(r) / np.linalg.norm(B) < 1e-8 * 1.01, st
+    assert st["rel_residual"] < 1e-8
