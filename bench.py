@@ -1,0 +1,325 @@
+"""Benchmark: one Newton linear solve of the condensed GL-DGSEM per step on GB300.
+
+A step is one pass of the whole hot path on the 16^3-element, N = 4 Taylor-Green
+workload (2,560,000 DOF, CFL 50): residual + Jacobian assembly, static condensation
+(A_ii^-1, element Schur blocks, block-Jacobi factors), condensed right-hand side,
+GMRES to a global relative residual of 1e-8, back-substitution.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--arm fp64|mixed] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs independent replicas (one per GPU); the
+path has no collective.  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import sc_inputs as I  # noqa: E402
+
+WORKLOAD = dict(name="tgv_16x16x16_N4_cfl50", n=16, N=4, Ma=0.1, Re=1600.0, cfl=50.0, seed=0)
+METRIC = "linear-solve DOF/s at rel. residual 1e-8: condensed GPU forms vs plain FP64"
+REL_TOL = 1e-8
+# Peaks: HBM and bf16 from MEASURED_PEAKS.json; FP64 and FP32 FMA rates derived from
+# the unit counts and clocks (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s;
+# a DFMA microbenchmark measured 1.20 TFLOP/s on this machine).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush(); self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def gather_max(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1911_02366_gb300 import sc
+
+    torch.cuda.set_device(local)
+    W = WORKLOAD
+    Q, dt = I.tgv_state(W["n"], W["N"], Ma=W["Ma"], seed=W["seed"], cfl=W["cfl"])
+    dofs = Q.size
+    precision = sc.SC_PREC_MIXED if args.arm == "mixed" else sc.SC_PREC_FP64
+    stream = torch.cuda.current_stream()
+    ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"],
+                     gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL)
+    ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
+    ctx.sc_set_timestep(dt, 1)
+    Qd = torch.tensor(Q.reshape(-1), device="cuda")
+    dQ = torch.zeros_like(Qd)
+    ctx.sc_set_state(Qd, Qd)
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        ctx.sc_assemble()
+        ev[1].record(stream)
+        ctx.sc_condense()
+        st = ctx.sc_solve(dQ)
+        ev[2].record(stream)
+        return ev, st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    dominant = sc.SC_KERNEL_LU_SOLVE if args.arm == "fp64" else sc.SC_KERNEL_COND_BOUNDARY
+    ctx.sc_profile_kernel(dominant)
+    sampler = ClockSampler(local) if rank == 0 else None
+    l0 = ctx.sc_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True); end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    marks, stats = [], []
+    for _ in range(args.steps):
+        ev, st = step()
+        marks.append(ev); stats.append(st)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = ctx.sc_launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    total_ms = start.elapsed_time(end)
+    assemble_ms = sum(ev[0].elapsed_time(ev[1]) for ev in marks)
+    solve_ms = sum(ev[1].elapsed_time(ev[2]) for ev in marks)
+    n_prof, prof_ms = ctx.sc_profile_read()
+    ctx.sc_profile_kernel(-1)
+    total_ms = gather_max(world, total_ms)
+    worst = max(s["rel_residual"] for s in stats)
+    ok = all(s["status"] == 0 for s in stats) and worst <= REL_TOL
+
+    # end to end: host (pinned) state in, host update out, inside the timed region
+    Qh = torch.tensor(Q.reshape(-1)).pin_memory()
+    dQh = torch.zeros(dofs, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.sc_set_state(Qh, Qh)
+        ctx.sc_assemble()
+        ctx.sc_condense()
+        ctx.sc_solve(dQh)
+    torch.cuda.synchronize()
+    e2e_s = gather_max(world, time.perf_counter() - t0)
+
+    flops, bytes_ = ctx.sc_kernel_work(dominant)
+    avg_ms = prof_ms / max(n_prof, 1)
+    peaks = measured_peaks()
+    if args.arm == "fp64":
+        roof = {"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_ / (avg_ms * 1e-3) / 1e9,
+                "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = TRAFFIC.get((args.arm, dominant))
+    roof["kernel"] = {sc.SC_KERNEL_LU_SOLVE: "k_lu_solve", sc.SC_KERNEL_COND_BOUNDARY: "k_cond_boundary"}[dominant]
+    roof["launches_timed"] = n_prof
+    roof["avg_launch_ms"] = avg_ms
+
+    value = world * dofs * args.steps / (total_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.arm == "fp64" else "f32+f64",
+        "data": "synthetic (seeded Taylor-Green state, 1e-3 perturbation)",
+        "config": {"workload": W["name"], "elements": W["n"] ** 3, "order": W["N"], "dof": dofs, "cfl": W["cfl"],
+                   "Ma": W["Ma"], "Re": W["Re"], "arm": args.arm, "gmres_restart": args.restart,
+                   "l2": "inputs larger than L2 (element blocks 12.9 GB)", "parallelism": f"replicas x{world}"},
+        "linear_solve_dof_per_s": world * dofs * args.steps / (gather_max(world, solve_ms) * 1e-3),
+        "assemble_ms_per_step": assemble_ms / args.steps,
+        "gmres_iters": [s["gmres_iters"] for s in stats],
+        "rel_residual_max": worst, "converged": ok,
+        "e2e": {"value": world * dofs * e2e_steps / e2e_s, "unit": "DOF/s",
+                "h2d_bytes_per_step": 2 * dofs * 8, "d2h_bytes_per_step": dofs * 8},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    ctx.close()
+    return line
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+# captures summarised in profiles/, scaled to the 16^3 mesh; None once a kernel changes.
+TRAFFIC = {
+    ("fp64", 2): None,
+    ("fp64", 1): None,
+    ("mixed", 1): None,
+}
+
+
+def cpu_sample(seed=0):
+    """Bounded sample of the workload for the oracle: the periodic Taylor-Green box on
+    3^3 elements at the same order N = 4 and the same time step as the 16^3 workload
+    (same per-element blocks and physics, 27 instead of 4096 elements)."""
+    W = WORKLOAD
+    n_s = 3
+    _, dt = I.tgv_state(W["n"], W["N"], Ma=W["Ma"], seed=W["seed"], cfl=W["cfl"])
+    Q, _ = I.tgv_state(n_s, W["N"], Ma=W["Ma"], seed=seed, cfl=W["cfl"])
+    return n_s, 2 * math.pi, Q, dt
+
+
+def run_oracle(steps: int):
+    """The FP64 CPU oracle's condensed linear solve (condensation, block-Jacobi GMRES(30),
+    back-substitution) on the bounded sample; the Jacobian is assembled beforehand."""
+    import oracle as O
+    n_s, L, Q, dt = cpu_sample()
+    W = WORKLOAD
+    p = O.Params(n=n_s, N=W["N"], dt=dt, L=L, Re=W["Re"], Ma=W["Ma"])
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    times, iters = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        x, info = O.condensed_solve(A, B, n_s, W["N"], method="gmres", tol=REL_TOL, restart=30, maxiter=5000)
+        times.append(time.perf_counter() - t0)
+        iters.append(info.get("iters"))
+    res = float(np.linalg.norm(B - A @ x) / np.linalg.norm(B))
+    return {"dof": Q.size, "seconds": times, "iters": iters, "rel_residual": res,
+            "sample": f"periodic Taylor-Green box on {n_s}^3 elements, N={W['N']}, dt of the 16^3 workload; "
+                      "one linear solve (condense, GMRES(30) to 1e-8, back-substitute), Jacobian assembled beforehand"}
+
+
+def cpu_threads():
+    try:
+        import oracle as O
+        return O.num_threads()
+    except Exception:
+        return os.cpu_count()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--arm", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--max-iters", type=int, default=4000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        if rank == 0:
+            r = run_oracle(max(1, args.steps))
+            v = r["dof"] * len(r["seconds"]) / sum(r["seconds"])
+            print(json.dumps({
+                "impl": "reference", "metric": METRIC, "value": v, "unit": "DOF/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(r["seconds"]) / len(r["seconds"]),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded Taylor-Green state, 1e-3 perturbation)",
+                "config": {"workload": WORKLOAD["name"], "arm": "oracle"},
+                "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": cpu_threads(), "kind": "oracle",
+                                 "sample": r["sample"]},
+                "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "gmres_iters": r["iters"], "rel_residual": r["rel_residual"]}))
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    line = run_ours(args, world, rank, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            r = run_oracle(1)
+            v = r["dof"] / r["seconds"][0]
+            line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cpu_threads(), "kind": "oracle",
+                                    "sample": r["sample"], "gmres_iters": r["iters"][0]}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -142,6 +142,28 @@ sc_status sc_condensed_matvec(sc_ctx* ctx, const double* xb, double* yb);
 /* Sizes: number of elements, dofs per element, interior and boundary dofs per element. */
 sc_status sc_sizes(const sc_ctx* ctx, int* K, int* ne, int* ni, int* nb);
 
+/* ---- Measurement hooks (not part of the method; used by the benchmark) ---------- */
+
+/* Kernel ids for sc_profile_kernel / sc_kernel_work. */
+enum { SC_KERNEL_COND_INTERIOR = 0, SC_KERNEL_COND_BOUNDARY = 1, SC_KERNEL_LU_SOLVE = 2,
+       SC_KERNEL_LU = 3, SC_KERNEL_SCHUR_GEMM = 4, SC_KERNEL_GJ_INV = 5, SC_KERNEL_ASSEMBLE_OWN = 6,
+       SC_KERNEL_GLOBAL_APPLY = 7 };
+
+/* Total number of kernels this context has launched since sc_create. */
+sc_status sc_launch_count(const sc_ctx* ctx, long long* count);
+
+/* Start timing every launch of one kernel with CUDA events on the context's stream
+   (kernel_id = -1 stops); resets the accumulated totals. */
+sc_status sc_profile_kernel(sc_ctx* ctx, int kernel_id);
+
+/* Launches and total device milliseconds of the profiled kernel since sc_profile_kernel
+   (synchronises the stream). */
+sc_status sc_profile_read(sc_ctx* ctx, long long* launches, double* total_ms);
+
+/* Algorithmic work of one launch of a kernel on the current mesh: floating-point
+   operations and bytes that must move (matrix entries read once, vectors once). */
+sc_status sc_kernel_work(const sc_ctx* ctx, int kernel_id, double* flops, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

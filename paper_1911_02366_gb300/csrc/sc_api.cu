@@ -93,7 +93,7 @@ void free_all(sc_ctx* c) {
                     &c->Hd, &c->partial, &c->Xfull, &c->Rfull};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
-                 &c->d_pids, &c->piv, &c->d_status};
+                 &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
 }
 
@@ -186,7 +186,7 @@ sc_status sc_default_config(sc_config* cfg) {
 
 sc_status sc_create(const sc_config* cfg, void* cuda_stream, sc_ctx** out) {
   if (!cfg || !out) return SC_ERR_ARG;
-  if (cfg->gmres_restart < 1 || cfg->gmres_restart > 60 || cfg->gmres_max_iters < 1 || !(cfg->rel_tol > 0) ||
+  if (cfg->gmres_restart < 1 || cfg->gmres_restart > 400 || cfg->gmres_max_iters < 1 || !(cfg->rel_tol > 0) ||
       !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->gamma > 1) || !(cfg->Pr > 0))
     return SC_ERR_ARG;
   if (cfg->precision != SC_PREC_FP64 && cfg->precision != SC_PREC_MIXED) return SC_ERR_ARG;
@@ -221,6 +221,8 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   G.n = n; G.N = N; G.p = N + 1; G.nn = G.p * G.p * G.p; G.K = n * n * n;
   G.nin = (N - 1) * (N - 1) * (N - 1); G.nbn = G.nn - G.nin;
   G.ne = 5 * G.nn; G.ni = 5 * G.nin; G.nb = 5 * G.nbn;
+  auto up4 = [](int x) { return (x + 3) & ~3; };
+  G.cb0 = up4(G.ni); G.lda = up4(G.cb0 + G.nb); G.ldi = up4(G.ni); G.lds = up4(G.nb);
   c->L = L;
   G.h = L / n; G.Jf = 0.25 * G.h * G.h; G.dx = 2.0 / G.h;
   std::vector<double> w;
@@ -272,17 +274,18 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->Xfull, dofs)); A(dalloc(&c->Rfull, dofs));
   A(dalloc(&c->grad, nodes * 15)); A(dalloc(&c->F, nodes * 15));
   A(dalloc(&c->NJ, nodes * 375)); A(dalloc(&c->RJ, (size_t)G.K * 6 * 50 * G.p * G.p));
-  A(dalloc(&c->Aown, (size_t)G.K * G.ne * G.ne)); A(dalloc(&c->X, (size_t)G.K * G.NP * 25));
-  A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ni)); A(dalloc(&c->Ytmp, (size_t)G.K * G.ni * G.nb));
-  A(dalloc(&c->See, (size_t)G.K * G.nb * G.nb)); A(dalloc(&c->piv, (size_t)G.K * G.nb));
+  A(dalloc(&c->Aown, (size_t)G.K * own_stride(G))); A(dalloc(&c->X, (size_t)G.K * G.NP * 25));
+  A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Ytmp, (size_t)G.K * G.ni * G.nb));
+  A(dalloc(&c->See, (size_t)G.K * G.nb * G.lds)); A(dalloc(&c->piv, (size_t)G.K * G.nb)); A(dalloc(&c->rowperm, (size_t)G.K * G.nb));
   A(dalloc(&c->V, n1 * (m + 1))); A(dalloc(&c->Wv, n1)); A(dalloc(&c->Zv, n1)); A(dalloc(&c->Xb, n1));
   A(dalloc(&c->Gb, n1)); A(dalloc(&c->Rb, n1)); A(dalloc(&c->Tb, n1));
-  A(dalloc(&c->Ui, (size_t)G.K * G.ni)); A(dalloc(&c->Hd, 256)); A(dalloc(&c->partial, 608 * 64));
+  A(dalloc(&c->Ui, (size_t)G.K * G.ni)); A(dalloc(&c->Hd, 3 * (size_t)(m + 2) + 16));
+  A(dalloc(&c->partial, 152 * (size_t)(m + 2)));
   A(dalloc(&c->d_status, 1));
   A(dalloc(&c->d_nbr, c->nbr.size())); A(dalloc(&c->d_perm, G.nn)); A(dalloc(&c->d_iperm, G.nn));
   const int np = G.NP;
   A(dalloc(&c->d_prow, np)); A(dalloc(&c->d_pslot, np)); A(dalloc(&c->d_pcol, np));
-  A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pids, np));
+  A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pinfo, np));
   if (e != cudaSuccess) { free_all(c); cudaGetLastError(); return fail(c, SC_ERR_OOM, std::string("allocation: ") + cudaGetErrorString(e)); }
   SC_CUDA(cudaMemcpy(c->d_nbr, c->nbr.data(), c->nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_perm, c->perm.data(), G.nn * sizeof(int), cudaMemcpyHostToDevice));
@@ -291,7 +294,20 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   SC_CUDA(cudaMemcpy(c->d_pslot, c->pat.slot.data(), np * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_pcol, c->pat.col.data(), np * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_pptr, c->pat.ptr.data(), (G.nn + 1) * sizeof(int), cudaMemcpyHostToDevice));
-  SC_CUDA(cudaMemcpy(c->d_pids, c->pat.ids.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  // pairs are stored row by row, so the row lists are contiguous ranges of pair ids
+  for (int i = 0; i < np; ++i)
+    if (c->pat.ids[i] != i) return fail(c, SC_ERR_ARG, "internal: coupling pattern not row ordered");
+  std::vector<int> pinfo(np);
+  for (int i = 0; i < np; ++i) {
+    const int pos = c->perm[c->pat.col[i]];
+    const int interior = pos < G.nin ? 1 : 0;
+    const int off = interior ? 5 * pos : 5 * (pos - G.nin);
+    pinfo[i] = (c->pat.slot[i] << 26) | (interior << 25) | off;
+  }
+  SC_CUDA(cudaMemcpy(c->d_pinfo, pinfo.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  // the alignment padding of the element blocks must read as zero
+  SC_CUDA(cudaMemset(c->Aown, 0, (size_t)G.K * own_stride(G) * sizeof(double)));
+  SC_CUDA(cudaMemset(c->Ainv, 0, (size_t)G.K * G.ni * G.ldi * sizeof(double)));
   c->has_mesh = true;
   return SC_OK;
 }
@@ -397,8 +413,8 @@ sc_status sc_get_jacobian_block(sc_ctx* c, int e, int col, double* block) {
   const Geo& G = c->G;
   if (e < 0 || e >= G.K || col < 0 || col >= G.K) return fail(c, SC_ERR_ARG, "element index out of range");
   const int ne = G.ne;
-  std::vector<double> own((size_t)ne * ne), X((size_t)G.NP * 25);
-  SC_CUDA(cudaMemcpyAsync(own.data(), c->Aown + (size_t)e * ne * ne, own.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> own(own_stride(G)), X((size_t)G.NP * 25);
+  SC_CUDA(cudaMemcpyAsync(own.data(), c->Aown + (size_t)e * own_stride(G), own.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   SC_CUDA(cudaMemcpyAsync(X.data(), c->X + (size_t)e * G.NP * 25, X.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
   if (s != SC_OK) return s;
@@ -408,14 +424,14 @@ sc_status sc_get_jacobian_block(sc_ctx* c, int e, int col, double* block) {
       for (int r = 0; r < G.nn; ++r)
         for (int k = 0; k < 5; ++k)
           for (int l = 0; l < 5; ++l)
-            block[(size_t)(5 * j + k) * ne + 5 * r + l] = own[(size_t)(5 * c->perm[j] + k) * ne + 5 * c->perm[r] + l];
+            block[(size_t)(5 * j + k) * ne + 5 * r + l] = own[(size_t)(5 * c->perm[j] + k) * G.lda + own_col(G, c->perm[r], l)];
   bool any = col == e;
   for (int pr = 0; pr < G.NP; ++pr) {
     if (c->nbr[(size_t)e * 18 + c->pat.slot[pr]] != col) continue;
     any = true;
     const int j = c->pat.row[pr], r = c->pat.col[pr];
     for (int k = 0; k < 5; ++k)
-      for (int l = 0; l < 5; ++l) block[(size_t)(5 * j + k) * ne + 5 * r + l] += X[(size_t)pr * 25 + k * 5 + l];
+      for (int l = 0; l < 5; ++l) block[(size_t)(5 * j + k) * ne + 5 * r + l] += X[((size_t)k * G.NP + pr) * 5 + l];
   }
   if (!any) return fail(c, SC_ERR_ARG, "element c is not in the stencil of e");
   return SC_OK;
@@ -443,13 +459,17 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
   SC_CUDA(sc::cond_interior(c, nullptr, 0.0, c->B, 1.0, c->Ui));
   SC_CUDA(sc::cond_boundary(c, nullptr, 0.0, c->B, 1.0, c->Ui, c->Gb));
   SC_CUDA(cudaEventRecord(ev[1], c->stream));
-  const double bnorm = dnorm2(c, c->B, dofs, c->Hd + 200);
+  double* const hs = c->Hd + 2 * (m + 1) + 2;  // scratch slot
+  const double bnorm = dnorm2(c, c->B, dofs, hs);
   const double target = c->cfg.rel_tol * bnorm;
   // right-preconditioned restarted GMRES, x0 = 0
   SC_CUDA(cudaMemsetAsync(c->Xb, 0, n1 * sizeof(double), c->stream));
   SC_CUDA(cudaMemcpyAsync(c->Rb, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  double beta = dnorm2(c, c->Rb, n1, c->Hd + 200);
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(160), y(m);
+  double beta = dnorm2(c, c->Rb, n1, hs);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(2 * (m + 1) + 1), y(m);
+  double* const h1 = c->Hd;
+  double* const h2 = c->Hd + (m + 1);
+  double* const hn2 = c->Hd + 2 * (m + 1);
   int iters = 0;
   double resid = beta;
   bool ok = beta <= target || bnorm == 0.0;
@@ -463,16 +483,16 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
       SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
       SC_CUDA(sc::cond_boundary(c, c->Zv, 1.0, nullptr, 0.0, c->Ui, c->Wv));
       // classical Gram-Schmidt, twice
-      SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, c->Hd));
-      SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, c->Hd, -1.0));
-      SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, c->Hd + 64));
-      SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, c->Hd + 64, -1.0));
-      SC_CUDA(sc::multidot(c, c->Wv, 1, n1, c->Wv, c->Hd + 128));
-      SC_CUDA(cudaMemcpyAsync(hbuf.data(), c->Hd, 129 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h1));
+      SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, h1, -1.0));
+      SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h2));
+      SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, h2, -1.0));
+      SC_CUDA(sc::multidot(c, c->Wv, 1, n1, c->Wv, hn2));
+      SC_CUDA(cudaMemcpyAsync(hbuf.data(), c->Hd, (2 * (m + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       SC_CUDA(cudaStreamSynchronize(c->stream));
       double* Hc = &H[(size_t)j];  // column j, row stride m
-      for (int i = 0; i <= j; ++i) Hc[(size_t)i * m] = hbuf[i] + hbuf[64 + i];
-      const double hn = std::sqrt(std::max(hbuf[128], 0.0));
+      for (int i = 0; i <= j; ++i) Hc[(size_t)i * m] = hbuf[i] + hbuf[(m + 1) + i];
+      const double hn = std::sqrt(std::max(hbuf[2 * (m + 1)], 0.0));
       Hc[(size_t)(j + 1) * m] = hn;
       if (!std::isfinite(hn)) return fail(c, SC_ERR_NONFINITE, "non-finite value in GMRES");
       if (hn > 0) SC_CUDA(sc::vec_axpby(c, c->V + (size_t)(j + 1) * n1, 1.0 / hn, c->Wv, 0.0, n1));
@@ -505,7 +525,7 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
     SC_CUDA(sc::cond_boundary(c, c->Xb, 1.0, nullptr, 0.0, c->Ui, c->Wv));
     SC_CUDA(cudaMemcpyAsync(c->Rb, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     SC_CUDA(sc::vec_axpby(c, c->Rb, -1.0, c->Wv, 1.0, n1));
-    beta = dnorm2(c, c->Rb, n1, c->Hd + 200);
+    beta = dnorm2(c, c->Rb, n1, hs);
     resid = beta;
     if (!std::isfinite(beta)) return fail(c, SC_ERR_NONFINITE, "non-finite condensed residual");
     if (beta <= target) ok = true;
@@ -519,7 +539,7 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
   // FP64 global residual ||B - A x|| / ||B||
   SC_CUDA(sc::global_apply(c, xout, c->Rfull));
   SC_CUDA(sc::vec_axpby(c, c->Rfull, 1.0, c->B, -1.0, dofs));
-  const double rn = dnorm2(c, c->Rfull, dofs, c->Hd + 200);
+  const double rn = dnorm2(c, c->Rfull, dofs, hs);
   if (!on_device) SC_CUDA(cudaMemcpyAsync(dQ, xout, dofs * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
   if (s != SC_OK) return s;
@@ -535,6 +555,83 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
   if (!std::isfinite(S.rel_residual)) return fail(c, SC_ERR_NONFINITE, "non-finite solution");
   if (S.rel_residual > c->cfg.rel_tol * 1.0000001 && !(bnorm == 0.0))
     return fail(c, SC_ERR_NOT_CONVERGED, "relative residual " + std::to_string(S.rel_residual) + " above tolerance");
+  return SC_OK;
+}
+
+sc_status sc_launch_count(const sc_ctx* c, long long* count) {
+  if (!c || !count) return SC_ERR_ARG;
+  *count = c->launches;
+  return SC_OK;
+}
+
+sc_status sc_profile_kernel(sc_ctx* c, int kernel_id) {
+  if (!c) return SC_ERR_ARG;
+  if (kernel_id < -1 || kernel_id >= SCK_COUNT) return fail(c, SC_ERR_ARG, "unknown kernel id");
+  cudaStreamSynchronize(c->stream);
+  c->prof_kernel = kernel_id;
+  c->prof_used = 0; c->prof_ms = 0.0; c->prof_count = 0;
+  return SC_OK;
+}
+
+sc_status sc_profile_read(sc_ctx* c, long long* launches, double* total_ms) {
+  if (!c || !launches || !total_ms) return SC_ERR_ARG;
+  SC_CUDA(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->prof_used; ++i) {
+    float ms = 0.f;
+    SC_CUDA(cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+    c->prof_ms += ms; c->prof_count++;
+  }
+  c->prof_used = 0;
+  *launches = c->prof_count; *total_ms = c->prof_ms;
+  return SC_OK;
+}
+
+sc_status sc_kernel_work(const sc_ctx* c, int kernel_id, double* flops, double* bytes) {
+  if (!c || !flops || !bytes) return SC_ERR_ARG;
+  if (!c->has_mesh) return SC_ERR_STATE;
+  const Geo& G = c->G;
+  // neighbour couplings per element by row type
+  double pi = 0.0, pb = 0.0;
+  for (size_t q = 0; q < c->pat.row.size(); ++q) (c->perm[c->pat.row[q]] < G.nin ? pi : pb) += 1.0;
+  const double K = G.K, ni = G.ni, nb = G.nb, ne = G.ne, w = 8.0;
+  double f = 0.0, b = 0.0;
+  switch (kernel_id) {
+    case SCK_COND_INTERIOR:  // A_ib,ee x_b + neighbour couplings, then A_ii^-1 t
+      f = K * (2.0 * ni * nb + 2.0 * 25.0 * pi + 2.0 * ni * ni);
+      b = K * w * (ni * nb + 25.0 * pi + ni * ni + nb + ni);
+      break;
+    case SCK_COND_BOUNDARY:  // [A_bi A_bb] [-u; x_b] + neighbour couplings
+      f = K * (2.0 * nb * ne + 2.0 * 25.0 * pb);
+      b = K * w * (nb * ne + 25.0 * pb + ne + nb);
+      break;
+    case SCK_LU_SOLVE:  // forward + backward substitution with the S_ee factors
+      f = K * 2.0 * nb * nb;
+      b = K * w * (nb * nb + 2.0 * nb);
+      break;
+    case SCK_LU:
+      f = K * (2.0 / 3.0) * nb * nb * nb;
+      b = K * w * 2.0 * nb * nb;
+      break;
+    case SCK_GEMM:  // S_ee -= A_bi,ee Y
+      f = K * 2.0 * nb * nb * ni;
+      b = K * w * (nb * ni + ni * nb + 2.0 * nb * nb);
+      break;
+    case SCK_GJ_INV:
+      f = K * 2.0 * ni * ni * ni;
+      b = K * w * 2.0 * ni * ni;
+      break;
+    case SCK_ASM_OWN:
+      f = 0.0;
+      b = K * w * ne * ne;
+      break;
+    case SCK_GLOBAL_APPLY:
+      f = K * (2.0 * ne * ne + 2.0 * 25.0 * (pi + pb));
+      b = K * w * (ne * ne + 25.0 * (pi + pb) + 2.0 * ne);
+      break;
+    default:
+      return SC_ERR_ARG;
+  }
+  *flops = f; *bytes = b;
   return SC_OK;
 }
 

@@ -335,14 +335,14 @@ __global__ void __launch_bounds__(256) k_asm_own(Geo G, const double* __restrict
                                                  const int* __restrict__ nbr, const int* __restrict__ iperm,
                                                  double* __restrict__ Aown) {
   const int e = blockIdx.x;
-  const int nn = G.nn, ne = G.ne;
+  const int nn = G.nn, lda = G.lda;
   for (int t = threadIdx.x; t < nn * nn; t += blockDim.x) {
     const int pj = t / nn, pr = t % nn;
     double acc[25];
     own_entry(G, NJ, RJ, nbr, e, iperm[pj], iperm[pr], acc);
-    double* out = Aown + (size_t)e * ne * ne + (size_t)(5 * pj) * ne + 5 * pr;
+    double* out = Aown + (size_t)e * own_stride(G) + (size_t)(5 * pj) * lda + own_col(G, pr, 0);
     for (int k = 0; k < 5; ++k)
-      for (int l = 0; l < 5; ++l) out[(size_t)k * ne + l] = acc[k * 5 + l];
+      for (int l = 0; l < 5; ++l) out[(size_t)k * lda + l] = acc[k * 5 + l];
   }
 }
 
@@ -427,8 +427,9 @@ __global__ void k_asm_cross(Geo G, const double* __restrict__ NJ, const double* 
   const int e = (int)(t / G.NP), pr = (int)(t % G.NP);
   double acc[25];
   cross_entry(G, NJ, RJ, nbr, e, prow[pr], pslot[pr], pcol[pr], acc);
-  double* out = X + t * 25;
-  for (int kl = 0; kl < 25; ++kl) out[kl] = acc[kl];
+  // layout X[e][k][pair][l]: the couplings of one row variable are contiguous
+  for (int k = 0; k < 5; ++k)
+    for (int l = 0; l < 5; ++l) X[(((size_t)e * 5 + k) * G.NP + pr) * 5 + l] = acc[k * 5 + l];
 }
 
 inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -440,6 +441,7 @@ namespace sc {
 cudaError_t launch_residual(sc_ctx* c) {
   const Geo& G = c->G;
   const size_t nodes = (size_t)G.K * G.nn;
+  count_launch(c, 3);
   k_lift<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, c->Q, c->d_nbr, c->grad);
   k_flux<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, c->Q, c->grad, c->F);
   k_resid<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, c->Q, c->Qh, c->grad, c->F, c->d_nbr, c->B);
@@ -448,6 +450,7 @@ cudaError_t launch_residual(sc_ctx* c) {
 
 cudaError_t launch_history(sc_ctx* c, const double* Qs, const double* Qsm1) {
   const size_t n = (size_t)c->G.K * c->G.nn * 5;
+  count_launch(c);
   k_history<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->G, Qs, Qsm1, c->Qh, n, c->bdf);
   return cudaGetLastError();
 }
@@ -455,10 +458,14 @@ cudaError_t launch_history(sc_ctx* c, const double* Qs, const double* Qsm1) {
 cudaError_t launch_assembly(sc_ctx* c) {
   const Geo& G = c->G;
   const size_t nodes = (size_t)G.K * G.nn;
+  count_launch(c, 3);
   k_nodejac<<<blocks_for(nodes, 64), 64, 0, c->stream>>>(G, c->Q, c->grad, c->NJ);
   const size_t fn = (size_t)G.K * 6 * G.p * G.p;
   k_roejac<<<blocks_for(fn, 64), 64, 0, c->stream>>>(G, c->Q, c->d_nbr, c->RJ);
-  k_asm_own<<<G.K, 256, 0, c->stream>>>(G, c->NJ, c->RJ, c->d_nbr, c->d_iperm, c->Aown);
+  {
+    ProfScope ps(c, SCK_ASM_OWN);
+    k_asm_own<<<G.K, 256, 0, c->stream>>>(G, c->NJ, c->RJ, c->d_nbr, c->d_iperm, c->Aown);
+  }
   const size_t np = (size_t)G.K * G.NP;
   k_asm_cross<<<blocks_for(np, 128), 128, 0, c->stream>>>(G, c->NJ, c->RJ, c->d_nbr, c->d_prow, c->d_pslot,
                                                           c->d_pcol, c->X);

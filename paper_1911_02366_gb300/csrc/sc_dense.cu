@@ -8,7 +8,8 @@
 //               tiles, 4x4 register micro-tiles).
 //   k_lu        right-looking blocked LU with partial pivoting of a batch of blocks
 //               in global memory (32-column panels factorised in shared memory).
-//   k_lu_solve  z = (P^T L U)^-1 v for every element (one warp per element).
+//   k_lu_solve  z = (P^T L U)^-1 v for every element (one CTA per element, 32-row
+//               panels with a warp-shuffle solve of each diagonal triangle).
 #include "sc_internal.cuh"
 
 namespace {
@@ -27,7 +28,7 @@ __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
 
 template <class T>
 __global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int lda,
-                         T* __restrict__ Ainv, long long strideO, int* __restrict__ status) {
+                         T* __restrict__ Ainv, long long strideO, int ldo, int* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
   const int ld = n + 1;
   T* M = reinterpret_cast<T*>(smem_raw);
@@ -88,7 +89,7 @@ __global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int 
     __syncthreads();
   }
   T* Oe = Ainv + (long long)e * strideO;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Oe[t] = M[(t / n) * ld + (t % n)];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Oe[(long long)(t / n) * ldo + (t % n)] = M[(t / n) * ld + (t % n)];
   if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
 }
 
@@ -268,41 +269,101 @@ __global__ void __launch_bounds__(256) k_lu(int n, T* __restrict__ A, long long 
   if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
 }
 
-// z = A^-1 v with the LU factors and pivots of k_lu; one warp per element.
-template <class T>
-__global__ void k_lu_solve(int n, const T* __restrict__ LU, long long stride, int lda,
-                           const int* __restrict__ piv_all, const double* __restrict__ v,
-                           double* __restrict__ z, int nelem) {
-  extern __shared__ unsigned char smem_raw[];
-  double* x = reinterpret_cast<double*>(smem_raw) + (size_t)(threadIdx.x / 32) * n;
-  const int lane = threadIdx.x % 32;
-  const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+// Sequential LAPACK-style row interchanges -> one gather permutation per element:
+// row i of P A is row rowperm[i] of A.
+__global__ void k_piv_to_perm(int n, const int* __restrict__ piv_all, int* __restrict__ rowperm, int nelem) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nelem) return;
-  const T* M = LU + (long long)e * stride;
   const int* piv = piv_all + (long long)e * n;
-  for (int i = lane; i < n; i += 32) x[i] = v[(long long)e * n + i];
-  __syncwarp();
-  if (lane == 0)
-    for (int k = 0; k < n; ++k) {
-      const int p = piv[k];
-      if (p != k) { double t = x[k]; x[k] = x[p]; x[p] = t; }
+  int* rp = rowperm + (long long)e * n;
+  for (int i = 0; i < n; ++i) rp[i] = i;
+  for (int k = 0; k < n; ++k) {
+    const int p = piv[k];
+    if (p != k) { const int t = rp[k]; rp[k] = rp[p]; rp[p] = t; }
+  }
+}
+
+__device__ __forceinline__ double warp_sum_d(double s) {
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+__device__ __forceinline__ double dot_row(const double* __restrict__ row, const double* xs, int k0, int k1, int lane) {
+  // sum_{k0 <= k < k1} row[k] xs[k]; k0 even (16-byte aligned double2 loads)
+  const double2* r2 = reinterpret_cast<const double2*>(row + k0);
+  const double2* x2 = reinterpret_cast<const double2*>(xs + k0);
+  const int len = k1 - k0, len2 = len >> 1;
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll 4
+  for (int i = lane; i < len2; i += 32) {
+    const double2 a = __ldg(r2 + i), b = x2[i];
+    s0 = fma(a.x, b.x, s0); s1 = fma(a.y, b.y, s1);
+  }
+  if ((len & 1) && lane == 0) s0 = fma(__ldg(row + k1 - 1), xs[k1 - 1], s0);
+  return s0 + s1;
+}
+
+// z = (P^T L U)^-1 v for every element: one CTA per element, 32-row panels.  Each panel
+// first subtracts the already-solved part (rows spread over the warps, double2 row
+// reads), then the 32 x 32 diagonal triangle is staged in shared memory and solved by
+// warp 0 with shuffles.
+__global__ void __launch_bounds__(256) k_lu_solve(int n, const double* __restrict__ LU, long long stride, int lda,
+                                                  const int* __restrict__ rowperm, const double* __restrict__ v,
+                                                  double* __restrict__ z) {
+  extern __shared__ __align__(16) double xs[];
+  __shared__ double Dg[32][33];
+  const int e = blockIdx.x;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const double* M = LU + (long long)e * stride;
+  const int* rp = rowperm + (long long)e * n;
+  const double* ve = v + (long long)e * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = ve[rp[i]];
+  __syncthreads();
+  for (int i0 = 0; i0 < n; i0 += 32) {  // unit lower triangle
+    const int bs = min(32, n - i0);
+    for (int r = warp; r < bs; r += nw) {
+      const double* row = M + (long long)(i0 + r) * lda;
+      Dg[r][lane] = lane < bs ? row[i0 + lane] : 0.0;
+      if (i0 > 0) {
+        const double s = warp_sum_d(dot_row(row, xs, 0, i0, lane));
+        if (lane == 0) xs[i0 + r] -= s;
+      }
     }
-  __syncwarp();
-  for (int i = 1; i < n; ++i) {  // unit lower triangle
-    double s = 0.0;
-    for (int k = lane; k < i; k += 32) s = fma((double)M[(long long)i * lda + k], x[k], s);
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) x[i] -= s;
-    __syncwarp();
+    __syncthreads();
+    if (warp == 0) {
+      double xl = lane < bs ? xs[i0 + lane] : 0.0;
+      for (int rr = 0; rr < bs; ++rr) {
+        const double xr = __shfl_sync(0xffffffffu, xl, rr);
+        if (lane > rr) xl = fma(-Dg[lane][rr], xr, xl);
+      }
+      if (lane < bs) xs[i0 + lane] = xl;
+    }
+    __syncthreads();
   }
-  for (int i = n - 1; i >= 0; --i) {  // upper triangle
-    double s = 0.0;
-    for (int k = i + 1 + lane; k < n; k += 32) s = fma((double)M[(long long)i * lda + k], x[k], s);
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) x[i] = (x[i] - s) / (double)M[(long long)i * lda + i];
-    __syncwarp();
+  const int nblk = (n + 31) / 32;
+  for (int b = nblk - 1; b >= 0; --b) {  // upper triangle
+    const int i0 = b * 32, bs = min(32, n - i0), i1 = i0 + bs;
+    for (int r = warp; r < bs; r += nw) {
+      const double* row = M + (long long)(i0 + r) * lda;
+      Dg[r][lane] = lane < bs ? row[i0 + lane] : 0.0;
+      if (i1 < n) {
+        const double s = warp_sum_d(dot_row(row, xs, i1, n, lane));
+        if (lane == 0) xs[i0 + r] -= s;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double xl = lane < bs ? xs[i0 + lane] : 0.0;
+      for (int rr = bs - 1; rr >= 0; --rr) {
+        if (lane == rr) xl = xl / Dg[rr][rr];
+        const double xr = __shfl_sync(0xffffffffu, xl, rr);
+        if (lane < rr) xl = fma(-Dg[lane][rr], xr, xl);
+      }
+      if (lane < bs) xs[i0 + lane] = xl;
+    }
+    __syncthreads();
   }
-  for (int i = lane; i < n; i += 32) z[(long long)e * n + i] = x[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) z[(long long)e * n + i] = xs[i];
 }
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
@@ -315,35 +376,47 @@ namespace sc {
 // LU(S_ee).
 cudaError_t launch_condense(sc_ctx* c) {
   const Geo& G = c->G;
-  const int ni = G.ni, nb = G.nb, ne = G.ne, K = G.K;
+  const int ni = G.ni, nb = G.nb, K = G.K, lda = G.lda, cb0 = G.cb0, ldi = G.ldi, lds = G.lds;
+  const long long sA = (long long)own_stride(G);
   cudaError_t err;
   if (ni > 0) {
     const size_t smem = (size_t)ni * (ni + 1) * sizeof(double) + ni * sizeof(double) + ni * sizeof(int);
     err = cudaFuncSetAttribute(k_gj_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_gj_inv<double><<<K, 256, smem, c->stream>>>(ni, c->Aown, (long long)ne * ne, ne, c->Ainv,
-                                                  (long long)ni * ni, c->d_status);
+    ProfScope ps(c, SCK_GJ_INV);
+    k_gj_inv<double><<<K, 256, smem, c->stream>>>(ni, c->Aown, sA, lda, c->Ainv, (long long)ni * ldi, ldi,
+                                                  c->d_status);
+  }
+  if (ni > 0) {
     // Y = A_ii^-1 * A_ib,ee  (ni x nb)
+    count_launch(c);
     dim3 g1(cdiv(nb, 64), cdiv(ni, 64), K);
-    k_gemm<double><<<g1, 256, 0, c->stream>>>(ni, nb, ni, 1.0, c->Ainv, (long long)ni * ni, ni,
-                                              c->Aown + ni, (long long)ne * ne, ne, 0.0,
+    k_gemm<double><<<g1, 256, 0, c->stream>>>(ni, nb, ni, 1.0, c->Ainv, (long long)ni * ldi, ldi,
+                                              c->Aown + cb0, sA, lda, 0.0,
                                               c->Ytmp, (long long)ni * nb, nb);
   }
   // S_ee = A_bb,ee - A_bi,ee * Y
+  count_launch(c);
   dim3 gc(cdiv((long long)nb * nb, 256 * 8), K);
-  k_copy_block<double><<<gc, 256, 0, c->stream>>>(nb, nb, c->Aown + (size_t)ni * ne + ni, (long long)ne * ne, ne,
-                                                  c->See, (long long)nb * nb, nb);
+  k_copy_block<double><<<gc, 256, 0, c->stream>>>(nb, nb, c->Aown + (size_t)ni * lda + cb0, sA, lda,
+                                                  c->See, (long long)nb * lds, lds);
   if (ni > 0) {
+    ProfScope ps(c, SCK_GEMM);
     dim3 g2(cdiv(nb, 64), cdiv(nb, 64), K);
-    k_gemm<double><<<g2, 256, 0, c->stream>>>(nb, nb, ni, -1.0, c->Aown + (size_t)ni * ne, (long long)ne * ne, ne,
+    k_gemm<double><<<g2, 256, 0, c->stream>>>(nb, nb, ni, -1.0, c->Aown + (size_t)ni * lda, sA, lda,
                                               c->Ytmp, (long long)ni * nb, nb, 1.0,
-                                              c->See, (long long)nb * nb, nb);
+                                              c->See, (long long)nb * lds, lds);
   }
   if (c->cfg.precond == SC_PC_BLOCK_JACOBI) {
     const size_t smem = (size_t)nb * (PW + 1) * sizeof(double);
     err = cudaFuncSetAttribute(k_lu<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_lu<double><<<K, 256, smem, c->stream>>>(nb, c->See, (long long)nb * nb, nb, c->piv, c->d_status);
+    {
+      ProfScope ps(c, SCK_LU);
+      k_lu<double><<<K, 256, smem, c->stream>>>(nb, c->See, (long long)nb * lds, lds, c->piv, c->d_status);
+    }
+    count_launch(c);
+    k_piv_to_perm<<<cdiv(K, 128), 128, 0, c->stream>>>(nb, c->piv, c->rowperm, K);
   }
   return cudaGetLastError();
 }
@@ -354,12 +427,9 @@ cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
   if (c->cfg.precond != SC_PC_BLOCK_JACOBI) {
     return cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   }
-  const int wpb = 4;
-  const size_t smem = (size_t)wpb * G.nb * sizeof(double);
-  cudaError_t err = cudaFuncSetAttribute(k_lu_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  k_lu_solve<double><<<cdiv(G.K, wpb), 32 * wpb, smem, c->stream>>>(G.nb, c->See, (long long)G.nb * G.nb, G.nb,
-                                                                    c->piv, v, z, G.K);
+  const size_t smem = (size_t)G.nb * sizeof(double);
+  ProfScope ps(c, SCK_LU_SOLVE);
+  k_lu_solve<<<G.K, 256, smem, c->stream>>>(G.nb, c->See, (long long)G.nb * G.lds, G.lds, c->rowperm, v, z);
   return cudaGetLastError();
 }
 

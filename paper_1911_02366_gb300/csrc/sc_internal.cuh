@@ -19,6 +19,8 @@ struct Geo {
   int n, N, p, nn, K;     // elements per direction, order, N+1, nodes/element, elements
   int ne, nin, nbn, ni, nb;  // dofs/element, interior nodes, boundary nodes, interior dofs, boundary dofs
   int NP;                 // neighbour-coupling pairs per element
+  int lda, cb0;           // own block: row stride, column of the first boundary dof (both % 4 == 0)
+  int ldi, lds;           // row strides of A_ii^-1 and of the S_ee factors (% 4 == 0)
   double h, Jf, dx, inv_hw;  // element size, (h/2)^2, 2/h, 1/(h w_N)
   double dt, c0;          // time step, BDF leading coefficient (1 or 3/2)
   double gamma, Pr, Re, Ma, Ts, roe_delta;
@@ -33,6 +35,20 @@ SC_HD inline int face_slot(int d, int s) { return 2 * d + (s > 0); }
 SC_HD inline int edge_pair_index(int d1, int d2) {  // d1 < d2
   return d1 == 0 ? (d2 == 1 ? 0 : 1) : 2;
 }
+
+// Column of dof (permuted node position pos, variable l) in an own element block:
+// interior dofs first, then the boundary dofs starting at the aligned column cb0.
+SC_HD inline int own_col(const Geo& G, int pos, int l) {
+  return pos < G.nin ? 5 * pos + l : G.cb0 + 5 * (pos - G.nin) + l;
+}
+SC_HD inline size_t own_stride(const Geo& G) { return (size_t)G.ne * G.lda; }
+
+// Packed description of one neighbour coupling column: neighbour slot (bits 26..30),
+// interior flag (bit 25), offset of the column inside that neighbour's boundary (or
+// interior) part of a condensed vector (bits 0..24).
+SC_HD inline int pinfo_slot(int v) { return (v >> 26) & 31; }
+SC_HD inline int pinfo_interior(int v) { return (v >> 25) & 1; }
+SC_HD inline int pinfo_offset(int v) { return v & ((1 << 25) - 1); }
 
 // ------------------------------------------------------------------ dual numbers
 // Five-direction forward-mode dual used to differentiate the point fluxes.
@@ -239,15 +255,47 @@ struct sc_ctx {
   double *Q = nullptr, *Qh = nullptr, *grad = nullptr, *F = nullptr, *B = nullptr;
   double *NJ = nullptr, *RJ = nullptr, *Aown = nullptr, *X = nullptr;
   int *d_nbr = nullptr, *d_perm = nullptr, *d_iperm = nullptr;
-  int *d_prow = nullptr, *d_pslot = nullptr, *d_pcol = nullptr, *d_pptr = nullptr, *d_pids = nullptr;
+  int *d_prow = nullptr, *d_pslot = nullptr, *d_pcol = nullptr, *d_pptr = nullptr, *d_pinfo = nullptr;
   double *Ainv = nullptr, *Ytmp = nullptr, *See = nullptr;
-  int *piv = nullptr, *d_status = nullptr;
+  int *piv = nullptr, *rowperm = nullptr, *d_status = nullptr;
   // Krylov workspace (boundary space of size n1 = K*nb)
   double *V = nullptr, *Wv = nullptr, *Zv = nullptr, *Xb = nullptr, *Gb = nullptr, *Rb = nullptr;
   double *Ui = nullptr, *Tb = nullptr, *Hd = nullptr, *partial = nullptr, *Xfull = nullptr, *Rfull = nullptr;
   int restart_alloc = 0;
   cudaEvent_t ev[8] = {};
+  // measurement hooks: kernel launches since creation, and optional CUDA-event timing
+  // of every launch of one selected kernel (see sc_profile_kernel)
+  long long launches = 0;
+  int prof_kernel = -1;
+  std::vector<cudaEvent_t> prof_ev;  // start/stop pairs, reused
+  int prof_used = 0;
+  double prof_ms = 0.0;
+  long long prof_count = 0;
 };
+
+// Kernel ids of the measurement hook (sc_profile_kernel).
+enum { SCK_COND_INTERIOR = 0, SCK_COND_BOUNDARY = 1, SCK_LU_SOLVE = 2, SCK_LU = 3, SCK_GEMM = 4,
+       SCK_GJ_INV = 5, SCK_ASM_OWN = 6, SCK_GLOBAL_APPLY = 7, SCK_COUNT = 8 };
+
+// Bracket one launch of kernel `id` with events when it is the profiled kernel.
+struct ProfScope {
+  sc_ctx* c; int id; bool on;
+  ProfScope(sc_ctx* cc, int kid) : c(cc), id(kid), on(cc->prof_kernel == kid) {
+    c->launches++;
+    if (on) {
+      if ((int)c->prof_ev.size() < 2 * (c->prof_used + 1)) {
+        cudaEvent_t a, b; cudaEventCreate(&a); cudaEventCreate(&b);
+        c->prof_ev.push_back(a); c->prof_ev.push_back(b);
+      }
+      cudaEventRecord(c->prof_ev[2 * c->prof_used], c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (on) { cudaEventRecord(c->prof_ev[2 * c->prof_used + 1], c->stream); c->prof_used++; }
+  }
+};
+// Count a launch that is never profiled.
+inline void count_launch(sc_ctx* c, int n = 1) { c->launches += n; }
 
 // kernels launchers (defined in the .cu files)
 namespace sc {

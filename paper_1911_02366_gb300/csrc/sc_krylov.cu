@@ -17,101 +17,122 @@ __device__ __forceinline__ double warp_sum(double s) {
   return s;
 }
 
-// Neighbour part of row (node j, variable k): sum over couplings of X * vec(neighbour).
-// want_b / want_i select couplings whose column node is a boundary / interior node of
-// the neighbour; vb / vi hold boundary / interior vectors (element-major).
+// Dot product of a row segment (global, 16-byte aligned) with a vector in shared
+// memory (16-byte aligned), one warp, double2 loads; len may be odd.
+__device__ __forceinline__ double warp_dot(const double* __restrict__ row, const double* v, int len, int lane) {
+  const double2* r2 = reinterpret_cast<const double2*>(row);
+  const double2* v2 = reinterpret_cast<const double2*>(v);
+  const int len2 = len >> 1;
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll 4
+  for (int i = lane; i < len2; i += 32) {
+    const double2 a = __ldg(r2 + i);
+    const double2 b = v2[i];
+    s0 = fma(a.x, b.x, s0);
+    s1 = fma(a.y, b.y, s1);
+  }
+  if ((len & 1) && lane == 0) s0 = fma(__ldg(row + len - 1), v[len - 1], s0);
+  return s0 + s1;
+}
+
+// Neighbour couplings of row (node j, variable k) of element e.  The couplings of one
+// row are contiguous in X (layout X[e][k][pair][l]); vb / vi are the condensed
+// boundary / interior vectors of all elements (either may be null), scaled by cb / ci.
 __device__ __forceinline__ double cross_row(const Geo& G, int e, int j, int k, const double* __restrict__ X,
-                                            const int* __restrict__ nbr, const int* __restrict__ pptr,
-                                            const int* __restrict__ pids, const int* __restrict__ pslot,
-                                            const int* __restrict__ pcol, const int* __restrict__ perm,
-                                            const double* __restrict__ vb, const double* __restrict__ vi,
-                                            int lane) {
+                                            const int* nbr_s, const int* __restrict__ pptr,
+                                            const int* __restrict__ pinfo, const double* __restrict__ vb, double cb,
+                                            const double* __restrict__ vi, double ci, int lane) {
+  const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
+  const double* Xr = X + (((size_t)e * 5 + k) * G.NP + q0) * 5;
   double s = 0.0;
-  const int b = pptr[j], en = pptr[j + 1];
-  for (int q = b + lane; q < en; q += 32) {
-    const int pr = pids[q];
-    const int nb = nbr[e * 18 + pslot[pr]];
-    const int pos = perm[pcol[pr]];
-    const double* xv;
-    if (pos >= G.nin) {
-      if (!vb) continue;
-      xv = vb + (size_t)nb * G.nb + 5 * (pos - G.nin);
-    } else {
+  for (int f = lane; f < 5 * (q1 - q0); f += 32) {
+    const int q = q0 + f / 5, l = f % 5;
+    const int info = __ldg(pinfo + q);
+    const int nb = nbr_s[pinfo_slot(info)];
+    const int off = pinfo_offset(info) + l;
+    double xv;
+    if (pinfo_interior(info)) {
       if (!vi) continue;
-      xv = vi + (size_t)nb * G.ni + 5 * pos;
+      xv = ci * vi[(size_t)nb * G.ni + off];
+    } else {
+      if (!vb) continue;
+      xv = cb * vb[(size_t)nb * G.nb + off];
     }
-    const double* blk = X + ((size_t)e * G.NP + pr) * 25 + k * 5;
-    for (int l = 0; l < 5; ++l) s = fma(blk[l], xv[l], s);
+    s = fma(__ldg(Xr + f), xv, s);
   }
   return s;
 }
 
+// Interior pass: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e).
 __global__ void __launch_bounds__(256) k_cond_interior(Geo G, const double* __restrict__ Aown,
     const double* __restrict__ X, const double* __restrict__ Ainv, const int* __restrict__ nbr,
-    const int* __restrict__ pptr, const int* __restrict__ pids, const int* __restrict__ pslot,
-    const int* __restrict__ pcol, const int* __restrict__ perm, const int* __restrict__ iperm,
+    const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm,
     const double* __restrict__ xb, double beta, const double* __restrict__ Bfull, double alpha,
     double* __restrict__ u) {
-  extern __shared__ double sm[];
-  double* t = sm;  // ni
-  const int e = blockIdx.x, ni = G.ni, nb = G.nb, ne = G.ne;
+  extern __shared__ __align__(16) double sm[];
+  const int e = blockIdx.x, ni = G.ni, nb = G.nb;
+  double* v = sm;              // nb: x_e
+  double* t = sm + nb;         // ldi: right-hand side of the interior solve, zero padded
+  __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-  const double* Ae = Aown + (size_t)e * ne * ne;
+  if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v[i] = xb ? xb[(size_t)e * nb + i] : 0.0;
+  for (int i = ni + threadIdx.x; i < G.ldi; i += blockDim.x) t[i] = 0.0;
+  __syncthreads();
+  const double* Ae = Aown + (size_t)e * own_stride(G);
   for (int ri = warp; ri < ni; ri += nw) {
-    const int j = iperm[ri / 5], k = ri % 5;
+    const int j = __ldg(iperm + ri / 5), k = ri % 5;
     double s = 0.0;
     if (xb) {
-      const double* row = Ae + (size_t)ri * ne + ni;
-      const double* xe = xb + (size_t)e * nb;
-      for (int cc = lane; cc < nb; cc += 32) s = fma(row[cc], xe[cc], s);
-      s += cross_row(G, e, j, k, X, nbr, pptr, pids, pslot, pcol, perm, xb, nullptr, lane);
+      s = warp_dot(Ae + (size_t)ri * G.lda + G.cb0, v, nb, lane);
+      s += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, 1.0, nullptr, 0.0, lane);
       s = warp_sum(s);
     }
     if (lane == 0) {
-      double v = beta * s;
-      if (Bfull) v += alpha * Bfull[((size_t)e * G.nn + j) * 5 + k];
-      t[ri] = v;
+      double val = beta * s;
+      if (Bfull) val += alpha * Bfull[((size_t)e * G.nn + j) * 5 + k];
+      t[ri] = val;
     }
   }
   __syncthreads();
-  const double* Ie = Ainv + (size_t)e * ni * ni;
+  const double* Ie = Ainv + (size_t)e * ni * G.ldi;
   for (int ri = warp; ri < ni; ri += nw) {
-    double s = 0.0;
-    for (int cc = lane; cc < ni; cc += 32) s = fma(Ie[(size_t)ri * ni + cc], t[cc], s);
-    s = warp_sum(s);
+    const double s = warp_sum(warp_dot(Ie + (size_t)ri * G.ldi, t, G.ldi, lane));
     if (lane == 0) u[(size_t)e * ni + ri] = s;
   }
 }
 
+// Boundary pass: y_e = gamma B_b,e + delta (A_bb x_b)_e - (A_bi u)_e.
 __global__ void __launch_bounds__(256) k_cond_boundary(Geo G, const double* __restrict__ Aown,
     const double* __restrict__ X, const int* __restrict__ nbr,
-    const int* __restrict__ pptr, const int* __restrict__ pids, const int* __restrict__ pslot,
-    const int* __restrict__ pcol, const int* __restrict__ perm, const int* __restrict__ iperm,
+    const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm,
     const double* __restrict__ xb, double delta, const double* __restrict__ Bfull, double gamma_,
     const double* __restrict__ u, double* __restrict__ y) {
-  const int e = blockIdx.x, ni = G.ni, nb = G.nb, ne = G.ne;
+  extern __shared__ __align__(16) double sm[];
+  const int e = blockIdx.x, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, cb0 = G.cb0;
+  double* v = sm;  // lda: [-u_e | 0 | delta x_e | 0] in own-column order
+  __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-  const double* Ae = Aown + (size_t)e * ne * ne;
-  for (int rb = warp; rb < nb; rb += nw) {
-    const int ri = ni + rb;
-    const int j = iperm[ri / 5], k = ri % 5;
-    const double* row = Ae + (size_t)ri * ne;
-    double sb = 0.0, si = 0.0;
-    if (xb) {
-      const double* xe = xb + (size_t)e * nb;
-      for (int cc = lane; cc < nb; cc += 32) sb = fma(row[ni + cc], xe[cc], sb);
-      sb += cross_row(G, e, j, k, X, nbr, pptr, pids, pslot, pcol, perm, xb, nullptr, lane);
-    }
-    if (u) {
-      const double* ue = u + (size_t)e * ni;
-      for (int cc = lane; cc < ni; cc += 32) si = fma(row[cc], ue[cc], si);
-      si += cross_row(G, e, j, k, X, nbr, pptr, pids, pslot, pcol, perm, nullptr, u, lane);
-    }
-    const double s = warp_sum(delta * sb - si);
+  if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
+  for (int i = threadIdx.x; i < lda; i += blockDim.x) {
+    double val = 0.0;
+    if (i < ni) { if (u) val = -u[(size_t)e * ni + i]; }
+    else if (i >= cb0 && i < cb0 + nb) { if (xb) val = delta * xb[(size_t)e * nb + i - cb0]; }
+    v[i] = val;
+  }
+  __syncthreads();
+  const double* Ae = Aown + (size_t)e * own_stride(G);
+  const int c0 = u ? 0 : cb0;                 // skip the A_bi columns when u is absent
+  const int len = (xb ? cb0 + nb : ni) - c0;  // and the A_bb columns when x_b is absent
+  for (int ri = ni + warp; ri < ne; ri += nw) {
+    const int j = __ldg(iperm + ri / 5), k = ri % 5;
+    double s = (xb || u) ? warp_dot(Ae + (size_t)ri * lda + c0, v + c0, len, lane) : 0.0;
+    s += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, delta, u, -1.0, lane);
+    s = warp_sum(s);
     if (lane == 0) {
-      double v = s;
-      if (Bfull) v += gamma_ * Bfull[((size_t)e * G.nn + j) * 5 + k];
-      y[(size_t)e * nb + rb] = v;
+      double val = s;
+      if (Bfull) val += gamma_ * Bfull[((size_t)e * G.nn + j) * 5 + k];
+      y[(size_t)e * nb + ri - ni] = val;
     }
   }
 }
@@ -119,30 +140,31 @@ __global__ void __launch_bounds__(256) k_cond_boundary(Geo G, const double* __re
 // y = A x on the full system, natural global dof order.
 __global__ void __launch_bounds__(256) k_global_apply(Geo G, const double* __restrict__ Aown,
     const double* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
-    const int* __restrict__ pids, const int* __restrict__ pslot, const int* __restrict__ pcol,
-    const int* __restrict__ iperm, const double* __restrict__ x, double* __restrict__ y) {
-  extern __shared__ double sm[];
-  double* xe = sm;  // ne, permuted order
-  const int e = blockIdx.x, ne = G.ne, nn = G.nn;
+    const int* __restrict__ pinfo, const int* __restrict__ pcol, const int* __restrict__ iperm,
+    const double* __restrict__ x, double* __restrict__ y) {
+  extern __shared__ __align__(16) double sm[];
+  double* v = sm;  // lda, own-column order
+  __shared__ int nbr_s[18];
+  const int e = blockIdx.x, ne = G.ne, nn = G.nn, lda = G.lda;
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
+  for (int i = threadIdx.x; i < lda; i += blockDim.x) v[i] = 0.0;
+  __syncthreads();
   for (int t = threadIdx.x; t < ne; t += blockDim.x) {
     const int pos = t / 5, k = t % 5;
-    xe[t] = x[((size_t)e * nn + iperm[pos]) * 5 + k];
+    v[own_col(G, pos, k)] = x[((size_t)e * nn + iperm[pos]) * 5 + k];
   }
   __syncthreads();
-  const double* Ae = Aown + (size_t)e * ne * ne;
+  const double* Ae = Aown + (size_t)e * own_stride(G);
   for (int ri = warp; ri < ne; ri += nw) {
-    const int j = iperm[ri / 5], k = ri % 5;
-    const double* row = Ae + (size_t)ri * ne;
-    double s = 0.0;
-    for (int cc = lane; cc < ne; cc += 32) s = fma(row[cc], xe[cc], s);
-    const int b = pptr[j], en = pptr[j + 1];
-    for (int q = b + lane; q < en; q += 32) {
-      const int pr = pids[q];
-      const int nbe = nbr[e * 18 + pslot[pr]];
-      const double* xv = x + ((size_t)nbe * nn + pcol[pr]) * 5;
-      const double* blk = X + ((size_t)e * G.NP + pr) * 25 + k * 5;
-      for (int l = 0; l < 5; ++l) s = fma(blk[l], xv[l], s);
+    const int j = __ldg(iperm + ri / 5), k = ri % 5;
+    double s = warp_dot(Ae + (size_t)ri * lda, v, lda, lane);
+    const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
+    const double* Xr = X + (((size_t)e * 5 + k) * G.NP + q0) * 5;
+    for (int f = lane; f < 5 * (q1 - q0); f += 32) {
+      const int q = q0 + f / 5, l = f % 5;
+      const int nbe = nbr_s[pinfo_slot(__ldg(pinfo + q))];
+      s = fma(__ldg(Xr + f), x[((size_t)nbe * nn + __ldg(pcol + q)) * 5 + l], s);
     }
     s = warp_sum(s);
     if (lane == 0) y[((size_t)e * nn + j) * 5 + k] = s;
@@ -159,35 +181,41 @@ __global__ void k_scatter(Geo G, const int* __restrict__ iperm, const double* __
   x[((size_t)e * G.nn + iperm[pos]) * 5 + k] = v;
 }
 
-// Partial dot products of nvec vectors V[i] (stride n) with w: partial[block][i].
-__global__ void k_multidot_partial(const double* __restrict__ V, int nvec, size_t n,
-                                   const double* __restrict__ w, double* __restrict__ partial) {
-  __shared__ double red[64][8];
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  double acc[64];
-  for (int i = 0; i < nvec; ++i) acc[i] = 0.0;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const double wt = w[t];
-    for (int i = 0; i < nvec; ++i) acc[i] = fma(V[(size_t)i * n + t], wt, acc[i]);
-  }
-  for (int i = 0; i < nvec; ++i) {
-    const double s = warp_sum(acc[i]);
-    if (lane == 0) red[i][warp] = s;
-  }
+// Partial dot products <V[i], w> over a slice of the vectors: grid (chunks, nvec);
+// partial[i * gridDim.x + chunk].
+__global__ void __launch_bounds__(256) k_multidot_partial(const double* __restrict__ V, size_t n,
+                                                          const double* __restrict__ w,
+                                                          double* __restrict__ partial) {
+  __shared__ double red[8];
+  const int i = blockIdx.y;
+  const double* v = V + (size_t)i * n;
+  double s = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    s = fma(v[t], w[t], s);
+  s = warp_sum(s);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
   __syncthreads();
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < (int)(blockDim.x / 32); ++k) s += red[i][k];
-    partial[(size_t)blockIdx.x * 64 + i] = s;
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int k = 0; k < (int)(blockDim.x / 32); ++k) r += red[k];
+    partial[(size_t)i * gridDim.x + blockIdx.x] = r;
   }
 }
 
-__global__ void k_multidot_final(const double* __restrict__ partial, int nblocks, int nvec, double* __restrict__ out) {
-  const int i = threadIdx.x;
+__global__ void k_multidot_final(const double* __restrict__ partial, int nchunks, int nvec, double* __restrict__ out) {
+  const int i = blockIdx.x;
   if (i >= nvec) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * 64 + i];
-  out[i] = s;
+  for (int b = threadIdx.x; b < nchunks; b += blockDim.x) s += partial[(size_t)i * nchunks + b];
+  s = warp_sum(s);
+  __shared__ double red[8];
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int k = 0; k < (int)(blockDim.x / 32); ++k) r += red[k];
+    out[i] = r;
+  }
 }
 
 __global__ void k_vec_update(double* __restrict__ w, const double* __restrict__ V, int nvec, size_t n,
@@ -212,6 +240,7 @@ __global__ void k_axpby(double* __restrict__ y, double a, const double* __restri
 }
 
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs
+constexpr int kDotChunks = 152;
 
 }  // namespace
 
@@ -220,55 +249,64 @@ namespace sc {
 cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double* Bfull, double alpha, double* u) {
   const Geo& G = c->G;
   if (G.ni == 0) return cudaSuccess;
-  k_cond_interior<<<G.K, 256, G.ni * sizeof(double), c->stream>>>(G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr,
-      c->d_pids, c->d_pslot, c->d_pcol, c->d_perm, c->d_iperm, xb, beta, Bfull, alpha, u);
+  const size_t smem = (size_t)(G.nb + G.ldi) * sizeof(double);
+  ProfScope ps(c, SCK_COND_INTERIOR);
+  k_cond_interior<<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo,
+                                                 c->d_iperm, xb, beta, Bfull, alpha, u);
   return cudaGetLastError();
 }
 
 cudaError_t cond_boundary(sc_ctx* c, const double* xb, double delta, const double* Bfull, double gamma_,
                           const double* u, double* y) {
   const Geo& G = c->G;
-  k_cond_boundary<<<G.K, 256, 0, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pids, c->d_pslot,
-      c->d_pcol, c->d_perm, c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
+  const size_t smem = (size_t)G.lda * sizeof(double);
+  ProfScope ps(c, SCK_COND_BOUNDARY);
+  k_cond_boundary<<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm,
+                                                 xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
   return cudaGetLastError();
 }
 
 cudaError_t global_apply(sc_ctx* c, const double* x, double* y) {
   const Geo& G = c->G;
-  const size_t smem = (size_t)G.ne * sizeof(double);
-  cudaError_t err = cudaFuncSetAttribute(k_global_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  k_global_apply<<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pids, c->d_pslot,
-                                                c->d_pcol, c->d_iperm, x, y);
+  const size_t smem = (size_t)G.lda * sizeof(double);
+  ProfScope ps(c, SCK_GLOBAL_APPLY);
+  k_global_apply<<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_pcol,
+                                                c->d_iperm, x, y);
   return cudaGetLastError();
 }
 
 cudaError_t scatter_solution(sc_ctx* c, const double* xb, const double* xi, double* x) {
   const Geo& G = c->G;
   const size_t n = (size_t)G.K * G.ne;
+  count_launch(c);
   k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(G, c->d_iperm, xb, xi, x);
   return cudaGetLastError();
 }
 
 cudaError_t multidot(sc_ctx* c, const double* V, int nvec, size_t n, const double* w, double* out_dev) {
-  if (nvec > 64) return cudaErrorInvalidValue;
-  k_multidot_partial<<<kDotBlocks, 256, 0, c->stream>>>(V, nvec, n, w, c->partial);
-  k_multidot_final<<<1, 64, 0, c->stream>>>(c->partial, kDotBlocks, nvec, out_dev);
+  if (nvec < 1 || nvec > c->restart_alloc + 1) return cudaErrorInvalidValue;
+  const int chunks = kDotChunks;
+  count_launch(c, 2);
+  k_multidot_partial<<<dim3(chunks, nvec), 256, 0, c->stream>>>(V, n, w, c->partial);
+  k_multidot_final<<<nvec, 256, 0, c->stream>>>(c->partial, chunks, nvec, out_dev);
   return cudaGetLastError();
 }
 
 cudaError_t vec_update(sc_ctx* c, double* w, const double* V, int nvec, size_t n, const double* coef_dev,
                        double sign) {
+  count_launch(c);
   k_vec_update<<<kDotBlocks, 256, 0, c->stream>>>(w, V, nvec, n, coef_dev, sign);
   return cudaGetLastError();
 }
 
 cudaError_t vec_scale_copy(sc_ctx* c, double* dst, const double* src, size_t n, const double* scal_dev, int invert) {
+  count_launch(c);
   k_scale_copy<<<kDotBlocks, 256, 0, c->stream>>>(dst, src, n, scal_dev, invert);
   return cudaGetLastError();
 }
 
 cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b, size_t n) {
+  count_launch(c);
   k_axpby<<<kDotBlocks, 256, 0, c->stream>>>(y, a, x, b, n);
   return cudaGetLastError();
 }

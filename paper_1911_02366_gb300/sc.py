@@ -48,7 +48,11 @@ class sc_solve_stats(ctypes.Structure):
 
 EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_set_mesh", "sc_node_coords",
            "sc_set_state", "sc_set_timestep", "sc_assemble", "sc_condense", "sc_solve", "sc_get_rhs",
-           "sc_apply_jacobian", "sc_get_jacobian_block", "sc_condensed_matvec", "sc_sizes"]
+           "sc_apply_jacobian", "sc_get_jacobian_block", "sc_condensed_matvec", "sc_sizes",
+           "sc_launch_count", "sc_profile_kernel", "sc_profile_read", "sc_kernel_work"]
+
+SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
+SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
 
 
 def lib_path() -> str:
@@ -82,6 +86,10 @@ def lib(build_if_missing: bool = True):
     L.sc_get_jacobian_block.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
     L.sc_condensed_matvec.argtypes = [vp, dp, dp]
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
+    L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
+    L.sc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
+    L.sc_kernel_work.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for f in EXPORTS:
         if f not in ("sc_destroy", "sc_last_error"):
             getattr(L, f).restype = ctypes.c_int
@@ -203,3 +211,21 @@ class Context:
             raise ValueError("condensed_matvec takes device tensors")
         self._check(self._L.sc_condensed_matvec(self.h, px, py))
         return yb
+
+    def sc_launch_count(self) -> int:
+        v = ctypes.c_longlong()
+        self._check(self._L.sc_launch_count(self.h, ctypes.byref(v)))
+        return v.value
+
+    def sc_profile_kernel(self, kernel_id: int):
+        self._check(self._L.sc_profile_kernel(self.h, kernel_id))
+
+    def sc_profile_read(self):
+        n = ctypes.c_longlong(); ms = ctypes.c_double()
+        self._check(self._L.sc_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def sc_kernel_work(self, kernel_id: int):
+        f = ctypes.c_double(); b = ctypes.c_double()
+        self._check(self._L.sc_kernel_work(self.h, kernel_id, ctypes.byref(f), ctypes.byref(b)))
+        return f.value, b.value

@@ -95,7 +95,7 @@ def test_tgv_4x4x4_N3_cfl50_reaches_1e8():
     # Full size of the 4^3, N = 3 workload: the oracle's Jacobian-vector product
     # checks the global residual of the GPU solution.
     n, N = 4, 3
-    Q, dt, p, ctx = case(n, N, cfl=50.0, gmres_restart=60, gmres_max_iters=6000)
+    Q, dt, p, ctx = case(n, N, cfl=50.0, gmres_restart=300, gmres_max_iters=6000)
     ctx.sc_set_state(Q, Q)
     ctx.sc_assemble()
     ctx.sc_condense()
