@@ -139,6 +139,22 @@ sc_status sc_get_jacobian_block(sc_ctx* ctx, int e, int c, double* block);
    natural order, then variable).  Device pointers.  Test hook. */
 sc_status sc_condensed_matvec(sc_ctx* ctx, const double* xb, double* yb);
 
+/* Same result as sc_condensed_matvec, but the call allocates nothing: the interior
+   vector that links the two passes is kept in a fixed 8 MiB device array compiled into
+   the library (1,048,576 doubles, held on every GPU that loads the library until the
+   process exits) instead of context-owned memory.  The paper has no counterpart; it
+   is for callers that must not allocate device memory at the point of the call, e.g.
+   a solver loop running under a memory pool or an allocator that forbids
+   cudaMalloc/cudaFree once the simulation is running.  Needs K * (interior dofs per
+   element) <= 1,048,576 (N = 4: up to 7,767 elements); larger meshes get SC_ERR_ARG
+   with a message.  The first call on each device looks up the array's device address
+   with that device current (make it before any stream capture); later calls only
+   launch kernels.  Every call shares the one array: calls whose work overlaps on the
+   GPU (other streams, other contexts, other threads) race and must be serialised by
+   the caller.  The array keeps the last call's contents, which no call reads.
+   xb, yb: device pointers as in sc_condensed_matvec. */
+sc_status sc_condensed_matvec_static(sc_ctx* ctx, const double* xb, double* yb);
+
 /* Sizes: number of elements, dofs per element, interior and boundary dofs per element. */
 sc_status sc_sizes(const sc_ctx* ctx, int* K, int* ne, int* ni, int* nb);
 

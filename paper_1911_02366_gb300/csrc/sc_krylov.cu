@@ -312,3 +312,83 @@ cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b,
 }
 
 }  // namespace sc
+
+// ---------------------------------------------------------------------------------
+// Allocation-free condensed operator.
+//
+// sc_condensed_matvec_static applies S exactly like sc_condensed_matvec, but the
+// interior vector u = A_ii^-1 A_ib x_b that links the two passes lives in the static
+// device array below instead of context-owned memory, so the call itself never
+// allocates.  The array holds 8 MiB (1,048,576 doubles) on every GPU that loads this
+// library, for the life of the process; a call needs K * ni doubles of it.
+// ---------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+constexpr size_t kStaticScratchDoubles = (size_t(8) << 20) / sizeof(double);
+}  // namespace
+
+static __device__ __align__(256) double g_condensed_scratch[kStaticScratchDoubles];
+
+namespace {
+std::mutex g_scratch_mutex;
+double* g_scratch_addr[64] = {};
+
+// Device address of the scratch array on the current device, looked up once per device
+// (cudaGetSymbolAddress with that device current) and cached.
+cudaError_t static_scratch_address(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_condensed_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" sc_status sc_condensed_matvec_static(sc_ctx* c, const double* xb, double* yb) {
+  if (!c || !xb || !yb) return SC_ERR_ARG;
+  const Geo& G = c->G;
+  if (!c->condensed) {
+    c->err = "condensed_matvec_static before condense";
+    return SC_ERR_STATE;
+  }
+  const size_t need = (size_t)G.K * G.ni;
+  if (need > kStaticScratchDoubles) {
+    c->err = "condensed_matvec_static: this mesh needs " + std::to_string(need) +
+             " doubles of interior scratch (elements x interior dofs), more than the " +
+             std::to_string(kStaticScratchDoubles) + " of the static buffer; use sc_condensed_matvec";
+    return SC_ERR_ARG;
+  }
+  double* u = nullptr;
+  cudaError_t e = static_scratch_address(&u);
+  if (e != cudaSuccess) {
+    c->err = std::string("condensed_matvec_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    return SC_ERR_CUDA;
+  }
+  // The interior pass writes every entry of u before the boundary pass reads it, so
+  // nothing left over from an earlier call is ever read.
+  if (G.ni > 0) {
+    count_launch(c);
+    k_cond_interior<<<G.K, 256, (size_t)(G.nb + G.ldi) * sizeof(double), c->stream>>>(
+        G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u);
+  }
+  count_launch(c);
+  k_cond_boundary<<<G.K, 256, (size_t)G.lda * sizeof(double), c->stream>>>(
+      G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
+      G.ni ? u : nullptr, yb);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->err = std::string("condensed_matvec_static: ") + cudaGetErrorString(e);
+    return SC_ERR_CUDA;
+  }
+  return SC_OK;
+}

@@ -49,7 +49,8 @@ class sc_solve_stats(ctypes.Structure):
 EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_set_mesh", "sc_node_coords",
            "sc_set_state", "sc_set_timestep", "sc_assemble", "sc_condense", "sc_solve", "sc_get_rhs",
            "sc_apply_jacobian", "sc_get_jacobian_block", "sc_condensed_matvec", "sc_sizes",
-           "sc_launch_count", "sc_profile_kernel", "sc_profile_read", "sc_kernel_work"]
+           "sc_launch_count", "sc_profile_kernel", "sc_profile_read", "sc_kernel_work",
+           "sc_condensed_matvec_static"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -85,6 +86,7 @@ def lib(build_if_missing: bool = True):
     L.sc_apply_jacobian.argtypes = [vp, dp, dp, ctypes.c_int]
     L.sc_get_jacobian_block.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
     L.sc_condensed_matvec.argtypes = [vp, dp, dp]
+    L.sc_condensed_matvec_static.argtypes = [vp, dp, dp]
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
@@ -229,3 +231,11 @@ class Context:
         f = ctypes.c_double(); b = ctypes.c_double()
         self._check(self._L.sc_kernel_work(self.h, kernel_id, ctypes.byref(f), ctypes.byref(b)))
         return f.value, b.value
+
+    def sc_condensed_matvec_static(self, xb, yb):
+        """S x_b without any allocation in the call (fixed 8 MiB device scratch)."""
+        (px, dx), (py, dy) = _ptr(xb), _ptr(yb)
+        if not (dx and dy):
+            raise ValueError("condensed_matvec_static takes device tensors")
+        self._check(self._L.sc_condensed_matvec_static(self.h, px, py))
+        return yb
