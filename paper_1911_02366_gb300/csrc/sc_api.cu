@@ -92,6 +92,10 @@ void free_all(sc_ctx* c) {
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
                     &c->Hd, &c->partial, &c->Xfull, &c->Rfull};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
+  float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32};
+  for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
+  if (c->Dfull) cudaFree(c->Dfull);
+  c->Dfull = nullptr;
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
@@ -275,8 +279,15 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->grad, nodes * 15)); A(dalloc(&c->F, nodes * 15));
   A(dalloc(&c->NJ, nodes * 375)); A(dalloc(&c->RJ, (size_t)G.K * 6 * 50 * G.p * G.p));
   A(dalloc(&c->Aown, (size_t)G.K * own_stride(G))); A(dalloc(&c->X, (size_t)G.K * G.NP * 25));
-  A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Ytmp, (size_t)G.K * G.ni * G.nb));
-  A(dalloc(&c->See, (size_t)G.K * G.nb * G.lds)); A(dalloc(&c->piv, (size_t)G.K * G.nb)); A(dalloc(&c->rowperm, (size_t)G.K * G.nb));
+  if (c->cfg.precision == SC_PREC_MIXED) {
+    A(dalloc(&c->Aown32, (size_t)G.K * own_stride(G))); A(dalloc(&c->X32, (size_t)G.K * G.NP * 25));
+    A(dalloc(&c->Ainv32, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Y32, (size_t)G.K * G.ni * G.nb));
+    A(dalloc(&c->See32, (size_t)G.K * G.nb * G.lds)); A(dalloc(&c->Dfull, dofs));
+  } else {
+    A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Ytmp, (size_t)G.K * G.ni * G.nb));
+    A(dalloc(&c->See, (size_t)G.K * G.nb * G.lds));
+  }
+  A(dalloc(&c->piv, (size_t)G.K * G.nb)); A(dalloc(&c->rowperm, (size_t)G.K * G.nb));
   A(dalloc(&c->V, n1 * (m + 1))); A(dalloc(&c->Wv, n1)); A(dalloc(&c->Zv, n1)); A(dalloc(&c->Xb, n1));
   A(dalloc(&c->Gb, n1)); A(dalloc(&c->Rb, n1)); A(dalloc(&c->Tb, n1));
   A(dalloc(&c->Ui, (size_t)G.K * G.ni)); A(dalloc(&c->Hd, 3 * (size_t)(m + 2) + 16));
@@ -307,7 +318,8 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   SC_CUDA(cudaMemcpy(c->d_pinfo, pinfo.data(), np * sizeof(int), cudaMemcpyHostToDevice));
   // the alignment padding of the element blocks must read as zero
   SC_CUDA(cudaMemset(c->Aown, 0, (size_t)G.K * own_stride(G) * sizeof(double)));
-  SC_CUDA(cudaMemset(c->Ainv, 0, (size_t)G.K * G.ni * G.ldi * sizeof(double)));
+  if (c->Ainv) SC_CUDA(cudaMemset(c->Ainv, 0, (size_t)G.K * G.ni * G.ldi * sizeof(double)));
+  if (c->Ainv32) SC_CUDA(cudaMemset(c->Ainv32, 0, (size_t)G.K * G.ni * G.ldi * sizeof(float)));
   c->has_mesh = true;
   return SC_OK;
 }
@@ -440,49 +452,46 @@ sc_status sc_get_jacobian_block(sc_ctx* c, int e, int col, double* block) {
 sc_status sc_condensed_matvec(sc_ctx* c, const double* xb, double* yb) {
   if (!c || !xb || !yb) return SC_ERR_ARG;
   if (!c->condensed) return fail(c, SC_ERR_STATE, "condensed_matvec before condense");
-  SC_CUDA(sc::cond_interior(c, xb, 1.0, nullptr, 0.0, c->Ui));
-  SC_CUDA(sc::cond_boundary(c, xb, 1.0, nullptr, 0.0, c->Ui, yb));
+  c->op32 = c->cfg.precision == SC_PREC_MIXED;
+  cudaError_t e1 = sc::cond_interior(c, xb, 1.0, nullptr, 0.0, c->Ui);
+  cudaError_t e2 = e1 == cudaSuccess ? sc::cond_boundary(c, xb, 1.0, nullptr, 0.0, c->Ui, yb) : e1;
+  c->op32 = false;
+  SC_CUDA(e2);
   return check(c);
 }
 
-sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
-  if (!c || !dQ) return SC_ERR_ARG;
-  if (!c->condensed) return fail(c, SC_ERR_STATE, "solve before condense");
+}  // extern "C"
+
+namespace {
+
+// Right-preconditioned restarted GMRES (classical Gram-Schmidt applied twice, Givens
+// rotations) on the condensed operator, right-hand side c->Gb, x0 = 0, solution in
+// c->Xb.  Stops when the true condensed residual ||g - S x|| <= abs_tol or after
+// max_iters iterations.  The operator and preconditioner precision follow c->op32.
+sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_out, double* resid_out) {
   const Geo& G = c->G;
-  const size_t n1 = (size_t)G.K * G.nb, dofs = (size_t)G.K * G.ne;
+  const size_t n1 = (size_t)G.K * G.nb;
   const int m = c->restart_alloc;
-  sc_solve_stats S{};
-  S.first_bad_element = -1;
-  cudaEvent_t* ev = c->ev;
-  SC_CUDA(cudaEventRecord(ev[0], c->stream));
-  // condensed right-hand side g = B_b - A_bi A_ii^-1 B_i   (eq. SC_step1)
-  SC_CUDA(sc::cond_interior(c, nullptr, 0.0, c->B, 1.0, c->Ui));
-  SC_CUDA(sc::cond_boundary(c, nullptr, 0.0, c->B, 1.0, c->Ui, c->Gb));
-  SC_CUDA(cudaEventRecord(ev[1], c->stream));
   double* const hs = c->Hd + 2 * (m + 1) + 2;  // scratch slot
-  const double bnorm = dnorm2(c, c->B, dofs, hs);
-  const double target = c->cfg.rel_tol * bnorm;
-  // right-preconditioned restarted GMRES, x0 = 0
+  double* const h1 = c->Hd;
+  double* const h2 = c->Hd + (m + 1);
+  double* const hn2 = c->Hd + 2 * (m + 1);
   SC_CUDA(cudaMemsetAsync(c->Xb, 0, n1 * sizeof(double), c->stream));
   SC_CUDA(cudaMemcpyAsync(c->Rb, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   double beta = dnorm2(c, c->Rb, n1, hs);
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(2 * (m + 1) + 1), y(m);
-  double* const h1 = c->Hd;
-  double* const h2 = c->Hd + (m + 1);
-  double* const hn2 = c->Hd + 2 * (m + 1);
   int iters = 0;
   double resid = beta;
-  bool ok = beta <= target || bnorm == 0.0;
-  while (!ok && iters < c->cfg.gmres_max_iters) {
+  bool ok = beta <= abs_tol;
+  while (!ok && iters < max_iters) {
     SC_CUDA(sc::vec_axpby(c, c->V, 1.0 / beta, c->Rb, 0.0, n1));
     std::fill(gv.begin(), gv.end(), 0.0); gv[0] = beta;
     int k = 0;
-    for (int j = 0; j < m && iters < c->cfg.gmres_max_iters; ++j) {
+    for (int j = 0; j < m && iters < max_iters; ++j) {
       double* Vj = c->V + (size_t)j * n1;
       SC_CUDA(sc::precond_apply(c, Vj, c->Zv));
       SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
       SC_CUDA(sc::cond_boundary(c, c->Zv, 1.0, nullptr, 0.0, c->Ui, c->Wv));
-      // classical Gram-Schmidt, twice
       SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h1));
       SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, h1, -1.0));
       SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h2));
@@ -508,12 +517,12 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
       gv[j] = cs[j] * gv[j];
       ++iters; k = j + 1;
       resid = std::fabs(gv[j + 1]);
-      if (resid <= target || hn == 0.0) break;
+      if (resid <= abs_tol || hn == 0.0) break;
     }
     for (int i = k - 1; i >= 0; --i) {
-      double s = gv[i];
-      for (int l = i + 1; l < k; ++l) s -= H[(size_t)i * m + l] * y[l];
-      y[i] = s / H[(size_t)i * m + i];
+      double sum = gv[i];
+      for (int l = i + 1; l < k; ++l) sum -= H[(size_t)i * m + l] * y[l];
+      y[i] = sum / H[(size_t)i * m + i];
     }
     SC_CUDA(cudaMemcpyAsync(c->Hd, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     SC_CUDA(cudaMemsetAsync(c->Tb, 0, n1 * sizeof(double), c->stream));
@@ -528,26 +537,88 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
     beta = dnorm2(c, c->Rb, n1, hs);
     resid = beta;
     if (!std::isfinite(beta)) return fail(c, SC_ERR_NONFINITE, "non-finite condensed residual");
-    if (beta <= target) ok = true;
+    if (beta <= abs_tol) ok = true;
   }
-  SC_CUDA(cudaEventRecord(ev[2], c->stream));
-  // back-substitution Q_i = A_ii^-1 (B_i - A_ib Q_b)   (eq. SC_step2)
-  SC_CUDA(sc::cond_interior(c, c->Xb, -1.0, c->B, 1.0, c->Ui));
+  *iters_out = iters;
+  *resid_out = resid;
+  return SC_OK;
+}
+
+// One condensed solve of A d = r (r a full vector): condensed right-hand side
+// (eq. SC_step1), GMRES, back-substitution (eq. SC_step2) into d.
+sc_status condensed_solve(sc_ctx* c, const double* r, double* d, double rel_tol_g, double abs_floor, int max_iters,
+                          int* iters, double* resid, double* gnorm) {
+  const Geo& G = c->G;
+  const size_t n1 = (size_t)G.K * G.nb;
+  SC_CUDA(sc::cond_interior(c, nullptr, 0.0, r, 1.0, c->Ui));
+  SC_CUDA(sc::cond_boundary(c, nullptr, 0.0, r, 1.0, c->Ui, c->Gb));
+  *gnorm = dnorm2(c, c->Gb, n1, c->Hd + 2 * (c->restart_alloc + 1) + 2);
+  sc_status s = gmres_condensed(c, std::max(rel_tol_g * *gnorm, abs_floor), max_iters, iters, resid);
+  if (s != SC_OK) return s;
+  SC_CUDA(sc::cond_interior(c, c->Xb, -1.0, r, 1.0, c->Ui));
+  SC_CUDA(sc::scatter_solution(c, c->Xb, c->Ui, d));
+  return SC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
+  if (!c || !dQ) return SC_ERR_ARG;
+  if (!c->condensed) return fail(c, SC_ERR_STATE, "solve before condense");
+  const Geo& G = c->G;
+  const size_t dofs = (size_t)G.K * G.ne;
+  sc_solve_stats S{};
+  S.first_bad_element = -1;
+  cudaEvent_t* ev = c->ev;
+  double* const hs = c->Hd + 2 * (c->restart_alloc + 1) + 2;
   double* xout = on_device ? dQ : c->Xfull;
-  SC_CUDA(sc::scatter_solution(c, c->Xb, c->Ui, xout));
+  SC_CUDA(cudaEventRecord(ev[0], c->stream));
+  const double bnorm = dnorm2(c, c->B, dofs, hs);
+  const double target = c->cfg.rel_tol * bnorm;
+  double rn = 0.0;
+  int iters = 0;
+  double resid = 0.0, gnorm = 0.0;
+  if (c->cfg.precision == SC_PREC_FP64) {
+    // one condensed FP64 solve to the target
+    sc_status s = condensed_solve(c, c->B, xout, 0.0, target, c->cfg.gmres_max_iters, &iters, &resid, &gnorm);
+    if (s != SC_OK) return s;
+    SC_CUDA(cudaEventRecord(ev[2], c->stream));
+    SC_CUDA(sc::global_apply(c, xout, c->Rfull));
+    SC_CUDA(sc::vec_axpby(c, c->Rfull, 1.0, c->B, -1.0, dofs));
+    rn = dnorm2(c, c->Rfull, dofs, hs);
+  } else {
+    // FP64 iterative refinement around FP32 condensed solves
+    c->op32 = true;
+    SC_CUDA(cudaMemsetAsync(xout, 0, dofs * sizeof(double), c->stream));
+    SC_CUDA(cudaMemcpyAsync(c->Rfull, c->B, dofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    rn = bnorm;
+    int sweeps = 0;
+    while (rn > target && sweeps < c->cfg.max_refine && iters < c->cfg.gmres_max_iters) {
+      int it = 0;
+      sc_status s = condensed_solve(c, c->Rfull, c->Dfull, c->cfg.inner_tol, 0.5 * target,
+                                    c->cfg.gmres_max_iters - iters, &it, &resid, &gnorm);
+      if (s != SC_OK) { c->op32 = false; return s; }
+      iters += it;
+      SC_CUDA(sc::vec_axpby(c, xout, 1.0, c->Dfull, 1.0, dofs));
+      SC_CUDA(sc::global_apply(c, xout, c->Rfull));
+      SC_CUDA(sc::vec_axpby(c, c->Rfull, 1.0, c->B, -1.0, dofs));
+      rn = dnorm2(c, c->Rfull, dofs, hs);
+      ++sweeps;
+      if (!std::isfinite(rn)) { c->op32 = false; return fail(c, SC_ERR_NONFINITE, "non-finite refinement residual"); }
+    }
+    c->op32 = false;
+    S.refinements = sweeps;
+    SC_CUDA(cudaEventRecord(ev[2], c->stream));
+  }
   SC_CUDA(cudaEventRecord(ev[3], c->stream));
-  // FP64 global residual ||B - A x|| / ||B||
-  SC_CUDA(sc::global_apply(c, xout, c->Rfull));
-  SC_CUDA(sc::vec_axpby(c, c->Rfull, 1.0, c->B, -1.0, dofs));
-  const double rn = dnorm2(c, c->Rfull, dofs, hs);
   if (!on_device) SC_CUDA(cudaMemcpyAsync(dQ, xout, dofs * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
   if (s != SC_OK) return s;
-  float t01 = 0, t12 = 0, t23 = 0;
-  cudaEventElapsedTime(&t01, ev[0], ev[1]);
-  cudaEventElapsedTime(&t12, ev[1], ev[2]);
-  cudaEventElapsedTime(&t23, ev[2], ev[3]);
-  S.ms_rhs = t01; S.ms_gmres = t12; S.ms_backsub = t23;
+  float t02 = 0;
+  cudaEventElapsedTime(&t02, ev[0], ev[2]);
+  S.ms_gmres = t02;
   S.gmres_iters = iters;
   S.cond_rel_residual = bnorm > 0 ? resid / bnorm : 0.0;
   S.rel_residual = bnorm > 0 ? rn / bnorm : 0.0;

@@ -288,52 +288,72 @@ __device__ __forceinline__ double warp_sum_d(double s) {
   return s;
 }
 
-__device__ __forceinline__ double dot_row(const double* __restrict__ row, const double* xs, int k0, int k1, int lane) {
-  // sum_{k0 <= k < k1} row[k] xs[k]; k0 even (16-byte aligned double2 loads)
-  const double2* r2 = reinterpret_cast<const double2*>(row + k0);
-  const double2* x2 = reinterpret_cast<const double2*>(xs + k0);
-  const int len = k1 - k0, len2 = len >> 1;
-  double s0 = 0.0, s1 = 0.0;
+template <class T> struct V16;
+template <> struct V16<double> { using type = double2; static constexpr int n = 2; };
+template <> struct V16<float> { using type = float4; static constexpr int n = 4; };
+__device__ __forceinline__ void vfma(const double2& a, const double2& b, double& s0, double& s1) {
+  s0 = fma(a.x, b.x, s0); s1 = fma(a.y, b.y, s1);
+}
+__device__ __forceinline__ void vfma(const float4& a, const float4& b, float& s0, float& s1) {
+  s0 = fmaf(a.x, b.x, s0); s1 = fmaf(a.y, b.y, s1); s0 = fmaf(a.z, b.z, s0); s1 = fmaf(a.w, b.w, s1);
+}
+__device__ __forceinline__ float warp_sum_t(float s) {
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+__device__ __forceinline__ double warp_sum_t(double s) {
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+// sum_{k0 <= k < k1} row[k] xs[k]; row + k0 and xs + k0 16-byte aligned.
+template <class T>
+__device__ __forceinline__ T dot_row(const T* __restrict__ row, const T* xs, int k0, int k1, int lane) {
+  using V = typename V16<T>::type;
+  constexpr int W = V16<T>::n;
+  const V* r = reinterpret_cast<const V*>(row + k0);
+  const V* x = reinterpret_cast<const V*>(xs + k0);
+  const int len = k1 - k0, nv = len / W;
+  T s0 = T(0), s1 = T(0);
 #pragma unroll 4
-  for (int i = lane; i < len2; i += 32) {
-    const double2 a = __ldg(r2 + i), b = x2[i];
-    s0 = fma(a.x, b.x, s0); s1 = fma(a.y, b.y, s1);
-  }
-  if ((len & 1) && lane == 0) s0 = fma(__ldg(row + k1 - 1), xs[k1 - 1], s0);
+  for (int i = lane; i < nv; i += 32) vfma(__ldg(r + i), x[i], s0, s1);
+  for (int i = k0 + nv * W + lane; i < k1; i += 32) s0 = fma(__ldg(row + i), xs[i], s0);
   return s0 + s1;
 }
 
 // z = (P^T L U)^-1 v for every element: one CTA per element, 32-row panels.  Each panel
-// first subtracts the already-solved part (rows spread over the warps, double2 row
+// first subtracts the already-solved part (rows spread over the warps, 16-byte row
 // reads), then the 32 x 32 diagonal triangle is staged in shared memory and solved by
-// warp 0 with shuffles.
-__global__ void __launch_bounds__(256) k_lu_solve(int n, const double* __restrict__ LU, long long stride, int lda,
+// warp 0 with shuffles.  Arithmetic in the factor precision T; v, z in double.
+template <class T>
+__global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ LU, long long stride, int lda,
                                                   const int* __restrict__ rowperm, const double* __restrict__ v,
                                                   double* __restrict__ z) {
-  extern __shared__ __align__(16) double xs[];
-  __shared__ double Dg[32][33];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  __shared__ T Dg[32][33];
   const int e = blockIdx.x;
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-  const double* M = LU + (long long)e * stride;
+  const T* M = LU + (long long)e * stride;
   const int* rp = rowperm + (long long)e * n;
   const double* ve = v + (long long)e * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = ve[rp[i]];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = (T)ve[rp[i]];
   __syncthreads();
   for (int i0 = 0; i0 < n; i0 += 32) {  // unit lower triangle
     const int bs = min(32, n - i0);
     for (int r = warp; r < bs; r += nw) {
-      const double* row = M + (long long)(i0 + r) * lda;
-      Dg[r][lane] = lane < bs ? row[i0 + lane] : 0.0;
+      const T* row = M + (long long)(i0 + r) * lda;
+      Dg[r][lane] = lane < bs ? row[i0 + lane] : T(0);
       if (i0 > 0) {
-        const double s = warp_sum_d(dot_row(row, xs, 0, i0, lane));
+        const T s = warp_sum_t(dot_row(row, xs, 0, i0, lane));
         if (lane == 0) xs[i0 + r] -= s;
       }
     }
     __syncthreads();
     if (warp == 0) {
-      double xl = lane < bs ? xs[i0 + lane] : 0.0;
+      T xl = lane < bs ? xs[i0 + lane] : T(0);
       for (int rr = 0; rr < bs; ++rr) {
-        const double xr = __shfl_sync(0xffffffffu, xl, rr);
+        const T xr = __shfl_sync(0xffffffffu, xl, rr);
         if (lane > rr) xl = fma(-Dg[lane][rr], xr, xl);
       }
       if (lane < bs) xs[i0 + lane] = xl;
@@ -344,26 +364,31 @@ __global__ void __launch_bounds__(256) k_lu_solve(int n, const double* __restric
   for (int b = nblk - 1; b >= 0; --b) {  // upper triangle
     const int i0 = b * 32, bs = min(32, n - i0), i1 = i0 + bs;
     for (int r = warp; r < bs; r += nw) {
-      const double* row = M + (long long)(i0 + r) * lda;
-      Dg[r][lane] = lane < bs ? row[i0 + lane] : 0.0;
+      const T* row = M + (long long)(i0 + r) * lda;
+      Dg[r][lane] = lane < bs ? row[i0 + lane] : T(0);
       if (i1 < n) {
-        const double s = warp_sum_d(dot_row(row, xs, i1, n, lane));
+        const T s = warp_sum_t(dot_row(row, xs, i1, n, lane));
         if (lane == 0) xs[i0 + r] -= s;
       }
     }
     __syncthreads();
     if (warp == 0) {
-      double xl = lane < bs ? xs[i0 + lane] : 0.0;
+      T xl = lane < bs ? xs[i0 + lane] : T(0);
       for (int rr = bs - 1; rr >= 0; --rr) {
         if (lane == rr) xl = xl / Dg[rr][rr];
-        const double xr = __shfl_sync(0xffffffffu, xl, rr);
+        const T xr = __shfl_sync(0xffffffffu, xl, rr);
         if (lane < rr) xl = fma(-Dg[lane][rr], xr, xl);
       }
       if (lane < bs) xs[i0 + lane] = xl;
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) z[(long long)e * n + i] = xs[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) z[(long long)e * n + i] = (double)xs[i];
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    b[t] = (float)a[t];
 }
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
@@ -374,51 +399,63 @@ namespace sc {
 
 // Condensation set-up (FP64): A_ii^-1, Y = A_ii^-1 A_ib,ee, S_ee = A_bb,ee - A_bi,ee Y,
 // LU(S_ee).
-cudaError_t launch_condense(sc_ctx* c) {
+template <class T>
+cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See) {
   const Geo& G = c->G;
   const int ni = G.ni, nb = G.nb, K = G.K, lda = G.lda, cb0 = G.cb0, ldi = G.ldi, lds = G.lds;
   const long long sA = (long long)own_stride(G);
   cudaError_t err;
   if (ni > 0) {
-    const size_t smem = (size_t)ni * (ni + 1) * sizeof(double) + ni * sizeof(double) + ni * sizeof(int);
-    err = cudaFuncSetAttribute(k_gj_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)ni * (ni + 1) * sizeof(T) + ni * sizeof(T) + ni * sizeof(int);
+    err = cudaFuncSetAttribute(k_gj_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     ProfScope ps(c, SCK_GJ_INV);
-    k_gj_inv<double><<<K, 256, smem, c->stream>>>(ni, c->Aown, sA, lda, c->Ainv, (long long)ni * ldi, ldi,
-                                                  c->d_status);
+    k_gj_inv<T><<<K, 256, smem, c->stream>>>(ni, Aown, sA, lda, Ainv, (long long)ni * ldi, ldi, c->d_status);
   }
   if (ni > 0) {
     // Y = A_ii^-1 * A_ib,ee  (ni x nb)
     count_launch(c);
     dim3 g1(cdiv(nb, 64), cdiv(ni, 64), K);
-    k_gemm<double><<<g1, 256, 0, c->stream>>>(ni, nb, ni, 1.0, c->Ainv, (long long)ni * ldi, ldi,
-                                              c->Aown + cb0, sA, lda, 0.0,
-                                              c->Ytmp, (long long)ni * nb, nb);
+    k_gemm<T><<<g1, 256, 0, c->stream>>>(ni, nb, ni, T(1), Ainv, (long long)ni * ldi, ldi, Aown + cb0, sA, lda, T(0),
+                                         Y, (long long)ni * nb, nb);
   }
   // S_ee = A_bb,ee - A_bi,ee * Y
   count_launch(c);
   dim3 gc(cdiv((long long)nb * nb, 256 * 8), K);
-  k_copy_block<double><<<gc, 256, 0, c->stream>>>(nb, nb, c->Aown + (size_t)ni * lda + cb0, sA, lda,
-                                                  c->See, (long long)nb * lds, lds);
+  k_copy_block<T><<<gc, 256, 0, c->stream>>>(nb, nb, Aown + (size_t)ni * lda + cb0, sA, lda, See, (long long)nb * lds,
+                                             lds);
   if (ni > 0) {
     ProfScope ps(c, SCK_GEMM);
     dim3 g2(cdiv(nb, 64), cdiv(nb, 64), K);
-    k_gemm<double><<<g2, 256, 0, c->stream>>>(nb, nb, ni, -1.0, c->Aown + (size_t)ni * lda, sA, lda,
-                                              c->Ytmp, (long long)ni * nb, nb, 1.0,
-                                              c->See, (long long)nb * lds, lds);
+    k_gemm<T><<<g2, 256, 0, c->stream>>>(nb, nb, ni, T(-1), Aown + (size_t)ni * lda, sA, lda, Y, (long long)ni * nb,
+                                         nb, T(1), See, (long long)nb * lds, lds);
   }
   if (c->cfg.precond == SC_PC_BLOCK_JACOBI) {
-    const size_t smem = (size_t)nb * (PW + 1) * sizeof(double);
-    err = cudaFuncSetAttribute(k_lu<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)nb * (PW + 1) * sizeof(T);
+    err = cudaFuncSetAttribute(k_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     {
       ProfScope ps(c, SCK_LU);
-      k_lu<double><<<K, 256, smem, c->stream>>>(nb, c->See, (long long)nb * lds, lds, c->piv, c->d_status);
+      k_lu<T><<<K, 256, smem, c->stream>>>(nb, See, (long long)nb * lds, lds, c->piv, c->d_status);
     }
     count_launch(c);
     k_piv_to_perm<<<cdiv(K, 128), 128, 0, c->stream>>>(nb, c->piv, c->rowperm, K);
   }
   return cudaGetLastError();
+}
+
+// Condensation set-up: A_ii^-1, Y = A_ii^-1 A_ib,ee, S_ee = A_bb,ee - A_bi,ee Y, LU(S_ee);
+// FP64 arm in place on the FP64 blocks, mixed arm on FP32 copies.
+cudaError_t launch_condense(sc_ctx* c) {
+  const Geo& G = c->G;
+  if (c->cfg.precision == SC_PREC_MIXED) {
+    count_launch(c, 2);
+    const size_t na = (size_t)G.K * own_stride(G), nx = (size_t)G.K * G.NP * 25;
+    k_to_float<<<608, 256, 0, c->stream>>>(c->Aown, c->Aown32, na);
+    k_to_float<<<608, 256, 0, c->stream>>>(c->X, c->X32, nx);
+    return condense_t<float>(c, c->Aown32, c->Ainv32, c->Y32, c->See32);
+  }
+  return condense_t<double>(c, c->Aown, c->Ainv, c->Ytmp, c->See);
 }
 
 cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
@@ -427,9 +464,16 @@ cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
   if (c->cfg.precond != SC_PC_BLOCK_JACOBI) {
     return cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   }
-  const size_t smem = (size_t)G.nb * sizeof(double);
   ProfScope ps(c, SCK_LU_SOLVE);
-  k_lu_solve<<<G.K, 256, smem, c->stream>>>(G.nb, c->See, (long long)G.nb * G.lds, G.lds, c->rowperm, v, z);
+  if (c->cfg.precision == SC_PREC_MIXED) {
+    const size_t smem = (size_t)G.nb * sizeof(float);
+    k_lu_solve<float><<<G.K, 256, smem, c->stream>>>(G.nb, c->See32, (long long)G.nb * G.lds, G.lds, c->rowperm,
+                                                     v, z);
+  } else {
+    const size_t smem = (size_t)G.nb * sizeof(double);
+    k_lu_solve<double><<<G.K, 256, smem, c->stream>>>(G.nb, c->See, (long long)G.nb * G.lds, G.lds, c->rowperm,
+                                                      v, z);
+  }
   return cudaGetLastError();
 }
 

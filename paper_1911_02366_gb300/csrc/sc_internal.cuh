@@ -262,6 +262,10 @@ struct sc_ctx {
   double *V = nullptr, *Wv = nullptr, *Zv = nullptr, *Xb = nullptr, *Gb = nullptr, *Rb = nullptr;
   double *Ui = nullptr, *Tb = nullptr, *Hd = nullptr, *partial = nullptr, *Xfull = nullptr, *Rfull = nullptr;
   int restart_alloc = 0;
+  // mixed-precision arm: FP32 copies of the element blocks and FP32 condensation
+  float *Aown32 = nullptr, *X32 = nullptr, *Ainv32 = nullptr, *Y32 = nullptr, *See32 = nullptr;
+  double* Dfull = nullptr;  // refinement correction
+  bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};
   // measurement hooks: kernel launches since creation, and optional CUDA-event timing
   // of every launch of one selected kernel (see sc_profile_kernel)

@@ -17,34 +17,46 @@ __device__ __forceinline__ double warp_sum(double s) {
   return s;
 }
 
-// Dot product of a row segment (global, 16-byte aligned) with a vector in shared
-// memory (16-byte aligned), one warp, double2 loads; len may be odd.
-__device__ __forceinline__ double warp_dot(const double* __restrict__ row, const double* v, int len, int lane) {
-  const double2* r2 = reinterpret_cast<const double2*>(row);
-  const double2* v2 = reinterpret_cast<const double2*>(v);
-  const int len2 = len >> 1;
-  double s0 = 0.0, s1 = 0.0;
+// 16-byte vector type of each storage precision.
+template <class T> struct Vec16;
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+
+__device__ __forceinline__ void fma16(const double2& a, const double2& b, double& s0, double& s1) {
+  s0 = fma(a.x, b.x, s0); s1 = fma(a.y, b.y, s1);
+}
+__device__ __forceinline__ void fma16(const float4& a, const float4& b, float& s0, float& s1) {
+  s0 = fmaf(a.x, b.x, s0); s1 = fmaf(a.y, b.y, s1); s0 = fmaf(a.z, b.z, s0); s1 = fmaf(a.w, b.w, s1);
+}
+
+// Dot product of a row segment (global, 16-byte aligned) with a vector in shared memory
+// (16-byte aligned), one warp, 16-byte loads, arithmetic in the storage precision T;
+// returns this lane's partial sum.
+template <class T>
+__device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* v, int len, int lane) {
+  using V = typename Vec16<T>::type;
+  constexpr int W = Vec16<T>::n;
+  const V* r = reinterpret_cast<const V*>(row);
+  const V* x = reinterpret_cast<const V*>(v);
+  const int nv = len / W;
+  T s0 = T(0), s1 = T(0);
 #pragma unroll 4
-  for (int i = lane; i < len2; i += 32) {
-    const double2 a = __ldg(r2 + i);
-    const double2 b = v2[i];
-    s0 = fma(a.x, b.x, s0);
-    s1 = fma(a.y, b.y, s1);
-  }
-  if ((len & 1) && lane == 0) s0 = fma(__ldg(row + len - 1), v[len - 1], s0);
+  for (int i = lane; i < nv; i += 32) fma16(__ldg(r + i), x[i], s0, s1);
+  for (int i = nv * W + lane; i < len; i += 32) s0 = fma(__ldg(row + i), v[i], s0);
   return s0 + s1;
 }
 
 // Neighbour couplings of row (node j, variable k) of element e.  The couplings of one
 // row are contiguous in X (layout X[e][k][pair][l]); vb / vi are the condensed
 // boundary / interior vectors of all elements (either may be null), scaled by cb / ci.
-__device__ __forceinline__ double cross_row(const Geo& G, int e, int j, int k, const double* __restrict__ X,
-                                            const int* nbr_s, const int* __restrict__ pptr,
-                                            const int* __restrict__ pinfo, const double* __restrict__ vb, double cb,
-                                            const double* __restrict__ vi, double ci, int lane) {
+template <class T>
+__device__ __forceinline__ T cross_row(const Geo& G, int e, int j, int k, const T* __restrict__ X,
+                                       const int* nbr_s, const int* __restrict__ pptr,
+                                       const int* __restrict__ pinfo, const double* __restrict__ vb, double cb,
+                                       const double* __restrict__ vi, double ci, int lane) {
   const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
-  const double* Xr = X + (((size_t)e * 5 + k) * G.NP + q0) * 5;
-  double s = 0.0;
+  const T* Xr = X + (((size_t)e * 5 + k) * G.NP + q0) * 5;
+  T s = T(0);
   for (int f = lane; f < 5 * (q1 - q0); f += 32) {
     const int q = q0 + f / 5, l = f % 5;
     const int info = __ldg(pinfo + q);
@@ -58,59 +70,62 @@ __device__ __forceinline__ double cross_row(const Geo& G, int e, int j, int k, c
       if (!vb) continue;
       xv = cb * vb[(size_t)nb * G.nb + off];
     }
-    s = fma(__ldg(Xr + f), xv, s);
+    s = fma(__ldg(Xr + f), (T)xv, s);
   }
   return s;
 }
 
-// Interior pass: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e).
-__global__ void __launch_bounds__(256) k_cond_interior(Geo G, const double* __restrict__ Aown,
-    const double* __restrict__ X, const double* __restrict__ Ainv, const int* __restrict__ nbr,
+// Interior pass: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e); matrices stored in T.
+template <class T>
+__global__ void __launch_bounds__(256) k_cond_interior(Geo G, const T* __restrict__ Aown,
+    const T* __restrict__ X, const T* __restrict__ Ainv, const int* __restrict__ nbr,
     const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm,
     const double* __restrict__ xb, double beta, const double* __restrict__ Bfull, double alpha,
     double* __restrict__ u) {
-  extern __shared__ __align__(16) double sm[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = blockIdx.x, ni = G.ni, nb = G.nb;
-  double* v = sm;              // nb: x_e
-  double* t = sm + nb;         // ldi: right-hand side of the interior solve, zero padded
+  T* v = reinterpret_cast<T*>(smem_raw);  // nb: x_e
+  T* t = v + ((nb + 3) & ~3);             // ldi: right-hand side of the interior solve, zero padded,
+                                          // 16-byte aligned for the vector loads of warp_dot
   __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) v[i] = xb ? xb[(size_t)e * nb + i] : 0.0;
-  for (int i = ni + threadIdx.x; i < G.ldi; i += blockDim.x) t[i] = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v[i] = xb ? (T)xb[(size_t)e * nb + i] : T(0);
+  for (int i = ni + threadIdx.x; i < G.ldi; i += blockDim.x) t[i] = T(0);
   __syncthreads();
-  const double* Ae = Aown + (size_t)e * own_stride(G);
+  const T* Ae = Aown + (size_t)e * own_stride(G);
   for (int ri = warp; ri < ni; ri += nw) {
     const int j = __ldg(iperm + ri / 5), k = ri % 5;
     double s = 0.0;
     if (xb) {
-      s = warp_dot(Ae + (size_t)ri * G.lda + G.cb0, v, nb, lane);
-      s += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, 1.0, nullptr, 0.0, lane);
-      s = warp_sum(s);
+      T p = warp_dot(Ae + (size_t)ri * G.lda + G.cb0, v, nb, lane);
+      p += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, 1.0, nullptr, 0.0, lane);
+      s = warp_sum((double)p);
     }
     if (lane == 0) {
       double val = beta * s;
       if (Bfull) val += alpha * Bfull[((size_t)e * G.nn + j) * 5 + k];
-      t[ri] = val;
+      t[ri] = (T)val;
     }
   }
   __syncthreads();
-  const double* Ie = Ainv + (size_t)e * ni * G.ldi;
+  const T* Ie = Ainv + (size_t)e * ni * G.ldi;
   for (int ri = warp; ri < ni; ri += nw) {
-    const double s = warp_sum(warp_dot(Ie + (size_t)ri * G.ldi, t, G.ldi, lane));
+    const double s = warp_sum((double)warp_dot(Ie + (size_t)ri * G.ldi, t, G.ldi, lane));
     if (lane == 0) u[(size_t)e * ni + ri] = s;
   }
 }
 
-// Boundary pass: y_e = gamma B_b,e + delta (A_bb x_b)_e - (A_bi u)_e.
-__global__ void __launch_bounds__(256) k_cond_boundary(Geo G, const double* __restrict__ Aown,
-    const double* __restrict__ X, const int* __restrict__ nbr,
+// Boundary pass: y_e = gamma B_b,e + delta (A_bb x_b)_e - (A_bi u)_e; matrices stored in T.
+template <class T>
+__global__ void __launch_bounds__(256) k_cond_boundary(Geo G, const T* __restrict__ Aown,
+    const T* __restrict__ X, const int* __restrict__ nbr,
     const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm,
     const double* __restrict__ xb, double delta, const double* __restrict__ Bfull, double gamma_,
     const double* __restrict__ u, double* __restrict__ y) {
-  extern __shared__ __align__(16) double sm[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = blockIdx.x, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, cb0 = G.cb0;
-  double* v = sm;  // lda: [-u_e | 0 | delta x_e | 0] in own-column order
+  T* v = reinterpret_cast<T*>(smem_raw);  // lda: [-u_e | 0 | delta x_e | 0] in own-column order
   __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
@@ -118,17 +133,17 @@ __global__ void __launch_bounds__(256) k_cond_boundary(Geo G, const double* __re
     double val = 0.0;
     if (i < ni) { if (u) val = -u[(size_t)e * ni + i]; }
     else if (i >= cb0 && i < cb0 + nb) { if (xb) val = delta * xb[(size_t)e * nb + i - cb0]; }
-    v[i] = val;
+    v[i] = (T)val;
   }
   __syncthreads();
-  const double* Ae = Aown + (size_t)e * own_stride(G);
+  const T* Ae = Aown + (size_t)e * own_stride(G);
   const int c0 = u ? 0 : cb0;                 // skip the A_bi columns when u is absent
   const int len = (xb ? cb0 + nb : ni) - c0;  // and the A_bb columns when x_b is absent
   for (int ri = ni + warp; ri < ne; ri += nw) {
     const int j = __ldg(iperm + ri / 5), k = ri % 5;
-    double s = (xb || u) ? warp_dot(Ae + (size_t)ri * lda + c0, v + c0, len, lane) : 0.0;
-    s += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, delta, u, -1.0, lane);
-    s = warp_sum(s);
+    T p = (xb || u) ? warp_dot(Ae + (size_t)ri * lda + c0, v + c0, len, lane) : T(0);
+    p += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, delta, u, -1.0, lane);
+    const double s = warp_sum((double)p);
     if (lane == 0) {
       double val = s;
       if (Bfull) val += gamma_ * Bfull[((size_t)e * G.nn + j) * 5 + k];
@@ -142,8 +157,8 @@ __global__ void __launch_bounds__(256) k_global_apply(Geo G, const double* __res
     const double* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
     const int* __restrict__ pinfo, const int* __restrict__ pcol, const int* __restrict__ iperm,
     const double* __restrict__ x, double* __restrict__ y) {
-  extern __shared__ __align__(16) double sm[];
-  double* v = sm;  // lda, own-column order
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* v = reinterpret_cast<double*>(smem_raw);  // lda, own-column order
   __shared__ int nbr_s[18];
   const int e = blockIdx.x, ne = G.ne, nn = G.nn, lda = G.lda;
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
@@ -249,20 +264,32 @@ namespace sc {
 cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double* Bfull, double alpha, double* u) {
   const Geo& G = c->G;
   if (G.ni == 0) return cudaSuccess;
-  const size_t smem = (size_t)(G.nb + G.ldi) * sizeof(double);
   ProfScope ps(c, SCK_COND_INTERIOR);
-  k_cond_interior<<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo,
-                                                 c->d_iperm, xb, beta, Bfull, alpha, u);
+  if (c->op32) {
+    const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(float);
+    k_cond_interior<float><<<G.K, 256, smem, c->stream>>>(G, c->Aown32, c->X32, c->Ainv32, c->d_nbr, c->d_pptr,
+                                                          c->d_pinfo, c->d_iperm, xb, beta, Bfull, alpha, u);
+  } else {
+    const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double);
+    k_cond_interior<double><<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr,
+                                                           c->d_pinfo, c->d_iperm, xb, beta, Bfull, alpha, u);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t cond_boundary(sc_ctx* c, const double* xb, double delta, const double* Bfull, double gamma_,
                           const double* u, double* y) {
   const Geo& G = c->G;
-  const size_t smem = (size_t)G.lda * sizeof(double);
   ProfScope ps(c, SCK_COND_BOUNDARY);
-  k_cond_boundary<<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm,
-                                                 xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
+  if (c->op32) {
+    const size_t smem = (size_t)G.lda * sizeof(float);
+    k_cond_boundary<float><<<G.K, 256, smem, c->stream>>>(G, c->Aown32, c->X32, c->d_nbr, c->d_pptr, c->d_pinfo,
+                                                          c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
+  } else {
+    const size_t smem = (size_t)G.lda * sizeof(double);
+    k_cond_boundary<double><<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo,
+                                                           c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
+  }
   return cudaGetLastError();
 }
 
@@ -375,15 +402,26 @@ extern "C" sc_status sc_condensed_matvec_static(sc_ctx* c, const double* xb, dou
   }
   // The interior pass writes every entry of u before the boundary pass reads it, so
   // nothing left over from an earlier call is ever read.
+  // Same kernels and precision as sc_condensed_matvec for this context.
+  const bool f32 = c->cfg.precision == SC_PREC_MIXED;
   if (G.ni > 0) {
     count_launch(c);
-    k_cond_interior<<<G.K, 256, (size_t)(G.nb + G.ldi) * sizeof(double), c->stream>>>(
-        G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u);
+    if (f32)
+      k_cond_interior<float><<<G.K, 256, (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(float), c->stream>>>(
+          G, c->Aown32, c->X32, c->Ainv32, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u);
+    else
+      k_cond_interior<double><<<G.K, 256, (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double), c->stream>>>(
+          G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u);
   }
   count_launch(c);
-  k_cond_boundary<<<G.K, 256, (size_t)G.lda * sizeof(double), c->stream>>>(
-      G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
-      G.ni ? u : nullptr, yb);
+  if (f32)
+    k_cond_boundary<float><<<G.K, 256, (size_t)G.lda * sizeof(float), c->stream>>>(
+        G, c->Aown32, c->X32, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
+        G.ni ? u : nullptr, yb);
+  else
+    k_cond_boundary<double><<<G.K, 256, (size_t)G.lda * sizeof(double), c->stream>>>(
+        G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
+        G.ni ? u : nullptr, yb);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {

@@ -105,3 +105,38 @@ def test_tgv_4x4x4_N3_cfl50_reaches_1e8():
     r = B - O.jvp(p, Q, dQ.reshape(Q.shape)).reshape(-1)
     assert np.linalg.norm(r) / np.linalg.norm(B) < 1e-8 * 1.01, st
     assert st["rel_residual"] < 1e-8
+
+
+@pytest.mark.parametrize("n,N,cfl", [(2, 3, 10.0), (3, 2, 10.0), (2, 4, 10.0)])
+def test_mixed_solve_matches_oracle_global_solve(n, N, cfl):
+    # FP32 condensation and condensed operator inside FP64 iterative refinement
+    from paper_1911_02366_gb300 import sc
+    Q, dt, p, ctx = case(n, N, cfl=cfl, precision=sc.SC_PREC_MIXED, rel_tol=1e-12, inner_tol=1e-4,
+                         gmres_restart=60, gmres_max_iters=4000, max_refine=20)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    dQ = np.zeros(Q.size)
+    st = ctx.sc_solve(dQ)
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    x = O.global_solve(A, B)
+    assert st["refinements"] >= 1
+    assert np.linalg.norm(B - A @ dQ) / np.linalg.norm(B) < 1e-11
+    assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < 1e-9, st
+
+
+@pytest.mark.parametrize("n,N", [(2, 3), (3, 2)])
+def test_mixed_condensed_operator_is_fp32_close(n, N):
+    from paper_1911_02366_gb300 import sc
+    Q, dt, p, ctx = case(n, N, precision=sc.SC_PREC_MIXED)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    cs = O.condensed_operator(O.jacobian(p, Q), n, N)
+    S = cs.dense_S()
+    xb = np.random.default_rng(8).standard_normal(S.shape[0])
+    yb = torch.zeros(S.shape[0], dtype=torch.float64, device="cuda")
+    ctx.sc_condensed_matvec(torch.tensor(xb, device="cuda"), yb)
+    torch.cuda.synchronize()
+    assert rel(yb.cpu().numpy(), S @ xb) < 1e-4
