@@ -92,7 +92,7 @@ void free_all(sc_ctx* c) {
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
                     &c->Hd, &c->partial, &c->Xfull, &c->Rfull};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
-  float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32};
+  float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf};
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
@@ -283,6 +283,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
     A(dalloc(&c->Aown32, (size_t)G.K * own_stride(G))); A(dalloc(&c->X32, (size_t)G.K * G.NP * 25));
     A(dalloc(&c->Ainv32, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Y32, (size_t)G.K * G.ni * G.nb));
     A(dalloc(&c->See32, (size_t)G.K * G.nb * G.lds)); A(dalloc(&c->Dfull, dofs));
+    A(dalloc(&c->Zf, n1)); A(dalloc(&c->Xbf, n1)); A(dalloc(&c->Uf, (size_t)G.K * G.ni));
   } else {
     A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Ytmp, (size_t)G.K * G.ni * G.nb));
     A(dalloc(&c->See, (size_t)G.K * G.nb * G.lds));
@@ -452,11 +453,15 @@ sc_status sc_get_jacobian_block(sc_ctx* c, int e, int col, double* block) {
 sc_status sc_condensed_matvec(sc_ctx* c, const double* xb, double* yb) {
   if (!c || !xb || !yb) return SC_ERR_ARG;
   if (!c->condensed) return fail(c, SC_ERR_STATE, "condensed_matvec before condense");
-  c->op32 = c->cfg.precision == SC_PREC_MIXED;
-  cudaError_t e1 = sc::cond_interior(c, xb, 1.0, nullptr, 0.0, c->Ui);
-  cudaError_t e2 = e1 == cudaSuccess ? sc::cond_boundary(c, xb, 1.0, nullptr, 0.0, c->Ui, yb) : e1;
-  c->op32 = false;
-  SC_CUDA(e2);
+  if (c->cfg.precision == SC_PREC_MIXED) {
+    const size_t n1 = (size_t)c->G.K * c->G.nb;
+    SC_CUDA(sc::vec_to_float(c, c->Xbf, xb, n1));
+    SC_CUDA(sc::cond_interior32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf));
+    SC_CUDA(sc::cond_boundary32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf, yb));
+  } else {
+    SC_CUDA(sc::cond_interior(c, xb, 1.0, nullptr, 0.0, c->Ui));
+    SC_CUDA(sc::cond_boundary(c, xb, 1.0, nullptr, 0.0, c->Ui, yb));
+  }
   return check(c);
 }
 
@@ -489,9 +494,15 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
     int k = 0;
     for (int j = 0; j < m && iters < max_iters; ++j) {
       double* Vj = c->V + (size_t)j * n1;
-      SC_CUDA(sc::precond_apply(c, Vj, c->Zv));
-      SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
-      SC_CUDA(sc::cond_boundary(c, c->Zv, 1.0, nullptr, 0.0, c->Ui, c->Wv));
+      if (c->op32) {
+        SC_CUDA(sc::precond_apply32(c, Vj, nullptr, c->Zf));
+        SC_CUDA(sc::cond_interior32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf));
+        SC_CUDA(sc::cond_boundary32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf, c->Wv));
+      } else {
+        SC_CUDA(sc::precond_apply(c, Vj, c->Zv));
+        SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
+        SC_CUDA(sc::cond_boundary(c, c->Zv, 1.0, nullptr, 0.0, c->Ui, c->Wv));
+      }
       SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h1));
       SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, h1, -1.0));
       SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h2));
@@ -527,11 +538,19 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
     SC_CUDA(cudaMemcpyAsync(c->Hd, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     SC_CUDA(cudaMemsetAsync(c->Tb, 0, n1 * sizeof(double), c->stream));
     SC_CUDA(sc::vec_update(c, c->Tb, c->V, k, n1, c->Hd, 1.0));
-    SC_CUDA(sc::precond_apply(c, c->Tb, c->Zv));
-    SC_CUDA(sc::vec_axpby(c, c->Xb, 1.0, c->Zv, 1.0, n1));
     // true condensed residual r = g - S x
-    SC_CUDA(sc::cond_interior(c, c->Xb, 1.0, nullptr, 0.0, c->Ui));
-    SC_CUDA(sc::cond_boundary(c, c->Xb, 1.0, nullptr, 0.0, c->Ui, c->Wv));
+    if (c->op32) {
+      SC_CUDA(sc::precond_apply32(c, c->Tb, c->Zv, nullptr));
+      SC_CUDA(sc::vec_axpby(c, c->Xb, 1.0, c->Zv, 1.0, n1));
+      SC_CUDA(sc::vec_to_float(c, c->Xbf, c->Xb, n1));
+      SC_CUDA(sc::cond_interior32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf));
+      SC_CUDA(sc::cond_boundary32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf, c->Wv));
+    } else {
+      SC_CUDA(sc::precond_apply(c, c->Tb, c->Zv));
+      SC_CUDA(sc::vec_axpby(c, c->Xb, 1.0, c->Zv, 1.0, n1));
+      SC_CUDA(sc::cond_interior(c, c->Xb, 1.0, nullptr, 0.0, c->Ui));
+      SC_CUDA(sc::cond_boundary(c, c->Xb, 1.0, nullptr, 0.0, c->Ui, c->Wv));
+    }
     SC_CUDA(cudaMemcpyAsync(c->Rb, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     SC_CUDA(sc::vec_axpby(c, c->Rb, -1.0, c->Wv, 1.0, n1));
     beta = dnorm2(c, c->Rb, n1, hs);
@@ -550,13 +569,24 @@ sc_status condensed_solve(sc_ctx* c, const double* r, double* d, double rel_tol_
                           int* iters, double* resid, double* gnorm) {
   const Geo& G = c->G;
   const size_t n1 = (size_t)G.K * G.nb;
-  SC_CUDA(sc::cond_interior(c, nullptr, 0.0, r, 1.0, c->Ui));
-  SC_CUDA(sc::cond_boundary(c, nullptr, 0.0, r, 1.0, c->Ui, c->Gb));
+  if (c->op32) {
+    SC_CUDA(sc::cond_interior32(c, nullptr, 0.0, r, 1.0, c->Uf));
+    SC_CUDA(sc::cond_boundary32(c, nullptr, 0.0, r, 1.0, c->Uf, c->Gb));
+  } else {
+    SC_CUDA(sc::cond_interior(c, nullptr, 0.0, r, 1.0, c->Ui));
+    SC_CUDA(sc::cond_boundary(c, nullptr, 0.0, r, 1.0, c->Ui, c->Gb));
+  }
   *gnorm = dnorm2(c, c->Gb, n1, c->Hd + 2 * (c->restart_alloc + 1) + 2);
   sc_status s = gmres_condensed(c, std::max(rel_tol_g * *gnorm, abs_floor), max_iters, iters, resid);
   if (s != SC_OK) return s;
-  SC_CUDA(sc::cond_interior(c, c->Xb, -1.0, r, 1.0, c->Ui));
-  SC_CUDA(sc::scatter_solution(c, c->Xb, c->Ui, d));
+  if (c->op32) {
+    SC_CUDA(sc::vec_to_float(c, c->Xbf, c->Xb, n1));
+    SC_CUDA(sc::cond_interior32(c, c->Xbf, -1.0, r, 1.0, c->Uf));
+    SC_CUDA(sc::scatter_solution32(c, c->Xb, c->Uf, d));
+  } else {
+    SC_CUDA(sc::cond_interior(c, c->Xb, -1.0, r, 1.0, c->Ui));
+    SC_CUDA(sc::scatter_solution(c, c->Xb, c->Ui, d));
+  }
   return SC_OK;
 }
 

@@ -321,6 +321,27 @@ __device__ __forceinline__ T dot_row(const T* __restrict__ row, const T* xs, int
   return s0 + s1;
 }
 
+// Two row dots at once over [k0, k1) (row + k0, xs + k0 16-byte aligned).
+template <class T>
+__device__ __forceinline__ void dot_row2(const T* __restrict__ ra, const T* __restrict__ rb, const T* xs, int k0,
+                                         int k1, int lane, T& sa, T& sb) {
+  using V = typename V16<T>::type;
+  constexpr int W = V16<T>::n;
+  const V* a = reinterpret_cast<const V*>(ra + k0);
+  const V* b = reinterpret_cast<const V*>(rb + k0);
+  const V* x = reinterpret_cast<const V*>(xs + k0);
+  const int len = k1 - k0, nv = len / W;
+  T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+#pragma unroll 2
+  for (int i = lane; i < nv; i += 32) {
+    const V xv = x[i];
+    vfma(__ldg(a + i), xv, a0, a1);
+    vfma(__ldg(b + i), xv, b0, b1);
+  }
+  for (int i = k0 + nv * W + lane; i < k1; i += 32) { a0 = fma(__ldg(ra + i), xs[i], a0); b0 = fma(__ldg(rb + i), xs[i], b0); }
+  sa = a0 + a1; sb = b0 + b1;
+}
+
 // z = (P^T L U)^-1 v for every element: one CTA per element, 32-row panels.  Each panel
 // first subtracts the already-solved part (rows spread over the warps, 16-byte row
 // reads), then the 32 x 32 diagonal triangle is staged in shared memory and solved by
@@ -328,7 +349,7 @@ __device__ __forceinline__ T dot_row(const T* __restrict__ row, const T* xs, int
 template <class T>
 __global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ LU, long long stride, int lda,
                                                   const int* __restrict__ rowperm, const double* __restrict__ v,
-                                                  double* __restrict__ z) {
+                                                  double* __restrict__ z, T* __restrict__ zt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);
   __shared__ T Dg[32][33];
@@ -341,12 +362,17 @@ __global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ L
   __syncthreads();
   for (int i0 = 0; i0 < n; i0 += 32) {  // unit lower triangle
     const int bs = min(32, n - i0);
-    for (int r = warp; r < bs; r += nw) {
+    for (int r = 2 * warp; r < bs; r += 2 * nw) {
+      const int r2 = r + 1 < bs ? r + 1 : r;
       const T* row = M + (long long)(i0 + r) * lda;
+      const T* row2 = M + (long long)(i0 + r2) * lda;
       Dg[r][lane] = lane < bs ? row[i0 + lane] : T(0);
+      Dg[r2][lane] = lane < bs ? row2[i0 + lane] : T(0);
       if (i0 > 0) {
-        const T s = warp_sum_t(dot_row(row, xs, 0, i0, lane));
-        if (lane == 0) xs[i0 + r] -= s;
+        T sa, sb;
+        dot_row2(row, row2, xs, 0, i0, lane, sa, sb);
+        sa = warp_sum_t(sa); sb = warp_sum_t(sb);
+        if (lane == 0) { xs[i0 + r] -= sa; if (r2 != r) xs[i0 + r2] -= sb; }
       }
     }
     __syncthreads();
@@ -363,12 +389,17 @@ __global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ L
   const int nblk = (n + 31) / 32;
   for (int b = nblk - 1; b >= 0; --b) {  // upper triangle
     const int i0 = b * 32, bs = min(32, n - i0), i1 = i0 + bs;
-    for (int r = warp; r < bs; r += nw) {
+    for (int r = 2 * warp; r < bs; r += 2 * nw) {
+      const int r2 = r + 1 < bs ? r + 1 : r;
       const T* row = M + (long long)(i0 + r) * lda;
+      const T* row2 = M + (long long)(i0 + r2) * lda;
       Dg[r][lane] = lane < bs ? row[i0 + lane] : T(0);
+      Dg[r2][lane] = lane < bs ? row2[i0 + lane] : T(0);
       if (i1 < n) {
-        const T s = warp_sum_t(dot_row(row, xs, i1, n, lane));
-        if (lane == 0) xs[i0 + r] -= s;
+        T sa, sb;
+        dot_row2(row, row2, xs, i1, n, lane, sa, sb);
+        sa = warp_sum_t(sa); sb = warp_sum_t(sb);
+        if (lane == 0) { xs[i0 + r] -= sa; if (r2 != r) xs[i0 + r2] -= sb; }
       }
     }
     __syncthreads();
@@ -383,7 +414,10 @@ __global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ L
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) z[(long long)e * n + i] = (double)xs[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (z) z[(long long)e * n + i] = (double)xs[i];
+    if (zt) zt[(long long)e * n + i] = xs[i];
+  }
 }
 
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
@@ -465,15 +499,26 @@ cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
     return cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   }
   ProfScope ps(c, SCK_LU_SOLVE);
-  if (c->cfg.precision == SC_PREC_MIXED) {
-    const size_t smem = (size_t)G.nb * sizeof(float);
-    k_lu_solve<float><<<G.K, 256, smem, c->stream>>>(G.nb, c->See32, (long long)G.nb * G.lds, G.lds, c->rowperm,
-                                                     v, z);
-  } else {
-    const size_t smem = (size_t)G.nb * sizeof(double);
-    k_lu_solve<double><<<G.K, 256, smem, c->stream>>>(G.nb, c->See, (long long)G.nb * G.lds, G.lds, c->rowperm,
-                                                      v, z);
+  const size_t smem = (size_t)G.nb * sizeof(double);
+  k_lu_solve<double><<<G.K, 256, smem, c->stream>>>(G.nb, c->See, (long long)G.nb * G.lds, G.lds, c->rowperm, v, z,
+                                                    nullptr);
+  return cudaGetLastError();
+}
+
+// Block-Jacobi with the FP32 factors; writes z in double and / or zf in float.
+cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
+  const Geo& G = c->G;
+  const size_t n1 = (size_t)G.K * G.nb;
+  if (c->cfg.precond != SC_PC_BLOCK_JACOBI) {
+    cudaError_t e = cudaSuccess;
+    if (z) e = cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && zf) e = vec_to_float(c, zf, v, n1);
+    return e;
   }
+  ProfScope ps(c, SCK_LU_SOLVE);
+  const size_t smem = (size_t)G.nb * sizeof(float);
+  k_lu_solve<float><<<G.K, 256, smem, c->stream>>>(G.nb, c->See32, (long long)G.nb * G.lds, G.lds, c->rowperm, v, z,
+                                                   zf);
   return cudaGetLastError();
 }
 

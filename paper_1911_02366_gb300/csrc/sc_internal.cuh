@@ -264,6 +264,7 @@ struct sc_ctx {
   int restart_alloc = 0;
   // mixed-precision arm: FP32 copies of the element blocks and FP32 condensation
   float *Aown32 = nullptr, *X32 = nullptr, *Ainv32 = nullptr, *Y32 = nullptr, *See32 = nullptr;
+  float *Zf = nullptr, *Xbf = nullptr, *Uf = nullptr;  // FP32 vectors of the FP32 operator
   double* Dfull = nullptr;  // refinement correction
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};
@@ -311,6 +312,12 @@ cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double
 cudaError_t cond_boundary(sc_ctx* c, const double* xb, double delta, const double* Bfull, double gamma_,
                           const double* u, double* y);
 cudaError_t precond_apply(sc_ctx* c, const double* v, double* z);
+cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf);
+cudaError_t cond_interior32(sc_ctx* c, const float* xb, double beta, const double* Bfull, double alpha, float* u);
+cudaError_t cond_boundary32(sc_ctx* c, const float* xb, double delta, const double* Bfull, double gamma_,
+                            const float* u, double* y);
+cudaError_t scatter_solution32(sc_ctx* c, const double* xb, const float* xi, double* x);
+cudaError_t vec_to_float(sc_ctx* c, float* y, const double* x, size_t n);
 cudaError_t global_apply(sc_ctx* c, const double* x, double* y);
 cudaError_t scatter_solution(sc_ctx* c, const double* xb, const double* xi, double* x);
 cudaError_t multidot(sc_ctx* c, const double* V, int nvec, size_t n, const double* w, double* out_dev);

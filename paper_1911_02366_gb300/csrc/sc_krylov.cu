@@ -46,14 +46,42 @@ __device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* v, int
   return s0 + s1;
 }
 
+__device__ __forceinline__ float warp_sum(float s) {
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+// Two row dots at once (independent loads in flight): lane partial sums of
+// rowA . v and rowB . v over len entries.
+template <class T>
+__device__ __forceinline__ void warp_dot2(const T* __restrict__ rowA, const T* __restrict__ rowB, const T* v, int len,
+                                          int lane, T& sa, T& sb) {
+  using V = typename Vec16<T>::type;
+  constexpr int W = Vec16<T>::n;
+  const V* ra = reinterpret_cast<const V*>(rowA);
+  const V* rb = reinterpret_cast<const V*>(rowB);
+  const V* x = reinterpret_cast<const V*>(v);
+  const int nv = len / W;
+  T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+#pragma unroll 2
+  for (int i = lane; i < nv; i += 32) {
+    const V xa = x[i];
+    fma16(__ldg(ra + i), xa, a0, a1);
+    fma16(__ldg(rb + i), xa, b0, b1);
+  }
+  for (int i = nv * W + lane; i < len; i += 32) { a0 = fma(__ldg(rowA + i), v[i], a0); b0 = fma(__ldg(rowB + i), v[i], b0); }
+  sa = a0 + a1; sb = b0 + b1;
+}
+
 // Neighbour couplings of row (node j, variable k) of element e.  The couplings of one
 // row are contiguous in X (layout X[e][k][pair][l]); vb / vi are the condensed
-// boundary / interior vectors of all elements (either may be null), scaled by cb / ci.
+// boundary / interior vectors of all elements in the storage precision T (either may
+// be null), scaled by cb / ci.
 template <class T>
 __device__ __forceinline__ T cross_row(const Geo& G, int e, int j, int k, const T* __restrict__ X,
                                        const int* nbr_s, const int* __restrict__ pptr,
-                                       const int* __restrict__ pinfo, const double* __restrict__ vb, double cb,
-                                       const double* __restrict__ vi, double ci, int lane) {
+                                       const int* __restrict__ pinfo, const T* __restrict__ vb, T cb,
+                                       const T* __restrict__ vi, T ci, int lane) {
   const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
   const T* Xr = X + (((size_t)e * 5 + k) * G.NP + q0) * 5;
   T s = T(0);
@@ -62,7 +90,7 @@ __device__ __forceinline__ T cross_row(const Geo& G, int e, int j, int k, const 
     const int info = __ldg(pinfo + q);
     const int nb = nbr_s[pinfo_slot(info)];
     const int off = pinfo_offset(info) + l;
-    double xv;
+    T xv;
     if (pinfo_interior(info)) {
       if (!vi) continue;
       xv = ci * vi[(size_t)nb * G.ni + off];
@@ -70,18 +98,19 @@ __device__ __forceinline__ T cross_row(const Geo& G, int e, int j, int k, const 
       if (!vb) continue;
       xv = cb * vb[(size_t)nb * G.nb + off];
     }
-    s = fma(__ldg(Xr + f), (T)xv, s);
+    s = fma(__ldg(Xr + f), xv, s);
   }
   return s;
 }
 
-// Interior pass: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e); matrices stored in T.
+// Interior pass: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e).  Matrices and the
+// vectors x_b, u in precision T; the full right-hand side B in double.
 template <class T>
 __global__ void __launch_bounds__(256) k_cond_interior(Geo G, const T* __restrict__ Aown,
     const T* __restrict__ X, const T* __restrict__ Ainv, const int* __restrict__ nbr,
     const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm,
-    const double* __restrict__ xb, double beta, const double* __restrict__ Bfull, double alpha,
-    double* __restrict__ u) {
+    const T* __restrict__ xb, double beta, const double* __restrict__ Bfull, double alpha,
+    T* __restrict__ u) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = blockIdx.x, ni = G.ni, nb = G.nb;
   T* v = reinterpret_cast<T*>(smem_raw);  // nb: x_e
@@ -90,64 +119,78 @@ __global__ void __launch_bounds__(256) k_cond_interior(Geo G, const T* __restric
   __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) v[i] = xb ? (T)xb[(size_t)e * nb + i] : T(0);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v[i] = xb ? xb[(size_t)e * nb + i] : T(0);
   for (int i = ni + threadIdx.x; i < G.ldi; i += blockDim.x) t[i] = T(0);
   __syncthreads();
   const T* Ae = Aown + (size_t)e * own_stride(G);
   for (int ri = warp; ri < ni; ri += nw) {
     const int j = __ldg(iperm + ri / 5), k = ri % 5;
-    double s = 0.0;
+    T s = T(0);
     if (xb) {
-      T p = warp_dot(Ae + (size_t)ri * G.lda + G.cb0, v, nb, lane);
-      p += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, 1.0, nullptr, 0.0, lane);
-      s = warp_sum((double)p);
+      s = warp_dot(Ae + (size_t)ri * G.lda + G.cb0, v, nb, lane);
+      s += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, T(1), (const T*)nullptr, T(0), lane);
+      s = warp_sum(s);
     }
     if (lane == 0) {
-      double val = beta * s;
-      if (Bfull) val += alpha * Bfull[((size_t)e * G.nn + j) * 5 + k];
-      t[ri] = (T)val;
+      T val = T(beta) * s;
+      if (Bfull) val += T(alpha * Bfull[((size_t)e * G.nn + j) * 5 + k]);
+      t[ri] = val;
     }
   }
   __syncthreads();
   const T* Ie = Ainv + (size_t)e * ni * G.ldi;
-  for (int ri = warp; ri < ni; ri += nw) {
-    const double s = warp_sum((double)warp_dot(Ie + (size_t)ri * G.ldi, t, G.ldi, lane));
-    if (lane == 0) u[(size_t)e * ni + ri] = s;
+  for (int ri = 2 * warp; ri < ni; ri += 2 * nw) {
+    const bool two = ri + 1 < ni;
+    T sa, sb;
+    warp_dot2(Ie + (size_t)ri * G.ldi, Ie + (size_t)(two ? ri + 1 : ri) * G.ldi, t, G.ldi, lane, sa, sb);
+    sa = warp_sum(sa); sb = warp_sum(sb);
+    if (lane == 0) {
+      u[(size_t)e * ni + ri] = sa;
+      if (two) u[(size_t)e * ni + ri + 1] = sb;
+    }
   }
 }
 
-// Boundary pass: y_e = gamma B_b,e + delta (A_bb x_b)_e - (A_bi u)_e; matrices stored in T.
+// Boundary pass: y_e = gamma B_b,e + delta (A_bb x_b)_e - (A_bi u)_e.  Matrices and x_b, u
+// in precision T; B and y in double.
 template <class T>
 __global__ void __launch_bounds__(256) k_cond_boundary(Geo G, const T* __restrict__ Aown,
     const T* __restrict__ X, const int* __restrict__ nbr,
     const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm,
-    const double* __restrict__ xb, double delta, const double* __restrict__ Bfull, double gamma_,
-    const double* __restrict__ u, double* __restrict__ y) {
+    const T* __restrict__ xb, double delta, const double* __restrict__ Bfull, double gamma_,
+    const T* __restrict__ u, double* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = blockIdx.x, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, cb0 = G.cb0;
   T* v = reinterpret_cast<T*>(smem_raw);  // lda: [-u_e | 0 | delta x_e | 0] in own-column order
   __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const T dT = T(delta);
   if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
   for (int i = threadIdx.x; i < lda; i += blockDim.x) {
-    double val = 0.0;
+    T val = T(0);
     if (i < ni) { if (u) val = -u[(size_t)e * ni + i]; }
-    else if (i >= cb0 && i < cb0 + nb) { if (xb) val = delta * xb[(size_t)e * nb + i - cb0]; }
-    v[i] = (T)val;
+    else if (i >= cb0 && i < cb0 + nb) { if (xb) val = dT * xb[(size_t)e * nb + i - cb0]; }
+    v[i] = val;
   }
   __syncthreads();
   const T* Ae = Aown + (size_t)e * own_stride(G);
   const int c0 = u ? 0 : cb0;                 // skip the A_bi columns when u is absent
   const int len = (xb ? cb0 + nb : ni) - c0;  // and the A_bb columns when x_b is absent
-  for (int ri = ni + warp; ri < ne; ri += nw) {
-    const int j = __ldg(iperm + ri / 5), k = ri % 5;
-    T p = (xb || u) ? warp_dot(Ae + (size_t)ri * lda + c0, v + c0, len, lane) : T(0);
-    p += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, delta, u, -1.0, lane);
-    const double s = warp_sum((double)p);
+  for (int ra = ni + 2 * warp; ra < ne; ra += 2 * nw) {
+    const int rb2 = ra + 1 < ne ? ra + 1 : ra;
+    T sa = T(0), sb = T(0);
+    if (xb || u) warp_dot2(Ae + (size_t)ra * lda + c0, Ae + (size_t)rb2 * lda + c0, v + c0, len, lane, sa, sb);
+    sa += cross_row(G, e, __ldg(iperm + ra / 5), ra % 5, X, nbr_s, pptr, pinfo, xb, dT, u, T(-1), lane);
+    sb += cross_row(G, e, __ldg(iperm + rb2 / 5), rb2 % 5, X, nbr_s, pptr, pinfo, xb, dT, u, T(-1), lane);
+    sa = warp_sum(sa); sb = warp_sum(sb);
     if (lane == 0) {
-      double val = s;
-      if (Bfull) val += gamma_ * Bfull[((size_t)e * G.nn + j) * 5 + k];
-      y[(size_t)e * nb + ri - ni] = val;
+      double va = (double)sa, vb = (double)sb;
+      if (Bfull) {
+        va += gamma_ * Bfull[((size_t)e * G.nn + __ldg(iperm + ra / 5)) * 5 + ra % 5];
+        vb += gamma_ * Bfull[((size_t)e * G.nn + __ldg(iperm + rb2 / 5)) * 5 + rb2 % 5];
+      }
+      y[(size_t)e * nb + ra - ni] = va;
+      if (rb2 != ra) y[(size_t)e * nb + rb2 - ni] = vb;
     }
   }
 }
@@ -186,13 +229,14 @@ __global__ void __launch_bounds__(256) k_global_apply(Geo G, const double* __res
   }
 }
 
+template <class TI>
 __global__ void k_scatter(Geo G, const int* __restrict__ iperm, const double* __restrict__ xb,
-                          const double* __restrict__ xi, double* __restrict__ x) {
+                          const TI* __restrict__ xi, double* __restrict__ x) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= (size_t)G.K * G.ne) return;
   const int e = (int)(t / G.ne), r = (int)(t % G.ne);
   const int pos = r / 5, k = r % 5;
-  const double v = pos < G.nin ? xi[(size_t)e * G.ni + r] : xb[(size_t)e * G.nb + r - G.ni];
+  const double v = pos < G.nin ? (double)xi[(size_t)e * G.ni + r] : xb[(size_t)e * G.nb + r - G.ni];
   x[((size_t)e * G.nn + iperm[pos]) * 5 + k] = v;
 }
 
@@ -249,6 +293,11 @@ __global__ void k_scale_copy(double* __restrict__ dst, const double* __restrict_
     dst[t] = a * src[t];
 }
 
+__global__ void k_vec_to_float(float* __restrict__ y, const double* __restrict__ x, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = (float)x[t];
+}
+
 __global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
     y[t] = a * x[t] + b * y[t];
@@ -265,15 +314,9 @@ cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double
   const Geo& G = c->G;
   if (G.ni == 0) return cudaSuccess;
   ProfScope ps(c, SCK_COND_INTERIOR);
-  if (c->op32) {
-    const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(float);
-    k_cond_interior<float><<<G.K, 256, smem, c->stream>>>(G, c->Aown32, c->X32, c->Ainv32, c->d_nbr, c->d_pptr,
-                                                          c->d_pinfo, c->d_iperm, xb, beta, Bfull, alpha, u);
-  } else {
-    const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double);
-    k_cond_interior<double><<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr,
-                                                           c->d_pinfo, c->d_iperm, xb, beta, Bfull, alpha, u);
-  }
+  const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double);
+  k_cond_interior<double><<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo,
+                                                         c->d_iperm, xb, beta, Bfull, alpha, u);
   return cudaGetLastError();
 }
 
@@ -281,15 +324,29 @@ cudaError_t cond_boundary(sc_ctx* c, const double* xb, double delta, const doubl
                           const double* u, double* y) {
   const Geo& G = c->G;
   ProfScope ps(c, SCK_COND_BOUNDARY);
-  if (c->op32) {
-    const size_t smem = (size_t)G.lda * sizeof(float);
-    k_cond_boundary<float><<<G.K, 256, smem, c->stream>>>(G, c->Aown32, c->X32, c->d_nbr, c->d_pptr, c->d_pinfo,
-                                                          c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
-  } else {
-    const size_t smem = (size_t)G.lda * sizeof(double);
-    k_cond_boundary<double><<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo,
-                                                           c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
-  }
+  const size_t smem = (size_t)G.lda * sizeof(double);
+  k_cond_boundary<double><<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo,
+                                                         c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
+  return cudaGetLastError();
+}
+
+cudaError_t cond_interior32(sc_ctx* c, const float* xb, double beta, const double* Bfull, double alpha, float* u) {
+  const Geo& G = c->G;
+  if (G.ni == 0) return cudaSuccess;
+  ProfScope ps(c, SCK_COND_INTERIOR);
+  const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(float);
+  k_cond_interior<float><<<G.K, 256, smem, c->stream>>>(G, c->Aown32, c->X32, c->Ainv32, c->d_nbr, c->d_pptr,
+                                                        c->d_pinfo, c->d_iperm, xb, beta, Bfull, alpha, u);
+  return cudaGetLastError();
+}
+
+cudaError_t cond_boundary32(sc_ctx* c, const float* xb, double delta, const double* Bfull, double gamma_,
+                            const float* u, double* y) {
+  const Geo& G = c->G;
+  ProfScope ps(c, SCK_COND_BOUNDARY);
+  const size_t smem = (size_t)G.lda * sizeof(float);
+  k_cond_boundary<float><<<G.K, 256, smem, c->stream>>>(G, c->Aown32, c->X32, c->d_nbr, c->d_pptr, c->d_pinfo,
+                                                        c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
   return cudaGetLastError();
 }
 
@@ -306,7 +363,15 @@ cudaError_t scatter_solution(sc_ctx* c, const double* xb, const double* xi, doub
   const Geo& G = c->G;
   const size_t n = (size_t)G.K * G.ne;
   count_launch(c);
-  k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(G, c->d_iperm, xb, xi, x);
+  k_scatter<double><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(G, c->d_iperm, xb, xi, x);
+  return cudaGetLastError();
+}
+
+cudaError_t scatter_solution32(sc_ctx* c, const double* xb, const float* xi, double* x) {
+  const Geo& G = c->G;
+  const size_t n = (size_t)G.K * G.ne;
+  count_launch(c);
+  k_scatter<float><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(G, c->d_iperm, xb, xi, x);
   return cudaGetLastError();
 }
 
@@ -329,6 +394,12 @@ cudaError_t vec_update(sc_ctx* c, double* w, const double* V, int nvec, size_t n
 cudaError_t vec_scale_copy(sc_ctx* c, double* dst, const double* src, size_t n, const double* scal_dev, int invert) {
   count_launch(c);
   k_scale_copy<<<kDotBlocks, 256, 0, c->stream>>>(dst, src, n, scal_dev, invert);
+  return cudaGetLastError();
+}
+
+cudaError_t vec_to_float(sc_ctx* c, float* y, const double* x, size_t n) {
+  count_launch(c);
+  k_vec_to_float<<<kDotBlocks, 256, 0, c->stream>>>(y, x, n);
   return cudaGetLastError();
 }
 
@@ -402,26 +473,19 @@ extern "C" sc_status sc_condensed_matvec_static(sc_ctx* c, const double* xb, dou
   }
   // The interior pass writes every entry of u before the boundary pass reads it, so
   // nothing left over from an earlier call is ever read.
-  // Same kernels and precision as sc_condensed_matvec for this context.
-  const bool f32 = c->cfg.precision == SC_PREC_MIXED;
+  if (c->cfg.precision != SC_PREC_FP64) {
+    c->err = "condensed_matvec_static: needs a context created with SC_PREC_FP64";
+    return SC_ERR_STATE;
+  }
   if (G.ni > 0) {
     count_launch(c);
-    if (f32)
-      k_cond_interior<float><<<G.K, 256, (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(float), c->stream>>>(
-          G, c->Aown32, c->X32, c->Ainv32, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u);
-    else
-      k_cond_interior<double><<<G.K, 256, (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double), c->stream>>>(
-          G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u);
+    k_cond_interior<double><<<G.K, 256, (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double), c->stream>>>(
+        G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u);
   }
   count_launch(c);
-  if (f32)
-    k_cond_boundary<float><<<G.K, 256, (size_t)G.lda * sizeof(float), c->stream>>>(
-        G, c->Aown32, c->X32, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
-        G.ni ? u : nullptr, yb);
-  else
-    k_cond_boundary<double><<<G.K, 256, (size_t)G.lda * sizeof(double), c->stream>>>(
-        G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
-        G.ni ? u : nullptr, yb);
+  k_cond_boundary<double><<<G.K, 256, (size_t)G.lda * sizeof(double), c->stream>>>(
+      G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
+      G.ni ? u : nullptr, yb);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
