@@ -90,9 +90,9 @@ void diff_matrix(const std::vector<double>& x, double D[SC_MAXP][SC_MAXP]) {
 void free_all(sc_ctx* c) {
   double** dps[] = {&c->Q, &c->Qh, &c->grad, &c->F, &c->B, &c->NJ, &c->RJ, &c->Aown, &c->X, &c->Ainv,
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
-                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull};
+                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
-  float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf};
+  float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32};
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
@@ -284,11 +284,13 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
     A(dalloc(&c->Ainv32, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Y32, (size_t)G.K * G.ni * G.nb));
     A(dalloc(&c->See32, (size_t)G.K * G.nb * G.lds)); A(dalloc(&c->Dfull, dofs));
     A(dalloc(&c->Zf, n1)); A(dalloc(&c->Xbf, n1)); A(dalloc(&c->Uf, (size_t)G.K * G.ni));
+    A(dalloc(&c->Cross32, n1 + (size_t)G.K * G.ni));
   } else {
     A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Ytmp, (size_t)G.K * G.ni * G.nb));
     A(dalloc(&c->See, (size_t)G.K * G.nb * G.lds));
   }
   A(dalloc(&c->piv, (size_t)G.K * G.nb)); A(dalloc(&c->rowperm, (size_t)G.K * G.nb));
+  A(dalloc(&c->Cross, n1 + (size_t)G.K * G.ni));
   A(dalloc(&c->V, n1 * (m + 1))); A(dalloc(&c->Wv, n1)); A(dalloc(&c->Zv, n1)); A(dalloc(&c->Xb, n1));
   A(dalloc(&c->Gb, n1)); A(dalloc(&c->Rb, n1)); A(dalloc(&c->Tb, n1));
   A(dalloc(&c->Ui, (size_t)G.K * G.ni)); A(dalloc(&c->Hd, 3 * (size_t)(m + 2) + 16));

@@ -269,6 +269,51 @@ __global__ void __launch_bounds__(256) k_lu(int n, T* __restrict__ A, long long 
   if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
 }
 
+// Replace every 32 x 32 diagonal block of the LU factors by the inverses of its
+// triangles: strictly lower part <- (unit lower L_bb)^-1, upper part <- (U_bb)^-1.  The
+// off-diagonal blocks (all the substitutions read besides these) are untouched.  One CTA
+// per element, one warp per block, one lane per column.
+template <class T>
+__global__ void __launch_bounds__(256) k_diag_inv(int n, T* __restrict__ LU, long long stride, int lda) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  T* Ds = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 2 * 32 * 33;  // block, then its inverse
+  T* Is = Ds + 32 * 33;
+  T* M = LU + (long long)blockIdx.x * stride;
+  const int nblk = (n + 31) / 32;
+  for (int b = warp; b < nblk; b += nw) {
+    const int i0 = b * 32, bs = min(32, n - i0);
+    for (int r = 0; r < bs; ++r) Ds[r * 33 + lane] = lane < bs ? M[(long long)(i0 + r) * lda + i0 + lane] : T(0);
+    __syncwarp();
+    if (lane < bs) {
+      const int c = lane;
+      // column c of L^-1 (unit lower)
+      for (int i = 0; i < bs; ++i) {
+        T x = T(0);
+        if (i == c) x = T(1);
+        else if (i > c) {
+          for (int k = c; k < i; ++k) x = fma(-Ds[i * 33 + k], Is[k * 33 + c], x);
+        }
+        Is[i * 33 + c] = x;
+      }
+      // column c of U^-1 (upper), rows c down to 0, stored in the upper part
+      T xc = T(1) / Ds[c * 33 + c];
+      T col[32];
+      col[c] = xc;
+      for (int i = c - 1; i >= 0; --i) {
+        T acc = T(0);
+        for (int k = i + 1; k <= c; ++k) acc = fma(Ds[i * 33 + k], col[k], acc);
+        col[i] = -acc / Ds[i * 33 + i];
+      }
+      for (int i = 0; i <= c; ++i) Is[i * 33 + c] = col[i];
+    }
+    __syncwarp();
+    for (int r = 0; r < bs; ++r)
+      if (lane < bs) M[(long long)(i0 + r) * lda + i0 + lane] = Is[r * 33 + lane];
+    __syncwarp();
+  }
+}
+
 // Sequential LAPACK-style row interchanges -> one gather permutation per element:
 // row i of P A is row rowperm[i] of A.
 __global__ void k_piv_to_perm(int n, const int* __restrict__ piv_all, int* __restrict__ rowperm, int nelem) {
@@ -344,8 +389,9 @@ __device__ __forceinline__ void dot_row2(const T* __restrict__ ra, const T* __re
 
 // z = (P^T L U)^-1 v for every element: one CTA per element, 32-row panels.  Each panel
 // first subtracts the already-solved part (rows spread over the warps, 16-byte row
-// reads), then the 32 x 32 diagonal triangle is staged in shared memory and solved by
-// warp 0 with shuffles.  Arithmetic in the factor precision T; v, z in double.
+// reads), then applies the stored inverse of its 32 x 32 diagonal triangle (see
+// k_diag_inv) as one 32-wide product.  Arithmetic in the factor precision T; v in
+// double, outputs z (double) and / or zt (T).
 template <class T>
 __global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ LU, long long stride, int lda,
                                                   const int* __restrict__ rowperm, const double* __restrict__ v,
@@ -376,13 +422,15 @@ __global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ L
       }
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0) {  // x_blk <- L_bb^-1 x_blk (unit lower inverse stored below the diagonal)
       T xl = lane < bs ? xs[i0 + lane] : T(0);
-      for (int rr = 0; rr < bs; ++rr) {
-        const T xr = __shfl_sync(0xffffffffu, xl, rr);
-        if (lane > rr) xl = fma(-Dg[lane][rr], xr, xl);
+      T acc = xl;
+      for (int jj = 0; jj < bs; ++jj) {
+        const T xj = xs[i0 + jj];
+        if (jj < lane) acc = fma(Dg[lane][jj], xj, acc);
       }
-      if (lane < bs) xs[i0 + lane] = xl;
+      __syncwarp();
+      if (lane < bs) xs[i0 + lane] = acc;
     }
     __syncthreads();
   }
@@ -403,14 +451,14 @@ __global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ L
       }
     }
     __syncthreads();
-    if (warp == 0) {
-      T xl = lane < bs ? xs[i0 + lane] : T(0);
-      for (int rr = bs - 1; rr >= 0; --rr) {
-        if (lane == rr) xl = xl / Dg[rr][rr];
-        const T xr = __shfl_sync(0xffffffffu, xl, rr);
-        if (lane < rr) xl = fma(-Dg[lane][rr], xr, xl);
+    if (warp == 0) {  // x_blk <- U_bb^-1 x_blk (upper inverse stored on and above the diagonal)
+      T acc = T(0);
+      for (int jj = 0; jj < bs; ++jj) {
+        const T xj = xs[i0 + jj];
+        if (jj >= lane) acc = fma(Dg[lane][jj], xj, acc);
       }
-      if (lane < bs) xs[i0 + lane] = xl;
+      __syncwarp();
+      if (lane < bs) xs[i0 + lane] = acc;
     }
     __syncthreads();
   }
@@ -472,8 +520,12 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See) {
       ProfScope ps(c, SCK_LU);
       k_lu<T><<<K, 256, smem, c->stream>>>(nb, See, (long long)nb * lds, lds, c->piv, c->d_status);
     }
-    count_launch(c);
+    count_launch(c, 2);
     k_piv_to_perm<<<cdiv(K, 128), 128, 0, c->stream>>>(nb, c->piv, c->rowperm, K);
+    const size_t dsm = (size_t)8 * 2 * 32 * 33 * sizeof(T);
+    err = cudaFuncSetAttribute(k_diag_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    if (err != cudaSuccess) return err;
+    k_diag_inv<T><<<K, 256, dsm, c->stream>>>(nb, See, (long long)nb * lds, lds);
   }
   return cudaGetLastError();
 }

@@ -265,6 +265,8 @@ struct sc_ctx {
   // mixed-precision arm: FP32 copies of the element blocks and FP32 condensation
   float *Aown32 = nullptr, *X32 = nullptr, *Ainv32 = nullptr, *Y32 = nullptr, *See32 = nullptr;
   float *Zf = nullptr, *Xbf = nullptr, *Uf = nullptr;  // FP32 vectors of the FP32 operator
+  double* Cross = nullptr;   // neighbour-coupling products of one pass, FP64 operator
+  float* Cross32 = nullptr;  // same, FP32 operator
   double* Dfull = nullptr;  // refinement correction
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};

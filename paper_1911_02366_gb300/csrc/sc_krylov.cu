@@ -103,6 +103,39 @@ __device__ __forceinline__ T cross_row(const Geo& G, int e, int j, int k, const 
   return s;
 }
 
+// Neighbour couplings of a set of rows, one thread per (element, row): rows are the
+// permuted positions [row0, row0 + nrows) of every element; out[e][r - row0] =
+// sum over the row's couplings of X * (cb x_b or ci v_i) of the neighbour.
+template <class T>
+__global__ void __launch_bounds__(256) k_cross_rows(Geo G, const T* __restrict__ X, const int* __restrict__ nbr,
+    const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm, int row0, int nrows,
+    const T* __restrict__ vb, T cb, const T* __restrict__ vi, T ci, T* __restrict__ out) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)G.K * nrows) return;
+  const int e = (int)(t / nrows), r = row0 + (int)(t % nrows);
+  const int j = __ldg(iperm + r / 5), k = r % 5;
+  const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
+  const T* Xr = X + (((size_t)e * 5 + k) * G.NP + q0) * 5;
+  const int* nb_e = nbr + e * 18;
+  T s = T(0);
+  for (int q = q0; q < q1; ++q) {
+    const int info = __ldg(pinfo + q);
+    const int nb = __ldg(nb_e + pinfo_slot(info));
+    const int off = pinfo_offset(info);
+    const T* vec;
+    T coef;
+    if (pinfo_interior(info)) { vec = vi ? vi + (size_t)nb * G.ni + off : nullptr; coef = ci; }
+    else { vec = vb ? vb + (size_t)nb * G.nb + off : nullptr; coef = cb; }
+    if (!vec) continue;
+    const T* xq = Xr + (q - q0) * 5;
+    T a = T(0);
+#pragma unroll
+    for (int l = 0; l < 5; ++l) a = fma(__ldg(xq + l), vec[l], a);
+    s = fma(coef, a, s);
+  }
+  out[t] = s;
+}
+
 // Interior pass: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e).  Matrices and the
 // vectors x_b, u in precision T; the full right-hand side B in double.
 template <class T>
@@ -110,7 +143,7 @@ __global__ void __launch_bounds__(256) k_cond_interior(Geo G, const T* __restric
     const T* __restrict__ X, const T* __restrict__ Ainv, const int* __restrict__ nbr,
     const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm,
     const T* __restrict__ xb, double beta, const double* __restrict__ Bfull, double alpha,
-    T* __restrict__ u) {
+    T* __restrict__ u, const T* __restrict__ cross) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = blockIdx.x, ni = G.ni, nb = G.nb;
   T* v = reinterpret_cast<T*>(smem_raw);  // nb: x_e
@@ -128,8 +161,9 @@ __global__ void __launch_bounds__(256) k_cond_interior(Geo G, const T* __restric
     T s = T(0);
     if (xb) {
       s = warp_dot(Ae + (size_t)ri * G.lda + G.cb0, v, nb, lane);
-      s += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, T(1), (const T*)nullptr, T(0), lane);
+      if (!cross) s += cross_row(G, e, j, k, X, nbr_s, pptr, pinfo, xb, T(1), (const T*)nullptr, T(0), lane);
       s = warp_sum(s);
+      if (cross) s += cross[(size_t)e * ni + ri];
     }
     if (lane == 0) {
       T val = T(beta) * s;
@@ -158,7 +192,7 @@ __global__ void __launch_bounds__(256) k_cond_boundary(Geo G, const T* __restric
     const T* __restrict__ X, const int* __restrict__ nbr,
     const int* __restrict__ pptr, const int* __restrict__ pinfo, const int* __restrict__ iperm,
     const T* __restrict__ xb, double delta, const double* __restrict__ Bfull, double gamma_,
-    const T* __restrict__ u, double* __restrict__ y) {
+    const T* __restrict__ u, double* __restrict__ y, const T* __restrict__ cross) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = blockIdx.x, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, cb0 = G.cb0;
   T* v = reinterpret_cast<T*>(smem_raw);  // lda: [-u_e | 0 | delta x_e | 0] in own-column order
@@ -180,9 +214,12 @@ __global__ void __launch_bounds__(256) k_cond_boundary(Geo G, const T* __restric
     const int rb2 = ra + 1 < ne ? ra + 1 : ra;
     T sa = T(0), sb = T(0);
     if (xb || u) warp_dot2(Ae + (size_t)ra * lda + c0, Ae + (size_t)rb2 * lda + c0, v + c0, len, lane, sa, sb);
-    sa += cross_row(G, e, __ldg(iperm + ra / 5), ra % 5, X, nbr_s, pptr, pinfo, xb, dT, u, T(-1), lane);
-    sb += cross_row(G, e, __ldg(iperm + rb2 / 5), rb2 % 5, X, nbr_s, pptr, pinfo, xb, dT, u, T(-1), lane);
+    if (!cross) {
+      sa += cross_row(G, e, __ldg(iperm + ra / 5), ra % 5, X, nbr_s, pptr, pinfo, xb, dT, u, T(-1), lane);
+      sb += cross_row(G, e, __ldg(iperm + rb2 / 5), rb2 % 5, X, nbr_s, pptr, pinfo, xb, dT, u, T(-1), lane);
+    }
     sa = warp_sum(sa); sb = warp_sum(sb);
+    if (cross) { sa += cross[(size_t)e * nb + ra - ni]; sb += cross[(size_t)e * nb + rb2 - ni]; }
     if (lane == 0) {
       double va = (double)sa, vb = (double)sb;
       if (Bfull) {
@@ -310,44 +347,59 @@ constexpr int kDotChunks = 152;
 
 namespace sc {
 
-cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double* Bfull, double alpha, double* u) {
+template <class T>
+cudaError_t cond_interior_t(sc_ctx* c, const T* Aown, const T* X, const T* Ainv, T* crossbuf, const T* xb,
+                            double beta, const double* Bfull, double alpha, T* u) {
   const Geo& G = c->G;
   if (G.ni == 0) return cudaSuccess;
+  if (xb) {
+    count_launch(c);
+    const size_t rows = (size_t)G.K * G.ni;
+    k_cross_rows<T><<<(unsigned)((rows + 255) / 256), 256, 0, c->stream>>>(G, X, c->d_nbr, c->d_pptr, c->d_pinfo,
+        c->d_iperm, 0, G.ni, xb, T(1), (const T*)nullptr, T(0), crossbuf);
+  }
   ProfScope ps(c, SCK_COND_INTERIOR);
-  const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double);
-  k_cond_interior<double><<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo,
-                                                         c->d_iperm, xb, beta, Bfull, alpha, u);
+  const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(T);
+  k_cond_interior<T><<<G.K, 256, smem, c->stream>>>(G, Aown, X, Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm,
+                                                    xb, beta, Bfull, alpha, u, xb ? crossbuf : (const T*)nullptr);
   return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t cond_boundary_t(sc_ctx* c, const T* Aown, const T* X, T* crossbuf, const T* xb, double delta,
+                            const double* Bfull, double gamma_, const T* u, double* y) {
+  const Geo& G = c->G;
+  if (G.ni == 0) u = nullptr;
+  const bool need = xb || u;
+  if (need) {
+    count_launch(c);
+    const size_t rows = (size_t)G.K * G.nb;
+    k_cross_rows<T><<<(unsigned)((rows + 255) / 256), 256, 0, c->stream>>>(G, X, c->d_nbr, c->d_pptr, c->d_pinfo,
+        c->d_iperm, G.ni, G.nb, xb, T(delta), u, T(-1), crossbuf);
+  }
+  ProfScope ps(c, SCK_COND_BOUNDARY);
+  const size_t smem = (size_t)G.lda * sizeof(T);
+  k_cond_boundary<T><<<G.K, 256, smem, c->stream>>>(G, Aown, X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb,
+                                                    delta, Bfull, gamma_, u, y, need ? crossbuf : (const T*)nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double* Bfull, double alpha, double* u) {
+  return cond_interior_t<double>(c, c->Aown, c->X, c->Ainv, c->Cross, xb, beta, Bfull, alpha, u);
 }
 
 cudaError_t cond_boundary(sc_ctx* c, const double* xb, double delta, const double* Bfull, double gamma_,
                           const double* u, double* y) {
-  const Geo& G = c->G;
-  ProfScope ps(c, SCK_COND_BOUNDARY);
-  const size_t smem = (size_t)G.lda * sizeof(double);
-  k_cond_boundary<double><<<G.K, 256, smem, c->stream>>>(G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo,
-                                                         c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
-  return cudaGetLastError();
+  return cond_boundary_t<double>(c, c->Aown, c->X, c->Cross, xb, delta, Bfull, gamma_, u, y);
 }
 
 cudaError_t cond_interior32(sc_ctx* c, const float* xb, double beta, const double* Bfull, double alpha, float* u) {
-  const Geo& G = c->G;
-  if (G.ni == 0) return cudaSuccess;
-  ProfScope ps(c, SCK_COND_INTERIOR);
-  const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(float);
-  k_cond_interior<float><<<G.K, 256, smem, c->stream>>>(G, c->Aown32, c->X32, c->Ainv32, c->d_nbr, c->d_pptr,
-                                                        c->d_pinfo, c->d_iperm, xb, beta, Bfull, alpha, u);
-  return cudaGetLastError();
+  return cond_interior_t<float>(c, c->Aown32, c->X32, c->Ainv32, c->Cross32, xb, beta, Bfull, alpha, u);
 }
 
 cudaError_t cond_boundary32(sc_ctx* c, const float* xb, double delta, const double* Bfull, double gamma_,
                             const float* u, double* y) {
-  const Geo& G = c->G;
-  ProfScope ps(c, SCK_COND_BOUNDARY);
-  const size_t smem = (size_t)G.lda * sizeof(float);
-  k_cond_boundary<float><<<G.K, 256, smem, c->stream>>>(G, c->Aown32, c->X32, c->d_nbr, c->d_pptr, c->d_pinfo,
-                                                        c->d_iperm, xb, delta, Bfull, gamma_, G.ni ? u : nullptr, y);
-  return cudaGetLastError();
+  return cond_boundary_t<float>(c, c->Aown32, c->X32, c->Cross32, xb, delta, Bfull, gamma_, u, y);
 }
 
 cudaError_t global_apply(sc_ctx* c, const double* x, double* y) {
@@ -480,12 +532,13 @@ extern "C" sc_status sc_condensed_matvec_static(sc_ctx* c, const double* xb, dou
   if (G.ni > 0) {
     count_launch(c);
     k_cond_interior<double><<<G.K, 256, (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double), c->stream>>>(
-        G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u);
+        G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u,
+        nullptr);
   }
   count_launch(c);
   k_cond_boundary<double><<<G.K, 256, (size_t)G.lda * sizeof(double), c->stream>>>(
       G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
-      G.ni ? u : nullptr, yb);
+      G.ni ? u : nullptr, yb, nullptr);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
