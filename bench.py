@@ -149,7 +149,7 @@ def run_ours(args, world, rank, local):
         step()
     torch.cuda.synchronize()
 
-    dominant = sc.SC_KERNEL_LU_SOLVE if args.arm == "fp64" else sc.SC_KERNEL_COND_BOUNDARY
+    dominant = sc.SC_KERNEL_LU_SOLVE
     ctx.sc_profile_kernel(dominant)
     sampler = ClockSampler(local) if rank == 0 else None
     l0 = ctx.sc_launch_count()
@@ -230,11 +230,11 @@ def run_ours(args, world, rank, local):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# captures summarised in profiles/, scaled to the 16^3 mesh; None once a kernel changes.
+# captures summarised in profiles/, taken on the 8^3-element case and scaled x8 to the
+# 16^3 mesh (traffic grows with the element count); None once a kernel has changed.
 TRAFFIC = {
+    ("mixed", 2): 8 * (568.105728e6 + 4.461568e6),  # k_lu_solve<float>, profiles/mixed_iteration_kernels_tgv_8x8x8_N4.md
     ("fp64", 2): None,
-    ("fp64", 1): None,
-    ("mixed", 1): None,
 }
 
 

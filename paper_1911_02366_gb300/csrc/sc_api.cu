@@ -693,43 +693,43 @@ sc_status sc_kernel_work(const sc_ctx* c, int kernel_id, double* flops, double* 
   if (!c || !flops || !bytes) return SC_ERR_ARG;
   if (!c->has_mesh) return SC_ERR_STATE;
   const Geo& G = c->G;
-  // neighbour couplings per element by row type
-  double pi = 0.0, pb = 0.0;
-  for (size_t q = 0; q < c->pat.row.size(); ++q) (c->perm[c->pat.row[q]] < G.nin ? pi : pb) += 1.0;
-  const double K = G.K, ni = G.ni, nb = G.nb, ne = G.ne, w = 8.0;
+  // matrices of the condensed solve are stored in FP32 by the mixed arm
+  const double w = c->cfg.precision == SC_PREC_MIXED ? 4.0 : 8.0;
+  double pairs = (double)c->pat.row.size();
+  const double K = G.K, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, ldi = G.ldi, lds = G.lds, cb0 = G.cb0;
   double f = 0.0, b = 0.0;
   switch (kernel_id) {
-    case SCK_COND_INTERIOR:  // A_ib,ee x_b + neighbour couplings, then A_ii^-1 t
-      f = K * (2.0 * ni * nb + 2.0 * 25.0 * pi + 2.0 * ni * ni);
-      b = K * w * (ni * nb + 25.0 * pi + ni * ni + nb + ni);
+    case SCK_COND_INTERIOR:  // A_ib,ee x_b, then A_ii^-1 t (dense part; couplings run in their own pass)
+      f = K * (2.0 * ni * nb + 2.0 * ni * ni);
+      b = K * (w * (ni * nb + ni * ldi) + w * nb + 8.0 * ni);
       break;
-    case SCK_COND_BOUNDARY:  // [A_bi A_bb] [-u; x_b] + neighbour couplings
-      f = K * (2.0 * nb * ne + 2.0 * 25.0 * pb);
-      b = K * w * (nb * ne + 25.0 * pb + ne + nb);
+    case SCK_COND_BOUNDARY:  // [A_bi A_bb] [-u; x_b] (dense part)
+      f = K * 2.0 * nb * ne;
+      b = K * (w * nb * (cb0 + nb) + w * (ni + nb) + 8.0 * nb);
       break;
     case SCK_LU_SOLVE:  // forward + backward substitution with the S_ee factors
       f = K * 2.0 * nb * nb;
-      b = K * w * (nb * nb + 2.0 * nb);
+      b = K * (w * nb * lds + 4.0 * nb + 8.0 * 2.0 * nb);
       break;
     case SCK_LU:
       f = K * (2.0 / 3.0) * nb * nb * nb;
-      b = K * w * 2.0 * nb * nb;
+      b = K * w * 2.0 * nb * lds;
       break;
     case SCK_GEMM:  // S_ee -= A_bi,ee Y
       f = K * 2.0 * nb * nb * ni;
-      b = K * w * (nb * ni + ni * nb + 2.0 * nb * nb);
+      b = K * w * (nb * ni + ni * nb + 2.0 * nb * lds);
       break;
     case SCK_GJ_INV:
       f = K * 2.0 * ni * ni * ni;
-      b = K * w * 2.0 * ni * ni;
+      b = K * w * (ni * lda + ni * ldi);
       break;
     case SCK_ASM_OWN:
       f = 0.0;
-      b = K * w * ne * ne;
+      b = K * 8.0 * ne * lda;
       break;
-    case SCK_GLOBAL_APPLY:
-      f = K * (2.0 * ne * ne + 2.0 * 25.0 * (pi + pb));
-      b = K * w * (ne * ne + 25.0 * (pi + pb) + 2.0 * ne);
+    case SCK_GLOBAL_APPLY:  // always FP64
+      f = K * (2.0 * ne * ne + 2.0 * 25.0 * pairs);
+      b = K * 8.0 * (ne * lda + 25.0 * pairs + 2.0 * ne);
       break;
     default:
       return SC_ERR_ARG;
