@@ -158,6 +158,17 @@ sc_status sc_condensed_matvec_static(sc_ctx* ctx, const double* xb, double* yb);
 /* Sizes: number of elements, dofs per element, interior and boundary dofs per element. */
 sc_status sc_sizes(const sc_ctx* ctx, int* K, int* ne, int* ni, int* nb);
 
+/* Batched C = alpha A B + beta C on the TF32 tensor cores (tcgen05, FP32 accumulation):
+   `batch` independent row-major FP32 problems, A: M x K (leading dimension lda >= K),
+   B: K x N (ldb >= N), C: M x N (ldc >= N), consecutive problems strideA / strideB /
+   strideC elements apart.  The building block of the mixed arm's element Schur
+   products (Sec. 3.2, matrix-matrix multiplications), exposed for testing.  Device
+   pointers; enqueued on cuda_stream and synchronised before return.  batch <= 65535.
+   Returns SC_ERR_CUDA if a tensor-core wait timed out. */
+sc_status sc_gemm_tf32(int batch, int M, int N, int K, float alpha, const float* A, long long strideA, int lda,
+                       const float* B, long long strideB, int ldb, float beta, float* C, long long strideC, int ldc,
+                       void* cuda_stream);
+
 /* ---- Measurement hooks (not part of the method; used by the benchmark) ---------- */
 
 /* Kernel ids for sc_profile_kernel / sc_kernel_work. */

@@ -328,10 +328,6 @@ __global__ void k_piv_to_perm(int n, const int* __restrict__ piv_all, int* __res
   }
 }
 
-__device__ __forceinline__ double warp_sum_d(double s) {
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
-}
 
 template <class T> struct V16;
 template <> struct V16<double> { using type = double2; static constexpr int n = 2; };

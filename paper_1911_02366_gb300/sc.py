@@ -50,7 +50,7 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_set_state", "sc_set_timestep", "sc_assemble", "sc_condense", "sc_solve", "sc_get_rhs",
            "sc_apply_jacobian", "sc_get_jacobian_block", "sc_condensed_matvec", "sc_sizes",
            "sc_launch_count", "sc_profile_kernel", "sc_profile_read", "sc_kernel_work",
-           "sc_condensed_matvec_static"]
+           "sc_condensed_matvec_static", "sc_gemm_tf32"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -87,6 +87,8 @@ def lib(build_if_missing: bool = True):
     L.sc_get_jacobian_block.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
     L.sc_condensed_matvec.argtypes = [vp, dp, dp]
     L.sc_condensed_matvec_static.argtypes = [vp, dp, dp]
+    ll, fl, ci = ctypes.c_longlong, ctypes.c_float, ctypes.c_int
+    L.sc_gemm_tf32.argtypes = [ci, ci, ci, ci, fl, vp, ll, ci, vp, ll, ci, fl, vp, ll, ci, vp]
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
@@ -239,3 +241,19 @@ class Context:
             raise ValueError("condensed_matvec_static takes device tensors")
         self._check(self._L.sc_condensed_matvec_static(self.h, px, py))
         return yb
+
+
+def sc_gemm_tf32(A, B, C, alpha=1.0, beta=0.0, stream=None):
+    """C[b] = alpha A[b] @ B[b] + beta C[b] on the TF32 tensor cores (float32 CUDA tensors,
+    shapes [batch, M, K], [batch, K, N], [batch, M, N], contiguous)."""
+    L = lib()
+    bt, M, K = A.shape
+    N = B.shape[2]
+    for t in (A, B, C):
+        if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"):
+            raise ValueError("contiguous float32 CUDA tensors required")
+    s = L.sc_gemm_tf32(bt, M, N, K, alpha, A.data_ptr(), M * K, K, B.data_ptr(), K * N, N, beta, C.data_ptr(),
+                       M * N, N, ctypes.c_void_p(stream or 0))
+    if s != SC_OK:
+        raise SCError(s, "sc_gemm_tf32 failed")
+    return C

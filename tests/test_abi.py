@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "sc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sc_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sc_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_pipeline():
@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol():
     from paper_1911_02366_gb300 import build
     lib = build.build()
     out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\sT\s(sc_[a-z_]+)", out))
+    exported = set(re.findall(r"\sT\s(sc_[a-z0-9_]+)", out))
     missing = [f for f in declared_functions() if f not in exported]
     assert not missing, missing
 
