@@ -128,7 +128,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
-                     inner_tol=args.inner_tol, max_refine=20)
+                     inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores)
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
     ctx.sc_set_timestep(dt, 1)
     Qd = torch.tensor(Q.reshape(-1), device="cuda")
@@ -213,6 +213,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": W["name"], "elements": W["n"] ** 3, "order": W["N"], "dof": dofs, "cfl": W["cfl"],
                    "Ma": W["Ma"], "Re": W["Re"], "arm": args.arm, "gmres_restart": args.restart,
                    "inner_tol": args.inner_tol if args.arm == "mixed" else None,
+                   "tensor_cores": bool(args.tensor_cores) if args.arm == "mixed" else False,
                    "l2": "inputs larger than L2 (element blocks 12.9 GB)", "parallelism": f"replicas x{world}"},
         "linear_solve_dof_per_s": world * dofs * args.steps / (gather_max(world, solve_ms) * 1e-3),
         "assemble_ms_per_step": assemble_ms / args.steps,
@@ -288,6 +289,8 @@ def main():
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=1,
+                    help="mixed arm: TF32 tcgen05 Schur products and LU trailing updates (1) or FP32 CUDA cores (0)")
     ap.add_argument("--n", type=int, default=None, help="elements per direction (profiling runs)")
     ap.add_argument("--order", type=int, default=None, help="polynomial order (profiling runs)")
     ap.add_argument("--allow-unconverged", action="store_true", help="profiling runs with capped iterations")

@@ -64,6 +64,8 @@ typedef struct {
   int max_refine;        /* mixed arm: cap on FP64 refinement sweeps */
   double rel_tol;        /* target ||B - A dQ||_2 / ||B||_2 on the global system (1e-8) */
   double inner_tol;      /* mixed arm: relative tolerance of each inner condensed solve */
+  int tensor_cores;      /* mixed arm: 1 = element Schur products and the LU trailing updates
+                            of S_ee on the TF32 tensor cores (tcgen05), 0 = FP32 CUDA cores */
 } sc_config;
 
 /* Per-solve statistics filled by sc_solve. */
@@ -77,7 +79,7 @@ typedef struct {
 } sc_solve_stats;
 
 /* Fill *cfg with the defaults listed above (Re = 1600, Ma = 0.1, FP64, block Jacobi,
-   GMRES(30), 4000 iterations, rel_tol 1e-8).  Never fails for a non-null cfg. */
+   GMRES(30), 4000 iterations, rel_tol 1e-8, tensor_cores 1).  Never fails for a non-null cfg. */
 sc_status sc_default_config(sc_config* cfg);
 
 /* Create a context that enqueues all work on `cuda_stream` (a cudaStream_t, or NULL
@@ -158,16 +160,19 @@ sc_status sc_condensed_matvec_static(sc_ctx* ctx, const double* xb, double* yb);
 /* Sizes: number of elements, dofs per element, interior and boundary dofs per element. */
 sc_status sc_sizes(const sc_ctx* ctx, int* K, int* ne, int* ni, int* nb);
 
-/* Batched C = alpha A B + beta C on the TF32 tensor cores (tcgen05, FP32 accumulation):
-   `batch` independent row-major FP32 problems, A: M x K (leading dimension lda >= K),
-   B: K x N (ldb >= N), C: M x N (ldc >= N), consecutive problems strideA / strideB /
-   strideC elements apart.  The building block of the mixed arm's element Schur
-   products (Sec. 3.2, matrix-matrix multiplications), exposed for testing.  Device
-   pointers; enqueued on cuda_stream and synchronised before return.  batch <= 65535.
-   Returns SC_ERR_CUDA if a tensor-core wait timed out. */
+/* Batched C = alpha op(A) op(B) + beta C on the TF32 tensor cores (tcgen05, FP32
+   accumulation) for `batch` independent row-major FP32 problems; consecutive problems
+   are strideA / strideB / strideC elements apart.  op(A) is M x K: A is stored M x K
+   (lda >= K) if transA == 0, else K x M (lda >= M).  op(B) is K x N: B is stored K x N
+   (ldb >= N) if transB == 0, else N x K (ldb >= K).  C is M x N (ldc >= N).  The
+   building block of the mixed arm's element Schur products and of the trailing
+   updates of its blocked LU (Sec. 3.2, matrix-matrix multiplications), exposed for
+   testing.  Device pointers; enqueued on cuda_stream and synchronised before return.
+   batch <= 65535.  Returns SC_ERR_ARG for bad sizes and SC_ERR_CUDA if a launch failed
+   or a tensor-core wait timed out. */
 sc_status sc_gemm_tf32(int batch, int M, int N, int K, float alpha, const float* A, long long strideA, int lda,
-                       const float* B, long long strideB, int ldb, float beta, float* C, long long strideC, int ldc,
-                       void* cuda_stream);
+                       int transA, const float* B, long long strideB, int ldb, int transB, float beta, float* C,
+                       long long strideC, int ldc, void* cuda_stream);
 
 /* ---- Measurement hooks (not part of the method; used by the benchmark) ---------- */
 

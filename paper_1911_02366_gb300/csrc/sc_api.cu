@@ -184,7 +184,7 @@ sc_status sc_default_config(sc_config* cfg) {
   cfg->Ts = 110.4 / 288.15; cfg->sutherland = 1; cfg->roe_delta = 0.05;
   cfg->precision = SC_PREC_FP64; cfg->precond = SC_PC_BLOCK_JACOBI;
   cfg->gmres_restart = 30; cfg->gmres_max_iters = 4000; cfg->max_refine = 10;
-  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4;
+  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4; cfg->tensor_cores = 1;
   return SC_OK;
 }
 
@@ -281,7 +281,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->Aown, (size_t)G.K * own_stride(G))); A(dalloc(&c->X, (size_t)G.K * G.NP * 25));
   if (c->cfg.precision == SC_PREC_MIXED) {
     A(dalloc(&c->Aown32, (size_t)G.K * own_stride(G))); A(dalloc(&c->X32, (size_t)G.K * G.NP * 25));
-    A(dalloc(&c->Ainv32, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Y32, (size_t)G.K * G.ni * G.nb));
+    A(dalloc(&c->Ainv32, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Y32, (size_t)G.K * G.nb * G.ldi));  // Y^T (nb x ldi) on the tensor-core path
     A(dalloc(&c->See32, (size_t)G.K * G.nb * G.lds)); A(dalloc(&c->Dfull, dofs));
     A(dalloc(&c->Zf, n1)); A(dalloc(&c->Xbf, n1)); A(dalloc(&c->Uf, (size_t)G.K * G.ni));
     A(dalloc(&c->Cross32, n1 + (size_t)G.K * G.ni));
@@ -397,6 +397,7 @@ sc_status sc_condense(sc_ctx* c) {
   SC_CUDA(cudaMemcpyAsync(&bad, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
   if (s != SC_OK) return s;
+  if (bad == SC_TC_TIMEOUT) return fail(c, SC_ERR_CUDA, "tensor-core wait timed out in the condensation");
   if (bad >= 0) return fail(c, SC_ERR_SINGULAR_BLOCK, "singular element block in element " + std::to_string(bad));
   c->condensed = true;
   return SC_OK;

@@ -10,6 +10,8 @@
 //               in global memory (32-column panels factorised in shared memory).
 //   k_lu_solve  z = (P^T L U)^-1 v for every element (one CTA per element, 32-row
 //               panels with a warp-shuffle solve of each diagonal triangle).
+#include <type_traits>
+
 #include "sc_internal.cuh"
 
 namespace {
@@ -164,6 +166,83 @@ __global__ void k_copy_block(int rows, int cols, const T* __restrict__ src, long
 
 constexpr int PW = 32;  // LU panel width
 
+// One panel step of the right-looking LU with partial pivoting (rows first index of the
+// largest |a|): factor columns k0 .. k0+bw-1 of rows k0 .. n-1 in shared memory, apply
+// the panel's row interchanges to the columns outside it, and form U12 = L11^-1 A12.
+// P: shared panel buffer [n][PW+1].  Returns with all threads synchronised.
+template <class T>
+__device__ void lu_panel(int n, int k0, T* __restrict__ Mx, int lda, int* __restrict__ piv, T* P, int* s_p,
+                         int* s_bad) {
+  constexpr int pld = PW + 1;
+  const int bw = min(PW, n - k0), rows = n - k0;
+  for (int t = threadIdx.x; t < rows * bw; t += blockDim.x) {
+    const int i = t / bw, c = t % bw;
+    P[i * pld + c] = Mx[(long long)(k0 + i) * lda + k0 + c];
+  }
+  __syncthreads();
+  for (int c = 0; c < bw; ++c) {
+    if (threadIdx.x < 32) {
+      double best = -1.0; int bi = c;
+      for (int i = c + threadIdx.x; i < rows; i += 32) {
+        const double v = (double)tabs(P[i * pld + c]);
+        if (v > best) { best = v; bi = i; }
+      }
+      warp_argmax(best, bi);
+      if (threadIdx.x == 0) {
+        *s_p = bi;
+        piv[k0 + c] = k0 + bi;
+        if (!(best > 0.0)) *s_bad = 1;
+      }
+    }
+    __syncthreads();
+    const int pr = *s_p;
+    if (pr != c)
+      for (int j = threadIdx.x; j < bw; j += blockDim.x) {
+        T t = P[c * pld + j]; P[c * pld + j] = P[pr * pld + j]; P[pr * pld + j] = t;
+      }
+    __syncthreads();
+    const T d = P[c * pld + c];
+    const T dinv = (d == T(0)) ? T(0) : T(1) / d;
+    for (int i = c + 1 + threadIdx.x; i < rows; i += blockDim.x) P[i * pld + c] *= dinv;
+    __syncthreads();
+    const int w = bw - c - 1;
+    if (w > 0)
+      for (int t = threadIdx.x; t < (rows - c - 1) * w; t += blockDim.x) {
+        const int i = c + 1 + t / w, j = c + 1 + t % w;
+        P[i * pld + j] -= P[i * pld + c] * P[c * pld + j];
+      }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < rows * bw; t += blockDim.x) {
+    const int i = t / bw, c = t % bw;
+    Mx[(long long)(k0 + i) * lda + k0 + c] = P[i * pld + c];
+  }
+  // row interchanges of this panel applied to the columns outside it
+  for (int c = 0; c < bw; ++c) {
+    const int r1 = k0 + c, r2 = piv[k0 + c];
+    if (r2 != r1)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        if (j >= k0 && j < k0 + bw) continue;
+        T t = Mx[(long long)r1 * lda + j]; Mx[(long long)r1 * lda + j] = Mx[(long long)r2 * lda + j];
+        Mx[(long long)r2 * lda + j] = t;
+      }
+    __syncthreads();
+  }
+  if (n - k0 - bw > 0) {
+    // U12 = L11^-1 A12, one column per thread
+    for (int j = k0 + bw + threadIdx.x; j < n; j += blockDim.x) {
+      T col[PW];
+      for (int c = 0; c < bw; ++c) col[c] = Mx[(long long)(k0 + c) * lda + j];
+      for (int c = 0; c < bw; ++c)
+        for (int i = c + 1; i < bw; ++i) col[i] -= P[i * pld + c] * col[c];
+      for (int c = 0; c < bw; ++c) Mx[(long long)(k0 + c) * lda + j] = col[c];
+    }
+  }
+  __syncthreads();
+}
+
+// Whole LU of one element block per CTA: panel steps with the trailing update
+// A22 -= L21 U12 done by the same CTA in 4 x 4 register tiles.
 template <class T>
 __global__ void __launch_bounds__(256) k_lu(int n, T* __restrict__ A, long long stride, int lda,
                                             int* __restrict__ piv_all, int* __restrict__ status) {
@@ -176,72 +255,11 @@ __global__ void __launch_bounds__(256) k_lu(int n, T* __restrict__ A, long long 
   T* Mx = A + (long long)e * stride;
   int* piv = piv_all + (long long)e * n;
   if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
   for (int k0 = 0; k0 < n; k0 += PW) {
-    const int bw = min(PW, n - k0), rows = n - k0;
-    for (int t = threadIdx.x; t < rows * bw; t += blockDim.x) {
-      const int i = t / bw, c = t % bw;
-      P[i * pld + c] = Mx[(long long)(k0 + i) * lda + k0 + c];
-    }
-    __syncthreads();
-    for (int c = 0; c < bw; ++c) {
-      if (threadIdx.x < 32) {
-        double best = -1.0; int bi = c;
-        for (int i = c + threadIdx.x; i < rows; i += 32) {
-          const double v = (double)tabs(P[i * pld + c]);
-          if (v > best) { best = v; bi = i; }
-        }
-        warp_argmax(best, bi);
-        if (threadIdx.x == 0) {
-          s_p = bi;
-          piv[k0 + c] = k0 + bi;
-          if (!(best > 0.0)) s_bad = 1;
-        }
-      }
-      __syncthreads();
-      const int pr = s_p;
-      if (pr != c)
-        for (int j = threadIdx.x; j < bw; j += blockDim.x) {
-          T t = P[c * pld + j]; P[c * pld + j] = P[pr * pld + j]; P[pr * pld + j] = t;
-        }
-      __syncthreads();
-      const T d = P[c * pld + c];
-      const T dinv = (d == T(0)) ? T(0) : T(1) / d;
-      for (int i = c + 1 + threadIdx.x; i < rows; i += blockDim.x) P[i * pld + c] *= dinv;
-      __syncthreads();
-      const int w = bw - c - 1;
-      if (w > 0)
-        for (int t = threadIdx.x; t < (rows - c - 1) * w; t += blockDim.x) {
-          const int i = c + 1 + t / w, j = c + 1 + t % w;
-          P[i * pld + j] -= P[i * pld + c] * P[c * pld + j];
-        }
-      __syncthreads();
-    }
-    for (int t = threadIdx.x; t < rows * bw; t += blockDim.x) {
-      const int i = t / bw, c = t % bw;
-      Mx[(long long)(k0 + i) * lda + k0 + c] = P[i * pld + c];
-    }
-    // row interchanges of this panel applied to the columns outside it
-    for (int c = 0; c < bw; ++c) {
-      const int r1 = k0 + c, r2 = piv[k0 + c];
-      if (r2 != r1)
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-          if (j >= k0 && j < k0 + bw) continue;
-          T t = Mx[(long long)r1 * lda + j]; Mx[(long long)r1 * lda + j] = Mx[(long long)r2 * lda + j];
-          Mx[(long long)r2 * lda + j] = t;
-        }
-      __syncthreads();
-    }
-    const int rest = n - k0 - bw;
+    lu_panel<T>(n, k0, Mx, lda, piv, P, &s_p, &s_bad);
+    const int bw = min(PW, n - k0), rest = n - k0 - bw;
     if (rest > 0) {
-      // U12 = L11^-1 A12, one column per thread
-      for (int j = k0 + bw + threadIdx.x; j < n; j += blockDim.x) {
-        T col[PW];
-        for (int c = 0; c < bw; ++c) col[c] = Mx[(long long)(k0 + c) * lda + j];
-        for (int c = 0; c < bw; ++c)
-          for (int i = c + 1; i < bw; ++i) col[i] -= P[i * pld + c] * col[c];
-        for (int c = 0; c < bw; ++c) Mx[(long long)(k0 + c) * lda + j] = col[c];
-      }
-      __syncthreads();
       // A22 -= L21 U12, 4x4 register tiles
       const int tr = (rest + 3) / 4, tcn = (rest + 3) / 4;
       for (int t = threadIdx.x; t < tr * tcn; t += blockDim.x) {
@@ -266,6 +284,21 @@ __global__ void __launch_bounds__(256) k_lu(int n, T* __restrict__ A, long long 
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
+}
+
+// One panel step for every element (the trailing update is a separate batched GEMM).
+template <class T>
+__global__ void __launch_bounds__(256) k_lu_panel(int n, int k0, T* __restrict__ A, long long stride, int lda,
+                                                  int* __restrict__ piv_all, int* __restrict__ status) {
+  extern __shared__ unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  const int e = blockIdx.x;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  lu_panel<T>(n, k0, A + (long long)e * stride, lda, piv_all + (long long)e * n, P, &s_p, &s_bad);
   if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
 }
 
@@ -475,10 +508,37 @@ inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) /
 
 namespace sc {
 
-// Condensation set-up (FP64): A_ii^-1, Y = A_ii^-1 A_ib,ee, S_ee = A_bb,ee - A_bi,ee Y,
-// LU(S_ee).
+// Blocked LU of the S_ee blocks with the trailing updates A22 -= L21 U12 as batched TF32
+// tensor-core GEMMs (mixed arm): per panel one k_lu_panel launch and one GEMM.
+cudaError_t lu_blocked_tf32(sc_ctx* c, float* See) {
+  const Geo& G = c->G;
+  const int nb = G.nb, K = G.K, lds = G.lds;
+  const long long sS = (long long)nb * lds;
+  const size_t smem = (size_t)nb * (PW + 1) * sizeof(float);
+  cudaError_t err = cudaFuncSetAttribute(k_lu_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  ProfScope ps(c, SCK_LU);  // one measured span over all panels
+  for (int k0 = 0; k0 < nb; k0 += PW) {
+    const int bw = min(PW, nb - k0), rest = nb - k0 - bw;
+    if (k0 > 0) count_launch(c);
+    k_lu_panel<float><<<K, 256, smem, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
+    if (rest > 0) {
+      count_launch(c);
+      err = gemm_tf32(c->stream, rest, rest, bw, -1.0f, See + (size_t)(k0 + bw) * lds + k0, sS, lds, false,
+                      See + (size_t)k0 * lds + k0 + bw, sS, lds, false, 1.0f, See + (size_t)(k0 + bw) * lds + k0 + bw,
+                      sS, lds, K, c->d_status);
+      if (err != cudaSuccess) return err;
+    }
+  }
+  return cudaGetLastError();
+}
+
+// Condensation set-up: A_ii^-1 (Gauss-Jordan), Y = A_ii^-1 A_ib,ee, S_ee = A_bb,ee -
+// A_bi,ee Y and the LU of S_ee.  With `tc` (FP32 only) the two products and the LU's
+// trailing updates run on the TF32 tensor cores and Y is kept transposed (nb x ldi), the
+// K-major operand layout of the second product.
 template <class T>
-cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See) {
+cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
   const Geo& G = c->G;
   const int ni = G.ni, nb = G.nb, K = G.K, lda = G.lda, cb0 = G.cb0, ldi = G.ldi, lds = G.lds;
   const long long sA = (long long)own_stride(G);
@@ -491,11 +551,21 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See) {
     k_gj_inv<T><<<K, 256, smem, c->stream>>>(ni, Aown, sA, lda, Ainv, (long long)ni * ldi, ldi, c->d_status);
   }
   if (ni > 0) {
-    // Y = A_ii^-1 * A_ib,ee  (ni x nb)
     count_launch(c);
-    dim3 g1(cdiv(nb, 64), cdiv(ni, 64), K);
-    k_gemm<T><<<g1, 256, 0, c->stream>>>(ni, nb, ni, T(1), Ainv, (long long)ni * ldi, ldi, Aown + cb0, sA, lda, T(0),
-                                         Y, (long long)ni * nb, nb);
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc) {
+        // Y^T = A_ib,ee^T A_ii^-T  (nb x ni)
+        err = gemm_tf32(c->stream, nb, ni, ni, 1.0f, Aown + cb0, sA, lda, true, Ainv, (long long)ni * ldi, ldi, true,
+                        0.0f, Y, (long long)nb * ldi, ldi, K, c->d_status);
+        if (err != cudaSuccess) return err;
+      }
+    }
+    if (!tc) {
+      // Y = A_ii^-1 * A_ib,ee  (ni x nb)
+      dim3 g1(cdiv(nb, 64), cdiv(ni, 64), K);
+      k_gemm<T><<<g1, 256, 0, c->stream>>>(ni, nb, ni, T(1), Ainv, (long long)ni * ldi, ldi, Aown + cb0, sA, lda,
+                                           T(0), Y, (long long)ni * nb, nb);
+    }
   }
   // S_ee = A_bb,ee - A_bi,ee * Y
   count_launch(c);
@@ -504,15 +574,32 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See) {
                                              lds);
   if (ni > 0) {
     ProfScope ps(c, SCK_GEMM);
-    dim3 g2(cdiv(nb, 64), cdiv(nb, 64), K);
-    k_gemm<T><<<g2, 256, 0, c->stream>>>(nb, nb, ni, T(-1), Aown + (size_t)ni * lda, sA, lda, Y, (long long)ni * nb,
-                                         nb, T(1), See, (long long)nb * lds, lds);
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc) {
+        err = gemm_tf32(c->stream, nb, nb, ni, -1.0f, Aown + (size_t)ni * lda, sA, lda, false, Y, (long long)nb * ldi,
+                        ldi, true, 1.0f, See, (long long)nb * lds, lds, K, c->d_status);
+        if (err != cudaSuccess) return err;
+      }
+    }
+    if (!tc) {
+      dim3 g2(cdiv(nb, 64), cdiv(nb, 64), K);
+      k_gemm<T><<<g2, 256, 0, c->stream>>>(nb, nb, ni, T(-1), Aown + (size_t)ni * lda, sA, lda, Y,
+                                           (long long)ni * nb, nb, T(1), See, (long long)nb * lds, lds);
+    }
   }
   if (c->cfg.precond == SC_PC_BLOCK_JACOBI) {
-    const size_t smem = (size_t)nb * (PW + 1) * sizeof(T);
-    err = cudaFuncSetAttribute(k_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    {
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc) {
+        err = lu_blocked_tf32(c, See);
+        if (err != cudaSuccess) return err;
+        done = true;
+      }
+    }
+    if (!done) {
+      const size_t smem = (size_t)nb * (PW + 1) * sizeof(T);
+      err = cudaFuncSetAttribute(k_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
       ProfScope ps(c, SCK_LU);
       k_lu<T><<<K, 256, smem, c->stream>>>(nb, See, (long long)nb * lds, lds, c->piv, c->d_status);
     }
@@ -535,9 +622,9 @@ cudaError_t launch_condense(sc_ctx* c) {
     const size_t na = (size_t)G.K * own_stride(G), nx = (size_t)G.K * G.NP * 25;
     k_to_float<<<608, 256, 0, c->stream>>>(c->Aown, c->Aown32, na);
     k_to_float<<<608, 256, 0, c->stream>>>(c->X, c->X32, nx);
-    return condense_t<float>(c, c->Aown32, c->Ainv32, c->Y32, c->See32);
+    return condense_t<float>(c, c->Aown32, c->Ainv32, c->Y32, c->See32, c->cfg.tensor_cores != 0);
   }
-  return condense_t<double>(c, c->Aown, c->Ainv, c->Ytmp, c->See);
+  return condense_t<double>(c, c->Aown, c->Ainv, c->Ytmp, c->See, false);
 }
 
 cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {

@@ -305,6 +305,10 @@ struct ProfScope {
 inline void count_launch(sc_ctx* c, int n = 1) { c->launches += n; }
 
 // kernels launchers (defined in the .cu files)
+// Status word value written by a tensor-core kernel whose bounded wait ran out (element
+// indices written by the factorisations are far below it).
+constexpr int SC_TC_TIMEOUT = 1 << 30;
+
 namespace sc {
 cudaError_t launch_residual(sc_ctx* c);
 cudaError_t launch_assembly(sc_ctx* c);
@@ -327,5 +331,11 @@ cudaError_t vec_update(sc_ctx* c, double* w, const double* V, int nvec, size_t n
                        double sign);
 cudaError_t vec_scale_copy(sc_ctx* c, double* dst, const double* src, size_t n, const double* scal_dev,
                            int invert);
+// Batched TF32 tensor-core GEMM C = alpha op(A) op(B) + beta C (row-major FP32 blocks;
+// ta: A stored K x M, tb: B stored N x K).  A tensor-core wait that times out stores
+// SC_TC_TIMEOUT into *status if it still holds -1.
+cudaError_t gemm_tf32(cudaStream_t stream, int M, int N, int K, float alpha, const float* A, long long sA, int lda,
+                      bool ta, const float* B, long long sB, int ldb, bool tb, float beta, float* C, long long sC,
+                      int ldc, int batch, int* status);
 cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b, size_t n);
 }  // namespace sc

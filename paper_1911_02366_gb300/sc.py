@@ -32,7 +32,8 @@ class sc_config(ctypes.Structure):
                 ("Ma", ctypes.c_double), ("Ts", ctypes.c_double), ("sutherland", ctypes.c_int),
                 ("roe_delta", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("gmres_max_iters", ctypes.c_int),
-                ("max_refine", ctypes.c_int), ("rel_tol", ctypes.c_double), ("inner_tol", ctypes.c_double)]
+                ("max_refine", ctypes.c_int), ("rel_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("tensor_cores", ctypes.c_int)]
 
 
 class sc_solve_stats(ctypes.Structure):
@@ -88,7 +89,7 @@ def lib(build_if_missing: bool = True):
     L.sc_condensed_matvec.argtypes = [vp, dp, dp]
     L.sc_condensed_matvec_static.argtypes = [vp, dp, dp]
     ll, fl, ci = ctypes.c_longlong, ctypes.c_float, ctypes.c_int
-    L.sc_gemm_tf32.argtypes = [ci, ci, ci, ci, fl, vp, ll, ci, vp, ll, ci, fl, vp, ll, ci, vp]
+    L.sc_gemm_tf32.argtypes = [ci, ci, ci, ci, fl, vp, ll, ci, ci, vp, ll, ci, ci, fl, vp, ll, ci, vp]
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
@@ -243,17 +244,20 @@ class Context:
         return yb
 
 
-def sc_gemm_tf32(A, B, C, alpha=1.0, beta=0.0, stream=None):
-    """C[b] = alpha A[b] @ B[b] + beta C[b] on the TF32 tensor cores (float32 CUDA tensors,
-    shapes [batch, M, K], [batch, K, N], [batch, M, N], contiguous)."""
+def sc_gemm_tf32(A, B, C, alpha=1.0, beta=0.0, stream=None, trans_a=False, trans_b=False):
+    """C[b] = alpha op(A[b]) @ op(B[b]) + beta C[b] on the TF32 tensor cores.
+
+    float32 contiguous CUDA tensors: A is [batch, M, K] ([batch, K, M] with trans_a),
+    B is [batch, K, N] ([batch, N, K] with trans_b), C is [batch, M, N]."""
     L = lib()
-    bt, M, K = A.shape
-    N = B.shape[2]
     for t in (A, B, C):
         if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"):
             raise ValueError("contiguous float32 CUDA tensors required")
-    s = L.sc_gemm_tf32(bt, M, N, K, alpha, A.data_ptr(), M * K, K, B.data_ptr(), K * N, N, beta, C.data_ptr(),
-                       M * N, N, ctypes.c_void_p(stream or 0))
+    bt, M, N = C.shape
+    K = A.shape[1] if trans_a else A.shape[2]
+    s = L.sc_gemm_tf32(bt, M, N, K, alpha, A.data_ptr(), A.shape[1] * A.shape[2], A.shape[2], int(trans_a),
+                       B.data_ptr(), B.shape[1] * B.shape[2], B.shape[2], int(trans_b), beta, C.data_ptr(), M * N, N,
+                       ctypes.c_void_p(stream or 0))
     if s != SC_OK:
         raise SCError(s, "sc_gemm_tf32 failed")
     return C

@@ -107,12 +107,14 @@ def test_tgv_4x4x4_N3_cfl50_reaches_1e8():
     assert st["rel_residual"] < 1e-8
 
 
+@pytest.mark.parametrize("tc", [1, 0])
 @pytest.mark.parametrize("n,N,cfl", [(2, 3, 10.0), (3, 2, 10.0), (2, 4, 10.0)])
-def test_mixed_solve_matches_oracle_global_solve(n, N, cfl):
-    # FP32 condensation and condensed operator inside FP64 iterative refinement
+def test_mixed_solve_matches_oracle_global_solve(n, N, cfl, tc):
+    # FP32 condensation (TF32 tensor-core products and LU updates when tc) and FP32
+    # condensed operator inside FP64 iterative refinement
     from paper_1911_02366_gb300 import sc
     Q, dt, p, ctx = case(n, N, cfl=cfl, precision=sc.SC_PREC_MIXED, rel_tol=1e-12, inner_tol=1e-4,
-                         gmres_restart=60, gmres_max_iters=4000, max_refine=20)
+                         gmres_restart=60, gmres_max_iters=4000, max_refine=20, tensor_cores=tc)
     ctx.sc_set_state(Q, Q)
     ctx.sc_assemble()
     ctx.sc_condense()
@@ -140,3 +142,30 @@ def test_mixed_condensed_operator_is_fp32_close(n, N):
     ctx.sc_condensed_matvec(torch.tensor(xb, device="cuda"), yb)
     torch.cuda.synchronize()
     assert rel(yb.cpu().numpy(), S @ xb) < 1e-4
+
+
+@pytest.mark.parametrize("n,N", [(2, 4), (3, 3)])
+def test_tensor_core_preconditioner_keeps_iteration_count(n, N):
+    """The block-Jacobi factors from the TF32 products and blocked LU precondition as well
+    as the FP32 CUDA-core ones; a wrong factor would multiply the GMRES iterations (the
+    unpreconditioned solve shows by how much)."""
+    from paper_1911_02366_gb300 import sc
+    iters = {}
+    for key, tc, pc in (("fp32", 0, sc.SC_PC_BLOCK_JACOBI), ("tf32", 1, sc.SC_PC_BLOCK_JACOBI),
+                        ("none", 1, sc.SC_PC_NONE)):
+        Q, dt, p, ctx = case(n, N, cfl=10.0, precision=sc.SC_PREC_MIXED, rel_tol=1e-8, inner_tol=1e-4,
+                             gmres_restart=60, gmres_max_iters=4000, max_refine=20, tensor_cores=tc, precond=pc)
+        ctx.sc_set_state(Q, Q)
+        ctx.sc_assemble()
+        ctx.sc_condense()
+        dQ = np.zeros(Q.size)
+        try:
+            st = ctx.sc_solve(dQ)
+        except sc.SCError:
+            assert key == "none"  # the unpreconditioned solve may exhaust the iteration cap
+            iters[key] = 4000
+            continue
+        assert st["rel_residual"] < 1e-8
+        iters[key] = st["gmres_iters"]
+    assert iters["tf32"] <= 1.25 * iters["fp32"] + 3, iters
+    assert iters["none"] > 1.5 * iters["fp32"], iters
