@@ -90,14 +90,17 @@ void diff_matrix(const std::vector<double>& x, double D[SC_MAXP][SC_MAXP]) {
 void free_all(sc_ctx* c) {
   double** dps[] = {&c->Q, &c->Qh, &c->grad, &c->F, &c->B, &c->NJ, &c->RJ, &c->Aown, &c->X, &c->Ainv,
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
-                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross};
+                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
-  float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32};
+  float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
+                   &c->Apk32};
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
+  c->packed = false;
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
-                 &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status};
+                 &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
+                 &c->d_pk_row_off, &c->d_pk_pos};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
 }
 
@@ -268,6 +271,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
     }
   }
   build_pattern(c);
+  sc::build_packed_pattern(c);
   const size_t nodes = (size_t)G.K * G.nn, dofs = nodes * 5;
   const size_t n1 = (size_t)G.K * G.nb;
   const int m = c->cfg.gmres_restart;
@@ -300,6 +304,10 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   const int np = G.NP;
   A(dalloc(&c->d_prow, np)); A(dalloc(&c->d_pslot, np)); A(dalloc(&c->d_pcol, np));
   A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pinfo, np));
+  A(dalloc(&c->d_pk_lptr, c->pk_lptr.size())); A(dalloc(&c->d_pk_list, c->pk_list.size()));
+  A(dalloc(&c->d_pk_row_off, c->pk_row_off.size())); A(dalloc(&c->d_pk_pos, c->pk_pos.size()));
+  if (c->cfg.precision == SC_PREC_MIXED) A(dalloc(&c->Apk32, (size_t)G.K * c->pk_stride));
+  else A(dalloc(&c->Apk, (size_t)G.K * c->pk_stride));
   if (e != cudaSuccess) { free_all(c); cudaGetLastError(); return fail(c, SC_ERR_OOM, std::string("allocation: ") + cudaGetErrorString(e)); }
   SC_CUDA(cudaMemcpy(c->d_nbr, c->nbr.data(), c->nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_perm, c->perm.data(), G.nn * sizeof(int), cudaMemcpyHostToDevice));
@@ -319,7 +327,10 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
     pinfo[i] = (c->pat.slot[i] << 26) | (interior << 25) | off;
   }
   SC_CUDA(cudaMemcpy(c->d_pinfo, pinfo.data(), np * sizeof(int), cudaMemcpyHostToDevice));
-  // the alignment padding of the element blocks must read as zero
+  SC_CUDA(sc::upload_packed_pattern(c));
+  // the alignment padding of the element blocks (dense and packed) must read as zero
+  if (c->Apk) SC_CUDA(cudaMemset(c->Apk, 0, (size_t)G.K * c->pk_stride * sizeof(double)));
+  if (c->Apk32) SC_CUDA(cudaMemset(c->Apk32, 0, (size_t)G.K * c->pk_stride * sizeof(float)));
   SC_CUDA(cudaMemset(c->Aown, 0, (size_t)G.K * own_stride(G) * sizeof(double)));
   if (c->Ainv) SC_CUDA(cudaMemset(c->Ainv, 0, (size_t)G.K * G.ni * G.ldi * sizeof(double)));
   if (c->Ainv32) SC_CUDA(cudaMemset(c->Ainv32, 0, (size_t)G.K * G.ni * G.ldi * sizeof(float)));
@@ -383,7 +394,7 @@ sc_status sc_assemble(sc_ctx* c) {
   SC_CUDA(sc::launch_assembly(c));
   sc_status s = check(c);
   if (s != SC_OK) return s;
-  c->assembled = true; c->condensed = false;
+  c->assembled = true; c->condensed = false; c->packed = false;
   return SC_OK;
 }
 
@@ -398,6 +409,8 @@ sc_status sc_condense(sc_ctx* c) {
   sc_status s = check(c);
   if (s != SC_OK) return s;
   if (bad == SC_TC_TIMEOUT) return fail(c, SC_ERR_CUDA, "tensor-core wait timed out in the condensation");
+  if (bad == SC_PACK_VIOLATION)
+    return fail(c, SC_ERR_STATE, "own-block entry outside the packed node pattern is nonzero");
   if (bad >= 0) return fail(c, SC_ERR_SINGULAR_BLOCK, "singular element block in element " + std::to_string(bad));
   c->condensed = true;
   return SC_OK;
@@ -700,13 +713,13 @@ sc_status sc_kernel_work(const sc_ctx* c, int kernel_id, double* flops, double* 
   const double K = G.K, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, ldi = G.ldi, lds = G.lds, cb0 = G.cb0;
   double f = 0.0, b = 0.0;
   switch (kernel_id) {
-    case SCK_COND_INTERIOR:  // A_ib,ee x_b, then A_ii^-1 t (dense part; couplings run in their own pass)
-      f = K * (2.0 * ni * nb + 2.0 * ni * ni);
-      b = K * (w * (ni * nb + ni * ldi) + w * nb + 8.0 * ni);
+    case SCK_COND_INTERIOR:  // A_ib,ee x_b (structural nonzeros), then A_ii^-1 t; couplings run in their own pass
+      f = K * (2.0 * (double)c->pk_nnz_int + 2.0 * ni * ni);
+      b = K * (w * ((double)c->pk_nnz_int + ni * ldi) + w * nb + 8.0 * ni);
       break;
-    case SCK_COND_BOUNDARY:  // [A_bi A_bb] [-u; x_b] (dense part)
-      f = K * 2.0 * nb * ne;
-      b = K * (w * nb * (cb0 + nb) + w * (ni + nb) + 8.0 * nb);
+    case SCK_COND_BOUNDARY:  // [A_bi A_bb] [-u; x_b] (structural nonzeros)
+      f = K * 2.0 * (double)c->pk_nnz_bnd;
+      b = K * (w * (double)c->pk_nnz_bnd + w * (ni + nb) + 8.0 * nb);
       break;
     case SCK_LU_SOLVE:  // forward + backward substitution with the S_ee factors
       f = K * 2.0 * nb * nb;

@@ -617,6 +617,9 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
 // FP64 arm in place on the FP64 blocks, mixed arm on FP32 copies.
 cudaError_t launch_condense(sc_ctx* c) {
   const Geo& G = c->G;
+  cudaError_t pe = pack_own(c);
+  if (pe != cudaSuccess) return pe;
+  c->packed = true;
   if (c->cfg.precision == SC_PREC_MIXED) {
     count_launch(c, 2);
     const size_t na = (size_t)G.K * own_stride(G), nx = (size_t)G.K * G.NP * 25;

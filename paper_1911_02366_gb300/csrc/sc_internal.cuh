@@ -268,6 +268,13 @@ struct sc_ctx {
   double* Cross = nullptr;   // neighbour-coupling products of one pass, FP64 operator
   float* Cross32 = nullptr;  // same, FP32 operator
   double* Dfull = nullptr;  // refinement correction
+  // pattern-packed own blocks of the condensed operator (A_ib rows, [A_bi A_bb] rows)
+  std::vector<int> pk_lptr, pk_list, pk_pos, pk_row_off;
+  long long pk_stride = 0, pk_nnz_int = 0, pk_nnz_bnd = 0;
+  int *d_pk_lptr = nullptr, *d_pk_list = nullptr, *d_pk_row_off = nullptr, *d_pk_pos = nullptr;
+  double* Apk = nullptr;   // FP64 arm
+  float* Apk32 = nullptr;  // mixed arm
+  bool packed = false;     // packed blocks match the assembled Jacobian
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};
   // measurement hooks: kernel launches since creation, and optional CUDA-event timing
@@ -308,6 +315,9 @@ inline void count_launch(sc_ctx* c, int n = 1) { c->launches += n; }
 // Status word value written by a tensor-core kernel whose bounded wait ran out (element
 // indices written by the factorisations are far below it).
 constexpr int SC_TC_TIMEOUT = 1 << 30;
+// Status word value written by the packing kernel when an own-block entry outside the
+// packed pattern is nonzero.
+constexpr int SC_PACK_VIOLATION = (1 << 30) + 1;
 
 namespace sc {
 cudaError_t launch_residual(sc_ctx* c);
@@ -337,5 +347,14 @@ cudaError_t vec_scale_copy(sc_ctx* c, double* dst, const double* src, size_t n, 
 cudaError_t gemm_tf32(cudaStream_t stream, int M, int N, int K, float alpha, const float* A, long long sA, int lda,
                       bool ta, const float* B, long long sB, int ldb, bool tb, float beta, float* C, long long sC,
                       int ldc, int batch, int* status);
+void build_packed_pattern(sc_ctx* c);
+cudaError_t upload_packed_pattern(sc_ctx* c);
+cudaError_t pack_own(sc_ctx* c);
+template <class T>
+cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* Ainv, const T* cross, const T* xb, double beta,
+                             const double* Bfull, double alpha, T* u);
+template <class T>
+cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* cross, const T* xb, double delta, const double* Bfull,
+                             double gamma_, const T* u, double* y);
 cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b, size_t n);
 }  // namespace sc

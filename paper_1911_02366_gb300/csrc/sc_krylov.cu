@@ -348,8 +348,8 @@ constexpr int kDotChunks = 152;
 namespace sc {
 
 template <class T>
-cudaError_t cond_interior_t(sc_ctx* c, const T* Aown, const T* X, const T* Ainv, T* crossbuf, const T* xb,
-                            double beta, const double* Bfull, double alpha, T* u) {
+cudaError_t cond_interior_t(sc_ctx* c, const T* Aown, const T* Apk, const T* X, const T* Ainv, T* crossbuf,
+                            const T* xb, double beta, const double* Bfull, double alpha, T* u) {
   const Geo& G = c->G;
   if (G.ni == 0) return cudaSuccess;
   if (xb) {
@@ -359,6 +359,7 @@ cudaError_t cond_interior_t(sc_ctx* c, const T* Aown, const T* X, const T* Ainv,
         c->d_iperm, 0, G.ni, xb, T(1), (const T*)nullptr, T(0), crossbuf);
   }
   ProfScope ps(c, SCK_COND_INTERIOR);
+  if (Apk) return cond_interior_pk<T>(c, Apk, Ainv, xb ? crossbuf : (const T*)nullptr, xb, beta, Bfull, alpha, u);
   const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(T);
   k_cond_interior<T><<<G.K, 256, smem, c->stream>>>(G, Aown, X, Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm,
                                                     xb, beta, Bfull, alpha, u, xb ? crossbuf : (const T*)nullptr);
@@ -366,8 +367,8 @@ cudaError_t cond_interior_t(sc_ctx* c, const T* Aown, const T* X, const T* Ainv,
 }
 
 template <class T>
-cudaError_t cond_boundary_t(sc_ctx* c, const T* Aown, const T* X, T* crossbuf, const T* xb, double delta,
-                            const double* Bfull, double gamma_, const T* u, double* y) {
+cudaError_t cond_boundary_t(sc_ctx* c, const T* Aown, const T* Apk, const T* X, T* crossbuf, const T* xb,
+                            double delta, const double* Bfull, double gamma_, const T* u, double* y) {
   const Geo& G = c->G;
   if (G.ni == 0) u = nullptr;
   const bool need = xb || u;
@@ -378,6 +379,7 @@ cudaError_t cond_boundary_t(sc_ctx* c, const T* Aown, const T* X, T* crossbuf, c
         c->d_iperm, G.ni, G.nb, xb, T(delta), u, T(-1), crossbuf);
   }
   ProfScope ps(c, SCK_COND_BOUNDARY);
+  if (Apk) return cond_boundary_pk<T>(c, Apk, need ? crossbuf : (const T*)nullptr, xb, delta, Bfull, gamma_, u, y);
   const size_t smem = (size_t)G.lda * sizeof(T);
   k_cond_boundary<T><<<G.K, 256, smem, c->stream>>>(G, Aown, X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb,
                                                     delta, Bfull, gamma_, u, y, need ? crossbuf : (const T*)nullptr);
@@ -385,21 +387,25 @@ cudaError_t cond_boundary_t(sc_ctx* c, const T* Aown, const T* X, T* crossbuf, c
 }
 
 cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double* Bfull, double alpha, double* u) {
-  return cond_interior_t<double>(c, c->Aown, c->X, c->Ainv, c->Cross, xb, beta, Bfull, alpha, u);
+  return cond_interior_t<double>(c, c->Aown, c->packed ? c->Apk : nullptr, c->X, c->Ainv, c->Cross, xb, beta, Bfull,
+                                 alpha, u);
 }
 
 cudaError_t cond_boundary(sc_ctx* c, const double* xb, double delta, const double* Bfull, double gamma_,
                           const double* u, double* y) {
-  return cond_boundary_t<double>(c, c->Aown, c->X, c->Cross, xb, delta, Bfull, gamma_, u, y);
+  return cond_boundary_t<double>(c, c->Aown, c->packed ? c->Apk : nullptr, c->X, c->Cross, xb, delta, Bfull, gamma_,
+                                 u, y);
 }
 
 cudaError_t cond_interior32(sc_ctx* c, const float* xb, double beta, const double* Bfull, double alpha, float* u) {
-  return cond_interior_t<float>(c, c->Aown32, c->X32, c->Ainv32, c->Cross32, xb, beta, Bfull, alpha, u);
+  return cond_interior_t<float>(c, c->Aown32, c->packed ? c->Apk32 : nullptr, c->X32, c->Ainv32, c->Cross32, xb, beta,
+                                Bfull, alpha, u);
 }
 
 cudaError_t cond_boundary32(sc_ctx* c, const float* xb, double delta, const double* Bfull, double gamma_,
                             const float* u, double* y) {
-  return cond_boundary_t<float>(c, c->Aown32, c->X32, c->Cross32, xb, delta, Bfull, gamma_, u, y);
+  return cond_boundary_t<float>(c, c->Aown32, c->packed ? c->Apk32 : nullptr, c->X32, c->Cross32, xb, delta, Bfull,
+                                gamma_, u, y);
 }
 
 cudaError_t global_apply(sc_ctx* c, const double* x, double* y) {

@@ -1,0 +1,296 @@
+// Pattern-packed element blocks for the condensed operator (Sec. 2.2, eq. SC_step1 with
+// the implicit Schur product; Sec. 3.1 on the sparsity of the element blocks).
+//
+// On a tensor-product GL element the own block couples node j only to the nodes that
+// share at least one of its three GL indices: the inviscid volume terms run along the
+// three grid lines through j, and the BR1 viscous terms differentiate a lifted gradient
+// that itself runs along lines, so they reach the three planes through j.  The operator
+// passes need A_ib (interior rows, boundary columns) and [A_bi A_bb] (boundary rows): of
+// these dense blocks only 43-50 % of the 5 x 5 node blocks can be nonzero.
+//
+// Packed layout, per element and shared by all elements: row r of the own block keeps
+// the entries of its node's column list (the column nodes sharing an index, interior
+// columns first, in own-column order), 5 per column node, padded to a multiple of 4
+// entries so that every row starts on 16 bytes.  The packing kernel also checks that
+// every entry left out is exactly zero and reports the element otherwise.
+#include "sc_internal.cuh"
+
+namespace {
+
+template <class T> struct PkVec;
+template <> struct PkVec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct PkVec<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One packed row (n entries) against the own-column-ordered vector v in shared memory:
+// entry j belongs to column node j / 5 of the row's list, variable j % 5.  Two rows are
+// walked together so that twice as many loads are in flight per warp.
+template <class T>
+__device__ __forceinline__ void dot_pk2(const T* __restrict__ ra, int na, const int* __restrict__ ca,
+                                        const T* __restrict__ rb, int nb, const int* __restrict__ cbl,
+                                        const T* __restrict__ v, int lane, T& sa, T& sb) {
+  using V = typename PkVec<T>::type;
+  constexpr int W = PkVec<T>::n;
+  const int n = max(na, nb);
+  for (int j0 = lane * W; j0 < n; j0 += 32 * W) {
+    V a, b;
+    const bool ia = j0 < na, ib = j0 < nb;
+    if (ia) a = __ldg(reinterpret_cast<const V*>(ra + j0));
+    if (ib) b = __ldg(reinterpret_cast<const V*>(rb + j0));
+    const T* av = reinterpret_cast<const T*>(&a);
+    const T* bv = reinterpret_cast<const T*>(&b);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const int j = j0 + w, q = j / 5, l = j - 5 * q;
+      if (ia && j < na) sa = fma(av[w], v[__ldg(ca + q) + l], sa);
+      if (ib && j < nb) sb = fma(bv[w], v[__ldg(cbl + q) + l], sb);
+    }
+  }
+}
+
+// Dense FP64 own blocks -> packed blocks of type T; entries outside the pattern must be
+// zero (status <- SC_PACK_VIOLATION).  One warp per row.
+template <class T>
+__global__ void __launch_bounds__(256) k_pack(Geo G, const double* __restrict__ Aown, const int* __restrict__ row_off,
+                                              const int* __restrict__ pos, T* __restrict__ Apk, long long pstride,
+                                              int* __restrict__ status) {
+  const int e = blockIdx.x, lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const double* Ae = Aown + (size_t)e * own_stride(G);
+  T* Pe = Apk + (size_t)e * pstride;
+  bool bad = false;
+  for (int r = warp; r < G.ne; r += nw) {
+    const int p = r / 5;
+    const int* posr = pos + (size_t)p * G.nn;
+    T* prow = Pe + __ldg(row_off + r);
+    for (int cidx = lane; cidx < G.lda; cidx += 32) {
+      int q, l;
+      if (cidx < G.ni) { q = cidx / 5; l = cidx - 5 * q; }
+      else if (cidx >= G.cb0 && cidx < G.cb0 + G.nb) { const int t = cidx - G.cb0; q = G.nin + t / 5; l = t - 5 * (t / 5); }
+      else continue;  // alignment padding
+      const double val = Ae[(size_t)r * G.lda + cidx];
+      const int b = __ldg(posr + q);
+      if (b >= 0) prow[5 * b + l] = (T)val;
+      else if (b == -1 && val != 0.0) bad = true;
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(status, -1, SC_PACK_VIOLATION);
+}
+
+// Interior pass with packed A_ib: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e).
+template <class T>
+__global__ void __launch_bounds__(256) k_cond_interior_pk(Geo G, const T* __restrict__ Apk, long long pstride,
+    const int* __restrict__ row_off, const int* __restrict__ lptr, const int* __restrict__ list,
+    const T* __restrict__ Ainv, const int* __restrict__ iperm, const T* __restrict__ xb, double beta,
+    const double* __restrict__ Bfull, double alpha, T* __restrict__ u, const T* __restrict__ cross) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int e = blockIdx.x, ni = G.ni, nb = G.nb, lda = G.lda, ldi = G.ldi;
+  T* v = reinterpret_cast<T*>(smem_raw);  // lda: x_e at the boundary columns
+  T* t = v + lda;                         // ldi: right-hand side of the interior solve
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  for (int i = threadIdx.x; i < lda; i += blockDim.x) {
+    T val = T(0);
+    if (xb && i >= G.cb0 && i < G.cb0 + nb) val = xb[(size_t)e * nb + i - G.cb0];
+    v[i] = val;
+  }
+  for (int i = ni + threadIdx.x; i < ldi; i += blockDim.x) t[i] = T(0);
+  __syncthreads();
+  const T* Pe = Apk + (size_t)e * pstride;
+  for (int ra = 2 * warp; ra < ni; ra += 2 * nw) {
+    const int rb = ra + 1 < ni ? ra + 1 : ra;
+    T sa = T(0), sb = T(0);
+    if (xb) {
+      const int pa = ra / 5, pb = rb / 5;
+      dot_pk2(Pe + __ldg(row_off + ra), 5 * (__ldg(lptr + pa + 1) - __ldg(lptr + pa)), list + __ldg(lptr + pa),
+              Pe + __ldg(row_off + rb), 5 * (__ldg(lptr + pb + 1) - __ldg(lptr + pb)), list + __ldg(lptr + pb), v,
+              lane, sa, sb);
+      sa = wsum(sa); sb = wsum(sb);
+      sa += cross[(size_t)e * ni + ra];
+      sb += cross[(size_t)e * ni + rb];
+    }
+    if (lane == 0) {
+      T va = T(beta) * sa, vb = T(beta) * sb;
+      if (Bfull) {
+        va += T(alpha * Bfull[((size_t)e * G.nn + __ldg(iperm + ra / 5)) * 5 + ra % 5]);
+        vb += T(alpha * Bfull[((size_t)e * G.nn + __ldg(iperm + rb / 5)) * 5 + rb % 5]);
+      }
+      t[ra] = va;
+      if (rb != ra) t[rb] = vb;
+    }
+  }
+  __syncthreads();
+  using V = typename PkVec<T>::type;
+  constexpr int W = PkVec<T>::n;
+  const T* Ie = Ainv + (size_t)e * ni * ldi;
+  for (int ra = 2 * warp; ra < ni; ra += 2 * nw) {
+    const int rb = ra + 1 < ni ? ra + 1 : ra;
+    const T* ia = Ie + (size_t)ra * ldi;
+    const T* ib = Ie + (size_t)rb * ldi;
+    T sa = T(0), sb = T(0);
+    for (int j0 = lane * W; j0 < ldi; j0 += 32 * W) {
+      const V a = __ldg(reinterpret_cast<const V*>(ia + j0));
+      const V b = __ldg(reinterpret_cast<const V*>(ib + j0));
+      const T* av = reinterpret_cast<const T*>(&a);
+      const T* bv = reinterpret_cast<const T*>(&b);
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        sa = fma(av[w], t[j0 + w], sa);
+        sb = fma(bv[w], t[j0 + w], sb);
+      }
+    }
+    sa = wsum(sa); sb = wsum(sb);
+    if (lane == 0) {
+      u[(size_t)e * ni + ra] = sa;
+      if (rb != ra) u[(size_t)e * ni + rb] = sb;
+    }
+  }
+}
+
+// Boundary pass with packed [A_bi A_bb]: y_e = gamma B_b,e + delta (A_bb x_b)_e - (A_bi u)_e
+// plus the neighbour couplings in `cross`.
+template <class T>
+__global__ void __launch_bounds__(256) k_cond_boundary_pk(Geo G, const T* __restrict__ Apk, long long pstride,
+    const int* __restrict__ row_off, const int* __restrict__ lptr, const int* __restrict__ list,
+    const int* __restrict__ iperm, const T* __restrict__ xb, double delta, const double* __restrict__ Bfull,
+    double gamma_, const T* __restrict__ u, double* __restrict__ y, const T* __restrict__ cross) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int e = blockIdx.x, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, cb0 = G.cb0;
+  T* v = reinterpret_cast<T*>(smem_raw);  // lda: [-u_e | 0 | delta x_e | 0]
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const T dT = T(delta);
+  for (int i = threadIdx.x; i < lda; i += blockDim.x) {
+    T val = T(0);
+    if (i < ni) { if (u) val = -u[(size_t)e * ni + i]; }
+    else if (i >= cb0 && i < cb0 + nb) { if (xb) val = dT * xb[(size_t)e * nb + i - cb0]; }
+    v[i] = val;
+  }
+  __syncthreads();
+  const T* Pe = Apk + (size_t)e * pstride;
+  const bool need = xb || u;
+  for (int ra = ni + 2 * warp; ra < ne; ra += 2 * nw) {
+    const int rb = ra + 1 < ne ? ra + 1 : ra;
+    T sa = T(0), sb = T(0);
+    if (need) {
+      const int pa = ra / 5, pb = rb / 5;
+      dot_pk2(Pe + __ldg(row_off + ra), 5 * (__ldg(lptr + pa + 1) - __ldg(lptr + pa)), list + __ldg(lptr + pa),
+              Pe + __ldg(row_off + rb), 5 * (__ldg(lptr + pb + 1) - __ldg(lptr + pb)), list + __ldg(lptr + pb), v,
+              lane, sa, sb);
+      sa = wsum(sa); sb = wsum(sb);
+      sa += cross[(size_t)e * nb + ra - ni];
+      sb += cross[(size_t)e * nb + rb - ni];
+    }
+    if (lane == 0) {
+      double va = (double)sa, vb = (double)sb;
+      if (Bfull) {
+        va += gamma_ * Bfull[((size_t)e * G.nn + __ldg(iperm + ra / 5)) * 5 + ra % 5];
+        vb += gamma_ * Bfull[((size_t)e * G.nn + __ldg(iperm + rb / 5)) * 5 + rb % 5];
+      }
+      y[(size_t)e * nb + ra - ni] = va;
+      if (rb != ra) y[(size_t)e * nb + rb - ni] = vb;
+    }
+  }
+}
+
+}  // namespace
+
+namespace sc {
+
+// Host tables of the packed layout (per mesh): column lists per node slot, row offsets,
+// and the slot-pair position table used by the packing kernel.
+void build_packed_pattern(sc_ctx* c) {
+  const Geo& G = c->G;
+  const int nn = G.nn, p1 = G.p;
+  c->pk_lptr.assign(nn + 1, 0);
+  c->pk_list.clear();
+  c->pk_pos.assign((size_t)nn * nn, -1);
+  auto nat = [&](int slot, int d) {
+    const int m = c->iperm[slot];
+    return d == 0 ? m % p1 : d == 1 ? (m / p1) % p1 : m / (p1 * p1);
+  };
+  for (int p = 0; p < nn; ++p) {
+    int len = 0;
+    for (int q = 0; q < nn; ++q) {
+      if (p < G.nin && q < G.nin) { c->pk_pos[(size_t)p * nn + q] = -2; continue; }  // A_ii: not packed
+      const bool share = nat(p, 0) == nat(q, 0) || nat(p, 1) == nat(q, 1) || nat(p, 2) == nat(q, 2);
+      if (!share) continue;
+      c->pk_pos[(size_t)p * nn + q] = len++;
+      c->pk_list.push_back(own_col(G, q, 0));
+    }
+    c->pk_lptr[p + 1] = c->pk_lptr[p] + len;
+  }
+  c->pk_row_off.assign(G.ne + 1, 0);
+  c->pk_nnz_int = c->pk_nnz_bnd = 0;
+  for (int r = 0; r < G.ne; ++r) {
+    const int p = r / 5, n = 5 * (c->pk_lptr[p + 1] - c->pk_lptr[p]);
+    c->pk_row_off[r + 1] = c->pk_row_off[r] + ((n + 3) & ~3);
+    (r < G.ni ? c->pk_nnz_int : c->pk_nnz_bnd) += n;
+  }
+  c->pk_stride = c->pk_row_off[G.ne];
+}
+
+cudaError_t upload_packed_pattern(sc_ctx* c) {
+  cudaError_t e = cudaMemcpy(c->d_pk_lptr, c->pk_lptr.data(), c->pk_lptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_pk_list, c->pk_list.data(), c->pk_list.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_pk_row_off, c->pk_row_off.data(), c->pk_row_off.size() * sizeof(int),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_pk_pos, c->pk_pos.data(), c->pk_pos.size() * sizeof(int), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Pack the FP64 own blocks into the operator's precision.
+cudaError_t pack_own(sc_ctx* c) {
+  const Geo& G = c->G;
+  count_launch(c);
+  if (c->cfg.precision == SC_PREC_MIXED)
+    k_pack<float><<<G.K, 256, 0, c->stream>>>(G, c->Aown, c->d_pk_row_off, c->d_pk_pos, c->Apk32, c->pk_stride,
+                                              c->d_status);
+  else
+    k_pack<double><<<G.K, 256, 0, c->stream>>>(G, c->Aown, c->d_pk_row_off, c->d_pk_pos, c->Apk, c->pk_stride,
+                                               c->d_status);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* Ainv, const T* cross, const T* xb, double beta,
+                             const double* Bfull, double alpha, T* u) {
+  const Geo& G = c->G;
+  const size_t smem = (size_t)(G.lda + G.ldi) * sizeof(T);
+  k_cond_interior_pk<T><<<G.K, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
+                                                       c->d_pk_list, Ainv, c->d_iperm, xb, beta, Bfull, alpha, u,
+                                                       cross);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* cross, const T* xb, double delta, const double* Bfull,
+                             double gamma_, const T* u, double* y) {
+  const Geo& G = c->G;
+  const size_t smem = (size_t)G.lda * sizeof(T);
+  k_cond_boundary_pk<T><<<G.K, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
+                                                       c->d_pk_list, c->d_iperm, xb, delta, Bfull, gamma_, u, y,
+                                                       cross);
+  return cudaGetLastError();
+}
+
+template cudaError_t cond_interior_pk<float>(sc_ctx*, const float*, const float*, const float*, const float*, double,
+                                             const double*, double, float*);
+template cudaError_t cond_interior_pk<double>(sc_ctx*, const double*, const double*, const double*, const double*,
+                                              double, const double*, double, double*);
+template cudaError_t cond_boundary_pk<float>(sc_ctx*, const float*, const float*, const float*, double, const double*,
+                                             double, const float*, double*);
+template cudaError_t cond_boundary_pk<double>(sc_ctx*, const double*, const double*, const double*, double,
+                                              const double*, double, const double*, double*);
+
+}  // namespace sc

@@ -104,3 +104,27 @@ def test_linear_model_jacobian_is_state_independent():
     A1 = O.jacobian(p, rng.standard_normal((n ** 3, (N + 1) ** 3, 5)))
     A2 = O.jacobian(p, rng.standard_normal((n ** 3, (N + 1) ** 3, 5)))
     assert abs(A1 - A2).max() < 1e-13 * abs(A1).max()
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_own_block_couples_only_nodes_sharing_a_gl_index(N):
+    """Own element block of the Jacobian: node a couples to node b only if they share at
+    least one of the three GL indices (volume terms act along grid lines, the BR1 viscous
+    terms along lines of lines).  The condensed operator stores only these node blocks,
+    so every other block must be exactly zero; the pattern is also tight (each kept
+    node pair carries a nonzero entry somewhere on the mesh)."""
+    n = 3
+    Q, dt = I.tgv_state(n, N, cfl=50.0)
+    p = O.Params(n=n, N=N, dt=dt, bdf=1)
+    A = O.jacobian(p, Q).tocsr()
+    nn = (N + 1) ** 3
+    ne = 5 * nn
+    idx = np.array([(m % (N + 1), (m // (N + 1)) % (N + 1), m // (N + 1) ** 2) for m in range(nn)])
+    share = (idx[:, None, :] == idx[None, :, :]).any(axis=2)
+    seen = np.zeros((nn, nn), bool)
+    for e in range(n ** 3):
+        blk = A[e * ne:(e + 1) * ne, e * ne:(e + 1) * ne].toarray().reshape(nn, 5, nn, 5)
+        nz = (blk != 0).any(axis=(1, 3))
+        assert not (nz & ~share).any()
+        seen |= nz
+    assert (seen == share).all()
