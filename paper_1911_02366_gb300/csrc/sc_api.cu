@@ -90,10 +90,10 @@ void diff_matrix(const std::vector<double>& x, double D[SC_MAXP][SC_MAXP]) {
 void free_all(sc_ctx* c) {
   double** dps[] = {&c->Q, &c->Qh, &c->grad, &c->F, &c->B, &c->NJ, &c->RJ, &c->Aown, &c->X, &c->Ainv,
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
-                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk};
+                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk, &c->Sls};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
-                   &c->Apk32};
+                   &c->Apk32, &c->Sls32};
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
@@ -306,8 +306,11 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pinfo, np));
   A(dalloc(&c->d_pk_lptr, c->pk_lptr.size())); A(dalloc(&c->d_pk_list, c->pk_list.size()));
   A(dalloc(&c->d_pk_row_off, c->pk_row_off.size())); A(dalloc(&c->d_pk_pos, c->pk_pos.size()));
-  if (c->cfg.precision == SC_PREC_MIXED) A(dalloc(&c->Apk32, (size_t)G.K * c->pk_stride));
-  else A(dalloc(&c->Apk, (size_t)G.K * c->pk_stride));
+  if (c->cfg.precision == SC_PREC_MIXED) {
+    A(dalloc(&c->Apk32, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls32, sc::solve_layout_elems(G)));
+  } else {
+    A(dalloc(&c->Apk, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls, sc::solve_layout_elems(G)));
+  }
   if (e != cudaSuccess) { free_all(c); cudaGetLastError(); return fail(c, SC_ERR_OOM, std::string("allocation: ") + cudaGetErrorString(e)); }
   SC_CUDA(cudaMemcpy(c->d_nbr, c->nbr.data(), c->nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_perm, c->perm.data(), G.nn * sizeof(int), cudaMemcpyHostToDevice));

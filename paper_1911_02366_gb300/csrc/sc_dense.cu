@@ -8,8 +8,9 @@
 //               tiles, 4x4 register micro-tiles).
 //   k_lu        right-looking blocked LU with partial pivoting of a batch of blocks
 //               in global memory (32-column panels factorised in shared memory).
-//   k_lu_solve  z = (P^T L U)^-1 v for every element (one CTA per element, 32-row
-//               panels with a warp-shuffle solve of each diagonal triangle).
+//   k_solve_prep  partitioned inverses of the LU factors in the solve layout (below).
+//   k_lu_solve    z = (P^T L U)^-1 v for every element, one warp per element, one lane
+//                 per row of each 32-row block.
 #include <type_traits>
 
 #include "sc_internal.cuh"
@@ -362,138 +363,151 @@ __global__ void k_piv_to_perm(int n, const int* __restrict__ piv_all, int* __res
 }
 
 
-template <class T> struct V16;
-template <> struct V16<double> { using type = double2; static constexpr int n = 2; };
-template <> struct V16<float> { using type = float4; static constexpr int n = 4; };
-__device__ __forceinline__ void vfma(const double2& a, const double2& b, double& s0, double& s1) {
-  s0 = fma(a.x, b.x, s0); s1 = fma(a.y, b.y, s1);
-}
-__device__ __forceinline__ void vfma(const float4& a, const float4& b, float& s0, float& s1) {
-  s0 = fmaf(a.x, b.x, s0); s1 = fmaf(a.y, b.y, s1); s0 = fmaf(a.z, b.z, s0); s1 = fmaf(a.w, b.w, s1);
-}
-__device__ __forceinline__ float warp_sum_t(float s) {
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
-}
-__device__ __forceinline__ double warp_sum_t(double s) {
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
-}
+// ---- block-Jacobi solve with partitioned inverses -----------------------------------
+// With D_b the 32 x 32 diagonal blocks of the factors (their triangles replaced by the
+// triangles' inverses, k_diag_inv), forward and backward substitution read
+//   x_b = L_bb^-1 v_b - M_b x_{<b},   M_b = L_bb^-1 L_{b,<b}
+//   z_b = U_bb^-1 x_b - N_b z_{>b},   N_b = U_bb^-1 U_{b,>b}
+// so every step is one dot product per row and needs no triangular solve.  The solve
+// layout stores, per element and 32-row block row b, columns in groups of four:
+// element (row 32 b + r, column c) at [b][c / 4][r][c % 4] (npad = n rounded up to 4
+// columns, rows beyond n zero).  A warp then reads one 4-column group of all 32 rows as
+// 32 consecutive 16- (FP32) or 32-byte (FP64) pieces.
 
-// sum_{k0 <= k < k1} row[k] xs[k]; row + k0 and xs + k0 16-byte aligned.
-template <class T>
-__device__ __forceinline__ T dot_row(const T* __restrict__ row, const T* xs, int k0, int k1, int lane) {
-  using V = typename V16<T>::type;
-  constexpr int W = V16<T>::n;
-  const V* r = reinterpret_cast<const V*>(row + k0);
-  const V* x = reinterpret_cast<const V*>(xs + k0);
-  const int len = k1 - k0, nv = len / W;
-  T s0 = T(0), s1 = T(0);
-#pragma unroll 4
-  for (int i = lane; i < nv; i += 32) vfma(__ldg(r + i), x[i], s0, s1);
-  for (int i = k0 + nv * W + lane; i < k1; i += 32) s0 = fma(__ldg(row + i), xs[i], s0);
-  return s0 + s1;
-}
-
-// Two row dots at once over [k0, k1) (row + k0, xs + k0 16-byte aligned).
-template <class T>
-__device__ __forceinline__ void dot_row2(const T* __restrict__ ra, const T* __restrict__ rb, const T* xs, int k0,
-                                         int k1, int lane, T& sa, T& sb) {
-  using V = typename V16<T>::type;
-  constexpr int W = V16<T>::n;
-  const V* a = reinterpret_cast<const V*>(ra + k0);
-  const V* b = reinterpret_cast<const V*>(rb + k0);
-  const V* x = reinterpret_cast<const V*>(xs + k0);
-  const int len = k1 - k0, nv = len / W;
-  T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
-#pragma unroll 2
-  for (int i = lane; i < nv; i += 32) {
-    const V xv = x[i];
-    vfma(__ldg(a + i), xv, a0, a1);
-    vfma(__ldg(b + i), xv, b0, b1);
+template <class T> struct Quad;
+template <> struct Quad<float> {
+  float v[4];
+  __device__ __forceinline__ void load(const float* p) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   }
-  for (int i = k0 + nv * W + lane; i < k1; i += 32) { a0 = fma(__ldg(ra + i), xs[i], a0); b0 = fma(__ldg(rb + i), xs[i], b0); }
-  sa = a0 + a1; sb = b0 + b1;
+};
+template <> struct Quad<double> {
+  double v[4];
+  __device__ __forceinline__ void load(const double* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+
+// One CTA per (block row b, element): D_b from the factors, then every column c of the
+// block row: c < i0 -> M_b, diagonal block -> D_b, c >= i0 + 32 -> N_b.
+template <class T>
+__global__ void __launch_bounds__(256) k_solve_prep(int n, const T* __restrict__ LU, long long stride, int lda,
+                                                    T* __restrict__ LS, long long lsstride, int npad) {
+  __shared__ T TL[32][33];  // L_bb^-1: unit diagonal, stored inverse below it
+  __shared__ T TU[32][33];  // U_bb^-1: stored inverse on and above the diagonal
+  __shared__ T D[32][33];   // diagonal block as stored (both inverse triangles)
+  const int b = blockIdx.x, e = blockIdx.y, i0 = 32 * b, bs = min(32, n - i0);
+  const T* M = LU + (long long)e * stride;
+  T* out = LS + (long long)e * lsstride + (long long)b * 32 * npad;
+  for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+    const int r = t / 32, k = t % 32;
+    const T dv = (r < bs && k < bs) ? M[(long long)(i0 + r) * lda + i0 + k] : T(0);
+    D[r][k] = dv;
+    TL[r][k] = (r < bs && k < bs) ? (k < r ? dv : (k == r ? T(1) : T(0))) : T(0);
+    TU[r][k] = (k >= r) ? dv : T(0);
+  }
+  __syncthreads();
+  for (int cidx = threadIdx.x; cidx < npad; cidx += blockDim.x) {
+    T col[32];
+    const bool left = cidx < i0, right = cidx >= i0 + 32;
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      col[k] = (k < bs && cidx < n && (left || right)) ? M[(long long)(i0 + k) * lda + cidx] : T(0);
+    T* o = out + (long long)(cidx / 4) * 128 + (cidx % 4);
+    if (left || right) {
+      T(*Tm)[33] = left ? TL : TU;
+      for (int r = 0; r < 32; ++r) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc = fma(Tm[r][k], col[k], acc);
+        o[4 * r] = acc;
+      }
+    } else {
+      for (int r = 0; r < 32; ++r) o[4 * r] = cidx < n ? D[r][cidx - i0] : T(0);
+    }
+  }
 }
 
-// z = (P^T L U)^-1 v for every element: one CTA per element, 32-row panels.  Each panel
-// first subtracts the already-solved part (rows spread over the warps, 16-byte row
-// reads), then applies the stored inverse of its 32 x 32 diagonal triangle (see
-// k_diag_inv) as one 32-wide product.  Arithmetic in the factor precision T; v in
-// double, outputs z (double) and / or zt (T).
+// z = (P^T L U)^-1 v, one warp per element (4 per CTA), lane r owns row 32 b + r of
+// every block; the running vector (v, then x, then z) sits in shared memory.
+// Arithmetic in the factor precision T; v in double, outputs z (double) and / or zt (T).
 template <class T>
-__global__ void __launch_bounds__(256) k_lu_solve(int n, const T* __restrict__ LU, long long stride, int lda,
-                                                  const int* __restrict__ rowperm, const double* __restrict__ v,
-                                                  double* __restrict__ z, T* __restrict__ zt) {
+__global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const T* __restrict__ LS, long long lsstride,
+                                                  int npad, const int* __restrict__ rowperm,
+                                                  const double* __restrict__ v, double* __restrict__ z,
+                                                  T* __restrict__ zt, int nelem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);
-  __shared__ T Dg[32][33];
-  const int e = blockIdx.x;
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-  const T* M = LU + (long long)e * stride;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int e = blockIdx.x * 4 + warp;
+  if (e >= nelem) return;  // whole warps leave; no block-level barrier follows
+  const int ls = nblk * 32;
+  T* s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * ls;
+  const T* Le = LS + (long long)e * lsstride;
   const int* rp = rowperm + (long long)e * n;
   const double* ve = v + (long long)e * n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = (T)ve[rp[i]];
-  __syncthreads();
-  for (int i0 = 0; i0 < n; i0 += 32) {  // unit lower triangle
-    const int bs = min(32, n - i0);
-    for (int r = 2 * warp; r < bs; r += 2 * nw) {
-      const int r2 = r + 1 < bs ? r + 1 : r;
-      const T* row = M + (long long)(i0 + r) * lda;
-      const T* row2 = M + (long long)(i0 + r2) * lda;
-      Dg[r][lane] = lane < bs ? row[i0 + lane] : T(0);
-      Dg[r2][lane] = lane < bs ? row2[i0 + lane] : T(0);
-      if (i0 > 0) {
-        T sa, sb;
-        dot_row2(row, row2, xs, 0, i0, lane, sa, sb);
-        sa = warp_sum_t(sa); sb = warp_sum_t(sb);
-        if (lane == 0) { xs[i0 + r] -= sa; if (r2 != r) xs[i0 + r2] -= sb; }
-      }
+  for (int i = lane; i < ls; i += 32) s[i] = i < n ? (T)ve[__ldg(rp + i)] : T(0);
+  __syncwarp();
+  const int nq = npad / 4;
+  for (int b = 0; b < nblk; ++b) {  // forward: x_b = L_bb^-1 v_b - M_b x_{<b}
+    const int i0 = 32 * b, R = i0 + lane;
+    const T* row = Le + (long long)b * 32 * npad + 4 * lane;
+    T a0 = T(0), a1 = T(0);
+#pragma unroll 8
+    for (int q = 0; q < i0 / 4; ++q) {
+      Quad<T> m;
+      m.load(row + (long long)q * 128);
+      a0 = fma(m.v[0], s[4 * q], a0);
+      a1 = fma(m.v[1], s[4 * q + 1], a1);
+      a0 = fma(m.v[2], s[4 * q + 2], a0);
+      a1 = fma(m.v[3], s[4 * q + 3], a1);
     }
-    __syncthreads();
-    if (warp == 0) {  // x_blk <- L_bb^-1 x_blk (unit lower inverse stored below the diagonal)
-      T xl = lane < bs ? xs[i0 + lane] : T(0);
-      T acc = xl;
-      for (int jj = 0; jj < bs; ++jj) {
-        const T xj = xs[i0 + jj];
-        if (jj < lane) acc = fma(Dg[lane][jj], xj, acc);
-      }
-      __syncwarp();
-      if (lane < bs) xs[i0 + lane] = acc;
+    T d = s[R];
+    const int qd = min(i0 / 4 + 8, nq);  // the last block row may end before 32 columns
+#pragma unroll
+    for (int q = i0 / 4; q < qd; ++q) {
+      Quad<T> m;
+      m.load(row + (long long)q * 128);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (4 * q + j < R) d = fma(m.v[j], s[4 * q + j], d);
     }
-    __syncthreads();
+    __syncwarp();
+    if (R < n) s[R] = d - (a0 + a1);
+    __syncwarp();
   }
-  const int nblk = (n + 31) / 32;
-  for (int b = nblk - 1; b >= 0; --b) {  // upper triangle
-    const int i0 = b * 32, bs = min(32, n - i0), i1 = i0 + bs;
-    for (int r = 2 * warp; r < bs; r += 2 * nw) {
-      const int r2 = r + 1 < bs ? r + 1 : r;
-      const T* row = M + (long long)(i0 + r) * lda;
-      const T* row2 = M + (long long)(i0 + r2) * lda;
-      Dg[r][lane] = lane < bs ? row[i0 + lane] : T(0);
-      Dg[r2][lane] = lane < bs ? row2[i0 + lane] : T(0);
-      if (i1 < n) {
-        T sa, sb;
-        dot_row2(row, row2, xs, i1, n, lane, sa, sb);
-        sa = warp_sum_t(sa); sb = warp_sum_t(sb);
-        if (lane == 0) { xs[i0 + r] -= sa; if (r2 != r) xs[i0 + r2] -= sb; }
-      }
+  for (int b = nblk - 1; b >= 0; --b) {  // backward: z_b = U_bb^-1 x_b - N_b z_{>b}
+    const int i0 = 32 * b, R = i0 + lane;
+    const T* row = Le + (long long)b * 32 * npad + 4 * lane;
+    T d = T(0);
+    const int qd = min(i0 / 4 + 8, nq);
+#pragma unroll
+    for (int q = i0 / 4; q < qd; ++q) {
+      Quad<T> m;
+      m.load(row + (long long)q * 128);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (4 * q + j >= R) d = fma(m.v[j], s[4 * q + j], d);
     }
-    __syncthreads();
-    if (warp == 0) {  // x_blk <- U_bb^-1 x_blk (upper inverse stored on and above the diagonal)
-      T acc = T(0);
-      for (int jj = 0; jj < bs; ++jj) {
-        const T xj = xs[i0 + jj];
-        if (jj >= lane) acc = fma(Dg[lane][jj], xj, acc);
-      }
-      __syncwarp();
-      if (lane < bs) xs[i0 + lane] = acc;
+    T a0 = T(0), a1 = T(0);
+#pragma unroll 8
+    for (int q = i0 / 4 + 8; q < nq; ++q) {
+      Quad<T> m;
+      m.load(row + (long long)q * 128);
+      a0 = fma(m.v[0], s[4 * q], a0);
+      a1 = fma(m.v[1], s[4 * q + 1], a1);
+      a0 = fma(m.v[2], s[4 * q + 2], a0);
+      a1 = fma(m.v[3], s[4 * q + 3], a1);
     }
-    __syncthreads();
+    __syncwarp();
+    if (R < n) s[R] = d - (a0 + a1);
+    __syncwarp();
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if (z) z[(long long)e * n + i] = (double)xs[i];
-    if (zt) zt[(long long)e * n + i] = xs[i];
+  for (int i = lane; i < n; i += 32) {
+    if (z) z[(long long)e * n + i] = (double)s[i];
+    if (zt) zt[(long long)e * n + i] = s[i];
   }
 }
 
@@ -609,6 +623,12 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
     err = cudaFuncSetAttribute(k_diag_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     if (err != cudaSuccess) return err;
     k_diag_inv<T><<<K, 256, dsm, c->stream>>>(nb, See, (long long)nb * lds, lds);
+    count_launch(c);
+    T* LS = nullptr;
+    if constexpr (std::is_same<T, float>::value) LS = c->Sls32; else LS = c->Sls;
+    const int nblk = (nb + 31) / 32, npad = (nb + 3) & ~3;
+    k_solve_prep<T><<<dim3(nblk, K), 256, 0, c->stream>>>(nb, See, (long long)nb * lds, lds, LS,
+                                                           (long long)nblk * 32 * npad, npad);
   }
   return cudaGetLastError();
 }
@@ -630,17 +650,28 @@ cudaError_t launch_condense(sc_ctx* c) {
   return condense_t<double>(c, c->Aown, c->Ainv, c->Ytmp, c->See, false);
 }
 
+// Solve-layout geometry of the S_ee factors.
+inline int ls_nblk(const Geo& G) { return (G.nb + 31) / 32; }
+inline int ls_npad(const Geo& G) { return (G.nb + 3) & ~3; }
+inline long long ls_stride(const Geo& G) { return (long long)ls_nblk(G) * 32 * ls_npad(G); }
+
+template <class T>
+cudaError_t lu_solve_t(sc_ctx* c, const T* LS, const double* v, double* z, T* zt) {
+  const Geo& G = c->G;
+  ProfScope ps(c, SCK_LU_SOLVE);
+  const size_t smem = (size_t)4 * ls_nblk(G) * 32 * sizeof(T);
+  k_lu_solve<T><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G), c->rowperm,
+                                                        v, z, zt, G.K);
+  return cudaGetLastError();
+}
+
 cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
   const Geo& G = c->G;
   const size_t n1 = (size_t)G.K * G.nb;
   if (c->cfg.precond != SC_PC_BLOCK_JACOBI) {
     return cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   }
-  ProfScope ps(c, SCK_LU_SOLVE);
-  const size_t smem = (size_t)G.nb * sizeof(double);
-  k_lu_solve<double><<<G.K, 256, smem, c->stream>>>(G.nb, c->See, (long long)G.nb * G.lds, G.lds, c->rowperm, v, z,
-                                                    nullptr);
-  return cudaGetLastError();
+  return lu_solve_t<double>(c, c->Sls, v, z, nullptr);
 }
 
 // Block-Jacobi with the FP32 factors; writes z in double and / or zf in float.
@@ -653,11 +684,9 @@ cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
     if (e == cudaSuccess && zf) e = vec_to_float(c, zf, v, n1);
     return e;
   }
-  ProfScope ps(c, SCK_LU_SOLVE);
-  const size_t smem = (size_t)G.nb * sizeof(float);
-  k_lu_solve<float><<<G.K, 256, smem, c->stream>>>(G.nb, c->See32, (long long)G.nb * G.lds, G.lds, c->rowperm, v, z,
-                                                   zf);
-  return cudaGetLastError();
+  return lu_solve_t<float>(c, c->Sls32, v, z, zf);
 }
+
+size_t solve_layout_elems(const Geo& G) { return (size_t)G.K * ls_stride(G); }
 
 }  // namespace sc

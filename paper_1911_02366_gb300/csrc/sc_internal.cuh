@@ -274,6 +274,9 @@ struct sc_ctx {
   int *d_pk_lptr = nullptr, *d_pk_list = nullptr, *d_pk_row_off = nullptr, *d_pk_pos = nullptr;
   double* Apk = nullptr;   // FP64 arm
   float* Apk32 = nullptr;  // mixed arm
+  // S_ee factors with partitioned inverses in the block-Jacobi solve layout
+  double* Sls = nullptr;
+  float* Sls32 = nullptr;
   bool packed = false;     // packed blocks match the assembled Jacobian
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};
@@ -347,6 +350,7 @@ cudaError_t vec_scale_copy(sc_ctx* c, double* dst, const double* src, size_t n, 
 cudaError_t gemm_tf32(cudaStream_t stream, int M, int N, int K, float alpha, const float* A, long long sA, int lda,
                       bool ta, const float* B, long long sB, int ldb, bool tb, float beta, float* C, long long sC,
                       int ldc, int batch, int* status);
+size_t solve_layout_elems(const Geo& G);
 void build_packed_pattern(sc_ctx* c);
 cudaError_t upload_packed_pattern(sc_ctx* c);
 cudaError_t pack_own(sc_ctx* c);
