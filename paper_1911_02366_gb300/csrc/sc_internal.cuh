@@ -355,10 +355,10 @@ void build_packed_pattern(sc_ctx* c);
 cudaError_t upload_packed_pattern(sc_ctx* c);
 cudaError_t pack_own(sc_ctx* c);
 template <class T>
-cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* Ainv, const T* cross, const T* xb, double beta,
+cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* X, const T* Ainv, const T* xb, double beta,
                              const double* Bfull, double alpha, T* u);
 template <class T>
-cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* cross, const T* xb, double delta, const double* Bfull,
+cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* X, const T* xb, double delta, const double* Bfull,
                              double gamma_, const T* u, double* y);
 cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b, size_t n);
 }  // namespace sc

@@ -347,11 +347,17 @@ constexpr int kDotChunks = 152;
 
 namespace sc {
 
+// The condensed operator's passes: fused kernels on the pattern-packed blocks once the
+// condensation has packed them, otherwise a coupling pass followed by the dense kernels.
 template <class T>
 cudaError_t cond_interior_t(sc_ctx* c, const T* Aown, const T* Apk, const T* X, const T* Ainv, T* crossbuf,
                             const T* xb, double beta, const double* Bfull, double alpha, T* u) {
   const Geo& G = c->G;
   if (G.ni == 0) return cudaSuccess;
+  if (Apk) {
+    ProfScope ps(c, SCK_COND_INTERIOR);
+    return cond_interior_pk<T>(c, Apk, X, Ainv, xb, beta, Bfull, alpha, u);
+  }
   if (xb) {
     count_launch(c);
     const size_t rows = (size_t)G.K * G.ni;
@@ -359,7 +365,6 @@ cudaError_t cond_interior_t(sc_ctx* c, const T* Aown, const T* Apk, const T* X, 
         c->d_iperm, 0, G.ni, xb, T(1), (const T*)nullptr, T(0), crossbuf);
   }
   ProfScope ps(c, SCK_COND_INTERIOR);
-  if (Apk) return cond_interior_pk<T>(c, Apk, Ainv, xb ? crossbuf : (const T*)nullptr, xb, beta, Bfull, alpha, u);
   const size_t smem = (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(T);
   k_cond_interior<T><<<G.K, 256, smem, c->stream>>>(G, Aown, X, Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm,
                                                     xb, beta, Bfull, alpha, u, xb ? crossbuf : (const T*)nullptr);
@@ -371,6 +376,10 @@ cudaError_t cond_boundary_t(sc_ctx* c, const T* Aown, const T* Apk, const T* X, 
                             double delta, const double* Bfull, double gamma_, const T* u, double* y) {
   const Geo& G = c->G;
   if (G.ni == 0) u = nullptr;
+  if (Apk) {
+    ProfScope ps(c, SCK_COND_BOUNDARY);
+    return cond_boundary_pk<T>(c, Apk, X, xb, delta, Bfull, gamma_, u, y);
+  }
   const bool need = xb || u;
   if (need) {
     count_launch(c);
@@ -379,7 +388,6 @@ cudaError_t cond_boundary_t(sc_ctx* c, const T* Aown, const T* Apk, const T* X, 
         c->d_iperm, G.ni, G.nb, xb, T(delta), u, T(-1), crossbuf);
   }
   ProfScope ps(c, SCK_COND_BOUNDARY);
-  if (Apk) return cond_boundary_pk<T>(c, Apk, need ? crossbuf : (const T*)nullptr, xb, delta, Bfull, gamma_, u, y);
   const size_t smem = (size_t)G.lda * sizeof(T);
   k_cond_boundary<T><<<G.K, 256, smem, c->stream>>>(G, Aown, X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb,
                                                     delta, Bfull, gamma_, u, y, need ? crossbuf : (const T*)nullptr);

@@ -32,30 +32,63 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// One packed row (n entries) against the own-column-ordered vector v in shared memory:
-// entry j belongs to column node j / 5 of the row's list, variable j % 5.  Two rows are
-// walked together so that twice as many loads are in flight per warp.
+// The 5 rows of node p (variables k = 0..4) against the own-column-ordered vector v in
+// shared memory: row k of the node starts at P0 + k * rs and holds n packed entries;
+// entry j belongs to column node j / 5 of the node's list `cols`, variable j % 5.  The
+// column decode and the gather from v are shared by the five rows.
 template <class T>
-__device__ __forceinline__ void dot_pk2(const T* __restrict__ ra, int na, const int* __restrict__ ca,
-                                        const T* __restrict__ rb, int nb, const int* __restrict__ cbl,
-                                        const T* __restrict__ v, int lane, T& sa, T& sb) {
+__device__ __forceinline__ void own_node5(const T* __restrict__ P0, int rs, int n, const int* __restrict__ cols,
+                                          const T* __restrict__ v, int lane, T acc[5]) {
   using V = typename PkVec<T>::type;
   constexpr int W = PkVec<T>::n;
-  const int n = max(na, nb);
+#pragma unroll 2
   for (int j0 = lane * W; j0 < n; j0 += 32 * W) {
-    V a, b;
-    const bool ia = j0 < na, ib = j0 < nb;
-    if (ia) a = __ldg(reinterpret_cast<const V*>(ra + j0));
-    if (ib) b = __ldg(reinterpret_cast<const V*>(rb + j0));
-    const T* av = reinterpret_cast<const T*>(&a);
-    const T* bv = reinterpret_cast<const T*>(&b);
+    V a[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) a[k] = __ldg(reinterpret_cast<const V*>(P0 + (size_t)k * rs + j0));
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      const int j = j0 + w, q = j / 5, l = j - 5 * q;
-      if (ia && j < na) sa = fma(av[w], v[__ldg(ca + q) + l], sa);
-      if (ib && j < nb) sb = fma(bv[w], v[__ldg(cbl + q) + l], sb);
+      const int j = j0 + w;
+      if (j < n) {
+        const int q = j / 5, l = j - 5 * q;
+        const T xv = v[__ldg(cols + q) + l];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[k] = fma(reinterpret_cast<const T*>(&a[k])[w], xv, acc[k]);
+      }
     }
   }
+}
+
+// Neighbour couplings of the 5 rows of one node: row k's pairs are the m = 5 * npairs
+// consecutive entries X0[k * ks + idx] (pair idx / 5, variable idx % 5); each pair's
+// packed info names the neighbour slot and the offset of its 5 entries in that
+// neighbour's boundary (vb, coefficient cb) or interior (vi, coefficient ci) vector.
+template <class T>
+__device__ __forceinline__ void cross_node5(const T* __restrict__ X0, long long ks, int m,
+                                            const int* __restrict__ info, const int* nbr_s, int nb, int ni,
+                                            const T* __restrict__ vb, T cb, const T* __restrict__ vi, T ci,
+                                            int lane, T acc[5]) {
+#pragma unroll 2
+  for (int idx = lane; idx < m; idx += 32) {
+    const int q = idx / 5, l = idx - 5 * q;
+    const int f = __ldg(info + q);
+    const int nbe = nbr_s[pinfo_slot(f)], off = pinfo_offset(f);
+    T g;
+    if (pinfo_interior(f)) {
+      if (!vi) continue;
+      g = ci * vi[(size_t)nbe * ni + off + l];
+    } else {
+      if (!vb) continue;
+      g = cb * vb[(size_t)nbe * nb + off + l];
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] = fma(__ldg(X0 + (size_t)k * ks + idx), g, acc[k]);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T pick5(const T acc[5], int k) {
+  return k == 0 ? acc[0] : k == 1 ? acc[1] : k == 2 ? acc[2] : k == 3 ? acc[3] : acc[4];
 }
 
 // Dense FP64 own blocks -> packed blocks of type T; entries outside the pattern must be
@@ -86,17 +119,21 @@ __global__ void __launch_bounds__(256) k_pack(Geo G, const double* __restrict__ 
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(status, -1, SC_PACK_VIOLATION);
 }
 
-// Interior pass with packed A_ib: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e).
+// Interior pass: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e), A_ib from the packed
+// own block and the neighbour couplings; one warp per interior node (its 5 rows).
 template <class T>
 __global__ void __launch_bounds__(256) k_cond_interior_pk(Geo G, const T* __restrict__ Apk, long long pstride,
     const int* __restrict__ row_off, const int* __restrict__ lptr, const int* __restrict__ list,
-    const T* __restrict__ Ainv, const int* __restrict__ iperm, const T* __restrict__ xb, double beta,
-    const double* __restrict__ Bfull, double alpha, T* __restrict__ u, const T* __restrict__ cross) {
+    const T* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
+    const int* __restrict__ pinfo, const T* __restrict__ Ainv, const int* __restrict__ iperm,
+    const T* __restrict__ xb, double beta, const double* __restrict__ Bfull, double alpha, T* __restrict__ u) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = blockIdx.x, ni = G.ni, nb = G.nb, lda = G.lda, ldi = G.ldi;
   T* v = reinterpret_cast<T*>(smem_raw);  // lda: x_e at the boundary columns
   T* t = v + lda;                         // ldi: right-hand side of the interior solve
+  __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
   for (int i = threadIdx.x; i < lda; i += blockDim.x) {
     T val = T(0);
     if (xb && i >= G.cb0 && i < G.cb0 + nb) val = xb[(size_t)e * nb + i - G.cb0];
@@ -105,26 +142,23 @@ __global__ void __launch_bounds__(256) k_cond_interior_pk(Geo G, const T* __rest
   for (int i = ni + threadIdx.x; i < ldi; i += blockDim.x) t[i] = T(0);
   __syncthreads();
   const T* Pe = Apk + (size_t)e * pstride;
-  for (int ra = 2 * warp; ra < ni; ra += 2 * nw) {
-    const int rb = ra + 1 < ni ? ra + 1 : ra;
-    T sa = T(0), sb = T(0);
+  const long long ks = (long long)G.NP * 5;
+  for (int p = warp; p < G.nin; p += nw) {
+    const int j = __ldg(iperm + p);
+    T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (xb) {
-      const int pa = ra / 5, pb = rb / 5;
-      dot_pk2(Pe + __ldg(row_off + ra), 5 * (__ldg(lptr + pa + 1) - __ldg(lptr + pa)), list + __ldg(lptr + pa),
-              Pe + __ldg(row_off + rb), 5 * (__ldg(lptr + pb + 1) - __ldg(lptr + pb)), list + __ldg(lptr + pb), v,
-              lane, sa, sb);
-      sa = wsum(sa); sb = wsum(sb);
-      sa += cross[(size_t)e * ni + ra];
-      sb += cross[(size_t)e * ni + rb];
+      const int l0 = __ldg(lptr + p), n = 5 * (__ldg(lptr + p + 1) - l0);
+      own_node5(Pe + __ldg(row_off + 5 * p), (n + 3) & ~3, n, list + l0, v, lane, acc);
+      const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
+      cross_node5(X + ((size_t)e * 5 * G.NP + q0) * 5, ks, 5 * (q1 - q0), pinfo + q0, nbr_s, nb, ni, xb, T(1),
+                  (const T*)nullptr, T(0), lane, acc);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] = wsum(acc[k]);
     }
-    if (lane == 0) {
-      T va = T(beta) * sa, vb = T(beta) * sb;
-      if (Bfull) {
-        va += T(alpha * Bfull[((size_t)e * G.nn + __ldg(iperm + ra / 5)) * 5 + ra % 5]);
-        vb += T(alpha * Bfull[((size_t)e * G.nn + __ldg(iperm + rb / 5)) * 5 + rb % 5]);
-      }
-      t[ra] = va;
-      if (rb != ra) t[rb] = vb;
+    if (lane < 5) {
+      T val = T(beta) * pick5(acc, lane);
+      if (Bfull) val += T(alpha * Bfull[((size_t)e * G.nn + j) * 5 + lane]);
+      t[5 * p + lane] = val;
     }
   }
   __syncthreads();
@@ -155,18 +189,22 @@ __global__ void __launch_bounds__(256) k_cond_interior_pk(Geo G, const T* __rest
   }
 }
 
-// Boundary pass with packed [A_bi A_bb]: y_e = gamma B_b,e + delta (A_bb x_b)_e - (A_bi u)_e
-// plus the neighbour couplings in `cross`.
+// Boundary pass: y_e = gamma B_b,e + delta (A_bb x_b)_e - (A_bi u)_e from the packed own
+// block and the neighbour couplings (delta x_b of boundary neighbours, -u of interior
+// ones); one warp per boundary node (its 5 rows).
 template <class T>
 __global__ void __launch_bounds__(256) k_cond_boundary_pk(Geo G, const T* __restrict__ Apk, long long pstride,
     const int* __restrict__ row_off, const int* __restrict__ lptr, const int* __restrict__ list,
-    const int* __restrict__ iperm, const T* __restrict__ xb, double delta, const double* __restrict__ Bfull,
-    double gamma_, const T* __restrict__ u, double* __restrict__ y, const T* __restrict__ cross) {
+    const T* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
+    const int* __restrict__ pinfo, const int* __restrict__ iperm, const T* __restrict__ xb, double delta,
+    const double* __restrict__ Bfull, double gamma_, const T* __restrict__ u, double* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int e = blockIdx.x, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, cb0 = G.cb0;
+  const int e = blockIdx.x, ni = G.ni, nb = G.nb, lda = G.lda, cb0 = G.cb0;
   T* v = reinterpret_cast<T*>(smem_raw);  // lda: [-u_e | 0 | delta x_e | 0]
+  __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   const T dT = T(delta);
+  if (threadIdx.x < 18) nbr_s[threadIdx.x] = nbr[e * 18 + threadIdx.x];
   for (int i = threadIdx.x; i < lda; i += blockDim.x) {
     T val = T(0);
     if (i < ni) { if (u) val = -u[(size_t)e * ni + i]; }
@@ -175,27 +213,24 @@ __global__ void __launch_bounds__(256) k_cond_boundary_pk(Geo G, const T* __rest
   }
   __syncthreads();
   const T* Pe = Apk + (size_t)e * pstride;
+  const long long ks = (long long)G.NP * 5;
   const bool need = xb || u;
-  for (int ra = ni + 2 * warp; ra < ne; ra += 2 * nw) {
-    const int rb = ra + 1 < ne ? ra + 1 : ra;
-    T sa = T(0), sb = T(0);
+  for (int p = G.nin + warp; p < G.nn; p += nw) {
+    const int j = __ldg(iperm + p);
+    T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (need) {
-      const int pa = ra / 5, pb = rb / 5;
-      dot_pk2(Pe + __ldg(row_off + ra), 5 * (__ldg(lptr + pa + 1) - __ldg(lptr + pa)), list + __ldg(lptr + pa),
-              Pe + __ldg(row_off + rb), 5 * (__ldg(lptr + pb + 1) - __ldg(lptr + pb)), list + __ldg(lptr + pb), v,
-              lane, sa, sb);
-      sa = wsum(sa); sb = wsum(sb);
-      sa += cross[(size_t)e * nb + ra - ni];
-      sb += cross[(size_t)e * nb + rb - ni];
+      const int l0 = __ldg(lptr + p), n = 5 * (__ldg(lptr + p + 1) - l0);
+      own_node5(Pe + __ldg(row_off + 5 * p), (n + 3) & ~3, n, list + l0, v, lane, acc);
+      const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
+      cross_node5(X + ((size_t)e * 5 * G.NP + q0) * 5, ks, 5 * (q1 - q0), pinfo + q0, nbr_s, nb, ni, xb, dT, u,
+                  T(-1), lane, acc);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] = wsum(acc[k]);
     }
-    if (lane == 0) {
-      double va = (double)sa, vb = (double)sb;
-      if (Bfull) {
-        va += gamma_ * Bfull[((size_t)e * G.nn + __ldg(iperm + ra / 5)) * 5 + ra % 5];
-        vb += gamma_ * Bfull[((size_t)e * G.nn + __ldg(iperm + rb / 5)) * 5 + rb % 5];
-      }
-      y[(size_t)e * nb + ra - ni] = va;
-      if (rb != ra) y[(size_t)e * nb + rb - ni] = vb;
+    if (lane < 5) {
+      double val = (double)pick5(acc, lane);
+      if (Bfull) val += gamma_ * Bfull[((size_t)e * G.nn + j) * 5 + lane];
+      y[(size_t)e * nb + 5 * (p - G.nin) + lane] = val;
     }
   }
 }
@@ -263,24 +298,24 @@ cudaError_t pack_own(sc_ctx* c) {
 }
 
 template <class T>
-cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* Ainv, const T* cross, const T* xb, double beta,
+cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* X, const T* Ainv, const T* xb, double beta,
                              const double* Bfull, double alpha, T* u) {
   const Geo& G = c->G;
   const size_t smem = (size_t)(G.lda + G.ldi) * sizeof(T);
   k_cond_interior_pk<T><<<G.K, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
-                                                       c->d_pk_list, Ainv, c->d_iperm, xb, beta, Bfull, alpha, u,
-                                                       cross);
+                                                       c->d_pk_list, X, c->d_nbr, c->d_pptr, c->d_pinfo, Ainv,
+                                                       c->d_iperm, xb, beta, Bfull, alpha, u);
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* cross, const T* xb, double delta, const double* Bfull,
+cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* X, const T* xb, double delta, const double* Bfull,
                              double gamma_, const T* u, double* y) {
   const Geo& G = c->G;
   const size_t smem = (size_t)G.lda * sizeof(T);
   k_cond_boundary_pk<T><<<G.K, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
-                                                       c->d_pk_list, c->d_iperm, xb, delta, Bfull, gamma_, u, y,
-                                                       cross);
+                                                       c->d_pk_list, X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm,
+                                                       xb, delta, Bfull, gamma_, u, y);
   return cudaGetLastError();
 }
 
