@@ -28,6 +28,8 @@
 #ifndef SC_H
 #define SC_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -173,6 +175,39 @@ sc_status sc_sizes(const sc_ctx* ctx, int* K, int* ne, int* ni, int* nb);
 sc_status sc_gemm_tf32(int batch, int M, int N, int K, float alpha, const float* A, long long strideA, int lda,
                        int transA, const float* B, long long strideB, int ldb, int transB, float beta, float* C,
                        long long strideC, int ldc, void* cuda_stream);
+
+/* ---- Learned correction of the block-Jacobi preconditioner ----------------------
+   Not in the paper (which preconditions GMRES on the condensed system with point Jacobi,
+   Sec. 4): a network maps 64 features of each boundary node k of each element to a 5 x 5
+   correction C_k of the diagonal node blocks of S_ee^-1.  Layout of the parameters
+   (shared by every call): weights W = [W1 (256 x 64) | W2 (256 x 256) | W3 (25 x 256)],
+   row-major, 88,320 values, kept as FP32 masters and as a BF16 copy (IEEE bfloat16 bit
+   patterns in uint16_t); biases b = [b1 (256) | b2 (256) | b3 (25)], FP32.  Layers:
+   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3; FP32 arithmetic.  All
+   pointers are device pointers; work is enqueued on cuda_stream and synchronised before
+   return.  SC_ERR_ARG for null pointers or bad sizes, SC_ERR_CUDA for launch failures. */
+
+/* y[n x 25] = net(X[n x 64]).  cache: NULL, or 4 n x 256 floats that receive z1, h1, z2,
+   h2 (pre- and post-activations) for sc_mlp_backward; with NULL the call allocates
+   temporaries on the stream. */
+sc_status sc_mlp_forward(const uint16_t* Wbf16, const float* bias, const float* X, int n, float* Y, float* cache,
+                         void* cuda_stream);
+
+/* Accumulate the gradients of sum(dY * y) into gW (88,320) and gb (537), FP32, from the
+   forward cache of the same X.  work: 2 n x 256 floats of scratch. */
+sc_status sc_mlp_backward(const uint16_t* Wbf16, const float* X, const float* cache, const float* dY, int n,
+                          float* gW, float* gb, float* work, void* cuda_stream);
+
+/* Loss of Y against targets T (both n x 25): mean over samples of
+   ||y - t||^2 / (||t||^2 + 1e-12).  Adds it to *loss_sum (device float) when non-NULL and
+   writes its gradient to dY (n x 25) when non-NULL. */
+sc_status sc_mlp_loss(const float* Y, const float* T, int n, float* dY, float* loss_sum, void* cuda_stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step >= 1 counts the
+   updates) on the FP32 masters W and bias with gradients gW, gb and moments m, v
+   (88,857 floats each: weights then biases); refreshes Wbf16 and zeroes gW and gb. */
+sc_status sc_mlp_adam(float* W, uint16_t* Wbf16, float* bias, float* gW, float* gb, float* m, float* v, int step,
+                      float lr, void* cuda_stream);
 
 /* ---- Measurement hooks (not part of the method; used by the benchmark) ---------- */
 

@@ -51,7 +51,8 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_set_state", "sc_set_timestep", "sc_assemble", "sc_condense", "sc_solve", "sc_get_rhs",
            "sc_apply_jacobian", "sc_get_jacobian_block", "sc_condensed_matvec", "sc_sizes",
            "sc_launch_count", "sc_profile_kernel", "sc_profile_read", "sc_kernel_work",
-           "sc_condensed_matvec_static", "sc_gemm_tf32"]
+           "sc_condensed_matvec_static", "sc_gemm_tf32", "sc_mlp_forward", "sc_mlp_backward", "sc_mlp_loss",
+           "sc_mlp_adam"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -90,6 +91,10 @@ def lib(build_if_missing: bool = True):
     L.sc_condensed_matvec_static.argtypes = [vp, dp, dp]
     ll, fl, ci = ctypes.c_longlong, ctypes.c_float, ctypes.c_int
     L.sc_gemm_tf32.argtypes = [ci, ci, ci, ci, fl, vp, ll, ci, ci, vp, ll, ci, ci, fl, vp, ll, ci, vp]
+    L.sc_mlp_forward.argtypes = [vp, vp, vp, ci, vp, vp, vp]
+    L.sc_mlp_backward.argtypes = [vp, vp, vp, vp, ci, vp, vp, vp, vp]
+    L.sc_mlp_loss.argtypes = [vp, vp, ci, vp, vp, vp]
+    L.sc_mlp_adam.argtypes = [vp, vp, vp, vp, vp, vp, vp, ci, fl, vp]
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
@@ -261,3 +266,101 @@ def sc_gemm_tf32(A, B, C, alpha=1.0, beta=0.0, stream=None, trans_a=False, trans
     if s != SC_OK:
         raise SCError(s, "sc_gemm_tf32 failed")
     return C
+
+
+# ---- learned block-Jacobi correction: the network ---------------------------------
+MLP_IN, MLP_H, MLP_OUT = 64, 256, 25
+MLP_NW = MLP_H * MLP_IN + MLP_H * MLP_H + MLP_OUT * MLP_H
+MLP_NB = 2 * MLP_H + MLP_OUT
+
+
+def bf16_bits(x):
+    """IEEE bfloat16 bit patterns (round to nearest even) of a float array, as uint16."""
+    import numpy as np
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def bf16_values(bits):
+    """float32 values of bfloat16 bit patterns."""
+    import numpy as np
+    return (np.asarray(bits, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+class MLP:
+    """Device parameters of the correction network and the C-ABI calls on them.
+
+    W: [W1 | W2 | W3] FP32 masters and their BF16 copy, b: [b1 | b2 | b3]; gradients and
+    Adam moments alongside.  Every computation runs in the library's kernels."""
+
+    def __init__(self, W, b, stream=None):
+        import numpy as np
+        import torch
+        self._L = lib()
+        self.stream = stream or 0
+        W = np.asarray(W, dtype=np.float32).reshape(-1)
+        b = np.asarray(b, dtype=np.float32).reshape(-1)
+        if W.size != MLP_NW or b.size != MLP_NB:
+            raise ValueError("wrong parameter sizes")
+        dev = "cuda"
+        self.W = torch.tensor(W, device=dev)
+        self.Wh = torch.tensor(bf16_bits(W).view(np.int16), device=dev)
+        self.b = torch.tensor(b, device=dev)
+        self.gW = torch.zeros(MLP_NW, device=dev)
+        self.gb = torch.zeros(MLP_NB, device=dev)
+        self.m = torch.zeros(MLP_NW + MLP_NB, device=dev)
+        self.v = torch.zeros(MLP_NW + MLP_NB, device=dev)
+        self.step = 0
+
+    def _ck(self, s, what):
+        if s != SC_OK:
+            raise SCError(s, what)
+
+    def forward(self, X, Y, cache=None):
+        self._ck(self._L.sc_mlp_forward(self.Wh.data_ptr(), self.b.data_ptr(), X.data_ptr(), X.shape[0], Y.data_ptr(),
+                                        cache.data_ptr() if cache is not None else None,
+                                        ctypes.c_void_p(self.stream)), "sc_mlp_forward")
+        return Y
+
+    def backward(self, X, cache, dY, work):
+        self._ck(self._L.sc_mlp_backward(self.Wh.data_ptr(), X.data_ptr(), cache.data_ptr(), dY.data_ptr(),
+                                         X.shape[0], self.gW.data_ptr(), self.gb.data_ptr(), work.data_ptr(),
+                                         ctypes.c_void_p(self.stream)), "sc_mlp_backward")
+
+    def loss(self, Y, T, dY=None, loss_sum=None):
+        self._ck(self._L.sc_mlp_loss(Y.data_ptr(), T.data_ptr(), Y.shape[0],
+                                     dY.data_ptr() if dY is not None else None,
+                                     loss_sum.data_ptr() if loss_sum is not None else None,
+                                     ctypes.c_void_p(self.stream)), "sc_mlp_loss")
+
+    def adam(self, lr):
+        self.step += 1
+        self._ck(self._L.sc_mlp_adam(self.W.data_ptr(), self.Wh.data_ptr(), self.b.data_ptr(), self.gW.data_ptr(),
+                                     self.gb.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.step,
+                                     ctypes.c_float(lr), ctypes.c_void_p(self.stream)), "sc_mlp_adam")
+
+    def train(self, X, T, epochs, batch, lr, seed=0):
+        """Mini-batch Adam on device features X [n, 64] and targets T [n, 25]; returns the
+        per-epoch mean loss."""
+        import numpy as np
+        import torch
+        n = X.shape[0]
+        cache = torch.empty(4 * batch * MLP_H, device=X.device)
+        work = torch.empty(2 * batch * MLP_H, device=X.device)
+        Y = torch.empty(batch, MLP_OUT, device=X.device)
+        dY = torch.empty(batch, MLP_OUT, device=X.device)
+        acc = torch.zeros(1, device=X.device)
+        rng = np.random.default_rng(seed)
+        starts = list(range(0, n - batch + 1, batch))  # fixed batches, visited in a new order each epoch
+        hist = []
+        for _ in range(epochs):
+            acc.zero_()
+            for s0 in rng.permutation(starts):
+                xb, tb = X[s0:s0 + batch], T[s0:s0 + batch]
+                self.forward(xb, Y, cache)
+                self.loss(Y, tb, dY, acc)
+                self.backward(xb, cache, dY, work)
+                self.adam(lr)
+            hist.append(float(acc.item()) / max(len(starts), 1))
+        return hist
