@@ -48,7 +48,7 @@ typedef enum {
 } sc_status;
 
 enum { SC_PREC_FP64 = 0, SC_PREC_MIXED = 1 };
-enum { SC_PC_BLOCK_JACOBI = 0, SC_PC_NONE = 1 };
+enum { SC_PC_BLOCK_JACOBI = 0, SC_PC_NONE = 1, SC_PC_LEARNED = 2 };
 
 /* Physics and solver settings (App. B parameters; solver choices of the build). */
 typedef struct {
@@ -68,6 +68,9 @@ typedef struct {
   double inner_tol;      /* mixed arm: relative tolerance of each inner condensed solve */
   int tensor_cores;      /* mixed arm: 1 = element Schur products and the LU trailing updates
                             of S_ee on the TF32 tensor cores (tcgen05), 0 = FP32 CUDA cores */
+  double learned_min_reduction;  /* SC_PC_LEARNED: a GMRES restart cycle that reduces the
+                            condensed residual by less than this factor switches the rest of
+                            the solve to plain block Jacobi (10) */
 } sc_config;
 
 /* Per-solve statistics filled by sc_solve. */
@@ -78,6 +81,7 @@ typedef struct {
   double cond_rel_residual; /* last condensed residual estimate / ||B||_2 */
   double ms_rhs, ms_gmres, ms_backsub, ms_refine;  /* device time per phase */
   int first_bad_element;    /* first element with a singular block, or -1 */
+  int learned_fallbacks;    /* SC_PC_LEARNED: 1 if the solve fell back to block Jacobi */
 } sc_solve_stats;
 
 /* Fill *cfg with the defaults listed above (Re = 1600, Ma = 0.1, FP64, block Jacobi,
@@ -208,6 +212,35 @@ sc_status sc_mlp_loss(const float* Y, const float* T, int n, float* dY, float* l
    (88,857 floats each: weights then biases); refreshes Wbf16 and zeroes gW and gb. */
 sc_status sc_mlp_adam(float* W, uint16_t* Wbf16, float* bias, float* gW, float* gb, float* m, float* v, int step,
                       float lr, void* cuda_stream);
+
+/* Features of the learned correction for every (element e, boundary node k) of the
+   condensed system, samples ordered element by element and boundary node by boundary
+   node (the condensed order): F[s][64] = q_k over free-stream scales (rho, rho u, rho v,
+   rho w over 1, rho E over p_inf/(gamma-1) + 1/2) | [S_ee]_kk / ||.||_F (row-major 5 x 5)
+   | S_(k,k') / ||.||_F with k' the node at the same point in the neighbour across the
+   lowest-index face of e containing k (order -x,+x,-y,+y,-z,+z) | Ma, Re/1000,
+   dt/(Ma h), N | 0 x 5; snorm[s] = ||[S_ee]_kk||_F.  After sc_condense on the mixed arm
+   (SC_ERR_STATE otherwise).  Device pointers, K * nbn * 64 and K * nbn floats. */
+sc_status sc_learned_features(sc_ctx* ctx, float* F, float* snorm);
+
+/* Training targets T[s][25] = ([S_patch^-1]_kk - [S_ee^-1]_kk) ||[S_ee]_kk||_F, S_patch the
+   condensed matrix on the boundary dofs of e and of the neighbour of the features.  Forms
+   the dense condensed matrix column by column with the condensed operator, so only for
+   small meshes ((K nb)^2 doubles <= 16 GB, else SC_ERR_ARG).  After sc_condense on the
+   mixed arm.  Device pointer, K * nbn * 25 floats. */
+sc_status sc_learned_targets(sc_ctx* ctx, float* T);
+
+/* Network parameters for SC_PC_LEARNED (device pointers, layout of sc_mlp_forward; copied
+   into the context).  With precond = SC_PC_LEARNED, sc_condense evaluates the network on
+   the features and the preconditioner becomes z_e = S_ee^-1 v_e + C_k v_k per boundary
+   node, C_k = y_k / ||[S_ee]_kk||_F. */
+sc_status sc_set_learned_weights(sc_ctx* ctx, const uint16_t* Wbf16, const float* bias);
+
+/* Measurement hook for SC_PC_LEARNED: after sc_condense, replace the corrections by
+   scale * Ck (device, K * nbn * 25 floats, C_k row-major per sample, unscaled: the
+   matrices added to the diagonal node blocks of S_ee^-1), e.g. the exact targets divided
+   by ||[S_ee]_kk||_F, to measure what a perfect network would give. */
+sc_status sc_set_learned_correction(sc_ctx* ctx, const float* Ck, float scale);
 
 /* ---- Measurement hooks (not part of the method; used by the benchmark) ---------- */
 

@@ -93,14 +93,18 @@ void free_all(sc_ctx* c) {
                     &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk, &c->Sls};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
-                   &c->Apk32, &c->Sls32};
+                   &c->Apk32, &c->Sls32, &c->Sdiag, &c->Cpl, &c->Feat, &c->Snorm, &c->Ynet, &c->Hbuf,
+                   &c->Ck, &c->Wbias};
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
   c->packed = false;
+  if (c->Wbf16) cudaFree(c->Wbf16);
+  c->Wbf16 = nullptr;
+  c->Sdiag_valid = c->weights_set = c->learned_on = false;
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
-                 &c->d_pk_row_off, &c->d_pk_pos};
+                 &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
 }
 
@@ -187,7 +191,7 @@ sc_status sc_default_config(sc_config* cfg) {
   cfg->Ts = 110.4 / 288.15; cfg->sutherland = 1; cfg->roe_delta = 0.05;
   cfg->precision = SC_PREC_FP64; cfg->precond = SC_PC_BLOCK_JACOBI;
   cfg->gmres_restart = 30; cfg->gmres_max_iters = 4000; cfg->max_refine = 10;
-  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4; cfg->tensor_cores = 1;
+  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4; cfg->tensor_cores = 1; cfg->learned_min_reduction = 10.0;
   return SC_OK;
 }
 
@@ -220,6 +224,8 @@ const char* sc_last_error(const sc_ctx* c) { return c ? c->err.c_str() : "null c
 sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   if (!c) return SC_ERR_ARG;
   if (n < 1 || n > 32 || N < 2 || N > 4 || !(L > 0)) return fail(c, SC_ERR_ARG, "mesh: need n in [1,32], N in [2,4], L > 0");
+  if (c->cfg.precond == SC_PC_LEARNED && c->cfg.precision != SC_PREC_MIXED)
+    return fail(c, SC_ERR_ARG, "the learned correction runs on the mixed arm's FP32 blocks");
   cudaStreamSynchronize(c->stream);
   free_all(c);
   c->has_mesh = c->has_state = c->assembled = c->condensed = false;
@@ -272,6 +278,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   }
   build_pattern(c);
   sc::build_packed_pattern(c);
+  sc::build_learned_tables(c);
   const size_t nodes = (size_t)G.K * G.nn, dofs = nodes * 5;
   const size_t n1 = (size_t)G.K * G.nb;
   const int m = c->cfg.gmres_restart;
@@ -306,7 +313,15 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pinfo, np));
   A(dalloc(&c->d_pk_lptr, c->pk_lptr.size())); A(dalloc(&c->d_pk_list, c->pk_list.size()));
   A(dalloc(&c->d_pk_row_off, c->pk_row_off.size())); A(dalloc(&c->d_pk_pos, c->pk_pos.size()));
+  A(dalloc(&c->d_lface, G.nbn)); A(dalloc(&c->d_lmirror, G.nbn));
   if (c->cfg.precision == SC_PREC_MIXED) {
+    const size_t nsmp = (size_t)G.K * G.nbn;
+    A(dalloc(&c->Sdiag, nsmp * 25)); A(dalloc(&c->Cpl, nsmp * 25));
+    if (c->cfg.precond == SC_PC_LEARNED) {
+      A(dalloc(&c->Feat, nsmp * 64)); A(dalloc(&c->Snorm, nsmp)); A(dalloc(&c->Ynet, nsmp * 25));
+      A(dalloc(&c->Hbuf, nsmp * 512)); A(dalloc(&c->Ck, nsmp * 25)); A(dalloc(&c->Wbias, (size_t)sc::kMlpBiases));
+      A(dalloc(&c->Wbf16, (size_t)sc::kMlpWeights));
+    }
     A(dalloc(&c->Apk32, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls32, sc::solve_layout_elems(G)));
   } else {
     A(dalloc(&c->Apk, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls, sc::solve_layout_elems(G)));
@@ -331,6 +346,8 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   }
   SC_CUDA(cudaMemcpy(c->d_pinfo, pinfo.data(), np * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(sc::upload_packed_pattern(c));
+  SC_CUDA(cudaMemcpy(c->d_lface, c->l_face.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_lmirror, c->l_mirror.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   // the alignment padding of the element blocks (dense and packed) must read as zero
   if (c->Apk) SC_CUDA(cudaMemset(c->Apk, 0, (size_t)G.K * c->pk_stride * sizeof(double)));
   if (c->Apk32) SC_CUDA(cudaMemset(c->Apk32, 0, (size_t)G.K * c->pk_stride * sizeof(float)));
@@ -406,7 +423,11 @@ sc_status sc_condense(sc_ctx* c) {
   if (!c->assembled) return fail(c, SC_ERR_STATE, "condense before assemble");
   const int minus1 = -1;
   SC_CUDA(cudaMemcpyAsync(c->d_status, &minus1, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  if (c->cfg.precond == SC_PC_LEARNED && !c->weights_set)
+    return fail(c, SC_ERR_STATE, "learned preconditioner without weights (sc_set_learned_weights)");
+  c->Sdiag_valid = false;
   SC_CUDA(sc::launch_condense(c));
+  if (c->cfg.precond == SC_PC_LEARNED) SC_CUDA(sc::learned_correction(c));
   int bad = -1;
   SC_CUDA(cudaMemcpyAsync(&bad, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
@@ -508,6 +529,7 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
   double resid = beta;
   bool ok = beta <= abs_tol;
   while (!ok && iters < max_iters) {
+    const double beta_cycle = beta;
     SC_CUDA(sc::vec_axpby(c, c->V, 1.0 / beta, c->Rb, 0.0, n1));
     std::fill(gv.begin(), gv.end(), 0.0); gv[0] = beta;
     int k = 0;
@@ -576,6 +598,12 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
     resid = beta;
     if (!std::isfinite(beta)) return fail(c, SC_ERR_NONFINITE, "non-finite condensed residual");
     if (beta <= abs_tol) ok = true;
+    // learned correction: a restart cycle that reduces the residual by less than the
+    // configured factor hands the rest of the solve to plain block Jacobi
+    if (!ok && c->learned_on && beta_cycle < c->cfg.learned_min_reduction * beta) {
+      c->learned_on = false;
+      c->learned_fallbacks++;
+    }
   }
   *iters_out = iters;
   *resid_out = resid;
@@ -623,6 +651,8 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
   cudaEvent_t* ev = c->ev;
   double* const hs = c->Hd + 2 * (c->restart_alloc + 1) + 2;
   double* xout = on_device ? dQ : c->Xfull;
+  c->learned_on = c->cfg.precond == SC_PC_LEARNED && c->weights_set;
+  c->learned_fallbacks = 0;
   SC_CUDA(cudaEventRecord(ev[0], c->stream));
   const double bnorm = dnorm2(c, c->B, dofs, hs);
   const double target = c->cfg.rel_tol * bnorm;
@@ -669,6 +699,7 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
   cudaEventElapsedTime(&t02, ev[0], ev[2]);
   S.ms_gmres = t02;
   S.gmres_iters = iters;
+  S.learned_fallbacks = c->learned_fallbacks;
   S.cond_rel_residual = bnorm > 0 ? resid / bnorm : 0.0;
   S.rel_residual = bnorm > 0 ? rn / bnorm : 0.0;
   if (st) *st = S;

@@ -431,25 +431,11 @@ __global__ void __launch_bounds__(256) k_solve_prep(int n, const T* __restrict__
   }
 }
 
-// z = (P^T L U)^-1 v, one warp per element (4 per CTA), lane r owns row 32 b + r of
-// every block; the running vector (v, then x, then z) sits in shared memory.
-// Arithmetic in the factor precision T; v in double, outputs z (double) and / or zt (T).
+// In-place (L U)^-1 s of one element's factors Le in the solve layout, by one warp: lane r
+// owns row 32 b + r of every block; s (shared memory, nblk * 32 entries, zero beyond n)
+// holds the permuted right-hand side on entry and the solution on exit.
 template <class T>
-__global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const T* __restrict__ LS, long long lsstride,
-                                                  int npad, const int* __restrict__ rowperm,
-                                                  const double* __restrict__ v, double* __restrict__ z,
-                                                  T* __restrict__ zt, int nelem) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  const int e = blockIdx.x * 4 + warp;
-  if (e >= nelem) return;  // whole warps leave; no block-level barrier follows
-  const int ls = nblk * 32;
-  T* s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * ls;
-  const T* Le = LS + (long long)e * lsstride;
-  const int* rp = rowperm + (long long)e * n;
-  const double* ve = v + (long long)e * n;
-  for (int i = lane; i < ls; i += 32) s[i] = i < n ? (T)ve[__ldg(rp + i)] : T(0);
-  __syncwarp();
+__device__ __forceinline__ void ls_solve_warp(int n, int nblk, const T* __restrict__ Le, int npad, T* s, int lane) {
   const int nq = npad / 4;
   for (int b = 0; b < nblk; ++b) {  // forward: x_b = L_bb^-1 v_b - M_b x_{<b}
     const int i0 = 32 * b, R = i0 + lane;
@@ -505,10 +491,65 @@ __global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const T* __re
     if (R < n) s[R] = d - (a0 + a1);
     __syncwarp();
   }
+}
+
+// z = (P^T L U)^-1 v, one warp per element (4 per CTA); the running vector (v, then x,
+// then z) sits in shared memory.  Arithmetic in the factor precision T; v in double,
+// outputs z (double) and / or zt (T).  Ck (or null): a 5 x 5 correction per boundary node
+// added as z_k += C_k v_k (the learned correction of the block-Jacobi inverse).
+template <class T>
+__global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const T* __restrict__ LS, long long lsstride,
+                                                  int npad, const int* __restrict__ rowperm,
+                                                  const double* __restrict__ v, double* __restrict__ z,
+                                                  T* __restrict__ zt, int nelem, const float* __restrict__ Ck) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int e = blockIdx.x * 4 + warp;
+  if (e >= nelem) return;  // whole warps leave; no block-level barrier follows
+  const int ls = nblk * 32;
+  T* s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * ls;
+  const int* rp = rowperm + (long long)e * n;
+  const double* ve = v + (long long)e * n;
+  for (int i = lane; i < ls; i += 32) s[i] = i < n ? (T)ve[__ldg(rp + i)] : T(0);
+  __syncwarp();
+  ls_solve_warp<T>(n, nblk, LS + (long long)e * lsstride, npad, s, lane);
   for (int i = lane; i < n; i += 32) {
-    if (z) z[(long long)e * n + i] = (double)s[i];
-    if (zt) zt[(long long)e * n + i] = s[i];
+    T val = s[i];
+    if (Ck) {
+      const int a = i / 5, k = i - 5 * a;
+      const float* C = Ck + ((long long)e * (n / 5) + a) * 25 + 5 * k;
+      const double* va = ve + 5 * a;
+      float c = 0.f;
+#pragma unroll
+      for (int l = 0; l < 5; ++l) c = fmaf(C[l], (float)va[l], c);
+      val += (T)c;
+    }
+    if (z) z[(long long)e * n + i] = (double)val;
+    if (zt) zt[(long long)e * n + i] = val;
   }
+}
+
+// Diagonal node blocks of inverses: warp w solves A_m x = e_c for the matrix m = mat[w]
+// and column c = 5 node[w] + var[w], and stores x at rows 5 node .. 5 node + 4 as column
+// var of the 5 x 5 block out[w / 5] (w enumerates (sample, var) pairs, var fastest).
+template <class T>
+__global__ void __launch_bounds__(128) k_unit_solve(int n, int nblk, const T* __restrict__ LS, long long lsstride,
+                                                    int npad, const int* __restrict__ rowperm,
+                                                    const int* __restrict__ mat, const int* __restrict__ node,
+                                                    int nw_total, float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int w = blockIdx.x * 4 + warp;
+  if (w >= nw_total) return;
+  const int smp = w / 5, var = w - 5 * smp;
+  const int m = mat[smp], a = node[smp], col = 5 * a + var;
+  const int ls = nblk * 32;
+  T* s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * ls;
+  const int* rp = rowperm + (long long)m * n;
+  for (int i = lane; i < ls; i += 32) s[i] = (i < n && __ldg(rp + i) == col) ? T(1) : T(0);
+  __syncwarp();
+  ls_solve_warp<T>(n, nblk, LS + (long long)m * lsstride, npad, s, lane);
+  if (lane < 5) out[(long long)smp * 25 + 5 * lane + var] = (float)s[5 * a + lane];
 }
 
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
@@ -601,7 +642,14 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
                                            (long long)ni * nb, nb, T(1), See, (long long)nb * lds, lds);
     }
   }
-  if (c->cfg.precond == SC_PC_BLOCK_JACOBI) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->Sdiag) {  // diagonal node blocks of S_ee for the learned correction's features
+      err = extract_sdiag(c, See);
+      if (err != cudaSuccess) return err;
+      c->Sdiag_valid = true;
+    }
+  }
+  if (c->cfg.precond != SC_PC_NONE) {
     bool done = false;
     if constexpr (std::is_same<T, float>::value) {
       if (tc) {
@@ -661,14 +709,14 @@ cudaError_t lu_solve_t(sc_ctx* c, const T* LS, const double* v, double* z, T* zt
   ProfScope ps(c, SCK_LU_SOLVE);
   const size_t smem = (size_t)4 * ls_nblk(G) * 32 * sizeof(T);
   k_lu_solve<T><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G), c->rowperm,
-                                                        v, z, zt, G.K);
+                                                        v, z, zt, G.K, c->learned_on ? c->Ck : nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
   const Geo& G = c->G;
   const size_t n1 = (size_t)G.K * G.nb;
-  if (c->cfg.precond != SC_PC_BLOCK_JACOBI) {
+  if (c->cfg.precond == SC_PC_NONE) {
     return cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   }
   return lu_solve_t<double>(c, c->Sls, v, z, nullptr);
@@ -678,7 +726,7 @@ cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
 cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
   const Geo& G = c->G;
   const size_t n1 = (size_t)G.K * G.nb;
-  if (c->cfg.precond != SC_PC_BLOCK_JACOBI) {
+  if (c->cfg.precond == SC_PC_NONE) {
     cudaError_t e = cudaSuccess;
     if (z) e = cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess && zf) e = vec_to_float(c, zf, v, n1);
@@ -688,5 +736,39 @@ cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
 }
 
 size_t solve_layout_elems(const Geo& G) { return (size_t)G.K * ls_stride(G); }
+long long solve_layout_stride(const Geo& G) { return ls_stride(G); }
+
+// LU with partial pivoting of `batch` FP32 n x n blocks (row-major, lda, `stride` apart),
+// then the gather permutation and the partitioned-inverse solve layout LS.
+cudaError_t factor_batch32(sc_ctx* c, float* A, int n, int lda, long long stride, int batch, int* piv, int* rowperm,
+                           float* LS, int* status) {
+  const size_t smem = (size_t)n * (PW + 1) * sizeof(float);
+  cudaError_t err = cudaFuncSetAttribute(k_lu<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  count_launch(c, 4);
+  k_lu<float><<<batch, 256, smem, c->stream>>>(n, A, stride, lda, piv, status);
+  k_piv_to_perm<<<cdiv(batch, 128), 128, 0, c->stream>>>(n, piv, rowperm, batch);
+  const size_t dsm = (size_t)8 * 2 * 32 * 33 * sizeof(float);
+  err = cudaFuncSetAttribute(k_diag_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+  if (err != cudaSuccess) return err;
+  k_diag_inv<float><<<batch, 256, dsm, c->stream>>>(n, A, stride, lda);
+  const int nblk = (n + 31) / 32, npad = (n + 3) & ~3;
+  k_solve_prep<float><<<dim3(nblk, batch), 256, 0, c->stream>>>(n, A, stride, lda, LS, (long long)nblk * 32 * npad,
+                                                               npad);
+  return cudaGetLastError();
+}
+
+// Diagonal node blocks [A_m^-1]_(node, node) for nsmp (matrix, node) samples.
+cudaError_t unit_solve32(sc_ctx* c, int n, const float* LS, long long lsstride, const int* rowperm, const int* mat,
+                         const int* node, int nsmp, float* out) {
+  const int nblk = (n + 31) / 32, npad = (n + 3) & ~3;
+  const size_t smem = (size_t)4 * nblk * 32 * sizeof(float);
+  cudaError_t err = cudaFuncSetAttribute(k_unit_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  count_launch(c);
+  k_unit_solve<float><<<cdiv((long long)nsmp * 5, 4), 128, smem, c->stream>>>(n, nblk, LS, lsstride, npad, rowperm,
+                                                                              mat, node, nsmp * 5, out);
+  return cudaGetLastError();
+}
 
 }  // namespace sc

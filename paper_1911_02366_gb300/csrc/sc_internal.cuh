@@ -278,6 +278,14 @@ struct sc_ctx {
   double* Sls = nullptr;
   float* Sls32 = nullptr;
   bool packed = false;     // packed blocks match the assembled Jacobian
+  // learned correction of the block-Jacobi preconditioner (mixed arm)
+  std::vector<int> l_face, l_mirror;  // per boundary position: face, co-located position
+  int *d_lface = nullptr, *d_lmirror = nullptr;
+  float *Sdiag = nullptr, *Cpl = nullptr;  // [K nbn][25]: [S_ee]_kk, S_(k,k')
+  float *Feat = nullptr, *Snorm = nullptr, *Ynet = nullptr, *Hbuf = nullptr, *Ck = nullptr, *Wbias = nullptr;
+  uint16_t* Wbf16 = nullptr;
+  bool Sdiag_valid = false, weights_set = false, learned_on = false;
+  int learned_fallbacks = 0;
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};
   // measurement hooks: kernel launches since creation, and optional CUDA-event timing
@@ -352,6 +360,18 @@ cudaError_t gemm_tf32(cudaStream_t stream, int M, int N, int K, float alpha, con
                       int ldc, int batch, int* status);
 size_t solve_layout_elems(const Geo& G);
 void build_packed_pattern(sc_ctx* c);
+long long solve_layout_stride(const Geo& G);
+cudaError_t factor_batch32(sc_ctx* c, float* A, int n, int lda, long long stride, int batch, int* piv, int* rowperm,
+                           float* LS, int* status);
+cudaError_t unit_solve32(sc_ctx* c, int n, const float* LS, long long lsstride, const int* rowperm, const int* mat,
+                         const int* node, int nsmp, float* out);
+void build_learned_tables(sc_ctx* c);
+cudaError_t extract_sdiag(sc_ctx* c, const float* See);
+cudaError_t learned_features(sc_ctx* c, float* F, float* snorm);
+cudaError_t learned_correction(sc_ctx* c);
+constexpr int kMlpWeights = 256 * 64 + 256 * 256 + 25 * 256, kMlpBiases = 2 * 256 + 25;
+cudaError_t mlp_forward(cudaStream_t st, const uint16_t* Wbf16, const float* bias, const float* X, int n, float* Y,
+                        float* h1, float* h2);
 cudaError_t upload_packed_pattern(sc_ctx* c);
 cudaError_t pack_own(sc_ctx* c);
 template <class T>

@@ -164,6 +164,25 @@ cudaError_t gemm(cudaStream_t st, int M, int N, int K, const TA_* A, int lda, co
 
 }  // namespace
 
+namespace sc {
+
+// Inference: Y = net(X) with the hidden activations in h1, h2 (n x 256 each).
+cudaError_t mlp_forward(cudaStream_t st, const uint16_t* Wbf16, const float* bias, const float* X, int n, float* Y,
+                        float* h1, float* h2) {
+  const __nv_bfloat16* W = reinterpret_cast<const __nv_bfloat16*>(Wbf16);
+  cudaError_t e = gemm<float, __nv_bfloat16, false, true, EPI_BIAS_RELU>(st, n, NH, NI, X, NI, W, NI, h1, NH, bias,
+                                                                         nullptr, nullptr);
+  if (e == cudaSuccess)
+    e = gemm<float, __nv_bfloat16, false, true, EPI_BIAS_RELU>(st, n, NH, NH, h1, NH, W + OFF_W2, NH, h2, NH,
+                                                               bias + OFF_B2, nullptr, nullptr);
+  if (e == cudaSuccess)
+    e = gemm<float, __nv_bfloat16, false, true, EPI_BIAS>(st, n, NO, NH, h2, NH, W + OFF_W3, NH, Y, NO, bias + OFF_B3,
+                                                          nullptr, nullptr);
+  return e;
+}
+
+}  // namespace sc
+
 extern "C" {
 
 sc_status sc_mlp_forward(const uint16_t* Wbf16, const float* bias, const float* X, int n, float* Y, float* cache,

@@ -16,7 +16,7 @@ from . import build as _build
 SC_OK, SC_ERR_ARG, SC_ERR_CUDA, SC_ERR_OOM, SC_ERR_STATE = 0, 1, 2, 3, 4
 SC_ERR_SINGULAR_BLOCK, SC_ERR_NONFINITE, SC_ERR_NOT_CONVERGED = 5, 6, 7
 SC_PREC_FP64, SC_PREC_MIXED = 0, 1
-SC_PC_BLOCK_JACOBI, SC_PC_NONE = 0, 1
+SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED = 0, 1, 2
 
 _lib = None
 
@@ -33,7 +33,7 @@ class sc_config(ctypes.Structure):
                 ("roe_delta", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("gmres_max_iters", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("rel_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("tensor_cores", ctypes.c_int)]
+                ("tensor_cores", ctypes.c_int), ("learned_min_reduction", ctypes.c_double)]
 
 
 class sc_solve_stats(ctypes.Structure):
@@ -41,7 +41,7 @@ class sc_solve_stats(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("cond_rel_residual", ctypes.c_double),
                 ("ms_rhs", ctypes.c_double), ("ms_gmres", ctypes.c_double),
                 ("ms_backsub", ctypes.c_double), ("ms_refine", ctypes.c_double),
-                ("first_bad_element", ctypes.c_int)]
+                ("first_bad_element", ctypes.c_int), ("learned_fallbacks", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -52,7 +52,7 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_apply_jacobian", "sc_get_jacobian_block", "sc_condensed_matvec", "sc_sizes",
            "sc_launch_count", "sc_profile_kernel", "sc_profile_read", "sc_kernel_work",
            "sc_condensed_matvec_static", "sc_gemm_tf32", "sc_mlp_forward", "sc_mlp_backward", "sc_mlp_loss",
-           "sc_mlp_adam"]
+           "sc_mlp_adam", "sc_learned_features", "sc_learned_targets", "sc_set_learned_weights", "sc_set_learned_correction"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -95,6 +95,10 @@ def lib(build_if_missing: bool = True):
     L.sc_mlp_backward.argtypes = [vp, vp, vp, vp, ci, vp, vp, vp, vp]
     L.sc_mlp_loss.argtypes = [vp, vp, ci, vp, vp, vp]
     L.sc_mlp_adam.argtypes = [vp, vp, vp, vp, vp, vp, vp, ci, fl, vp]
+    L.sc_learned_features.argtypes = [vp, vp, vp]
+    L.sc_learned_targets.argtypes = [vp, vp]
+    L.sc_set_learned_weights.argtypes = [vp, vp, vp]
+    L.sc_set_learned_correction.argtypes = [vp, vp, ctypes.c_float]
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
@@ -239,6 +243,24 @@ class Context:
         f = ctypes.c_double(); b = ctypes.c_double()
         self._check(self._L.sc_kernel_work(self.h, kernel_id, ctypes.byref(f), ctypes.byref(b)))
         return f.value, b.value
+
+    def sc_learned_features(self, F, snorm):
+        """Features [K*nbn, 64] and ||[S_ee]_kk||_F [K*nbn] (float32 device tensors)."""
+        self._check(self._L.sc_learned_features(self.h, F.data_ptr(), snorm.data_ptr()))
+        return F, snorm
+
+    def sc_learned_targets(self, T):
+        """Training targets [K*nbn, 25] (float32 device tensor); small meshes only."""
+        self._check(self._L.sc_learned_targets(self.h, T.data_ptr()))
+        return T
+
+    def sc_set_learned_weights(self, net):
+        """Copy the parameters of an MLP (its BF16 weights and biases) into the context."""
+        self._check(self._L.sc_set_learned_weights(self.h, net.Wh.data_ptr(), net.b.data_ptr()))
+
+    def sc_set_learned_correction(self, Ck, scale=1.0):
+        """Replace the per-node corrections by scale * Ck ([K*nbn, 25] float32 device)."""
+        self._check(self._L.sc_set_learned_correction(self.h, Ck.data_ptr(), ctypes.c_float(scale)))
 
     def sc_condensed_matvec_static(self, xb, yb):
         """S x_b without any allocation in the call (fixed 8 MiB device scratch)."""
