@@ -5,7 +5,7 @@ workload (2,560,000 DOF, CFL 50): residual + Jacobian assembly, static condensat
 (A_ii^-1, element Schur blocks, block-Jacobi factors), condensed right-hand side,
 GMRES to a global relative residual of 1e-8, back-substitution.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--arm fp64|mixed] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--arm fp64|mixed|learned] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  N > 1 runs independent replicas (one per GPU); the
 path has no collective.  `--impl reference` times the FP64 CPU oracle on a bounded
@@ -116,6 +116,45 @@ def gather_max(world, x):
     return float(t.item())
 
 
+def train_correction(args, stream):
+    """The learned arm's network, trained before the timed region on systems the method
+    forms: 3^3-element N = 4 Taylor-Green states, seeds 100.., Ma 0.05..0.3; features and
+    targets from the library, mini-batch Adam through its kernels."""
+    import torch
+    from paper_1911_02366_gb300 import sc
+    rng = np.random.default_rng(0)
+    Fs, Ts = [], []
+    t0 = time.perf_counter()
+    n, N = 3, WORKLOAD["N"]
+    for i, Ma in enumerate((0.05, 0.1, 0.2, 0.3)):
+        Q, dt = I.tgv_state(n, N, Ma=Ma, seed=100 + i, cfl=WORKLOAD["cfl"])
+        c = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Ma=Ma, Re=WORKLOAD["Re"])
+        c.sc_set_mesh(n, 2 * math.pi, N)
+        c.sc_set_timestep(dt, 1)
+        Qd = torch.tensor(Q.reshape(-1), device="cuda")
+        c.sc_set_state(Qd, Qd)
+        c.sc_assemble()
+        c.sc_condense()
+        K, _, _, nb = c.sc_sizes()
+        nsmp = K * nb // 5
+        F = torch.empty(nsmp, 64, device="cuda")
+        sn = torch.empty(nsmp, device="cuda")
+        T = torch.empty(nsmp, 25, device="cuda")
+        c.sc_learned_features(F, sn)
+        c.sc_learned_targets(T)
+        Fs.append(F)
+        Ts.append(T)
+        c.close()
+    X = torch.cat(Fs).contiguous()
+    Y = torch.cat(Ts).contiguous()
+    P = [rng.standard_normal((256, 64)) * math.sqrt(2 / 64), rng.standard_normal((256, 256)) * math.sqrt(2 / 256),
+         rng.standard_normal((25, 256)) * math.sqrt(1 / 256) * 0.1]
+    net = sc.MLP(np.concatenate([w.ravel() for w in P]), np.zeros(sc.MLP_NB), stream=stream.cuda_stream)
+    hist = net.train(X, Y, epochs=args.train_epochs, batch=256, lr=1e-3)
+    return net, {"samples": int(X.shape[0]), "epochs": args.train_epochs, "loss_first": hist[0],
+                 "loss_last": hist[-1], "seconds": time.perf_counter() - t0}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1911_02366_gb300 import sc
@@ -124,12 +163,20 @@ def run_ours(args, world, rank, local):
     W = WORKLOAD
     Q, dt = I.tgv_state(W["n"], W["N"], Ma=W["Ma"], seed=W["seed"], cfl=W["cfl"])
     dofs = Q.size
-    precision = sc.SC_PREC_MIXED if args.arm == "mixed" else sc.SC_PREC_FP64
+    precision = sc.SC_PREC_FP64 if args.arm == "fp64" else sc.SC_PREC_MIXED
     stream = torch.cuda.current_stream()
+    extra = {}
+    train_info = None
+    if args.arm == "learned":
+        net, train_info = train_correction(args, stream)
+        extra = dict(precond=sc.SC_PC_LEARNED)
     ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
-                     inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores)
+                     inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores, **extra)
+
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
+    if args.arm == "learned":
+        ctx.sc_set_learned_weights(net)
     ctx.sc_set_timestep(dt, 1)
     Qd = torch.tensor(Q.reshape(-1), device="cuda")
     dQ = torch.zeros_like(Qd)
@@ -212,12 +259,14 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded Taylor-Green state, 1e-3 perturbation)",
         "config": {"workload": W["name"], "elements": W["n"] ** 3, "order": W["N"], "dof": dofs, "cfl": W["cfl"],
                    "Ma": W["Ma"], "Re": W["Re"], "arm": args.arm, "gmres_restart": args.restart,
-                   "inner_tol": args.inner_tol if args.arm == "mixed" else None,
-                   "tensor_cores": bool(args.tensor_cores) if args.arm == "mixed" else False,
+                   "inner_tol": args.inner_tol if args.arm != "fp64" else None,
+                   "tensor_cores": bool(args.tensor_cores) if args.arm != "fp64" else False,
                    "l2": "inputs larger than L2 (element blocks 12.9 GB)", "parallelism": f"replicas x{world}"},
         "linear_solve_dof_per_s": world * dofs * args.steps / (gather_max(world, solve_ms) * 1e-3),
         "assemble_ms_per_step": assemble_ms / args.steps,
         "gmres_iters": [s["gmres_iters"] for s in stats],
+        "learned_fallbacks": [s["learned_fallbacks"] for s in stats] if args.arm == "learned" else None,
+        "training": train_info,
         "refinement_sweeps": [s["refinements"] for s in stats],
         "rel_residual_max": worst, "converged": ok,
         "e2e": {"value": world * dofs * e2e_steps / e2e_s, "unit": "DOF/s",
@@ -285,7 +334,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--arm", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--arm", choices=["fp64", "mixed", "learned"], default="mixed")
+    ap.add_argument("--train-epochs", type=int, default=20, help="learned arm: training epochs (untimed)")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
