@@ -172,7 +172,8 @@ def run_ours(args, world, rank, local):
         extra = dict(precond=sc.SC_PC_LEARNED)
     ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
-                     inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores, **extra)
+                     inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
+                     explicit_schur=1 if args.operator == "explicit" else 0, **extra)
 
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
     if args.arm == "learned":
@@ -196,7 +197,7 @@ def run_ours(args, world, rank, local):
         step()
     torch.cuda.synchronize()
 
-    dominant = sc.SC_KERNEL_LU_SOLVE
+    dominant = sc.SC_KERNEL_EXPLICIT_APPLY if args.operator == "explicit" else sc.SC_KERNEL_LU_SOLVE
     ctx.sc_profile_kernel(dominant)
     sampler = ClockSampler(local) if rank == 0 else None
     l0 = ctx.sc_launch_count()
@@ -247,7 +248,8 @@ def run_ours(args, world, rank, local):
                 "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = TRAFFIC.get((args.arm, dominant))
-    roof["kernel"] = {sc.SC_KERNEL_LU_SOLVE: "k_lu_solve", sc.SC_KERNEL_COND_BOUNDARY: "k_cond_boundary"}[dominant]
+    roof["kernel"] = {sc.SC_KERNEL_LU_SOLVE: "k_lu_solve", sc.SC_KERNEL_COND_BOUNDARY: "k_cond_boundary",
+                      sc.SC_KERNEL_EXPLICIT_APPLY: "k_explicit_w"}[dominant]
     roof["launches_timed"] = n_prof
     roof["avg_launch_ms"] = avg_ms
 
@@ -261,6 +263,7 @@ def run_ours(args, world, rank, local):
                    "Ma": W["Ma"], "Re": W["Re"], "arm": args.arm, "gmres_restart": args.restart,
                    "inner_tol": args.inner_tol if args.arm != "fp64" else None,
                    "tensor_cores": bool(args.tensor_cores) if args.arm != "fp64" else False,
+                   "operator": args.operator,
                    "l2": "inputs larger than L2 (element blocks 12.9 GB)", "parallelism": f"replicas x{world}"},
         "linear_solve_dof_per_s": world * dofs * args.steps / (gather_max(world, solve_ms) * 1e-3),
         "assemble_ms_per_step": assemble_ms / args.steps,
@@ -336,6 +339,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--arm", choices=["fp64", "mixed", "learned"], default="mixed")
     ap.add_argument("--train-epochs", type=int, default=20, help="learned arm: training epochs (untimed)")
+    ap.add_argument("--operator", choices=["implicit", "explicit"], default="implicit",
+                    help="mixed arm: condensed operator applied implicitly or from explicit W_e blocks")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)

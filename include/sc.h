@@ -71,6 +71,10 @@ typedef struct {
   double learned_min_reduction;  /* SC_PC_LEARNED: a GMRES restart cycle that reduces the
                             condensed residual by less than this factor switches the rest of
                             the solve to plain block Jacobi (10) */
+  int explicit_schur;    /* mixed arm, meshes with n >= 3: 1 = form the Schur blocks W_e over
+                            the extended boundary sets (Sec. 2.2) in sc_condense and apply
+                            S = A_bb - sum_e P_e^T W_e P_e explicitly in GMRES; 0 = implicit
+                            operator (default) */
 } sc_config;
 
 /* Per-solve statistics filled by sc_solve. */
@@ -247,7 +251,8 @@ sc_status sc_set_learned_correction(sc_ctx* ctx, const float* Ck, float scale);
 /* Kernel ids for sc_profile_kernel / sc_kernel_work. */
 enum { SC_KERNEL_COND_INTERIOR = 0, SC_KERNEL_COND_BOUNDARY = 1, SC_KERNEL_LU_SOLVE = 2,
        SC_KERNEL_LU = 3, SC_KERNEL_SCHUR_GEMM = 4, SC_KERNEL_GJ_INV = 5, SC_KERNEL_ASSEMBLE_OWN = 6,
-       SC_KERNEL_GLOBAL_APPLY = 7 };
+       SC_KERNEL_GLOBAL_APPLY = 7, SC_KERNEL_EXPLICIT_GEMM = 8 /* Y_e and W_e products */,
+       SC_KERNEL_EXPLICIT_APPLY = 9 /* W_e part of the explicit matvec */ };
 
 /* Total number of kernels this context has launched since sc_create. */
 sc_status sc_launch_count(const sc_ctx* ctx, long long* count);

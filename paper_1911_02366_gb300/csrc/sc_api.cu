@@ -94,7 +94,7 @@ void free_all(sc_ctx* c) {
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
                    &c->Apk32, &c->Sls32, &c->Sdiag, &c->Cpl, &c->Feat, &c->Snorm, &c->Ynet, &c->Hbuf,
-                   &c->Ck, &c->Wbias};
+                   &c->Ck, &c->Wbias, &c->ExIb, &c->ExBi, &c->ExY, &c->ExW};
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
@@ -104,7 +104,7 @@ void free_all(sc_ctx* c) {
   c->Sdiag_valid = c->weights_set = c->learned_on = false;
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
-                 &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror};
+                 &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
 }
 
@@ -226,6 +226,8 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   if (n < 1 || n > 32 || N < 2 || N > 4 || !(L > 0)) return fail(c, SC_ERR_ARG, "mesh: need n in [1,32], N in [2,4], L > 0");
   if (c->cfg.precond == SC_PC_LEARNED && c->cfg.precision != SC_PREC_MIXED)
     return fail(c, SC_ERR_ARG, "the learned correction runs on the mixed arm's FP32 blocks");
+  if (c->cfg.explicit_schur && (c->cfg.precision != SC_PREC_MIXED || n < 3))
+    return fail(c, SC_ERR_ARG, "explicit Schur blocks: mixed arm on meshes with n >= 3 (distinct neighbours)");
   cudaStreamSynchronize(c->stream);
   free_all(c);
   c->has_mesh = c->has_state = c->assembled = c->condensed = false;
@@ -279,6 +281,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   build_pattern(c);
   sc::build_packed_pattern(c);
   sc::build_learned_tables(c);
+  if (c->cfg.explicit_schur) sc::build_explicit_tables(c);
   const size_t nodes = (size_t)G.K * G.nn, dofs = nodes * 5;
   const size_t n1 = (size_t)G.K * G.nb;
   const int m = c->cfg.gmres_restart;
@@ -323,6 +326,11 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
       A(dalloc(&c->Wbf16, (size_t)sc::kMlpWeights));
     }
     A(dalloc(&c->Apk32, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls32, sc::solve_layout_elems(G)));
+    if (c->cfg.explicit_schur) {
+      A(dalloc(&c->d_ex_nbpos, c->ex_nbpos.size())); A(dalloc(&c->d_ex_face_idx, c->ex_face_idx.size()));
+      A(dalloc(&c->ExIb, (size_t)G.K * G.ni * c->ex_ldm)); A(dalloc(&c->ExBi, (size_t)G.K * c->ex_m * G.ldi));
+      A(dalloc(&c->ExY, (size_t)G.K * G.ni * c->ex_ldm)); A(dalloc(&c->ExW, sc::explicit_elems_W(G, c)));
+    }
   } else {
     A(dalloc(&c->Apk, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls, sc::solve_layout_elems(G)));
   }
@@ -346,6 +354,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   }
   SC_CUDA(cudaMemcpy(c->d_pinfo, pinfo.data(), np * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(sc::upload_packed_pattern(c));
+  if (c->cfg.explicit_schur) SC_CUDA(sc::upload_explicit_tables(c));
   SC_CUDA(cudaMemcpy(c->d_lface, c->l_face.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_lmirror, c->l_mirror.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   // the alignment padding of the element blocks (dense and packed) must read as zero
@@ -428,11 +437,14 @@ sc_status sc_condense(sc_ctx* c) {
   c->Sdiag_valid = false;
   SC_CUDA(sc::launch_condense(c));
   if (c->cfg.precond == SC_PC_LEARNED) SC_CUDA(sc::learned_correction(c));
+  if (c->cfg.explicit_schur) SC_CUDA(sc::explicit_build(c));
   int bad = -1;
   SC_CUDA(cudaMemcpyAsync(&bad, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
   if (s != SC_OK) return s;
   if (bad == SC_TC_TIMEOUT) return fail(c, SC_ERR_CUDA, "tensor-core wait timed out in the condensation");
+  if (bad == SC_EXPLICIT_PATTERN)
+    return fail(c, SC_ERR_STATE, "an interior row couples outside the extended boundary set");
   if (bad == SC_PACK_VIOLATION)
     return fail(c, SC_ERR_STATE, "own-block entry outside the packed node pattern is nonzero");
   if (bad >= 0) return fail(c, SC_ERR_SINGULAR_BLOCK, "singular element block in element " + std::to_string(bad));
@@ -496,8 +508,12 @@ sc_status sc_condensed_matvec(sc_ctx* c, const double* xb, double* yb) {
   if (c->cfg.precision == SC_PREC_MIXED) {
     const size_t n1 = (size_t)c->G.K * c->G.nb;
     SC_CUDA(sc::vec_to_float(c, c->Xbf, xb, n1));
-    SC_CUDA(sc::cond_interior32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf));
-    SC_CUDA(sc::cond_boundary32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf, yb));
+    if (c->cfg.explicit_schur) {
+      SC_CUDA(sc::explicit_matvec32(c, c->Xbf, yb));
+    } else {
+      SC_CUDA(sc::cond_interior32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf));
+      SC_CUDA(sc::cond_boundary32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf, yb));
+    }
   } else {
     SC_CUDA(sc::cond_interior(c, xb, 1.0, nullptr, 0.0, c->Ui));
     SC_CUDA(sc::cond_boundary(c, xb, 1.0, nullptr, 0.0, c->Ui, yb));
@@ -537,8 +553,12 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
       double* Vj = c->V + (size_t)j * n1;
       if (c->op32) {
         SC_CUDA(sc::precond_apply32(c, Vj, nullptr, c->Zf));
-        SC_CUDA(sc::cond_interior32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf));
-        SC_CUDA(sc::cond_boundary32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf, c->Wv));
+        if (c->cfg.explicit_schur) {
+          SC_CUDA(sc::explicit_matvec32(c, c->Zf, c->Wv));
+        } else {
+          SC_CUDA(sc::cond_interior32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf));
+          SC_CUDA(sc::cond_boundary32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf, c->Wv));
+        }
       } else {
         SC_CUDA(sc::precond_apply(c, Vj, c->Zv));
         SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
@@ -584,8 +604,12 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
       SC_CUDA(sc::precond_apply32(c, c->Tb, c->Zv, nullptr));
       SC_CUDA(sc::vec_axpby(c, c->Xb, 1.0, c->Zv, 1.0, n1));
       SC_CUDA(sc::vec_to_float(c, c->Xbf, c->Xb, n1));
-      SC_CUDA(sc::cond_interior32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf));
-      SC_CUDA(sc::cond_boundary32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf, c->Wv));
+      if (c->cfg.explicit_schur) {
+        SC_CUDA(sc::explicit_matvec32(c, c->Xbf, c->Wv));
+      } else {
+        SC_CUDA(sc::cond_interior32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf));
+        SC_CUDA(sc::cond_boundary32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf, c->Wv));
+      }
     } else {
       SC_CUDA(sc::precond_apply(c, c->Tb, c->Zv));
       SC_CUDA(sc::vec_axpby(c, c->Xb, 1.0, c->Zv, 1.0, n1));
@@ -774,6 +798,14 @@ sc_status sc_kernel_work(const sc_ctx* c, int kernel_id, double* flops, double* 
     case SCK_ASM_OWN:
       f = 0.0;
       b = K * 8.0 * ne * lda;
+      break;
+    case SCK_EXPLICIT_GEMM:  // Y_e = A_ii^-1 A_ib[., E_e], W_e = A_bi[E_e, .] Y_e
+      f = K * (2.0 * ni * ni * c->ex_m + 2.0 * (double)c->ex_m * c->ex_m * ni);
+      b = K * 4.0 * (ni * ldi + 2.0 * ni * c->ex_m + c->ex_m * ldi + 2.0 * ni * c->ex_m + (double)c->ex_m * c->ex_m);
+      break;
+    case SCK_EXPLICIT_APPLY:  // W_e (P_e x), subtracted at the extended dofs
+      f = K * 2.0 * (double)c->ex_m * c->ex_m;
+      b = K * (4.0 * (double)c->ex_m * c->ex_ldm + 4.0 * c->ex_m + 8.0 * c->ex_m);
       break;
     case SCK_GLOBAL_APPLY:  // always FP64
       f = K * (2.0 * ne * ne + 2.0 * 25.0 * pairs);

@@ -736,6 +736,14 @@ cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
 }
 
 size_t solve_layout_elems(const Geo& G) { return (size_t)G.K * ls_stride(G); }
+
+// C = A B for `batch` row-major FP32 blocks on the CUDA cores.
+cudaError_t gemm_fp32(sc_ctx* c, int M, int N, int K, const float* A, long long sA, int lda, const float* B,
+                      long long sB, int ldb, float* C, long long sC, int ldc, int batch) {
+  dim3 g(cdiv(N, 64), cdiv(M, 64), batch);
+  k_gemm<float><<<g, 256, 0, c->stream>>>(M, N, K, 1.0f, A, sA, lda, B, sB, ldb, 0.0f, C, sC, ldc);
+  return cudaGetLastError();
+}
 long long solve_layout_stride(const Geo& G) { return ls_stride(G); }
 
 // LU with partial pivoting of `batch` FP32 n x n blocks (row-major, lda, `stride` apart),

@@ -286,6 +286,11 @@ struct sc_ctx {
   uint16_t* Wbf16 = nullptr;
   bool Sdiag_valid = false, weights_set = false, learned_on = false;
   int learned_fallbacks = 0;
+  // explicit Schur blocks W_e over the extended boundary sets (measured alternative)
+  int ex_F = 0, ex_m = 0, ex_ldm = 0;
+  std::vector<int> ex_nbpos, ex_face_idx;
+  int *d_ex_nbpos = nullptr, *d_ex_face_idx = nullptr;
+  float *ExIb = nullptr, *ExBi = nullptr, *ExY = nullptr, *ExW = nullptr;
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};
   // measurement hooks: kernel launches since creation, and optional CUDA-event timing
@@ -300,7 +305,8 @@ struct sc_ctx {
 
 // Kernel ids of the measurement hook (sc_profile_kernel).
 enum { SCK_COND_INTERIOR = 0, SCK_COND_BOUNDARY = 1, SCK_LU_SOLVE = 2, SCK_LU = 3, SCK_GEMM = 4,
-       SCK_GJ_INV = 5, SCK_ASM_OWN = 6, SCK_GLOBAL_APPLY = 7, SCK_COUNT = 8 };
+       SCK_GJ_INV = 5, SCK_ASM_OWN = 6, SCK_GLOBAL_APPLY = 7, SCK_EXPLICIT_GEMM = 8, SCK_EXPLICIT_APPLY = 9,
+       SCK_COUNT = 10 };
 
 // Bracket one launch of kernel `id` with events when it is the profiled kernel.
 struct ProfScope {
@@ -329,6 +335,9 @@ constexpr int SC_TC_TIMEOUT = 1 << 30;
 // Status word value written by the packing kernel when an own-block entry outside the
 // packed pattern is nonzero.
 constexpr int SC_PACK_VIOLATION = (1 << 30) + 1;
+// Status word value written when an interior row couples outside the extended boundary
+// set of the explicit Schur blocks.
+constexpr int SC_EXPLICIT_PATTERN = (1 << 30) + 2;
 
 namespace sc {
 cudaError_t launch_residual(sc_ctx* c);
@@ -366,6 +375,13 @@ cudaError_t factor_batch32(sc_ctx* c, float* A, int n, int lda, long long stride
 cudaError_t unit_solve32(sc_ctx* c, int n, const float* LS, long long lsstride, const int* rowperm, const int* mat,
                          const int* node, int nsmp, float* out);
 void build_learned_tables(sc_ctx* c);
+void build_explicit_tables(sc_ctx* c);
+cudaError_t upload_explicit_tables(sc_ctx* c);
+size_t explicit_elems_W(const Geo& G, const sc_ctx* c);
+cudaError_t explicit_build(sc_ctx* c);
+cudaError_t explicit_matvec32(sc_ctx* c, const float* x, double* y);
+cudaError_t gemm_fp32(sc_ctx* c, int M, int N, int K, const float* A, long long sA, int lda, const float* B,
+                      long long sB, int ldb, float* C, long long sC, int ldc, int batch);
 cudaError_t extract_sdiag(sc_ctx* c, const float* See);
 cudaError_t learned_features(sc_ctx* c, float* F, float* snorm);
 cudaError_t learned_correction(sc_ctx* c);

@@ -33,7 +33,8 @@ class sc_config(ctypes.Structure):
                 ("roe_delta", ctypes.c_double), ("precision", ctypes.c_int), ("precond", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("gmres_max_iters", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("rel_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("tensor_cores", ctypes.c_int), ("learned_min_reduction", ctypes.c_double)]
+                ("tensor_cores", ctypes.c_int), ("learned_min_reduction", ctypes.c_double),
+                ("explicit_schur", ctypes.c_int)]
 
 
 class sc_solve_stats(ctypes.Structure):
@@ -56,6 +57,7 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
+SC_KERNEL_EXPLICIT_GEMM, SC_KERNEL_EXPLICIT_APPLY = 8, 9
 
 
 def lib_path() -> str:
