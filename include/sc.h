@@ -71,6 +71,10 @@ typedef struct {
   double learned_min_reduction;  /* SC_PC_LEARNED: a GMRES restart cycle that reduces the
                             condensed residual by less than this factor switches the rest of
                             the solve to plain block Jacobi (10) */
+  int factor_fp16;       /* mixed arm: 1 = keep a copy of the block-Jacobi factors in FP16 for the
+                            GMRES preconditioner (FP32 arithmetic; used only when every entry is
+                            within the FP16 range, else the FP32 copy), 0 = FP32 only (default 0:
+                            at CFL 50 the FP16 factors nearly double the GMRES iterations) */
   int explicit_schur;    /* mixed arm, meshes with n >= 3: 1 = form the Schur blocks W_e over
                             the extended boundary sets (Sec. 2.2) in sc_condense and apply
                             S = A_bb - sum_e P_e^T W_e P_e explicitly in GMRES; 0 = implicit

@@ -99,6 +99,9 @@ void free_all(sc_ctx* c) {
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
   c->packed = false;
+  if (c->Sls16) cudaFree(c->Sls16);
+  c->Sls16 = nullptr;
+  c->ls16_ok = false;
   if (c->Wbf16) cudaFree(c->Wbf16);
   c->Wbf16 = nullptr;
   c->Sdiag_valid = c->weights_set = c->learned_on = false;
@@ -309,7 +312,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->Gb, n1)); A(dalloc(&c->Rb, n1)); A(dalloc(&c->Tb, n1));
   A(dalloc(&c->Ui, (size_t)G.K * G.ni)); A(dalloc(&c->Hd, 3 * (size_t)(m + 2) + 16));
   A(dalloc(&c->partial, 152 * (size_t)(m + 2)));
-  A(dalloc(&c->d_status, 1));
+  A(dalloc(&c->d_status, 2));  // [0] first bad element / error code, [1] FP16 range overflow
   A(dalloc(&c->d_nbr, c->nbr.size())); A(dalloc(&c->d_perm, G.nn)); A(dalloc(&c->d_iperm, G.nn));
   const int np = G.NP;
   A(dalloc(&c->d_prow, np)); A(dalloc(&c->d_pslot, np)); A(dalloc(&c->d_pcol, np));
@@ -326,6 +329,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
       A(dalloc(&c->Wbf16, (size_t)sc::kMlpWeights));
     }
     A(dalloc(&c->Apk32, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls32, sc::solve_layout_elems(G)));
+    if (c->cfg.factor_fp16) A(dalloc(&c->Sls16, sc::solve_layout_elems(G)));
     if (c->cfg.explicit_schur) {
       A(dalloc(&c->d_ex_nbpos, c->ex_nbpos.size())); A(dalloc(&c->d_ex_face_idx, c->ex_face_idx.size()));
       A(dalloc(&c->ExIb, (size_t)G.K * G.ni * c->ex_ldm)); A(dalloc(&c->ExBi, (size_t)G.K * c->ex_m * G.ldi));
@@ -435,11 +439,14 @@ sc_status sc_condense(sc_ctx* c) {
   if (c->cfg.precond == SC_PC_LEARNED && !c->weights_set)
     return fail(c, SC_ERR_STATE, "learned preconditioner without weights (sc_set_learned_weights)");
   c->Sdiag_valid = false;
+  const int zero = 0;
+  SC_CUDA(cudaMemcpyAsync(c->d_status + 1, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   SC_CUDA(sc::launch_condense(c));
   if (c->cfg.precond == SC_PC_LEARNED) SC_CUDA(sc::learned_correction(c));
   if (c->cfg.explicit_schur) SC_CUDA(sc::explicit_build(c));
-  int bad = -1;
+  int bad = -1, ovf = 0;
   SC_CUDA(cudaMemcpyAsync(&bad, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SC_CUDA(cudaMemcpyAsync(&ovf, c->d_status + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
   if (s != SC_OK) return s;
   if (bad == SC_TC_TIMEOUT) return fail(c, SC_ERR_CUDA, "tensor-core wait timed out in the condensation");
@@ -448,6 +455,8 @@ sc_status sc_condense(sc_ctx* c) {
   if (bad == SC_PACK_VIOLATION)
     return fail(c, SC_ERR_STATE, "own-block entry outside the packed node pattern is nonzero");
   if (bad >= 0) return fail(c, SC_ERR_SINGULAR_BLOCK, "singular element block in element " + std::to_string(bad));
+  // FP16 factors for the block-Jacobi solve only when every entry fits the FP16 range
+  c->ls16_ok = c->Sls16 != nullptr && ovf == 0 && c->cfg.precond != SC_PC_NONE;
   c->condensed = true;
   return SC_OK;
 }
@@ -779,9 +788,11 @@ sc_status sc_kernel_work(const sc_ctx* c, int kernel_id, double* flops, double* 
       f = K * 2.0 * (double)c->pk_nnz_bnd;
       b = K * (w * (double)c->pk_nnz_bnd + w * (ni + nb) + 8.0 * nb);
       break;
-    case SCK_LU_SOLVE:  // forward + backward substitution with the S_ee factors
+    case SCK_LU_SOLVE: {  // forward + backward substitution with the S_ee factors (FP16 when stored so)
+      const double wf = c->ls16_ok ? 2.0 : w;
       f = K * 2.0 * nb * nb;
-      b = K * (w * nb * lds + 4.0 * nb + 8.0 * 2.0 * nb);
+      b = K * (wf * nb * lds + 4.0 * nb + 8.0 * 2.0 * nb);
+    }
       break;
     case SCK_LU:
       f = K * (2.0 / 3.0) * nb * nb * nb;

@@ -11,6 +11,8 @@
 //   k_solve_prep  partitioned inverses of the LU factors in the solve layout (below).
 //   k_lu_solve    z = (P^T L U)^-1 v for every element, one warp per element, one lane
 //                 per row of each 32-row block.
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "sc_internal.cuh"
@@ -374,15 +376,16 @@ __global__ void k_piv_to_perm(int n, const int* __restrict__ piv_all, int* __res
 // columns, rows beyond n zero).  A warp then reads one 4-column group of all 32 rows as
 // 32 consecutive 16- (FP32) or 32-byte (FP64) pieces.
 
-template <class T> struct Quad;
-template <> struct Quad<float> {
+// Four consecutive stored factor entries (type TS) widened to the arithmetic type T.
+template <class T, class TS> struct Quad;
+template <> struct Quad<float, float> {
   float v[4];
   __device__ __forceinline__ void load(const float* p) {
     const float4 a = __ldg(reinterpret_cast<const float4*>(p));
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   }
 };
-template <> struct Quad<double> {
+template <> struct Quad<double, double> {
   double v[4];
   __device__ __forceinline__ void load(const double* p) {
     const double2 a = __ldg(reinterpret_cast<const double2*>(p));
@@ -390,18 +393,32 @@ template <> struct Quad<double> {
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
 };
+template <> struct Quad<float, __half> {
+  float v[4];
+  __device__ __forceinline__ void load(const __half* p) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
 
 // One CTA per (block row b, element): D_b from the factors, then every column c of the
 // block row: c < i0 -> M_b, diagonal block -> D_b, c >= i0 + 32 -> N_b.
+// With LS16 non-null (FP32 factors only) the layout is also written in FP16; an entry
+// beyond the FP16 range sets *ovf.
 template <class T>
 __global__ void __launch_bounds__(256) k_solve_prep(int n, const T* __restrict__ LU, long long stride, int lda,
-                                                    T* __restrict__ LS, long long lsstride, int npad) {
+                                                    T* __restrict__ LS, long long lsstride, int npad,
+                                                    __half* __restrict__ LS16, int* __restrict__ ovf) {
   __shared__ T TL[32][33];  // L_bb^-1: unit diagonal, stored inverse below it
   __shared__ T TU[32][33];  // U_bb^-1: stored inverse on and above the diagonal
   __shared__ T D[32][33];   // diagonal block as stored (both inverse triangles)
   const int b = blockIdx.x, e = blockIdx.y, i0 = 32 * b, bs = min(32, n - i0);
   const T* M = LU + (long long)e * stride;
   T* out = LS + (long long)e * lsstride + (long long)b * 32 * npad;
+  __half* out16 = LS16 ? LS16 + (long long)e * lsstride + (long long)b * 32 * npad : nullptr;
+  bool big = false;
   for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
     const int r = t / 32, k = t % 32;
     const T dv = (r < bs && k < bs) ? M[(long long)(i0 + r) * lda + i0 + k] : T(0);
@@ -416,34 +433,40 @@ __global__ void __launch_bounds__(256) k_solve_prep(int n, const T* __restrict__
 #pragma unroll
     for (int k = 0; k < 32; ++k)
       col[k] = (k < bs && cidx < n && (left || right)) ? M[(long long)(i0 + k) * lda + cidx] : T(0);
-    T* o = out + (long long)(cidx / 4) * 128 + (cidx % 4);
-    if (left || right) {
-      T(*Tm)[33] = left ? TL : TU;
-      for (int r = 0; r < 32; ++r) {
-        T acc = T(0);
+    const long long oo = (long long)(cidx / 4) * 128 + (cidx % 4);
+    T* o = out + oo;
+    for (int r = 0; r < 32; ++r) {
+      T acc = T(0);
+      if (left || right) {
+        T(*Tm)[33] = left ? TL : TU;
 #pragma unroll
         for (int k = 0; k < 32; ++k) acc = fma(Tm[r][k], col[k], acc);
-        o[4 * r] = acc;
+      } else {
+        acc = cidx < n ? D[r][cidx - i0] : T(0);
       }
-    } else {
-      for (int r = 0; r < 32; ++r) o[4 * r] = cidx < n ? D[r][cidx - i0] : T(0);
+      o[4 * r] = acc;
+      if (out16) {
+        out16[oo + 4 * r] = __float2half_rn((float)acc);
+        big = big || !(fabs((double)acc) <= 65000.0);
+      }
     }
   }
+  if (out16 && big) atomicExch(ovf, 1);
 }
 
 // In-place (L U)^-1 s of one element's factors Le in the solve layout, by one warp: lane r
 // owns row 32 b + r of every block; s (shared memory, nblk * 32 entries, zero beyond n)
 // holds the permuted right-hand side on entry and the solution on exit.
-template <class T>
-__device__ __forceinline__ void ls_solve_warp(int n, int nblk, const T* __restrict__ Le, int npad, T* s, int lane) {
+template <class T, class TS>
+__device__ __forceinline__ void ls_solve_warp(int n, int nblk, const TS* __restrict__ Le, int npad, T* s, int lane) {
   const int nq = npad / 4;
   for (int b = 0; b < nblk; ++b) {  // forward: x_b = L_bb^-1 v_b - M_b x_{<b}
     const int i0 = 32 * b, R = i0 + lane;
-    const T* row = Le + (long long)b * 32 * npad + 4 * lane;
+    const TS* row = Le + (long long)b * 32 * npad + 4 * lane;
     T a0 = T(0), a1 = T(0);
 #pragma unroll 8
     for (int q = 0; q < i0 / 4; ++q) {
-      Quad<T> m;
+      Quad<T, TS> m;
       m.load(row + (long long)q * 128);
       a0 = fma(m.v[0], s[4 * q], a0);
       a1 = fma(m.v[1], s[4 * q + 1], a1);
@@ -454,7 +477,7 @@ __device__ __forceinline__ void ls_solve_warp(int n, int nblk, const T* __restri
     const int qd = min(i0 / 4 + 8, nq);  // the last block row may end before 32 columns
 #pragma unroll
     for (int q = i0 / 4; q < qd; ++q) {
-      Quad<T> m;
+      Quad<T, TS> m;
       m.load(row + (long long)q * 128);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
@@ -466,12 +489,12 @@ __device__ __forceinline__ void ls_solve_warp(int n, int nblk, const T* __restri
   }
   for (int b = nblk - 1; b >= 0; --b) {  // backward: z_b = U_bb^-1 x_b - N_b z_{>b}
     const int i0 = 32 * b, R = i0 + lane;
-    const T* row = Le + (long long)b * 32 * npad + 4 * lane;
+    const TS* row = Le + (long long)b * 32 * npad + 4 * lane;
     T d = T(0);
     const int qd = min(i0 / 4 + 8, nq);
 #pragma unroll
     for (int q = i0 / 4; q < qd; ++q) {
-      Quad<T> m;
+      Quad<T, TS> m;
       m.load(row + (long long)q * 128);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
@@ -480,7 +503,7 @@ __device__ __forceinline__ void ls_solve_warp(int n, int nblk, const T* __restri
     T a0 = T(0), a1 = T(0);
 #pragma unroll 8
     for (int q = i0 / 4 + 8; q < nq; ++q) {
-      Quad<T> m;
+      Quad<T, TS> m;
       m.load(row + (long long)q * 128);
       a0 = fma(m.v[0], s[4 * q], a0);
       a1 = fma(m.v[1], s[4 * q + 1], a1);
@@ -497,8 +520,8 @@ __device__ __forceinline__ void ls_solve_warp(int n, int nblk, const T* __restri
 // then z) sits in shared memory.  Arithmetic in the factor precision T; v in double,
 // outputs z (double) and / or zt (T).  Ck (or null): a 5 x 5 correction per boundary node
 // added as z_k += C_k v_k (the learned correction of the block-Jacobi inverse).
-template <class T>
-__global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const T* __restrict__ LS, long long lsstride,
+template <class T, class TS>
+__global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const TS* __restrict__ LS, long long lsstride,
                                                   int npad, const int* __restrict__ rowperm,
                                                   const double* __restrict__ v, double* __restrict__ z,
                                                   T* __restrict__ zt, int nelem, const float* __restrict__ Ck) {
@@ -512,7 +535,7 @@ __global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const T* __re
   const double* ve = v + (long long)e * n;
   for (int i = lane; i < ls; i += 32) s[i] = i < n ? (T)ve[__ldg(rp + i)] : T(0);
   __syncwarp();
-  ls_solve_warp<T>(n, nblk, LS + (long long)e * lsstride, npad, s, lane);
+  ls_solve_warp<T, TS>(n, nblk, LS + (long long)e * lsstride, npad, s, lane);
   for (int i = lane; i < n; i += 32) {
     T val = s[i];
     if (Ck) {
@@ -548,7 +571,7 @@ __global__ void __launch_bounds__(128) k_unit_solve(int n, int nblk, const T* __
   const int* rp = rowperm + (long long)m * n;
   for (int i = lane; i < ls; i += 32) s[i] = (i < n && __ldg(rp + i) == col) ? T(1) : T(0);
   __syncwarp();
-  ls_solve_warp<T>(n, nblk, LS + (long long)m * lsstride, npad, s, lane);
+  ls_solve_warp<T, T>(n, nblk, LS + (long long)m * lsstride, npad, s, lane);
   if (lane < 5) out[(long long)smp * 25 + 5 * lane + var] = (float)s[5 * a + lane];
 }
 
@@ -675,8 +698,10 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
     T* LS = nullptr;
     if constexpr (std::is_same<T, float>::value) LS = c->Sls32; else LS = c->Sls;
     const int nblk = (nb + 31) / 32, npad = (nb + 3) & ~3;
+    __half* LS16 = nullptr;
+    if constexpr (std::is_same<T, float>::value) LS16 = c->Sls16;
     k_solve_prep<T><<<dim3(nblk, K), 256, 0, c->stream>>>(nb, See, (long long)nb * lds, lds, LS,
-                                                           (long long)nblk * 32 * npad, npad);
+                                                           (long long)nblk * 32 * npad, npad, LS16, c->d_status + 1);
   }
   return cudaGetLastError();
 }
@@ -703,13 +728,14 @@ inline int ls_nblk(const Geo& G) { return (G.nb + 31) / 32; }
 inline int ls_npad(const Geo& G) { return (G.nb + 3) & ~3; }
 inline long long ls_stride(const Geo& G) { return (long long)ls_nblk(G) * 32 * ls_npad(G); }
 
-template <class T>
-cudaError_t lu_solve_t(sc_ctx* c, const T* LS, const double* v, double* z, T* zt) {
+template <class T, class TS>
+cudaError_t lu_solve_t(sc_ctx* c, const TS* LS, const double* v, double* z, T* zt) {
   const Geo& G = c->G;
   ProfScope ps(c, SCK_LU_SOLVE);
   const size_t smem = (size_t)4 * ls_nblk(G) * 32 * sizeof(T);
-  k_lu_solve<T><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G), c->rowperm,
-                                                        v, z, zt, G.K, c->learned_on ? c->Ck : nullptr);
+  k_lu_solve<T, TS><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
+                                                            c->rowperm, v, z, zt, G.K,
+                                                            c->learned_on ? c->Ck : nullptr);
   return cudaGetLastError();
 }
 
@@ -719,7 +745,7 @@ cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
   if (c->cfg.precond == SC_PC_NONE) {
     return cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   }
-  return lu_solve_t<double>(c, c->Sls, v, z, nullptr);
+  return lu_solve_t<double, double>(c, c->Sls, v, z, nullptr);
 }
 
 // Block-Jacobi with the FP32 factors; writes z in double and / or zf in float.
@@ -732,7 +758,8 @@ cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
     if (e == cudaSuccess && zf) e = vec_to_float(c, zf, v, n1);
     return e;
   }
-  return lu_solve_t<float>(c, c->Sls32, v, z, zf);
+  if (c->ls16_ok) return lu_solve_t<float, __half>(c, c->Sls16, v, z, zf);
+  return lu_solve_t<float, float>(c, c->Sls32, v, z, zf);
 }
 
 size_t solve_layout_elems(const Geo& G) { return (size_t)G.K * ls_stride(G); }
@@ -762,7 +789,7 @@ cudaError_t factor_batch32(sc_ctx* c, float* A, int n, int lda, long long stride
   k_diag_inv<float><<<batch, 256, dsm, c->stream>>>(n, A, stride, lda);
   const int nblk = (n + 31) / 32, npad = (n + 3) & ~3;
   k_solve_prep<float><<<dim3(nblk, batch), 256, 0, c->stream>>>(n, A, stride, lda, LS, (long long)nblk * 32 * npad,
-                                                               npad);
+                                                               npad, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 // public ABI is include/sc.h.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -277,6 +278,8 @@ struct sc_ctx {
   // S_ee factors with partitioned inverses in the block-Jacobi solve layout
   double* Sls = nullptr;
   float* Sls32 = nullptr;
+  __half* Sls16 = nullptr;  // FP16 copy of the mixed arm's layout, used when every entry is in range
+  bool ls16_ok = false;
   bool packed = false;     // packed blocks match the assembled Jacobian
   // learned correction of the block-Jacobi preconditioner (mixed arm)
   std::vector<int> l_face, l_mirror;  // per boundary position: face, co-located position

@@ -169,3 +169,22 @@ def test_tensor_core_preconditioner_keeps_iteration_count(n, N):
         iters[key] = st["gmres_iters"]
     assert iters["tf32"] <= 1.25 * iters["fp32"] + 3, iters
     assert iters["none"] > 1.5 * iters["fp32"], iters
+
+
+@pytest.mark.parametrize("n,N", [(2, 4), (3, 3)])
+def test_fp16_factor_copy_keeps_iteration_count(n, N):
+    """The block-Jacobi factors stored in FP16 for the solve (FP32 arithmetic) precondition
+    like the FP32 ones; the FP64 refinement still reaches the target."""
+    from paper_1911_02366_gb300 import sc
+    iters = {}
+    for f16 in (0, 1):
+        Q, dt, p, ctx = case(n, N, cfl=10.0, precision=sc.SC_PREC_MIXED, rel_tol=1e-8, inner_tol=1e-4,
+                             gmres_restart=60, gmres_max_iters=4000, max_refine=20, factor_fp16=f16)
+        ctx.sc_set_state(Q, Q)
+        ctx.sc_assemble()
+        ctx.sc_condense()
+        dQ = np.zeros(Q.size)
+        st = ctx.sc_solve(dQ)
+        assert st["rel_residual"] < 1e-8
+        iters[f16] = st["gmres_iters"]
+    assert iters[1] <= 1.1 * iters[0] + 3, iters
