@@ -150,6 +150,30 @@ sc_status sc_apply_jacobian(sc_ctx* ctx, const double* x, double* y, int on_devi
    the block sums every coupling between the two elements.  Test hook. */
 sc_status sc_get_jacobian_block(sc_ctx* ctx, int e, int c, double* block);
 
+/* Current state Q [K][(N+1)^3][5] (after sc_set_state or sc_newton_step) into Qout (device
+   or host per on_device). */
+sc_status sc_get_state(sc_ctx* ctx, double* Qout, int on_device);
+
+/* Condensed right-hand side g = B_b - A_bi A_ii^-1 B_i (Sec. 2.2, eq. SC_step1) of the
+   assembled system, in the condensed boundary order (element by element, boundary nodes
+   in natural order, 5 variables), K * nb doubles; computed with the context's operator
+   precision (FP32 blocks on the mixed arm).  After sc_condense. */
+sc_status sc_condensed_rhs(sc_ctx* ctx, double* g, int on_device);
+
+/* Back-substitution (Sec. 2.2, eq. SC_step2): given the condensed solution xb (K * nb),
+   Q_i = A_ii^-1 (B_i - A_ib Q_b), and the full update dQ [K][(N+1)^3][5] with Q_b = xb.
+   After sc_condense; sc_solve performs the same step internally. */
+sc_status sc_backsubstitute(sc_ctx* ctx, const double* xb, double* dQ, int on_device);
+
+/* Newton iterations on the current time step (Sec. 2.1, eq. NeqtonEq): assemble, stop if
+   ||R(Q)||_2 <= newton_tol ||R(Q_0)||_2 or after max_newton updates, else condense, solve
+   A dQ = -R(Q) to the configured rel_tol and set Q <- Q + dQ.  The Jacobian is recomputed
+   every iteration; the history term of sc_set_state is kept.  last: statistics of the last
+   linear solve (or NULL); newton_iters: updates applied; newton_rel: final
+   ||R|| / ||R_0||.  SC_ERR_NOT_CONVERGED if the tolerance is not reached. */
+sc_status sc_newton_step(sc_ctx* ctx, int max_newton, double newton_tol, sc_solve_stats* last, int* newton_iters,
+                         double* newton_rel);
+
 /* y_b = S x_b with the condensed operator (boundary dof vectors of length
    K * 5 * (number of boundary nodes), ordered element-major, then boundary node in
    natural order, then variable).  Device pointers.  Test hook. */

@@ -90,7 +90,7 @@ void diff_matrix(const std::vector<double>& x, double D[SC_MAXP][SC_MAXP]) {
 void free_all(sc_ctx* c) {
   double** dps[] = {&c->Q, &c->Qh, &c->grad, &c->F, &c->B, &c->NJ, &c->RJ, &c->Aown, &c->X, &c->Ainv,
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
-                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk, &c->Sls};
+                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk, &c->Sls, &c->dQn};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
                    &c->Apk32, &c->Sls32, &c->Sdiag, &c->Cpl, &c->Feat, &c->Snorm, &c->Ynet, &c->Hbuf,
@@ -292,7 +292,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(dalloc(&c->Q, dofs)); A(dalloc(&c->Qh, dofs)); A(dalloc(&c->B, dofs));
-  A(dalloc(&c->Xfull, dofs)); A(dalloc(&c->Rfull, dofs));
+  A(dalloc(&c->Xfull, dofs)); A(dalloc(&c->Rfull, dofs)); A(dalloc(&c->dQn, dofs));
   A(dalloc(&c->grad, nodes * 15)); A(dalloc(&c->F, nodes * 15));
   A(dalloc(&c->NJ, nodes * 375)); A(dalloc(&c->RJ, (size_t)G.K * 6 * 50 * G.p * G.p));
   A(dalloc(&c->Aown, (size_t)G.K * own_stride(G))); A(dalloc(&c->X, (size_t)G.K * G.NP * 25));
@@ -458,6 +458,83 @@ sc_status sc_condense(sc_ctx* c) {
   // FP16 factors for the block-Jacobi solve only when every entry fits the FP16 range
   c->ls16_ok = c->Sls16 != nullptr && ovf == 0 && c->cfg.precond != SC_PC_NONE;
   c->condensed = true;
+  return SC_OK;
+}
+
+sc_status sc_get_state(sc_ctx* c, double* Qout, int on_device) {
+  if (!c || !Qout) return SC_ERR_ARG;
+  if (!c->has_state) return fail(c, SC_ERR_STATE, "get_state before set_state");
+  const size_t bytes = (size_t)c->G.K * c->G.ne * sizeof(double);
+  SC_CUDA(cudaMemcpyAsync(Qout, c->Q, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  return check(c);
+}
+
+sc_status sc_condensed_rhs(sc_ctx* c, double* g, int on_device) {
+  if (!c || !g) return SC_ERR_ARG;
+  if (!c->condensed) return fail(c, SC_ERR_STATE, "condensed_rhs before condense");
+  const size_t n1 = (size_t)c->G.K * c->G.nb;
+  double* out = on_device ? g : c->Gb;
+  if (c->cfg.precision == SC_PREC_MIXED) {
+    SC_CUDA(sc::cond_interior32(c, nullptr, 0.0, c->B, 1.0, c->Uf));
+    SC_CUDA(sc::cond_boundary32(c, nullptr, 0.0, c->B, 1.0, c->Uf, out));
+  } else {
+    SC_CUDA(sc::cond_interior(c, nullptr, 0.0, c->B, 1.0, c->Ui));
+    SC_CUDA(sc::cond_boundary(c, nullptr, 0.0, c->B, 1.0, c->Ui, out));
+  }
+  if (!on_device) SC_CUDA(cudaMemcpyAsync(g, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check(c);
+}
+
+sc_status sc_backsubstitute(sc_ctx* c, const double* xb, double* dQ, int on_device) {
+  if (!c || !xb || !dQ) return SC_ERR_ARG;
+  if (!c->condensed) return fail(c, SC_ERR_STATE, "backsubstitute before condense");
+  const Geo& G = c->G;
+  const size_t n1 = (size_t)G.K * G.nb, dofs = (size_t)G.K * G.ne;
+  const double* xd = xb;
+  if (!on_device) {
+    SC_CUDA(cudaMemcpyAsync(c->Xb, xb, n1 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    xd = c->Xb;
+  }
+  double* out = on_device ? dQ : c->Xfull;
+  if (c->cfg.precision == SC_PREC_MIXED) {
+    SC_CUDA(sc::vec_to_float(c, c->Xbf, xd, n1));
+    SC_CUDA(sc::cond_interior32(c, c->Xbf, -1.0, c->B, 1.0, c->Uf));
+    SC_CUDA(sc::scatter_solution32(c, xd, c->Uf, out));
+  } else {
+    SC_CUDA(sc::cond_interior(c, xd, -1.0, c->B, 1.0, c->Ui));
+    SC_CUDA(sc::scatter_solution(c, xd, c->Ui, out));
+  }
+  if (!on_device) SC_CUDA(cudaMemcpyAsync(dQ, c->Xfull, dofs * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check(c);
+}
+
+sc_status sc_newton_step(sc_ctx* c, int max_newton, double newton_tol, sc_solve_stats* last, int* newton_iters,
+                         double* newton_rel) {
+  if (!c || max_newton < 1 || !(newton_tol > 0)) return SC_ERR_ARG;
+  if (!c->has_mesh || !c->has_state || !c->has_dt) return fail(c, SC_ERR_STATE, "newton_step needs mesh, state, timestep");
+  const size_t dofs = (size_t)c->G.K * c->G.ne;
+  double* hs = c->Hd + 2 * (c->restart_alloc + 1) + 2;
+  double r0 = -1.0, rn = 0.0;
+  int it = 0;
+  sc_solve_stats st{};
+  for (;;) {
+    sc_status s = sc_assemble(c);
+    if (s != SC_OK) return s;
+    rn = dnorm2(c, c->B, dofs, hs);
+    if (r0 < 0.0) r0 = rn;
+    if (!std::isfinite(rn)) return fail(c, SC_ERR_NONFINITE, "non-finite Newton residual");
+    if (rn <= newton_tol * r0 || it >= max_newton) break;
+    s = sc_condense(c);
+    if (s == SC_OK) s = sc_solve(c, c->dQn, 1, &st);
+    if (s != SC_OK) return s;
+    // Q <- Q + dQ (the Newton update of eq. NeqtonEq)
+    SC_CUDA(sc::vec_axpby(c, c->Q, 1.0, c->dQn, 1.0, dofs));
+    ++it;
+  }
+  if (last) *last = st;
+  if (newton_iters) *newton_iters = it;
+  if (newton_rel) *newton_rel = r0 > 0.0 ? rn / r0 : 0.0;
+  if (rn > newton_tol * r0) return fail(c, SC_ERR_NOT_CONVERGED, "Newton did not reach the tolerance");
   return SC_OK;
 }
 

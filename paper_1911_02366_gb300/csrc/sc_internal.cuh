@@ -269,6 +269,7 @@ struct sc_ctx {
   double* Cross = nullptr;   // neighbour-coupling products of one pass, FP64 operator
   float* Cross32 = nullptr;  // same, FP32 operator
   double* Dfull = nullptr;  // refinement correction
+  double* dQn = nullptr;    // Newton update of sc_newton_step
   // pattern-packed own blocks of the condensed operator (A_ib rows, [A_bi A_bb] rows)
   std::vector<int> pk_lptr, pk_list, pk_pos, pk_row_off;
   long long pk_stride = 0, pk_nnz_int = 0, pk_nnz_bnd = 0;

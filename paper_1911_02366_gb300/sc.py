@@ -53,7 +53,8 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_apply_jacobian", "sc_get_jacobian_block", "sc_condensed_matvec", "sc_sizes",
            "sc_launch_count", "sc_profile_kernel", "sc_profile_read", "sc_kernel_work",
            "sc_condensed_matvec_static", "sc_gemm_tf32", "sc_mlp_forward", "sc_mlp_backward", "sc_mlp_loss",
-           "sc_mlp_adam", "sc_learned_features", "sc_learned_targets", "sc_set_learned_weights", "sc_set_learned_correction"]
+           "sc_mlp_adam", "sc_learned_features", "sc_learned_targets", "sc_set_learned_weights", "sc_set_learned_correction",
+           "sc_get_state", "sc_condensed_rhs", "sc_backsubstitute", "sc_newton_step"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -101,6 +102,11 @@ def lib(build_if_missing: bool = True):
     L.sc_learned_targets.argtypes = [vp, vp]
     L.sc_set_learned_weights.argtypes = [vp, vp, vp]
     L.sc_set_learned_correction.argtypes = [vp, vp, ctypes.c_float]
+    L.sc_get_state.argtypes = [vp, dp, ctypes.c_int]
+    L.sc_condensed_rhs.argtypes = [vp, dp, ctypes.c_int]
+    L.sc_backsubstitute.argtypes = [vp, dp, dp, ctypes.c_int]
+    L.sc_newton_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(sc_solve_stats),
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
@@ -207,6 +213,32 @@ class Context:
         p, dev = _ptr(B)
         self._check(self._L.sc_get_rhs(self.h, p, dev))
         return B
+
+    def sc_get_state(self, Q):
+        p, dev = _ptr(Q)
+        self._check(self._L.sc_get_state(self.h, p, dev))
+        return Q
+
+    def sc_condensed_rhs(self, g):
+        p, dev = _ptr(g)
+        self._check(self._L.sc_condensed_rhs(self.h, p, dev))
+        return g
+
+    def sc_backsubstitute(self, xb, dQ):
+        (px, dx), (pq, dq) = _ptr(xb), _ptr(dQ)
+        if dx != dq:
+            raise ValueError("xb and dQ must live on the same side")
+        self._check(self._L.sc_backsubstitute(self.h, px, pq, dq))
+        return dQ
+
+    def sc_newton_step(self, max_newton=10, newton_tol=1e-8):
+        """Newton iterations on the current step; returns (updates, ||R||/||R0||, last solve stats)."""
+        st = sc_solve_stats()
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        self._check(self._L.sc_newton_step(self.h, max_newton, newton_tol, ctypes.byref(st), ctypes.byref(it),
+                                           ctypes.byref(rel)))
+        return it.value, rel.value, st.as_dict()
 
     def sc_apply_jacobian(self, x, y):
         (px, dx), (py, dy) = _ptr(x), _ptr(y)

@@ -188,3 +188,45 @@ def test_fp16_factor_copy_keeps_iteration_count(n, N):
         assert st["rel_residual"] < 1e-8
         iters[f16] = st["gmres_iters"]
     assert iters[1] <= 1.1 * iters[0] + 3, iters
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_condensed_rhs_and_backsubstitution_match_oracle(prec):
+    """The two condensation steps as separate calls (eq. SC_step1 right-hand side, eq.
+    SC_step2) against the oracle's on the same system."""
+    from paper_1911_02366_gb300 import sc
+    n, N = 2, 3
+    precision = sc.SC_PREC_FP64 if prec == "fp64" else sc.SC_PREC_MIXED
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    Q, dt, p, ctx = case(n, N, cfl=10.0, precision=precision)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    cs = O.condensed_operator(A, n, N)
+    g = np.zeros(cs.K * cs.nb)
+    ctx.sc_condensed_rhs(g)
+    assert rel(g, cs.rhs(B)) < tol
+    xb = np.random.default_rng(3).standard_normal(cs.K * cs.nb)
+    dQ = np.zeros(Q.size)
+    ctx.sc_backsubstitute(xb, dQ)
+    assert rel(dQ, cs.back_substitute(B, xb)) < tol
+
+
+def test_newton_step_converges_and_the_oracle_confirms_the_root():
+    """Newton on one backward-Euler step (Jacobian recomputed each iteration): the final
+    state zeroes the oracle's residual of the same step to the requested factor."""
+    from paper_1911_02366_gb300 import sc
+    n, N = 2, 3
+    Q0, dt, p, ctx = case(n, N, cfl=10.0, eps=1e-2, precision=sc.SC_PREC_FP64, rel_tol=1e-10)
+    ctx.sc_set_state(Q0, Q0)
+    its, relr, st = ctx.sc_newton_step(max_newton=10, newton_tol=1e-9)
+    assert its >= 1 and relr <= 1e-9
+    Q = np.zeros(Q0.size)
+    ctx.sc_get_state(Q)
+    Q = Q.reshape(Q0.shape)
+    ps = O.Params(n=n, N=N, dt=dt, bdf=1)
+    R0 = np.linalg.norm(O.residual(ps, Q0, Q0))
+    R = np.linalg.norm(O.residual(ps, Q, Q0))
+    assert R <= 1e-8 * R0, (R, R0)
