@@ -274,6 +274,35 @@ sc_status sc_set_learned_weights(sc_ctx* ctx, const uint16_t* Wbf16, const float
    by ||[S_ee]_kk||_F, to measure what a perfect network would give. */
 sc_status sc_set_learned_correction(sc_ctx* ctx, const float* Ck, float scale);
 
+/* ---- Batched condensation of elements of uneven order ---------------------------
+   Not in the paper: the condensation set-up (A_ii^-1, Y, S_ee, LU of S_ee, solve layout;
+   Sec. 2.2 eq. StaticCondBlock) of several assembled systems, each of one order N (mixed
+   arm, block Jacobi, tensor cores, FP32 factors, implicit operator, one shared stream), run
+   together: the per-element steps as grouped launches over all elements of all orders, the
+   TF32 products per order through tables of block addresses.  After sc_batch_condense each
+   system is condensed exactly as by its own sc_condense and is solved with sc_solve. */
+typedef struct sc_batch sc_batch;
+enum { SC_BATCH_GRAPH = 1,    /* capture the sequence into a CUDA graph once, then replay it */
+       SC_BATCH_AUTOTUNE = 2  /* first call: time the N-tile widths 64/144/256 of every product on
+                                 the batch's data and keep the fastest per order */ };
+
+/* Create a batch over nctx contexts (meshes set; SC_ERR_ARG if one is not as listed above or
+   uses another stream).  The contexts must outlive the batch and keep their meshes; the
+   batch owns a stream of its own, ordered after the contexts' stream at every call. */
+sc_status sc_batch_create(sc_ctx* const* ctxs, int nctx, sc_batch** out);
+
+/* Condense every system of the batch (each assembled, SC_ERR_STATE otherwise); flags:
+   SC_BATCH_GRAPH | SC_BATCH_AUTOTUNE.  Synchronous.  On failure the message is in
+   sc_last_error of the first context. */
+sc_status sc_batch_condense(sc_batch* batch, int flags);
+
+/* Tile widths in use for order class c (classes in order of first appearance): the
+   interior size ni of the class and the N-tile widths of the Y^T, S_ee and trailing-update
+   products. */
+sc_status sc_batch_tiles(const sc_batch* batch, int c, int* ni, int* bn_y, int* bn_s, int* bn_t);
+
+void sc_batch_destroy(sc_batch* batch);
+
 /* ---- Measurement hooks (not part of the method; used by the benchmark) ---------- */
 
 /* Kernel ids for sc_profile_kernel / sc_kernel_work. */

@@ -31,9 +31,10 @@ __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
   }
 }
 
+// A_ii^-1 of one block by one CTA (shared memory: n (n+1) + n values and n pivots).
 template <class T>
-__global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int lda,
-                         T* __restrict__ Ainv, long long strideO, int ldo, int* __restrict__ status) {
+__device__ void gj_inv_body(int n, const T* __restrict__ Ae, int lda, T* __restrict__ Oe, int ldo,
+                            int* __restrict__ status, int e) {
   extern __shared__ unsigned char smem_raw[];
   const int ld = n + 1;
   T* M = reinterpret_cast<T*>(smem_raw);
@@ -41,8 +42,6 @@ __global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int 
   int* piv = reinterpret_cast<int*>(colk + n);
   __shared__ int s_p;
   __shared__ int s_bad;
-  const int e = blockIdx.x;
-  const T* Ae = A + (long long)e * strideA;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t / n, j = t % n;
     M[i * ld + j] = Ae[(long long)i * lda + j];
@@ -93,9 +92,31 @@ __global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int 
       }
     __syncthreads();
   }
-  T* Oe = Ainv + (long long)e * strideO;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) Oe[(long long)(t / n) * ldo + (t % n)] = M[(t / n) * ld + (t % n)];
   if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
+  __syncthreads();
+}
+
+template <class T>
+__global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int lda,
+                         T* __restrict__ Ainv, long long strideO, int ldo, int* __restrict__ status) {
+  const int e = blockIdx.x;
+  gj_inv_body<T>(n, A + (long long)e * strideA, lda, Ainv + (long long)e * strideO, ldo, status, e);
+}
+
+// ---- grouped kernels of the batched condensation: one CTA per CondItem ----------------
+__global__ void k_gj_inv_grouped(const CondItem* __restrict__ items) {
+  const CondItem it = items[blockIdx.x];
+  gj_inv_body<float>(it.ni, it.Aown, it.lda, it.Ainv, it.ldi, it.status, it.e);
+}
+
+__global__ void k_copy_bb_grouped(const CondItem* __restrict__ items) {
+  const CondItem it = items[blockIdx.x];
+  const float* src = it.Aown + (size_t)it.ni * it.lda + it.cb0;
+  for (int t = threadIdx.x; t < it.nb * it.nb; t += blockDim.x) {
+    const int i = t / it.nb, j = t % it.nb;
+    it.See[(size_t)i * it.lds + j] = src[(size_t)i * it.lda + j];
+  }
 }
 
 // C = alpha * A * B + beta * C, all row-major, one batch entry per blockIdx.z.
@@ -305,17 +326,30 @@ __global__ void __launch_bounds__(256) k_lu_panel(int n, int k0, T* __restrict__
   if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
 }
 
+// One panel step of every batched item whose S_ee extends beyond column k0.
+__global__ void __launch_bounds__(256) k_lu_panel_grouped(const CondItem* __restrict__ items, int k0) {
+  extern __shared__ unsigned char smem_raw[];
+  float* P = reinterpret_cast<float*>(smem_raw);
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  const CondItem it = items[blockIdx.x];
+  if (it.nb <= k0) return;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  lu_panel<float>(it.nb, k0, it.See, it.lds, it.piv, P, &s_p, &s_bad);
+  if (threadIdx.x == 0 && s_bad) atomicCAS(it.status, -1, it.e);
+}
+
 // Replace every 32 x 32 diagonal block of the LU factors by the inverses of its
 // triangles: strictly lower part <- (unit lower L_bb)^-1, upper part <- (U_bb)^-1.  The
 // off-diagonal blocks (all the substitutions read besides these) are untouched.  One CTA
 // per element, one warp per block, one lane per column.
 template <class T>
-__global__ void __launch_bounds__(256) k_diag_inv(int n, T* __restrict__ LU, long long stride, int lda) {
+__device__ void diag_inv_body(int n, T* __restrict__ M, int lda) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   T* Ds = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 2 * 32 * 33;  // block, then its inverse
   T* Is = Ds + 32 * 33;
-  T* M = LU + (long long)blockIdx.x * stride;
   const int nblk = (n + 31) / 32;
   for (int b = warp; b < nblk; b += nw) {
     const int i0 = b * 32, bs = min(32, n - i0);
@@ -350,18 +384,37 @@ __global__ void __launch_bounds__(256) k_diag_inv(int n, T* __restrict__ LU, lon
   }
 }
 
+template <class T>
+__global__ void __launch_bounds__(256) k_diag_inv(int n, T* __restrict__ LU, long long stride, int lda) {
+  diag_inv_body<T>(n, LU + (long long)blockIdx.x * stride, lda);
+}
+
+__global__ void __launch_bounds__(256) k_diag_inv_grouped(const CondItem* __restrict__ items) {
+  const CondItem it = items[blockIdx.x];
+  diag_inv_body<float>(it.nb, it.See, it.lds);
+}
+
 // Sequential LAPACK-style row interchanges -> one gather permutation per element:
 // row i of P A is row rowperm[i] of A.
-__global__ void k_piv_to_perm(int n, const int* __restrict__ piv_all, int* __restrict__ rowperm, int nelem) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nelem) return;
-  const int* piv = piv_all + (long long)e * n;
-  int* rp = rowperm + (long long)e * n;
+__device__ void piv_to_perm_body(int n, const int* __restrict__ piv, int* __restrict__ rp) {
   for (int i = 0; i < n; ++i) rp[i] = i;
   for (int k = 0; k < n; ++k) {
     const int p = piv[k];
     if (p != k) { const int t = rp[k]; rp[k] = rp[p]; rp[p] = t; }
   }
+}
+
+__global__ void k_piv_to_perm(int n, const int* __restrict__ piv_all, int* __restrict__ rowperm, int nelem) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nelem) return;
+  piv_to_perm_body(n, piv_all + (long long)e * n, rowperm + (long long)e * n);
+}
+
+__global__ void k_piv_to_perm_grouped(const CondItem* __restrict__ items, int nitems) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nitems) return;
+  const CondItem it = items[t];
+  piv_to_perm_body(it.nb, it.piv, it.rowperm);
 }
 
 
@@ -408,16 +461,12 @@ template <> struct Quad<float, __half> {
 // With LS16 non-null (FP32 factors only) the layout is also written in FP16; an entry
 // beyond the FP16 range sets *ovf.
 template <class T>
-__global__ void __launch_bounds__(256) k_solve_prep(int n, const T* __restrict__ LU, long long stride, int lda,
-                                                    T* __restrict__ LS, long long lsstride, int npad,
-                                                    __half* __restrict__ LS16, int* __restrict__ ovf) {
+__device__ void solve_prep_body(int n, int b, const T* __restrict__ M, int lda, T* __restrict__ out, int npad,
+                                __half* __restrict__ out16, int* __restrict__ ovf) {
   __shared__ T TL[32][33];  // L_bb^-1: unit diagonal, stored inverse below it
   __shared__ T TU[32][33];  // U_bb^-1: stored inverse on and above the diagonal
   __shared__ T D[32][33];   // diagonal block as stored (both inverse triangles)
-  const int b = blockIdx.x, e = blockIdx.y, i0 = 32 * b, bs = min(32, n - i0);
-  const T* M = LU + (long long)e * stride;
-  T* out = LS + (long long)e * lsstride + (long long)b * 32 * npad;
-  __half* out16 = LS16 ? LS16 + (long long)e * lsstride + (long long)b * 32 * npad : nullptr;
+  const int i0 = 32 * b, bs = min(32, n - i0);
   bool big = false;
   for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
     const int r = t / 32, k = t % 32;
@@ -452,6 +501,22 @@ __global__ void __launch_bounds__(256) k_solve_prep(int n, const T* __restrict__
     }
   }
   if (out16 && big) atomicExch(ovf, 1);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_solve_prep(int n, const T* __restrict__ LU, long long stride, int lda,
+                                                    T* __restrict__ LS, long long lsstride, int npad,
+                                                    __half* __restrict__ LS16, int* __restrict__ ovf) {
+  const int b = blockIdx.x, e = blockIdx.y;
+  const long long off = (long long)e * lsstride + (long long)b * 32 * npad;
+  solve_prep_body<T>(n, b, LU + (long long)e * stride, lda, LS + off, npad, LS16 ? LS16 + off : nullptr, ovf);
+}
+
+__global__ void __launch_bounds__(256) k_solve_prep_grouped(const CondItem* __restrict__ items) {
+  const CondItem it = items[blockIdx.y];
+  const int b = blockIdx.x, nblk = (it.nb + 31) / 32, npad = (it.nb + 3) & ~3;
+  if (b >= nblk) return;
+  solve_prep_body<float>(it.nb, b, it.See, it.lds, it.Sls + (long long)b * 32 * npad, npad, nullptr, nullptr);
 }
 
 // In-place (L U)^-1 s of one element's factors Le in the solve layout, by one warp: lane r
@@ -763,6 +828,44 @@ cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
 }
 
 size_t solve_layout_elems(const Geo& G) { return (size_t)G.K * ls_stride(G); }
+
+// ---- grouped launches of the batched condensation (one CTA per CondItem) --------------
+cudaError_t grouped_gj(cudaStream_t st, const CondItem* items, int n, int max_ni) {
+  const size_t smem = (size_t)max_ni * (max_ni + 1) * sizeof(float) + max_ni * sizeof(float) + max_ni * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(k_gj_inv_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gj_inv_grouped<<<n, 256, smem, st>>>(items);
+  return cudaGetLastError();
+}
+
+cudaError_t grouped_copy_bb(cudaStream_t st, const CondItem* items, int n) {
+  k_copy_bb_grouped<<<n, 256, 0, st>>>(items);
+  return cudaGetLastError();
+}
+
+cudaError_t grouped_lu_panel(cudaStream_t st, const CondItem* items, int n, int k0, int max_nb) {
+  const size_t smem = (size_t)max_nb * (PW + 1) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_lu_panel_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_lu_panel_grouped<<<n, 256, smem, st>>>(items, k0);
+  return cudaGetLastError();
+}
+
+cudaError_t grouped_finish(cudaStream_t st, const CondItem* items, int n, int max_nb) {
+  k_piv_to_perm_grouped<<<cdiv(n, 128), 128, 0, st>>>(items, n);
+  const size_t dsm = (size_t)8 * 2 * 32 * 33 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_diag_inv_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+  if (e != cudaSuccess) return e;
+  k_diag_inv_grouped<<<n, 256, dsm, st>>>(items);
+  k_solve_prep_grouped<<<dim3((max_nb + 31) / 32, n), 256, 0, st>>>(items);
+  return cudaGetLastError();
+}
+
+cudaError_t to_float(sc_ctx* c, const double* a, float* b, size_t n) {
+  count_launch(c);
+  k_to_float<<<608, 256, 0, c->stream>>>(a, b, n);
+  return cudaGetLastError();
+}
 
 // C = A B for `batch` row-major FP32 blocks on the CUDA cores.
 cudaError_t gemm_fp32(sc_ctx* c, int M, int N, int K, const float* A, long long sA, int lda, const float* B,

@@ -333,6 +333,17 @@ struct ProfScope {
 inline void count_launch(sc_ctx* c, int n = 1) { c->launches += n; }
 
 // kernels launchers (defined in the .cu files)
+// One element of a batched condensation (elements of several systems, any order): its
+// sizes and the addresses of its FP32 blocks.
+struct CondItem {
+  int ni, nb, lda, ldi, lds, e;  // sizes and leading dimensions; e: element index reported on failure
+  const float* Aown;              // own block (ne x lda), interior columns first, boundary at cb0
+  int cb0;
+  float *Ainv, *Yt, *See, *Sls;   // A_ii^-1 (ni x ldi), Y^T (nb x ldi), S_ee (nb x lds), solve layout
+  int *piv, *rowperm;
+  int* status;
+};
+
 // Status word value written by a tensor-core kernel whose bounded wait ran out (element
 // indices written by the factorisations are far below it).
 constexpr int SC_TC_TIMEOUT = 1 << 30;
@@ -384,6 +395,14 @@ cudaError_t upload_explicit_tables(sc_ctx* c);
 size_t explicit_elems_W(const Geo& G, const sc_ctx* c);
 cudaError_t explicit_build(sc_ctx* c);
 cudaError_t explicit_matvec32(sc_ctx* c, const float* x, double* y);
+cudaError_t grouped_gj(cudaStream_t st, const CondItem* items, int n, int max_ni);
+cudaError_t grouped_copy_bb(cudaStream_t st, const CondItem* items, int n);
+cudaError_t grouped_lu_panel(cudaStream_t st, const CondItem* items, int n, int k0, int max_nb);
+cudaError_t grouped_finish(cudaStream_t st, const CondItem* items, int n, int max_nb);
+cudaError_t to_float(sc_ctx* c, const double* a, float* b, size_t n);
+cudaError_t gemm_tf32_ptrs(cudaStream_t stream, int M, int N, int K, float alpha, const float* const* Ap, int lda,
+                           bool ta, const float* const* Bp, int ldb, bool tb, float beta, float* const* Cp, int ldc,
+                           int batch, int bn, int* status);
 cudaError_t gemm_fp32(sc_ctx* c, int M, int N, int K, const float* A, long long sA, int lda, const float* B,
                       long long sB, int ldb, float* C, long long sC, int ldc, int batch);
 cudaError_t extract_sdiag(sc_ctx* c, const float* See);

@@ -16,6 +16,7 @@
 //   * the four warps read their 32 TMEM lanes (rows) with tcgen05.ld and write
 //     C = alpha * acc + beta * C.
 #include <cstdint>
+#include <type_traits>
 
 #include "sc_internal.cuh"
 
@@ -202,7 +203,9 @@ template <int BN, bool TA, bool TB>
 __global__ void __launch_bounds__(128) k_gemm_tf32(int M, int N, int K, float alpha, const float* __restrict__ A,
                                                    long long sA, int lda, const float* __restrict__ B, long long sB,
                                                    int ldb, float beta, float* __restrict__ C, long long sC, int ldc,
-                                                   int flags, int* __restrict__ status) {
+                                                   int flags, int* __restrict__ status,
+                                                   const float* const* __restrict__ Ap,
+                                                   const float* const* __restrict__ Bp, float* const* __restrict__ Cp) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= TC_TMEM_COLS, "M = 128 needs N % 16 == 0 and N <= 256");
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr size_t kA = (size_t)(TC_BM / 8) * TC_SBO, kStage = tc_stage_bytes<BN>();
@@ -210,9 +213,15 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(int M, int N, int K, float al
   __shared__ uint32_t tmem_base_s;
   __shared__ int s_err;
   const int z = blockIdx.z;
-  A += z * sA;
-  B += z * sB;
-  C += z * sC;
+  if (Ap) {  // per-entry block addresses (batched condensation of several systems)
+    A = Ap[z];
+    B = Bp[z];
+    C = Cp[z];
+  } else {
+    A += z * sA;
+    B += z * sB;
+    C += z * sC;
+  }
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool vecA = flags & 1, vecB = flags & 2, vecC = flags & 4;
@@ -340,7 +349,8 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(int M, int N, int K, float al
 template <int BN, bool TA, bool TB>
 cudaError_t launch_tf32(cudaStream_t stream, int M, int N, int K, float alpha, const float* A, long long sA, int lda,
                         const float* B, long long sB, int ldb, float beta, float* C, long long sC, int ldc, int batch,
-                        int flags, int* status) {
+                        int flags, int* status, const float* const* Ap = nullptr, const float* const* Bp = nullptr,
+                        float* const* Cp = nullptr) {
   constexpr size_t smem = 2 * tc_stage_bytes<BN>();
   // two CTAs per SM: 2 x 256 TMEM columns fill the 512 of an SM
   static_assert(2 * (smem + 1024) <= 228 * 1024, "two CTAs per SM must fit");
@@ -348,7 +358,7 @@ cudaError_t launch_tf32(cudaStream_t stream, int M, int N, int K, float alpha, c
   if (e != cudaSuccess) return e;
   dim3 grid((N + BN - 1) / BN, (M + TC_BM - 1) / TC_BM, batch);
   k_gemm_tf32<BN, TA, TB><<<grid, 128, smem, stream>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC, ldc, flags,
-                                                       status);
+                                                       status, Ap, Bp, Cp);
   return cudaGetLastError();
 }
 
@@ -396,6 +406,37 @@ cudaError_t gemm_tf32(cudaStream_t stream, int M, int N, int K, float alpha, con
                               status);
   return launch_tf32_t<256>(stream, M, N, K, alpha, A, sA, lda, ta, B, sB, ldb, tb, beta, C, sC, ldc, batch, flags,
                             status);
+}
+
+// Pointer-table form: entry z multiplies Ap[z], Bp[z] into Cp[z] (row-major, the given
+// leading dimensions; rows are read as float4 when the leading dimensions are multiples
+// of 4, which holds for every condensation block), N-tile width bn in {64, 144, 256}.
+cudaError_t gemm_tf32_ptrs(cudaStream_t stream, int M, int N, int K, float alpha, const float* const* Ap, int lda,
+                           bool ta, const float* const* Bp, int ldb, bool tb, float beta, float* const* Cp, int ldc,
+                           int batch, int bn, int* status) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  const int flags = (lda % 4 == 0 ? 1 : 0) | (ldb % 4 == 0 ? 2 : 0) | (ldc % 4 == 0 ? 4 : 0);
+  const float* A0 = nullptr;
+  const float* B0 = nullptr;
+  float* C0 = nullptr;
+  auto go = [&](auto bnc) -> cudaError_t {
+    constexpr int BNC = decltype(bnc)::value;
+    if (!ta && !tb)
+      return launch_tf32<BNC, false, false>(stream, M, N, K, alpha, A0, 0, lda, B0, 0, ldb, beta, C0, 0, ldc, batch,
+                                            flags, status, Ap, Bp, Cp);
+    if (!ta && tb)
+      return launch_tf32<BNC, false, true>(stream, M, N, K, alpha, A0, 0, lda, B0, 0, ldb, beta, C0, 0, ldc, batch,
+                                           flags, status, Ap, Bp, Cp);
+    if (ta && !tb)
+      return launch_tf32<BNC, true, false>(stream, M, N, K, alpha, A0, 0, lda, B0, 0, ldb, beta, C0, 0, ldc, batch,
+                                           flags, status, Ap, Bp, Cp);
+    return launch_tf32<BNC, true, true>(stream, M, N, K, alpha, A0, 0, lda, B0, 0, ldb, beta, C0, 0, ldc, batch, flags,
+                                        status, Ap, Bp, Cp);
+  };
+  if (bn == 64) return go(std::integral_constant<int, 64>{});
+  if (bn == 144) return go(std::integral_constant<int, 144>{});
+  return go(std::integral_constant<int, 256>{});
 }
 
 }  // namespace sc

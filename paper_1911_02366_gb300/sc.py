@@ -54,7 +54,8 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_launch_count", "sc_profile_kernel", "sc_profile_read", "sc_kernel_work",
            "sc_condensed_matvec_static", "sc_gemm_tf32", "sc_mlp_forward", "sc_mlp_backward", "sc_mlp_loss",
            "sc_mlp_adam", "sc_learned_features", "sc_learned_targets", "sc_set_learned_weights", "sc_set_learned_correction",
-           "sc_get_state", "sc_condensed_rhs", "sc_backsubstitute", "sc_newton_step"]
+           "sc_get_state", "sc_condensed_rhs", "sc_backsubstitute", "sc_newton_step", "sc_batch_create",
+           "sc_batch_condense", "sc_batch_tiles", "sc_batch_destroy"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -107,13 +108,17 @@ def lib(build_if_missing: bool = True):
     L.sc_backsubstitute.argtypes = [vp, dp, dp, ctypes.c_int]
     L.sc_newton_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(sc_solve_stats),
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.sc_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+    L.sc_batch_condense.argtypes = [vp, ctypes.c_int]
+    L.sc_batch_tiles.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip]
+    L.sc_batch_destroy.argtypes = [vp]; L.sc_batch_destroy.restype = None
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
     L.sc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
     L.sc_kernel_work.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for f in EXPORTS:
-        if f not in ("sc_destroy", "sc_last_error"):
+        if f not in ("sc_destroy", "sc_last_error", "sc_batch_destroy"):
             getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -420,3 +425,46 @@ class MLP:
                 self.adam(lr)
             hist.append(float(acc.item()) / max(len(starts), 1))
         return hist
+
+
+SC_BATCH_GRAPH, SC_BATCH_AUTOTUNE = 1, 2
+
+
+class Batch:
+    """Batched condensation of several assembled systems of (possibly) different orders."""
+
+    def __init__(self, contexts):
+        self._L = lib()
+        self.h = None
+        self.contexts = list(contexts)  # kept alive with the batch
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h for c in self.contexts])
+        h = ctypes.c_void_p()
+        s = self._L.sc_batch_create(arr, len(self.contexts), ctypes.byref(h))
+        if s != SC_OK:
+            raise SCError(s, "sc_batch_create failed")
+        self.h = h
+
+    def condense(self, graph=True, autotune=True):
+        flags = (SC_BATCH_GRAPH if graph else 0) | (SC_BATCH_AUTOTUNE if autotune else 0)
+        s = self._L.sc_batch_condense(self.h, flags)
+        if s != SC_OK:
+            msg = self._L.sc_last_error(self.contexts[0].h).decode()
+            raise SCError(s, msg or "sc_batch_condense failed")
+
+    def tiles(self, c):
+        v = [ctypes.c_int() for _ in range(4)]
+        s = self._L.sc_batch_tiles(self.h, c, *[ctypes.byref(x) for x in v])
+        if s != SC_OK:
+            raise SCError(s, "sc_batch_tiles failed")
+        return tuple(x.value for x in v)
+
+    def close(self):
+        if self.h:
+            self._L.sc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
