@@ -5,7 +5,7 @@ workload (2,560,000 DOF, CFL 50): residual + Jacobian assembly, static condensat
 (A_ii^-1, element Schur blocks, block-Jacobi factors), condensed right-hand side,
 GMRES to a global relative residual of 1e-8, back-substitution.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--arm fp64|mixed|learned] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--arm fp64|mixed|learned|batched] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  N > 1 runs independent replicas (one per GPU); the
 path has no collective.  `--impl reference` times the FP64 CPU oracle on a bounded
@@ -323,6 +323,134 @@ def run_oracle(steps: int):
                       "one linear solve (condense, GMRES(30) to 1e-8, back-substitute), Jacobian assembled beforehand"}
 
 
+BATCH_ORDERS = ((7, 2), (7, 3), (7, 4))  # (elements per direction, N) of the uneven-order batch
+BATCH_CFL = 10.0  # GMRES(30) stalls on these small meshes at CFL 50
+
+
+def run_batched(args, world, rank, local):
+    """Uneven-order batch: one system per order N = 2, 3, 4 on 7^3 elements each (1029
+    elements, ~ the orders 2-4 share of a 12^3 mesh with N drawn from 2..6).  A step
+    assembles every system, condenses all of them in one replayed CUDA graph (grouped
+    launches, autotuned TF32 tiles) and solves each to 1e-8."""
+    import torch
+    from paper_1911_02366_gb300 import sc
+
+    torch.cuda.set_device(local)
+    W = WORKLOAD
+    stream = torch.cuda.current_stream()
+    ctxs, states, dofs = [], [], 0
+    for n, N in BATCH_ORDERS:
+        Q, dt = I.tgv_state(n, N, Ma=W["Ma"], seed=W["seed"], cfl=BATCH_CFL)
+        c = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
+                       gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
+                       inner_tol=args.inner_tol, max_refine=20)
+        c.sc_set_mesh(n, 2 * math.pi, N)
+        c.sc_set_timestep(dt, 1)
+        Qd = torch.tensor(Q.reshape(-1), device="cuda")
+        c.sc_set_state(Qd, Qd)
+        ctxs.append(c)
+        states.append((Qd, torch.zeros_like(Qd)))
+        dofs += Q.size
+    batch = sc.Batch(ctxs)
+
+    def step(batched=True):
+        for c in ctxs:
+            c.sc_assemble()
+        if batched:
+            batch.condense(graph=True, autotune=True)
+        else:
+            for c in ctxs:
+                c.sc_condense()
+        return [c.sc_solve(dq, raise_on_not_converged=not args.allow_unconverged) for c, (_, dq) in zip(ctxs, states)]
+
+    def condense_ms(batched, reps=3):
+        for c in ctxs:
+            c.sc_assemble()
+        t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            if batched:
+                batch.condense(graph=True, autotune=True)
+            else:
+                for c in ctxs:
+                    c.sc_condense()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / reps
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    big = ctxs[-1]
+    big.sc_profile_kernel(sc.SC_KERNEL_LU_SOLVE)
+    sampler = ClockSampler(local) if rank == 0 else None
+    l0 = sum(c.sc_launch_count() for c in ctxs)
+    barrier(world)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True); end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(step())
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = sum(c.sc_launch_count() for c in ctxs) - l0
+    clocks = sampler.stop() if sampler else None
+    n_prof, prof_ms = big.sc_profile_read()
+    big.sc_profile_kernel(-1)
+    total_ms = gather_max(world, start.elapsed_time(end))
+    worst = max(s["rel_residual"] for st in stats for s in st)
+    ms_batched = condense_ms(True)
+    ms_separate = condense_ms(False)
+
+    # end to end: host (pinned) states in, host updates out
+    hosts = [(torch.tensor(Qd.cpu().numpy()).pin_memory(), torch.zeros(Qd.numel(), dtype=torch.float64).pin_memory())
+             for Qd, _ in states]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for c, (qh, _) in zip(ctxs, hosts):
+            c.sc_set_state(qh, qh)
+            c.sc_assemble()
+        batch.condense(graph=True, autotune=True)
+        for c, (_, dqh) in zip(ctxs, hosts):
+            c.sc_solve(dqh, raise_on_not_converged=not args.allow_unconverged)
+    torch.cuda.synchronize()
+    e2e_s = gather_max(world, time.perf_counter() - t0)
+
+    flops, bytes_ = big.sc_kernel_work(sc.SC_KERNEL_LU_SOLVE)
+    avg_ms = prof_ms / max(n_prof, 1)
+    peaks = measured_peaks()
+    roof = {"bound": "hbm", "achieved": bytes_ / (avg_ms * 1e-3) / 1e9, "peak": float(peaks["hbm_gbs"]),
+            "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update(traffic=None, kernel="k_lu_solve (N = 4 system)", launches_timed=n_prof, avg_launch_ms=avg_ms)
+    tiles = {f"ni={t[0]}": {"Y": t[1], "S": t[2], "LU": t[3]} for t in (batch.tiles(i) for i in range(3))}
+    line = {
+        "metric": METRIC, "value": world * dofs * args.steps / (total_ms * 1e-3), "unit": "DOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded Taylor-Green states, 1e-3 perturbation)",
+        "config": {"workload": "tgv_uneven_order_7x7x7_N2_N3_N4_cfl10", "systems": [list(o) for o in BATCH_ORDERS],
+                   "elements": sum(n ** 3 for n, _ in BATCH_ORDERS), "dof": dofs, "cfl": BATCH_CFL,
+                   "arm": "batched", "gmres_restart": args.restart, "inner_tol": args.inner_tol,
+                   "l2": "element blocks of the three systems below L2 size are not flushed between steps",
+                   "parallelism": f"replicas x{world}"},
+        "condense_ms_batched_graph": ms_batched, "condense_ms_separate": ms_separate, "autotuned_tiles": tiles,
+        "gmres_iters": [[s["gmres_iters"] for s in st] for st in stats], "rel_residual_max": worst,
+        "converged": worst <= REL_TOL,
+        "e2e": {"value": world * dofs * e2e_steps / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 2 * dofs * 8,
+                "d2h_bytes_per_step": dofs * 8},
+        "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+    }
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return line
+
+
 def cpu_threads():
     try:
         import oracle as O
@@ -337,7 +465,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--arm", choices=["fp64", "mixed", "learned"], default="mixed")
+    ap.add_argument("--arm", choices=["fp64", "mixed", "learned", "batched"], default="mixed")
     ap.add_argument("--train-epochs", type=int, default=20, help="learned arm: training epochs (untimed)")
     ap.add_argument("--operator", choices=["implicit", "explicit"], default="implicit",
                     help="mixed arm: condensed operator applied implicitly or from explicit W_e blocks")
@@ -376,9 +504,9 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    line = run_ours(args, world, rank, local)
+    line = run_batched(args, world, rank, local) if args.arm == "batched" else run_ours(args, world, rank, local)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.arm != "batched":
             r = run_oracle(1)
             v = r["dof"] / r["seconds"][0]
             line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cpu_threads(), "kind": "oracle",

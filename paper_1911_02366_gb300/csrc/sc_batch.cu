@@ -43,6 +43,7 @@ struct sc_batch {
   int max_ni = 0, max_nb = 0;
   int* d_status = nullptr;
   bool tuned = false;
+  long long grouped_launches = 0;  // kernel launches of one run outside the systems' own
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -85,6 +86,13 @@ cudaError_t run_all(sc_batch* b, cudaStream_t st) {
     c->stream = own;
   }
   const int n = (int)b->items.size();
+  // grouped launches of this run: GJ, copy, 3 finishing kernels, the products and the panels
+  long long nl = 5 + 2 * (long long)b->cls.size();
+  for (int step = 0; 32 * step < b->max_nb; ++step) {
+    ++nl;
+    for (const OrderClass& oc : b->cls) nl += step < (int)oc.off_t.size() ? 1 : 0;
+  }
+  b->grouped_launches = nl;
   if (e == cudaSuccess) e = sc::grouped_gj(st, b->d_items, n, b->max_ni);
   for (const OrderClass& oc : b->cls)
     if (e == cudaSuccess) e = run_products_y(b, st, oc, oc.bn_y);
@@ -277,6 +285,9 @@ sc_status sc_batch_condense(sc_batch* b, int flags) {
       return batch_fail(b, SC_ERR_CUDA, "status read");
     if (cb >= 0) return batch_fail(b, SC_ERR_STATE, "own-block entry outside the packed node pattern");
   }
+  b->ctx[0]->launches += b->grouped_launches;  // the systems count their own conversions
+  if (use_graph)
+    for (sc_ctx* c : b->ctx) c->launches += 3;  // replayed conversions of each system
   for (sc_ctx* c : b->ctx) {
     c->packed = true;
     c->condensed = true;
