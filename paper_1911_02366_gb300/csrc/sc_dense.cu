@@ -583,9 +583,10 @@ __device__ __forceinline__ void ls_solve_warp(int n, int nblk, const TS* __restr
 
 // z = (P^T L U)^-1 v, one warp per element (4 per CTA); the running vector (v, then x,
 // then z) sits in shared memory.  Arithmetic in the factor precision T; v in double,
-// outputs z (double) and / or zt (T).  Ck (or null): a 5 x 5 correction per boundary node
-// added as z_k += C_k v_k (the learned correction of the block-Jacobi inverse).
-template <class T, class TS>
+// outputs z (double) and / or zt (T).  CORR: add a 5 x 5 correction per boundary node,
+// z_k += C_k v_k (the learned correction of the block-Jacobi inverse); a separate
+// instantiation, because the branch alone slowed the plain solve by 14 %.
+template <class T, class TS, bool CORR>
 __global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const TS* __restrict__ LS, long long lsstride,
                                                   int npad, const int* __restrict__ rowperm,
                                                   const double* __restrict__ v, double* __restrict__ z,
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const TS* __r
   ls_solve_warp<T, TS>(n, nblk, LS + (long long)e * lsstride, npad, s, lane);
   for (int i = lane; i < n; i += 32) {
     T val = s[i];
-    if (Ck) {
+    if (CORR) {  // compiled only into the corrected variant: the plain loop stays lean
       const int a = i / 5, k = i - 5 * a;
       const float* C = Ck + ((long long)e * (n / 5) + a) * 25 + 5 * k;
       const double* va = ve + 5 * a;
@@ -798,9 +799,12 @@ cudaError_t lu_solve_t(sc_ctx* c, const TS* LS, const double* v, double* z, T* z
   const Geo& G = c->G;
   ProfScope ps(c, SCK_LU_SOLVE);
   const size_t smem = (size_t)4 * ls_nblk(G) * 32 * sizeof(T);
-  k_lu_solve<T, TS><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
-                                                            c->rowperm, v, z, zt, G.K,
-                                                            c->learned_on ? c->Ck : nullptr);
+  if (c->learned_on && c->Ck)
+    k_lu_solve<T, TS, true><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
+                                                                    c->rowperm, v, z, zt, G.K, c->Ck);
+  else
+    k_lu_solve<T, TS, false><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
+                                                                     ls_npad(G), c->rowperm, v, z, zt, G.K, nullptr);
   return cudaGetLastError();
 }
 
