@@ -17,6 +17,13 @@
 
 namespace {
 
+// Resident CTAs per SM asked of the operator passes: the FP32 passes are latency-bound at
+// their natural 64 registers (4 CTAs); capping them at 40 (6 CTAs) measured 14 % (boundary)
+// and 29 % (interior) faster at 16^3, N = 4.  The FP64 passes are FP64-ALU bound and keep
+// their natural allocation (3 CTAs allow the 71-80 registers they use).
+template <class T> struct PkOcc { static constexpr int v = 3; };
+template <> struct PkOcc<float> { static constexpr int v = 6; };
+
 template <class T> struct PkVec;
 template <> struct PkVec<float> { using type = float4; static constexpr int n = 4; };
 template <> struct PkVec<double> { using type = double2; static constexpr int n = 2; };
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(256) k_pack(Geo G, const double* __restrict__ 
 // Interior pass: u_e = A_ii,e^-1 (alpha B_i,e + beta (A_ib x_b)_e), A_ib from the packed
 // own block and the neighbour couplings; one warp per interior node (its 5 rows).
 template <class T>
-__global__ void __launch_bounds__(256) k_cond_interior_pk(Geo G, const T* __restrict__ Apk, long long pstride,
+__global__ void __launch_bounds__(256, PkOcc<T>::v) k_cond_interior_pk(Geo G, const T* __restrict__ Apk, long long pstride,
     const int* __restrict__ row_off, const int* __restrict__ lptr, const int* __restrict__ list,
     const T* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
     const int* __restrict__ pinfo, const T* __restrict__ Ainv, const int* __restrict__ iperm,
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(256) k_cond_interior_pk(Geo G, const T* __rest
 // block and the neighbour couplings (delta x_b of boundary neighbours, -u of interior
 // ones); one warp per boundary node (its 5 rows).
 template <class T>
-__global__ void __launch_bounds__(256) k_cond_boundary_pk(Geo G, const T* __restrict__ Apk, long long pstride,
+__global__ void __launch_bounds__(256, PkOcc<T>::v) k_cond_boundary_pk(Geo G, const T* __restrict__ Apk, long long pstride,
     const int* __restrict__ row_off, const int* __restrict__ lptr, const int* __restrict__ list,
     const T* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
     const int* __restrict__ pinfo, const int* __restrict__ iperm, const T* __restrict__ xb, double delta,
