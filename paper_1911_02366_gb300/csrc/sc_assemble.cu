@@ -330,7 +330,7 @@ SC_HD void own_entry(const Geo& G, const double* NJ, const double* RJ, const int
   }
 }
 
-__global__ void __launch_bounds__(256) k_asm_own(Geo G, const double* __restrict__ NJ,
+__global__ void __launch_bounds__(256, 3) k_asm_own(Geo G, const double* __restrict__ NJ,
                                                  const double* __restrict__ RJ,
                                                  const int* __restrict__ nbr, const int* __restrict__ iperm,
                                                  double* __restrict__ Aown) {
@@ -338,8 +338,15 @@ __global__ void __launch_bounds__(256) k_asm_own(Geo G, const double* __restrict
   const int nn = G.nn, lda = G.lda;
   for (int t = threadIdx.x; t < nn * nn; t += blockDim.x) {
     const int pj = t / nn, pr = t % nn;
+    const int j = iperm[pj], r = iperm[pr];
+    int cj[3], cr[3];
+    node_coords(j, G.p, cj);
+    node_coords(r, G.p, cr);
+    // node pairs sharing no GL index are structurally zero and keep the zeros written
+    // when the mesh was set
+    if (cj[0] != cr[0] && cj[1] != cr[1] && cj[2] != cr[2]) continue;
     double acc[25];
-    own_entry(G, NJ, RJ, nbr, e, iperm[pj], iperm[pr], acc);
+    own_entry(G, NJ, RJ, nbr, e, j, r, acc);
     double* out = Aown + (size_t)e * own_stride(G) + (size_t)(5 * pj) * lda + own_col(G, pr, 0);
     for (int k = 0; k < 5; ++k)
       for (int l = 0; l < 5; ++l) out[(size_t)k * lda + l] = acc[k * 5 + l];
