@@ -650,17 +650,11 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
         SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
         SC_CUDA(sc::cond_boundary(c, c->Zv, 1.0, nullptr, 0.0, c->Ui, c->Wv));
       }
-      // classical Gram-Schmidt twice: each projection update also yields the next sums
       SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h1));
-      if (j + 1 <= 32) {
-        SC_CUDA(sc::update_dot(c, c->Wv, c->V, j + 1, n1, h1, false, h2));
-        SC_CUDA(sc::update_dot(c, c->Wv, c->V, j + 1, n1, h2, true, hn2));
-      } else {
-        SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, h1, -1.0));
-        SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h2));
-        SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, h2, -1.0));
-        SC_CUDA(sc::multidot(c, c->Wv, 1, n1, c->Wv, hn2));
-      }
+      SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, h1, -1.0));
+      SC_CUDA(sc::multidot(c, c->V, j + 1, n1, c->Wv, h2));
+      SC_CUDA(sc::vec_update(c, c->Wv, c->V, j + 1, n1, h2, -1.0));
+      SC_CUDA(sc::multidot(c, c->Wv, 1, n1, c->Wv, hn2));
       SC_CUDA(cudaMemcpyAsync(hbuf.data(), c->Hd, (2 * (m + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       SC_CUDA(cudaStreamSynchronize(c->stream));
       double* Hc = &H[(size_t)j];  // column j, row stride m

@@ -419,7 +419,5 @@ cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* X, const T* Ainv,
 template <class T>
 cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* X, const T* xb, double delta, const double* Bfull,
                              double gamma_, const T* u, double* y);
-cudaError_t update_dot(sc_ctx* c, double* w, const double* V, int nvec, size_t n, const double* coef_dev, bool norm,
-                       double* out_dev);
 cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b, size_t n);
 }  // namespace sc

@@ -323,52 +323,6 @@ __global__ void k_vec_update(double* __restrict__ w, const double* __restrict__ 
   }
 }
 
-// w <- w - sum_i coef_i V_i and, in the same sweep over V, the partial sums of the next
-// Gram-Schmidt pass, partial[i][block] = sum_t V_i[t] w[t] (NORM: partial[0][block] =
-// sum_t w[t]^2 instead).  MAXV >= nvec bounds the accumulators held per thread.
-template <int MAXV, int THREADS, bool NORM>
-__global__ void __launch_bounds__(THREADS) k_update_dot(double* __restrict__ w, const double* __restrict__ V, int nvec,
-                                                        size_t n,
-                             const double* __restrict__ coef, double* __restrict__ partial) {
-  __shared__ double cs[MAXV];
-  __shared__ double red[THREADS / 32][MAXV];
-  if (threadIdx.x < MAXV) cs[threadIdx.x] = threadIdx.x < nvec ? coef[threadIdx.x] : 0.0;
-  __syncthreads();
-  double p[NORM ? 1 : MAXV];
-#pragma unroll
-  for (int i = 0; i < (NORM ? 1 : MAXV); ++i) p[i] = 0.0;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-#pragma unroll
-    for (int i = 0; i < MAXV; ++i)
-      if (i < nvec) s = fma(cs[i], V[(size_t)i * n + t], s);
-    const double wt = w[t] - s;
-    w[t] = wt;
-    if (NORM) {
-      p[0] = fma(wt, wt, p[0]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < (NORM ? 1 : MAXV); ++i)
-        if (i < nvec) p[i] = fma(V[(size_t)i * n + t], wt, p[i]);
-    }
-  }
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  const int nout = NORM ? 1 : nvec;
-#pragma unroll
-  for (int i = 0; i < (NORM ? 1 : MAXV); ++i) {
-    if (i < nout) {
-      const double r = warp_sum(p[i]);
-      if (lane == 0) red[warp][i] = r;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < nout) {
-    double r = 0.0;
-    for (int k = 0; k < (int)(blockDim.x / 32); ++k) r += red[k][threadIdx.x];
-    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = r;
-  }
-}
-
 __global__ void k_scale_copy(double* __restrict__ dst, const double* __restrict__ src, size_t n,
                              const double* __restrict__ scal, int invert) {
   const double a = invert ? 1.0 / scal[0] : scal[0];
@@ -493,27 +447,6 @@ cudaError_t multidot(sc_ctx* c, const double* V, int nvec, size_t n, const doubl
   count_launch(c, 2);
   k_multidot_partial<<<dim3(chunks, nvec), 256, 0, c->stream>>>(V, n, w, c->partial);
   k_multidot_final<<<nvec, 256, 0, c->stream>>>(c->partial, chunks, nvec, out_dev);
-  return cudaGetLastError();
-}
-
-// w <- w - V coef, then out_dev = V^T w (norm: out_dev[0] = w^T w), one sweep over V.
-cudaError_t update_dot(sc_ctx* c, double* w, const double* V, int nvec, size_t n, const double* coef_dev, bool norm,
-                       double* out_dev) {
-  if (nvec < 1 || nvec > 32) return cudaErrorInvalidValue;
-  count_launch(c, 2);
-  double* P = c->partial;
-  cudaStream_t st = c->stream;
-  if (nvec <= 8) {
-    if (norm) k_update_dot<8, 512, true><<<kDotChunks, 512, 0, st>>>(w, V, nvec, n, coef_dev, P);
-    else k_update_dot<8, 512, false><<<kDotChunks, 512, 0, st>>>(w, V, nvec, n, coef_dev, P);
-  } else if (nvec <= 16) {
-    if (norm) k_update_dot<16, 256, true><<<kDotChunks, 256, 0, st>>>(w, V, nvec, n, coef_dev, P);
-    else k_update_dot<16, 256, false><<<kDotChunks, 256, 0, st>>>(w, V, nvec, n, coef_dev, P);
-  } else {
-    if (norm) k_update_dot<32, 256, true><<<kDotChunks, 256, 0, st>>>(w, V, nvec, n, coef_dev, P);
-    else k_update_dot<32, 256, false><<<kDotChunks, 256, 0, st>>>(w, V, nvec, n, coef_dev, P);
-  }
-  k_multidot_final<<<norm ? 1 : nvec, 256, 0, c->stream>>>(c->partial, kDotChunks, norm ? 1 : nvec, out_dev);
   return cudaGetLastError();
 }
 
