@@ -524,59 +524,72 @@ __global__ void __launch_bounds__(256) k_solve_prep_grouped(const CondItem* __re
 // holds the permuted right-hand side on entry and the solution on exit.
 template <class T, class TS>
 __device__ __forceinline__ void ls_solve_warp(int n, int nblk, const TS* __restrict__ Le, int npad, T* s, int lane) {
+  // Lanes of padding rows (R >= n) load nothing, and in the diagonal block each lane
+  // loads only the 4-column groups that hold entries of its own triangle: those sectors
+  // are never fetched.
   const int nq = npad / 4;
   for (int b = 0; b < nblk; ++b) {  // forward: x_b = L_bb^-1 v_b - M_b x_{<b}
     const int i0 = 32 * b, R = i0 + lane;
+    const bool live = R < n;
     const TS* row = Le + (long long)b * 32 * npad + 4 * lane;
     T a0 = T(0), a1 = T(0);
+    if (live) {
 #pragma unroll 8
-    for (int q = 0; q < i0 / 4; ++q) {
-      Quad<T, TS> m;
-      m.load(row + (long long)q * 128);
-      a0 = fma(m.v[0], s[4 * q], a0);
-      a1 = fma(m.v[1], s[4 * q + 1], a1);
-      a0 = fma(m.v[2], s[4 * q + 2], a0);
-      a1 = fma(m.v[3], s[4 * q + 3], a1);
+      for (int q = 0; q < i0 / 4; ++q) {
+        Quad<T, TS> m;
+        m.load(row + (long long)q * 128);
+        a0 = fma(m.v[0], s[4 * q], a0);
+        a1 = fma(m.v[1], s[4 * q + 1], a1);
+        a0 = fma(m.v[2], s[4 * q + 2], a0);
+        a1 = fma(m.v[3], s[4 * q + 3], a1);
+      }
     }
     T d = s[R];
     const int qd = min(i0 / 4 + 8, nq);  // the last block row may end before 32 columns
 #pragma unroll
     for (int q = i0 / 4; q < qd; ++q) {
-      Quad<T, TS> m;
-      m.load(row + (long long)q * 128);
+      if (live && 4 * q < R) {  // strictly lower part: columns < R
+        Quad<T, TS> m;
+        m.load(row + (long long)q * 128);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (4 * q + j < R) d = fma(m.v[j], s[4 * q + j], d);
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j < R) d = fma(m.v[j], s[4 * q + j], d);
+      }
     }
     __syncwarp();
-    if (R < n) s[R] = d - (a0 + a1);
+    if (live) s[R] = d - (a0 + a1);
     __syncwarp();
   }
   for (int b = nblk - 1; b >= 0; --b) {  // backward: z_b = U_bb^-1 x_b - N_b z_{>b}
     const int i0 = 32 * b, R = i0 + lane;
+    const bool live = R < n;
     const TS* row = Le + (long long)b * 32 * npad + 4 * lane;
     T d = T(0);
     const int qd = min(i0 / 4 + 8, nq);
 #pragma unroll
     for (int q = i0 / 4; q < qd; ++q) {
-      Quad<T, TS> m;
-      m.load(row + (long long)q * 128);
+      if (live && 4 * q + 3 >= R) {  // upper part: columns >= R
+        Quad<T, TS> m;
+        m.load(row + (long long)q * 128);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (4 * q + j >= R) d = fma(m.v[j], s[4 * q + j], d);
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j >= R) d = fma(m.v[j], s[4 * q + j], d);
+      }
     }
     T a0 = T(0), a1 = T(0);
+    if (live) {
 #pragma unroll 8
-    for (int q = i0 / 4 + 8; q < nq; ++q) {
-      Quad<T, TS> m;
-      m.load(row + (long long)q * 128);
-      a0 = fma(m.v[0], s[4 * q], a0);
-      a1 = fma(m.v[1], s[4 * q + 1], a1);
-      a0 = fma(m.v[2], s[4 * q + 2], a0);
-      a1 = fma(m.v[3], s[4 * q + 3], a1);
+      for (int q = i0 / 4 + 8; q < nq; ++q) {
+        Quad<T, TS> m;
+        m.load(row + (long long)q * 128);
+        a0 = fma(m.v[0], s[4 * q], a0);
+        a1 = fma(m.v[1], s[4 * q + 1], a1);
+        a0 = fma(m.v[2], s[4 * q + 2], a0);
+        a1 = fma(m.v[3], s[4 * q + 3], a1);
+      }
     }
     __syncwarp();
-    if (R < n) s[R] = d - (a0 + a1);
+    if (live) s[R] = d - (a0 + a1);
     __syncwarp();
   }
 }
