@@ -80,8 +80,7 @@ cudaError_t run_all(sc_batch* b, cudaStream_t st) {
     const Geo& G = c->G;
     const cudaStream_t own = c->stream;
     c->stream = st;  // the per-system conversions go to the same stream as the rest
-    if (e == cudaSuccess) e = sc::pack_own(c);
-    if (e == cudaSuccess) e = sc::to_float(c, c->Aown, c->Aown32, (size_t)G.K * own_stride(G));
+    if (e == cudaSuccess) e = sc::pack_own(c);  // also writes the FP32 own blocks
     if (e == cudaSuccess) e = sc::to_float(c, c->X, c->X32, (size_t)G.K * G.NP * 25);
     c->stream = own;
   }
@@ -287,7 +286,7 @@ sc_status sc_batch_condense(sc_batch* b, int flags) {
   }
   b->ctx[0]->launches += b->grouped_launches;  // the systems count their own conversions
   if (use_graph)
-    for (sc_ctx* c : b->ctx) c->launches += 3;  // replayed conversions of each system
+    for (sc_ctx* c : b->ctx) c->launches += 2;  // replayed packing and conversion of each system
   for (sc_ctx* c : b->ctx) {
     c->packed = true;
     c->condensed = true;

@@ -792,10 +792,9 @@ cudaError_t launch_condense(sc_ctx* c) {
   cudaError_t pe = pack_own(c);
   if (pe != cudaSuccess) return pe;
   c->packed = true;
-  if (c->cfg.precision == SC_PREC_MIXED) {
-    count_launch(c, 2);
-    const size_t na = (size_t)G.K * own_stride(G), nx = (size_t)G.K * G.NP * 25;
-    k_to_float<<<608, 256, 0, c->stream>>>(c->Aown, c->Aown32, na);
+  if (c->cfg.precision == SC_PREC_MIXED) {  // the packing pass wrote the FP32 own blocks
+    count_launch(c);
+    const size_t nx = (size_t)G.K * G.NP * 25;
     k_to_float<<<608, 256, 0, c->stream>>>(c->X, c->X32, nx);
     return condense_t<float>(c, c->Aown32, c->Ainv32, c->Y32, c->See32, c->cfg.tensor_cores != 0);
   }

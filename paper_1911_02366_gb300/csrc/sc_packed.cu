@@ -100,10 +100,12 @@ __device__ __forceinline__ T pick5(const T acc[5], int k) {
 
 // Dense FP64 own blocks -> packed blocks of type T; entries outside the pattern must be
 // zero (status <- SC_PACK_VIOLATION).  One warp per row.
+// With dense32 non-null (mixed arm) the same pass also writes the FP32 copy of the whole
+// dense block (padding included) that the condensation products read.
 template <class T>
 __global__ void __launch_bounds__(256) k_pack(Geo G, const double* __restrict__ Aown, const int* __restrict__ row_off,
                                               const int* __restrict__ pos, T* __restrict__ Apk, long long pstride,
-                                              int* __restrict__ status) {
+                                              int* __restrict__ status, float* __restrict__ dense32) {
   const int e = blockIdx.x, lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   const double* Ae = Aown + (size_t)e * own_stride(G);
   T* Pe = Apk + (size_t)e * pstride;
@@ -113,11 +115,12 @@ __global__ void __launch_bounds__(256) k_pack(Geo G, const double* __restrict__ 
     const int* posr = pos + (size_t)p * G.nn;
     T* prow = Pe + __ldg(row_off + r);
     for (int cidx = lane; cidx < G.lda; cidx += 32) {
+      const double val = Ae[(size_t)r * G.lda + cidx];
+      if (dense32) dense32[(size_t)e * own_stride(G) + (size_t)r * G.lda + cidx] = (float)val;
       int q, l;
       if (cidx < G.ni) { q = cidx / 5; l = cidx - 5 * q; }
       else if (cidx >= G.cb0 && cidx < G.cb0 + G.nb) { const int t = cidx - G.cb0; q = G.nin + t / 5; l = t - 5 * (t / 5); }
       else continue;  // alignment padding
-      const double val = Ae[(size_t)r * G.lda + cidx];
       const int b = __ldg(posr + q);
       if (b >= 0) prow[5 * b + l] = (T)val;
       else if (b == -1 && val != 0.0) bad = true;
@@ -291,16 +294,17 @@ cudaError_t upload_packed_pattern(sc_ctx* c) {
   return e;
 }
 
-// Pack the FP64 own blocks into the operator's precision.
+// Pack the FP64 own blocks into the operator's precision (mixed arm: and write their
+// dense FP32 copy).
 cudaError_t pack_own(sc_ctx* c) {
   const Geo& G = c->G;
   count_launch(c);
   if (c->cfg.precision == SC_PREC_MIXED)
     k_pack<float><<<G.K, 256, 0, c->stream>>>(G, c->Aown, c->d_pk_row_off, c->d_pk_pos, c->Apk32, c->pk_stride,
-                                              c->d_status);
+                                              c->d_status, c->Aown32);
   else
     k_pack<double><<<G.K, 256, 0, c->stream>>>(G, c->Aown, c->d_pk_row_off, c->d_pk_pos, c->Apk, c->pk_stride,
-                                               c->d_status);
+                                               c->d_status, nullptr);
   return cudaGetLastError();
 }
 
