@@ -286,8 +286,8 @@ def run_ours(args, world, rank, local):
 # captures summarised in profiles/, taken on the 8^3-element case and scaled x8 to the
 # 16^3 mesh (traffic grows with the element count); None once a kernel has changed.
 TRAFFIC = {
-    ("mixed", 2): None,  # k_lu_solve changed since the last DRAM capture
-    ("fp64", 2): None,
+    ("mixed", 2): 8 * (509.318144e6 + 3.564288e6),  # k_lu_solve<float>, profiles/mixed_iteration_kernels_tgv_8x8x8_N4.md
+    ("fp64", 2): 8 * (1.002096e9 + 3.80032e6),  # k_lu_solve<double>, profiles/fp64_iteration_kernels_tgv_8x8x8_N4.md
 }
 
 
