@@ -105,7 +105,7 @@ void free_all(sc_ctx* c) {
   if (c->Wbf16) cudaFree(c->Wbf16);
   c->Wbf16 = nullptr;
   c->Sdiag_valid = c->weights_set = c->learned_on = false;
-  int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
+  int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_own_pairs, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
                  &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
@@ -261,6 +261,16 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
     c->perm[m] = inner ? ii++ : bb++;
   }
   for (int m = 0; m < G.nn; ++m) c->iperm[c->perm[m]] = m;
+  // own node pairs (positions pj, pr) whose nodes share at least one GL index, grouped by the
+  // number of differing indices (2, 1, 0) so that a warp of the assembly follows one branch
+  c->own_pairs.clear();
+  for (int nd = 2; nd >= 0; --nd)
+    for (int pj = 0; pj < G.nn; ++pj)
+      for (int pr = 0; pr < G.nn; ++pr) {
+        const int a = c->iperm[pj], b = c->iperm[pr];
+        const int diff = (a % p != b % p) + ((a / p) % p != (b / p) % p) + (a / (p * p) != b / (p * p));
+        if (diff == nd) c->own_pairs.push_back((pj << 16) | pr);
+      }
   // neighbour table
   c->nbr.assign((size_t)G.K * 18, 0);
   auto E = [&](int x, int y, int z) { x = (x % n + n) % n; y = (y % n + n) % n; z = (z % n + n) % n; return x + n * (y + n * z); };
@@ -314,6 +324,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->partial, 152 * (size_t)(m + 2)));
   A(dalloc(&c->d_status, 2));  // [0] first bad element / error code, [1] FP16 range overflow
   A(dalloc(&c->d_nbr, c->nbr.size())); A(dalloc(&c->d_perm, G.nn)); A(dalloc(&c->d_iperm, G.nn));
+  A(dalloc(&c->d_own_pairs, c->own_pairs.size()));
   const int np = G.NP;
   A(dalloc(&c->d_prow, np)); A(dalloc(&c->d_pslot, np)); A(dalloc(&c->d_pcol, np));
   A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pinfo, np));
@@ -342,6 +353,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   SC_CUDA(cudaMemcpy(c->d_nbr, c->nbr.data(), c->nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_perm, c->perm.data(), G.nn * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_iperm, c->iperm.data(), G.nn * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_own_pairs, c->own_pairs.data(), c->own_pairs.size() * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_prow, c->pat.row.data(), np * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_pslot, c->pat.slot.data(), np * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_pcol, c->pat.col.data(), np * sizeof(int), cudaMemcpyHostToDevice));
@@ -883,9 +895,9 @@ sc_status sc_kernel_work(const sc_ctx* c, int kernel_id, double* flops, double* 
       f = K * 2.0 * ni * ni * ni;
       b = K * w * (ni * lda + ni * ldi);
       break;
-    case SCK_ASM_OWN:
+    case SCK_ASM_OWN:  // the 5x5 blocks of the node pairs sharing a GL index
       f = 0.0;
-      b = K * 8.0 * ne * lda;
+      b = K * 8.0 * 25.0 * (double)c->own_pairs.size();
       break;
     case SCK_EXPLICIT_GEMM:  // Y_e = A_ii^-1 A_ib[., E_e], W_e = A_bi[E_e, .] Y_e
       f = K * (2.0 * ni * ni * c->ex_m + 2.0 * (double)c->ex_m * c->ex_m * ni);

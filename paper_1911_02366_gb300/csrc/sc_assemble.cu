@@ -330,23 +330,20 @@ SC_HD void own_entry(const Geo& G, const double* NJ, const double* RJ, const int
   }
 }
 
+// Pairs sharing no GL index are structurally zero: they are not in the pair list and keep the
+// zeros written when the mesh was set.
 __global__ void __launch_bounds__(256, 3) k_asm_own(Geo G, const double* __restrict__ NJ,
                                                  const double* __restrict__ RJ,
                                                  const int* __restrict__ nbr, const int* __restrict__ iperm,
+                                                 const int* __restrict__ pairs, int npairs,
                                                  double* __restrict__ Aown) {
   const int e = blockIdx.x;
-  const int nn = G.nn, lda = G.lda;
-  for (int t = threadIdx.x; t < nn * nn; t += blockDim.x) {
-    const int pj = t / nn, pr = t % nn;
-    const int j = iperm[pj], r = iperm[pr];
-    int cj[3], cr[3];
-    node_coords(j, G.p, cj);
-    node_coords(r, G.p, cr);
-    // node pairs sharing no GL index are structurally zero and keep the zeros written
-    // when the mesh was set
-    if (cj[0] != cr[0] && cj[1] != cr[1] && cj[2] != cr[2]) continue;
+  const int lda = G.lda;
+  for (int t = threadIdx.x; t < npairs; t += blockDim.x) {
+    const int code = pairs[t];
+    const int pj = code >> 16, pr = code & 0xffff;
     double acc[25];
-    own_entry(G, NJ, RJ, nbr, e, j, r, acc);
+    own_entry(G, NJ, RJ, nbr, e, iperm[pj], iperm[pr], acc);
     double* out = Aown + (size_t)e * own_stride(G) + (size_t)(5 * pj) * lda + own_col(G, pr, 0);
     for (int k = 0; k < 5; ++k)
       for (int l = 0; l < 5; ++l) out[(size_t)k * lda + l] = acc[k * 5 + l];
@@ -471,7 +468,8 @@ cudaError_t launch_assembly(sc_ctx* c) {
   k_roejac<<<blocks_for(fn, 64), 64, 0, c->stream>>>(G, c->Q, c->d_nbr, c->RJ);
   {
     ProfScope ps(c, SCK_ASM_OWN);
-    k_asm_own<<<G.K, 256, 0, c->stream>>>(G, c->NJ, c->RJ, c->d_nbr, c->d_iperm, c->Aown);
+    k_asm_own<<<G.K, 256, 0, c->stream>>>(G, c->NJ, c->RJ, c->d_nbr, c->d_iperm, c->d_own_pairs,
+                                          (int)c->own_pairs.size(), c->Aown);
   }
   const size_t np = (size_t)G.K * G.NP;
   k_asm_cross<<<blocks_for(np, 128), 128, 0, c->stream>>>(G, c->NJ, c->RJ, c->d_nbr, c->d_prow, c->d_pslot,

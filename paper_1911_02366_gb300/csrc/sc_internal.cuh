@@ -250,12 +250,13 @@ struct sc_ctx {
   double L = 0.0;
   std::vector<double> xi;          // Gauss-Lobatto nodes
   std::vector<int> perm, iperm;    // natural node -> position (interior first), inverse
+  std::vector<int> own_pairs;      // (pj << 16) | pr of the own node pairs sharing a GL index, grouped by kind
   std::vector<int> nbr;            // [K][18] neighbour element per slot
   Pattern pat;
   // device memory
   double *Q = nullptr, *Qh = nullptr, *grad = nullptr, *F = nullptr, *B = nullptr;
   double *NJ = nullptr, *RJ = nullptr, *Aown = nullptr, *X = nullptr;
-  int *d_nbr = nullptr, *d_perm = nullptr, *d_iperm = nullptr;
+  int *d_nbr = nullptr, *d_perm = nullptr, *d_iperm = nullptr, *d_own_pairs = nullptr;
   int *d_prow = nullptr, *d_pslot = nullptr, *d_pcol = nullptr, *d_pptr = nullptr, *d_pinfo = nullptr;
   double *Ainv = nullptr, *Ytmp = nullptr, *See = nullptr;
   int *piv = nullptr, *rowperm = nullptr, *d_status = nullptr;
