@@ -97,6 +97,117 @@ __device__ void gj_inv_body(int n, const T* __restrict__ Ae, int lda, T* __restr
   __syncthreads();
 }
 
+// A_ii^-1 of one FP32 block of order n <= 136 by one CTA of 256 threads with the block held
+// in registers: thread (warp w, lane l) owns rows w + 8 r (r < 17) and columns l + 32 c
+// (c < 5).  Partial pivoting is implicit: step k takes as pivot row p_k the unused row with
+// the largest |M[., k]| and eliminates in place without moving rows, which is Gauss-Jordan
+// on B = P A (row k of B = row p_k of A) with B^-1 left in physical row p_k.  Since
+// A^-1 = B^-1 P, the result is A^-1[i][p_k] = M[p_i][k], applied while staging the output.
+constexpr int GJR_R = 17, GJR_C = 5, GJR_N = 8 * GJR_R, GJR_LDS = GJR_N + 1;
+
+__device__ void gj_inv_reg_body(int n, const float* __restrict__ Ae, int lda, float* __restrict__ Oe, int ldo,
+                                int* __restrict__ status, int e) {
+  extern __shared__ unsigned char smem_raw[];
+  float* S = reinterpret_cast<float*>(smem_raw);  // [GJR_N][GJR_LDS] output staging
+  __shared__ float colk[2][GJR_N];                // column k of the current matrix
+  __shared__ float rowk[32 * GJR_C];              // pivot row before scaling
+  __shared__ int pk[GJR_N], invp[GJR_N];          // step -> pivot row, pivot row -> step
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float M[GJR_R][GJR_C];
+#pragma unroll
+  for (int r = 0; r < GJR_R; ++r)
+#pragma unroll
+    for (int c = 0; c < GJR_C; ++c) {
+      const int i = ty + 8 * r, j = tx + 32 * c;
+      M[r][c] = (i < n && j < n) ? Ae[(long long)i * lda + j] : 0.f;
+    }
+  if (tx == 0) {
+#pragma unroll
+    for (int r = 0; r < GJR_R; ++r) colk[0][ty + 8 * r] = M[r][0];
+  }
+  unsigned used = 0;  // bit t: row tx + 32 t is a pivot row already, or padding
+#pragma unroll
+  for (int t = 0; t < GJR_C; ++t)
+    if (tx + 32 * t >= n) used |= 1u << t;
+  bool bad = false;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const float* ck = colk[k & 1];
+    // pivot search, repeated by every warp on the same data: key = (|v| bits + 1, -row),
+    // so NaN ranks above every number and ties go to the smallest row
+    unsigned long long key = 0ull;
+#pragma unroll
+    for (int t = 0; t < GJR_C; ++t) {
+      const int i = tx + 32 * t;
+      if (!((used >> t) & 1u)) {
+        const unsigned long long kv = ((unsigned long long)(__float_as_uint(fabsf(ck[i])) + 1u) << 32) |
+                                      (unsigned)(0x7fffffff - i);
+        key = kv > key ? kv : key;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
+      key = o > key ? o : key;
+    }
+    const int p = 0x7fffffff - (int)(unsigned)(key & 0xffffffffull);
+    const float piv = ck[p];
+    const bool ok = fabsf(piv) > 0.f;
+    bad |= !ok;
+    const float pinv = ok ? 1.f / piv : 0.f;
+    if (tx == (p & 31)) used |= 1u << (p >> 5);
+    if (threadIdx.x == 0) { pk[k] = p; invp[p] = k; }
+    if (ty == (p & 7)) {
+      const int pr = p >> 3;
+#pragma unroll
+      for (int r = 0; r < GJR_R; ++r)
+        if (r == pr) {
+#pragma unroll
+          for (int c = 0; c < GJR_C; ++c) rowk[tx + 32 * c] = M[r][c];
+        }
+    }
+    __syncthreads();
+    float rk[GJR_C];
+#pragma unroll
+    for (int c = 0; c < GJR_C; ++c) rk[c] = rowk[tx + 32 * c];
+    const int k1 = k + 1, nx = k1 & 31, nc = k1 >> 5;
+    float* cn = colk[k1 & 1];
+#pragma unroll
+    for (int r = 0; r < GJR_R; ++r) {
+      const int i = ty + 8 * r;
+      const float f = ck[i] * pinv;
+      const bool isp = i == p;
+#pragma unroll
+      for (int c = 0; c < GJR_C; ++c) {
+        const bool isk = tx + 32 * c == k;
+        const float m = M[r][c];
+        const float v = isp ? (isk ? pinv : m * pinv) : (isk ? -f : fmaf(-f, rk[c], m));
+        M[r][c] = v;
+        if (c == nc && tx == nx) cn[i] = v;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < GJR_R; ++r)
+#pragma unroll
+    for (int c = 0; c < GJR_C; ++c) {
+      const int i = ty + 8 * r, j = tx + 32 * c;
+      if (i < n && j < n) S[invp[i] * GJR_LDS + pk[j]] = M[r][c];
+    }
+  __syncthreads();
+  for (int i = ty; i < n; i += 8)
+    for (int j = tx; j < n; j += 32) Oe[(long long)i * ldo + j] = S[i * GJR_LDS + j];
+  if (threadIdx.x == 0 && bad) atomicCAS(status, -1, e);
+}
+
+__global__ void __launch_bounds__(256, 2) k_gj_inv_reg(int n, const float* __restrict__ A, long long strideA,
+                                                       int lda, float* __restrict__ Ainv, long long strideO,
+                                                       int ldo, int* __restrict__ status) {
+  const int e = blockIdx.x;
+  gj_inv_reg_body(n, A + (long long)e * strideA, lda, Ainv + (long long)e * strideO, ldo, status, e);
+}
+
 template <class T>
 __global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int lda,
                          T* __restrict__ Ainv, long long strideO, int ldo, int* __restrict__ status) {
@@ -108,6 +219,11 @@ __global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int 
 __global__ void k_gj_inv_grouped(const CondItem* __restrict__ items) {
   const CondItem it = items[blockIdx.x];
   gj_inv_body<float>(it.ni, it.Aown, it.lda, it.Ainv, it.ldi, it.status, it.e);
+}
+
+__global__ void __launch_bounds__(256, 2) k_gj_inv_reg_grouped(const CondItem* __restrict__ items) {
+  const CondItem it = items[blockIdx.x];
+  gj_inv_reg_body(it.ni, it.Aown, it.lda, it.Ainv, it.ldi, it.status, it.e);
 }
 
 __global__ void k_copy_bb_grouped(const CondItem* __restrict__ items) {
@@ -701,11 +817,24 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
   const long long sA = (long long)own_stride(G);
   cudaError_t err;
   if (ni > 0) {
-    const size_t smem = (size_t)ni * (ni + 1) * sizeof(T) + ni * sizeof(T) + ni * sizeof(int);
-    err = cudaFuncSetAttribute(k_gj_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    ProfScope ps(c, SCK_GJ_INV);
-    k_gj_inv<T><<<K, 256, smem, c->stream>>>(ni, Aown, sA, lda, Ainv, (long long)ni * ldi, ldi, c->d_status);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (ni <= GJR_N) {
+        const size_t smem = (size_t)GJR_N * GJR_LDS * sizeof(float);
+        err = cudaFuncSetAttribute(k_gj_inv_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        ProfScope ps(c, SCK_GJ_INV);
+        k_gj_inv_reg<<<K, 256, smem, c->stream>>>(ni, Aown, sA, lda, Ainv, (long long)ni * ldi, ldi, c->d_status);
+        done = true;
+      }
+    }
+    if (!done) {
+      const size_t smem = (size_t)ni * (ni + 1) * sizeof(T) + ni * sizeof(T) + ni * sizeof(int);
+      err = cudaFuncSetAttribute(k_gj_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      ProfScope ps(c, SCK_GJ_INV);
+      k_gj_inv<T><<<K, 256, smem, c->stream>>>(ni, Aown, sA, lda, Ainv, (long long)ni * ldi, ldi, c->d_status);
+    }
   }
   if (ni > 0) {
     count_launch(c);
@@ -847,6 +976,13 @@ size_t solve_layout_elems(const Geo& G) { return (size_t)G.K * ls_stride(G); }
 
 // ---- grouped launches of the batched condensation (one CTA per CondItem) --------------
 cudaError_t grouped_gj(cudaStream_t st, const CondItem* items, int n, int max_ni) {
+  if (max_ni <= GJR_N) {
+    const size_t smem = (size_t)GJR_N * GJR_LDS * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_gj_inv_reg_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gj_inv_reg_grouped<<<n, 256, smem, st>>>(items);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)max_ni * (max_ni + 1) * sizeof(float) + max_ni * sizeof(float) + max_ni * sizeof(int);
   cudaError_t e = cudaFuncSetAttribute(k_gj_inv_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
