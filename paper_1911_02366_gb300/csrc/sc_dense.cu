@@ -442,6 +442,156 @@ __global__ void __launch_bounds__(256) k_lu_panel(int n, int k0, T* __restrict__
   if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
 }
 
+// The same panel step of an FP32 block with n - k0 <= 496 rows, held in registers: lane l
+// is panel column l, warp w holds panel rows w + 8 r (r < 62).  Pivoting is implicit (the
+// pivot rows p_c are marked, nothing moves during the 32 eliminations); the pivot order is
+// then turned into the interchange sequence that row-by-row partial pivoting records
+// (piv[k0 + c] = k0 + position swapped with c), the panel is written in its final row
+// order, and one thread per column outside the panel applies the interchanges to its
+// column in registers and, right of the panel, forms U12 = L11^-1 A12 there.
+constexpr int LPR_R = 62, LPR_ROWS = 8 * LPR_R;
+
+__device__ void lu_panel_reg_body(int n, int k0, float* __restrict__ Mx, int lda, int* __restrict__ piv,
+                                  int* __restrict__ status, int e) {
+  __shared__ float colk[2][LPR_ROWS];  // column c of the current panel
+  __shared__ float rowk[PW];           // pivot row
+  __shared__ float L11[PW][PW + 1];    // unit lower triangle of the factored panel, final order
+  __shared__ int pk[PW], ipv[PW], xl[PW];
+  __shared__ int at[LPR_ROWS], where_[LPR_ROWS];  // position -> physical row, inverse
+  __shared__ int s_nx;
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int bw = min(PW, n - k0), rows = n - k0;
+  float M[LPR_R];
+#pragma unroll
+  for (int r = 0; r < LPR_R; ++r) {
+    const int i = w + 8 * r;
+    M[r] = (i < rows && l < bw) ? Mx[(long long)(k0 + i) * lda + k0 + l] : 0.f;
+  }
+  if (l == 0) {
+#pragma unroll
+    for (int r = 0; r < LPR_R; ++r) colk[0][w + 8 * r] = M[r];
+  }
+  for (int i = threadIdx.x; i < LPR_ROWS; i += blockDim.x) { at[i] = i; where_[i] = i; }
+  if (threadIdx.x == 0) s_nx = 0;
+  unsigned sel = 0;  // bit t: search row l + 32 t is a pivot row already, or past the panel
+#pragma unroll
+  for (int t = 0; t < 16; ++t)
+    if (l + 32 * t >= rows) sel |= 1u << t;
+  unsigned long long done = 0ull;  // bit r: row w + 8 r is a pivot row already, or past the panel
+#pragma unroll
+  for (int r = 0; r < LPR_R; ++r)
+    if (w + 8 * r >= rows) done |= 1ull << r;
+  bool bad = false;
+  __syncthreads();
+  for (int c = 0; c < bw; ++c) {
+    const float* ck = colk[c & 1];
+    // pivot search, repeated by every warp: key = (|v| bits + 1, -row), NaN above numbers,
+    // ties to the smallest row
+    unsigned long long key = 0ull;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int i = l + 32 * t;
+      if (!((sel >> t) & 1u)) {
+        const unsigned long long kv = ((unsigned long long)(__float_as_uint(fabsf(ck[i])) + 1u) << 32) |
+                                      (unsigned)(0x7fffffff - i);
+        key = kv > key ? kv : key;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
+      key = o > key ? o : key;
+    }
+    const int p = 0x7fffffff - (int)(unsigned)(key & 0xffffffffull);
+    const float d = ck[p];
+    bad |= !(fabsf(d) > 0.f);
+    const float dinv = (d == 0.f) ? 0.f : 1.f / d;
+    if (l == (p & 31)) sel |= 1u << (p >> 5);
+    if (w == (p & 7)) {
+      const int pr = p >> 3;
+      done |= 1ull << pr;
+#pragma unroll
+      for (int r = 0; r < LPR_R; ++r)
+        if (r == pr) rowk[l] = M[r];
+    }
+    if (threadIdx.x == 0) pk[c] = p;
+    __syncthreads();
+    const float rk = rowk[l];
+    const int c1 = c + 1;
+    float* cn = colk[c1 & 1];
+#pragma unroll
+    for (int r = 0; r < LPR_R; ++r) {
+      const int i = w + 8 * r;
+      if (!((done >> r) & 1ull)) {
+        const float m = ck[i] * dinv;
+        const float v = M[r];
+        M[r] = (l == c) ? m : ((l > c) ? fmaf(-m, rk, v) : v);
+      }
+      if (l == c1) cn[i] = M[r];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < bw; ++c) {
+      const int p = pk[c], q = where_[p], rc = at[c];
+      ipv[c] = q;
+      at[c] = p; at[q] = rc;
+      where_[p] = c; where_[rc] = q;
+    }
+  }
+  __syncthreads();
+  // positions below the panel's first bw that received another row (at most bw of them)
+  for (int q = bw + threadIdx.x; q < rows; q += blockDim.x)
+    if (at[q] != q) xl[atomicAdd(&s_nx, 1)] = q;
+#pragma unroll
+  for (int r = 0; r < LPR_R; ++r) {
+    const int i = w + 8 * r;
+    if (i < rows && l < bw) {
+      const int pos = where_[i];
+      Mx[(long long)(k0 + pos) * lda + k0 + l] = M[r];
+      if (pos < bw) L11[pos][l] = M[r];
+    }
+  }
+  if (threadIdx.x < bw) piv[k0 + threadIdx.x] = k0 + ipv[threadIdx.x];
+  __syncthreads();
+  const int nx = s_nx;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    if (j >= k0 && j < k0 + bw) continue;
+    float v1[PW], v2[PW];
+#pragma unroll
+    for (int c = 0; c < PW; ++c) v1[c] = c < bw ? Mx[(long long)(k0 + at[c]) * lda + j] : 0.f;
+#pragma unroll
+    for (int q = 0; q < PW; ++q) v2[q] = q < nx ? Mx[(long long)(k0 + at[xl[q]]) * lda + j] : 0.f;
+    // every load of the column precedes its stores (the two row sets overlap)
+#pragma unroll
+    for (int q = 0; q < PW; ++q)
+      if (q < nx) Mx[(long long)(k0 + xl[q]) * lda + j] = v2[q];
+    if (j >= k0 + bw) {
+#pragma unroll
+      for (int c = 0; c < PW; ++c)
+#pragma unroll
+        for (int i = c + 1; i < PW; ++i) v1[i] = fmaf(-L11[i][c], v1[c], v1[i]);
+    }
+#pragma unroll
+    for (int c = 0; c < PW; ++c)
+      if (c < bw) Mx[(long long)(k0 + c) * lda + j] = v1[c];
+  }
+  if (threadIdx.x == 0 && bad) atomicCAS(status, -1, e);
+}
+
+__global__ void __launch_bounds__(256, 2) k_lu_panel_reg(int n, int k0, float* __restrict__ A, long long stride,
+                                                         int lda, int* __restrict__ piv_all,
+                                                         int* __restrict__ status) {
+  const int e = blockIdx.x;
+  lu_panel_reg_body(n, k0, A + (long long)e * stride, lda, piv_all + (long long)e * n, status, e);
+}
+
+__global__ void __launch_bounds__(256, 2) k_lu_panel_reg_grouped(const CondItem* __restrict__ items, int k0) {
+  const CondItem it = items[blockIdx.x];
+  if (it.nb <= k0) return;
+  lu_panel_reg_body(it.nb, k0, it.See, it.lds, it.piv, it.status, it.e);
+}
+
 // One panel step of every batched item whose S_ee extends beyond column k0.
 __global__ void __launch_bounds__(256) k_lu_panel_grouped(const CondItem* __restrict__ items, int k0) {
   extern __shared__ unsigned char smem_raw[];
@@ -788,13 +938,17 @@ cudaError_t lu_blocked_tf32(sc_ctx* c, float* See) {
   const int nb = G.nb, K = G.K, lds = G.lds;
   const long long sS = (long long)nb * lds;
   const size_t smem = (size_t)nb * (PW + 1) * sizeof(float);
+  const bool reg = nb <= LPR_ROWS;
   cudaError_t err = cudaFuncSetAttribute(k_lu_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   ProfScope ps(c, SCK_LU);  // one measured span over all panels
   for (int k0 = 0; k0 < nb; k0 += PW) {
     const int bw = min(PW, nb - k0), rest = nb - k0 - bw;
     if (k0 > 0) count_launch(c);
-    k_lu_panel<float><<<K, 256, smem, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
+    if (reg)
+      k_lu_panel_reg<<<K, 256, 0, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
+    else
+      k_lu_panel<float><<<K, 256, smem, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
     if (rest > 0) {
       count_launch(c);
       err = gemm_tf32(c->stream, rest, rest, bw, -1.0f, See + (size_t)(k0 + bw) * lds + k0, sS, lds, false,
@@ -996,6 +1150,10 @@ cudaError_t grouped_copy_bb(cudaStream_t st, const CondItem* items, int n) {
 }
 
 cudaError_t grouped_lu_panel(cudaStream_t st, const CondItem* items, int n, int k0, int max_nb) {
+  if (max_nb <= LPR_ROWS) {
+    k_lu_panel_reg_grouped<<<n, 256, 0, st>>>(items, k0);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)max_nb * (PW + 1) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_lu_panel_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
