@@ -107,8 +107,9 @@ void sc_destroy(sc_ctx* ctx);
 const char* sc_last_error(const sc_ctx* ctx);
 
 /* Mesh and order (App. C): periodic n x n x n Cartesian hexahedra on [0, L]^3,
-   polynomial order N in every element (2 <= N <= 4 and 1 <= n <= 32 in this build).  Allocates
-   all per-mesh device storage; invalidates any previous state and Jacobian. */
+   polynomial order N in every element (2 <= N <= 6 and 1 <= n <= 32; the FP64 arm takes
+   N <= 5 and the explicit Schur operator N <= 4, else SC_ERR_ARG).  Allocates all per-mesh
+   device storage (SC_ERR_OOM if it does not fit); invalidates any previous state and Jacobian. */
 sc_status sc_set_mesh(sc_ctx* ctx, int n, double L, int N);
 
 /* Physical coordinates [K][(N+1)^3][3] of the Gauss-Lobatto nodes (host array). */

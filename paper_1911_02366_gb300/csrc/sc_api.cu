@@ -98,6 +98,8 @@ void free_all(sc_ctx* c) {
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
+  if (c->gj_scale) cudaFree(c->gj_scale);
+  c->gj_scale = nullptr;
   c->packed = false;
   if (c->Sls16) cudaFree(c->Sls16);
   c->Sls16 = nullptr;
@@ -226,7 +228,12 @@ const char* sc_last_error(const sc_ctx* c) { return c ? c->err.c_str() : "null c
 
 sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   if (!c) return SC_ERR_ARG;
-  if (n < 1 || n > 32 || N < 2 || N > 4 || !(L > 0)) return fail(c, SC_ERR_ARG, "mesh: need n in [1,32], N in [2,4], L > 0");
+  if (n < 1 || n > 32 || N < 2 || N > 6 || !(L > 0)) return fail(c, SC_ERR_ARG, "mesh: need n in [1,32], N in [2,6], L > 0");
+  // the FP64 arm factors S_ee in one CTA's shared memory: n_b x 33 doubles, 200 KB at N = 5
+  if (N > 5 && c->cfg.precision != SC_PREC_MIXED)
+    return fail(c, SC_ERR_ARG, "mesh: the FP64 arm takes N <= 5 (N = 6 runs on the mixed arm)");
+  if (c->cfg.explicit_schur && N > 4)
+    return fail(c, SC_ERR_ARG, "explicit Schur blocks: N <= 4 (W_e holds (n_b + 30 (N+1)^2)^2 values per element)");
   if (c->cfg.precond == SC_PC_LEARNED && c->cfg.precision != SC_PREC_MIXED)
     return fail(c, SC_ERR_ARG, "the learned correction runs on the mixed arm's FP32 blocks");
   if (c->cfg.explicit_schur && (c->cfg.precision != SC_PREC_MIXED || n < 3))
@@ -325,6 +332,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->d_status, 2));  // [0] first bad element / error code, [1] FP16 range overflow
   A(dalloc(&c->d_nbr, c->nbr.size())); A(dalloc(&c->d_perm, G.nn)); A(dalloc(&c->d_iperm, G.nn));
   A(dalloc(&c->d_own_pairs, c->own_pairs.size()));
+  A(dalloc(&c->gj_scale, (size_t)G.K * G.ni));
   const int np = G.NP;
   A(dalloc(&c->d_prow, np)); A(dalloc(&c->d_pslot, np)); A(dalloc(&c->d_pcol, np));
   A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pinfo, np));

@@ -103,7 +103,12 @@ __device__ void gj_inv_body(int n, const T* __restrict__ Ae, int lda, T* __restr
 // the largest |M[., k]| and eliminates in place without moving rows, which is Gauss-Jordan
 // on B = P A (row k of B = row p_k of A) with B^-1 left in physical row p_k.  Since
 // A^-1 = B^-1 P, the result is A^-1[i][p_k] = M[p_i][k], applied while staging the output.
+// The rows are equilibrated first (D A with d_i = 1 / max_j |a_ij|, then A^-1 = (D A)^-1 D):
+// the Jacobian's rows span three orders of magnitude, and unscaled FP32 Gauss-Jordan loses
+// about two digits against an LU-based inverse on these blocks.
 constexpr int GJR_R = 17, GJR_C = 5, GJR_N = 8 * GJR_R, GJR_LDS = GJR_N + 1;
+// dynamic shared memory the one-CTA Gauss-Jordan may take (227 KB less its static part)
+constexpr size_t kGjSmemMax = 227 * 1024 - 64;
 
 __device__ void gj_inv_reg_body(int n, const float* __restrict__ Ae, int lda, float* __restrict__ Oe, int ldo,
                                 int* __restrict__ status, int e) {
@@ -113,14 +118,24 @@ __device__ void gj_inv_reg_body(int n, const float* __restrict__ Ae, int lda, fl
   __shared__ float rowk[32 * GJR_C];              // pivot row before scaling
   __shared__ int pk[GJR_N], invp[GJR_N];          // step -> pivot row, pivot row -> step
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  __shared__ float dsc[GJR_N];                    // row equilibration: d_i = 1 / max_j |a_ij|
   float M[GJR_R][GJR_C];
 #pragma unroll
-  for (int r = 0; r < GJR_R; ++r)
+  for (int r = 0; r < GJR_R; ++r) {
+    float mx = 0.f;
 #pragma unroll
     for (int c = 0; c < GJR_C; ++c) {
       const int i = ty + 8 * r, j = tx + 32 * c;
       M[r][c] = (i < n && j < n) ? Ae[(long long)i * lda + j] : 0.f;
+      mx = fmaxf(mx, fabsf(M[r][c]));
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    const float d = mx > 0.f ? 1.f / mx : 1.f;
+#pragma unroll
+    for (int c = 0; c < GJR_C; ++c) M[r][c] *= d;
+    if (tx == 0) dsc[ty + 8 * r] = d;
+  }
   if (tx == 0) {
 #pragma unroll
     for (int r = 0; r < GJR_R; ++r) colk[0][ty + 8 * r] = M[r][0];
@@ -197,7 +212,7 @@ __device__ void gj_inv_reg_body(int n, const float* __restrict__ Ae, int lda, fl
     }
   __syncthreads();
   for (int i = ty; i < n; i += 8)
-    for (int j = tx; j < n; j += 32) Oe[(long long)i * ldo + j] = S[i * GJR_LDS + j];
+    for (int j = tx; j < n; j += 32) Oe[(long long)i * ldo + j] = S[i * GJR_LDS + j] * dsc[j];
   if (threadIdx.x == 0 && bad) atomicCAS(status, -1, e);
 }
 
@@ -592,6 +607,247 @@ __global__ void __launch_bounds__(256, 2) k_lu_panel_reg_grouped(const CondItem*
   lu_panel_reg_body(it.nb, k0, it.See, it.lds, it.piv, it.status, it.e);
 }
 
+// ---- blocked Gauss-Jordan inverse (blocks too large for one CTA's registers) ----------
+// A is inverted in place, 32 pivot columns K = k0 .. k0+31 at a time:
+//   k_gjb_panel   Gauss-Jordan on the n x 32 panel (pivots among rows >= k0, implicit
+//                 during the eliminations, then applied as row interchanges to every
+//                 column): the pivot rows P = k0 .. k0+31 of the panel hold G^-1
+//                 (G = A[P, K]), the other rows -A[R, K] G^-1;
+//   k_gjb_update  A[P, J] <- G^-1 A[P, J] and A[R, J] <- A[R, J] - A[R, K] G^-1 A[P, J] for
+//                 the columns J outside the panel, both as A[., J] (+)= panel x A_old[P, J];
+//   k_gjb_unpermute  the row interchanges undone as column interchanges, last first.
+// The panel kernel holds rows w + 16 r (r < 40) of lane l's column: n <= 640.
+constexpr int GJB_R = 40, GJB_ROWS = 16 * GJB_R, GJB_CH = 64;
+
+// Warp argmax of |v| over (value, row) with NaN above every number and ties to the
+// smallest row; every lane ends with the same pair.
+template <class T>
+__device__ __forceinline__ bool gjb_better(T a, int ia, T b, int ib) {
+  const bool na = a != a, nb_ = b != b;
+  if (na || nb_) return na && (!nb_ || ia < ib);
+  return a > b || (a == b && ia < ib);
+}
+
+template <class T>
+__global__ void __launch_bounds__(512, 1) k_gjb_panel(int n, int k0, T* __restrict__ A, long long stride, int lda,
+                                                      int* __restrict__ piv_all, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* stage = reinterpret_cast<T*>(smem_raw);  // [2 PW][GJB_CH + 1]: moved rows of one column chunk
+  __shared__ T colk[2][GJB_ROWS];
+  __shared__ T rowk[PW];
+  __shared__ int pk[PW], ipv[PW], xl[PW];
+  __shared__ int at[GJB_ROWS], where_[GJB_ROWS];  // positions k0 + q (q relative) <-> rows
+  __shared__ int s_nx;
+  const int e = blockIdx.x;
+  T* Mx = A + (long long)e * stride;
+  int* piv = piv_all + (long long)e * n;
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int bw = min(PW, n - k0), rows = n - k0;
+  T M[GJB_R];
+#pragma unroll
+  for (int r = 0; r < GJB_R; ++r) {
+    const int i = w + 16 * r;
+    M[r] = (i < n && l < bw) ? Mx[(long long)i * lda + k0 + l] : T(0);
+  }
+  if (l == 0) {
+#pragma unroll
+    for (int r = 0; r < GJB_R; ++r) colk[0][w + 16 * r] = M[r];
+  }
+  for (int i = threadIdx.x; i < GJB_ROWS; i += blockDim.x) { at[i] = i; where_[i] = i; }
+  if (threadIdx.x == 0) s_nx = 0;
+  unsigned sel = 0;  // bit t: row l + 32 t is not a pivot candidate (above k0, chosen, or past n)
+#pragma unroll
+  for (int t = 0; t < GJB_ROWS / 32; ++t) {
+    const int i = l + 32 * t;
+    if (i < k0 || i >= n) sel |= 1u << t;
+  }
+  bool bad = false;
+  __syncthreads();
+  for (int c = 0; c < bw; ++c) {
+    const T* ck = colk[c & 1];
+    T best = T(-1);
+    int bi = 0x7fffffff;
+#pragma unroll
+    for (int t = 0; t < GJB_ROWS / 32; ++t) {
+      const int i = l + 32 * t;
+      if (!((sel >> t) & 1u)) {
+        const T a = tabs(ck[i]);
+        if (gjb_better(a, i, best, bi)) { best = a; bi = i; }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (gjb_better(ob, oi, best, bi)) { best = ob; bi = oi; }
+    }
+    const int p = bi;
+    const T d = ck[p];
+    const bool ok = tabs(d) > T(0);
+    bad |= !ok;
+    const T pinv = ok ? T(1) / d : T(0);
+    if (l == (p & 31)) sel |= 1u << (p >> 5);
+    if (w == (p & 15)) {
+      const int pr = p >> 4;
+#pragma unroll
+      for (int r = 0; r < GJB_R; ++r)
+        if (r == pr) rowk[l] = M[r];
+    }
+    if (threadIdx.x == 0) pk[c] = p;
+    __syncthreads();
+    const T rk = rowk[l];
+    const int c1 = c + 1;
+    T* cn = colk[c1 & 1];
+#pragma unroll
+    for (int r = 0; r < GJB_R; ++r) {
+      const int i = w + 16 * r;
+      const T f = ck[i] * pinv;
+      const T v = M[r];
+      M[r] = (i == p) ? ((l == c) ? pinv : v * pinv) : ((l == c) ? -f : fma(-f, rk, v));
+      if (l == c1) cn[i] = M[r];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < bw; ++c) {
+      const int p = pk[c] - k0, q = where_[p], rc = at[c];
+      ipv[c] = q;
+      at[c] = p; at[q] = rc;
+      where_[p] = c; where_[rc] = q;
+    }
+  }
+  __syncthreads();
+  for (int q = bw + threadIdx.x; q < rows; q += blockDim.x)
+    if (at[q] != q) xl[atomicAdd(&s_nx, 1)] = q;
+#pragma unroll
+  for (int r = 0; r < GJB_R; ++r) {
+    const int i = w + 16 * r;
+    if (i < n && l < bw) {
+      const int pos = i < k0 ? i : k0 + where_[i - k0];
+      Mx[(long long)pos * lda + k0 + l] = M[r];
+    }
+  }
+  if (threadIdx.x < bw) piv[k0 + threadIdx.x] = k0 + ipv[threadIdx.x];
+  __syncthreads();
+  // the interchanges on the columns outside the panel, one chunk of columns at a time
+  const int nm = bw + s_nx;  // moved positions: 0 .. bw-1, then xl[]
+  for (int j0 = 0; j0 < n; j0 += GJB_CH) {
+    for (int t = threadIdx.x; t < nm * GJB_CH; t += blockDim.x) {
+      const int m = t / GJB_CH, j = j0 + t % GJB_CH;
+      if (j < n && (j < k0 || j >= k0 + bw)) {
+        const int src = k0 + (m < bw ? at[m] : at[xl[m - bw]]);
+        stage[m * (GJB_CH + 1) + t % GJB_CH] = Mx[(long long)src * lda + j];
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nm * GJB_CH; t += blockDim.x) {
+      const int m = t / GJB_CH, j = j0 + t % GJB_CH;
+      if (j < n && (j < k0 || j >= k0 + bw)) {
+        const int dst = k0 + (m < bw ? m : xl[m - bw]);
+        Mx[(long long)dst * lda + j] = stage[m * (GJB_CH + 1) + t % GJB_CH];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) atomicCAS(status, -1, e);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gjb_update(int n, int k0, T* __restrict__ A, long long stride, int lda) {
+  __shared__ T Ts[PW][GJB_CH];      // A_old[P, J] of this column block
+  __shared__ T As[GJB_CH][PW + 1];  // panel columns of a 64-row tile
+  const int e = blockIdx.y, j0 = blockIdx.x * GJB_CH;
+  T* Mx = A + (long long)e * stride;
+  const int bw = min(PW, n - k0);
+  for (int t = threadIdx.x; t < PW * GJB_CH; t += blockDim.x) {
+    const int k = t / GJB_CH, jj = t % GJB_CH, j = j0 + jj;
+    Ts[k][jj] = (k < bw && j < n && (j < k0 || j >= k0 + bw)) ? Mx[(long long)(k0 + k) * lda + j] : T(0);
+  }
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;  // rows 4 tr + a, columns tc + 16 b
+  for (int i0 = 0; i0 < n; i0 += GJB_CH) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < GJB_CH * PW; t += blockDim.x) {
+      const int ii = t / PW, k = t % PW;
+      As[ii][k] = (i0 + ii < n && k < bw) ? Mx[(long long)(i0 + ii) * lda + k0 + k] : T(0);
+    }
+    __syncthreads();
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+#pragma unroll 8
+    for (int k = 0; k < PW; ++k) {
+      T x[4], y[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) x[a] = As[4 * tr + a][k];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) y[b] = Ts[k][tc + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = i0 + 4 * tr + a;
+      if (i >= n) continue;
+      const bool pivot_row = i >= k0 && i < k0 + bw;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int j = j0 + tc + 16 * b;
+        if (j >= n || (j >= k0 && j < k0 + bw)) continue;
+        T* dst = Mx + (long long)i * lda + j;
+        *dst = pivot_row ? acc[a][b] : *dst + acc[a][b];
+      }
+    }
+  }
+}
+
+// Row equilibration before the blocked Gauss-Jordan: a row <- d_i row, d_i = 1 / max |a_i.|,
+// one warp per row; the unpermute pass multiplies column j of the inverse by d_j.
+template <class T>
+__global__ void k_row_equilibrate(int n, T* __restrict__ A, long long stride, int lda, T* __restrict__ dsc) {
+  const int e = blockIdx.y;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), l = threadIdx.x & 31;
+  if (i >= n) return;
+  T* row = A + (long long)e * stride + (long long)i * lda;
+  T mx = T(0);
+  for (int j = l; j < n; j += 32) mx = fmax(mx, tabs(row[j]));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const T d = mx > T(0) ? T(1) / mx : T(1);
+  for (int j = l; j < n; j += 32) row[j] *= d;
+  if (l == 0) dsc[(long long)e * n + i] = d;
+}
+
+template <class T>
+__global__ void __launch_bounds__(512) k_gjb_unpermute(int n, T* __restrict__ A, long long stride, int lda,
+                                                       const int* __restrict__ piv_all, const T* __restrict__ dsc_all) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* rowbuf = reinterpret_cast<T*>(smem_raw);  // [16 warps][GJB_ROWS]
+  __shared__ int perm[GJB_ROWS];
+  const int e = blockIdx.x;
+  T* Mx = A + (long long)e * stride;
+  const int* piv = piv_all + (long long)e * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) perm[j] = j;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = piv[k];
+      if (p != k) { const int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
+    }
+  __syncthreads();
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const T* dsc = dsc_all + (long long)e * n;
+  T* rb = rowbuf + (size_t)w * GJB_ROWS;
+  for (int i = w; i < n; i += 16) {
+    for (int j = l; j < n; j += 32) rb[j] = Mx[(long long)i * lda + j];
+    __syncwarp();
+    for (int j = l; j < n; j += 32) Mx[(long long)i * lda + j] = rb[perm[j]] * dsc[j];
+    __syncwarp();
+  }
+}
+
 // One panel step of every batched item whose S_ee extends beyond column k0.
 __global__ void __launch_bounds__(256) k_lu_panel_grouped(const CondItem* __restrict__ items, int k0) {
   extern __shared__ unsigned char smem_raw[];
@@ -960,6 +1216,35 @@ cudaError_t lu_blocked_tf32(sc_ctx* c, float* See) {
   return cudaGetLastError();
 }
 
+// A_ii^-1 of blocks with n_i > 136 (FP32) or too large for a shared-memory copy (FP64):
+// copy A_ii into Ainv, equilibrate its rows, blocked Gauss-Jordan there, undo the
+// interchanges and the row scaling.  The pivot
+// indices use the S_ee pivot array as scratch (n_i <= n_b), which the LU overwrites later.
+template <class T>
+cudaError_t gj_blocked(sc_ctx* c, const T* Aown, long long sA, int lda, T* Ainv, int ldi) {
+  const Geo& G = c->G;
+  const int ni = G.ni, K = G.K;
+  const long long sI = (long long)ni * ldi;
+  if (ni > GJB_ROWS) return cudaErrorInvalidValue;
+  const size_t psm = (size_t)2 * PW * (GJB_CH + 1) * sizeof(T);
+  const size_t usm = (size_t)16 * GJB_ROWS * sizeof(T);
+  cudaError_t err = cudaFuncSetAttribute(k_gjb_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_gjb_unpermute<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usm);
+  if (err != cudaSuccess) return err;
+  ProfScope ps(c, SCK_GJ_INV);
+  count_launch(c, 2 + 2 * ((ni + PW - 1) / PW));
+  T* dsc = reinterpret_cast<T*>(c->gj_scale);
+  k_copy_block<T><<<dim3(cdiv((long long)ni * ni, 256 * 8), K), 256, 0, c->stream>>>(ni, ni, Aown, sA, lda, Ainv, sI, ldi);
+  k_row_equilibrate<T><<<dim3(cdiv(ni, 8), K), 256, 0, c->stream>>>(ni, Ainv, sI, ldi, dsc);
+  for (int k0 = 0; k0 < ni; k0 += PW) {
+    k_gjb_panel<T><<<K, 512, psm, c->stream>>>(ni, k0, Ainv, sI, ldi, c->piv, c->d_status);
+    k_gjb_update<T><<<dim3(cdiv(ni, GJB_CH), K), 256, 0, c->stream>>>(ni, k0, Ainv, sI, ldi);
+  }
+  k_gjb_unpermute<T><<<K, 512, usm, c->stream>>>(ni, Ainv, sI, ldi, c->piv, dsc);
+  return cudaGetLastError();
+}
+
 // Condensation set-up: A_ii^-1 (Gauss-Jordan), Y = A_ii^-1 A_ib,ee, S_ee = A_bb,ee -
 // A_bi,ee Y and the LU of S_ee.  With `tc` (FP32 only) the two products and the LU's
 // trailing updates run on the TF32 tensor cores and Y is kept transposed (nb x ldi), the
@@ -982,8 +1267,13 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
         done = true;
       }
     }
+    const size_t smem = (size_t)ni * (ni + 1) * sizeof(T) + ni * sizeof(T) + ni * sizeof(int);
+    if (!done && (ni > GJR_N || std::is_same<T, double>::value) && smem > kGjSmemMax) {
+      err = gj_blocked<T>(c, Aown, sA, lda, Ainv, ldi);
+      if (err != cudaSuccess) return err;
+      done = true;
+    }
     if (!done) {
-      const size_t smem = (size_t)ni * (ni + 1) * sizeof(T) + ni * sizeof(T) + ni * sizeof(int);
       err = cudaFuncSetAttribute(k_gj_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
       ProfScope ps(c, SCK_GJ_INV);
