@@ -5,7 +5,9 @@
 // Every element of every system becomes one item (its sizes and block addresses).  The
 // Gauss-Jordan inverses, the S_ee copies, the LU panel steps, the pivot permutations, the
 // diagonal-block inverses and the solve layout run as grouped launches over all items
-// (one CTA per item, shared memory sized for the largest).  The TF32 tensor-core
+// (one CTA per item).  Items are ordered by decreasing block size, so that the orders
+// N >= 5 (n_i > 136, n_b > 496) form a prefix that takes the large-block kernels (blocked
+// Gauss-Jordan, shared-memory LU panels) while the rest run register-resident.  The TF32 tensor-core
 // products (Y^T, S_ee, the LU trailing updates) run per order through tables of block
 // addresses, with the N-tile width of each chosen by timing the candidates on the
 // batch's own data (autotune).  The whole sequence can be captured once into a CUDA
@@ -41,6 +43,7 @@ struct sc_batch {
   void** d_ptrs = nullptr;
   std::vector<void*> h_ptrs;
   int max_ni = 0, max_nb = 0;
+  int nbig_gj = 0, nbig_lu = 0;  // leading items that take the large-block GJ / LU panel kernels
   int* d_status = nullptr;
   bool tuned = false;
   long long grouped_launches = 0;  // kernel launches of one run outside the systems' own
@@ -86,20 +89,20 @@ cudaError_t run_all(sc_batch* b, cudaStream_t st) {
   }
   const int n = (int)b->items.size();
   // grouped launches of this run: GJ, copy, 3 finishing kernels, the products and the panels
-  long long nl = 5 + 2 * (long long)b->cls.size();
+  long long nl = sc::grouped_gj_launches(b->nbig_gj, n, b->max_ni) + 4 + 2 * (long long)b->cls.size();
   for (int step = 0; 32 * step < b->max_nb; ++step) {
-    ++nl;
+    nl += (b->nbig_lu > 0 ? 1 : 0) + (n > b->nbig_lu ? 1 : 0);
     for (const OrderClass& oc : b->cls) nl += step < (int)oc.off_t.size() ? 1 : 0;
   }
   b->grouped_launches = nl;
-  if (e == cudaSuccess) e = sc::grouped_gj(st, b->d_items, n, b->max_ni);
+  if (e == cudaSuccess) e = sc::grouped_gj(st, b->d_items, n, b->nbig_gj, b->max_ni);
   for (const OrderClass& oc : b->cls)
     if (e == cudaSuccess) e = run_products_y(b, st, oc, oc.bn_y);
   if (e == cudaSuccess) e = sc::grouped_copy_bb(st, b->d_items, n);
   for (const OrderClass& oc : b->cls)
     if (e == cudaSuccess) e = run_products_s(b, st, oc, oc.bn_s);
   for (int step = 0; 32 * step < b->max_nb && e == cudaSuccess; ++step) {
-    e = sc::grouped_lu_panel(st, b->d_items, n, 32 * step, b->max_nb);
+    e = sc::grouped_lu_panel(st, b->d_items, n, b->nbig_lu, 32 * step, b->max_nb);
     for (const OrderClass& oc : b->cls)
       if (e == cudaSuccess && step < (int)oc.off_t.size()) e = run_trailing(b, st, oc, step, oc.bn_t);
   }
@@ -183,9 +186,22 @@ sc_status sc_batch_create(sc_ctx* const* ctxs, int nctx, sc_batch** out) {
       it.piv = c->piv + (size_t)e * G.nb;
       it.rowperm = c->rowperm + (size_t)e * G.nb;
       it.status = nullptr;  // set once the status word exists
+      it.dsc = reinterpret_cast<float*>(c->gj_scale) + (size_t)e * G.ni;
       b->items.push_back(it);
     }
   }
+  // the large-block kernels take a prefix of the items (sorted by decreasing n_b, and n_i
+  // grows with n_b)
+  for (const CondItem& it : b->items) {
+    if (sc::gj_blocked_item(it.ni)) ++b->nbig_gj;
+    if (sc::lu_panel_smem_item(it.nb)) ++b->nbig_lu;
+  }
+  for (int i = 0; i < (int)b->items.size(); ++i)
+    if (sc::gj_blocked_item(b->items[i].ni) != (i < b->nbig_gj) ||
+        sc::lu_panel_smem_item(b->items[i].nb) != (i < b->nbig_lu)) {
+      delete b;
+      return SC_ERR_ARG;
+    }
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_status), sizeof(int));
   for (CondItem& it : b->items) it.status = b->d_status;
   // address tables of the products, per order class

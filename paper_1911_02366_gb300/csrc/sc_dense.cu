@@ -231,11 +231,6 @@ __global__ void k_gj_inv(int n, const T* __restrict__ A, long long strideA, int 
 }
 
 // ---- grouped kernels of the batched condensation: one CTA per CondItem ----------------
-__global__ void k_gj_inv_grouped(const CondItem* __restrict__ items) {
-  const CondItem it = items[blockIdx.x];
-  gj_inv_body<float>(it.ni, it.Aown, it.lda, it.Ainv, it.ldi, it.status, it.e);
-}
-
 __global__ void __launch_bounds__(256, 2) k_gj_inv_reg_grouped(const CondItem* __restrict__ items) {
   const CondItem it = items[blockIdx.x];
   gj_inv_reg_body(it.ni, it.Aown, it.lda, it.Ainv, it.ldi, it.status, it.e);
@@ -629,8 +624,8 @@ __device__ __forceinline__ bool gjb_better(T a, int ia, T b, int ib) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(512, 1) k_gjb_panel(int n, int k0, T* __restrict__ A, long long stride, int lda,
-                                                      int* __restrict__ piv_all, int* __restrict__ status) {
+__device__ void gjb_panel_body(int n, int k0, T* __restrict__ Mx, int lda, int* __restrict__ piv,
+                               int* __restrict__ status, int e) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stage = reinterpret_cast<T*>(smem_raw);  // [2 PW][GJB_CH + 1]: moved rows of one column chunk
   __shared__ T colk[2][GJB_ROWS];
@@ -638,9 +633,6 @@ __global__ void __launch_bounds__(512, 1) k_gjb_panel(int n, int k0, T* __restri
   __shared__ int pk[PW], ipv[PW], xl[PW];
   __shared__ int at[GJB_ROWS], where_[GJB_ROWS];  // positions k0 + q (q relative) <-> rows
   __shared__ int s_nx;
-  const int e = blockIdx.x;
-  T* Mx = A + (long long)e * stride;
-  int* piv = piv_all + (long long)e * n;
   const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int bw = min(PW, n - k0), rows = n - k0;
   T M[GJB_R];
@@ -753,11 +745,9 @@ __global__ void __launch_bounds__(512, 1) k_gjb_panel(int n, int k0, T* __restri
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_gjb_update(int n, int k0, T* __restrict__ A, long long stride, int lda) {
+__device__ void gjb_update_body(int n, int k0, T* __restrict__ Mx, int lda, int j0) {
   __shared__ T Ts[PW][GJB_CH];      // A_old[P, J] of this column block
   __shared__ T As[GJB_CH][PW + 1];  // panel columns of a 64-row tile
-  const int e = blockIdx.y, j0 = blockIdx.x * GJB_CH;
-  T* Mx = A + (long long)e * stride;
   const int bw = min(PW, n - k0);
   for (int t = threadIdx.x; t < PW * GJB_CH; t += blockDim.x) {
     const int k = t / GJB_CH, jj = t % GJB_CH, j = j0 + jj;
@@ -807,28 +797,24 @@ __global__ void __launch_bounds__(256) k_gjb_update(int n, int k0, T* __restrict
 // Row equilibration before the blocked Gauss-Jordan: a row <- d_i row, d_i = 1 / max |a_i.|,
 // one warp per row; the unpermute pass multiplies column j of the inverse by d_j.
 template <class T>
-__global__ void k_row_equilibrate(int n, T* __restrict__ A, long long stride, int lda, T* __restrict__ dsc) {
-  const int e = blockIdx.y;
+__device__ void row_equilibrate_body(int n, T* __restrict__ Mx, int lda, T* __restrict__ dsc) {
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), l = threadIdx.x & 31;
   if (i >= n) return;
-  T* row = A + (long long)e * stride + (long long)i * lda;
+  T* row = Mx + (long long)i * lda;
   T mx = T(0);
   for (int j = l; j < n; j += 32) mx = fmax(mx, tabs(row[j]));
   for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   const T d = mx > T(0) ? T(1) / mx : T(1);
   for (int j = l; j < n; j += 32) row[j] *= d;
-  if (l == 0) dsc[(long long)e * n + i] = d;
+  if (l == 0) dsc[i] = d;
 }
 
 template <class T>
-__global__ void __launch_bounds__(512) k_gjb_unpermute(int n, T* __restrict__ A, long long stride, int lda,
-                                                       const int* __restrict__ piv_all, const T* __restrict__ dsc_all) {
+__device__ void gjb_unpermute_body(int n, T* __restrict__ Mx, int lda, const int* __restrict__ piv,
+                                   const T* __restrict__ dsc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* rowbuf = reinterpret_cast<T*>(smem_raw);  // [16 warps][GJB_ROWS]
   __shared__ int perm[GJB_ROWS];
-  const int e = blockIdx.x;
-  T* Mx = A + (long long)e * stride;
-  const int* piv = piv_all + (long long)e * n;
   for (int j = threadIdx.x; j < n; j += blockDim.x) perm[j] = j;
   __syncthreads();
   if (threadIdx.x == 0)
@@ -838,7 +824,6 @@ __global__ void __launch_bounds__(512) k_gjb_unpermute(int n, T* __restrict__ A,
     }
   __syncthreads();
   const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const T* dsc = dsc_all + (long long)e * n;
   T* rb = rowbuf + (size_t)w * GJB_ROWS;
   for (int i = w; i < n; i += 16) {
     for (int j = l; j < n; j += 32) rb[j] = Mx[(long long)i * lda + j];
@@ -846,6 +831,62 @@ __global__ void __launch_bounds__(512) k_gjb_unpermute(int n, T* __restrict__ A,
     for (int j = l; j < n; j += 32) Mx[(long long)i * lda + j] = rb[perm[j]] * dsc[j];
     __syncwarp();
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(512, 1) k_gjb_panel(int n, int k0, T* __restrict__ A, long long stride, int lda,
+                                                      int* __restrict__ piv_all, int* __restrict__ status) {
+  const int e = blockIdx.x;
+  gjb_panel_body<T>(n, k0, A + (long long)e * stride, lda, piv_all + (long long)e * n, status, e);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gjb_update(int n, int k0, T* __restrict__ A, long long stride, int lda) {
+  gjb_update_body<T>(n, k0, A + (long long)blockIdx.y * stride, lda, blockIdx.x * GJB_CH);
+}
+
+template <class T>
+__global__ void k_row_equilibrate(int n, T* __restrict__ A, long long stride, int lda, T* __restrict__ dsc) {
+  row_equilibrate_body<T>(n, A + (long long)blockIdx.y * stride, lda, dsc + (long long)blockIdx.y * n);
+}
+
+template <class T>
+__global__ void __launch_bounds__(512) k_gjb_unpermute(int n, T* __restrict__ A, long long stride, int lda,
+                                                       const int* __restrict__ piv_all, const T* __restrict__ dsc) {
+  const int e = blockIdx.x;
+  gjb_unpermute_body<T>(n, A + (long long)e * stride, lda, piv_all + (long long)e * n, dsc + (long long)e * n);
+}
+
+// The same four steps for batched items (one item per CTA, blockIdx.y for the 2-D grids);
+// items whose A_ii is done or narrower than the block return at once.
+__global__ void k_copy_aii_grouped(const CondItem* __restrict__ items) {
+  const CondItem it = items[blockIdx.y];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < it.ni * it.ni; t += gridDim.x * blockDim.x) {
+    const int i = t / it.ni, j = t % it.ni;
+    it.Ainv[(long long)i * it.ldi + j] = it.Aown[(long long)i * it.lda + j];
+  }
+}
+
+__global__ void k_row_equilibrate_grouped(const CondItem* __restrict__ items) {
+  const CondItem it = items[blockIdx.y];
+  row_equilibrate_body<float>(it.ni, it.Ainv, it.ldi, it.dsc);
+}
+
+__global__ void __launch_bounds__(512, 1) k_gjb_panel_grouped(const CondItem* __restrict__ items, int k0) {
+  const CondItem it = items[blockIdx.x];
+  if (it.ni <= k0) return;
+  gjb_panel_body<float>(it.ni, k0, it.Ainv, it.ldi, it.piv, it.status, it.e);
+}
+
+__global__ void __launch_bounds__(256) k_gjb_update_grouped(const CondItem* __restrict__ items, int k0) {
+  const CondItem it = items[blockIdx.y];
+  if (it.ni <= k0 || (int)blockIdx.x * GJB_CH >= it.ni) return;
+  gjb_update_body<float>(it.ni, k0, it.Ainv, it.ldi, blockIdx.x * GJB_CH);
+}
+
+__global__ void __launch_bounds__(512) k_gjb_unpermute_grouped(const CondItem* __restrict__ items) {
+  const CondItem it = items[blockIdx.x];
+  gjb_unpermute_body<float>(it.ni, it.Ainv, it.ldi, it.piv, it.dsc);
 }
 
 // One panel step of every batched item whose S_ee extends beyond column k0.
@@ -1419,35 +1460,56 @@ cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
 size_t solve_layout_elems(const Geo& G) { return (size_t)G.K * ls_stride(G); }
 
 // ---- grouped launches of the batched condensation (one CTA per CondItem) --------------
-cudaError_t grouped_gj(cudaStream_t st, const CondItem* items, int n, int max_ni) {
-  if (max_ni <= GJR_N) {
-    const size_t smem = (size_t)GJR_N * GJR_LDS * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_gj_inv_reg_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t grouped_gj(cudaStream_t st, const CondItem* items, int n, int nbig, int max_ni) {
+  // items [0, nbig): n_i > 136, blocked Gauss-Jordan; the rest in registers
+  cudaError_t e = cudaSuccess;
+  if (nbig > 0) {
+    const size_t psm = (size_t)2 * PW * (GJB_CH + 1) * sizeof(float);
+    const size_t usm = (size_t)16 * GJB_ROWS * sizeof(float);
+    e = cudaFuncSetAttribute(k_gjb_panel_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_gjb_unpermute_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usm);
     if (e != cudaSuccess) return e;
-    k_gj_inv_reg_grouped<<<n, 256, smem, st>>>(items);
-    return cudaGetLastError();
+    k_copy_aii_grouped<<<dim3(cdiv((long long)max_ni * max_ni, 256 * 8), nbig), 256, 0, st>>>(items);
+    k_row_equilibrate_grouped<<<dim3(cdiv(max_ni, 8), nbig), 256, 0, st>>>(items);
+    for (int k0 = 0; k0 < max_ni; k0 += PW) {
+      k_gjb_panel_grouped<<<nbig, 512, psm, st>>>(items, k0);
+      k_gjb_update_grouped<<<dim3(cdiv(max_ni, GJB_CH), nbig), 256, 0, st>>>(items, k0);
+    }
+    k_gjb_unpermute_grouped<<<nbig, 512, usm, st>>>(items);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  const size_t smem = (size_t)max_ni * (max_ni + 1) * sizeof(float) + max_ni * sizeof(float) + max_ni * sizeof(int);
-  cudaError_t e = cudaFuncSetAttribute(k_gj_inv_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_gj_inv_grouped<<<n, 256, smem, st>>>(items);
+  if (n > nbig) {
+    const size_t smem = (size_t)GJR_N * GJR_LDS * sizeof(float);
+    e = cudaFuncSetAttribute(k_gj_inv_reg_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gj_inv_reg_grouped<<<n - nbig, 256, smem, st>>>(items + nbig);
+  }
   return cudaGetLastError();
 }
+
+int grouped_gj_launches(int nbig, int n, int max_ni) {
+  return (nbig > 0 ? 3 + 2 * ((max_ni + PW - 1) / PW) : 0) + (n > nbig ? 1 : 0);
+}
+
+bool gj_blocked_item(int ni) { return ni > GJR_N; }
+bool lu_panel_smem_item(int nb) { return nb > LPR_ROWS; }
 
 cudaError_t grouped_copy_bb(cudaStream_t st, const CondItem* items, int n) {
   k_copy_bb_grouped<<<n, 256, 0, st>>>(items);
   return cudaGetLastError();
 }
 
-cudaError_t grouped_lu_panel(cudaStream_t st, const CondItem* items, int n, int k0, int max_nb) {
-  if (max_nb <= LPR_ROWS) {
-    k_lu_panel_reg_grouped<<<n, 256, 0, st>>>(items, k0);
-    return cudaGetLastError();
+cudaError_t grouped_lu_panel(cudaStream_t st, const CondItem* items, int n, int nbig, int k0, int max_nb) {
+  // items [0, nbig): n_b > 496, panel in shared memory; the rest in registers
+  if (nbig > 0) {
+    const size_t smem = (size_t)max_nb * (PW + 1) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_lu_panel_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_lu_panel_grouped<<<nbig, 256, smem, st>>>(items, k0);
   }
-  const size_t smem = (size_t)max_nb * (PW + 1) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_lu_panel_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_lu_panel_grouped<<<n, 256, smem, st>>>(items, k0);
+  if (n > nbig) k_lu_panel_reg_grouped<<<n - nbig, 256, 0, st>>>(items + nbig, k0);
   return cudaGetLastError();
 }
 

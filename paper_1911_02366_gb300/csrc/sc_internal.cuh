@@ -344,6 +344,7 @@ struct CondItem {
   float *Ainv, *Yt, *See, *Sls;   // A_ii^-1 (ni x ldi), Y^T (nb x ldi), S_ee (nb x lds), solve layout
   int *piv, *rowperm;
   int* status;
+  float* dsc;                     // n_i row scales of the blocked Gauss-Jordan (n_i > 136)
 };
 
 // Status word value written by a tensor-core kernel whose bounded wait ran out (element
@@ -397,9 +398,14 @@ cudaError_t upload_explicit_tables(sc_ctx* c);
 size_t explicit_elems_W(const Geo& G, const sc_ctx* c);
 cudaError_t explicit_build(sc_ctx* c);
 cudaError_t explicit_matvec32(sc_ctx* c, const float* x, double* y);
-cudaError_t grouped_gj(cudaStream_t st, const CondItem* items, int n, int max_ni);
+// Items are sorted by decreasing block size; the first nbig of them take the large-block
+// kernels (blocked Gauss-Jordan for n_i > 136, shared-memory panels for n_b > 496).
+cudaError_t grouped_gj(cudaStream_t st, const CondItem* items, int n, int nbig, int max_ni);
+int grouped_gj_launches(int nbig, int n, int max_ni);
+bool gj_blocked_item(int ni);
+bool lu_panel_smem_item(int nb);
 cudaError_t grouped_copy_bb(cudaStream_t st, const CondItem* items, int n);
-cudaError_t grouped_lu_panel(cudaStream_t st, const CondItem* items, int n, int k0, int max_nb);
+cudaError_t grouped_lu_panel(cudaStream_t st, const CondItem* items, int n, int nbig, int k0, int max_nb);
 cudaError_t grouped_finish(cudaStream_t st, const CondItem* items, int n, int max_nb);
 cudaError_t to_float(sc_ctx* c, const double* a, float* b, size_t n);
 cudaError_t gemm_tf32_ptrs(cudaStream_t stream, int M, int N, int K, float alpha, const float* const* Ap, int lda,

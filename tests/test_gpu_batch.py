@@ -1,4 +1,4 @@
-"""Batched condensation of systems of uneven order (N = 2, 3, 4) in grouped launches,
+"""Batched condensation of systems of uneven order (N = 2 .. 6) in grouped launches,
 captured in a CUDA graph with autotuned tile widths: every system must come out exactly as
 its own sc_condense makes it, and solve to the same answer."""
 import numpy as np
@@ -10,7 +10,7 @@ from gpu_common import TWO_PI, gpu_context
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ORDERS = [(3, 2), (3, 3), (2, 4)]  # (elements per direction, N)
+ORDERS = [(3, 2), (3, 3), (2, 4), (1, 5), (1, 6)]  # (elements per direction, N)
 
 
 def _context(n, N):
@@ -52,9 +52,9 @@ def test_batched_condensation_equals_each_systems_own(graph):
             assert st_b["gmres_iters"] == st_r["gmres_iters"], (N, seed, st_b, st_r)
             assert np.max(np.abs(dQ_b - dQ_r)) <= 1e-13 * np.max(np.abs(dQ_r)), (N, seed)
             assert st_b["rel_residual"] < 1e-8
-    for cidx in range(3):
+    for cidx in range(len(ORDERS)):
         ni, by, bs, bt = batch.tiles(cidx)
-        assert ni in (5, 40, 135) and {by, bs, bt} <= {64, 144, 256}
+        assert ni in (5, 40, 135, 320, 625) and {by, bs, bt} <= {64, 144, 256}
     batch.close()
 
 
