@@ -1157,6 +1157,117 @@ __device__ __forceinline__ void ls_solve_warp(int n, int nblk, const TS* __restr
   }
 }
 
+// The same substitutions by a CTA of W warps per element, for meshes with too few elements
+// to fill the GPU one warp each: in every block row the W warps share the off-diagonal
+// 4-column groups (strided), their partial dot products meet in shared memory, and warp
+// 0 adds the diagonal block's part and writes the row.  Two CTA barriers per block row.
+template <class T, class TS, int W>
+__device__ __forceinline__ void ls_solve_cta(int n, int nblk, const TS* __restrict__ Le, int npad, T* s, T* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nq = npad / 4;
+  for (int b = 0; b < nblk; ++b) {  // forward
+    const int i0 = 32 * b, R = i0 + lane;
+    const bool live = R < n;
+    const TS* row = Le + (long long)b * 32 * npad + 4 * lane;
+    T a0 = T(0), a1 = T(0);
+    if (live) {
+#pragma unroll 4
+      for (int q = w; q < i0 / 4; q += W) {
+        Quad<T, TS> m;
+        m.load(row + (long long)q * 128);
+        a0 = fma(m.v[0], s[4 * q], a0);
+        a1 = fma(m.v[1], s[4 * q + 1], a1);
+        a0 = fma(m.v[2], s[4 * q + 2], a0);
+        a1 = fma(m.v[3], s[4 * q + 3], a1);
+      }
+    }
+    red[w * 32 + lane] = a0 + a1;
+    __syncthreads();
+    if (w == 0) {
+      T d = s[R];
+      const int qd = min(i0 / 4 + 8, nq);
+#pragma unroll
+      for (int q = i0 / 4; q < qd; ++q) {
+        if (live && 4 * q < R) {
+          Quad<T, TS> m;
+          m.load(row + (long long)q * 128);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (4 * q + j < R) d = fma(m.v[j], s[4 * q + j], d);
+        }
+      }
+      T sum = T(0);
+#pragma unroll
+      for (int k = 0; k < W; ++k) sum += red[k * 32 + lane];
+      __syncwarp();
+      if (live) s[R] = d - sum;
+    }
+    __syncthreads();
+  }
+  for (int b = nblk - 1; b >= 0; --b) {  // backward
+    const int i0 = 32 * b, R = i0 + lane;
+    const bool live = R < n;
+    const TS* row = Le + (long long)b * 32 * npad + 4 * lane;
+    T a0 = T(0), a1 = T(0);
+    if (live) {
+#pragma unroll 4
+      for (int q = i0 / 4 + 8 + w; q < nq; q += W) {
+        Quad<T, TS> m;
+        m.load(row + (long long)q * 128);
+        a0 = fma(m.v[0], s[4 * q], a0);
+        a1 = fma(m.v[1], s[4 * q + 1], a1);
+        a0 = fma(m.v[2], s[4 * q + 2], a0);
+        a1 = fma(m.v[3], s[4 * q + 3], a1);
+      }
+    }
+    red[w * 32 + lane] = a0 + a1;
+    __syncthreads();
+    if (w == 0) {
+      T d = T(0);
+      const int qd = min(i0 / 4 + 8, nq);
+#pragma unroll
+      for (int q = i0 / 4; q < qd; ++q) {
+        if (live && 4 * q + 3 >= R) {
+          Quad<T, TS> m;
+          m.load(row + (long long)q * 128);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (4 * q + j >= R) d = fma(m.v[j], s[4 * q + j], d);
+        }
+      }
+      T sum = T(0);
+#pragma unroll
+      for (int k = 0; k < W; ++k) sum += red[k * 32 + lane];
+      __syncwarp();
+      if (live) s[R] = d - sum;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int kSolveCtaWarps = 8;
+
+template <class T, class TS>
+__global__ void __launch_bounds__(32 * kSolveCtaWarps) k_lu_solve_cta(int n, int nblk, const TS* __restrict__ LS,
+                                                                      long long lsstride, int npad,
+                                                                      const int* __restrict__ rowperm,
+                                                                      const double* __restrict__ v,
+                                                                      double* __restrict__ z, T* __restrict__ zt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int e = blockIdx.x, ls = nblk * 32;
+  T* s = reinterpret_cast<T*>(smem_raw);
+  T* red = s + ls;
+  const int* rp = rowperm + (long long)e * n;
+  const double* ve = v + (long long)e * n;
+  for (int i = threadIdx.x; i < ls; i += blockDim.x) s[i] = i < n ? (T)ve[__ldg(rp + i)] : T(0);
+  __syncthreads();
+  ls_solve_cta<T, TS, kSolveCtaWarps>(n, nblk, LS + (long long)e * lsstride, npad, s, red);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (z) z[(long long)e * n + i] = (double)s[i];
+    if (zt) zt[(long long)e * n + i] = s[i];
+  }
+}
+
 // z = (P^T L U)^-1 v, one warp per element (4 per CTA); the running vector (v, then x,
 // then z) sits in shared memory.  Arithmetic in the factor precision T; v in double,
 // outputs z (double) and / or zt (T).  CORR: add a 5 x 5 correction per boundary node,
@@ -1420,11 +1531,20 @@ inline int ls_nblk(const Geo& G) { return (G.nb + 31) / 32; }
 inline int ls_npad(const Geo& G) { return (G.nb + 3) & ~3; }
 inline long long ls_stride(const Geo& G) { return (long long)ls_nblk(G) * 32 * ls_npad(G); }
 
+// Meshes with fewer elements than this solve the block-Jacobi system with a CTA per element.
+constexpr int kSolveCtaMaxElems = 2048;
+
 template <class T, class TS>
 cudaError_t lu_solve_t(sc_ctx* c, const TS* LS, const double* v, double* z, T* zt) {
   const Geo& G = c->G;
   ProfScope ps(c, SCK_LU_SOLVE);
   const size_t smem = (size_t)4 * ls_nblk(G) * 32 * sizeof(T);
+  if (G.K < kSolveCtaMaxElems && !(c->learned_on && c->Ck)) {
+    const size_t csm = (size_t)(ls_nblk(G) + kSolveCtaWarps) * 32 * sizeof(T);
+    k_lu_solve_cta<T, TS><<<G.K, 32 * kSolveCtaWarps, csm, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
+                                                                       ls_npad(G), c->rowperm, v, z, zt);
+    return cudaGetLastError();
+  }
   if (c->learned_on && c->Ck)
     k_lu_solve<T, TS, true><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
                                                                     c->rowperm, v, z, zt, G.K, c->Ck);

@@ -230,3 +230,20 @@ def test_newton_step_converges_and_the_oracle_confirms_the_root():
     R0 = np.linalg.norm(O.residual(ps, Q0, Q0))
     R = np.linalg.norm(O.residual(ps, Q, Q0))
     assert R <= 1e-8 * R0, (R, R0)
+
+
+def test_mesh_above_the_cta_solve_threshold_reaches_1e8():
+    # 13^3 = 2197 elements: the block-Jacobi solve runs one warp per element (meshes of
+    # fewer than 2048 elements take a CTA per element); the oracle's Jacobian-vector
+    # product checks the global residual of the GPU solution
+    from paper_1911_02366_gb300 import sc
+    n, N = 13, 2
+    Q, dt, p, ctx = case(n, N, cfl=10.0, precision=sc.SC_PREC_MIXED, gmres_max_iters=4000, max_refine=20)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    dQ = np.zeros(Q.size)
+    st = ctx.sc_solve(dQ)
+    B = -O.residual(p, Q).reshape(-1)
+    r = B - O.jvp(p, Q, dQ.reshape(Q.shape)).reshape(-1)
+    assert np.linalg.norm(r) / np.linalg.norm(B) < 1e-8 * 1.01, st
