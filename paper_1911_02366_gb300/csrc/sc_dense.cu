@@ -452,45 +452,52 @@ __global__ void __launch_bounds__(256) k_lu_panel(int n, int k0, T* __restrict__
   if (threadIdx.x == 0 && s_bad) atomicCAS(status, -1, e);
 }
 
-// The same panel step of an FP32 block with n - k0 <= 496 rows, held in registers: lane l
-// is panel column l, warp w holds panel rows w + 8 r (r < 62).  Pivoting is implicit (the
+// The same panel step of an FP32 block with n - k0 <= NW R rows, held in registers: lane l
+// is panel column l, warp w of NW holds panel rows w + NW r (r < R).  Pivoting is implicit (the
 // pivot rows p_c are marked, nothing moves during the 32 eliminations); the pivot order is
 // then turned into the interchange sequence that row-by-row partial pivoting records
 // (piv[k0 + c] = k0 + position swapped with c), the panel is written in its final row
 // order, and one thread per column outside the panel applies the interchanges to its
 // column in registers and, right of the panel, forms U12 = L11^-1 A12 there.
+// Two shapes: 8 warps x 62 rows (496, n_b up to N = 4) and 16 warps x 69 rows (1104, N = 5, 6).
 constexpr int LPR_R = 62, LPR_ROWS = 8 * LPR_R;
+constexpr int LPR2_W = 16, LPR2_R = 69, LPR2_ROWS = LPR2_W * LPR2_R;
 
+template <int NW, int R>
 __device__ void lu_panel_reg_body(int n, int k0, float* __restrict__ Mx, int lda, int* __restrict__ piv,
                                   int* __restrict__ status, int e) {
-  __shared__ float colk[2][LPR_ROWS];  // column c of the current panel
+  constexpr int ROWS = NW * R, NT = (ROWS + 31) / 32, ND = (R + 63) / 64;
+  static_assert(NT <= 64, "pivot-search mask");
+  __shared__ float colk[2][ROWS];  // column c of the current panel
   __shared__ float rowk[PW];           // pivot row
   __shared__ float L11[PW][PW + 1];    // unit lower triangle of the factored panel, final order
   __shared__ int pk[PW], ipv[PW], xl[PW];
-  __shared__ int at[LPR_ROWS], where_[LPR_ROWS];  // position -> physical row, inverse
+  __shared__ int at[ROWS], where_[ROWS];  // position -> physical row, inverse
   __shared__ int s_nx;
   const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int bw = min(PW, n - k0), rows = n - k0;
-  float M[LPR_R];
+  float M[R];
 #pragma unroll
-  for (int r = 0; r < LPR_R; ++r) {
-    const int i = w + 8 * r;
+  for (int r = 0; r < R; ++r) {
+    const int i = w + NW * r;
     M[r] = (i < rows && l < bw) ? Mx[(long long)(k0 + i) * lda + k0 + l] : 0.f;
   }
   if (l == 0) {
 #pragma unroll
-    for (int r = 0; r < LPR_R; ++r) colk[0][w + 8 * r] = M[r];
+    for (int r = 0; r < R; ++r) colk[0][w + NW * r] = M[r];
   }
-  for (int i = threadIdx.x; i < LPR_ROWS; i += blockDim.x) { at[i] = i; where_[i] = i; }
+  for (int i = threadIdx.x; i < ROWS; i += blockDim.x) { at[i] = i; where_[i] = i; }
   if (threadIdx.x == 0) s_nx = 0;
-  unsigned sel = 0;  // bit t: search row l + 32 t is a pivot row already, or past the panel
+  unsigned long long sel = 0;  // bit t: search row l + 32 t is a pivot row already, or past the panel
 #pragma unroll
-  for (int t = 0; t < 16; ++t)
-    if (l + 32 * t >= rows) sel |= 1u << t;
-  unsigned long long done = 0ull;  // bit r: row w + 8 r is a pivot row already, or past the panel
+  for (int t = 0; t < NT; ++t)
+    if (l + 32 * t >= rows) sel |= 1ull << t;
+  unsigned long long done[ND];  // bit r: row w + NW r is a pivot row already, or past the panel
 #pragma unroll
-  for (int r = 0; r < LPR_R; ++r)
-    if (w + 8 * r >= rows) done |= 1ull << r;
+  for (int q = 0; q < ND; ++q) done[q] = 0ull;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (w + NW * r >= rows) done[r >> 6] |= 1ull << (r & 63);
   bool bad = false;
   __syncthreads();
   for (int c = 0; c < bw; ++c) {
@@ -499,9 +506,9 @@ __device__ void lu_panel_reg_body(int n, int k0, float* __restrict__ Mx, int lda
     // ties to the smallest row
     unsigned long long key = 0ull;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
+    for (int t = 0; t < NT; ++t) {
       const int i = l + 32 * t;
-      if (!((sel >> t) & 1u)) {
+      if (!((sel >> t) & 1ull)) {
         const unsigned long long kv = ((unsigned long long)(__float_as_uint(fabsf(ck[i])) + 1u) << 32) |
                                       (unsigned)(0x7fffffff - i);
         key = kv > key ? kv : key;
@@ -516,12 +523,14 @@ __device__ void lu_panel_reg_body(int n, int k0, float* __restrict__ Mx, int lda
     const float d = ck[p];
     bad |= !(fabsf(d) > 0.f);
     const float dinv = (d == 0.f) ? 0.f : 1.f / d;
-    if (l == (p & 31)) sel |= 1u << (p >> 5);
-    if (w == (p & 7)) {
-      const int pr = p >> 3;
-      done |= 1ull << pr;
+    if (l == (p & 31)) sel |= 1ull << (p >> 5);
+    if (w == p % NW) {
+      const int pr = p / NW;
 #pragma unroll
-      for (int r = 0; r < LPR_R; ++r)
+      for (int q = 0; q < ND; ++q)
+        if ((pr >> 6) == q) done[q] |= 1ull << (pr & 63);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
         if (r == pr) rowk[l] = M[r];
     }
     if (threadIdx.x == 0) pk[c] = p;
@@ -530,9 +539,9 @@ __device__ void lu_panel_reg_body(int n, int k0, float* __restrict__ Mx, int lda
     const int c1 = c + 1;
     float* cn = colk[c1 & 1];
 #pragma unroll
-    for (int r = 0; r < LPR_R; ++r) {
-      const int i = w + 8 * r;
-      if (!((done >> r) & 1ull)) {
+    for (int r = 0; r < R; ++r) {
+      const int i = w + NW * r;
+      if (!((done[r >> 6] >> (r & 63)) & 1ull)) {
         const float m = ck[i] * dinv;
         const float v = M[r];
         M[r] = (l == c) ? m : ((l > c) ? fmaf(-m, rk, v) : v);
@@ -554,8 +563,8 @@ __device__ void lu_panel_reg_body(int n, int k0, float* __restrict__ Mx, int lda
   for (int q = bw + threadIdx.x; q < rows; q += blockDim.x)
     if (at[q] != q) xl[atomicAdd(&s_nx, 1)] = q;
 #pragma unroll
-  for (int r = 0; r < LPR_R; ++r) {
-    const int i = w + 8 * r;
+  for (int r = 0; r < R; ++r) {
+    const int i = w + NW * r;
     if (i < rows && l < bw) {
       const int pos = where_[i];
       Mx[(long long)(k0 + pos) * lda + k0 + l] = M[r];
@@ -593,13 +602,26 @@ __global__ void __launch_bounds__(256, 2) k_lu_panel_reg(int n, int k0, float* _
                                                          int lda, int* __restrict__ piv_all,
                                                          int* __restrict__ status) {
   const int e = blockIdx.x;
-  lu_panel_reg_body(n, k0, A + (long long)e * stride, lda, piv_all + (long long)e * n, status, e);
+  lu_panel_reg_body<8, LPR_R>(n, k0, A + (long long)e * stride, lda, piv_all + (long long)e * n, status, e);
+}
+
+__global__ void __launch_bounds__(32 * LPR2_W, 1) k_lu_panel_reg2(int n, int k0, float* __restrict__ A,
+                                                                  long long stride, int lda,
+                                                                  int* __restrict__ piv_all, int* __restrict__ status) {
+  const int e = blockIdx.x;
+  lu_panel_reg_body<LPR2_W, LPR2_R>(n, k0, A + (long long)e * stride, lda, piv_all + (long long)e * n, status, e);
 }
 
 __global__ void __launch_bounds__(256, 2) k_lu_panel_reg_grouped(const CondItem* __restrict__ items, int k0) {
   const CondItem it = items[blockIdx.x];
   if (it.nb <= k0) return;
-  lu_panel_reg_body(it.nb, k0, it.See, it.lds, it.piv, it.status, it.e);
+  lu_panel_reg_body<8, LPR_R>(it.nb, k0, it.See, it.lds, it.piv, it.status, it.e);
+}
+
+__global__ void __launch_bounds__(32 * LPR2_W, 1) k_lu_panel_reg2_grouped(const CondItem* __restrict__ items, int k0) {
+  const CondItem it = items[blockIdx.x];
+  if (it.nb <= k0) return;
+  lu_panel_reg_body<LPR2_W, LPR2_R>(it.nb, k0, it.See, it.lds, it.piv, it.status, it.e);
 }
 
 // ---- blocked Gauss-Jordan inverse (blocks too large for one CTA's registers) ----------
@@ -1346,7 +1368,7 @@ cudaError_t lu_blocked_tf32(sc_ctx* c, float* See) {
   const int nb = G.nb, K = G.K, lds = G.lds;
   const long long sS = (long long)nb * lds;
   const size_t smem = (size_t)nb * (PW + 1) * sizeof(float);
-  const bool reg = nb <= LPR_ROWS;
+  const bool reg = nb <= LPR_ROWS, reg2 = !reg && nb <= LPR2_ROWS;
   cudaError_t err = cudaFuncSetAttribute(k_lu_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   ProfScope ps(c, SCK_LU);  // one measured span over all panels
@@ -1355,6 +1377,8 @@ cudaError_t lu_blocked_tf32(sc_ctx* c, float* See) {
     if (k0 > 0) count_launch(c);
     if (reg)
       k_lu_panel_reg<<<K, 256, 0, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
+    else if (reg2)
+      k_lu_panel_reg2<<<K, 32 * LPR2_W, 0, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
     else
       k_lu_panel<float><<<K, 256, smem, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
     if (rest > 0) {
@@ -1622,8 +1646,11 @@ cudaError_t grouped_copy_bb(cudaStream_t st, const CondItem* items, int n) {
 }
 
 cudaError_t grouped_lu_panel(cudaStream_t st, const CondItem* items, int n, int nbig, int k0, int max_nb) {
-  // items [0, nbig): n_b > 496, panel in shared memory; the rest in registers
-  if (nbig > 0) {
+  // items [0, nbig): n_b > 496, 16-warp register panel (shared memory beyond 1104 rows);
+  // the rest in the 8-warp register panel
+  if (nbig > 0 && max_nb <= LPR2_ROWS) {
+    k_lu_panel_reg2_grouped<<<nbig, 32 * LPR2_W, 0, st>>>(items, k0);
+  } else if (nbig > 0) {
     const size_t smem = (size_t)max_nb * (PW + 1) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_lu_panel_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
