@@ -88,6 +88,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// Eight consecutive accumulator columns of this thread's TMEM lane, without the wait:
+// the registers are valid only after tmem_wait_ld.
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t r[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -192,6 +201,7 @@ struct Stager {
 };
 
 constexpr int TC_TMEM_COLS = 256;
+constexpr int TC_EG = 4;  // 8-column chunks per epilogue group
 template <int BN>
 constexpr size_t tc_stage_bytes() {
   return (size_t)(TC_BM / 8) * TC_SBO + (size_t)(BN / 8) * TC_SBO;
@@ -298,17 +308,38 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(int M, int N, int K, float al
   if (!s_err) {
     const int row = warp * 32 + lane;
     float* crow = C + (long long)(m0 + row) * ldc + n0;
+    // groups of TC_EG 8-column chunks: the C loads of a group are issued together, then
+    // its TMEM loads with one wait, so that each thread has TC_EG x 32 bytes in flight
 #pragma unroll 1
-    for (int cc = 0; cc < BN; cc += 8) {
-      float v[8];
-      tmem_ld8(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(cc), v);
-      if (row < mrows && cc < nrows) {
+    for (int cg = 0; cg < BN; cg += 8 * TC_EG) {
+      float4 cl[TC_EG][2];
+#pragma unroll
+      for (int g = 0; g < TC_EG; ++g) {
+        const int cc = cg + 8 * g;
+        cl[g][0] = cl[g][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (beta != 0.0f && vecC && row < mrows && cc + 8 <= nrows) {
+          cl[g][0] = *reinterpret_cast<const float4*>(crow + cc);
+          cl[g][1] = *reinterpret_cast<const float4*>(crow + cc + 4);
+        }
+      }
+      uint32_t r[TC_EG][8];
+#pragma unroll
+      for (int g = 0; g < TC_EG; ++g)
+        tmem_ld8_async(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(cg + 8 * g), r[g]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int g = 0; g < TC_EG; ++g)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) asm volatile("" : "+r"(r[g][i]));  // no use moves above the wait
+#pragma unroll
+      for (int g = 0; g < TC_EG; ++g) {
+        const int cc = cg + 8 * g;
+        if (row >= mrows || cc >= nrows) continue;
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[g][i]);
         if (vecC && cc + 8 <= nrows) {
-          float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
-          if (beta != 0.0f) {
-            lo = *reinterpret_cast<const float4*>(crow + cc);
-            hi = *reinterpret_cast<const float4*>(crow + cc + 4);
-          }
+          float4 lo = cl[g][0], hi = cl[g][1];
           lo.x = fmaf(alpha, v[0], beta * lo.x);
           lo.y = fmaf(alpha, v[1], beta * lo.y);
           lo.z = fmaf(alpha, v[2], beta * lo.z);
