@@ -22,7 +22,7 @@ def test_condensed_size_ratio_table(N):
         assert O.ratio_formula(N, int(d)) == pytest.approx(eval(tab[d], {"N": N}), rel=1e-15)
 
 
-@pytest.mark.parametrize("n,N", [(2, 3), (3, 2), (1, 3)])
+@pytest.mark.parametrize("n,N", [(2, 3), (3, 2), (1, 3), (1, 5), (1, 6)])
 def test_condensed_equals_global(n, N):
     # Block Gauss elimination is exact algebra (eqs. StaticCondBlock, SC_step1/2).
     Q, dt = I.tgv_state(n, N, cfl=10.0)

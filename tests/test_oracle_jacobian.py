@@ -25,6 +25,24 @@ def test_jacobian_matches_central_differences(tgv_small):
         assert np.abs(y - fd).max() / np.abs(y).max() < 1e-8
 
 
+@pytest.mark.parametrize("N", [5, 6])
+def test_high_order_jacobian_matches_central_differences(N):
+    # the orders of the two largest workloads: the 1-direction dual product against
+    # central differences of the residual, and one element's rows of the 5-direction
+    # build against that product
+    n = 2
+    Q, dt = I.tgv_state(n, N, eps=1e-2)
+    p = O.Params(n=n, N=N, dt=dt)
+    x = np.random.default_rng(7).standard_normal(Q.shape)
+    y = O.jvp(p, Q, x)
+    h = 1e-5
+    fd = (O.residual(p, Q + h * x, Q) - O.residual(p, Q - h * x, Q)) / (2 * h)
+    assert np.abs(y - fd).max() / np.abs(y).max() < 1e-8
+    e = 3
+    ye = sum(blk @ x[c].reshape(-1) for c, blk in O.jacobian_element_rows(p, Q, e).items())
+    assert np.abs(ye - y[e].reshape(-1)).max() < 1e-12 * np.abs(y).max()
+
+
 def test_jvp_equals_matrix(tgv_small):
     p, Q, A = tgv_small
     x = np.random.default_rng(2).standard_normal(Q.shape)
@@ -106,14 +124,14 @@ def test_linear_model_jacobian_is_state_independent():
     assert abs(A1 - A2).max() < 1e-13 * abs(A1).max()
 
 
-@pytest.mark.parametrize("N", [2, 3, 4])
-def test_own_block_couples_only_nodes_sharing_a_gl_index(N):
+@pytest.mark.parametrize("n,N", [(3, 2), (3, 3), (3, 4), (2, 5), (2, 6)])
+def test_own_block_couples_only_nodes_sharing_a_gl_index(n, N):
     """Own element block of the Jacobian: node a couples to node b only if they share at
     least one of the three GL indices (volume terms act along grid lines, the BR1 viscous
     terms along lines of lines).  The condensed operator stores only these node blocks,
     so every other block must be exactly zero; the pattern is also tight (each kept
-    node pair carries a nonzero entry somewhere on the mesh)."""
-    n = 3
+    node pair carries a nonzero entry somewhere on the mesh).  On the 2^3 meshes (N = 5,
+    6) an element's neighbours across opposite faces coincide but are never the element."""
     Q, dt = I.tgv_state(n, N, cfl=50.0)
     p = O.Params(n=n, N=N, dt=dt, bdf=1)
     A = O.jacobian(p, Q).tocsr()
