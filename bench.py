@@ -464,13 +464,73 @@ def cpu_threads():
         return os.cpu_count()
 
 
+def run_timesteps(args, world, rank, local):
+    """Implicit time stepping of the workload's state: BDF2 steps (the first BDF1) at the
+    given CFL, each solved by Newton iterations (sc_newton_step: assemble, condense, solve,
+    update) until ||R|| <= newton_tol ||R_0||.  The value is DOF x time steps per second of
+    the whole loop; the per-step Newton and GMRES counts go with it."""
+    import torch
+    from paper_1911_02366_gb300 import sc
+
+    torch.cuda.set_device(local)
+    W = WORKLOAD
+    Q, dt = I.tgv_state(W["n"], W["N"], Ma=W["Ma"], seed=W["seed"], cfl=args.cfl)
+    dofs = Q.size
+    stream = torch.cuda.current_stream()
+    ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
+                     gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
+                     inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores)
+    ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
+    Qs = torch.tensor(Q.reshape(-1), device="cuda")
+    Qsm1 = None
+    sampler = ClockSampler(local) if rank == 0 else None
+    l0 = ctx.sc_launch_count()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True); end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    steps = []
+    for s in range(args.time_steps):
+        bdf = 1 if Qsm1 is None else 2
+        ctx.sc_set_timestep(dt, bdf)
+        ctx.sc_set_state(Qs, Qs, Qsm1)  # Newton starts from the last level
+        it, nrel, st = ctx.sc_newton_step(max_newton=args.max_newton, newton_tol=args.newton_tol)
+        Qn = torch.empty_like(Qs)
+        ctx.sc_get_state(Qn)
+        Qsm1, Qs = Qs, Qn
+        steps.append({"bdf": bdf, "newton": it, "newton_rel": nrel, "last_gmres_iters": st["gmres_iters"],
+                      "last_rel_residual": st["rel_residual"]})
+    end.record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.sc_launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    total_ms = gather_max(world, start.elapsed_time(end))
+    ctx.close()
+    return {
+        "metric": "implicit time steps: DOF x steps / s (Newton on each step, condensed mixed-precision solves)",
+        "value": world * dofs * args.time_steps / (total_ms * 1e-3), "unit": "DOF*steps/s", "n_gpus": world,
+        "steps": args.time_steps, "warmup": 0, "ms_per_step": total_ms / args.time_steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded Taylor-Green state, 1e-3 perturbation)",
+        "config": {"workload": f"tgv_{W['n']}x{W['n']}x{W['n']}_N{W['N']}_bdf2_cfl{args.cfl:g}",
+                   "elements": W["n"] ** 3, "order": W["N"], "dof": dofs, "cfl": args.cfl, "dt": dt,
+                   "newton_tol": args.newton_tol, "linear_rel_tol": REL_TOL, "arm": "timesteps",
+                   "gmres_restart": args.restart, "parallelism": f"replicas x{world}"},
+        "time_steps": steps, "newton_total": sum(x["newton"] for x in steps),
+        "gpu_launches": launches, "clocks": clocks,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--arm", choices=["fp64", "mixed", "learned", "batched"], default="mixed")
+    ap.add_argument("--arm", choices=["fp64", "mixed", "learned", "batched", "timesteps"], default="mixed")
+    ap.add_argument("--time-steps", type=int, default=10, help="timesteps arm: BDF2 steps")
+    ap.add_argument("--cfl", type=float, default=100.0, help="timesteps arm: CFL of the time step")
+    ap.add_argument("--newton-tol", type=float, default=1e-6, help="timesteps arm: ||R|| / ||R_0|| per step")
+    ap.add_argument("--max-newton", type=int, default=8, help="timesteps arm: Newton updates per step")
     ap.add_argument("--train-epochs", type=int, default=20, help="learned arm: training epochs (untimed)")
     ap.add_argument("--operator", choices=["implicit", "explicit"], default="implicit",
                     help="mixed arm: condensed operator applied implicitly or from explicit W_e blocks")
@@ -509,9 +569,10 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    line = run_batched(args, world, rank, local) if args.arm == "batched" else run_ours(args, world, rank, local)
+    runner = {"batched": run_batched, "timesteps": run_timesteps}.get(args.arm, run_ours)
+    line = runner(args, world, rank, local)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline and args.arm != "batched":
+        if world == 1 and not args.no_cpu_baseline and args.arm not in ("batched", "timesteps"):
             r = run_oracle(1)
             v = r["dof"] / r["seconds"][0]
             line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cpu_threads(), "kind": "oracle",
