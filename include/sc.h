@@ -50,7 +50,7 @@ typedef enum {
 enum { SC_PREC_FP64 = 0, SC_PREC_MIXED = 1 };
 enum { SC_PC_BLOCK_JACOBI = 0, SC_PC_NONE = 1, SC_PC_LEARNED = 2 };
 
-/* Physics and solver settings (App. B parameters; solver choices of the build). */
+/* Physics and solver settings (App. B parameters; solver choices of this library). */
 typedef struct {
   double gamma;          /* heat capacity ratio (1.4) */
   double Pr;             /* Prandtl number (0.72) */
