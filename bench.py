@@ -173,6 +173,7 @@ def run_ours(args, world, rank, local):
     ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
+                     outer_krylov=args.outer_krylov if args.arm != "fp64" else 0, inner_iters=args.inner_iters,
                      explicit_schur=1 if args.operator == "explicit" else 0, **extra)
 
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
@@ -265,6 +266,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": W["name"], "elements": W["n"] ** 3, "order": W["N"], "dof": dofs, "cfl": W["cfl"],
                    "Ma": W["Ma"], "Re": W["Re"], "arm": args.arm, "gmres_restart": args.restart,
                    "inner_tol": args.inner_tol if args.arm != "fp64" else None,
+                   "outer": (f"fgmres({args.outer_krylov})" if args.outer_krylov else "refinement sweeps")
+                   if args.arm != "fp64" else None,
                    "tensor_cores": bool(args.tensor_cores) if args.arm != "fp64" else False,
                    "operator": args.operator,
                    "l2": f"inputs larger than L2 (element blocks {blocks_gb:.1f} GB)", "parallelism": f"replicas x{world}"},
@@ -479,7 +482,8 @@ def run_timesteps(args, world, rank, local):
     stream = torch.cuda.current_stream()
     ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
-                     inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores)
+                     inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
+                     outer_krylov=args.outer_krylov, inner_iters=args.inner_iters)
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
     Qs = torch.tensor(Q.reshape(-1), device="cuda")
     Qsm1 = None
@@ -514,6 +518,8 @@ def run_timesteps(args, world, rank, local):
         "config": {"workload": f"tgv_{W['n']}x{W['n']}x{W['n']}_N{W['N']}_bdf2_cfl{args.cfl:g}",
                    "elements": W["n"] ** 3, "order": W["N"], "dof": dofs, "cfl": args.cfl, "dt": dt,
                    "newton_tol": args.newton_tol, "linear_rel_tol": REL_TOL, "arm": "timesteps",
+                   "outer": f"fgmres({args.outer_krylov})" if args.outer_krylov else "refinement sweeps",
+                   "inner_iters_cap": args.inner_iters or None,
                    "gmres_restart": args.restart, "parallelism": f"replicas x{world}"},
         "time_steps": steps, "newton_total": sum(x["newton"] for x in steps),
         "gpu_launches": launches, "clocks": clocks,
@@ -537,6 +543,9 @@ def main():
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--outer-krylov", type=int, default=0,
+                    help="mixed arms: 0 = refinement sweeps, m > 0 = outer FGMRES(m) on the FP64 system")
+    ap.add_argument("--inner-iters", type=int, default=0, help="mixed arms: cap per inner condensed solve (0 = none)")
     ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=1,
                     help="mixed arm: TF32 tcgen05 Schur products and LU trailing updates (1) or FP32 CUDA cores (0)")
     ap.add_argument("--n", type=int, default=None, help="elements per direction (profiling runs)")

@@ -79,12 +79,21 @@ typedef struct {
                             the extended boundary sets (Sec. 2.2) in sc_condense and apply
                             S = A_bb - sum_e P_e^T W_e P_e explicitly in GMRES; 0 = implicit
                             operator (default) */
+  int outer_krylov;      /* mixed arm: 0 = FP64 refinement sweeps x += A~^-1 (B - A x) (default);
+                            m in [1, gmres_restart] = the inner condensed solves act as a flexible
+                            preconditioner of FGMRES(m) on the global FP64 system (each outer step:
+                            one inner solve, one FP64 product with A, CGS2 on global vectors).  It
+                            converges where the sweeps diverge because the FP32 inner solves are
+                            too inexact for the conditioning */
+  int inner_iters;       /* mixed arm: cap on the GMRES iterations of one inner condensed solve
+                            (0 = no cap; the inner tolerance alone ends it) */
 } sc_config;
 
 /* Per-solve statistics filled by sc_solve. */
 typedef struct {
   int gmres_iters;          /* total GMRES iterations */
-  int refinements;          /* FP64 refinement sweeps (mixed arm), 0 for FP64 */
+  int refinements;          /* mixed arm: FP64 refinement sweeps, or outer FGMRES steps with
+                               outer_krylov; 0 for FP64 */
   double rel_residual;      /* ||B - A dQ||_2 / ||B||_2 recomputed in FP64 after the solve */
   double cond_rel_residual; /* last condensed residual estimate / ||B||_2 */
   double ms_rhs, ms_gmres, ms_backsub, ms_refine;  /* device time per phase */

@@ -90,7 +90,8 @@ void diff_matrix(const std::vector<double>& x, double D[SC_MAXP][SC_MAXP]) {
 void free_all(sc_ctx* c) {
   double** dps[] = {&c->Q, &c->Qh, &c->grad, &c->F, &c->B, &c->NJ, &c->RJ, &c->Aown, &c->X, &c->Ainv,
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
-                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk, &c->Sls, &c->dQn};
+                    &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk, &c->Sls, &c->dQn,
+                    &c->OV, &c->OZ};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
                    &c->Apk32, &c->Sls32, &c->Sdiag, &c->Cpl, &c->Feat, &c->Snorm, &c->Ynet, &c->Hbuf,
@@ -206,6 +207,7 @@ sc_status sc_create(const sc_config* cfg, void* cuda_stream, sc_ctx** out) {
       !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->gamma > 1) || !(cfg->Pr > 0))
     return SC_ERR_ARG;
   if (cfg->precision != SC_PREC_FP64 && cfg->precision != SC_PREC_MIXED) return SC_ERR_ARG;
+  if (cfg->outer_krylov < 0 || cfg->outer_krylov > cfg->gmres_restart || cfg->inner_iters < 0) return SC_ERR_ARG;
   sc_ctx* c = new sc_ctx();
   c->cfg = *cfg;
   c->stream = (cudaStream_t)cuda_stream;
@@ -319,6 +321,9 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
     A(dalloc(&c->See32, (size_t)G.K * G.nb * G.lds)); A(dalloc(&c->Dfull, dofs));
     A(dalloc(&c->Zf, n1)); A(dalloc(&c->Xbf, n1)); A(dalloc(&c->Uf, (size_t)G.K * G.ni));
     A(dalloc(&c->Cross32, n1 + (size_t)G.K * G.ni));
+    if (c->cfg.outer_krylov > 0) {
+      A(dalloc(&c->OV, dofs * (size_t)(c->cfg.outer_krylov + 1))); A(dalloc(&c->OZ, dofs * (size_t)c->cfg.outer_krylov));
+    }
   } else {
     A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Ytmp, (size_t)G.K * G.ni * G.nb));
     A(dalloc(&c->See, (size_t)G.K * G.nb * G.lds));
@@ -767,6 +772,84 @@ sc_status condensed_solve(sc_ctx* c, const double* r, double* d, double rel_tol_
   return SC_OK;
 }
 
+// FGMRES(m) on the global FP64 system A x = B with the FP32 condensed solve (condensed
+// right-hand side, inner GMRES, back-substitution) as a flexible preconditioner: the
+// FP64 products with A keep the outer iteration exact, so it converges even where the
+// inner solves are too inexact for refinement sweeps to contract.  x starts at 0.
+sc_status fgmres_global(sc_ctx* c, double* x, double target, int* iters_io, int* outer_io, double* rn_io) {
+  const Geo& G = c->G;
+  const size_t dofs = (size_t)G.K * G.ne;
+  const int m = c->cfg.outer_krylov, ma = c->restart_alloc;
+  double* const hs = c->Hd + 2 * (ma + 1) + 2;
+  double* const h1 = c->Hd;
+  double* const h2 = c->Hd + (ma + 1);
+  double* const hn2 = c->Hd + 2 * (ma + 1);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(2 * (ma + 1) + 1), y(m);
+  const int cap = c->cfg.inner_iters > 0 ? c->cfg.inner_iters : c->cfg.gmres_max_iters;
+  int iters = *iters_io, outer = *outer_io;
+  double rn = *rn_io;
+  const int max_outer = std::max(1, c->cfg.max_refine) * m;
+  while (rn > target && iters < c->cfg.gmres_max_iters && outer < max_outer) {
+    SC_CUDA(sc::vec_axpby(c, c->OV, 1.0 / rn, c->Rfull, 0.0, dofs));
+    std::fill(gv.begin(), gv.end(), 0.0); gv[0] = rn;
+    int k = 0;
+    for (int j = 0; j < m && iters < c->cfg.gmres_max_iters && outer < max_outer; ++j) {
+      double* Vj = c->OV + (size_t)j * dofs;
+      double* Zj = c->OZ + (size_t)j * dofs;
+      int it = 0;
+      double resid = 0.0, gnorm = 0.0;
+      sc_status s = condensed_solve(c, Vj, Zj, c->cfg.inner_tol, 0.0, std::min(cap, c->cfg.gmres_max_iters - iters),
+                                    &it, &resid, &gnorm);
+      if (s != SC_OK) return s;
+      iters += it;
+      ++outer;
+      SC_CUDA(sc::global_apply(c, Zj, c->Rfull));  // w = A z_j
+      SC_CUDA(sc::multidot(c, c->OV, j + 1, dofs, c->Rfull, h1));
+      SC_CUDA(sc::vec_update(c, c->Rfull, c->OV, j + 1, dofs, h1, -1.0));
+      SC_CUDA(sc::multidot(c, c->OV, j + 1, dofs, c->Rfull, h2));
+      SC_CUDA(sc::vec_update(c, c->Rfull, c->OV, j + 1, dofs, h2, -1.0));
+      SC_CUDA(sc::multidot(c, c->Rfull, 1, dofs, c->Rfull, hn2));
+      SC_CUDA(cudaMemcpyAsync(hbuf.data(), c->Hd, (2 * (ma + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+      SC_CUDA(cudaStreamSynchronize(c->stream));
+      double* Hc = &H[(size_t)j];  // column j, row stride m
+      for (int i = 0; i <= j; ++i) Hc[(size_t)i * m] = hbuf[i] + hbuf[(ma + 1) + i];
+      const double hn = std::sqrt(std::max(hbuf[2 * (ma + 1)], 0.0));
+      Hc[(size_t)(j + 1) * m] = hn;
+      if (!std::isfinite(hn)) return fail(c, SC_ERR_NONFINITE, "non-finite value in the outer FGMRES");
+      if (hn > 0) SC_CUDA(sc::vec_axpby(c, c->OV + (size_t)(j + 1) * dofs, 1.0 / hn, c->Rfull, 0.0, dofs));
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hc[(size_t)i * m] + sn[i] * Hc[(size_t)(i + 1) * m];
+        Hc[(size_t)(i + 1) * m] = -sn[i] * Hc[(size_t)i * m] + cs[i] * Hc[(size_t)(i + 1) * m];
+        Hc[(size_t)i * m] = t;
+      }
+      const double den = std::hypot(Hc[(size_t)j * m], Hc[(size_t)(j + 1) * m]);
+      cs[j] = Hc[(size_t)j * m] / den; sn[j] = Hc[(size_t)(j + 1) * m] / den;
+      Hc[(size_t)j * m] = den; Hc[(size_t)(j + 1) * m] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      k = j + 1;
+      if (std::fabs(gv[j + 1]) <= 0.9 * target || hn == 0.0) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double sum = gv[i];
+      for (int l = i + 1; l < k; ++l) sum -= H[(size_t)i * m + l] * y[l];
+      y[i] = sum / H[(size_t)i * m + i];
+    }
+    SC_CUDA(cudaMemcpyAsync(c->Hd, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    SC_CUDA(sc::vec_update(c, x, c->OZ, k, dofs, c->Hd, 1.0));
+    // true FP64 residual
+    SC_CUDA(sc::global_apply(c, x, c->Rfull));
+    SC_CUDA(sc::vec_axpby(c, c->Rfull, 1.0, c->B, -1.0, dofs));
+    rn = dnorm2(c, c->Rfull, dofs, hs);
+    if (!std::isfinite(rn)) return fail(c, SC_ERR_NONFINITE, "non-finite outer FGMRES residual");
+  }
+  *iters_io = iters;
+  *outer_io = outer;
+  *rn_io = rn;
+  return SC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -804,7 +887,12 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
     SC_CUDA(cudaMemcpyAsync(c->Rfull, c->B, dofs * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     rn = bnorm;
     int sweeps = 0;
-    while (rn > target && sweeps < c->cfg.max_refine && iters < c->cfg.gmres_max_iters) {
+    if (c->cfg.outer_krylov > 0) {
+      sc_status s = fgmres_global(c, xout, target, &iters, &sweeps, &rn);
+      if (s != SC_OK) { c->op32 = false; return s; }
+    }
+    while (rn > target && sweeps < c->cfg.max_refine && iters < c->cfg.gmres_max_iters &&
+           c->cfg.outer_krylov == 0) {
       int it = 0;
       sc_status s = condensed_solve(c, c->Rfull, c->Dfull, c->cfg.inner_tol, 0.5 * target,
                                     c->cfg.gmres_max_iters - iters, &it, &resid, &gnorm);

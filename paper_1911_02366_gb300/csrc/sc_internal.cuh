@@ -258,6 +258,7 @@ struct sc_ctx {
   double *NJ = nullptr, *RJ = nullptr, *Aown = nullptr, *X = nullptr;
   int *d_nbr = nullptr, *d_perm = nullptr, *d_iperm = nullptr, *d_own_pairs = nullptr;
   double* gj_scale = nullptr;      // [K][n_i] row scaling of the blocked Gauss-Jordan (T-typed)
+  double *OV = nullptr, *OZ = nullptr;  // outer FGMRES: Arnoldi basis (m+1 global vectors), preconditioned (m)
   int *d_prow = nullptr, *d_pslot = nullptr, *d_pcol = nullptr, *d_pptr = nullptr, *d_pinfo = nullptr;
   double *Ainv = nullptr, *Ytmp = nullptr, *See = nullptr;
   int *piv = nullptr, *rowperm = nullptr, *d_status = nullptr;

@@ -247,3 +247,24 @@ def test_mesh_above_the_cta_solve_threshold_reaches_1e8():
     B = -O.residual(p, Q).reshape(-1)
     r = B - O.jvp(p, Q, dQ.reshape(Q.shape)).reshape(-1)
     assert np.linalg.norm(r) / np.linalg.norm(B) < 1e-8 * 1.01, st
+
+
+@pytest.mark.parametrize("mo,cap", [(10, 30), (5, 0)])
+def test_mixed_solve_with_outer_fgmres_matches_oracle_global_solve(mo, cap):
+    # the inner FP32 condensed solves as a flexible preconditioner of FGMRES(mo) on the
+    # FP64 system (capped at `cap` inner iterations each, or by the inner tolerance)
+    from paper_1911_02366_gb300 import sc
+    n, N = 2, 3
+    Q, dt, p, ctx = case(n, N, cfl=10.0, precision=sc.SC_PREC_MIXED, rel_tol=1e-12, inner_tol=1e-4,
+                         gmres_restart=30, gmres_max_iters=4000, max_refine=20, outer_krylov=mo, inner_iters=cap)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    dQ = np.zeros(Q.size)
+    st = ctx.sc_solve(dQ)
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    x = O.global_solve(A, B)
+    assert st["refinements"] >= 1
+    assert np.linalg.norm(B - A @ dQ) / np.linalg.norm(B) < 1e-11
+    assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < 1e-9, st
