@@ -115,6 +115,9 @@ def lib():
         L.or_jacobian_elem_rows.argtypes = [P, dp, ctypes.c_int, ip, dp]
         L.or_num_flux.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_int, dp]
         L.or_phys_flux.argtypes = [P, dp, dp, ctypes.c_int, dp, dp]
+        L.or_residual_mixed.argtypes = [P, ip, ctypes.c_int, dp, dp, dp, dp]
+        L.or_jvp_mixed.argtypes = [P, ip, ctypes.c_int, dp, dp, dp]
+        L.or_jacobian_mixed.argtypes = [P, ip, ctypes.c_int, dp, dp]
         _lib = L
     return _lib
 
@@ -217,3 +220,54 @@ from .linalg import (  # noqa: E402
     boundary_interior_split, condensed_operator, condensed_solve, global_solve, gmres,
     ratio_formula,
 )
+
+
+# ---- meshes of mixed order (element e of order orders[e]; mortar faces between orders)
+# States are flat [sum_e (N_e+1)^3, 5], element by element.  `force_mortar` routes the
+# faces between equal orders through the mortar too (it must then reduce to the
+# conforming face).
+
+def _orders(p: Params, orders) -> np.ndarray:
+    o = np.ascontiguousarray(orders, dtype=np.int32)
+    if o.shape != (p.K,):
+        raise ValueError("one order per element")
+    return o
+
+
+def mixed_nodes(orders) -> int:
+    return int(sum((int(N) + 1) ** 3 for N in orders))
+
+
+def residual_mixed(p: Params, orders, Q, Qs=None, Qsm1=None, force_mortar: bool = False) -> np.ndarray:
+    """R(Q) of eq. NeqtonEq on a mixed-order mesh, flat [nodes, 5]."""
+    o = _orders(p, orders)
+    Q = _f64(Q)
+    Qs = Q if Qs is None else _f64(Qs)
+    Qsm1 = Qs if Qsm1 is None else _f64(Qsm1)
+    R = np.zeros((mixed_nodes(o), 5))
+    if lib().or_residual_mixed(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), _dp(Qs), _dp(Qsm1),
+                               _dp(R)) != 0:
+        raise ValueError("orders must lie in 1..7")
+    return R
+
+
+def jvp_mixed(p: Params, orders, Q, x, force_mortar: bool = False) -> np.ndarray:
+    """(dR/dQ)(Q) x on a mixed-order mesh, flat [nodes, 5]."""
+    o = _orders(p, orders)
+    Q = _f64(Q); x = _f64(x)
+    y = np.zeros((mixed_nodes(o), 5))
+    if lib().or_jvp_mixed(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), _dp(x), _dp(y)) != 0:
+        raise ValueError("orders must lie in 1..7")
+    return y
+
+
+def jacobian_mixed(p: Params, orders, Q, force_mortar: bool = False) -> np.ndarray:
+    """Dense dR/dQ on a (small) mixed-order mesh, [dofs, dofs]."""
+    o = _orders(p, orders)
+    Q = _f64(Q)
+    dofs = mixed_nodes(o) * 5
+    A = np.zeros((dofs, dofs))
+    if lib().or_jacobian_mixed(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), _dp(A)) != 0:
+        raise ValueError("orders must lie in 1..7")
+    return A
+

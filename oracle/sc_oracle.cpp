@@ -710,3 +710,390 @@ int or_num_threads() {
 }
 
 }  // extern "C"
+
+// ============================================================ meshes of mixed order
+// Element e carries its own order N_e (periodic n^3 mesh, same Cartesian cells).  A face
+// between two orders is a mortar (the survey's reading of an unstated case): both
+// traces, of the state and of the lifted gradient, are interpolated to the Gauss-Lobatto
+// nodes of order M = max(N_L, N_R) on the face; qhat (BR1) and fhat are formed there
+// point by point, exactly as on a conforming face, and each side takes the L2 projection
+// of them onto its own face polynomials (degree N_e in each in-face direction), with a
+// Gauss rule of M + 1 points (exact to degree 2M + 1).  The element's weak form then
+// integrates the projected values with its own Gauss-Lobatto face quadrature.  Faces
+// between equal orders are conforming unless force_mortar is set; the mortar of equal
+// orders reduces to the conforming face, which is what the pins check.
+namespace {
+
+struct MDisc {
+  or_params P;
+  int n, K, force_mortar;
+  double h, J, Jf, dx;
+  std::vector<int> ord, off;  // order and first node of every element
+  std::vector<Basis> B;       // B[N], N = 1..7
+  MDisc(const or_params& pp, const int* orders, int fm) : P(pp), force_mortar(fm) {
+    n = P.n; K = n * n * n;
+    h = P.L / n; J = std::pow(0.5 * h, 3); Jf = std::pow(0.5 * h, 2); dx = 2.0 / h;
+    ord.assign(orders, orders + K);
+    off.assign(K + 1, 0);
+    for (int e = 0; e < K; ++e) off[e + 1] = off[e] + (ord[e] + 1) * (ord[e] + 1) * (ord[e] + 1);
+    B.resize(8);
+    for (int N = 1; N <= 7; ++N) B[N] = make_basis(N);
+  }
+  int p(int e) const { return ord[e] + 1; }
+  int nn(int e) const { return p(e) * p(e) * p(e); }
+  int node(int e, int i, int j, int k) const { const int q = p(e); return i + q * (j + q * k); }
+  void coords(int e, int m, int c[3]) const { const int q = p(e); c[0] = m % q; c[1] = (m / q) % q; c[2] = m / (q * q); }
+  int elem(int ex, int ey, int ez) const {
+    ex = ((ex % n) + n) % n; ey = ((ey % n) + n) % n; ez = ((ez % n) + n) % n;
+    return ex + n * (ey + n * ez);
+  }
+  int neighbor(int e, int d, int s) const {
+    int c[3] = {e % n, (e / n) % n, e / (n * n)}; c[d] += s; return elem(c[0], c[1], c[2]);
+  }
+  size_t nodes() const { return (size_t)off[K]; }
+};
+
+template <class T> struct IsDual { static constexpr bool v = false; };
+template <int ND> struct IsDual<Dual<ND>> { static constexpr bool v = true; };
+
+// Ragged state accessor, with the same seeding rules as Access.
+template <class T>
+struct MAccess {
+  const MDisc* D; const double* Q; int se = -1, sn = -1; const double* dir = nullptr;
+  T get(int e, int m, int k) const {
+    const size_t i = ((size_t)D->off[e] + m) * NV + k;
+    T t(Q[i]);
+    if constexpr (IsDual<T>::v) {
+      if (dir) t.d[0] = dir[i];
+      else if (e == se && m == sn && k < (int)(sizeof(t.d) / sizeof(double))) t.d[k] = 1.0;
+    }
+    return t;
+  }
+};
+
+// Gauss-Legendre points and weights (Newton on P_m from the Chebyshev guesses).
+void gauss_legendre(int m, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(m, 0.0); w.assign(m, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < m; ++i) {
+    double z = -std::cos(pi * (i + 0.75) / (m + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP, d2P; legendre(m, z, P, dP, d2P);
+      const double dz = P / dP;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double P, dP, d2P; legendre(m, z, P, dP, d2P);
+    x[i] = z; w[i] = 2.0 / ((1.0 - z * z) * dP * dP);
+  }
+}
+
+// 1-D transfer matrices of a mortar: interpolation from order a to order b nodes
+// (rows: b nodes) and L2 projection from order M mortar nodes to order Ne (rows: Ne nodes).
+struct Mortar1D {
+  std::vector<double> interp[8][8];  // interp[a][b][(b nodes) x (a+1)]
+  std::vector<double> proj[8][8];    // proj[M][Ne][(Ne+1) x (M+1)]
+  explicit Mortar1D(const std::vector<Basis>& B) {
+    for (int a = 1; a <= 7; ++a)
+      for (int b = 1; b <= 7; ++b) {
+        interp[a][b].assign((size_t)(b + 1) * (a + 1), 0.0);
+        for (int g = 0; g <= b; ++g)
+          for (int i = 0; i <= a; ++i) interp[a][b][(size_t)g * (a + 1) + i] = lagrange(B[a].xi, i, B[b].xi[g]);
+      }
+    for (int M = 1; M <= 7; ++M)
+      for (int Ne = 1; Ne <= M; ++Ne) {
+        std::vector<double> gx, gw;
+        gauss_legendre(M + 1, gx, gw);
+        const int pe = Ne + 1, pm = M + 1;
+        std::vector<double> Mm((size_t)pe * pe, 0.0), Bm((size_t)pe * pm, 0.0);
+        for (size_t q = 0; q < gx.size(); ++q) {
+          std::vector<double> le(pe), lm(pm);
+          for (int i = 0; i < pe; ++i) le[i] = lagrange(B[Ne].xi, i, gx[q]);
+          for (int i = 0; i < pm; ++i) lm[i] = lagrange(B[M].xi, i, gx[q]);
+          for (int i = 0; i < pe; ++i) {
+            for (int j = 0; j < pe; ++j) Mm[(size_t)i * pe + j] += gw[q] * le[i] * le[j];
+            for (int j = 0; j < pm; ++j) Bm[(size_t)i * pm + j] += gw[q] * le[i] * lm[j];
+          }
+        }
+        // proj = Mm^-1 Bm by Gauss-Jordan on the small symmetric positive mass matrix
+        std::vector<double> A = Mm, X = Bm;
+        for (int c = 0; c < pe; ++c) {
+          int piv = c;
+          for (int r = c + 1; r < pe; ++r)
+            if (std::fabs(A[(size_t)r * pe + c]) > std::fabs(A[(size_t)piv * pe + c])) piv = r;
+          for (int j = 0; j < pe; ++j) std::swap(A[(size_t)c * pe + j], A[(size_t)piv * pe + j]);
+          for (int j = 0; j < pm; ++j) std::swap(X[(size_t)c * pm + j], X[(size_t)piv * pm + j]);
+          const double d = A[(size_t)c * pe + c];
+          for (int j = 0; j < pe; ++j) A[(size_t)c * pe + j] /= d;
+          for (int j = 0; j < pm; ++j) X[(size_t)c * pm + j] /= d;
+          for (int r = 0; r < pe; ++r) {
+            if (r == c) continue;
+            const double f = A[(size_t)r * pe + c];
+            for (int j = 0; j < pe; ++j) A[(size_t)r * pe + j] -= f * A[(size_t)c * pe + j];
+            for (int j = 0; j < pm; ++j) X[(size_t)r * pm + j] -= f * X[(size_t)c * pm + j];
+          }
+        }
+        proj[M][Ne] = X;
+      }
+  }
+};
+
+// out[a][b] = sum_{i,j} T[a][i] T[b][j] in[i][j] for nc components per point
+// (T rows: ro, cols: ci).
+template <class T>
+void tensor2(const std::vector<double>& Tm, int ro, int ci, const T* in, T* out, int nc) {
+  std::vector<T> tmp((size_t)ro * ci * nc, T(0.0));
+  for (int a = 0; a < ro; ++a)
+    for (int i = 0; i < ci; ++i) {
+      const double t = Tm[(size_t)a * ci + i];
+      if (t == 0.0) continue;
+      for (int j = 0; j < ci; ++j)
+        for (int k = 0; k < nc; ++k) tmp[((size_t)a * ci + j) * nc + k] += t * in[((size_t)i * ci + j) * nc + k];
+    }
+  for (size_t x = 0; x < (size_t)ro * ro * nc; ++x) out[x] = T(0.0);
+  for (int b = 0; b < ro; ++b)
+    for (int j = 0; j < ci; ++j) {
+      const double t = Tm[(size_t)b * ci + j];
+      if (t == 0.0) continue;
+      for (int a = 0; a < ro; ++a)
+        for (int k = 0; k < nc; ++k) out[((size_t)a * ro + b) * nc + k] += t * tmp[((size_t)a * ci + j) * nc + k];
+    }
+}
+
+// Face values of element e on face (d, s): the state (5) and, with g, the lifted gradient
+// (15) at its face nodes [fb + p fc], fb / fc the in-face indices along (d+1)%3, (d+2)%3.
+template <class T, class A>
+void face_values(const MDisc& D, const A& acc, int e, int d, int s, const T* g, T* q, T* gf) {
+  const int p = D.p(e), N = D.ord[e], db = (d + 1) % 3, dc = (d + 2) % 3;
+  for (int fc = 0; fc < p; ++fc)
+    for (int fb = 0; fb < p; ++fb) {
+      int c[3]; c[d] = s > 0 ? N : 0; c[db] = fb; c[dc] = fc;
+      const int m = D.node(e, c[0], c[1], c[2]);
+      for (int k = 0; k < NV; ++k) q[((size_t)fc * p + fb) * NV + k] = acc.get(e, m, k);
+      if (g && gf)
+        for (int x = 0; x < 3 * NV; ++x) gf[((size_t)fc * p + fb) * 3 * NV + x] = g[(size_t)m * 3 * NV + x];
+    }
+}
+
+// qhat (lifting) or fhat (with gradients) at element e's face nodes on face (d, s).
+template <class T, class A>
+void face_flux(const MDisc& D, const Mortar1D& Mo, const A& acc, int e, int d, int s,
+               const std::vector<std::vector<T>>* G, bool want_f, T* out /* p*p*NV */) {
+  const int nb = D.neighbor(e, d, s);
+  const int Ne = D.ord[e], Nn = D.ord[nb], pe = Ne + 1, pn = Nn + 1;
+  const bool mortar = Ne != Nn || D.force_mortar;
+  const int M = std::max(Ne, Nn), pm = M + 1;
+  std::vector<T> qp((size_t)pe * pe * NV), qm((size_t)pn * pn * NV);
+  std::vector<T> gp, gm;
+  if (want_f) { gp.resize((size_t)pe * pe * 3 * NV); gm.resize((size_t)pn * pn * 3 * NV); }
+  face_values<T>(D, acc, e, d, s, want_f ? (*G)[e].data() : nullptr, qp.data(), want_f ? gp.data() : nullptr);
+  face_values<T>(D, acc, nb, d, -s, want_f ? (*G)[nb].data() : nullptr, qm.data(), want_f ? gm.data() : nullptr);
+  // values on the mortar points (the element's own face nodes when conforming)
+  const int pt = mortar ? pm : pe;
+  std::vector<T> QP, QM, GP, GM;
+  if (mortar) {
+    QP.resize((size_t)pm * pm * NV); QM.resize((size_t)pm * pm * NV);
+    tensor2<T>(Mo.interp[Ne][M], pm, pe, qp.data(), QP.data(), NV);
+    tensor2<T>(Mo.interp[Nn][M], pm, pn, qm.data(), QM.data(), NV);
+    if (want_f) {
+      GP.resize((size_t)pm * pm * 3 * NV); GM.resize((size_t)pm * pm * 3 * NV);
+      tensor2<T>(Mo.interp[Ne][M], pm, pe, gp.data(), GP.data(), 3 * NV);
+      tensor2<T>(Mo.interp[Nn][M], pm, pn, gm.data(), GM.data(), 3 * NV);
+    }
+  } else {
+    QP = qp; QM = qm; GP = gp; GM = gm;
+  }
+  std::vector<T> F((size_t)pt * pt * NV);
+  for (int x = 0; x < pt * pt; ++x) {
+    const T* a = &QP[(size_t)x * NV];
+    const T* b = &QM[(size_t)x * NV];
+    if (!want_f) {
+      for (int k = 0; k < NV; ++k) F[(size_t)x * NV + k] = 0.5 * (a[k] + b[k]);
+    } else {
+      T fa[NV], fvp[NV], fvm[NV];
+      num_flux_adv(D.P, a, b, d, s, fa);
+      visc_flux(D.P, a, &GP[(size_t)x * 3 * NV], d, fvp);
+      visc_flux(D.P, b, &GM[(size_t)x * 3 * NV], d, fvm);
+      for (int k = 0; k < NV; ++k) F[(size_t)x * NV + k] = fa[k] - 0.5 * (double)s * (fvp[k] + fvm[k]);
+    }
+  }
+  if (mortar) tensor2<T>(Mo.proj[M][Ne], pe, pm, F.data(), out, NV);
+  else for (size_t x = 0; x < F.size(); ++x) out[x] = F[x];
+}
+
+// Lifted gradient of element e (as `lifting`, with the face qhat of face_flux).
+template <class T, class A>
+void mlifting(const MDisc& D, const Mortar1D& Mo, const A& acc, int e, T* g) {
+  const Basis& B = D.B[D.ord[e]];
+  const int p = D.p(e), nn = D.nn(e);
+  std::vector<T> qh[6];
+  for (int f = 0; f < 6; ++f) {
+    qh[f].resize((size_t)p * p * NV);
+    face_flux<T>(D, Mo, acc, e, f / 2, (f & 1) ? 1 : -1, nullptr, false, qh[f].data());
+  }
+  for (int m = 0; m < nn; ++m) {
+    int cm[3]; D.coords(e, m, cm);
+    T s3[3][NV];
+    for (int a = 0; a < 3; ++a) for (int k = 0; k < NV; ++k) s3[a][k] = T(0.0);
+    for (int nidx = 0; nidx < nn; ++nidx) {
+      int cn[3]; D.coords(e, nidx, cn);
+      const double wn = B.w[cn[0]] * B.w[cn[1]] * B.w[cn[2]];
+      const double e0 = B.ell[cm[0] * p + cn[0]], e1 = B.ell[cm[1] * p + cn[1]], e2 = B.ell[cm[2] * p + cn[2]];
+      const double d0 = B.dell[cm[0] * p + cn[0]], d1 = B.dell[cm[1] * p + cn[1]], d2 = B.dell[cm[2] * p + cn[2]];
+      const double gp[3] = {D.dx * d0 * e1 * e2, D.dx * e0 * d1 * e2, D.dx * e0 * e1 * d2};
+      for (int k = 0; k < NV; ++k) {
+        const T qn = acc.get(e, nidx, k);
+        for (int a = 0; a < 3; ++a)
+          if (gp[a] != 0.0) s3[a][k] -= (D.J * wn * gp[a]) * qn;
+      }
+    }
+    for (int d = 0; d < 3; ++d) {
+      const int db = (d + 1) % 3, dc = (d + 2) % 3;
+      for (int s = -1; s <= 1; s += 2) {
+        const double phin = ((s > 0) ? B.eR : B.eL)[cm[d]];
+        if (phin == 0.0) continue;
+        const int fb = cm[db], fc = cm[dc];
+        const double wf = B.w[fb] * B.w[fc];
+        const T* qhat = &qh[2 * d + (s > 0 ? 1 : 0)][((size_t)fc * p + fb) * NV];
+        for (int k = 0; k < NV; ++k) s3[d][k] += (D.Jf * wf * phin * (double)s) * qhat[k];
+      }
+    }
+    const double wm = B.w[cm[0]] * B.w[cm[1]] * B.w[cm[2]];
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < NV; ++k) g[((size_t)m * 3 + a) * NV + k] = s3[a][k] / (D.J * wm);
+  }
+}
+
+// Residual rows of element e (as elem_residual, with the face fhat of face_flux).
+template <class T, class A>
+void melem_residual(const MDisc& D, const Mortar1D& Mo, const A& acc, int e, const std::vector<std::vector<T>>& G,
+                    const double* Qs, const double* Qsm1, T* R) {
+  const Basis& B = D.B[D.ord[e]];
+  const int p = D.p(e), nn = D.nn(e);
+  const std::vector<T>& g = G[e];
+  std::vector<T> F((size_t)nn * 3 * NV);
+  for (int m = 0; m < nn; ++m) {
+    T q[NV];
+    for (int k = 0; k < NV; ++k) q[k] = acc.get(e, m, k);
+    for (int d = 0; d < 3; ++d) {
+      T fa[NV], fv[NV];
+      adv_flux(D.P, q, d, fa);
+      visc_flux(D.P, q, &g[(size_t)m * 3 * NV], d, fv);
+      for (int k = 0; k < NV; ++k) F[((size_t)m * 3 + d) * NV + k] = fa[k] - fv[k];
+    }
+  }
+  std::vector<T> fh[6];
+  for (int f = 0; f < 6; ++f) {
+    fh[f].resize((size_t)p * p * NV);
+    face_flux<T>(D, Mo, acc, e, f / 2, (f & 1) ? 1 : -1, &G, true, fh[f].data());
+  }
+  for (int j = 0; j < nn; ++j) {
+    int cj[3]; D.coords(e, j, cj);
+    const double wj = B.w[cj[0]] * B.w[cj[1]] * B.w[cj[2]];
+    T r[NV];
+    for (int k = 0; k < NV; ++k) r[k] = T(0.0);
+    if (D.P.with_time) {
+      for (int k = 0; k < NV; ++k) {
+        const size_t idx = ((size_t)D.off[e] + j) * NV + k;
+        const T qj = acc.get(e, j, k);
+        if (D.P.bdf == 2) r[k] = (D.J * wj / D.P.dt) * (1.5 * qj - 2.0 * Qs[idx] + 0.5 * Qsm1[idx]);
+        else r[k] = (D.J * wj / D.P.dt) * (qj - Qs[idx]);
+      }
+    }
+    for (int m = 0; m < nn; ++m) {
+      int cm[3]; D.coords(e, m, cm);
+      const double e0 = B.ell[cj[0] * p + cm[0]], e1 = B.ell[cj[1] * p + cm[1]], e2 = B.ell[cj[2] * p + cm[2]];
+      const double d0 = B.dell[cj[0] * p + cm[0]], d1 = B.dell[cj[1] * p + cm[1]], d2 = B.dell[cj[2] * p + cm[2]];
+      const double gp[3] = {D.dx * d0 * e1 * e2, D.dx * e0 * d1 * e2, D.dx * e0 * e1 * d2};
+      const double wm = B.w[cm[0]] * B.w[cm[1]] * B.w[cm[2]];
+      for (int d = 0; d < 3; ++d) {
+        if (gp[d] == 0.0) continue;
+        for (int k = 0; k < NV; ++k) r[k] -= (D.J * wm * gp[d]) * F[((size_t)m * 3 + d) * NV + k];
+      }
+    }
+    for (int d = 0; d < 3; ++d) {
+      const int db = (d + 1) % 3, dc = (d + 2) % 3;
+      for (int s = -1; s <= 1; s += 2) {
+        const double phin = ((s > 0) ? B.eR : B.eL)[cj[d]];
+        if (phin == 0.0) continue;
+        const int fb = cj[db], fc = cj[dc];
+        const double wf = B.w[fb] * B.w[fc];
+        const T* fhat = &fh[2 * d + (s > 0 ? 1 : 0)][((size_t)fc * p + fb) * NV];
+        for (int k = 0; k < NV; ++k) r[k] += (D.Jf * wf * phin) * fhat[k];
+      }
+    }
+    for (int k = 0; k < NV; ++k) R[(size_t)j * NV + k] = r[k];
+  }
+}
+
+// The whole residual of a mixed-order mesh in type T.
+template <class T, class A>
+void mresidual(const MDisc& D, const Mortar1D& Mo, const A& acc, const double* Qs, const double* Qsm1, T* R) {
+  std::vector<std::vector<T>> G(D.K);
+  for (int e = 0; e < D.K; ++e) {
+    G[e].resize((size_t)D.nn(e) * 3 * NV);
+    mlifting<T>(D, Mo, acc, e, G[e].data());
+  }
+  for (int e = 0; e < D.K; ++e) melem_residual<T>(D, Mo, acc, e, G, Qs, Qsm1, R + (size_t)D.off[e] * NV);
+}
+
+bool orders_ok(const or_params* P, const int* orders) {
+  const int K = P->n * P->n * P->n;
+  for (int e = 0; e < K; ++e)
+    if (orders[e] < 1 || orders[e] > 7) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Residual of a mixed-order mesh: Q, Qs, Qsm1, R are flat [sum_e (N_e+1)^3][5] (element by
+// element, nodes in natural order).  Returns 1 for an order outside 1..7.
+int or_residual_mixed(const or_params* P, const int* orders, int force_mortar, const double* Q, const double* Qs,
+                      const double* Qsm1, double* R) {
+  if (!orders_ok(P, orders)) return 1;
+  MDisc D(*P, orders, force_mortar);
+  Mortar1D Mo(D.B);
+  MAccess<double> acc{&D, Q};
+  mresidual<double>(D, Mo, acc, Qs, Qsm1 ? Qsm1 : Qs, R);
+  return 0;
+}
+
+// y = (dR/dQ) x on a mixed-order mesh (one-direction dual).
+int or_jvp_mixed(const or_params* P, const int* orders, int force_mortar, const double* Q, const double* x,
+                 double* y) {
+  if (!orders_ok(P, orders)) return 1;
+  MDisc D(*P, orders, force_mortar);
+  Mortar1D Mo(D.B);
+  using T = Dual<1>;
+  MAccess<T> acc{&D, Q}; acc.dir = x;
+  std::vector<T> R(D.nodes() * NV);
+  mresidual<T>(D, Mo, acc, Q, Q, R.data());
+  for (size_t i = 0; i < R.size(); ++i) y[i] = R[i].d[0];
+  return 0;
+}
+
+// Dense Jacobian of a mixed-order mesh, A[row][col] (dofs x dofs, row-major), column
+// node by column node with a five-direction dual (small meshes only).
+int or_jacobian_mixed(const or_params* P, const int* orders, int force_mortar, const double* Q, double* A) {
+  if (!orders_ok(P, orders)) return 1;
+  MDisc D(*P, orders, force_mortar);
+  Mortar1D Mo(D.B);
+  const size_t dofs = D.nodes() * NV;
+#pragma omp parallel for schedule(dynamic)
+  for (int c = 0; c < D.K; ++c) {
+    using T = Dual<5>;
+    std::vector<T> R(dofs);
+    for (int r = 0; r < D.nn(c); ++r) {
+      MAccess<T> acc{&D, Q}; acc.se = c; acc.sn = r;
+      mresidual<T>(D, Mo, acc, Q, Q, R.data());
+      const size_t col0 = ((size_t)D.off[c] + r) * NV;
+      for (size_t i = 0; i < dofs; ++i)
+        for (int k = 0; k < NV; ++k) A[i * dofs + col0 + k] = R[i].d[k];
+    }
+  }
+  return 0;
+}
+
+}  // extern "C"

@@ -141,6 +141,39 @@ def uniform_state(n: int, N: int, Ma: float = 0.1, vel=(1.0, 0.3, -0.2), gamma: 
     return np.ascontiguousarray(conserved_from_primitive(rho, u, v, w, p, gamma))
 
 
+def order_draw(seed: int, K: int) -> np.ndarray:
+    """Per-element polynomial orders N_e = 2 + (splitmix64(seed, e) mod 5), e = 0..K-1."""
+    return (2 + (splitmix64(seed, np.arange(K, dtype=np.uint64)) % np.uint64(5))).astype(np.int32)
+
+
+def node_coordinates_mixed(n: int, orders, L: float = 2.0 * np.pi) -> np.ndarray:
+    """Coordinates [sum_e (N_e+1)^3, 3] of every node of a mesh whose element e has order
+    orders[e], element by element (each block as node_coordinates gives it for its order)."""
+    orders = np.asarray(orders)
+    by_order = {int(N): node_coordinates(n, int(N), L) for N in np.unique(orders)}
+    return np.concatenate([by_order[int(N)][e] for e, N in enumerate(orders)])
+
+
+def tgv_state_mixed(n: int, orders, Ma: float = 0.1, seed: int = 0, eps: float = 1e-3,
+                    cfl: float = 50.0, gamma: float = 1.4):
+    """Perturbed Taylor-Green state on a mixed-order mesh, flat [sum_e (N_e+1)^3, 5], and
+    the CFL time step taken with the largest order (the finest node spacing)."""
+    xyz = node_coordinates_mixed(n, orders)
+    prim = taylor_green_primitive(xyz, Ma, gamma)
+    q = conserved_from_primitive(*prim, gamma=gamma)
+    dt = cfl_timestep(n, int(np.max(orders)), prim, cfl, gamma)
+    return np.ascontiguousarray(perturb(q, seed, eps)), dt
+
+
+def uniform_state_mixed(n: int, orders, Ma: float = 0.1, vel=(1.0, 0.3, -0.2), gamma: float = 1.4):
+    """Uniform free-stream state on a mixed-order mesh, flat [sum_e (N_e+1)^3, 5]."""
+    tot = int(sum((int(N) + 1) ** 3 for N in orders))
+    rho = np.ones(tot)
+    p = np.full(tot, 1.0 / (gamma * Ma * Ma))
+    u, v, w = (np.full(tot, c) for c in vel)
+    return np.ascontiguousarray(conserved_from_primitive(rho, u, v, w, p, gamma))
+
+
 # The five workloads, named by what they are.
 WORKLOADS = {
     "tgv_4x4x4_N3_cfl50": dict(n=4, N=3, Ma=0.1, Re=1600.0, cfl=50.0, seed=0),
