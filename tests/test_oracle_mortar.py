@@ -164,3 +164,24 @@ def test_mixed_orders_are_as_accurate_as_the_lower_order_and_converge_spectrally
         uniform[N] = _advection_l2_error(n, np.full(8, N))
         assert mixed[N] <= 1.05 * uniform[N], (N, mixed[N], uniform[N])
     assert mixed[5] < 0.1 * mixed[3] and mixed[6] < 0.1 * mixed[4], mixed
+
+
+def test_mortar_faces_take_the_own_block_out_of_the_gl_index_pattern():
+    # through interpolation and projection a face node's fluxes depend on every node of its
+    # face, and through the lifted gradients on the lines through them: the own block of an
+    # element with mortar faces leaves the conforming pattern (node pairs sharing a GL
+    # index), which a conforming mesh of the same order keeps
+    n = 2
+    Q, dt = I.tgv_state_mixed(n, ORDERS_2x2x2, eps=1e-2)
+    p = O.Params(n=n, N=3, dt=dt)
+    A = O.jacobian_mixed(p, ORDERS_2x2x2, Q)
+    N = int(ORDERS_2x2x2[0])
+    q = N + 1
+    c = np.array([(m % q, (m // q) % q, m // (q * q)) for m in range(q ** 3)])
+    share = (c[:, None, :] == c[None, :, :]).any(axis=2)
+    blk = A[:5 * q ** 3, :5 * q ** 3].reshape(q ** 3, 5, q ** 3, 5)
+    assert ((blk != 0).any(axis=(1, 3)) & ~share).any()
+    Qc, dtc = I.tgv_state(n, N, eps=1e-2)
+    Ac = O.jacobian_mixed(O.Params(n=n, N=N, dt=dtc), np.full(8, N), Qc.reshape(-1, 5))
+    bc = Ac[:5 * q ** 3, :5 * q ** 3].reshape(q ** 3, 5, q ** 3, 5)
+    assert not ((bc != 0).any(axis=(1, 3)) & ~share).any()
