@@ -1027,13 +1027,17 @@ void melem_residual(const MDisc& D, const Mortar1D& Mo, const A& acc, int e, con
 }
 
 // The whole residual of a mixed-order mesh in type T.
+// (Element loops in parallel: every iteration writes its own element's arrays; inside
+// the column loop of or_jacobian_mixed the nested regions run on one thread.)
 template <class T, class A>
 void mresidual(const MDisc& D, const Mortar1D& Mo, const A& acc, const double* Qs, const double* Qsm1, T* R) {
   std::vector<std::vector<T>> G(D.K);
+#pragma omp parallel for schedule(dynamic)
   for (int e = 0; e < D.K; ++e) {
     G[e].resize((size_t)D.nn(e) * 3 * NV);
     mlifting<T>(D, Mo, acc, e, G[e].data());
   }
+#pragma omp parallel for schedule(dynamic)
   for (int e = 0; e < D.K; ++e) melem_residual<T>(D, Mo, acc, e, G, Qs, Qsm1, R + (size_t)D.off[e] * NV);
 }
 

@@ -185,3 +185,16 @@ def test_mortar_faces_take_the_own_block_out_of_the_gl_index_pattern():
     Ac = O.jacobian_mixed(O.Params(n=n, N=N, dt=dtc), np.full(8, N), Qc.reshape(-1, 5))
     bc = Ac[:5 * q ** 3, :5 * q ** 3].reshape(q ** 3, 5, q ** 3, 5)
     assert not ((bc != 0).any(axis=(1, 3)) & ~share).any()
+
+
+def test_the_uneven_order_workload_mesh_preserves_free_stream_and_conserves():
+    # the 12^3 mesh with orders drawn from 2..6 (seed 1) at full size
+    n = 12
+    orders = I.order_draw(1, n ** 3)
+    Q = I.uniform_state_mixed(n, orders)
+    p = O.Params(n=n, N=6, with_time=False)
+    R = O.residual_mixed(p, orders, Q)
+    assert np.abs(R).max() < 1e-11 * np.abs(Q).max()
+    Q, dt = I.tgv_state_mixed(n, orders, eps=1e-2)
+    R = O.residual_mixed(p, orders, Q)
+    assert np.all(np.abs(R.sum(0)) < 1e-12 * np.abs(R).max() * R.shape[0] ** 0.5)
