@@ -118,6 +118,8 @@ def lib():
         L.or_residual_mixed.argtypes = [P, ip, ctypes.c_int, dp, dp, dp, dp]
         L.or_jvp_mixed.argtypes = [P, ip, ctypes.c_int, dp, dp, dp]
         L.or_jacobian_mixed.argtypes = [P, ip, ctypes.c_int, dp, dp]
+        L.or_jacobian_mixed_coo.argtypes = [P, ip, ctypes.c_int, dp, ctypes.c_long, ip, ip, dp]
+        L.or_jacobian_mixed_coo.restype = ctypes.c_long
         _lib = L
     return _lib
 
@@ -217,8 +219,8 @@ def phys_flux(p: Params, q, g, d: int):
 
 
 from .linalg import (  # noqa: E402
-    boundary_interior_split, condensed_operator, condensed_solve, global_solve, gmres,
-    ratio_formula,
+    MixedCondensedSystem, boundary_interior_split, boundary_interior_split_mixed, condensed_operator,
+    condensed_solve, condensed_solve_mixed, global_solve, gmres, ratio_formula,
 )
 
 
@@ -269,5 +271,27 @@ def jacobian_mixed(p: Params, orders, Q, force_mortar: bool = False) -> np.ndarr
     A = np.zeros((dofs, dofs))
     if lib().or_jacobian_mixed(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), _dp(A)) != 0:
         raise ValueError("orders must lie in 1..7")
+    return A
+
+
+def jacobian_mixed_sparse(p: Params, orders, Q, force_mortar: bool = False):
+    """dR/dQ on a mixed-order mesh as a scipy CSR matrix (flat ragged dof order)."""
+    import scipy.sparse as sp
+    o = _orders(p, orders)
+    Q = _f64(Q)
+    dofs = mixed_nodes(o) * 5
+    ne_max = 5 * (int(o.max()) + 1) ** 3
+    cap = int(dofs * min(27 * ne_max, dofs) * 0.3) + 1024
+    while True:
+        rows = np.zeros(cap, np.int32); cols = np.zeros(cap, np.int32); vals = np.zeros(cap)
+        nnz = lib().or_jacobian_mixed_coo(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), cap,
+                                          _ip(rows), _ip(cols), _dp(vals))
+        if nnz < 0:
+            raise ValueError("orders must lie in 1..7")
+        if nnz <= cap:
+            break
+        cap = int(nnz)
+    A = sp.csr_matrix((vals[:nnz], (rows[:nnz], cols[:nnz])), shape=(dofs, dofs))
+    A.sum_duplicates()
     return A
 

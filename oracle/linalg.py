@@ -219,3 +219,110 @@ def condensed_solve(A, Bvec: np.ndarray, n: int, N: int, method: str = "direct",
                           tol=0.0, atol=tol * bnorm, maxiter=maxiter)
         info.update(ginfo)
     return cs.back_substitute(Bvec, xb), info
+
+
+# ---- meshes of mixed order: element blocks of uneven sizes --------------------------
+
+def boundary_interior_split_mixed(orders):
+    """Per element, the global dof indices of its interior and boundary nodes (flat
+    ragged order, element by element; a node (i, j, k) of an order-N element is interior
+    when 0 < i, j, k < N).  Returns (I_list, B_list)."""
+    I_list, B_list, off = [], [], 0
+    for N in orders:
+        N = int(N)
+        p = N + 1
+        idx = np.arange(p ** 3)
+        i, j, k = idx % p, (idx // p) % p, idx // (p * p)
+        inner = (i > 0) & (i < N) & (j > 0) & (j < N) & (k > 0) & (k < N)
+        dof = lambda nodes: ((off + nodes[:, None]) * 5 + np.arange(5)[None, :]).reshape(-1)
+        I_list.append(dof(idx[inner]))
+        B_list.append(dof(idx[~inner]))
+        off += p ** 3
+    return I_list, B_list
+
+
+class MixedCondensedSystem:
+    """The condensed system of a mixed-order mesh (same algebra as CondensedSystem, with
+    element blocks of uneven sizes): S = A_bb - A_bi A_ii^{-1} A_ib, one dense LU per A_ii."""
+
+    def __init__(self, A, orders):
+        self.I_list, self.B_list = boundary_interior_split_mixed(orders)
+        If, Bf = np.concatenate(self.I_list), np.concatenate(self.B_list)
+        self.If, self.Bf = If, Bf
+        A = sp.csr_matrix(A)
+        self.A_ii = A[If][:, If].tocsr()
+        self.A_ib = A[If][:, Bf].tocsr()
+        self.A_bi = A[Bf][:, If].tocsr()
+        self.A_bb = A[Bf][:, Bf].tocsr()
+        self.isz = [len(x) for x in self.I_list]
+        self.bsz = [len(x) for x in self.B_list]
+        self.ioff = np.concatenate([[0], np.cumsum(self.isz)])
+        self.boff = np.concatenate([[0], np.cumsum(self.bsz)])
+        coo = self.A_ii.tocoo()
+        blk = np.searchsorted(self.ioff, np.arange(len(If)), side="right") - 1
+        self.aii_offblock_nnz = int(np.count_nonzero(blk[coo.row] != blk[coo.col]))
+        self.blocks = [sla.lu_factor(self.A_ii[a:b, a:b].toarray()) if b > a else None
+                       for a, b in zip(self.ioff[:-1], self.ioff[1:])]
+
+    def aii_solve(self, v):
+        out = np.empty_like(v)
+        for e, (a, b) in enumerate(zip(self.ioff[:-1], self.ioff[1:])):
+            if b > a:
+                out[a:b] = sla.lu_solve(self.blocks[e], v[a:b])
+        return out
+
+    def matvec(self, xb):
+        return self.A_bb @ xb - self.A_bi @ self.aii_solve(self.A_ib @ xb)
+
+    def rhs(self, Bvec):
+        return Bvec[self.Bf] - self.A_bi @ self.aii_solve(Bvec[self.If])
+
+    def back_substitute(self, Bvec, xb):
+        x = np.zeros(Bvec.size)
+        x[self.If] = self.aii_solve(Bvec[self.If] - self.A_ib @ xb)
+        x[self.Bf] = xb
+        return x
+
+    def dense_S(self):
+        Y = np.zeros((len(self.If), len(self.Bf)))
+        Aib = self.A_ib.toarray()
+        for e, (a, b) in enumerate(zip(self.ioff[:-1], self.ioff[1:])):
+            if b > a:
+                Y[a:b] = sla.lu_solve(self.blocks[e], Aib[a:b])
+        return self.A_bb.toarray() - self.A_bi @ Y
+
+    def block_jacobi(self):
+        """z = blockdiag(S_ee)^{-1} v with every element's own Schur block."""
+        facs = []
+        for e in range(len(self.bsz)):
+            rb = slice(self.boff[e], self.boff[e + 1])
+            ri = slice(self.ioff[e], self.ioff[e + 1])
+            Abb = self.A_bb[rb, rb].toarray()
+            if self.isz[e]:
+                Y = sla.lu_solve(self.blocks[e], self.A_ib[ri, rb].toarray())
+                Abb = Abb - self.A_bi[rb, ri].toarray() @ Y
+            facs.append(sla.lu_factor(Abb))
+
+        def apply(v):
+            out = np.empty_like(v)
+            for e in range(len(self.bsz)):
+                rb = slice(self.boff[e], self.boff[e + 1])
+                out[rb] = sla.lu_solve(facs[e], v[rb])
+            return out
+        return apply
+
+
+def condensed_solve_mixed(A, Bvec: np.ndarray, orders, method: str = "direct", tol: float = 1e-10,
+                          restart: int = 30, maxiter: int = 2000):
+    """condensed_solve on a mixed-order mesh."""
+    cs = MixedCondensedSystem(A, orders)
+    g = cs.rhs(Bvec)
+    info = {"aii_offblock_nnz": cs.aii_offblock_nnz}
+    if method == "direct":
+        xb = np.linalg.solve(cs.dense_S(), g)
+    else:
+        bnorm = np.linalg.norm(Bvec)
+        xb, ginfo = gmres(cs.matvec, g, precond=cs.block_jacobi(), restart=restart,
+                          tol=0.0, atol=tol * bnorm, maxiter=maxiter)
+        info.update(ginfo)
+    return cs.back_substitute(Bvec, xb), info

@@ -1078,6 +1078,88 @@ int or_jvp_mixed(const or_params* P, const int* orders, int force_mortar, const 
   return 0;
 }
 
+// Sparse Jacobian of a mixed-order mesh in COO form (global dof rows / columns, flat
+// ragged order).  For each column node only the rows of the 3x3x3 block of elements
+// around it are evaluated: the seed changes the lifted gradients of its own element and
+// of its face neighbours only, and the other gradients those rows read are the base
+// ones.  Returns the number of non-zeros; nothing beyond cap is written.
+long or_jacobian_mixed_coo(const or_params* P, const int* orders, int force_mortar, const double* Q, long cap,
+                           int* rows, int* cols, double* vals) {
+  if (!orders_ok(P, orders)) return -1;
+  MDisc D(*P, orders, force_mortar);
+  Mortar1D Mo(D.B);
+  std::vector<std::vector<double>> G0(D.K);
+  {
+    MAccess<double> acc0{&D, Q};
+#pragma omp parallel for schedule(dynamic)
+    for (int e = 0; e < D.K; ++e) {
+      G0[e].resize((size_t)D.nn(e) * 3 * NV);
+      mlifting<double>(D, Mo, acc0, e, G0[e].data());
+    }
+  }
+  std::vector<std::vector<long>> R_(D.K), C_(D.K);
+  std::vector<std::vector<double>> V_(D.K);
+#pragma omp parallel for schedule(dynamic)
+  for (int c = 0; c < D.K; ++c) {
+    using T = Dual<5>;
+    // rows: the distinct elements of the 3x3x3 block around c
+    std::vector<int> nbh;
+    const int cx = c % D.n, cy = (c / D.n) % D.n, cz = c / (D.n * D.n);
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dxx = -1; dxx <= 1; ++dxx) {
+          const int x = D.elem(cx + dxx, cy + dy, cz + dz);
+          if (std::find(nbh.begin(), nbh.end(), x) == nbh.end()) nbh.push_back(x);
+        }
+    // gradients those rows read: their elements and face neighbours
+    std::vector<int> ring = nbh;
+    for (int e : nbh)
+      for (int f = 0; f < 6; ++f) {
+        const int x = D.neighbor(e, f / 2, (f & 1) ? 1 : -1);
+        if (std::find(ring.begin(), ring.end(), x) == ring.end()) ring.push_back(x);
+      }
+    std::vector<int> seeded(1, c);
+    for (int f = 0; f < 6; ++f) {
+      const int x = D.neighbor(c, f / 2, (f & 1) ? 1 : -1);
+      if (std::find(seeded.begin(), seeded.end(), x) == seeded.end()) seeded.push_back(x);
+    }
+    std::vector<std::vector<T>> G(D.K);
+    for (int x : ring) G[x].resize((size_t)D.nn(x) * 3 * NV);
+    std::vector<T> Rb;
+    for (int r = 0; r < D.nn(c); ++r) {
+      MAccess<T> acc{&D, Q}; acc.se = c; acc.sn = r;
+      for (int x : ring) {
+        if (std::find(seeded.begin(), seeded.end(), x) != seeded.end()) {
+          mlifting<T>(D, Mo, acc, x, G[x].data());
+        } else {
+          for (size_t i = 0; i < G[x].size(); ++i) G[x][i] = T(G0[x][i]);
+        }
+      }
+      const long col0 = ((long)D.off[c] + r) * NV;
+      for (int e : nbh) {
+        Rb.assign((size_t)D.nn(e) * NV, T(0.0));
+        melem_residual<T>(D, Mo, acc, e, G, Q, Q, Rb.data());
+        for (int j = 0; j < D.nn(e); ++j)
+          for (int v = 0; v < NV; ++v)
+            for (int k = 0; k < NV; ++k) {
+              const double a = Rb[(size_t)j * NV + v].d[k];
+              if (a == 0.0) continue;
+              R_[c].push_back(((long)D.off[e] + j) * NV + v);
+              C_[c].push_back(col0 + k);
+              V_[c].push_back(a);
+            }
+      }
+    }
+  }
+  long total = 0;
+  for (int c = 0; c < D.K; ++c)
+    for (size_t i = 0; i < R_[c].size(); ++i) {
+      if (total < cap) { rows[total] = (int)R_[c][i]; cols[total] = (int)C_[c][i]; vals[total] = V_[c][i]; }
+      ++total;
+    }
+  return total;
+}
+
 // Dense Jacobian of a mixed-order mesh, A[row][col] (dofs x dofs, row-major), column
 // node by column node with a five-direction dual (small meshes only).
 int or_jacobian_mixed(const or_params* P, const int* orders, int force_mortar, const double* Q, double* A) {

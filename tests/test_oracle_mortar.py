@@ -198,3 +198,35 @@ def test_the_uneven_order_workload_mesh_preserves_free_stream_and_conserves():
     Q, dt = I.tgv_state_mixed(n, orders, eps=1e-2)
     R = O.residual_mixed(p, orders, Q)
     assert np.all(np.abs(R.sum(0)) < 1e-12 * np.abs(R).max() * R.shape[0] ** 0.5)
+
+
+def test_sparse_mixed_jacobian_equals_the_dense_one_and_the_product():
+    n = 2
+    Q, dt = I.tgv_state_mixed(n, ORDERS_2x2x2, eps=1e-2)
+    p = O.Params(n=n, N=3, dt=dt)
+    assert np.abs(O.jacobian_mixed_sparse(p, ORDERS_2x2x2, Q).toarray()
+                  - O.jacobian_mixed(p, ORDERS_2x2x2, Q)).max() == 0.0
+    n = 3
+    orders = np.array([2, 3, 4, 3, 2, 4, 2, 3, 4] * 3)
+    Q, dt = I.tgv_state_mixed(n, orders, eps=1e-2)
+    p = O.Params(n=n, N=4, dt=dt)
+    A = O.jacobian_mixed_sparse(p, orders, Q)
+    x = np.random.default_rng(9).standard_normal(Q.shape)
+    y = O.jvp_mixed(p, orders, Q, x).reshape(-1)
+    assert np.abs(A @ x.reshape(-1) - y).max() < 1e-12 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("method", ["direct", "gmres"])
+def test_mixed_condensed_solve_equals_the_global_solve(method):
+    # condensation with element blocks of uneven sizes on a 3^3 mesh of orders 2..4
+    n = 3
+    orders = np.array([2, 3, 4, 3, 2, 4, 2, 3, 4] * 3)
+    Q, dt = I.tgv_state_mixed(n, orders, cfl=10.0)
+    p = O.Params(n=n, N=4, dt=dt)
+    A = O.jacobian_mixed_sparse(p, orders, Q)
+    B = -O.residual_mixed(p, orders, Q).reshape(-1)
+    xg = np.linalg.solve(A.toarray(), B)  # dense: sparse LU fills in heavily here
+    xc, info = O.condensed_solve_mixed(A, B, orders, method=method, tol=1e-12, restart=60, maxiter=3000)
+    assert info["aii_offblock_nnz"] == 0
+    assert np.linalg.norm(xc - xg) / np.linalg.norm(xg) < 1e-9
+    assert np.linalg.norm(B - A @ xc) / np.linalg.norm(B) < 1e-11
