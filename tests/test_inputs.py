@@ -30,3 +30,27 @@ def test_lobatto_points_are_symmetric():
         x = I.lobatto_points(N)
         np.testing.assert_allclose(x, -x[::-1], atol=0)
         assert x[0] == -1.0 and x[-1] == 1.0
+
+
+def test_mixed_order_inputs_reduce_to_the_uniform_ones():
+    # one order everywhere: same nodes, same state, same perturbation counters, same dt
+    n, N = 3, 3
+    orders = np.full(n ** 3, N)
+    np.testing.assert_array_equal(I.node_coordinates_mixed(n, orders), I.node_coordinates(n, N).reshape(-1, 3))
+    Qm, dtm = I.tgv_state_mixed(n, orders, seed=4)
+    Q, dt = I.tgv_state(n, N, seed=4)
+    np.testing.assert_array_equal(Qm, Q.reshape(-1, 5))
+    assert dtm == dt
+    np.testing.assert_array_equal(I.uniform_state_mixed(n, orders), I.uniform_state(n, N).reshape(-1, 5))
+
+
+def test_mixed_order_coordinates_follow_each_elements_order():
+    n = 2
+    orders = np.array([2, 3, 4, 5, 6, 2, 3, 4])
+    xyz = I.node_coordinates_mixed(n, orders)
+    assert xyz.shape == (sum((N + 1) ** 3 for N in orders), 3)
+    off = 0
+    for e, N in enumerate(orders):
+        blk = xyz[off:off + (N + 1) ** 3]
+        np.testing.assert_array_equal(blk, I.node_coordinates(n, int(N))[e])
+        off += (N + 1) ** 3
