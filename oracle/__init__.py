@@ -120,6 +120,7 @@ def lib():
         L.or_jacobian_mixed.argtypes = [P, ip, ctypes.c_int, dp, dp]
         L.or_jacobian_mixed_coo.argtypes = [P, ip, ctypes.c_int, dp, ctypes.c_long, ip, ip, dp]
         L.or_jacobian_mixed_coo.restype = ctypes.c_long
+        L.or_jacobian_mixed_elem_rows.argtypes = [P, ip, ctypes.c_int, dp, ctypes.c_int, ip, dp]
         _lib = L
     return _lib
 
@@ -294,4 +295,26 @@ def jacobian_mixed_sparse(p: Params, orders, Q, force_mortar: bool = False):
     A = sp.csr_matrix((vals[:nnz], (rows[:nnz], cols[:nnz])), shape=(dofs, dofs))
     A.sum_duplicates()
     return A
+
+
+def jacobian_mixed_element_rows(p: Params, orders, Q, e: int, force_mortar: bool = False):
+    """Rows of element e on a mixed-order mesh: {column element c: dense block
+    [(N_e+1)^3 5, (N_c+1)^3 5]} over the 3x3x3 block of elements around e."""
+    o = _orders(p, orders)
+    Q = _f64(Q)
+    ne = lambda x: 5 * (int(o[x]) + 1) ** 3
+    elems = np.zeros(27, np.int32)
+    total = ne(e) * 27 * 5 * (int(o.max()) + 1) ** 3
+    blocks = np.zeros(total)
+    cnt = lib().or_jacobian_mixed_elem_rows(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), int(e),
+                                            _ip(elems), _dp(blocks))
+    if cnt < 0:
+        raise ValueError("orders must lie in 1..7")
+    out, off = {}, 0
+    for i in range(cnt):
+        c = int(elems[i])
+        size = ne(e) * ne(c)
+        out[c] = blocks[off:off + size].reshape(ne(e), ne(c)).copy()
+        off += size
+    return out
 

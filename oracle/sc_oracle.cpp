@@ -1160,6 +1160,66 @@ long or_jacobian_mixed_coo(const or_params* P, const int* orders, int force_mort
   return total;
 }
 
+// Rows of element e only (mixed orders): for each distinct element c of the 3x3x3 block
+// around e, the dense block dR_e/dQ_c ((N_e+1)^3 5 x (N_c+1)^3 5, row-major), written one
+// after the other into blocks; col_elems receives the elements.  Returns their number.
+int or_jacobian_mixed_elem_rows(const or_params* P, const int* orders, int force_mortar, const double* Q, int e,
+                                int* col_elems, double* blocks) {
+  if (!orders_ok(P, orders)) return -1;
+  MDisc D(*P, orders, force_mortar);
+  Mortar1D Mo(D.B);
+  std::vector<int> nbh;
+  const int ex = e % D.n, ey = (e / D.n) % D.n, ez = e / (D.n * D.n);
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dxx = -1; dxx <= 1; ++dxx) {
+        const int x = D.elem(ex + dxx, ey + dy, ez + dz);
+        if (std::find(nbh.begin(), nbh.end(), x) == nbh.end()) nbh.push_back(x);
+      }
+  // gradients row e reads: e and its face neighbours
+  std::vector<int> need(1, e);
+  for (int f = 0; f < 6; ++f) {
+    const int x = D.neighbor(e, f / 2, (f & 1) ? 1 : -1);
+    if (std::find(need.begin(), need.end(), x) == need.end()) need.push_back(x);
+  }
+  std::vector<std::vector<double>> G0(D.K);
+  {
+    MAccess<double> acc0{&D, Q};
+    for (int x : need) {
+      G0[x].resize((size_t)D.nn(x) * 3 * NV);
+      mlifting<double>(D, Mo, acc0, x, G0[x].data());
+    }
+  }
+  std::vector<size_t> boff(nbh.size() + 1, 0);
+  const size_t rows_e = (size_t)D.nn(e) * NV;
+  for (size_t i = 0; i < nbh.size(); ++i) boff[i + 1] = boff[i] + rows_e * (size_t)D.nn(nbh[i]) * NV;
+#pragma omp parallel for schedule(dynamic)
+  for (int i = 0; i < (int)nbh.size(); ++i) {
+    using T = Dual<5>;
+    const int c = nbh[i];
+    col_elems[i] = c;
+    double* blk = blocks + boff[i];
+    const size_t cols = (size_t)D.nn(c) * NV;
+    std::vector<std::vector<T>> G(D.K);
+    for (int x : need) G[x].resize((size_t)D.nn(x) * 3 * NV);
+    std::vector<T> Rb(rows_e);
+    for (int r = 0; r < D.nn(c); ++r) {
+      MAccess<T> acc{&D, Q}; acc.se = c; acc.sn = r;
+      for (int x : need) {
+        // the seed reaches the gradient of x only if c is x or one of its face neighbours
+        bool touched = x == c;
+        for (int f = 0; f < 6 && !touched; ++f) touched = D.neighbor(x, f / 2, (f & 1) ? 1 : -1) == c;
+        if (touched) mlifting<T>(D, Mo, acc, x, G[x].data());
+        else for (size_t t = 0; t < G[x].size(); ++t) G[x][t] = T(G0[x][t]);
+      }
+      melem_residual<T>(D, Mo, acc, e, G, Q, Q, Rb.data());
+      for (size_t row = 0; row < rows_e; ++row)
+        for (int k = 0; k < NV; ++k) blk[row * cols + (size_t)r * NV + k] = Rb[row].d[k];
+    }
+  }
+  return (int)nbh.size();
+}
+
 // Dense Jacobian of a mixed-order mesh, A[row][col] (dofs x dofs, row-major), column
 // node by column node with a five-direction dual (small meshes only).
 int or_jacobian_mixed(const or_params* P, const int* orders, int force_mortar, const double* Q, double* A) {

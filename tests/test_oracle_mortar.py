@@ -230,3 +230,18 @@ def test_mixed_condensed_solve_equals_the_global_solve(method):
     assert info["aii_offblock_nnz"] == 0
     assert np.linalg.norm(xc - xg) / np.linalg.norm(xg) < 1e-9
     assert np.linalg.norm(B - A @ xc) / np.linalg.norm(B) < 1e-11
+
+
+def test_mixed_element_rows_equal_the_sparse_jacobian():
+    n = 3
+    orders = np.array([2, 3, 4, 3, 2, 4, 2, 3, 4] * 3)
+    Q, dt = I.tgv_state_mixed(n, orders, eps=1e-2)
+    p = O.Params(n=n, N=4, dt=dt)
+    A = O.jacobian_mixed_sparse(p, orders, Q).tocsr()
+    off = np.concatenate([[0], np.cumsum([5 * (int(N) + 1) ** 3 for N in orders])])
+    for e in (0, 13, 26):
+        rows = O.jacobian_mixed_element_rows(p, orders, Q, e)
+        assert len(rows) == 27
+        for c, blk in rows.items():
+            ref = A[off[e]:off[e + 1], off[c]:off[c + 1]].toarray()
+            assert np.abs(blk - ref).max() <= 1e-14 * np.abs(A.data).max(), (e, c)
