@@ -180,4 +180,6 @@ WORKLOADS = {
     "tgv_16x16x16_N4_cfl50": dict(n=16, N=4, Ma=0.1, Re=1600.0, cfl=50.0, seed=0),
     "tgv_16x16x16_N5_cfl50": dict(n=16, N=5, Ma=0.1, Re=1600.0, cfl=50.0, seed=0),
     "tgv_16x16x16_N6_cfl100": dict(n=16, N=6, Ma=0.1, Re=1600.0, cfl=100.0, seed=0),
+    # orders N_e = 2 + (splitmix64(1, e) mod 5): order_draw(order_seed, n^3), tgv_state_mixed
+    "tgv_12x12x12_N2to6_cfl50": dict(n=12, N=None, order_seed=1, Ma=0.1, Re=1600.0, cfl=50.0, seed=0),
 }
