@@ -37,3 +37,27 @@ def test_library_loads_without_gpu_and_binding_matches():
     for f in declared_functions():
         assert hasattr(L, f)
     assert set(sc.EXPORTS) <= set(declared_functions())
+
+
+def test_default_config_values():
+    from paper_1911_02366_gb300 import sc
+    cfg = sc.default_config()
+    assert (cfg.gmres_restart, cfg.gmres_max_iters, cfg.rel_tol, cfg.inner_tol) == (30, 4000, 1e-8, 1e-4)
+    assert (cfg.precision, cfg.precond, cfg.tensor_cores) == (sc.SC_PREC_FP64, sc.SC_PC_BLOCK_JACOBI, 1)
+    assert (cfg.outer_krylov, cfg.inner_iters, cfg.factor_fp16, cfg.explicit_schur) == (0, 0, 0, 0)
+    assert (cfg.gamma, cfg.Pr, cfg.Re, cfg.Ma) == (1.4, 0.72, 1600.0, 0.1)
+
+
+def test_create_rejects_invalid_configs_before_any_cuda_call():
+    # argument checks come first, so they answer SC_ERR_ARG without a GPU
+    import ctypes
+    from paper_1911_02366_gb300 import sc
+    bad = [dict(gmres_restart=0), dict(gmres_restart=401), dict(gmres_max_iters=0), dict(rel_tol=0.0),
+           dict(Re=0.0), dict(Ma=-1.0), dict(gamma=1.0), dict(Pr=0.0), dict(precision=7),
+           dict(outer_krylov=31), dict(outer_krylov=-1), dict(inner_iters=-1)]
+    L = sc.lib()
+    for kw in bad:
+        cfg = sc.default_config(**kw)
+        h = ctypes.c_void_p()
+        assert L.sc_create(ctypes.byref(cfg), None, ctypes.byref(h)) == sc.SC_ERR_ARG, kw
+        assert not h.value
