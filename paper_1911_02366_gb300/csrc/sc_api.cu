@@ -962,16 +962,20 @@ sc_status sc_kernel_work(const sc_ctx* c, int kernel_id, double* flops, double* 
   // matrices of the condensed solve are stored in FP32 by the mixed arm
   const double w = c->cfg.precision == SC_PREC_MIXED ? 4.0 : 8.0;
   double pairs = (double)c->pat.row.size();
+  // neighbour node pairs on interior / boundary rows (the pattern is the same for every element)
+  double pairs_i = 0.0;
+  for (int r : c->pat.row) pairs_i += c->perm[r] < G.nin ? 1.0 : 0.0;
+  const double pairs_b = pairs - pairs_i;
   const double K = G.K, ni = G.ni, nb = G.nb, ne = G.ne, lda = G.lda, ldi = G.ldi, lds = G.lds, cb0 = G.cb0;
   double f = 0.0, b = 0.0;
   switch (kernel_id) {
-    case SCK_COND_INTERIOR:  // A_ib,ee x_b (structural nonzeros), then A_ii^-1 t; couplings run in their own pass
-      f = K * (2.0 * (double)c->pk_nnz_int + 2.0 * ni * ni);
-      b = K * (w * ((double)c->pk_nnz_int + ni * ldi) + w * nb + 8.0 * ni);
+    case SCK_COND_INTERIOR:  // A_ib,ee x_b and the couplings of interior rows (structural nonzeros), then A_ii^-1 t
+      f = K * (2.0 * (double)c->pk_nnz_int + 50.0 * pairs_i + 2.0 * ni * ni);
+      b = K * (w * ((double)c->pk_nnz_int + 25.0 * pairs_i + ni * ldi) + w * nb + 8.0 * ni);
       break;
-    case SCK_COND_BOUNDARY:  // [A_bi A_bb] [-u; x_b] (structural nonzeros)
-      f = K * 2.0 * (double)c->pk_nnz_bnd;
-      b = K * (w * (double)c->pk_nnz_bnd + w * (ni + nb) + 8.0 * nb);
+    case SCK_COND_BOUNDARY:  // [A_bi A_bb] [-u; x_b] and the couplings of boundary rows (structural nonzeros)
+      f = K * (2.0 * (double)c->pk_nnz_bnd + 50.0 * pairs_b);
+      b = K * (w * ((double)c->pk_nnz_bnd + 25.0 * pairs_b) + w * (ni + nb) + 8.0 * nb);
       break;
     case SCK_LU_SOLVE: {  // forward + backward substitution with the S_ee factors (FP16 when stored so)
       const double wf = c->ls16_ok ? 2.0 : w;
