@@ -189,19 +189,25 @@ sc_status sc_newton_step(sc_ctx* ctx, int max_newton, double newton_tol, sc_solv
    natural order, then variable).  Device pointers.  Test hook. */
 sc_status sc_condensed_matvec(sc_ctx* ctx, const double* xb, double* yb);
 
-/* Same result as sc_condensed_matvec, but the call allocates nothing: the interior
-   vector that links the two passes is kept in a fixed 8 MiB device array compiled into
-   the library (1,048,576 doubles, held on every GPU that loads the library until the
-   process exits) instead of context-owned memory.  The paper has no counterpart; it
-   is for callers that must not allocate device memory at the point of the call, e.g.
-   a solver loop running under a memory pool or an allocator that forbids
-   cudaMalloc/cudaFree once the simulation is running.  Needs K * (interior dofs per
-   element) <= 1,048,576 (N = 4: up to 7,767 elements); larger meshes get SC_ERR_ARG
-   with a message.  The first call on each device looks up the array's device address
-   with that device current (make it before any stream capture); later calls only
-   launch kernels.  Every call shares the one array: calls whose work overlaps on the
-   GPU (other streams, other contexts, other threads) race and must be serialised by
-   the caller.  The array keeps the last call's contents, which no call reads.
+/* Same result as sc_condensed_matvec (the same operator passes, FP64 or mixed arm), but
+   the call allocates nothing: the vectors that link the passes (the interior vector, and
+   on the mixed arm the FP32 copy of xb) are kept in a fixed 8 MiB device array compiled
+   into the library (held on every GPU that loads the library until the process exits)
+   instead of context-owned memory.  The paper has no counterpart.  It is for callers that
+   must not allocate device memory at the point of the call, e.g. a solver loop running
+   under a memory pool or an allocator that forbids cudaMalloc/cudaFree once the
+   simulation is running.
+   Limit: the FP64 arm needs 8 K ni bytes (K * interior dofs per element <= 1,048,576;
+   N = 4: up to 7,767 elements), the mixed arm 4 K (nb + ni) bytes (<= 2,097,152 floats;
+   N = 4: up to 3,355 elements; explicit operator: 4 K nb bytes).  Larger meshes get
+   SC_ERR_ARG with a message (checked once the mesh is set, before the condensed state).
+   Every call looks up the array's device address with the current device (which must be
+   the context's); the first call on a device may load the library's device code, so make
+   it before any stream capture.  The call only enqueues work on the context's stream and
+   returns without synchronising it.  Every call shares the one array: calls whose work
+   overlaps on the GPU (other streams, other contexts, other threads) race and must be
+   serialised by the caller.  The array keeps the last call's contents, which no call
+   reads (each pass writes what the next one reads).
    xb, yb: device pointers as in sc_condensed_matvec. */
 sc_status sc_condensed_matvec_static(sc_ctx* ctx, const double* xb, double* yb);
 
@@ -221,6 +227,29 @@ sc_status sc_sizes(const sc_ctx* ctx, int* K, int* ne, int* ni, int* nb);
 sc_status sc_gemm_tf32(int batch, int M, int N, int K, float alpha, const float* A, long long strideA, int lda,
                        int transA, const float* B, long long strideB, int ldb, int transB, float beta, float* C,
                        long long strideC, int ldc, void* cuda_stream);
+
+/* ---- Spectrum and condition-number estimate (Sec. 4, Fig. ConditionNumber) ------
+   The paper approximates the L2 condition number of the global and of the condensed
+   matrix by the ratio of the largest to the smallest eigenvalue modulus, both found by
+   shift-and-invert Arnoldi.  sc_spectrum_estimate does the same on the assembled system:
+   which = 0 for the global Jacobian A, 1 for the condensed matrix S.  The eigenvalue of
+   largest modulus is the largest-modulus Ritz value of m_max Arnoldi steps (classical
+   Gram-Schmidt twice) on the matrix; the eigenvalue of smallest modulus is the inverse of
+   the largest-modulus Ritz value of m_min Arnoldi steps on the inverse (shift 0), each
+   inverse applied by a condensed GMRES solve to relative tolerance inv_tol (A^-1: condensed
+   right-hand side, GMRES on S, back-substitution; S^-1: GMRES on S).  Both start from the
+   same fixed pseudo-random vector.  out[6] = {Re, Im of the largest, Re, Im of the
+   smallest eigenvalue, |largest| / |smallest|, total inner GMRES iterations}.  FP64 arm,
+   after sc_condense (SC_ERR_STATE otherwise); 1 <= m_max, m_min <= gmres_restart.  The
+   call allocates (m + 1) vectors of the operator's size for the Arnoldi basis and frees
+   them before it returns. */
+sc_status sc_spectrum_estimate(sc_ctx* ctx, int which, int m_max, int m_min, double inv_tol, double* out);
+
+/* Eigenvalues of an m x m upper Hessenberg matrix H (row-major, host) by the shifted QR
+   algorithm in complex arithmetic, the step sc_spectrum_estimate applies to its Arnoldi
+   matrices: re[m], im[m] (host).  Host-only; SC_ERR_NOT_CONVERGED if QR does not
+   converge. */
+sc_status sc_hessenberg_eigvals(int m, const double* H, double* re, double* im);
 
 /* ---- Learned correction of the block-Jacobi preconditioner ----------------------
    Not in the paper (which preconditions GMRES on the condensed system with point Jacobi,

@@ -12,8 +12,8 @@ Layers:
   * ``oracle/linalg.py``: the static condensation of Sec. 2.2 / 3.2 (eqs. StaticCondBlock,
     SC_step1, SC_step2) and a right-preconditioned restarted GMRES, on numpy/scipy.
 
-Parity status of each function is recorded in the design doc (all pinned by tests in
-``tests/test_oracle_*.py``).
+Every function is pinned by tests in ``tests/test_oracle_*.py`` against closed forms,
+invariants and brute-force solves.
 """
 from __future__ import annotations
 

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <set>
@@ -1016,6 +1017,214 @@ sc_status sc_kernel_work(const sc_ctx* c, int kernel_id, double* flops, double* 
   }
   *flops = f; *bytes = b;
   return SC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Spectrum estimate of the global and the condensed matrices (Sec. 4, Fig.
+// ConditionNumber): the L2 condition number approximated by the ratio of the largest and
+// the smallest eigenvalue moduli, the largest from Arnoldi on the matrix, the smallest
+// from Arnoldi on its inverse (shift-and-invert with shift 0), each inverse applied by a
+// condensed GMRES solve.
+// ---------------------------------------------------------------------------------
+namespace {
+using cplx = std::complex<double>;
+
+// Eigenvalues of an upper Hessenberg matrix (row-major m x m) by the shifted QR algorithm
+// in complex arithmetic: Wilkinson shift from the trailing 2 x 2 block of the active
+// window (an exceptional shift every tenth sweep), one Givens rotation per subdiagonal
+// entry, deflation when a subdiagonal entry falls below eps times its diagonal
+// neighbours.  Returns false if one eigenvalue needs more than 200 sweeps.
+bool hessenberg_eigvals(int m, const double* Hin, std::vector<cplx>& ev) {
+  std::vector<cplx> H((size_t)m * m);
+  double hnorm = 0.0;
+  for (size_t i = 0; i < (size_t)m * m; ++i) { H[i] = Hin[i]; hnorm = std::max(hnorm, std::fabs(Hin[i])); }
+  ev.assign(m, cplx(0.0));
+  const double eps = 2.220446049250313e-16;
+  auto at = [&](int i, int j) -> cplx& { return H[(size_t)i * m + j]; };
+  int hi = m - 1, iter = 0;
+  std::vector<double> cs(m);
+  std::vector<cplx> sn(m);
+  while (hi >= 0) {
+    if (hi == 0) { ev[0] = at(0, 0); break; }
+    int l = hi;
+    while (l > 0) {
+      double s = std::abs(at(l - 1, l - 1)) + std::abs(at(l, l));
+      if (s == 0.0) s = hnorm;
+      if (std::abs(at(l, l - 1)) <= eps * s) { at(l, l - 1) = 0.0; break; }
+      --l;
+    }
+    if (l == hi) { ev[hi] = at(hi, hi); --hi; iter = 0; continue; }
+    if (++iter > 200) return false;
+    const cplx a = at(hi - 1, hi - 1), b = at(hi - 1, hi), cc = at(hi, hi - 1), d = at(hi, hi);
+    const cplx tr = a + d, det = a * d - b * cc;
+    const cplx disc = std::sqrt(tr * tr * 0.25 - det);
+    const cplx mu1 = tr * 0.5 + disc, mu2 = tr * 0.5 - disc;
+    cplx mu = std::abs(mu1 - d) < std::abs(mu2 - d) ? mu1 : mu2;
+    if (iter % 10 == 0) mu = d + cplx(std::abs(cc), 0.0);
+    for (int k = l; k <= hi; ++k) at(k, k) -= mu;
+    // H - mu I = Q R by Givens rotations G_k acting on rows k, k+1 ...
+    for (int k = l; k < hi; ++k) {
+      const cplx x = at(k, k), y = at(k + 1, k);
+      const double ax = std::abs(x), r = std::hypot(ax, std::abs(y));
+      double c = 1.0;
+      cplx sv = 0.0;
+      if (r > 0.0) {
+        if (ax == 0.0) { c = 0.0; sv = 1.0; }
+        else { c = ax / r; sv = (x / ax) * std::conj(y) / r; }
+      }
+      for (int j = k; j <= hi; ++j) {
+        const cplx t1 = at(k, j), t2 = at(k + 1, j);
+        at(k, j) = c * t1 + sv * t2;
+        at(k + 1, j) = -std::conj(sv) * t1 + c * t2;
+      }
+      cs[k] = c; sn[k] = sv;
+    }
+    // ... then R Q + mu I: the adjoint rotations from the right on columns k, k+1
+    for (int k = l; k < hi; ++k) {
+      const double c = cs[k];
+      const cplx sv = sn[k];
+      const int iend = std::min(k + 2, hi);
+      for (int i = l; i <= iend; ++i) {
+        const cplx t1 = at(i, k), t2 = at(i, k + 1);
+        at(i, k) = c * t1 + std::conj(sv) * t2;
+        at(i, k + 1) = -sv * t1 + c * t2;
+      }
+    }
+    for (int k = l; k <= hi; ++k) at(k, k) += mu;
+  }
+  return true;
+}
+
+// m steps of Arnoldi (classical Gram-Schmidt applied twice) on the operator op over
+// vectors of length n, from a fixed pseudo-random start vector; the Ritz values (the
+// eigenvalues of the m x m Hessenberg matrix) in ritz.  V holds (m + 1) n doubles, w n.
+template <class Op>
+sc_status arnoldi_ritz(sc_ctx* c, size_t n, int m, Op op, double* V, double* w, std::vector<cplx>& ritz,
+                       int* steps) {
+  const int ma = c->restart_alloc;
+  double* const h1 = c->Hd;
+  double* const h2 = c->Hd + (ma + 1);
+  double* const hn2 = c->Hd + 2 * (ma + 1);
+  double* const hs = c->Hd + 2 * (ma + 1) + 2;
+  {
+    std::vector<double> v0(n);
+    uint64_t z = 0x2545F4914F6CDD1DULL;
+    for (size_t i = 0; i < n; ++i) {  // xorshift64*: a fixed, well-spread start vector
+      z ^= z >> 12; z ^= z << 25; z ^= z >> 27;
+      v0[i] = (double)((z * 0x2545F4914F6CDD1DULL) >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    SC_CUDA(cudaMemcpyAsync(V, v0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const double nv = dnorm2(c, V, n, hs);
+    SC_CUDA(sc::vec_axpby(c, V, 1.0 / nv, V, 0.0, n));
+  }
+  std::vector<double> H((size_t)m * m, 0.0), hbuf(2 * (ma + 1) + 1);
+  int k = 0;
+  for (int j = 0; j < m; ++j) {
+    sc_status s = op(V + (size_t)j * n, w);
+    if (s != SC_OK) return s;
+    SC_CUDA(sc::multidot(c, V, j + 1, n, w, h1));
+    SC_CUDA(sc::vec_update(c, w, V, j + 1, n, h1, -1.0));
+    SC_CUDA(sc::multidot(c, V, j + 1, n, w, h2));
+    SC_CUDA(sc::vec_update(c, w, V, j + 1, n, h2, -1.0));
+    SC_CUDA(sc::multidot(c, w, 1, n, w, hn2));
+    SC_CUDA(cudaMemcpyAsync(hbuf.data(), c->Hd, (2 * (ma + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+    SC_CUDA(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hbuf[i] + hbuf[(ma + 1) + i];
+    const double hn = std::sqrt(std::max(hbuf[2 * (ma + 1)], 0.0));
+    if (!std::isfinite(hn)) return fail(c, SC_ERR_NONFINITE, "non-finite value in the Arnoldi process");
+    k = j + 1;
+    if (j + 1 < m) H[(size_t)(j + 1) * m + j] = hn;
+    if (hn == 0.0) break;  // invariant subspace: its Ritz values are exact
+    SC_CUDA(sc::vec_axpby(c, V + (size_t)(j + 1) * n, 1.0 / hn, w, 0.0, n));
+  }
+  std::vector<double> Hk((size_t)k * k);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) Hk[(size_t)i * k + j] = H[(size_t)i * m + j];
+  if (!hessenberg_eigvals(k, Hk.data(), ritz)) return fail(c, SC_ERR_NOT_CONVERGED, "Hessenberg QR did not converge");
+  *steps = k;
+  return SC_OK;
+}
+
+cplx largest_modulus(const std::vector<cplx>& v) {
+  cplx best = 0.0;
+  for (const cplx& z : v) if (std::abs(z) > std::abs(best)) best = z;
+  return best;
+}
+}  // namespace
+
+extern "C" {
+
+sc_status sc_hessenberg_eigvals(int m, const double* H, double* re, double* im) {
+  if (m < 1 || !H || !re || !im) return SC_ERR_ARG;
+  std::vector<cplx> ev;
+  if (!hessenberg_eigvals(m, H, ev)) return SC_ERR_NOT_CONVERGED;
+  for (int i = 0; i < m; ++i) { re[i] = ev[i].real(); im[i] = ev[i].imag(); }
+  return SC_OK;
+}
+
+sc_status sc_spectrum_estimate(sc_ctx* c, int which, int m_max, int m_min, double inv_tol, double* out) {
+  if (!c || !out || (which != 0 && which != 1)) return SC_ERR_ARG;
+  if (m_max < 1 || m_min < 1 || m_max > c->restart_alloc || m_min > c->restart_alloc || !(inv_tol > 0.0))
+    return fail(c, SC_ERR_ARG, "spectrum: need 1 <= m_max, m_min <= gmres_restart and inv_tol > 0");
+  if (!c->condensed) return fail(c, SC_ERR_STATE, "spectrum estimate before condense");
+  if (c->cfg.precision != SC_PREC_FP64)
+    return fail(c, SC_ERR_STATE, "spectrum estimate: needs the FP64 arm (its operators and solves are exact to FP64)");
+  const Geo& G = c->G;
+  const size_t n = which == 0 ? (size_t)G.K * G.ne : (size_t)G.K * G.nb;
+  double *V = nullptr, *w = nullptr;
+  cudaError_t e = cudaMalloc((void**)&V, (size_t)(std::max(m_max, m_min) + 1) * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&w, n * sizeof(double));
+  if (e != cudaSuccess) {
+    if (V) cudaFree(V);
+    cudaGetLastError();
+    return fail(c, SC_ERR_OOM, "spectrum estimate: Arnoldi basis does not fit");
+  }
+  struct Free { double *a, *b; ~Free() { cudaFree(a); cudaFree(b); } } guard{V, w};
+  const size_t n1 = (size_t)G.K * G.nb;
+  double* const hs = c->Hd + 2 * (c->restart_alloc + 1) + 2;
+  long long inner = 0;
+  auto fwd = [&](const double* x, double* y) -> sc_status {
+    if (which == 0) {
+      SC_CUDA(sc::global_apply(c, x, y));
+    } else {
+      SC_CUDA(sc::cond_interior(c, x, 1.0, nullptr, 0.0, c->Ui));
+      SC_CUDA(sc::cond_boundary(c, x, 1.0, nullptr, 0.0, c->Ui, y));
+    }
+    return SC_OK;
+  };
+  auto inv = [&](const double* x, double* y) -> sc_status {
+    int it = 0;
+    double resid = 0.0, gnorm = 0.0;
+    sc_status s;
+    if (which == 0) {  // y = A^-1 x by condensation: condensed rhs, GMRES on S, back-substitution
+      s = condensed_solve(c, x, y, inv_tol, 0.0, c->cfg.gmres_max_iters, &it, &resid, &gnorm);
+    } else {           // y = S^-1 x by GMRES on S
+      SC_CUDA(cudaMemcpyAsync(c->Gb, x, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      const double xn = dnorm2(c, c->Gb, n1, hs);
+      s = gmres_condensed(c, inv_tol * xn, c->cfg.gmres_max_iters, &it, &resid);
+      if (s == SC_OK) SC_CUDA(cudaMemcpyAsync(y, c->Xb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    inner += it;
+    return s;
+  };
+  std::vector<cplx> ritz;
+  int steps = 0;
+  sc_status s = arnoldi_ritz(c, n, m_max, fwd, V, w, ritz, &steps);
+  if (s != SC_OK) return s;
+  const cplx lmax = largest_modulus(ritz);
+  s = arnoldi_ritz(c, n, m_min, inv, V, w, ritz, &steps);
+  if (s != SC_OK) return s;
+  const cplx th = largest_modulus(ritz);
+  if (std::abs(th) == 0.0) return fail(c, SC_ERR_NONFINITE, "spectrum estimate: zero Ritz value of the inverse");
+  const cplx lmin = 1.0 / th;
+  out[0] = lmax.real(); out[1] = lmax.imag();
+  out[2] = lmin.real(); out[3] = lmin.imag();
+  out[4] = std::abs(lmax) / std::abs(lmin);
+  out[5] = (double)inner;
+  return check(c);
 }
 
 }  // extern "C"

@@ -480,81 +480,83 @@ cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b,
 // ---------------------------------------------------------------------------------
 // Allocation-free condensed operator.
 //
-// sc_condensed_matvec_static applies S exactly like sc_condensed_matvec, but the
-// interior vector u = A_ii^-1 A_ib x_b that links the two passes lives in the static
+// sc_condensed_matvec_static applies S with the same operator passes as
+// sc_condensed_matvec, but the vectors that link its passes (the interior vector
+// u = A_ii^-1 A_ib x_b, and on the mixed arm also the FP32 copy of x_b) live in the static
 // device array below instead of context-owned memory, so the call itself never
-// allocates.  The array holds 8 MiB (1,048,576 doubles) on every GPU that loads this
-// library, for the life of the process; a call needs K * ni doubles of it.
+// allocates.  The array holds 8 MiB on every GPU that loads this library, for the life
+// of the process.
 // ---------------------------------------------------------------------------------
-#include <mutex>
-
 namespace {
-constexpr size_t kStaticScratchDoubles = (size_t(8) << 20) / sizeof(double);
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;
 }  // namespace
 
-static __device__ __align__(256) double g_condensed_scratch[kStaticScratchDoubles];
+static __device__ __align__(256) unsigned char g_condensed_scratch[kStaticScratchBytes];
 
 namespace {
-std::mutex g_scratch_mutex;
-double* g_scratch_addr[64] = {};
-
-// Device address of the scratch array on the current device, looked up once per device
-// (cudaGetSymbolAddress with that device current) and cached.
-cudaError_t static_scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+// Device address of the scratch array on the current device.  Looked up on every call
+// with that device current: the lookup allocates nothing, and it stays valid across a
+// cudaDeviceReset, which reloads the module at a possibly different address.
+cudaError_t static_scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_condensed_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_condensed_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 }  // namespace
 
 extern "C" sc_status sc_condensed_matvec_static(sc_ctx* c, const double* xb, double* yb) {
   if (!c || !xb || !yb) return SC_ERR_ARG;
+  if (!c->has_mesh) {
+    c->err = "condensed_matvec_static before set_mesh";
+    return SC_ERR_STATE;
+  }
   const Geo& G = c->G;
+  const bool mixed = c->cfg.precision == SC_PREC_MIXED;
+  const bool expl = mixed && c->cfg.explicit_schur;
+  const size_t n1 = (size_t)G.K * G.nb, nint = (size_t)G.K * G.ni;
+  // FP64 arm: u in doubles; mixed arm: the FP32 copy of x_b (aligned to 256 bytes), then u
+  // in floats (the explicit operator needs no u)
+  const size_t xf_bytes = mixed ? ((n1 * sizeof(float) + 255) & ~size_t(255)) : 0;
+  const size_t need = mixed ? xf_bytes + (expl ? 0 : nint * sizeof(float)) : nint * sizeof(double);
+  if (need > kStaticScratchBytes) {
+    c->err = "condensed_matvec_static: this mesh needs " + std::to_string(need) +
+             " bytes of scratch (FP64 arm: 8 x elements x interior dofs; mixed arm: 4 x elements x"
+             " (boundary + interior dofs)), more than the " + std::to_string(kStaticScratchBytes) +
+             " bytes of the static buffer; use sc_condensed_matvec";
+    return SC_ERR_ARG;
+  }
   if (!c->condensed) {
     c->err = "condensed_matvec_static before condense";
     return SC_ERR_STATE;
   }
-  const size_t need = (size_t)G.K * G.ni;
-  if (need > kStaticScratchDoubles) {
-    c->err = "condensed_matvec_static: this mesh needs " + std::to_string(need) +
-             " doubles of interior scratch (elements x interior dofs), more than the " +
-             std::to_string(kStaticScratchDoubles) + " of the static buffer; use sc_condensed_matvec";
-    return SC_ERR_ARG;
-  }
-  double* u = nullptr;
-  cudaError_t e = static_scratch_address(&u);
+  unsigned char* scratch = nullptr;
+  cudaError_t e = static_scratch_address(&scratch);
   if (e != cudaSuccess) {
     c->err = std::string("condensed_matvec_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
     return SC_ERR_CUDA;
   }
-  // The interior pass writes every entry of u before the boundary pass reads it, so
-  // nothing left over from an earlier call is ever read.
-  if (c->cfg.precision != SC_PREC_FP64) {
-    c->err = "condensed_matvec_static: needs a context created with SC_PREC_FP64";
-    return SC_ERR_STATE;
+  // Every pass writes the entries it later reads (x_b's FP32 copy, then u) before reading
+  // them, so nothing left in the array by an earlier call is ever read.
+  if (mixed) {
+    float* xf = reinterpret_cast<float*>(scratch);
+    float* uf = reinterpret_cast<float*>(scratch + xf_bytes);
+    e = sc::vec_to_float(c, xf, xb, n1);
+    if (e == cudaSuccess) {
+      if (expl) {
+        e = sc::explicit_matvec32(c, xf, yb);
+      } else {
+        e = sc::cond_interior32(c, xf, 1.0, nullptr, 0.0, uf);
+        if (e == cudaSuccess) e = sc::cond_boundary32(c, xf, 1.0, nullptr, 0.0, uf, yb);
+      }
+    }
+  } else {
+    double* u = reinterpret_cast<double*>(scratch);
+    e = sc::cond_interior(c, xb, 1.0, nullptr, 0.0, u);
+    if (e == cudaSuccess) e = sc::cond_boundary(c, xb, 1.0, nullptr, 0.0, u, yb);
   }
-  if (G.ni > 0) {
-    count_launch(c);
-    k_cond_interior<double><<<G.K, 256, (size_t)(((G.nb + 3) & ~3) + G.ldi) * sizeof(double), c->stream>>>(
-        G, c->Aown, c->X, c->Ainv, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0, u,
-        nullptr);
-  }
-  count_launch(c);
-  k_cond_boundary<double><<<G.K, 256, (size_t)G.lda * sizeof(double), c->stream>>>(
-      G, c->Aown, c->X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm, xb, 1.0, nullptr, 0.0,
-      G.ni ? u : nullptr, yb, nullptr);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     c->err = std::string("condensed_matvec_static: ") + cudaGetErrorString(e);
     return SC_ERR_CUDA;

@@ -56,7 +56,8 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_condensed_matvec_static", "sc_gemm_tf32", "sc_mlp_forward", "sc_mlp_backward", "sc_mlp_loss",
            "sc_mlp_adam", "sc_learned_features", "sc_learned_targets", "sc_set_learned_weights", "sc_set_learned_correction",
            "sc_get_state", "sc_condensed_rhs", "sc_backsubstitute", "sc_newton_step", "sc_batch_create",
-           "sc_batch_condense", "sc_batch_tiles", "sc_batch_destroy"]
+           "sc_batch_condense", "sc_batch_tiles", "sc_batch_destroy", "sc_spectrum_estimate",
+           "sc_hessenberg_eigvals"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -114,6 +115,8 @@ def lib(build_if_missing: bool = True):
     L.sc_batch_tiles.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip]
     L.sc_batch_destroy.argtypes = [vp]; L.sc_batch_destroy.restype = None
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
+    L.sc_spectrum_estimate.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+    L.sc_hessenberg_eigvals.argtypes = [ctypes.c_int, dp, dp, dp]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
     L.sc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
@@ -302,13 +305,32 @@ class Context:
         """Replace the per-node corrections by scale * Ck ([K*nbn, 25] float32 device)."""
         self._check(self._L.sc_set_learned_correction(self.h, Ck.data_ptr(), ctypes.c_float(scale)))
 
+    def sc_spectrum_estimate(self, which: str = "S", m_max: int = 30, m_min: int = 30, inv_tol: float = 1e-12):
+        """Largest and smallest eigenvalues of A ('A') or S ('S') and their modulus ratio."""
+        out = np.zeros(6)
+        self._check(self._L.sc_spectrum_estimate(self.h, {"A": 0, "S": 1}[which], m_max, m_min, inv_tol,
+                                                 out.ctypes.data))
+        return {"lam_max": complex(out[0], out[1]), "lam_min": complex(out[2], out[3]), "cond": out[4],
+                "inner_iters": int(out[5])}
+
     def sc_condensed_matvec_static(self, xb, yb):
-        """S x_b without any allocation in the call (fixed 8 MiB device scratch)."""
+        """S x_b without any allocation in the call (fixed 8 MiB device scratch); enqueues only."""
         (px, dx), (py, dy) = _ptr(xb), _ptr(yb)
         if not (dx and dy):
             raise ValueError("condensed_matvec_static takes device tensors")
         self._check(self._L.sc_condensed_matvec_static(self.h, px, py))
         return yb
+
+
+def sc_hessenberg_eigvals(H: np.ndarray) -> np.ndarray:
+    """Eigenvalues of an upper Hessenberg matrix (host routine of the spectrum estimate)."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    m = H.shape[0]
+    re, im = np.zeros(m), np.zeros(m)
+    s = lib().sc_hessenberg_eigvals(m, H.ctypes.data, re.ctypes.data, im.ctypes.data)
+    if s != SC_OK:
+        raise SCError(s, "Hessenberg QR failed")
+    return re + 1j * im
 
 
 def sc_gemm_tf32(A, B, C, alpha=1.0, beta=0.0, stream=None, trans_a=False, trans_b=False):

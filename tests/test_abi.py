@@ -61,3 +61,21 @@ def test_create_rejects_invalid_configs_before_any_cuda_call():
         h = ctypes.c_void_p()
         assert L.sc_create(ctypes.byref(cfg), None, ctypes.byref(h)) == sc.SC_ERR_ARG, kw
         assert not h.value
+
+
+def test_hessenberg_eigenvalues_match_numpy():
+    """Host QR step of the spectrum estimate (sc_hessenberg_eigvals), no GPU needed."""
+    import numpy as np
+    from paper_1911_02366_gb300 import sc
+    rng = np.random.default_rng(5)
+    for m in (1, 2, 7, 30, 60):
+        H = np.triu(rng.standard_normal((m, m)), -1)
+        got = sc.sc_hessenberg_eigvals(H)
+        ref = np.linalg.eigvals(H)
+        # each computed eigenvalue next to a reference one and vice versa (multisets match)
+        d = np.abs(got[:, None] - ref[None, :])
+        tol = 1e-9 * max(1.0, np.max(np.abs(ref)))
+        assert np.max(d.min(axis=1)) <= tol and np.max(d.min(axis=0)) <= tol, m
+    # a matrix with a known real spectrum and one with an exact zero subdiagonal
+    H = np.diag([5.0, -3.0, 1e-3, 2.0]) + np.diag([1.0, 0.0, 1.0], -1)
+    assert np.allclose(np.sort_complex(sc.sc_hessenberg_eigvals(H)), np.sort_complex(np.linalg.eigvals(H)))

@@ -4,6 +4,7 @@ its own sc_condense makes it, and solve to the same answer."""
 import numpy as np
 import pytest
 
+import oracle as O
 import sc_inputs as I
 from gpu_common import TWO_PI, gpu_context
 
@@ -13,9 +14,9 @@ pytestmark = pytest.mark.gpu
 ORDERS = [(3, 2), (3, 3), (2, 4), (1, 5), (1, 6)]  # (elements per direction, N)
 
 
-def _context(n, N):
+def _context(n, N, rel_tol=1e-8):
     from paper_1911_02366_gb300 import sc
-    ctx = gpu_context(precision=sc.SC_PREC_MIXED, rel_tol=1e-8, gmres_restart=60, gmres_max_iters=4000,
+    ctx = gpu_context(precision=sc.SC_PREC_MIXED, rel_tol=rel_tol, gmres_restart=60, gmres_max_iters=4000,
                       max_refine=20)
     ctx.sc_set_mesh(n, TWO_PI, N)
     return ctx
@@ -55,6 +56,27 @@ def test_batched_condensation_equals_each_systems_own(graph):
     for cidx in range(len(ORDERS)):
         ni, by, bs, bt = batch.tiles(cidx)
         assert ni in (5, 40, 135, 320, 625) and {by, bs, bt} <= {64, 144, 256}
+    batch.close()
+
+
+def test_batched_condensation_solves_match_oracle_global_solves():
+    """Every system of one graph-captured, autotuned batch over the orders N = 2..6 solves
+    to the oracle's global sparse-LU solution x = A^-1 B (Sec. 2.1, eq. NewtonLinSys1) within
+    the mixed arm's bound after FP64 refinement."""
+    from paper_1911_02366_gb300 import sc
+    ctxs = [_context(n, N, rel_tol=1e-12) for n, N in ORDERS]
+    batch = sc.Batch(ctxs)
+    Qs = [_load(c, n, N, 2) for c, (n, N) in zip(ctxs, ORDERS)]
+    batch.condense(graph=True, autotune=True)
+    for c, Q, (n, N) in zip(ctxs, Qs, ORDERS):
+        dQ, st = _solve(c, Q)
+        _, dt = I.tgv_state(n, N, cfl=10.0, seed=2)
+        p = O.Params(n=n, N=N, dt=dt)
+        A = O.jacobian(p, Q)
+        B = -O.residual(p, Q).reshape(-1)
+        x = O.global_solve(A, B)
+        assert np.linalg.norm(B - A @ dQ) / np.linalg.norm(B) < 1e-11, (N, st)
+        assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < 1e-9, (N, st)
     batch.close()
 
 

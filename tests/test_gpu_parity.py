@@ -107,6 +107,46 @@ def test_tgv_4x4x4_N3_cfl50_reaches_1e8():
     assert st["rel_residual"] < 1e-8
 
 
+@pytest.fixture(scope="module")
+def tgv_4x4x4_N3_cfl50_global():
+    """The 4^3, N = 3, CFL 50 Newton system (20,480 dofs) solved globally by the oracle's
+    sparse LU: the plain definition x = A^-1 B of the update (Sec. 2.1, eq. NewtonLinSys1)."""
+    n, N = 4, 3
+    Q, dt = I.tgv_state(n, N, cfl=50.0, seed=0)
+    p = O.Params(n=n, N=N, dt=dt)
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    return Q, A, B, O.global_solve(A, B)
+
+
+@pytest.mark.parametrize("arm", ["fp64", "mixed"])
+def test_tgv_4x4x4_N3_cfl50_condensed_equals_global_solve(arm, tgv_4x4x4_N3_cfl50_global):
+    """The 4^3, N = 3 workload solved globally and by condensation, with the results
+    compared (Sec. 2.2, eqs. SC_step1 and SC_step2): relative solution error <= 1e-10 on
+    the FP64 arm and <= 1e-8 after FP64 refinement on the mixed arm."""
+    from paper_1911_02366_gb300 import sc
+    Q, A, B, x = tgv_4x4x4_N3_cfl50_global
+    n, N = 4, 3
+    if arm == "fp64":
+        cfg = dict(rel_tol=1e-12, gmres_restart=300, gmres_max_iters=8000)
+        tol = 1e-10
+    else:
+        cfg = dict(precision=sc.SC_PREC_MIXED, rel_tol=1e-11, inner_tol=1e-4, gmres_restart=300,
+                   gmres_max_iters=8000, max_refine=30)
+        tol = 1e-8
+    _, dt, p, ctx = case(n, N, cfl=50.0, **cfg)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    dQ = np.zeros(Q.size)
+    # GMRES stops on the condensed residual; the FP64 global residual after
+    # back-substitution may sit a rounding step above rel_tol, so the status is not used
+    st = ctx.sc_solve(dQ, raise_on_not_converged=False)
+    err = np.linalg.norm(dQ - x) / np.linalg.norm(x)
+    assert err <= tol, (err, st)
+    assert np.linalg.norm(B - A @ dQ) / np.linalg.norm(B) <= 10 * cfg["rel_tol"], st
+
+
 @pytest.mark.parametrize("tc", [1, 0])
 @pytest.mark.parametrize("n,N,cfl", [(2, 3, 10.0), (3, 2, 10.0), (2, 4, 10.0)])
 def test_mixed_solve_matches_oracle_global_solve(n, N, cfl, tc):
