@@ -228,6 +228,41 @@ sc_status sc_gemm_tf32(int batch, int M, int N, int K, float alpha, const float*
                        int transA, const float* B, long long strideB, int ldb, int transB, float beta, float* C,
                        long long strideC, int ldc, void* cuda_stream);
 
+/* ---- Time marching to a steady state (Sec. 4, numerical example) ------------------
+   The paper drives its discretisation to a steady state, ||M^-1 H(Q)||_inf <= tol (M the
+   diagonal Gauss-Lobatto mass matrix, H the spatial operator of eq. DGSEMsystem), with an
+   explicit low-storage RK3 scheme and with BDF1 steps whose Newton-linearised systems reuse
+   one Jacobian, solved globally or by static condensation, and reports the convergence rate
+   eta = d log ||M^-1 H||_inf / d tau (tau the compute time; Table tab:Advantages2).  These
+   calls march the context's state Q in place (after sc_set_mesh and sc_set_state) and leave
+   the BDF1 history equal to the new state; any assembled Jacobian is invalidated. */
+
+/* ||M^-1 H(Q)||_inf of the current state (host double). */
+sc_status sc_steady_residual(sc_ctx* ctx, double* res_inf);
+
+/* nsteps steps of Williamson's low-storage third-order Runge-Kutta scheme
+   (A = 0, -5/9, -153/128; B = 1/3, 15/16, 8/15) on dQ/dt = -M^-1 H(Q).  Each step's dt is
+   adapted to the state on the device: dt = min(cfl (h/N) / max(|v| + c),
+   dfl (h/N)^2 / max(max(4/3, gamma/Pr) mu / (rho Re))) (dfl <= 0 drops the diffusive limit).
+   res_hist (host, nsteps + 1 or NULL): ||M^-1 H||_inf after 0..nsteps steps; dt_hist (host,
+   nsteps or NULL): the steps taken; ms_total: device milliseconds of the march.
+   SC_ERR_NONFINITE if the state blows up. */
+sc_status sc_explicit_march(sc_ctx* ctx, double cfl, double dfl, int nsteps, double* res_hist, double* dt_hist,
+                            double* ms_total);
+
+/* nsteps BDF1 steps of size dt, each one Newton-linearised solve
+   A dQ = -R(Q) = -H(Q) (eq. NeqtonEq at the step's start, where Q equals the history), solved
+   by sc_solve with the context's configuration (static condensation, FP64 or mixed arm),
+   Q <- Q + dQ.  The Jacobian is assembled and condensed at the first step and then every
+   jacobian_every steps (0 = once: the frozen Jacobian of the paper's experiment); the other
+   steps only evaluate the residual.  res_hist (host, nsteps + 1 or NULL):
+   ||M^-1 H||_inf at the start of each step and after the last; ms_hist (host, nsteps + 1 or
+   NULL): device milliseconds from the start to the end of each step (ms_hist[0] = 0);
+   gmres_iters (host, nsteps or NULL): GMRES iterations of each solve.  A solve that misses
+   rel_tol returns its status (SC_ERR_NOT_CONVERGED) and stops the march. */
+sc_status sc_implicit_march(sc_ctx* ctx, double dt, int nsteps, int jacobian_every, double* res_hist,
+                            double* ms_hist, int* gmres_iters);
+
 /* ---- Spectrum and condition-number estimate (Sec. 4, Fig. ConditionNumber) ------
    The paper approximates the L2 condition number of the global and of the condensed
    matrix by the ratio of the largest to the smallest eigenvalue modulus, both found by

@@ -442,15 +442,16 @@ inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / 
 
 namespace sc {
 
-cudaError_t launch_residual(sc_ctx* c) {
-  const Geo& G = c->G;
+cudaError_t launch_residual_geo(sc_ctx* c, const Geo& G, const double* Q, const double* Qh, double* out) {
   const size_t nodes = (size_t)G.K * G.nn;
   count_launch(c, 3);
-  k_lift<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, c->Q, c->d_nbr, c->grad);
-  k_flux<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, c->Q, c->grad, c->F);
-  k_resid<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, c->Q, c->Qh, c->grad, c->F, c->d_nbr, c->B);
+  k_lift<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, c->d_nbr, c->grad);
+  k_flux<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, c->grad, c->F);
+  k_resid<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, Qh, c->grad, c->F, c->d_nbr, out);
   return cudaGetLastError();
 }
+
+cudaError_t launch_residual(sc_ctx* c) { return launch_residual_geo(c, c->G, c->Q, c->Qh, c->B); }
 
 cudaError_t launch_history(sc_ctx* c, const double* Qs, const double* Qsm1) {
   const size_t n = (size_t)c->G.K * c->G.nn * 5;

@@ -360,6 +360,10 @@ constexpr int SC_EXPLICIT_PATTERN = (1 << 30) + 2;
 
 namespace sc {
 cudaError_t launch_residual(sc_ctx* c);
+// -R(Q) with the geometry G (c0 = 0 gives -H(Q), the spatial operator alone) into out;
+// uses c->grad and c->F as scratch.
+cudaError_t launch_residual_geo(sc_ctx* c, const Geo& G, const double* Q, const double* Qh, double* out);
+cudaError_t launch_history(sc_ctx* c, const double* Qs, const double* Qsm1);
 cudaError_t launch_assembly(sc_ctx* c);
 cudaError_t launch_condense(sc_ctx* c);
 cudaError_t cond_interior(sc_ctx* c, const double* xb, double beta, const double* Bfull, double alpha,

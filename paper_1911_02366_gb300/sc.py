@@ -57,7 +57,7 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_mlp_adam", "sc_learned_features", "sc_learned_targets", "sc_set_learned_weights", "sc_set_learned_correction",
            "sc_get_state", "sc_condensed_rhs", "sc_backsubstitute", "sc_newton_step", "sc_batch_create",
            "sc_batch_condense", "sc_batch_tiles", "sc_batch_destroy", "sc_spectrum_estimate",
-           "sc_hessenberg_eigvals"]
+           "sc_hessenberg_eigvals", "sc_steady_residual", "sc_explicit_march", "sc_implicit_march"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -117,6 +117,9 @@ def lib(build_if_missing: bool = True):
     L.sc_sizes.argtypes = [vp, ip, ip, ip, ip]
     L.sc_spectrum_estimate.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
     L.sc_hessenberg_eigvals.argtypes = [ctypes.c_int, dp, dp, dp]
+    L.sc_steady_residual.argtypes = [vp, dp]
+    L.sc_explicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]
+    L.sc_implicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
     L.sc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
@@ -312,6 +315,28 @@ class Context:
                                                  out.ctypes.data))
         return {"lam_max": complex(out[0], out[1]), "lam_min": complex(out[2], out[3]), "cond": out[4],
                 "inner_iters": int(out[5])}
+
+    def sc_steady_residual(self) -> float:
+        """||M^-1 H(Q)||_inf of the current state."""
+        r = np.zeros(1)
+        self._check(self._L.sc_steady_residual(self.h, r.ctypes.data))
+        return float(r[0])
+
+    def sc_explicit_march(self, cfl: float, nsteps: int, dfl: float = 0.0):
+        """Low-storage RK3 steps; returns (residual history, dt history, device ms)."""
+        res, dts, ms = np.zeros(nsteps + 1), np.zeros(max(nsteps, 1)), np.zeros(1)
+        self._check(self._L.sc_explicit_march(self.h, cfl, dfl, nsteps, res.ctypes.data, dts.ctypes.data,
+                                              ms.ctypes.data))
+        return res, dts[:nsteps], float(ms[0])
+
+    def sc_implicit_march(self, dt: float, nsteps: int, jacobian_every: int = 0):
+        """Linearised BDF1 steps with a reused Jacobian; returns (residual history,
+        cumulative device ms, GMRES iterations per step)."""
+        res, ms = np.zeros(nsteps + 1), np.zeros(nsteps + 1)
+        its = np.zeros(max(nsteps, 1), dtype=np.int32)
+        self._check(self._L.sc_implicit_march(self.h, dt, nsteps, jacobian_every, res.ctypes.data, ms.ctypes.data,
+                                              its.ctypes.data))
+        return res, ms, its[:nsteps]
 
     def sc_condensed_matvec_static(self, xb, yb):
         """S x_b without any allocation in the call (fixed 8 MiB device scratch); enqueues only."""
