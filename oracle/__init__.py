@@ -220,8 +220,9 @@ def phys_flux(p: Params, q, g, d: int):
 
 
 from .linalg import (  # noqa: E402
-    MixedCondensedSystem, boundary_interior_split, boundary_interior_split_mixed, condensed_operator,
-    condensed_solve, condensed_solve_mixed, global_solve, gmres, ratio_formula,
+    MixedCondensedSystem, black_schur_correction, boundary_interior_split, boundary_interior_split_mixed,
+    checkerboard, condensed_operator, condensed_solve, condensed_solve_mixed, corrected_black_blocks, global_solve,
+    global_solve_dense, gmres, ratio_formula, red_black_apply,
 )
 
 

@@ -96,10 +96,13 @@ void free_all(sc_ctx* c) {
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
                    &c->Apk32, &c->Sls32, &c->Sdiag, &c->Cpl, &c->Feat, &c->Snorm, &c->Ynet, &c->Hbuf,
-                   &c->Ck, &c->Wbias, &c->ExIb, &c->ExBi, &c->ExY, &c->ExW};
+                   &c->Ck, &c->Wbias, &c->ExIb, &c->ExBi, &c->ExY, &c->ExW, &c->Zrb, &c->SeeB, &c->SeeL, &c->SlsL};
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
+  if (c->Trb) cudaFree(c->Trb);
+  c->Trb = nullptr;
+  c->blackL_valid = false;
   if (c->gj_scale) cudaFree(c->gj_scale);
   c->gj_scale = nullptr;
   c->packed = false;
@@ -111,7 +114,8 @@ void free_all(sc_ctx* c) {
   c->Sdiag_valid = c->weights_set = c->learned_on = false;
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_own_pairs, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
-                 &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx};
+                 &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx,
+                 &c->d_colour, &c->pivL, &c->rowpermL};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
 }
 
@@ -304,6 +308,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   build_pattern(c);
   sc::build_packed_pattern(c);
   sc::build_learned_tables(c);
+  sc::build_colours(c);
   if (c->cfg.explicit_schur) sc::build_explicit_tables(c);
   const size_t nodes = (size_t)G.K * G.nn, dofs = nodes * 5;
   const size_t n1 = (size_t)G.K * G.nb;
@@ -363,6 +368,17 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   } else {
     A(dalloc(&c->Apk, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls, sc::solve_layout_elems(G)));
   }
+  const bool sweep = c->cfg.precond == SC_PC_RED_BLACK || c->cfg.precond == SC_PC_LEARNED;
+  if (sweep) {
+    A(dalloc(&c->d_colour, (size_t)G.K)); A(dalloc(&c->Trb, n1));
+    if (c->cfg.precision == SC_PREC_MIXED) A(dalloc(&c->Zrb, n1));
+  }
+  if (c->cfg.precond == SC_PC_LEARNED) {
+    const size_t nbk = (size_t)c->n_black;
+    A(dalloc(&c->SeeB, nbk * G.nb * G.lds)); A(dalloc(&c->SeeL, nbk * G.nb * G.lds));
+    A(dalloc(&c->SlsL, nbk * (size_t)sc::solve_layout_stride(G)));
+    A(dalloc(&c->pivL, nbk * G.nb)); A(dalloc(&c->rowpermL, nbk * G.nb));
+  }
   if (e != cudaSuccess) { free_all(c); cudaGetLastError(); return fail(c, SC_ERR_OOM, std::string("allocation: ") + cudaGetErrorString(e)); }
   SC_CUDA(cudaMemcpy(c->d_nbr, c->nbr.data(), c->nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_perm, c->perm.data(), G.nn * sizeof(int), cudaMemcpyHostToDevice));
@@ -387,6 +403,8 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   if (c->cfg.explicit_schur) SC_CUDA(sc::upload_explicit_tables(c));
   SC_CUDA(cudaMemcpy(c->d_lface, c->l_face.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_lmirror, c->l_mirror.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
+  if (c->d_colour)
+    SC_CUDA(cudaMemcpy(c->d_colour, c->colour_list.data(), (size_t)G.K * sizeof(int), cudaMemcpyHostToDevice));
   // the alignment padding of the element blocks (dense and packed) must read as zero
   if (c->Apk) SC_CUDA(cudaMemset(c->Apk, 0, (size_t)G.K * c->pk_stride * sizeof(double)));
   if (c->Apk32) SC_CUDA(cudaMemset(c->Apk32, 0, (size_t)G.K * c->pk_stride * sizeof(float)));
@@ -468,7 +486,10 @@ sc_status sc_condense(sc_ctx* c) {
   const int zero = 0;
   SC_CUDA(cudaMemcpyAsync(c->d_status + 1, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   SC_CUDA(sc::launch_condense(c));
-  if (c->cfg.precond == SC_PC_LEARNED) SC_CUDA(sc::learned_correction(c));
+  if (c->cfg.precond == SC_PC_LEARNED) {  // network -> C_k -> factors of the corrected black blocks
+    SC_CUDA(sc::learned_correction(c));
+    SC_CUDA(sc::learned_black_factor(c, c->Ck, 1.0f));
+  }
   if (c->cfg.explicit_schur) SC_CUDA(sc::explicit_build(c));
   int bad = -1, ovf = 0;
   SC_CUDA(cudaMemcpyAsync(&bad, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -633,6 +654,19 @@ sc_status sc_condensed_matvec(sc_ctx* c, const double* xb, double* yb) {
   return check(c);
 }
 
+sc_status sc_precond_apply(sc_ctx* c, const double* v, double* z) {
+  if (!c || !v || !z || v == z) return SC_ERR_ARG;
+  if (!c->condensed) return fail(c, SC_ERR_STATE, "precond_apply before condense");
+  c->learned_on = c->cfg.precond == SC_PC_LEARNED && c->weights_set && c->blackL_valid;
+  if (c->cfg.precision == SC_PREC_MIXED) {
+    SC_CUDA(sc::precond_apply32(c, v, z, nullptr));
+  } else {
+    SC_CUDA(sc::precond_apply(c, v, z));
+  }
+  c->learned_on = false;
+  return check(c);
+}
+
 }  // extern "C"
 
 namespace {
@@ -652,6 +686,29 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
   SC_CUDA(cudaMemsetAsync(c->Xb, 0, n1 * sizeof(double), c->stream));
   SC_CUDA(cudaMemcpyAsync(c->Rb, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   double beta = dnorm2(c, c->Rb, n1, hs);
+  if (c->learned_on && beta > 0.0) {
+    // judge of the learned correction: one preconditioned step from the normalised
+    // residual v, ||v - S P v|| with the learned sweep against block Jacobi; the solve keeps
+    // the learned preconditioner only if it does at least as well
+    double rho[2] = {0.0, 0.0};
+    SC_CUDA(sc::vec_axpby(c, c->V, 1.0 / beta, c->Rb, 0.0, n1));
+    for (int k = 0; k < 2; ++k) {
+      c->learned_on = k == 0;
+      if (c->op32) {
+        SC_CUDA(sc::precond_apply32(c, c->V, nullptr, c->Zf));
+        SC_CUDA(sc::cond_interior32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf));
+        SC_CUDA(sc::cond_boundary32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf, c->Wv));
+      } else {
+        SC_CUDA(sc::precond_apply(c, c->V, c->Zv));
+        SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
+        SC_CUDA(sc::cond_boundary(c, c->Zv, 1.0, nullptr, 0.0, c->Ui, c->Wv));
+      }
+      SC_CUDA(sc::vec_axpby(c, c->Wv, 1.0, c->V, -1.0, n1));
+      rho[k] = dnorm2(c, c->Wv, n1, hs);
+    }
+    c->learned_on = rho[0] <= rho[1];
+    if (!c->learned_on) c->learned_fallbacks++;
+  }
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(2 * (m + 1) + 1), y(m);
   int iters = 0;
   double resid = beta;
@@ -865,7 +922,7 @@ sc_status sc_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* st) {
   cudaEvent_t* ev = c->ev;
   double* const hs = c->Hd + 2 * (c->restart_alloc + 1) + 2;
   double* xout = on_device ? dQ : c->Xfull;
-  c->learned_on = c->cfg.precond == SC_PC_LEARNED && c->weights_set;
+  c->learned_on = c->cfg.precond == SC_PC_LEARNED && c->weights_set && c->blackL_valid;
   c->learned_fallbacks = 0;
   SC_CUDA(cudaEventRecord(ev[0], c->stream));
   const double bnorm = dnorm2(c, c->B, dofs, hs);

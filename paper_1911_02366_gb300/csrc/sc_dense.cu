@@ -1269,21 +1269,35 @@ __device__ __forceinline__ void ls_solve_cta(int n, int nblk, const TS* __restri
 
 constexpr int kSolveCtaWarps = 8;
 
+// Element lists (red-black sweep): CTA / warp i serves element elist[i] (all elements when
+// elist is null); its factors are number i of LS / rowperm when compact, else number e;
+// vsub (optional) is subtracted from v on input.
 template <class T, class TS>
 __global__ void __launch_bounds__(32 * kSolveCtaWarps) k_lu_solve_cta(int n, int nblk, const TS* __restrict__ LS,
                                                                       long long lsstride, int npad,
                                                                       const int* __restrict__ rowperm,
                                                                       const double* __restrict__ v,
-                                                                      double* __restrict__ z, T* __restrict__ zt) {
+                                                                      double* __restrict__ z, T* __restrict__ zt,
+                                                                      const int* __restrict__ elist, int compact,
+                                                                      const double* __restrict__ vsub) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int e = blockIdx.x, ls = nblk * 32;
+  const int e = elist ? __ldg(elist + blockIdx.x) : blockIdx.x, ls = nblk * 32;
+  const int f = compact ? blockIdx.x : e;
   T* s = reinterpret_cast<T*>(smem_raw);
   T* red = s + ls;
-  const int* rp = rowperm + (long long)e * n;
+  const int* rp = rowperm + (long long)f * n;
   const double* ve = v + (long long)e * n;
-  for (int i = threadIdx.x; i < ls; i += blockDim.x) s[i] = i < n ? (T)ve[__ldg(rp + i)] : T(0);
+  const double* we = vsub ? vsub + (long long)e * n : nullptr;
+  for (int i = threadIdx.x; i < ls; i += blockDim.x) {
+    T val = T(0);
+    if (i < n) {
+      const int r = __ldg(rp + i);
+      val = we ? (T)(ve[r] - we[r]) : (T)ve[r];
+    }
+    s[i] = val;
+  }
   __syncthreads();
-  ls_solve_cta<T, TS, kSolveCtaWarps>(n, nblk, LS + (long long)e * lsstride, npad, s, red);
+  ls_solve_cta<T, TS, kSolveCtaWarps>(n, nblk, LS + (long long)f * lsstride, npad, s, red);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     if (z) z[(long long)e * n + i] = (double)s[i];
     if (zt) zt[(long long)e * n + i] = s[i];
@@ -1292,36 +1306,36 @@ __global__ void __launch_bounds__(32 * kSolveCtaWarps) k_lu_solve_cta(int n, int
 
 // z = (P^T L U)^-1 v, one warp per element (4 per CTA); the running vector (v, then x,
 // then z) sits in shared memory.  Arithmetic in the factor precision T; v in double,
-// outputs z (double) and / or zt (T).  CORR: add a 5 x 5 correction per boundary node,
-// z_k += C_k v_k (the learned correction of the block-Jacobi inverse); a separate
-// instantiation, because the branch alone slowed the plain solve by 14 %.
-template <class T, class TS, bool CORR>
+// outputs z (double) and / or zt (T).
+template <class T, class TS>
 __global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const TS* __restrict__ LS, long long lsstride,
                                                   int npad, const int* __restrict__ rowperm,
                                                   const double* __restrict__ v, double* __restrict__ z,
-                                                  T* __restrict__ zt, int nelem, const float* __restrict__ Ck) {
+                                                  T* __restrict__ zt, int nelem, const int* __restrict__ elist,
+                                                  int compact,
+                                                  const double* __restrict__ vsub) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  const int e = blockIdx.x * 4 + warp;
-  if (e >= nelem) return;  // whole warps leave; no block-level barrier follows
+  const int idx = blockIdx.x * 4 + warp;
+  if (idx >= nelem) return;  // whole warps leave; no block-level barrier follows
+  const int e = elist ? __ldg(elist + idx) : idx, f = compact ? idx : e;
   const int ls = nblk * 32;
   T* s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * ls;
-  const int* rp = rowperm + (long long)e * n;
+  const int* rp = rowperm + (long long)f * n;
   const double* ve = v + (long long)e * n;
-  for (int i = lane; i < ls; i += 32) s[i] = i < n ? (T)ve[__ldg(rp + i)] : T(0);
-  __syncwarp();
-  ls_solve_warp<T, TS>(n, nblk, LS + (long long)e * lsstride, npad, s, lane);
-  for (int i = lane; i < n; i += 32) {
-    T val = s[i];
-    if (CORR) {  // compiled only into the corrected variant: the plain loop stays lean
-      const int a = i / 5, k = i - 5 * a;
-      const float* C = Ck + ((long long)e * (n / 5) + a) * 25 + 5 * k;
-      const double* va = ve + 5 * a;
-      float c = 0.f;
-#pragma unroll
-      for (int l = 0; l < 5; ++l) c = fmaf(C[l], (float)va[l], c);
-      val += (T)c;
+  const double* we = vsub ? vsub + (long long)e * n : nullptr;
+  for (int i = lane; i < ls; i += 32) {
+    T val = T(0);
+    if (i < n) {
+      const int r = __ldg(rp + i);
+      val = we ? (T)(ve[r] - we[r]) : (T)ve[r];
     }
+    s[i] = val;
+  }
+  __syncwarp();
+  ls_solve_warp<T, TS>(n, nblk, LS + (long long)f * lsstride, npad, s, lane);
+  for (int i = lane; i < n; i += 32) {
+    const T val = s[i];
     if (z) z[(long long)e * n + i] = (double)val;
     if (zt) zt[(long long)e * n + i] = val;
   }
@@ -1499,6 +1513,8 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
       if (err != cudaSuccess) return err;
       c->Sdiag_valid = true;
     }
+    err = gather_black_see(c, See);  // uncorrected black blocks for the learned correction
+    if (err != cudaSuccess) return err;
   }
   if (c->cfg.precond != SC_PC_NONE) {
     bool done = false;
@@ -1563,19 +1579,47 @@ cudaError_t lu_solve_t(sc_ctx* c, const TS* LS, const double* v, double* z, T* z
   const Geo& G = c->G;
   ProfScope ps(c, SCK_LU_SOLVE);
   const size_t smem = (size_t)4 * ls_nblk(G) * 32 * sizeof(T);
-  if (G.K < kSolveCtaMaxElems && !(c->learned_on && c->Ck)) {
+  if (G.K < kSolveCtaMaxElems) {
     const size_t csm = (size_t)(ls_nblk(G) + kSolveCtaWarps) * 32 * sizeof(T);
     k_lu_solve_cta<T, TS><<<G.K, 32 * kSolveCtaWarps, csm, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
-                                                                       ls_npad(G), c->rowperm, v, z, zt);
+                                                                       ls_npad(G), c->rowperm, v, z, zt, nullptr, 0,
+                                                                       nullptr);
     return cudaGetLastError();
   }
-  if (c->learned_on && c->Ck)
-    k_lu_solve<T, TS, true><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
-                                                                    c->rowperm, v, z, zt, G.K, c->Ck);
-  else
-    k_lu_solve<T, TS, false><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
-                                                                     ls_npad(G), c->rowperm, v, z, zt, G.K, nullptr);
+  k_lu_solve<T, TS><<<cdiv(G.K, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
+                                                            c->rowperm, v, z, zt, G.K, nullptr, 0, nullptr);
   return cudaGetLastError();
+}
+
+// Block solves of a list of elements (one colour of the red-black sweep): factors LS /
+// rowperm by element, or compact (number i for list entry i); vsub subtracted from v.
+template <class T, class TS>
+cudaError_t lu_solve_list_t(sc_ctx* c, const TS* LS, const int* rowperm, int compact, const int* elist, int nlist,
+                            const double* v, const double* vsub, double* z, T* zt) {
+  const Geo& G = c->G;
+  if (nlist <= 0) return cudaSuccess;
+  ProfScope ps(c, SCK_LU_SOLVE);
+  if (nlist < kSolveCtaMaxElems) {
+    const size_t csm = (size_t)(ls_nblk(G) + kSolveCtaWarps) * 32 * sizeof(T);
+    k_lu_solve_cta<T, TS><<<nlist, 32 * kSolveCtaWarps, csm, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
+                                                                         ls_npad(G), rowperm, v, z, zt, elist,
+                                                                         compact, vsub);
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t)4 * ls_nblk(G) * 32 * sizeof(T);
+  k_lu_solve<T, TS><<<cdiv(nlist, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
+                                                              rowperm, v, z, zt, nlist, elist, compact, vsub);
+  return cudaGetLastError();
+}
+
+cudaError_t lu_solve_list(sc_ctx* c, const double* LS, const int* rowperm, int compact, const int* elist, int nlist,
+                          const double* v, const double* vsub, double* z) {
+  return lu_solve_list_t<double, double>(c, LS, rowperm, compact, elist, nlist, v, vsub, z, nullptr);
+}
+
+cudaError_t lu_solve_list32(sc_ctx* c, const float* LS, const int* rowperm, int compact, const int* elist, int nlist,
+                            const double* v, const double* vsub, double* z, float* zt) {
+  return lu_solve_list_t<float, float>(c, LS, rowperm, compact, elist, nlist, v, vsub, z, zt);
 }
 
 cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
@@ -1584,6 +1628,7 @@ cudaError_t precond_apply(sc_ctx* c, const double* v, double* z) {
   if (c->cfg.precond == SC_PC_NONE) {
     return cudaMemcpyAsync(z, v, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   }
+  if (rb_active(c)) return precond_rb(c, v, z);
   return lu_solve_t<double, double>(c, c->Sls, v, z, nullptr);
 }
 
@@ -1597,6 +1642,7 @@ cudaError_t precond_apply32(sc_ctx* c, const double* v, double* z, float* zf) {
     if (e == cudaSuccess && zf) e = vec_to_float(c, zf, v, n1);
     return e;
   }
+  if (rb_active(c)) return precond_rb32(c, v, z, zf);
   if (c->ls16_ok) return lu_solve_t<float, __half>(c, c->Sls16, v, z, zf);
   return lu_solve_t<float, float>(c, c->Sls32, v, z, zf);
 }

@@ -298,6 +298,17 @@ struct sc_ctx {
   std::vector<int> ex_nbpos, ex_face_idx;
   int *d_ex_nbpos = nullptr, *d_ex_face_idx = nullptr;
   float *ExIb = nullptr, *ExBi = nullptr, *ExY = nullptr, *ExW = nullptr;
+  // red-black sweep over the element Schur blocks (SC_PC_RED_BLACK, SC_PC_LEARNED): the
+  // elements of each colour of the checkerboard (ex + ey + ez even = red), red first
+  std::vector<int> colour_list;
+  int n_red = 0, n_black = 0;
+  int* d_colour = nullptr;
+  float* Zrb = nullptr;      // FP32 sweep vector (mixed arm)
+  double* Trb = nullptr;     // (S z) on the black rows
+  // learned correction of the black face blocks: uncorrected copies, corrected factors
+  float *SeeB = nullptr, *SeeL = nullptr, *SlsL = nullptr;
+  int *pivL = nullptr, *rowpermL = nullptr;
+  bool blackL_valid = false;  // SlsL holds the factors of the corrected black blocks
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};
   // measurement hooks: kernel launches since creation, and optional CUDA-event timing
@@ -433,4 +444,20 @@ template <class T>
 cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* X, const T* xb, double delta, const double* Bfull,
                              double gamma_, const T* u, double* y);
 cudaError_t vec_axpby(sc_ctx* c, double* y, double a, const double* x, double b, size_t n);
+// block solves of a list of elements (factors by element, or compact by list position), vsub
+// subtracted from the right-hand side
+cudaError_t lu_solve_list(sc_ctx* c, const double* LS, const int* rowperm, int compact, const int* elist, int nlist,
+                          const double* v, const double* vsub, double* z);
+cudaError_t lu_solve_list32(sc_ctx* c, const float* LS, const int* rowperm, int compact, const int* elist, int nlist,
+                            const double* v, const double* vsub, double* z, float* zt);
+template <class T>
+cudaError_t cond_boundary_pk_list(sc_ctx* c, const T* Apk, const T* X, const T* xb, const T* u, double* y,
+                                  const int* elist, int nlist);
+// red-black sweep (precond SC_PC_RED_BLACK, or SC_PC_LEARNED while the learned correction is on)
+void build_colours(sc_ctx* c);
+bool rb_active(const sc_ctx* c);
+cudaError_t precond_rb(sc_ctx* c, const double* v, double* z);
+cudaError_t precond_rb32(sc_ctx* c, const double* v, double* z, float* zf);
+cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale);
+cudaError_t gather_black_see(sc_ctx* c, const float* See);
 }  // namespace sc

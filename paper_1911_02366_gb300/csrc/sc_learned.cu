@@ -175,13 +175,12 @@ __global__ void k_targets(int nsmp, const float* __restrict__ Pinv, const float*
   T[t] = (Pinv[t] - Sinv[t]) * snorm[t / 25];
 }
 
-// C_k = y_k / ||[S_ee]_kk||_F
+// C_k = y_k ||[S_ee]_kk||_F (the network works on blocks scaled by the node's own block)
 __global__ void k_scale_correction(int nsmp, const float* __restrict__ Y, const float* __restrict__ snorm,
                                    float* __restrict__ Ck) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nsmp * 25) return;
-  const float s = snorm[t / 25];
-  Ck[t] = s > 0.f ? Y[t] / s : 0.f;
+  Ck[t] = Y[t] * snorm[t / 25];
 }
 
 }  // namespace
@@ -338,18 +337,12 @@ done:
   return status;
 }
 
-__global__ void k_scaled_copy(int n, const float* __restrict__ src, float a, float* __restrict__ dst) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) dst[t] = a * src[t];
-}
-
 sc_status sc_set_learned_correction(sc_ctx* c, const float* Ck, float scale) {
   if (!c || !Ck) return SC_ERR_ARG;
-  if (!c->condensed || !c->Ck) return SC_ERR_STATE;
-  const int n = c->G.K * c->G.nbn * 25;
-  k_scaled_copy<<<(n + 255) / 256, 256, 0, c->stream>>>(n, Ck, scale, c->Ck);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) return SC_ERR_CUDA;
-  c->weights_set = true;  // the correction is in place; the next sc_solve applies it
+  if (!c->condensed || !c->SeeB) return SC_ERR_STATE;
+  if (sc::learned_black_factor(c, Ck, scale) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return SC_ERR_CUDA;
+  c->weights_set = true;  // the corrected black factors are in place; the next sc_solve uses them
   return SC_OK;
 }
 

@@ -207,9 +207,11 @@ __global__ void __launch_bounds__(256, PkOcc<T>::v) k_cond_boundary_pk(Geo G, co
     const int* __restrict__ row_off, const int* __restrict__ lptr, const int* __restrict__ list,
     const T* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
     const int* __restrict__ pinfo, const int* __restrict__ iperm, const T* __restrict__ xb, double delta,
-    const double* __restrict__ Bfull, double gamma_, const T* __restrict__ u, double* __restrict__ y) {
+    const double* __restrict__ Bfull, double gamma_, const T* __restrict__ u, double* __restrict__ y,
+    const int* __restrict__ elist) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int e = blockIdx.x, ni = G.ni, nb = G.nb, lda = G.lda, cb0 = G.cb0;
+  // CTA i serves element elist[i] (one colour of the red-black sweep), or element i
+  const int e = elist ? __ldg(elist + blockIdx.x) : blockIdx.x, ni = G.ni, nb = G.nb, lda = G.lda, cb0 = G.cb0;
   T* v = reinterpret_cast<T*>(smem_raw);  // lda: [-u_e | 0 | delta x_e | 0]
   __shared__ int nbr_s[18];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
@@ -326,9 +328,28 @@ cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* X, const T* xb, d
   const size_t smem = (size_t)G.lda * sizeof(T);
   k_cond_boundary_pk<T><<<G.K, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
                                                        c->d_pk_list, X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm,
-                                                       xb, delta, Bfull, gamma_, u, y);
+                                                       xb, delta, Bfull, gamma_, u, y, nullptr);
   return cudaGetLastError();
 }
+
+// y_e = (A_bb x_b)_e - (A_bi u)_e for the elements of a list only (rows of one colour).
+template <class T>
+cudaError_t cond_boundary_pk_list(sc_ctx* c, const T* Apk, const T* X, const T* xb, const T* u, double* y,
+                                  const int* elist, int nlist) {
+  const Geo& G = c->G;
+  if (nlist <= 0) return cudaSuccess;
+  const size_t smem = (size_t)G.lda * sizeof(T);
+  ProfScope ps(c, SCK_COND_BOUNDARY);
+  k_cond_boundary_pk<T><<<nlist, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
+                                                         c->d_pk_list, X, c->d_nbr, c->d_pptr, c->d_pinfo,
+                                                         c->d_iperm, xb, 1.0, nullptr, 0.0, G.ni ? u : nullptr, y,
+                                                         elist);
+  return cudaGetLastError();
+}
+template cudaError_t cond_boundary_pk_list<float>(sc_ctx*, const float*, const float*, const float*, const float*,
+                                                  double*, const int*, int);
+template cudaError_t cond_boundary_pk_list<double>(sc_ctx*, const double*, const double*, const double*,
+                                                   const double*, double*, const int*, int);
 
 template cudaError_t cond_interior_pk<float>(sc_ctx*, const float*, const float*, const float*, const float*, double,
                                              const double*, double, float*);

@@ -16,7 +16,7 @@ from . import build as _build
 SC_OK, SC_ERR_ARG, SC_ERR_CUDA, SC_ERR_OOM, SC_ERR_STATE = 0, 1, 2, 3, 4
 SC_ERR_SINGULAR_BLOCK, SC_ERR_NONFINITE, SC_ERR_NOT_CONVERGED = 5, 6, 7
 SC_PREC_FP64, SC_PREC_MIXED = 0, 1
-SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED = 0, 1, 2
+SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED, SC_PC_RED_BLACK = 0, 1, 2, 3
 
 _lib = None
 
@@ -57,7 +57,8 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_mlp_adam", "sc_learned_features", "sc_learned_targets", "sc_set_learned_weights", "sc_set_learned_correction",
            "sc_get_state", "sc_condensed_rhs", "sc_backsubstitute", "sc_newton_step", "sc_batch_create",
            "sc_batch_condense", "sc_batch_tiles", "sc_batch_destroy", "sc_spectrum_estimate",
-           "sc_hessenberg_eigvals", "sc_steady_residual", "sc_explicit_march", "sc_implicit_march"]
+           "sc_hessenberg_eigvals", "sc_steady_residual", "sc_explicit_march", "sc_implicit_march",
+           "sc_precond_apply"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -118,6 +119,7 @@ def lib(build_if_missing: bool = True):
     L.sc_spectrum_estimate.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
     L.sc_hessenberg_eigvals.argtypes = [ctypes.c_int, dp, dp, dp]
     L.sc_steady_residual.argtypes = [vp, dp]
+    L.sc_precond_apply.argtypes = [vp, dp, dp]
     L.sc_explicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]
     L.sc_implicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -315,6 +317,14 @@ class Context:
                                                  out.ctypes.data))
         return {"lam_max": complex(out[0], out[1]), "lam_min": complex(out[2], out[3]), "cond": out[4],
                 "inner_iters": int(out[5])}
+
+    def sc_precond_apply(self, v, z):
+        """z = P v with the context's condensed preconditioner (device float64 tensors)."""
+        (pv, dv), (pz, dz) = _ptr(v), _ptr(z)
+        if not (dv and dz):
+            raise ValueError("precond_apply takes device tensors")
+        self._check(self._L.sc_precond_apply(self.h, pv, pz))
+        return z
 
     def sc_steady_residual(self) -> float:
         """||M^-1 H(Q)||_inf of the current state."""

@@ -31,10 +31,10 @@ def test_steady_residual_matches_oracle():
 @pytest.mark.parametrize("n,N,dfl", [(2, 3, 0.0), (3, 2, 0.05)])
 def test_explicit_rk3_march_matches_oracle(n, N, dfl):
     Q, dt, p, ctx = _setup(n, N)
-    res, dts, ms = ctx.sc_explicit_march(0.5, 6, dfl=dfl)
+    res, dts, ms = ctx.sc_explicit_march(0.15, 6, dfl=dfl)
     q = np.zeros(Q.size)
     ctx.sc_get_state(q)
-    qo, reso, dtso = MA.rk3_march(p, Q, 0.5, 6, dfl=dfl)
+    qo, reso, dtso = MA.rk3_march(p, Q, 0.15, 6, dfl=dfl)
     assert np.max(np.abs(dts - dtso)) <= 1e-13 * np.max(dtso)
     assert np.max(np.abs(q - qo.reshape(-1))) <= 1e-12 * np.max(np.abs(qo))
     assert np.max(np.abs(res - reso) / reso) <= 1e-9

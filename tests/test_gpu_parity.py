@@ -116,7 +116,7 @@ def tgv_4x4x4_N3_cfl50_global():
     p = O.Params(n=n, N=N, dt=dt)
     A = O.jacobian(p, Q)
     B = -O.residual(p, Q).reshape(-1)
-    return Q, A, B, O.global_solve(A, B)
+    return Q, A, B, O.global_solve_dense(A, B)
 
 
 @pytest.mark.parametrize("arm", ["fp64", "mixed"])
@@ -131,8 +131,10 @@ def test_tgv_4x4x4_N3_cfl50_condensed_equals_global_solve(arm, tgv_4x4x4_N3_cfl5
         cfg = dict(rel_tol=1e-12, gmres_restart=300, gmres_max_iters=8000)
         tol = 1e-10
     else:
-        cfg = dict(precision=sc.SC_PREC_MIXED, rel_tol=1e-11, inner_tol=1e-4, gmres_restart=300,
-                   gmres_max_iters=8000, max_refine=30)
+        # FP32 inner solves inside the outer FGMRES on the FP64 system: at this conditioning
+        # plain refinement sweeps stall, the outer Krylov space keeps converging
+        cfg = dict(precision=sc.SC_PREC_MIXED, rel_tol=1e-11, inner_tol=1e-2, gmres_restart=60,
+                   gmres_max_iters=20000, max_refine=20, outer_krylov=30, inner_iters=200)
         tol = 1e-8
     _, dt, p, ctx = case(n, N, cfl=50.0, **cfg)
     ctx.sc_set_state(Q, Q)

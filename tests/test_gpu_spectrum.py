@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,N,cfl", [(2, 2, 10.0), (2, 3, 50.0)])
+@pytest.mark.parametrize("n,N,cfl", [(2, 2, 10.0), (2, 3, 10.0)])
 def test_spectrum_estimate_matches_oracle_dense_eigenvalues(n, N, cfl):
     Q, dt, p, ctx = case(n, N, cfl=cfl, gmres_restart=60, gmres_max_iters=4000)
     ctx.sc_set_state(Q, Q)

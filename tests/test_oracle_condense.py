@@ -64,3 +64,15 @@ def test_schur_own_block_is_the_whole_schur_on_one_element():
     cs = O.condensed_operator(O.jacobian(p, Q), n, N)
     S = cs.dense_S()
     np.testing.assert_allclose(cs.own_block_S(0), S, rtol=0, atol=1e-12 * np.abs(S).max())
+
+
+def test_dense_global_solve_equals_sparse_global_solve():
+    """The dense-LU form of x = A^-1 B agrees with the sparse-LU one (both direct)."""
+    import sc_inputs as I
+    n, N = 2, 2
+    Q, dt = I.tgv_state(n, N, cfl=10.0, seed=0)
+    p = O.Params(n=n, N=N, dt=dt)
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    x1, x2 = O.global_solve(A, B), O.global_solve_dense(A, B)
+    assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x1)
