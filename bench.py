@@ -170,6 +170,8 @@ def run_ours(args, world, rank, local):
     if args.arm == "learned":
         net, train_info = train_correction(args, stream)
         extra = dict(precond=sc.SC_PC_LEARNED)
+    elif args.precond == "rb":
+        extra = dict(precond=sc.SC_PC_RED_BLACK)
     ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
@@ -269,7 +271,7 @@ def run_ours(args, world, rank, local):
                    "outer": (f"fgmres({args.outer_krylov})" if args.outer_krylov else "refinement sweeps")
                    if args.arm != "fp64" else None,
                    "tensor_cores": bool(args.tensor_cores) if args.arm != "fp64" else False,
-                   "operator": args.operator,
+                   "operator": args.operator, "precond": "learned" if args.arm == "learned" else args.precond,
                    "l2": f"inputs larger than L2 (element blocks {blocks_gb:.1f} GB)", "parallelism": f"replicas x{world}"},
         "linear_solve_dof_per_s": world * dofs * args.steps / (gather_max(world, solve_ms) * 1e-3),
         "assemble_ms_per_step": assemble_ms / args.steps,
@@ -540,6 +542,8 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=20, help="learned arm: training epochs (untimed)")
     ap.add_argument("--operator", choices=["implicit", "explicit"], default="implicit",
                     help="mixed arm: condensed operator applied implicitly or from explicit W_e blocks")
+    ap.add_argument("--precond", choices=["bj", "rb"], default="bj",
+                    help="condensed preconditioner: block Jacobi or the red-black block Gauss-Seidel sweep")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)

@@ -115,7 +115,7 @@ void free_all(sc_ctx* c) {
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_own_pairs, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
                  &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx,
-                 &c->d_colour, &c->pivL, &c->rowpermL};
+                 &c->d_colour, &c->pivL, &c->rowpermL, &c->d_lnfaces};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
 }
 
@@ -349,7 +349,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pinfo, np));
   A(dalloc(&c->d_pk_lptr, c->pk_lptr.size())); A(dalloc(&c->d_pk_list, c->pk_list.size()));
   A(dalloc(&c->d_pk_row_off, c->pk_row_off.size())); A(dalloc(&c->d_pk_pos, c->pk_pos.size()));
-  A(dalloc(&c->d_lface, G.nbn)); A(dalloc(&c->d_lmirror, G.nbn));
+  A(dalloc(&c->d_lface, G.nbn)); A(dalloc(&c->d_lmirror, G.nbn)); A(dalloc(&c->d_lnfaces, G.nbn));
   if (c->cfg.precision == SC_PREC_MIXED) {
     const size_t nsmp = (size_t)G.K * G.nbn;
     A(dalloc(&c->Sdiag, nsmp * 25)); A(dalloc(&c->Cpl, nsmp * 25));
@@ -403,6 +403,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   if (c->cfg.explicit_schur) SC_CUDA(sc::upload_explicit_tables(c));
   SC_CUDA(cudaMemcpy(c->d_lface, c->l_face.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_lmirror, c->l_mirror.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_lnfaces, c->l_nfaces.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   if (c->d_colour)
     SC_CUDA(cudaMemcpy(c->d_colour, c->colour_list.data(), (size_t)G.K * sizeof(int), cudaMemcpyHostToDevice));
   // the alignment padding of the element blocks (dense and packed) must read as zero

@@ -1341,29 +1341,6 @@ __global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const TS* __r
   }
 }
 
-// Diagonal node blocks of inverses: warp w solves A_m x = e_c for the matrix m = mat[w]
-// and column c = 5 node[w] + var[w], and stores x at rows 5 node .. 5 node + 4 as column
-// var of the 5 x 5 block out[w / 5] (w enumerates (sample, var) pairs, var fastest).
-template <class T>
-__global__ void __launch_bounds__(128) k_unit_solve(int n, int nblk, const T* __restrict__ LS, long long lsstride,
-                                                    int npad, const int* __restrict__ rowperm,
-                                                    const int* __restrict__ mat, const int* __restrict__ node,
-                                                    int nw_total, float* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  const int w = blockIdx.x * 4 + warp;
-  if (w >= nw_total) return;
-  const int smp = w / 5, var = w - 5 * smp;
-  const int m = mat[smp], a = node[smp], col = 5 * a + var;
-  const int ls = nblk * 32;
-  T* s = reinterpret_cast<T*>(smem_raw) + (size_t)warp * ls;
-  const int* rp = rowperm + (long long)m * n;
-  for (int i = lane; i < ls; i += 32) s[i] = (i < n && __ldg(rp + i) == col) ? T(1) : T(0);
-  __syncwarp();
-  ls_solve_warp<T, T>(n, nblk, LS + (long long)m * lsstride, npad, s, lane);
-  if (lane < 5) out[(long long)smp * 25 + 5 * lane + var] = (float)s[5 * a + lane];
-}
-
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
     b[t] = (float)a[t];
@@ -1751,16 +1728,41 @@ cudaError_t factor_batch32(sc_ctx* c, float* A, int n, int lda, long long stride
   return cudaGetLastError();
 }
 
-// Diagonal node blocks [A_m^-1]_(node, node) for nsmp (matrix, node) samples.
-cudaError_t unit_solve32(sc_ctx* c, int n, const float* LS, long long lsstride, const int* rowperm, const int* mat,
-                         const int* node, int nsmp, float* out) {
-  const int nblk = (n + 31) / 32, npad = (n + 3) & ~3;
+// X[p][j][:] = S_mm^-1 S[m rows, column b nb + j] for every pair p = (black element b, red
+// neighbour m) and column j < n of b's block, from the dense S stored column by column
+// (n1 rows); one warp per (pair, column), S_mm from the condensation's own factors.
+__global__ void __launch_bounds__(128) k_solve_cols(int n, int nblk, const float* __restrict__ LS, long long lsstride,
+                                                    int npad, const int* __restrict__ rowperm,
+                                                    const double* __restrict__ Scm, long long n1,
+                                                    const int* __restrict__ pb, const int* __restrict__ pm,
+                                                    int npairs, float* __restrict__ X) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const long long w = (long long)blockIdx.x * 4 + warp;
+  if (w >= (long long)npairs * n) return;
+  const int pidx = (int)(w / n), j = (int)(w % n);
+  const int b = __ldg(pb + pidx), m = __ldg(pm + pidx);
+  const int ls = nblk * 32;
+  float* s = reinterpret_cast<float*>(smem_raw) + (size_t)warp * ls;
+  const int* rp = rowperm + (long long)m * n;
+  const double* col = Scm + ((long long)b * n + j) * n1 + (long long)m * n;
+  for (int i = lane; i < ls; i += 32) s[i] = i < n ? (float)col[__ldg(rp + i)] : 0.f;
+  __syncwarp();
+  ls_solve_warp<float, float>(n, nblk, LS + (long long)m * lsstride, npad, s, lane);
+  float* out = X + ((long long)pidx * n + j) * n;
+  for (int i = lane; i < n; i += 32) out[i] = s[i];
+}
+
+cudaError_t solve_columns32(sc_ctx* c, const double* Scm, long long n1, const int* pb, const int* pm, int npairs,
+                            float* X) {
+  const Geo& G = c->G;
+  const int n = G.nb, nblk = ls_nblk(G);
   const size_t smem = (size_t)4 * nblk * 32 * sizeof(float);
-  cudaError_t err = cudaFuncSetAttribute(k_unit_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = cudaFuncSetAttribute(k_solve_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   count_launch(c);
-  k_unit_solve<float><<<cdiv((long long)nsmp * 5, 4), 128, smem, c->stream>>>(n, nblk, LS, lsstride, npad, rowperm,
-                                                                              mat, node, nsmp * 5, out);
+  k_solve_cols<<<(unsigned)cdiv((long long)npairs * n, 4), 128, smem, c->stream>>>(
+      n, nblk, c->Sls32, ls_stride(G), ls_npad(G), c->rowperm, Scm, n1, pb, pm, npairs, X);
   return cudaGetLastError();
 }
 

@@ -287,6 +287,8 @@ struct sc_ctx {
   bool packed = false;     // packed blocks match the assembled Jacobian
   // learned correction of the block-Jacobi preconditioner (mixed arm)
   std::vector<int> l_face, l_mirror;  // per boundary position: face, co-located position
+  std::vector<int> l_nfaces;          // per boundary position: number of element faces containing the node
+  int* d_lnfaces = nullptr;
   int *d_lface = nullptr, *d_lmirror = nullptr;
   float *Sdiag = nullptr, *Cpl = nullptr;  // [K nbn][25]: [S_ee]_kk, S_(k,k')
   float *Feat = nullptr, *Snorm = nullptr, *Ynet = nullptr, *Hbuf = nullptr, *Ck = nullptr, *Wbias = nullptr;
@@ -406,8 +408,6 @@ void build_packed_pattern(sc_ctx* c);
 long long solve_layout_stride(const Geo& G);
 cudaError_t factor_batch32(sc_ctx* c, float* A, int n, int lda, long long stride, int batch, int* piv, int* rowperm,
                            float* LS, int* status);
-cudaError_t unit_solve32(sc_ctx* c, int n, const float* LS, long long lsstride, const int* rowperm, const int* mat,
-                         const int* node, int nsmp, float* out);
 void build_learned_tables(sc_ctx* c);
 void build_explicit_tables(sc_ctx* c);
 cudaError_t upload_explicit_tables(sc_ctx* c);
@@ -460,4 +460,8 @@ cudaError_t precond_rb(sc_ctx* c, const double* v, double* z);
 cudaError_t precond_rb32(sc_ctx* c, const double* v, double* z, float* zf);
 cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale);
 cudaError_t gather_black_see(sc_ctx* c, const float* See);
+// X[p] = S_mm^-1 S[m rows, b cols] (nb x nb, column j contiguous) for pairs (b, m), from the
+// dense S stored column by column
+cudaError_t solve_columns32(sc_ctx* c, const double* Scm, long long n1, const int* pb, const int* pm, int npairs,
+                            float* X);
 }  // namespace sc

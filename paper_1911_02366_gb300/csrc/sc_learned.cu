@@ -1,15 +1,23 @@
-// Learned correction of the block-Jacobi preconditioner of the condensed system (not in
-// the paper; its GMRES runs on S x_b = g of Sec. 2.2, eq. SC_step1).  For boundary node
-// k of element e, with f the lowest-index face of e containing k (order -x, +x, -y, +y,
-// -z, +z), n the neighbour across f and k' the node of n at the same point:
-//   features (64): q_k over free-stream scales | [S_ee]_kk / ||.||_F | S_(k,k') / ||.||_F |
-//                  (Ma, Re / 1000, dt c_inf / h, N) | 0 0 0 0 0
-//   correction    C_k = net(features) / ||[S_ee]_kk||_F, preconditioner S_ee^-1 + C_k
-//   target        [S_patch^-1]_kk - [S_ee^-1]_kk, S_patch = S on the boundary dofs of e, n.
+// Learned correction of the red-black block sweep of the condensed system (not in the
+// paper; its GMRES runs on S x_b = g of Sec. 2.2, eq. SC_step1).  For boundary node k of a
+// black element b (checkerboard colouring, ex + ey + ez odd), with f the lowest-index face of
+// b containing k (order -x, +x, -y, +y, -z, +z), n the neighbour across f and k' the node of n
+// at the same point:
+//   features (64): q_k over free-stream scales | [S_bb]_kk / ||.||_F | S_(k,k') / ||.||_F |
+//                  (Ma, Re / 1000, dt c_inf / h, N) | (faces of b containing k) / 3 | 0 0 0 0
+//   correction    C_k = net(features) ||[S_bb]_kk||_F, added to the diagonal node block k of
+//                  S_bb before it is factorised for the black half of the sweep
+//   target        C*_k / ||[S_bb]_kk||_F with C*_k = -(1/2) sum_{red m} [S_bm S_mm^-1 S_mb]_kk:
+//                  half the node-diagonal part of what eliminating the red neighbours adds to
+//                  the black block (the whole of it over-corrects: the off-diagonal node
+//                  blocks it leaves out would have balanced it).
 // The coupling block of S between k and k' has three parts (no other element reaches a
-// boundary row of e through its interior):
+// boundary row of b through its interior):
 //   S_(k,k') = A_bb[k,k'] - A_bi,e[k,:] A_ii,e^-1 A_ib[e_int, k'] - A_bi[k, n_int] Y_n[:, k']
 // with Y_n = A_ii,n^-1 A_ib,n (kept transposed by the mixed condensation).
+#include <algorithm>
+#include <vector>
+
 #include <cuda_bf16.h>
 
 #include "sc_internal.cuh"
@@ -132,7 +140,8 @@ __device__ __forceinline__ void put_unit(float* dst, const float* src, float* no
 
 __global__ void k_learned_features(Geo G, const double* __restrict__ Q, const int* __restrict__ iperm,
                                    const float* __restrict__ Sdiag, const float* __restrict__ Cpl, float4 scal,
-                                   float e_inf, float* __restrict__ F, float* __restrict__ snorm) {
+                                   float e_inf, const int* __restrict__ nfaces, float* __restrict__ F,
+                                   float* __restrict__ snorm) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= G.K * G.nbn) return;
   const int e = s / G.nbn, a = s % G.nbn;
@@ -143,7 +152,8 @@ __global__ void k_learned_features(Geo G, const double* __restrict__ Q, const in
   put_unit(f + 5, Sdiag + (size_t)s * 25, snorm + s);
   put_unit(f + 30, Cpl + (size_t)s * 25, nullptr);
   f[55] = scal.x; f[56] = scal.y; f[57] = scal.z; f[58] = scal.w;
-  for (int i = 59; i < 64; ++i) f[i] = 0.f;
+  f[59] = (float)__ldg(nfaces + a) * (1.0f / 3.0f);
+  for (int i = 60; i < 64; ++i) f[i] = 0.f;
 }
 
 __global__ void k_set_unit(double* x, size_t n, long long on, long long off) {
@@ -153,26 +163,31 @@ __global__ void k_set_unit(double* x, size_t n, long long on, long long off) {
   (void)n;
 }
 
-// Patch matrix of (e, face f): S on [boundary dofs of e | boundary dofs of n], FP32,
-// from the dense S stored column by column.
-__global__ void k_gather_patch(int nb, long long n1, const double* __restrict__ Scm, const int* __restrict__ pe,
-                               const int* __restrict__ pn, float* __restrict__ P) {
-  const int pidx = blockIdx.y, m = 2 * nb;
-  const long long e0 = (long long)pe[pidx] * nb, n0 = (long long)pn[pidx] * nb;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)m * m;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(t / m), cc = (int)(t % m);
-    const long long gr = r < nb ? e0 + r : n0 + r - nb;
-    const long long gc = cc < nb ? e0 + cc : n0 + cc - nb;
-    P[(long long)pidx * m * m + t] = (float)Scm[gc * n1 + gr];
-  }
-}
+// Share of the node-diagonal Schur correction the target keeps.
+constexpr float kLearnedDamping = 0.5f;
 
-__global__ void k_targets(int nsmp, const float* __restrict__ Pinv, const float* __restrict__ Sinv,
-                          const float* __restrict__ snorm, float* __restrict__ T) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nsmp * 25) return;
-  T[t] = (Pinv[t] - Sinv[t]) * snorm[t / 25];
+// T[s] = -kLearnedDamping sum_{pairs p of b} [S_bm X_p]_(k,k) / ||[S_bb]_kk||_F for every sample
+// s = (black element b, boundary node a); red samples get zero.  X_p = S_mm^-1 S_mb with
+// column j contiguous (k_solve_cols); S column by column with n1 rows.
+__global__ void k_black_targets(int nb, int nbn, long long n1, const double* __restrict__ Scm,
+                                const float* __restrict__ X, const int* __restrict__ bidx,
+                                const int* __restrict__ pptr, const int* __restrict__ pm,
+                                const float* __restrict__ snorm, int nsmp, float* __restrict__ T) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nsmp * 25) return;
+  const int smp = (int)(t / 25), r = (int)((t / 5) % 5), l = (int)(t % 5);
+  const int e = smp / nbn, a = smp % nbn;
+  const int bi = __ldg(bidx + e);
+  if (bi < 0) { T[t] = 0.f; return; }
+  const long long row = (long long)e * nb + 5 * a + r;
+  double acc = 0.0;
+  for (int p = __ldg(pptr + bi); p < __ldg(pptr + bi + 1); ++p) {
+    const long long m0 = (long long)__ldg(pm + p) * nb;
+    const float* xc = X + ((long long)p * nb + 5 * a + l) * nb;
+    for (int i = 0; i < nb; ++i) acc += Scm[(m0 + i) * n1 + row] * (double)xc[i];
+  }
+  const float sn = snorm[smp];
+  T[t] = sn > 0.f ? (float)(-(double)kLearnedDamping * acc) / sn : 0.f;
 }
 
 // C_k = y_k ||[S_ee]_kk||_F (the network works on blocks scaled by the node's own block)
@@ -194,6 +209,7 @@ void build_learned_tables(sc_ctx* c) {
   const int p = G.p, N = G.N;
   c->l_face.assign(G.nbn, 0);
   c->l_mirror.assign(G.nbn, 0);
+  c->l_nfaces.assign(G.nbn, 0);
   for (int a = 0; a < G.nbn; ++a) {
     const int m = c->iperm[G.nin + a];
     int cc[3] = {m % p, (m / p) % p, m / (p * p)};
@@ -203,6 +219,7 @@ void build_learned_tables(sc_ctx* c) {
       else if (cc[d] == N) f = 2 * d + 1;
     }
     c->l_face[a] = f;
+    c->l_nfaces[a] = (cc[0] == 0 || cc[0] == N) + (cc[1] == 0 || cc[1] == N) + (cc[2] == 0 || cc[2] == N);
     cc[f / 2] = N - cc[f / 2];
     const int mm = cc[0] + p * (cc[1] + p * cc[2]);
     c->l_mirror[a] = c->perm[mm] - G.nin;
@@ -234,7 +251,7 @@ cudaError_t learned_features(sc_ctx* c, float* F, float* snorm) {
   const float4 scal = make_float4((float)Ma, (float)(c->cfg.Re / 1000.0), (float)(G.dt * (1.0 / Ma) / G.h),
                                   (float)G.N);
   k_learned_features<<<(nsmp + 255) / 256, 256, 0, c->stream>>>(G, c->Q, c->d_iperm, c->Sdiag, c->Cpl, scal, e_inf,
-                                                                F, snorm);
+                                                                c->d_lnfaces, F, snorm);
   return cudaGetLastError();
 }
 
@@ -268,27 +285,36 @@ sc_status sc_learned_targets(sc_ctx* c, float* T) {
   if (!c->condensed || c->cfg.precision != SC_PREC_MIXED || !c->Sdiag_valid) return SC_ERR_STATE;
   const Geo& G = c->G;
   const long long n1 = (long long)G.K * G.nb;
-  const int nsmp = G.K * G.nbn, m = 2 * G.nb, np = 6 * G.K;
-  if ((double)n1 * n1 * 8.0 > 16e9) return SC_ERR_ARG;  // training meshes only
+  const int nsmp = G.K * G.nbn;
+  if ((double)n1 * n1 * 8.0 > 40e9) return SC_ERR_ARG;  // training meshes only
+  // pairs (black element, distinct red neighbour), grouped by black element
+  std::vector<int> hb, hm, hptr(1, 0), hbidx(G.K, -1);
+  for (int i = c->n_red; i < G.K; ++i) {
+    const int b = c->colour_list[i];
+    hbidx[b] = i - c->n_red;
+    std::vector<int> seen;
+    for (int sl = 0; sl < 18; ++sl) {
+      const int m = c->nbr[(size_t)b * 18 + sl];
+      const int ex = m % G.n, ey = (m / G.n) % G.n, ez = m / (G.n * G.n);
+      if (((ex + ey + ez) & 1) != 0 || std::find(seen.begin(), seen.end(), m) != seen.end()) continue;
+      seen.push_back(m);
+      hb.push_back(b); hm.push_back(m);
+    }
+    hptr.push_back((int)hb.size());
+  }
+  const int npairs = (int)hb.size();
   cudaStream_t st = c->stream;
   double* Scm = nullptr;
-  float *P = nullptr, *LSp = nullptr, *Pinv = nullptr, *Sinv = nullptr, *F = nullptr, *sn = nullptr;
-  int *piv = nullptr, *rperm = nullptr, *pe = nullptr, *pn = nullptr, *mat = nullptr, *node = nullptr;
-  const int nblk = (m + 31) / 32, npad = (m + 3) & ~3;
-  const long long lss = (long long)nblk * 32 * npad;
+  float *X = nullptr, *F = nullptr, *sn = nullptr;
+  int *pb = nullptr, *pm = nullptr, *pptr = nullptr, *bidx = nullptr;
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(cudaMalloc(&Scm, (size_t)n1 * n1 * sizeof(double)));
-  A(cudaMalloc(&P, (size_t)np * m * m * sizeof(float)));
-  A(cudaMalloc(&LSp, (size_t)np * lss * sizeof(float)));
-  A(cudaMalloc(&piv, (size_t)np * m * sizeof(int)));
-  A(cudaMalloc(&rperm, (size_t)np * m * sizeof(int)));
-  A(cudaMalloc(&Pinv, (size_t)nsmp * 25 * sizeof(float)));
-  A(cudaMalloc(&Sinv, (size_t)nsmp * 25 * sizeof(float)));
+  A(cudaMalloc(&X, (size_t)std::max(npairs, 1) * G.nb * G.nb * sizeof(float)));
   A(cudaMalloc(&F, (size_t)nsmp * 64 * sizeof(float)));
   A(cudaMalloc(&sn, (size_t)nsmp * sizeof(float)));
-  A(cudaMalloc(&pe, np * sizeof(int))); A(cudaMalloc(&pn, np * sizeof(int)));
-  A(cudaMalloc(&mat, nsmp * sizeof(int))); A(cudaMalloc(&node, nsmp * sizeof(int)));
+  A(cudaMalloc(&pb, std::max(npairs, 1) * sizeof(int))); A(cudaMalloc(&pm, std::max(npairs, 1) * sizeof(int)));
+  A(cudaMalloc(&pptr, hptr.size() * sizeof(int))); A(cudaMalloc(&bidx, G.K * sizeof(int)));
   sc_status status = SC_OK;
   if (e != cudaSuccess) { status = SC_ERR_OOM; goto done; }
   {
@@ -301,39 +327,26 @@ sc_status sc_learned_targets(sc_ctx* c, float* T) {
       A(sc::cond_interior32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf));
       A(sc::cond_boundary32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf, Scm + jcol * n1));
     }
-    // patches (e, f) and the samples' patch / node indices
-    std::vector<int> hpe(np), hpn(np), hmat(nsmp), hnode(nsmp);
-    for (int el = 0; el < G.K; ++el)
-      for (int f = 0; f < 6; ++f) { hpe[el * 6 + f] = el; hpn[el * 6 + f] = c->nbr[(size_t)el * 18 + f]; }
-    for (int el = 0; el < G.K; ++el)
-      for (int a = 0; a < G.nbn; ++a) { hmat[el * G.nbn + a] = el * 6 + c->l_face[a]; hnode[el * G.nbn + a] = a; }
-    A(cudaMemcpyAsync(pe, hpe.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-    A(cudaMemcpyAsync(pn, hpn.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-    A(cudaMemcpyAsync(mat, hmat.data(), nsmp * sizeof(int), cudaMemcpyHostToDevice, st));
-    A(cudaMemcpyAsync(node, hnode.data(), nsmp * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (e == cudaSuccess) {
-      k_gather_patch<<<dim3(256, np), 256, 0, st>>>(G.nb, n1, Scm, pe, pn, P);
-      A(cudaGetLastError());
+    if (npairs > 0) {
+      A(cudaMemcpyAsync(pb, hb.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
+      A(cudaMemcpyAsync(pm, hm.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
     }
-    A(sc::factor_batch32(c, P, m, m, (long long)m * m, np, piv, rperm, LSp, c->d_status));
-    A(sc::unit_solve32(c, m, LSp, lss, rperm, mat, node, nsmp, Pinv));
-    // [S_ee^-1]_kk from the condensation's own factors
-    std::vector<int> hself(nsmp);
-    for (int el = 0; el < G.K; ++el)
-      for (int a = 0; a < G.nbn; ++a) hself[el * G.nbn + a] = el;
-    A(cudaMemcpyAsync(mat, hself.data(), nsmp * sizeof(int), cudaMemcpyHostToDevice, st));
-    A(sc::unit_solve32(c, G.nb, c->Sls32, sc::solve_layout_stride(G), c->rowperm, mat, node, nsmp, Sinv));
+    A(cudaMemcpyAsync(pptr, hptr.data(), hptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    A(cudaMemcpyAsync(bidx, hbidx.data(), G.K * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (npairs > 0) A(sc::solve_columns32(c, Scm, n1, pb, pm, npairs, X));
     A(sc::learned_features(c, F, sn));
     if (e == cudaSuccess) {
-      k_targets<<<(nsmp * 25 + 255) / 256, 256, 0, st>>>(nsmp, Pinv, Sinv, sn, T);
+      count_launch(c);
+      const long long nt = (long long)nsmp * 25;
+      k_black_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(G.nb, G.nbn, n1, Scm, X, bidx, pptr, pm, sn,
+                                                                    nsmp, T);
       A(cudaGetLastError());
     }
     A(cudaStreamSynchronize(st));
     if (e != cudaSuccess) status = SC_ERR_CUDA;
   }
 done:
-  cudaFree(Scm); cudaFree(P); cudaFree(LSp); cudaFree(piv); cudaFree(rperm); cudaFree(Pinv); cudaFree(Sinv);
-  cudaFree(F); cudaFree(sn); cudaFree(pe); cudaFree(pn); cudaFree(mat); cudaFree(node);
+  cudaFree(Scm); cudaFree(X); cudaFree(F); cudaFree(sn); cudaFree(pb); cudaFree(pm); cudaFree(pptr); cudaFree(bidx);
   return status;
 }
 
