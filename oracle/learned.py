@@ -1,9 +1,11 @@
-"""Learned correction of the block-Jacobi preconditioner (test infrastructure only).
+"""Learned correction of the red-black block sweep (test infrastructure only).
 
 Not in the paper: the condensed system S x_b = g of Sec. 2.2 (eq. SC_step1) is solved by
-GMRES preconditioned with the inverses of the element blocks S_ee; a small network adds
-a 5 x 5 correction to the diagonal node blocks of each S_ee^{-1}.  Everything here is a
-plain FP64 restatement, written against the dense condensed matrix S of the oracle.
+GMRES preconditioned with one forward block sweep over the checkerboard colouring of the
+elements (red: ex + ey + ez even): z_r = S_rr^{-1} v_r, then z_b = D_b^{-1} (v_b - sum S_bm z_m).
+A small network corrects the black blocks, D_b = S_bb + C_b with C_b block-diagonal over the
+5 x 5 node blocks.  Everything here is a plain FP64 restatement, written against the dense
+condensed matrix S of the oracle.
 
 Definitions (one sample per element e and boundary node k of e; boundary nodes in the
 natural order of the oracle's condensed system, 5 variables per node):
@@ -11,11 +13,14 @@ natural order of the oracle's condensed system, 5 variables per node):
 * face of k: the lowest-index face containing k in the order -x, +x, -y, +y, -z, +z;
   n = the face neighbour of e across it; k' = the node of n at the same point (k with
   its index normal to the face mirrored, 0 <-> N);
-* S_patch = S restricted to the boundary dofs of e and n;
-* target  C*_k = [S_patch^{-1}]_kk - [S_ee^{-1}]_kk;
+* exact correction of a black element b: C*_k = -(1/2) sum_{red m} [S_bm S_mm^{-1} S_mb]_kk,
+  half the node-diagonal part of what eliminating the red neighbours adds to S_bb (the
+  whole of it over-corrects: the off-diagonal node blocks it leaves out balance it);
+* target = C*_k / ||[S_ee]_kk||_F for black samples, 0 for red ones;
 * features (64): q_k over free-stream scales (5); [S_ee]_kk and [S]_(k, k'), each over
-  its Frobenius norm (25 + 25); (Ma, Re / 1000, dt c_inf / h, N) (4); 5 zeros;
-* the network predicts the target times ||[S_ee]_kk||_F (a dimensionless 5 x 5 block);
+  its Frobenius norm (25 + 25); (Ma, Re / 1000, dt c_inf / h, N) (4); the number of faces
+  of e containing k over 3 (1); 4 zeros;
+* the network predicts the target (a dimensionless 5 x 5 block): C_k = y_k ||[S_ee]_kk||_F;
 * network: 64 -> 256 -> 256 -> 25, ReLU after the two hidden layers;
 * loss: mean over samples of ||y - t||^2 / (||t||^2 + eps) (squared relative Frobenius
   error of the scaled correction).
@@ -77,6 +82,16 @@ def _unit(b: np.ndarray) -> np.ndarray:
     return b / nrm if nrm > 0 else np.zeros_like(b)
 
 
+def node_face_count(N: int, m: int) -> int:
+    """Number of element faces containing boundary node m (1 on a face, 2 on an edge, 3 at a corner)."""
+    p = N + 1
+    c = (m % p, (m // p) % p, m // (p * p))
+    return sum(1 for d in range(3) if c[d] in (0, N))
+
+
+LEARNED_DAMPING = 0.5
+
+
 def features_and_targets(S: np.ndarray, Q: np.ndarray, n: int, N: int, Ma: float, Re: float, dt: float,
                          L: float = 2.0 * np.pi, gamma: float = 1.4):
     """Features [K*nbn, 64], scaled targets [K*nbn, 25] and the block norms ||[S_ee]_kk||_F.
@@ -84,6 +99,7 @@ def features_and_targets(S: np.ndarray, Q: np.ndarray, n: int, N: int, Ma: float
     S: dense condensed matrix (K*nb x K*nb) in the element-major condensed order.
     Q: state [K, (N+1)^3, 5].
     """
+    from .linalg import black_schur_correction
     Bn = boundary_nodes(N)
     nbn = len(Bn)
     nb = 5 * nbn
@@ -95,8 +111,7 @@ def features_and_targets(S: np.ndarray, Q: np.ndarray, n: int, N: int, Ma: float
     F = np.zeros((K * nbn, N_IN))
     T = np.zeros((K * nbn, N_OUT))
     snorm = np.zeros(K * nbn)
-    Sinv_ee = [np.linalg.inv(S[e * nb:(e + 1) * nb, e * nb:(e + 1) * nb]) for e in range(K)]
-    patch_inv = {}
+    C = black_schur_correction(S, n)
     for e in range(K):
         for a, m in enumerate(Bn):
             f = node_face(N, int(m))
@@ -111,14 +126,16 @@ def features_and_targets(S: np.ndarray, Q: np.ndarray, n: int, N: int, Ma: float
             F[s, 5:30] = _unit(Skk).reshape(-1)
             F[s, 30:55] = _unit(Skc).reshape(-1)
             F[s, 55:59] = scal
-            if (e, f) not in patch_inv:
-                ids = np.concatenate([np.arange(e * nb, (e + 1) * nb), np.arange(nbe * nb, (nbe + 1) * nb)])
-                patch_inv[(e, f)] = np.linalg.inv(S[np.ix_(ids, ids)])
-            Pinv = patch_inv[(e, f)]
-            Cstar = Pinv[5 * a:5 * a + 5, 5 * a:5 * a + 5] - Sinv_ee[e][5 * a:5 * a + 5, 5 * a:5 * a + 5]
+            F[s, 59] = node_face_count(N, int(m)) / 3.0
             snorm[s] = np.linalg.norm(Skk)
-            T[s] = (Cstar * snorm[s]).reshape(-1)
+            T[s] = (LEARNED_DAMPING * C[s] / snorm[s]).reshape(-1)
     return F, T, snorm
+
+
+def black_mask(n: int, N: int) -> np.ndarray:
+    """True for the samples of black elements (the ones the correction applies to)."""
+    from .linalg import checkerboard
+    return np.repeat(checkerboard(n) == 1, len(boundary_nodes(N)))
 
 
 # ---- the network -------------------------------------------------------------------
@@ -187,16 +204,9 @@ def adam_step(P, g, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         P[k] -= lr * mh / (np.sqrt(vh) + eps)
 
 
-def corrected_apply(S: np.ndarray, y: np.ndarray, snorm: np.ndarray, v: np.ndarray, K: int, nb: int):
-    """P v = S_ee^{-1} v_e + C_k v_k with C_k = y_k / ||[S_ee]_kk||_F, per element."""
-    out = np.empty_like(v)
-    nbn = nb // 5
-    for e in range(K):
-        sl = slice(e * nb, (e + 1) * nb)
-        z = np.linalg.solve(S[sl, sl], v[sl])
-        for a in range(nbn):
-            s = e * nbn + a
-            C = y[s].reshape(5, 5) / snorm[s]
-            z[5 * a:5 * a + 5] += C @ v[e * nb + 5 * a:e * nb + 5 * a + 5]
-        out[sl] = z
-    return out
+def corrected_apply(S: np.ndarray, y: np.ndarray, snorm: np.ndarray, v: np.ndarray, n: int):
+    """The learned sweep: red-black with D_b = S_bb + C, C_k = y_k ||[S_ee]_kk||_F on the black
+    elements' diagonal node blocks."""
+    from .linalg import corrected_black_blocks, red_black_apply
+    C = (y.reshape(-1, 5, 5) * snorm[:, None, None])
+    return red_black_apply(S, n, v, black_blocks=corrected_black_blocks(S, n, C))

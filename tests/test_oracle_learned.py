@@ -83,17 +83,6 @@ def test_first_adam_step_moves_each_parameter_by_lr_times_sign():
     assert np.allclose(P["w"], expect, rtol=0, atol=1e-15)
 
 
-def test_patch_inverse_block_equals_schur_complement_inverse():
-    """[S_patch^-1]_ee = (S_ee - S_en S_nn^-1 S_ne)^-1 (block elimination)."""
-    rng = np.random.default_rng(9)
-    m = 12
-    A = rng.standard_normal((2 * m, 2 * m)) + 6 * np.eye(2 * m)
-    Pinv = np.linalg.inv(A)
-    See, Sen, Sne, Snn = A[:m, :m], A[:m, m:], A[m:, :m], A[m:, m:]
-    T = See - Sen @ np.linalg.solve(Snn, Sne)
-    assert np.allclose(Pinv[:m, :m], np.linalg.inv(T), atol=1e-12)
-
-
 def _mesh_S(n, N, cfl=10.0):
     Q, dt = I.tgv_state(n, N, cfl=cfl)
     p = O.Params(n=n, N=N, dt=dt, bdf=1)
@@ -116,18 +105,45 @@ def test_targets_vanish_without_coupling_and_features_are_normalised():
     assert np.allclose(np.linalg.norm(F[:, 5:30], axis=1), 1.0)
     assert np.allclose(np.linalg.norm(F[:, 30:55], axis=1), 1.0)
     assert np.allclose(F[:, 55:59], [0.1, 1.6, dt * 10.0 / (np.pi), 2.0])
-    assert np.all(F[:, 59:] == 0)
-    assert np.max(np.abs(T)) > 0
+    # nodes of a face, an edge, a corner: 1, 2 or 3 faces (N = 2: 6 face, 12 edge, 8 corner nodes)
+    nf = np.round(F[:len(LN.boundary_nodes(N)), 59] * 3).astype(int)
+    assert sorted(np.bincount(nf)[1:]) == [6, 8, 12]
+    assert np.all(F[:, 60:] == 0)
+    black = LN.black_mask(n, N)
+    assert np.max(np.abs(T[~black])) == 0 and np.max(np.abs(T[black])) > 0
 
 
-def test_corrected_apply_without_correction_is_block_jacobi():
+def test_targets_are_half_the_node_diagonal_schur_correction():
+    """Black targets times ||[S_ee]_kk||_F: half the node blocks of -sum_red S_bm S_mm^-1 S_mb,
+    here formed through the exact inverse of each two-element patch [[S_bb, S_bm], [S_mb, S_mm]]
+    (block elimination: S_bb - S_bm S_mm^-1 S_mb = inverse of the patch inverse's bb block)."""
+    n, N = 2, 2
+    Q, dt, S = _mesh_S(n, N)
+    nb = 5 * len(LN.boundary_nodes(N))
+    nbn = nb // 5
+    F, T, sn = LN.features_and_targets(S, Q, n, N, 0.1, 1600.0, dt)
+    col = O.checkerboard(n)
+    blk = lambda e: slice(e * nb, (e + 1) * nb)
+    for b in np.where(col == 1)[0][:3]:
+        corr = np.zeros((nb, nb))
+        for m in np.where(col == 0)[0]:
+            if not np.any(S[blk(b), blk(m)]):
+                continue
+            ids = np.r_[np.arange(b * nb, (b + 1) * nb), np.arange(m * nb, (m + 1) * nb)]
+            Pinv = np.linalg.inv(S[np.ix_(ids, ids)])
+            corr += np.linalg.inv(Pinv[:nb, :nb]) - S[blk(b), blk(b)]
+        for a in range(nbn):
+            s = b * nbn + a
+            ref = 0.5 * corr[5 * a:5 * a + 5, 5 * a:5 * a + 5] / sn[s]
+            assert np.allclose(T[s].reshape(5, 5), ref, rtol=0, atol=1e-10 * max(1.0, np.max(np.abs(ref))))
+
+
+def test_corrected_apply_without_correction_is_the_red_black_sweep():
     n, N = 2, 2
     Q, dt, S = _mesh_S(n, N)
     nb = 5 * len(LN.boundary_nodes(N))
     K = n ** 3
     v = np.random.default_rng(1).standard_normal(S.shape[0])
     y = np.zeros((K * nb // 5, LN.N_OUT))
-    z = LN.corrected_apply(S, y, np.ones(K * nb // 5), v, K, nb)
-    for e in range(K):
-        sl = slice(e * nb, (e + 1) * nb)
-        assert np.allclose(S[sl, sl] @ z[sl], v[sl])
+    z = LN.corrected_apply(S, y, np.ones(K * nb // 5), v, n)
+    assert np.allclose(z, O.red_black_apply(S, n, v), rtol=0, atol=1e-12)
