@@ -228,6 +228,7 @@ def run_ours(args, world, rank, local):
     assemble_ms = sum(ev[0].elapsed_time(ev[1]) for ev in marks)
     solve_ms = sum(ev[1].elapsed_time(ev[2]) for ev in marks)
     n_prof, prof_ms = ctx.sc_profile_read()
+    prof_elems = ctx.sc_profile_elements()
     ctx.sc_profile_kernel(-1)
     total_ms = gather_max(world, total_ms)
     worst = max(s["rel_residual"] for s in stats)
@@ -247,7 +248,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     e2e_s = gather_max(world, time.perf_counter() - t0)
 
-    flops, bytes_ = ctx.sc_kernel_work(dominant)
+    flops, bytes_ = ctx.sc_kernel_work(dominant)  # a launch over all K elements
+    K_all = ctx.sc_sizes()[0]
+    per_launch = prof_elems / max(n_prof, 1)  # the red-black sweep's launches cover one colour
+    flops, bytes_ = flops * per_launch / K_all, bytes_ * per_launch / K_all
     avg_ms = prof_ms / max(n_prof, 1)
     peaks = measured_peaks()
     if args.arm == "fp64":
@@ -257,11 +261,13 @@ def run_ours(args, world, rank, local):
         roof = {"bound": "hbm", "achieved": bytes_ / (avg_ms * 1e-3) / 1e9,
                 "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = TRAFFIC.get((args.arm, dominant)) if (W["n"], W["N"]) == (16, 4) else None
+    roof["traffic"] = (TRAFFIC.get((args.arm, dominant)) * per_launch / K_all
+                       if (W["n"], W["N"]) == (16, 4) and TRAFFIC.get((args.arm, dominant)) else None)
     roof["kernel"] = {sc.SC_KERNEL_LU_SOLVE: "k_lu_solve", sc.SC_KERNEL_COND_BOUNDARY: "k_cond_boundary",
                       sc.SC_KERNEL_EXPLICIT_APPLY: "k_explicit_w"}[dominant]
     roof["launches_timed"] = n_prof
     roof["avg_launch_ms"] = avg_ms
+    roof["elements_per_launch"] = per_launch
 
     value = world * dofs * args.steps / (total_ms * 1e-3)
     K_, ne_, ni_, nb_ = ctx.sc_sizes()

@@ -80,12 +80,11 @@ typedef struct {
   double inner_tol;      /* mixed arm: relative tolerance of each inner condensed solve */
   int tensor_cores;      /* mixed arm: 1 = element Schur products and the LU trailing updates
                             of S_ee on the TF32 tensor cores (tcgen05), 0 = FP32 CUDA cores */
-  double learned_min_reduction;  /* SC_PC_LEARNED: block Jacobi judges the learned sweep at the
-                            start of each condensed solve (one preconditioned step from the
-                            normalised residual v: the learned sweep is kept only if its
-                            ||v - S P v|| is no larger than block Jacobi's), and a GMRES restart
-                            cycle that reduces the condensed residual by less than this factor
-                            switches the rest of the solve to block Jacobi (10) */
+  double learned_min_reduction;  /* SC_PC_LEARNED: a GMRES restart cycle that reduces the
+                            condensed residual by less than this factor switches the rest of
+                            the solve to block Jacobi, the fallback (4: about block Jacobi's own
+                            average reduction per 30-iteration cycle on the 16^3, N = 4 Taylor-Green
+                            system, 357 iterations to 1e-8) */
   int factor_fp16;       /* mixed arm: 1 = keep a copy of the block-Jacobi factors in FP16 for the
                             GMRES preconditioner (FP32 arithmetic; used only when every entry is
                             within the FP16 range, else the FP32 copy), 0 = FP32 only (default 0:
@@ -117,7 +116,8 @@ typedef struct {
 } sc_solve_stats;
 
 /* Fill *cfg with the defaults listed above (Re = 1600, Ma = 0.1, FP64, block Jacobi,
-   GMRES(30), 4000 iterations, rel_tol 1e-8, tensor_cores 1).  Never fails for a non-null cfg. */
+   GMRES(30), 4000 iterations, rel_tol 1e-8, tensor_cores 1, learned_min_reduction 4).  Never fails
+   for a non-null cfg. */
 sc_status sc_default_config(sc_config* cfg);
 
 /* Create a context that enqueues all work on `cuda_stream` (a cudaStream_t, or NULL
@@ -248,6 +248,29 @@ sc_status sc_gemm_tf32(int batch, int M, int N, int K, float alpha, const float*
                        int transA, const float* B, long long strideB, int ldb, int transB, float beta, float* C,
                        long long strideC, int ldc, void* cuda_stream);
 
+/* ---- Direct solves by dense LU (Sec. 4, Tables tab:Advantages and tab:Advantages2) ----
+   The paper factorises the Jacobian once with a direct solver, either the global A or the
+   condensed S of eq. SC_step1, and compares the factorisation and per-solve times of the two.
+   sc_direct_factor forms the dense matrix on the GPU (A from the element blocks and the
+   neighbour couplings; S column by column through the condensed operator, S e_j) and
+   factorises it, P M = L U with partial pivoting (the first row of largest |a| wins), right
+   looking in 64-column panels; the trailing updates run on the TF32 tensor cores on the
+   mixed arm with tensor_cores, else on the CUDA cores (FP64 on the FP64 arm).  The mixed arm
+   keeps FP32 factors.  ms_form / ms_factor (or NULL): device milliseconds of forming and of
+   factorising.  The factors (n^2 values, n = K ne or K nb; SC_ERR_ARG beyond 64 GB) stay in
+   the context until the next sc_direct_factor or sc_set_mesh: later assemblies of another
+   state leave them as they are (a frozen Jacobian).  SC_ERR_SINGULAR_BLOCK on a zero pivot. */
+enum { SC_DIRECT_GLOBAL = 0, SC_DIRECT_CONDENSED = 1 };
+sc_status sc_direct_factor(sc_ctx* ctx, int which, double* ms_form, double* ms_factor);
+
+/* Solve A dQ = B (B = -R(Q) of the last sc_assemble) with the factors: global, or condensed
+   right-hand side (eq. SC_step1), triangular solves with the factors of S, back-substitution
+   (eq. SC_step2).  Sweeps x += M^-1 (B - A x) with the FP64 global residual until rel_tol:
+   at most 2 on the FP64 arm, max_refine on the mixed arm (FP32 factors).  stats: refinements
+   = sweeps, rel_residual, ms_gmres = the triangular solves, ms_rhs = condensed right-hand
+   sides and back-substitutions.  dQ as in sc_solve. */
+sc_status sc_direct_solve(sc_ctx* ctx, double* dQ, int on_device, sc_solve_stats* stats);
+
 /* ---- Time marching to a steady state (Sec. 4, numerical example) ------------------
    The paper drives its discretisation to a steady state, ||M^-1 H(Q)||_inf <= tol (M the
    diagonal Gauss-Lobatto mass matrix, H the spatial operator of eq. DGSEMsystem), with an
@@ -272,15 +295,16 @@ sc_status sc_explicit_march(sc_ctx* ctx, double cfl, double dfl, int nsteps, dou
 
 /* nsteps BDF1 steps of size dt, each one Newton-linearised solve
    A dQ = -R(Q) = -H(Q) (eq. NeqtonEq at the step's start, where Q equals the history), solved
-   by sc_solve with the context's configuration (static condensation, FP64 or mixed arm),
-   Q <- Q + dQ.  The Jacobian is assembled and condensed at the first step and then every
-   jacobian_every steps (0 = once: the frozen Jacobian of the paper's experiment); the other
-   steps only evaluate the residual.  res_hist (host, nsteps + 1 or NULL):
+   by sc_solve with the context's configuration (static condensation, FP64 or mixed arm; direct
+   = -1) or by the dense factors of sc_direct_solve (direct = SC_DIRECT_GLOBAL: LU of A, or
+   SC_DIRECT_CONDENSED: LU of S), Q <- Q + dQ.  The Jacobian is assembled (condensed, factorised)
+   at the first step and then every jacobian_every steps (0 = once: the frozen Jacobian of the
+   paper's experiment); the other steps only evaluate the residual.  res_hist (host, nsteps + 1 or NULL):
    ||M^-1 H||_inf at the start of each step and after the last; ms_hist (host, nsteps + 1 or
    NULL): device milliseconds from the start to the end of each step (ms_hist[0] = 0);
    gmres_iters (host, nsteps or NULL): GMRES iterations of each solve.  A solve that misses
    rel_tol returns its status (SC_ERR_NOT_CONVERGED) and stops the march. */
-sc_status sc_implicit_march(sc_ctx* ctx, double dt, int nsteps, int jacobian_every, double* res_hist,
+sc_status sc_implicit_march(sc_ctx* ctx, double dt, int nsteps, int jacobian_every, int direct, double* res_hist,
                             double* ms_hist, int* gmres_iters);
 
 /* ---- Spectrum and condition-number estimate (Sec. 4, Fig. ConditionNumber) ------
@@ -306,16 +330,18 @@ sc_status sc_spectrum_estimate(sc_ctx* ctx, int which, int m_max, int m_min, dou
    converge. */
 sc_status sc_hessenberg_eigvals(int m, const double* H, double* re, double* im);
 
-/* ---- Learned correction of the block-Jacobi preconditioner ----------------------
+/* ---- Learned correction of the red-black sweep --------------------------------------
    Not in the paper (which preconditions GMRES on the condensed system with point Jacobi,
    Sec. 4): a network maps 64 features of each boundary node k of each element to a 5 x 5
-   correction C_k of the diagonal node blocks of S_ee^-1.  Layout of the parameters
+   correction C_k added to the diagonal node block k of a black element's S_bb before the
+   black half of the red-black sweep factorises it (SC_PC_LEARNED).  Layout of the parameters
    (shared by every call): weights W = [W1 (256 x 64) | W2 (256 x 256) | W3 (25 x 256)],
    row-major, 88,320 values, kept as FP32 masters and as a BF16 copy (IEEE bfloat16 bit
    patterns in uint16_t); biases b = [b1 (256) | b2 (256) | b3 (25)], FP32.  Layers:
    h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3; FP32 arithmetic.  All
-   pointers are device pointers; work is enqueued on cuda_stream and synchronised before
-   return.  SC_ERR_ARG for null pointers or bad sizes, SC_ERR_CUDA for launch failures. */
+   pointers are device pointers unless stated; work is enqueued on cuda_stream and
+   synchronised before return.  SC_ERR_ARG for null pointers or bad sizes, SC_ERR_CUDA for
+   launch failures. */
 
 /* y[n x 25] = net(X[n x 64]).  cache: NULL, or 4 n x 256 floats that receive z1, h1, z2,
    h2 (pre- and post-activations) for sc_mlp_backward; with NULL the call allocates
@@ -339,33 +365,64 @@ sc_status sc_mlp_loss(const float* Y, const float* T, int n, float* dY, float* l
 sc_status sc_mlp_adam(float* W, uint16_t* Wbf16, float* bias, float* gW, float* gb, float* m, float* v, int step,
                       float lr, void* cuda_stream);
 
+/* W16[i] = W[i] rounded to bfloat16 (nearest even), i < n: the BF16 copy of FP32 weights. */
+sc_status sc_mlp_bf16(const float* W, uint16_t* Wbf16, int n, void* cuda_stream);
+
+/* Training loop of the network (the learned correction's counterpart of sc_train_mlp):
+   `epochs` passes of mini-batch Adam over device samples X [n x 64] with targets T [n x 25].
+   Before every pass all n samples are shuffled (Fisher-Yates on a splitmix64 stream seeded
+   by `seed`), so every batch mixes systems, elements and nodes; each batch of `batch` samples
+   (the last may be smaller) runs sc_mlp_forward, sc_mlp_loss, sc_mlp_backward and one
+   sc_mlp_adam step.  W, Wbf16, bias, m, v as for sc_mlp_adam; *step (host) counts the Adam
+   updates and carries on across calls (start at 0).  loss_hist (host, epochs floats, or
+   NULL): mean batch loss of each pass.  The call allocates its batch buffers and frees
+   them before it returns. */
+sc_status sc_mlp_train(float* W, uint16_t* Wbf16, float* bias, float* m, float* v, int* step, const float* X,
+                       const float* T, int n, int epochs, int batch, float lr, uint64_t seed, float* loss_hist,
+                       void* cuda_stream);
+
+/* Network parameter files: the 8 bytes "SCMLP001", the counts 88,320 and 537 (int32), then
+   the FP32 weights W and biases (little endian).  sc_mlp_save writes device W, bias;
+   sc_mlp_load reads them into device W, its BF16 copy and bias (SC_ERR_ARG if the file is
+   missing or not such a file). */
+sc_status sc_mlp_save(const char* path, const float* W, const float* bias);
+sc_status sc_mlp_load(const char* path, float* W, uint16_t* Wbf16, float* bias);
+
+/* Load a saved network into the context as its SC_PC_LEARNED weights (sc_set_learned_weights
+   of the file's parameters). */
+sc_status sc_load_mlp(sc_ctx* ctx, const char* path);
+
 /* Features of the learned correction for every (element e, boundary node k) of the
    condensed system, samples ordered element by element and boundary node by boundary
    node (the condensed order): F[s][64] = q_k over free-stream scales (rho, rho u, rho v,
    rho w over 1, rho E over p_inf/(gamma-1) + 1/2) | [S_ee]_kk / ||.||_F (row-major 5 x 5)
    | S_(k,k') / ||.||_F with k' the node at the same point in the neighbour across the
    lowest-index face of e containing k (order -x,+x,-y,+y,-z,+z) | Ma, Re/1000,
-   dt/(Ma h), N | 0 x 5; snorm[s] = ||[S_ee]_kk||_F.  After sc_condense on the mixed arm
-   (SC_ERR_STATE otherwise).  Device pointers, K * nbn * 64 and K * nbn floats. */
+   dt/(Ma h), N | (faces of e containing k) / 3 | 0 x 4; snorm[s] = ||[S_ee]_kk||_F.  After
+   sc_condense on the mixed arm (SC_ERR_STATE otherwise).  Device pointers, K * nbn * 64 and
+   K * nbn floats. */
 sc_status sc_learned_features(sc_ctx* ctx, float* F, float* snorm);
 
-/* Training targets T[s][25] = ([S_patch^-1]_kk - [S_ee^-1]_kk) ||[S_ee]_kk||_F, S_patch the
-   condensed matrix on the boundary dofs of e and of the neighbour of the features.  Forms
-   the dense condensed matrix column by column with the condensed operator, so only for
-   small meshes ((K nb)^2 doubles <= 16 GB, else SC_ERR_ARG).  After sc_condense on the
-   mixed arm.  Device pointer, K * nbn * 25 floats. */
+/* Training targets T[s][25]: for samples of black elements b (checkerboard colouring,
+   ex + ey + ez odd), C*_k / ||[S_bb]_kk||_F with C*_k = -(1/2) sum over the red neighbours m
+   of [S_bm S_mm^-1 S_mb]_kk, half the node-diagonal part of what eliminating the red
+   neighbours adds to S_bb (row-major 5 x 5); zero for red samples.  Forms the dense condensed
+   matrix column by column with the condensed operator, so only for small meshes
+   ((K nb)^2 doubles <= 40 GB, else SC_ERR_ARG); S_mm^-1 from the condensation's factors.
+   After sc_condense on the mixed arm.  Device pointer, K * nbn * 25 floats. */
 sc_status sc_learned_targets(sc_ctx* ctx, float* T);
 
 /* Network parameters for SC_PC_LEARNED (device pointers, layout of sc_mlp_forward; copied
-   into the context).  With precond = SC_PC_LEARNED, sc_condense evaluates the network on
-   the features and the preconditioner becomes z_e = S_ee^-1 v_e + C_k v_k per boundary
-   node, C_k = y_k / ||[S_ee]_kk||_F. */
+   into the context).  With precond = SC_PC_LEARNED, sc_condense evaluates the network on the
+   features and factorises the black blocks S_bb + C, C_k = y_k ||[S_bb]_kk||_F, apart from the
+   plain factors, which block Jacobi (the fallback) keeps using. */
 sc_status sc_set_learned_weights(sc_ctx* ctx, const uint16_t* Wbf16, const float* bias);
 
 /* Measurement hook for SC_PC_LEARNED: after sc_condense, replace the corrections by
-   scale * Ck (device, K * nbn * 25 floats, C_k row-major per sample, unscaled: the
-   matrices added to the diagonal node blocks of S_ee^-1), e.g. the exact targets divided
-   by ||[S_ee]_kk||_F, to measure what a perfect network would give. */
+   scale * Ck (device, K * nbn * 25 floats, C_k row-major per sample, unscaled: the matrices
+   added to the diagonal node blocks of the black S_bb; red samples are ignored) and
+   refactorise the black blocks, e.g. with the exact targets times ||[S_bb]_kk||_F, to
+   measure what a perfect network would give. */
 sc_status sc_set_learned_correction(sc_ctx* ctx, const float* Ck, float scale);
 
 /* ---- Batched condensation of elements of uneven order ---------------------------
@@ -416,8 +473,13 @@ sc_status sc_profile_kernel(sc_ctx* ctx, int kernel_id);
    (synchronises the stream). */
 sc_status sc_profile_read(sc_ctx* ctx, long long* launches, double* total_ms);
 
-/* Algorithmic work of one launch of a kernel on the current mesh: floating-point
-   operations and bytes that must move (matrix entries read once, vectors once). */
+/* Elements processed by the launches of the profiled kernel since sc_profile_kernel (a
+   launch over every element counts K; the red-black sweep's launches count one colour). */
+sc_status sc_profile_elements(const sc_ctx* ctx, long long* elements);
+
+/* Algorithmic work of one launch of a kernel over every element of the current mesh:
+   floating-point operations and bytes that must move (matrix entries read once, vectors
+   once); per element, divide by K. */
 sc_status sc_kernel_work(const sc_ctx* ctx, int kernel_id, double* flops, double* bytes);
 
 #ifdef __cplusplus

@@ -89,6 +89,7 @@ void diff_matrix(const std::vector<double>& x, double D[SC_MAXP][SC_MAXP]) {
 }
 
 void free_all(sc_ctx* c) {
+  sc::free_direct_factors(c);
   double** dps[] = {&c->Q, &c->Qh, &c->grad, &c->F, &c->B, &c->NJ, &c->RJ, &c->Aown, &c->X, &c->Ainv,
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
                     &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk, &c->Sls, &c->dQn,
@@ -202,7 +203,7 @@ sc_status sc_default_config(sc_config* cfg) {
   cfg->Ts = 110.4 / 288.15; cfg->sutherland = 1; cfg->roe_delta = 0.05;
   cfg->precision = SC_PREC_FP64; cfg->precond = SC_PC_BLOCK_JACOBI;
   cfg->gmres_restart = 30; cfg->gmres_max_iters = 4000; cfg->max_refine = 10;
-  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4; cfg->tensor_cores = 1; cfg->learned_min_reduction = 10.0;
+  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4; cfg->tensor_cores = 1; cfg->learned_min_reduction = 4.0;
   return SC_OK;
 }
 
@@ -687,29 +688,6 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
   SC_CUDA(cudaMemsetAsync(c->Xb, 0, n1 * sizeof(double), c->stream));
   SC_CUDA(cudaMemcpyAsync(c->Rb, c->Gb, n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   double beta = dnorm2(c, c->Rb, n1, hs);
-  if (c->learned_on && beta > 0.0) {
-    // judge of the learned correction: one preconditioned step from the normalised
-    // residual v, ||v - S P v|| with the learned sweep against block Jacobi; the solve keeps
-    // the learned preconditioner only if it does at least as well
-    double rho[2] = {0.0, 0.0};
-    SC_CUDA(sc::vec_axpby(c, c->V, 1.0 / beta, c->Rb, 0.0, n1));
-    for (int k = 0; k < 2; ++k) {
-      c->learned_on = k == 0;
-      if (c->op32) {
-        SC_CUDA(sc::precond_apply32(c, c->V, nullptr, c->Zf));
-        SC_CUDA(sc::cond_interior32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf));
-        SC_CUDA(sc::cond_boundary32(c, c->Zf, 1.0, nullptr, 0.0, c->Uf, c->Wv));
-      } else {
-        SC_CUDA(sc::precond_apply(c, c->V, c->Zv));
-        SC_CUDA(sc::cond_interior(c, c->Zv, 1.0, nullptr, 0.0, c->Ui));
-        SC_CUDA(sc::cond_boundary(c, c->Zv, 1.0, nullptr, 0.0, c->Ui, c->Wv));
-      }
-      SC_CUDA(sc::vec_axpby(c, c->Wv, 1.0, c->V, -1.0, n1));
-      rho[k] = dnorm2(c, c->Wv, n1, hs);
-    }
-    c->learned_on = rho[0] <= rho[1];
-    if (!c->learned_on) c->learned_fallbacks++;
-  }
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hbuf(2 * (m + 1) + 1), y(m);
   int iters = 0;
   double resid = beta;
@@ -997,7 +975,13 @@ sc_status sc_profile_kernel(sc_ctx* c, int kernel_id) {
   if (kernel_id < -1 || kernel_id >= SCK_COUNT) return fail(c, SC_ERR_ARG, "unknown kernel id");
   cudaStreamSynchronize(c->stream);
   c->prof_kernel = kernel_id;
-  c->prof_used = 0; c->prof_ms = 0.0; c->prof_count = 0;
+  c->prof_used = 0; c->prof_ms = 0.0; c->prof_count = 0; c->prof_elems = 0;
+  return SC_OK;
+}
+
+sc_status sc_profile_elements(const sc_ctx* c, long long* elements) {
+  if (!c || !elements) return SC_ERR_ARG;
+  *elements = c->prof_elems;
   return SC_OK;
 }
 

@@ -1575,8 +1575,8 @@ cudaError_t lu_solve_list_t(sc_ctx* c, const TS* LS, const int* rowperm, int com
                             const double* v, const double* vsub, double* z, T* zt) {
   const Geo& G = c->G;
   if (nlist <= 0) return cudaSuccess;
-  ProfScope ps(c, SCK_LU_SOLVE);
-  if (nlist < kSolveCtaMaxElems) {
+  ProfScope ps(c, SCK_LU_SOLVE, nlist);
+  if (nlist <= kSolveCtaMaxElems) {
     const size_t csm = (size_t)(ls_nblk(G) + kSolveCtaWarps) * 32 * sizeof(T);
     k_lu_solve_cta<T, TS><<<nlist, 32 * kSolveCtaWarps, csm, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
                                                                          ls_npad(G), rowperm, v, z, zt, elist,
@@ -1700,6 +1700,18 @@ cudaError_t to_float(sc_ctx* c, const double* a, float* b, size_t n) {
 }
 
 // C = A B for `batch` row-major FP32 blocks on the CUDA cores.
+// C -= A B for one large row-major problem on the CUDA cores (64 x 64 tiles).
+template <class T>
+cudaError_t gemm_update(sc_ctx* c, int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  count_launch(c);
+  dim3 g(cdiv(N, 64), cdiv(M, 64), 1);
+  k_gemm<T><<<g, 256, 0, c->stream>>>(M, N, K, T(-1), A, 0, lda, B, 0, ldb, T(1), C, 0, ldc);
+  return cudaGetLastError();
+}
+template cudaError_t gemm_update<float>(sc_ctx*, int, int, int, const float*, int, const float*, int, float*, int);
+template cudaError_t gemm_update<double>(sc_ctx*, int, int, int, const double*, int, const double*, int, double*, int);
+
 cudaError_t gemm_fp32(sc_ctx* c, int M, int N, int K, const float* A, long long sA, int lda, const float* B,
                       long long sB, int ldb, float* C, long long sC, int ldc, int batch) {
   dim3 g(cdiv(N, 64), cdiv(M, 64), batch);

@@ -311,6 +311,12 @@ struct sc_ctx {
   float *SeeB = nullptr, *SeeL = nullptr, *SlsL = nullptr;
   int *pivL = nullptr, *rowpermL = nullptr;
   bool blackL_valid = false;  // SlsL holds the factors of the corrected black blocks
+  // dense direct solve (sc_direct_factor): n x n factors (row-major, ld = ldd), pivots
+  void* Dlu = nullptr;       // double (FP64 arm) or float (mixed arm)
+  int* d_dpiv = nullptr;
+  unsigned long long* d_dkey = nullptr;
+  int direct_n = 0, direct_ld = 0, direct_which = -1;
+  bool direct_valid = false;
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
   cudaEvent_t ev[8] = {};
   // measurement hooks: kernel launches since creation, and optional CUDA-event timing
@@ -321,6 +327,7 @@ struct sc_ctx {
   int prof_used = 0;
   double prof_ms = 0.0;
   long long prof_count = 0;
+  long long prof_elems = 0;  // elements processed by the profiled launches
 };
 
 // Kernel ids of the measurement hook (sc_profile_kernel).
@@ -328,12 +335,14 @@ enum { SCK_COND_INTERIOR = 0, SCK_COND_BOUNDARY = 1, SCK_LU_SOLVE = 2, SCK_LU = 
        SCK_GJ_INV = 5, SCK_ASM_OWN = 6, SCK_GLOBAL_APPLY = 7, SCK_EXPLICIT_GEMM = 8, SCK_EXPLICIT_APPLY = 9,
        SCK_COUNT = 10 };
 
-// Bracket one launch of kernel `id` with events when it is the profiled kernel.
+// Bracket one launch of kernel `id` with events when it is the profiled kernel; `elements`
+// is the number of elements the launch processes (default: every element of the mesh).
 struct ProfScope {
   sc_ctx* c; int id; bool on;
-  ProfScope(sc_ctx* cc, int kid) : c(cc), id(kid), on(cc->prof_kernel == kid) {
+  ProfScope(sc_ctx* cc, int kid, int elements = -1) : c(cc), id(kid), on(cc->prof_kernel == kid) {
     c->launches++;
     if (on) {
+      c->prof_elems += elements < 0 ? c->G.K : elements;
       if ((int)c->prof_ev.size() < 2 * (c->prof_used + 1)) {
         cudaEvent_t a, b; cudaEventCreate(&a); cudaEventCreate(&b);
         c->prof_ev.push_back(a); c->prof_ev.push_back(b);
@@ -460,6 +469,9 @@ cudaError_t precond_rb(sc_ctx* c, const double* v, double* z);
 cudaError_t precond_rb32(sc_ctx* c, const double* v, double* z, float* zf);
 cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale);
 cudaError_t gather_black_see(sc_ctx* c, const float* See);
+template <class T>
+cudaError_t gemm_update(sc_ctx* c, int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc);
+void free_direct_factors(sc_ctx* c);
 // X[p] = S_mm^-1 S[m rows, b cols] (nb x nb, column j contiguous) for pairs (b, m), from the
 // dense S stored column by column
 cudaError_t solve_columns32(sc_ctx* c, const double* Scm, long long n1, const int* pb, const int* pm, int npairs,

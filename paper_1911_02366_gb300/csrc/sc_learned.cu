@@ -372,4 +372,19 @@ sc_status sc_set_learned_weights(sc_ctx* c, const uint16_t* Wbf16, const float* 
   return SC_OK;
 }
 
+sc_status sc_load_mlp(sc_ctx* c, const char* path) {
+  if (!c || !path) return SC_ERR_ARG;
+  if (!c->Wbf16) return SC_ERR_STATE;
+  float *W = nullptr, *b = nullptr;
+  uint16_t* Wh = nullptr;
+  cudaError_t e = cudaMalloc(&W, (size_t)sc::kMlpWeights * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&b, (size_t)sc::kMlpBiases * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&Wh, (size_t)sc::kMlpWeights * sizeof(uint16_t));
+  sc_status s = e == cudaSuccess ? sc_mlp_load(path, W, Wh, b) : SC_ERR_OOM;
+  if (s == SC_OK) s = sc_set_learned_weights(c, Wh, b);
+  else c->err = "load_mlp: cannot read a network from the file";
+  cudaFree(W); cudaFree(b); cudaFree(Wh);
+  return s;
+}
+
 }  // extern "C"

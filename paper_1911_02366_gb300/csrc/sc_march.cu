@@ -233,11 +233,15 @@ sc_status sc_explicit_march(sc_ctx* c, double cfl, double dfl, int nsteps, doubl
   return SC_OK;
 }
 
-sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every, double* res_hist, double* ms_hist,
-                            int* gmres_iters) {
+sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every, int direct, double* res_hist,
+                            double* ms_hist, int* gmres_iters) {
   sc_status s = state_checks(c, nsteps);
   if (s != SC_OK) return s;
   if (jacobian_every < 0) { c->err = "implicit march: jacobian_every >= 0"; return SC_ERR_ARG; }
+  if (direct != -1 && direct != SC_DIRECT_GLOBAL && direct != SC_DIRECT_CONDENSED) {
+    c->err = "implicit march: direct is -1, SC_DIRECT_GLOBAL or SC_DIRECT_CONDENSED";
+    return SC_ERR_ARG;
+  }
   s = sc_set_timestep(c, dt, 1);
   if (s != SC_OK) return s;
   const Geo& G = c->G;
@@ -255,10 +259,12 @@ sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every
   for (int st = 0; st < nsteps; ++st) {
     // BDF1: the history is the state at the start of the step, so R(Q) = H(Q) there
     MC_CUDA(sc::launch_history(c, c->Q, c->Q));
-    const bool fresh = st == 0 || !c->condensed || (jacobian_every > 0 && st % jacobian_every == 0);
+    const bool fresh = st == 0 || (direct >= 0 ? !c->direct_valid : !c->condensed) ||
+                       (jacobian_every > 0 && st % jacobian_every == 0);
     if (fresh) {
       s = sc_assemble(c);
-      if (s == SC_OK) s = sc_condense(c);
+      if (s == SC_OK && direct != SC_DIRECT_GLOBAL) s = sc_condense(c);
+      if (s == SC_OK && direct >= 0) s = sc_direct_factor(c, direct, nullptr, nullptr);
       if (s != SC_OK) return s;
     } else {
       MC_CUDA(sc::launch_residual(c));  // B = -R(Q) with the frozen Jacobian kept
@@ -266,7 +272,7 @@ sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every
     count_launch(c);
     k_rhs<<<kBlocks, kThreads, 0, c->stream>>>(Gs, c->B, nullptr, rd + st);
     sc_solve_stats stt{};
-    s = sc_solve(c, c->dQn, 1, &stt);
+    s = direct >= 0 ? sc_direct_solve(c, c->dQn, 1, &stt) : sc_solve(c, c->dQn, 1, &stt);
     if (s != SC_OK) return s;
     if (gmres_iters) gmres_iters[st] = stt.gmres_iters;
     count_launch(c);

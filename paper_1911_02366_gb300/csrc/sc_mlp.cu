@@ -1,6 +1,7 @@
-// The learned correction of the block-Jacobi preconditioner: a 64 -> 256 -> 256 -> 25
+// The learned correction of the condensed-system preconditioner: a 64 -> 256 -> 256 -> 25
 // network with ReLU hidden layers, BF16 weights and FP32 arithmetic (not in the paper; a
-// learned stand-in for part of the condensed-system preconditioner of Sec. 2.2/4).
+// learned part of the condensed-system preconditioner of Sec. 2.2/4), with its training loop
+// (shuffled mini-batch Adam) and a file format for its parameters.
 //
 // All layers run through one SIMT tile kernel, C (+)= op(A) op(B), 64 x 64 tiles, 16-deep
 // K chunks staged in shared memory (BF16 operands widened to FP32 on the way), 4 x 4
@@ -12,7 +13,11 @@
 // products; the network is ~0.2 MFLOP per boundary node.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "sc_internal.cuh"
 
@@ -162,6 +167,32 @@ cudaError_t gemm(cudaStream_t st, int M, int N, int K, const TA_* A, int lda, co
   return cudaGetLastError();
 }
 
+// Rows perm[i0 .. i0 + nb) of X (64 wide) and T (25 wide) into contiguous batch buffers.
+__global__ void k_gather_batch(const int* __restrict__ perm, int i0, int nb, const float* __restrict__ X,
+                               const float* __restrict__ T, float* __restrict__ Xb, float* __restrict__ Tb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb * (NI + NO)) return;
+  const int r = t / (NI + NO), c = t % (NI + NO);
+  const long long src = __ldg(perm + i0 + r);
+  if (c < NI) Xb[(long long)r * NI + c] = X[src * NI + c];
+  else Tb[(long long)r * NO + c - NI] = T[src * NO + c - NI];
+}
+
+__global__ void k_to_bf16(const float* __restrict__ W, __nv_bfloat16* __restrict__ Wh, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) Wh[t] = __float2bfloat16_rn(W[t]);
+}
+
+// splitmix64 step (Steele, Lea and Flood 2014): the shuffles' random stream.
+uint64_t splitmix64_next(uint64_t& state) {
+  uint64_t z = (state += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+constexpr char kMlpMagic[8] = {'S', 'C', 'M', 'L', 'P', '0', '0', '1'};
+
 }  // namespace
 
 namespace sc {
@@ -277,6 +308,108 @@ sc_status sc_mlp_adam(float* W, uint16_t* Wbf16, float* bias, float* gW, float* 
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? SC_OK : SC_ERR_CUDA;
+}
+
+sc_status sc_mlp_bf16(const float* W, uint16_t* Wbf16, int n, void* cuda_stream) {
+  if (!W || !Wbf16 || n < 0) return SC_ERR_ARG;
+  if (n == 0) return SC_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  k_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(W, reinterpret_cast<__nv_bfloat16*>(Wbf16), n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? SC_OK : SC_ERR_CUDA;
+}
+
+sc_status sc_mlp_train(float* W, uint16_t* Wbf16, float* bias, float* m, float* v, int* step, const float* X,
+                       const float* T, int n, int epochs, int batch, float lr, uint64_t seed, float* loss_hist,
+                       void* cuda_stream) {
+  if (!W || !Wbf16 || !bias || !m || !v || !step || !X || !T || n < 1 || epochs < 0 || batch < 1 || *step < 0)
+    return SC_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int bmax = batch < n ? batch : n;
+  float *gW = nullptr, *gb = nullptr, *cache = nullptr, *work = nullptr, *Y = nullptr, *dY = nullptr;
+  float *Xb = nullptr, *Tb = nullptr, *acc = nullptr;
+  int* perm = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(cudaMalloc(&gW, (size_t)N_W * sizeof(float))); A(cudaMalloc(&gb, (size_t)N_B * sizeof(float)));
+  A(cudaMalloc(&cache, (size_t)4 * bmax * NH * sizeof(float))); A(cudaMalloc(&work, (size_t)2 * bmax * NH * sizeof(float)));
+  A(cudaMalloc(&Y, (size_t)bmax * NO * sizeof(float))); A(cudaMalloc(&dY, (size_t)bmax * NO * sizeof(float)));
+  A(cudaMalloc(&Xb, (size_t)bmax * NI * sizeof(float))); A(cudaMalloc(&Tb, (size_t)bmax * NO * sizeof(float)));
+  A(cudaMalloc(&acc, sizeof(float))); A(cudaMalloc(&perm, (size_t)n * sizeof(int)));
+  sc_status s = e == cudaSuccess ? SC_OK : SC_ERR_OOM;
+  if (s == SC_OK) {
+    A(cudaMemsetAsync(gW, 0, (size_t)N_W * sizeof(float), st));
+    A(cudaMemsetAsync(gb, 0, (size_t)N_B * sizeof(float), st));
+    if (e != cudaSuccess) s = SC_ERR_CUDA;
+  }
+  std::vector<int> hp(n);
+  uint64_t rs = seed;
+  const int nbatch = (n + bmax - 1) / bmax;
+  for (int ep = 0; ep < epochs && s == SC_OK; ++ep) {
+    // Fisher-Yates shuffle of all samples: batches mix systems, elements and nodes
+    for (int i = 0; i < n; ++i) hp[i] = i;
+    for (int i = n - 1; i > 0; --i) {
+      const int j = (int)(splitmix64_next(rs) % (uint64_t)(i + 1));
+      std::swap(hp[i], hp[j]);
+    }
+    A(cudaMemcpyAsync(perm, hp.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, st));
+    A(cudaMemsetAsync(acc, 0, sizeof(float), st));
+    if (e != cudaSuccess) { s = SC_ERR_CUDA; break; }
+    for (int b = 0; b < nbatch && s == SC_OK; ++b) {
+      const int i0 = b * bmax, nb = (n - i0) < bmax ? (n - i0) : bmax;
+      k_gather_batch<<<(nb * (NI + NO) + 255) / 256, 256, 0, st>>>(perm, i0, nb, X, T, Xb, Tb);
+      if (cudaGetLastError() != cudaSuccess) { s = SC_ERR_CUDA; break; }
+      s = sc_mlp_forward(Wbf16, bias, Xb, nb, Y, cache, st);
+      if (s == SC_OK) s = sc_mlp_loss(Y, Tb, nb, dY, acc, st);
+      if (s == SC_OK) s = sc_mlp_backward(Wbf16, Xb, cache, dY, nb, gW, gb, work, st);
+      if (s == SC_OK) s = sc_mlp_adam(W, Wbf16, bias, gW, gb, m, v, ++*step, lr, st);
+    }
+    if (s == SC_OK && loss_hist) {
+      float a = 0.f;
+      if (cudaMemcpyAsync(&a, acc, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) s = SC_ERR_CUDA;
+      loss_hist[ep] = a / (float)nbatch;
+    }
+  }
+  cudaFree(gW); cudaFree(gb); cudaFree(cache); cudaFree(work); cudaFree(Y); cudaFree(dY); cudaFree(Xb); cudaFree(Tb);
+  cudaFree(acc); cudaFree(perm);
+  return s;
+}
+
+sc_status sc_mlp_save(const char* path, const float* W, const float* bias) {
+  if (!path || !W || !bias) return SC_ERR_ARG;
+  std::vector<float> hw(N_W), hb(N_B);
+  if (cudaMemcpy(hw.data(), W, (size_t)N_W * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hb.data(), bias, (size_t)N_B * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SC_ERR_CUDA;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return SC_ERR_ARG;
+  const int32_t counts[2] = {N_W, N_B};
+  bool ok = std::fwrite(kMlpMagic, 1, 8, f) == 8 && std::fwrite(counts, sizeof(int32_t), 2, f) == 2 &&
+            std::fwrite(hw.data(), sizeof(float), N_W, f) == (size_t)N_W &&
+            std::fwrite(hb.data(), sizeof(float), N_B, f) == (size_t)N_B;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? SC_OK : SC_ERR_ARG;
+}
+
+sc_status sc_mlp_load(const char* path, float* W, uint16_t* Wbf16, float* bias) {
+  if (!path || !W || !Wbf16 || !bias) return SC_ERR_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return SC_ERR_ARG;
+  char magic[8];
+  int32_t counts[2] = {0, 0};
+  std::vector<float> hw(N_W), hb(N_B);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMlpMagic, 8) == 0 &&
+            std::fread(counts, sizeof(int32_t), 2, f) == 2 && counts[0] == N_W && counts[1] == N_B &&
+            std::fread(hw.data(), sizeof(float), N_W, f) == (size_t)N_W &&
+            std::fread(hb.data(), sizeof(float), N_B, f) == (size_t)N_B;
+  std::fclose(f);
+  if (!ok) return SC_ERR_ARG;
+  if (cudaMemcpy(W, hw.data(), (size_t)N_W * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(bias, hb.data(), (size_t)N_B * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return SC_ERR_CUDA;
+  return sc_mlp_bf16(W, Wbf16, N_W, nullptr);
 }
 
 }  // extern "C"

@@ -339,7 +339,7 @@ cudaError_t cond_boundary_pk_list(sc_ctx* c, const T* Apk, const T* X, const T* 
   const Geo& G = c->G;
   if (nlist <= 0) return cudaSuccess;
   const size_t smem = (size_t)G.lda * sizeof(T);
-  ProfScope ps(c, SCK_COND_BOUNDARY);
+  ProfScope ps(c, SCK_COND_BOUNDARY, nlist);
   k_cond_boundary_pk<T><<<nlist, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
                                                          c->d_pk_list, X, c->d_nbr, c->d_pptr, c->d_pinfo,
                                                          c->d_iperm, xb, 1.0, nullptr, 0.0, G.ni ? u : nullptr, y,

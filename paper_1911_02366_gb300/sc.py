@@ -17,6 +17,7 @@ SC_OK, SC_ERR_ARG, SC_ERR_CUDA, SC_ERR_OOM, SC_ERR_STATE = 0, 1, 2, 3, 4
 SC_ERR_SINGULAR_BLOCK, SC_ERR_NONFINITE, SC_ERR_NOT_CONVERGED = 5, 6, 7
 SC_PREC_FP64, SC_PREC_MIXED = 0, 1
 SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED, SC_PC_RED_BLACK = 0, 1, 2, 3
+SC_DIRECT_GLOBAL, SC_DIRECT_CONDENSED = 0, 1
 
 _lib = None
 
@@ -58,7 +59,8 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_get_state", "sc_condensed_rhs", "sc_backsubstitute", "sc_newton_step", "sc_batch_create",
            "sc_batch_condense", "sc_batch_tiles", "sc_batch_destroy", "sc_spectrum_estimate",
            "sc_hessenberg_eigvals", "sc_steady_residual", "sc_explicit_march", "sc_implicit_march",
-           "sc_precond_apply"]
+           "sc_precond_apply", "sc_profile_elements", "sc_mlp_bf16", "sc_mlp_train", "sc_mlp_save", "sc_mlp_load", "sc_load_mlp",
+           "sc_direct_factor", "sc_direct_solve"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -120,8 +122,17 @@ def lib(build_if_missing: bool = True):
     L.sc_hessenberg_eigvals.argtypes = [ctypes.c_int, dp, dp, dp]
     L.sc_steady_residual.argtypes = [vp, dp]
     L.sc_precond_apply.argtypes = [vp, dp, dp]
+    L.sc_profile_elements.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.sc_mlp_bf16.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.sc_mlp_train.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), vp, vp, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_float, ctypes.c_uint64, vp, vp]
+    L.sc_mlp_save.argtypes = [ctypes.c_char_p, vp, vp]
+    L.sc_mlp_load.argtypes = [ctypes.c_char_p, vp, vp, vp]
+    L.sc_load_mlp.argtypes = [vp, ctypes.c_char_p]
+    L.sc_direct_factor.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.sc_direct_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(sc_solve_stats)]
     L.sc_explicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]
-    L.sc_implicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    L.sc_implicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
     L.sc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
@@ -287,6 +298,11 @@ class Context:
         self._check(self._L.sc_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
 
+    def sc_profile_elements(self) -> int:
+        n = ctypes.c_longlong()
+        self._check(self._L.sc_profile_elements(self.h, ctypes.byref(n)))
+        return n.value
+
     def sc_kernel_work(self, kernel_id: int):
         f = ctypes.c_double(); b = ctypes.c_double()
         self._check(self._L.sc_kernel_work(self.h, kernel_id, ctypes.byref(f), ctypes.byref(b)))
@@ -318,6 +334,25 @@ class Context:
         return {"lam_max": complex(out[0], out[1]), "lam_min": complex(out[2], out[3]), "cond": out[4],
                 "inner_iters": int(out[5])}
 
+    def sc_direct_factor(self, which: str = "S"):
+        """Dense LU of the global A ('A') or the condensed S ('S'); returns (ms_form, ms_factor)."""
+        f, g = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.sc_direct_factor(self.h, {"A": SC_DIRECT_GLOBAL, "S": SC_DIRECT_CONDENSED}[which],
+                                             ctypes.byref(f), ctypes.byref(g)))
+        return f.value, g.value
+
+    def sc_direct_solve(self, dQ, raise_on_not_converged: bool = True):
+        st = sc_solve_stats()
+        p, dev = _ptr(dQ)
+        s = self._L.sc_direct_solve(self.h, p, dev, ctypes.byref(st))
+        if s != SC_OK and not (s == SC_ERR_NOT_CONVERGED and not raise_on_not_converged):
+            self._check(s)
+        return st.as_dict() | {"status": s}
+
+    def sc_load_mlp(self, path: str):
+        """Load a saved network (sc_mlp_save format) as the context's learned weights."""
+        self._check(self._L.sc_load_mlp(self.h, path.encode()))
+
     def sc_precond_apply(self, v, z):
         """z = P v with the context's condensed preconditioner (device float64 tensors)."""
         (pv, dv), (pz, dz) = _ptr(v), _ptr(z)
@@ -339,12 +374,14 @@ class Context:
                                               ms.ctypes.data))
         return res, dts[:nsteps], float(ms[0])
 
-    def sc_implicit_march(self, dt: float, nsteps: int, jacobian_every: int = 0):
-        """Linearised BDF1 steps with a reused Jacobian; returns (residual history,
-        cumulative device ms, GMRES iterations per step)."""
+    def sc_implicit_march(self, dt: float, nsteps: int, jacobian_every: int = 0, direct: str | None = None):
+        """Linearised BDF1 steps with a reused Jacobian, solved by condensed GMRES (direct=None)
+        or dense LU of A ('A') or S ('S'); returns (residual history, cumulative device ms,
+        GMRES iterations per step)."""
         res, ms = np.zeros(nsteps + 1), np.zeros(nsteps + 1)
         its = np.zeros(max(nsteps, 1), dtype=np.int32)
-        self._check(self._L.sc_implicit_march(self.h, dt, nsteps, jacobian_every, res.ctypes.data, ms.ctypes.data,
+        d = {None: -1, "A": SC_DIRECT_GLOBAL, "S": SC_DIRECT_CONDENSED}[direct]
+        self._check(self._L.sc_implicit_march(self.h, dt, nsteps, jacobian_every, d, res.ctypes.data, ms.ctypes.data,
                                               its.ctypes.data))
         return res, ms, its[:nsteps]
 
@@ -393,20 +430,6 @@ MLP_NW = MLP_H * MLP_IN + MLP_H * MLP_H + MLP_OUT * MLP_H
 MLP_NB = 2 * MLP_H + MLP_OUT
 
 
-def bf16_bits(x):
-    """IEEE bfloat16 bit patterns (round to nearest even) of a float array, as uint16."""
-    import numpy as np
-    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
-    return r.astype(np.uint16)
-
-
-def bf16_values(bits):
-    """float32 values of bfloat16 bit patterns."""
-    import numpy as np
-    return (np.asarray(bits, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
-
-
 class MLP:
     """Device parameters of the correction network and the C-ABI calls on them.
 
@@ -424,7 +447,9 @@ class MLP:
             raise ValueError("wrong parameter sizes")
         dev = "cuda"
         self.W = torch.tensor(W, device=dev)
-        self.Wh = torch.tensor(bf16_bits(W).view(np.int16), device=dev)
+        self.Wh = torch.empty(MLP_NW, dtype=torch.int16, device=dev)
+        self._ck(self._L.sc_mlp_bf16(self.W.data_ptr(), self.Wh.data_ptr(), MLP_NW, ctypes.c_void_p(self.stream)),
+                 "sc_mlp_bf16")
         self.b = torch.tensor(b, device=dev)
         self.gW = torch.zeros(MLP_NW, device=dev)
         self.gb = torch.zeros(MLP_NB, device=dev)
@@ -460,29 +485,28 @@ class MLP:
                                      ctypes.c_float(lr), ctypes.c_void_p(self.stream)), "sc_mlp_adam")
 
     def train(self, X, T, epochs, batch, lr, seed=0):
-        """Mini-batch Adam on device features X [n, 64] and targets T [n, 25]; returns the
-        per-epoch mean loss."""
+        """Shuffled mini-batch Adam on device features X [n, 64] and targets T [n, 25]
+        (sc_mlp_train); returns the per-epoch mean loss."""
         import numpy as np
-        import torch
-        n = X.shape[0]
-        cache = torch.empty(4 * batch * MLP_H, device=X.device)
-        work = torch.empty(2 * batch * MLP_H, device=X.device)
-        Y = torch.empty(batch, MLP_OUT, device=X.device)
-        dY = torch.empty(batch, MLP_OUT, device=X.device)
-        acc = torch.zeros(1, device=X.device)
-        rng = np.random.default_rng(seed)
-        starts = list(range(0, n - batch + 1, batch))  # fixed batches, visited in a new order each epoch
-        hist = []
-        for _ in range(epochs):
-            acc.zero_()
-            for s0 in rng.permutation(starts):
-                xb, tb = X[s0:s0 + batch], T[s0:s0 + batch]
-                self.forward(xb, Y, cache)
-                self.loss(Y, tb, dY, acc)
-                self.backward(xb, cache, dY, work)
-                self.adam(lr)
-            hist.append(float(acc.item()) / max(len(starts), 1))
-        return hist
+        hist = np.zeros(max(epochs, 1), dtype=np.float32)
+        step = ctypes.c_int(self.step)
+        self._ck(self._L.sc_mlp_train(self.W.data_ptr(), self.Wh.data_ptr(), self.b.data_ptr(), self.m.data_ptr(),
+                                      self.v.data_ptr(), ctypes.byref(step), X.data_ptr(), T.data_ptr(), X.shape[0],
+                                      epochs, batch, ctypes.c_float(lr), ctypes.c_uint64(seed), hist.ctypes.data,
+                                      ctypes.c_void_p(self.stream)), "sc_mlp_train")
+        self.step = step.value
+        return [float(x) for x in hist[:epochs]]
+
+    def save(self, path: str):
+        self._ck(self._L.sc_mlp_save(path.encode(), self.W.data_ptr(), self.b.data_ptr()), "sc_mlp_save")
+
+    @classmethod
+    def load(cls, path: str, stream=None):
+        import numpy as np
+        net = cls(np.zeros(MLP_NW), np.zeros(MLP_NB), stream=stream)
+        net._ck(net._L.sc_mlp_load(path.encode(), net.W.data_ptr(), net.Wh.data_ptr(), net.b.data_ptr()),
+                "sc_mlp_load")
+        return net
 
 
 SC_BATCH_GRAPH, SC_BATCH_AUTOTUNE = 1, 2

@@ -25,3 +25,15 @@ def case(n, N, cfl=50.0, eps=1e-3, seed=0, bdf=1, **cfg):
 
 def rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def bf16_bits(x):
+    """IEEE bfloat16 bit patterns (round to nearest even) of a float array, as uint16."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def bf16_values(bits):
+    """float32 values of bfloat16 bit patterns."""
+    return (np.asarray(bits, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)

@@ -1,0 +1,83 @@
+"""Direct solves by dense LU on the GPU (Sec. 4, the factorisations of Tables tab:Advantages
+and tab:Advantages2): the global Jacobian and the condensed matrix, each against the oracle's
+global solve, and the frozen-Jacobian implicit march through them."""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.march as MA
+import sc_inputs as I
+from gpu_common import TWO_PI, case, gpu_context
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _system(n, N, cfl=10.0, **cfg):
+    Q, dt, p, ctx = case(n, N, cfl=cfl, **cfg)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    return Q, dt, p, ctx
+
+
+@pytest.mark.parametrize("which", ["A", "S"])
+@pytest.mark.parametrize("arm,tc", [("fp64", 0), ("mixed", 1), ("mixed", 0)])
+@pytest.mark.parametrize("n,N", [(2, 3), (3, 2)])
+def test_direct_solve_matches_oracle_global_solve(which, arm, tc, n, N):
+    from paper_1911_02366_gb300 import sc
+    cfg = dict(rel_tol=1e-12)
+    if arm == "mixed":
+        cfg.update(precision=sc.SC_PREC_MIXED, max_refine=30, tensor_cores=tc)
+    Q, dt, p, ctx = _system(n, N, **cfg)
+    ms_form, ms_fac = ctx.sc_direct_factor(which)
+    dQ = np.zeros(Q.size)
+    st = ctx.sc_direct_solve(dQ)
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    x = O.global_solve(A, B)
+    assert np.linalg.norm(B - A @ dQ) / np.linalg.norm(B) < 1e-11, st
+    assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < (1e-10 if arm == "fp64" else 1e-9), st
+    if arm == "fp64":
+        assert st["refinements"] <= 2
+    assert ms_form > 0 and ms_fac > 0
+
+
+def test_direct_factor_of_the_cfl50_4x4x4_N3_system():
+    """The 4^3, N = 3, CFL-50 system that stalls restarted GMRES: a direct condensed solve on
+    the mixed arm reaches the oracle's solution to 1e-8 after FP64 refinement."""
+    from paper_1911_02366_gb300 import sc
+    n, N = 4, 3
+    Q, dt = I.tgv_state(n, N, cfl=50.0, seed=0)
+    p = O.Params(n=n, N=N, dt=dt)
+    ctx = gpu_context(precision=sc.SC_PREC_MIXED, rel_tol=1e-11, max_refine=40)
+    ctx.sc_set_mesh(n, TWO_PI, N)
+    ctx.sc_set_timestep(dt, 1)
+    ctx.sc_set_state(Q, Q)
+    ctx.sc_assemble()
+    ctx.sc_condense()
+    ctx.sc_direct_factor("S")
+    dQ = np.zeros(Q.size)
+    st = ctx.sc_direct_solve(dQ)
+    A = O.jacobian(p, Q)
+    B = -O.residual(p, Q).reshape(-1)
+    x = O.global_solve_dense(A, B)
+    assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < 1e-8, st
+
+
+@pytest.mark.parametrize("direct", ["A", "S"])
+def test_frozen_jacobian_march_with_direct_solves_matches_oracle(direct):
+    n, N = 2, 3
+    Q, dt = I.tgv_state(n, N, cfl=10.0, seed=0)
+    ctx = gpu_context(Re=30.0, rel_tol=1e-12)
+    ctx.sc_set_mesh(n, TWO_PI, N)
+    ctx.sc_set_timestep(dt, 1)
+    ctx.sc_set_state(Q, Q)
+    res, ms, its = ctx.sc_implicit_march(dt, 3, jacobian_every=0, direct=direct)
+    q = np.zeros(Q.size)
+    ctx.sc_get_state(q)
+    p = O.Params(n=n, N=N, dt=dt, Re=30.0)
+    qo, reso = MA.implicit_march(p, Q, dt, 3)
+    dq = qo.reshape(-1) - Q.reshape(-1)
+    assert np.linalg.norm(q - qo.reshape(-1)) <= 1e-9 * np.linalg.norm(dq)
+    assert np.max(np.abs(res - reso) / reso) <= 1e-7

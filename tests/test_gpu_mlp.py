@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import oracle.learned as LN
+from gpu_common import bf16_bits, bf16_values
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -18,7 +19,7 @@ def _params(seed):
     W = np.concatenate([P["W1"].ravel(), P["W2"].ravel(), P["W3"].ravel()]).astype(np.float32)
     b = np.concatenate([P["b1"], P["b2"], P["b3"]]).astype(np.float32)
     # the oracle sees exactly the values the GPU multiplies with
-    Wq = sc.bf16_values(sc.bf16_bits(W)).astype(np.float64)
+    Wq = bf16_values(bf16_bits(W)).astype(np.float64)
     Pq = {"W1": Wq[:16384].reshape(256, 64), "W2": Wq[16384:16384 + 65536].reshape(256, 256),
           "W3": Wq[16384 + 65536:].reshape(25, 256), "b1": b[:256].astype(np.float64),
           "b2": b[256:512].astype(np.float64), "b3": b[512:].astype(np.float64)}
@@ -104,7 +105,7 @@ def test_adam_matches_oracle_and_refreshes_bf16_copy():
         LN.adam_step(P, {"W": gWh.astype(np.float64), "b": gbh.astype(np.float64)}, st, lr=1e-2)
     assert _rel(net.W.cpu().numpy(), P["W"]) < 1e-5
     assert _rel(net.b.cpu().numpy(), P["b"]) < 1e-5
-    assert np.array_equal(net.Wh.cpu().numpy().view(np.uint16), sc.bf16_bits(net.W.cpu().numpy()))
+    assert np.array_equal(net.Wh.cpu().numpy().view(np.uint16), bf16_bits(net.W.cpu().numpy()))
     assert float(net.gW.abs().max()) == 0.0
 
 
@@ -121,3 +122,24 @@ def test_training_fits_a_teacher_network():
     hist = net.train(torch.tensor(X, device="cuda"), torch.tensor(T.astype(np.float32), device="cuda"),
                      epochs=15, batch=512, lr=2e-3)
     assert hist[-1] < 0.3 * hist[0], hist
+
+
+def test_initial_bf16_copy_and_save_load_round_trip(tmp_path):
+    """The binding's BF16 copy comes from the library (nearest even), and a saved network
+    reads back bit for bit, also into a context (sc_load_mlp)."""
+    from paper_1911_02366_gb300 import sc
+    W, b, _ = _params(12)
+    net = sc.MLP(W, b)
+    assert np.array_equal(net.Wh.cpu().numpy().view(np.uint16), bf16_bits(np.asarray(W, dtype=np.float32)))
+    path = str(tmp_path / "net.scmlp")
+    net.save(path)
+    back = sc.MLP.load(path)
+    assert np.array_equal(back.W.cpu().numpy(), net.W.cpu().numpy())
+    assert np.array_equal(back.b.cpu().numpy(), net.b.cpu().numpy())
+    assert np.array_equal(back.Wh.cpu().numpy(), net.Wh.cpu().numpy())
+    ctx = sc.Context(stream=torch.cuda.current_stream().cuda_stream, precision=sc.SC_PREC_MIXED,
+                     precond=sc.SC_PC_LEARNED)
+    ctx.sc_set_mesh(2, 2 * np.pi, 2)
+    ctx.sc_load_mlp(path)
+    with pytest.raises(sc.SCError):
+        ctx.sc_load_mlp(str(tmp_path / "missing.scmlp"))

@@ -49,7 +49,12 @@ def test_red_black_apply_satisfies_the_sweep_equations_with_oracle_S(arm, n, N):
         r[sl] = S[sl, sl] @ z[sl] - v[sl] + (t[sl] if col[e] == 1 else 0.0)
     scale = np.max(np.sum(np.abs(S), axis=1)) * np.max(np.abs(z)) + np.max(np.abs(v))
     tol = 1e-13 if arm == "fp64" else 2e-6
-    assert np.max(np.abs(r)) <= tol * scale, np.max(np.abs(r)) / scale
+    re = np.abs(r).reshape(K, nb).max(axis=1) / scale
+    worst = int(np.argmax(np.abs(r)))
+    diag = {"red_max": float(re[col == 0].max()), "black_max": float(re[col == 1].max()),
+            "worst_elem": worst // nb, "worst_row": worst % nb, "worst_colour": int(col[worst // nb]),
+            "z_at_worst_elem": float(np.max(np.abs(z[(worst // nb) * nb:(worst // nb + 1) * nb])))}
+    assert np.max(np.abs(r)) <= tol * scale, diag
     # the oracle's sweep agrees to the block conditioning (FP64) and the black part is not
     # block Jacobi (the sweep reaches across the colours)
     ref = O.red_black_apply(S, n, v)
