@@ -144,7 +144,7 @@ def train_correction(args, stream):
         c.sc_condense()
         K, _, _, nb = c.sc_sizes()
         nsmp = K * nb // 5
-        F = torch.empty(nsmp, 64, device="cuda")
+        F = torch.empty(nsmp, 128, device="cuda")
         sn = torch.empty(nsmp, device="cuda")
         T = torch.empty(nsmp, 25, device="cuda")
         c.sc_learned_features(F, sn)
@@ -154,7 +154,7 @@ def train_correction(args, stream):
         c.close()
     X = torch.cat(Fs).contiguous()
     Y = torch.cat(Ts).contiguous()
-    P = [rng.standard_normal((256, 64)) * math.sqrt(2 / 64), rng.standard_normal((256, 256)) * math.sqrt(2 / 256),
+    P = [rng.standard_normal((256, 128)) * math.sqrt(2 / 128), rng.standard_normal((256, 256)) * math.sqrt(2 / 256),
          rng.standard_normal((25, 256)) * math.sqrt(1 / 256) * 0.1]
     net = sc.MLP(np.concatenate([w.ravel() for w in P]), np.zeros(sc.MLP_NB), stream=stream.cuda_stream)
     hist = net.train(X, Y, epochs=args.train_epochs, batch=256, lr=1e-3)
@@ -299,8 +299,48 @@ def run_ours(args, world, rank, local):
         "roofline": roof,
         "clocks": clocks,
     }
+    if args.arm != "fp64" and not args.no_fp64_arm:
+        line["fp64_arm"] = fp64_reference_arm(args, W, Q, dt, stream, dQ)
+        line["speedup_vs_fp64_arm"] = value / line["fp64_arm"]["value"]
     ctx.close()
     return line
+
+
+def fp64_reference_arm(args, W, Q, dt, stream, dQ_mixed):
+    """The metric's denominator in the same run: the plain FP64 condensed GPU solve (FP64
+    blocks and operator, block-Jacobi GMRES(30), no refinement) of the same system, timed the
+    same way (2 timed steps after 1 warm-up); and the relative difference of the two arms'
+    solutions (the FP64 arm matches the oracle's global solve to 1e-10 on the 4^3, N = 3
+    system in the tests)."""
+    import torch
+    from paper_1911_02366_gb300 import sc
+    ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_FP64, Re=W["Re"], Ma=W["Ma"],
+                     gmres_restart=30, gmres_max_iters=args.max_iters, rel_tol=REL_TOL)
+    ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
+    ctx.sc_set_timestep(dt, 1)
+    Qd = torch.tensor(Q.reshape(-1), device="cuda")
+    dQ = torch.zeros_like(Qd)
+    ctx.sc_set_state(Qd, Qd)
+
+    def step():
+        ctx.sc_assemble()
+        ctx.sc_condense()
+        return ctx.sc_solve(dQ)
+
+    step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    stats = [step() for _ in range(2)]
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 2
+    diff = float(torch.linalg.vector_norm(dQ_mixed - dQ) / torch.linalg.vector_norm(dQ))
+    ctx.close()
+    return {"value": Q.size / (ms * 1e-3), "unit": "DOF/s", "ms_per_step": ms, "steps": 2, "warmup": 1,
+            "precond": "bj", "gmres_iters": [s["gmres_iters"] for s in stats],
+            "rel_residual_max": max(s["rel_residual"] for s in stats),
+            "solution_rel_diff_mixed_vs_fp64": diff}
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
@@ -541,18 +581,183 @@ def run_timesteps(args, world, rank, local):
     }
 
 
+def eta(res, ms, decades=1.0):
+    """Convergence rate of Sec. 4: the slope of log10 ||M^-1 H||_inf against the compute time
+    (1/s) over the final `decades` of the history."""
+    res, ms = np.asarray(res, float), np.asarray(ms, float)
+    ok = np.isfinite(res) & (res > 0)
+    res, ms = res[ok], ms[ok]
+    if len(res) < 2:
+        return None
+    sel = np.log10(res) <= np.log10(res[-1]) + decades
+    if sel.sum() < 2:
+        sel[-2:] = True
+    t, y = ms[sel] * 1e-3, np.log10(res[sel])
+    if t.max() <= t.min():
+        return None
+    return float(np.polyfit(t, y, 1)[0])
+
+
+def run_march(args, world, rank, local):
+    """The paper's steady-state experiment (Sec. 4) restated on a decaying Taylor-Green state:
+    explicit low-storage RK3 against frozen-Jacobian BDF1 solved globally (dense LU of A) and
+    by static condensation (dense LU of S, and the condensed GMRES), each to
+    ||M^-1 H||_inf <= steady_tol; time to the tolerance, eta, and the one-time and per-step
+    costs of Tables tab:SpeedUp, tab:Advantages and tab:Advantages2."""
+    import torch
+    from paper_1911_02366_gb300 import sc
+
+    torch.cuda.set_device(local)
+    n, N = args.n or 4, args.order or 3
+    Ma, Re = args.march_ma, args.march_re
+    Q, _ = I.tgv_state(n, N, Ma=Ma, seed=0, cfl=1.0)
+    dofs = Q.size
+    stream = torch.cuda.current_stream()
+    prec = sc.SC_PREC_FP64 if args.march_precision == "fp64" else sc.SC_PREC_MIXED
+
+    def ctx_new(**kw):
+        c = sc.Context(stream=stream.cuda_stream, precision=prec, Re=Re, Ma=Ma, rel_tol=1e-10,
+                       gmres_restart=args.restart, gmres_max_iters=args.max_iters, max_refine=40,
+                       tensor_cores=args.tensor_cores, **kw)
+        c.sc_set_mesh(n, 2 * math.pi, N)
+        Qd = torch.tensor(Q.reshape(-1), device="cuda")
+        c.sc_set_state(Qd, Qd)
+        return c
+
+    out = {}
+    tol = args.steady_tol
+    # explicit RK3 in chunks until the tolerance or the step cap
+    c = ctx_new()
+    res_all, t_all, t0, steps = [c.sc_steady_residual()], [0.0], 0.0, 0
+    while res_all[-1] > tol and steps < args.max_explicit_steps:
+        k = min(2000, args.max_explicit_steps - steps)
+        res, dts, ms = c.sc_explicit_march(args.explicit_cfl, k, dfl=args.explicit_dfl)
+        res_all += list(res[1:])
+        t_all += list(t0 + ms * np.arange(1, k + 1) / k)
+        t0 += ms
+        steps += k
+    hit = next((i for i, r in enumerate(res_all) if r <= tol), None)
+    out["explicit_rk3"] = {"steps": hit if hit is not None else steps, "reached": hit is not None,
+                           "seconds_to_tol": (t_all[hit] if hit is not None else t0) * 1e-3,
+                           "final_residual": res_all[-1], "eta_per_s": eta(res_all, t_all),
+                           "cfl": args.explicit_cfl}
+    c.close()
+    # implicit BDF1 with a frozen Jacobian, three solvers
+    for name, direct, extra in (("bdf1_global_lu", "A", {}), ("bdf1_condensed_lu", "S", {}),
+                                ("bdf1_condensed_gmres", None, {"precond": sc.SC_PC_RED_BLACK})):
+        c = ctx_new(**extra)
+        res, ms, its = c.sc_implicit_march(args.march_dt, args.max_implicit_steps, jacobian_every=0, direct=direct,
+                                           steady_tol=tol)
+        hit = next((i for i, r in enumerate(res) if r <= tol), None)
+        row = {"steps": hit if hit is not None else len(res) - 1, "reached": hit is not None,
+               "seconds_to_tol": (ms[hit] if hit is not None else ms[-1]) * 1e-3, "final_residual": float(res[-1]),
+               "eta_per_s": eta(res[:hit + 1] if hit else res, ms[:hit + 1] if hit else ms),
+               "first_step_ms": float(ms[1]), "later_step_ms": float(np.median(np.diff(ms[1:]))) if len(ms) > 2 else None}
+        if direct is None:
+            row["gmres_iters_per_step"] = float(np.mean(its))
+        c.close()
+        # one-time and per-solve costs (Tables tab:Advantages, tab:Advantages2)
+        if direct is not None:
+            c = ctx_new()
+            c.sc_set_timestep(args.march_dt, 1)
+            c.sc_assemble()
+            c.sc_condense()
+            form_ms, fac_ms = c.sc_direct_factor(direct)
+            dQ = torch.zeros(dofs, dtype=torch.float64, device="cuda")
+            st = c.sc_direct_solve(dQ, raise_on_not_converged=False)
+            row.update({"form_ms": form_ms, "lu_factor_ms": fac_ms, "lu_solve_ms_per_solve": st["ms_gmres"] / max(st["refinements"], 1),
+                        "cond_ops_ms_per_solve": st["ms_rhs"] / max(st["refinements"], 1), "sweeps": st["refinements"]})
+            c.close()
+        out[name] = row
+    g, cs = out["bdf1_global_lu"], out["bdf1_condensed_lu"]
+    ex = out["explicit_rk3"]
+    speed = {k: (ex["seconds_to_tol"] / v["seconds_to_tol"] if v["reached"] and ex["reached"] else None)
+             for k, v in out.items() if k != "explicit_rk3"}
+    return {
+        "metric": "time to steady state ||M^-1 H||_inf <= tol (s): explicit RK3 vs frozen-Jacobian BDF1, global vs condensed",
+        "value": cs["seconds_to_tol"], "unit": "s", "n_gpus": world, "steps": cs["steps"], "warmup": 0,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == sc.SC_PREC_FP64 else "f32+f64", "data": "synthetic (decaying Taylor-Green state)",
+        "config": {"workload": f"tgv_{n}x{n}x{n}_N{N}_Re{Re:g}_Ma{Ma:g}", "elements": n ** 3, "order": N, "dof": dofs,
+                   "steady_tol": tol, "bdf1_dt": args.march_dt, "arm": "march", "precision": args.march_precision},
+        "methods": out,
+        "speedup_vs_explicit": speed,
+        "eta_ratio_condensed_over_global": (cs["eta_per_s"] / g["eta_per_s"]
+                                            if cs["eta_per_s"] and g["eta_per_s"] else None),
+        "speedup_condensed_over_global": (g["seconds_to_tol"] / cs["seconds_to_tol"]
+                                          if g["reached"] and cs["reached"] else None),
+    }
+
+
+def run_peaks(args, world, rank, local):
+    """Peak rates of the arithmetic this project's kernels run in, on this GPU: dense GEMM
+    through cuBLAS (torch.matmul) in FP64 and in TF32 (FP32 storage, TF32 tensor cores), and
+    this library's TF32 tcgen05 GEMM (sc_gemm_tf32) at the same size; best of 5 after 2
+    warm-ups, CUDA events."""
+    import torch
+    from paper_1911_02366_gb300 import sc
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+
+    def best(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(stream); fn(); b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    out = {}
+    n64 = 8192
+    A = torch.randn(n64, n64, dtype=torch.float64, device="cuda")
+    B = torch.randn(n64, n64, dtype=torch.float64, device="cuda")
+    ms = best(lambda: torch.matmul(A, B))
+    out["fp64_gemm_cublas_tflops"] = 2 * n64 ** 3 / (ms * 1e-3) / 1e12
+    del A, B
+    n32 = 8192
+    A = torch.randn(n32, n32, dtype=torch.float32, device="cuda")
+    B = torch.randn(n32, n32, dtype=torch.float32, device="cuda")
+    C = torch.empty(n32, n32, dtype=torch.float32, device="cuda")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    ms = best(lambda: torch.matmul(A, B, out=C))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    out["tf32_gemm_cublas_tflops"] = 2 * n32 ** 3 / (ms * 1e-3) / 1e12
+    ms = best(lambda: sc.sc_gemm_tf32(A.view(1, n32, n32), B.view(1, n32, n32), C.view(1, n32, n32),
+                                      stream=stream.cuda_stream))
+    out["tf32_gemm_sc_tflops"] = 2 * n32 ** 3 / (ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    return {"metric": "peak rates of the arithmetic on this GPU (GEMM)", "value": out["tf32_gemm_sc_tflops"],
+            "unit": "TFLOP/s", "n_gpus": world, "steps": 5, "warmup": 2, "higher_is_better": True,
+            "config": {"workload": f"gemm {n32}^3 (TF32), {n64}^3 (FP64)", "arm": "peaks"},
+            **out, "bf16_cublas_measured_tflops": peaks.get("bf16_tflops"), "hbm_measured_gbs": peaks.get("hbm_gbs")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--arm", choices=["fp64", "mixed", "learned", "batched", "timesteps"], default="mixed")
+    ap.add_argument("--arm", choices=["fp64", "mixed", "learned", "batched", "timesteps", "march", "peaks"], default="mixed")
+    ap.add_argument("--steady-tol", type=float, default=1e-9, help="march arm: ||M^-1 H||_inf of the steady state")
+    ap.add_argument("--march-dt", type=float, default=1.0, help="march arm: BDF1 time step (the paper's dt = 1)")
+    ap.add_argument("--march-re", type=float, default=30.0, help="march arm: Reynolds number (the paper's 30)")
+    ap.add_argument("--march-ma", type=float, default=0.2, help="march arm: Mach number (the paper's 0.2)")
+    ap.add_argument("--march-precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--explicit-cfl", type=float, default=0.15, help="march arm: RK3 CFL (h/N spacing)")
+    ap.add_argument("--explicit-dfl", type=float, default=0.5, help="march arm: RK3 diffusive limit factor")
+    ap.add_argument("--max-explicit-steps", type=int, default=200000)
+    ap.add_argument("--max-implicit-steps", type=int, default=400)
     ap.add_argument("--time-steps", type=int, default=10, help="timesteps arm: BDF2 steps")
     ap.add_argument("--cfl", type=float, default=100.0, help="timesteps arm: CFL of the time step")
     ap.add_argument("--newton-tol", type=float, default=1e-6, help="timesteps arm: ||R|| / ||R_0|| per step")
     ap.add_argument("--max-newton", type=int, default=8, help="timesteps arm: Newton updates per step")
-    ap.add_argument("--train-epochs", type=int, default=40, help="learned arm: training epochs (untimed)")
+    ap.add_argument("--train-epochs", type=int, default=100, help="learned arm: training epochs (untimed)")
     ap.add_argument("--operator", choices=["implicit", "explicit"], default="implicit",
                     help="mixed arm: condensed operator applied implicitly or from explicit W_e blocks")
     ap.add_argument("--precond", choices=["bj", "rb"], default="bj",
@@ -569,6 +774,7 @@ def main():
     ap.add_argument("--order", type=int, default=None, help="polynomial order (profiling runs)")
     ap.add_argument("--allow-unconverged", action="store_true", help="profiling runs with capped iterations")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 arm beside the mixed line")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.n or args.order:
@@ -595,10 +801,11 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    runner = {"batched": run_batched, "timesteps": run_timesteps}.get(args.arm, run_ours)
+    runner = {"batched": run_batched, "timesteps": run_timesteps, "march": run_march,
+              "peaks": run_peaks}.get(args.arm, run_ours)
     line = runner(args, world, rank, local)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline and args.arm not in ("batched", "timesteps"):
+        if world == 1 and not args.no_cpu_baseline and args.arm not in ("batched", "timesteps", "march", "peaks"):
             r = run_oracle(1)
             v = r["dof"] / r["seconds"][0]
             line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cpu_threads(), "kind": "oracle",

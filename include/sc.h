@@ -299,13 +299,16 @@ sc_status sc_explicit_march(sc_ctx* ctx, double cfl, double dfl, int nsteps, dou
    = -1) or by the dense factors of sc_direct_solve (direct = SC_DIRECT_GLOBAL: LU of A, or
    SC_DIRECT_CONDENSED: LU of S), Q <- Q + dQ.  The Jacobian is assembled (condensed, factorised)
    at the first step and then every jacobian_every steps (0 = once: the frozen Jacobian of the
-   paper's experiment); the other steps only evaluate the residual.  res_hist (host, nsteps + 1 or NULL):
-   ||M^-1 H||_inf at the start of each step and after the last; ms_hist (host, nsteps + 1 or
-   NULL): device milliseconds from the start to the end of each step (ms_hist[0] = 0);
-   gmres_iters (host, nsteps or NULL): GMRES iterations of each solve.  A solve that misses
-   rel_tol returns its status (SC_ERR_NOT_CONVERGED) and stops the march. */
-sc_status sc_implicit_march(sc_ctx* ctx, double dt, int nsteps, int jacobian_every, int direct, double* res_hist,
-                            double* ms_hist, int* gmres_iters);
+   paper's experiment); the other steps only evaluate the residual.  steady_tol > 0 ends the
+   march early, before the solve of the first step whose start state has
+   ||M^-1 H||_inf <= steady_tol (0: all nsteps).  res_hist (host, nsteps + 1 or NULL):
+   ||M^-1 H||_inf at the start of each step taken and after the last (NaN beyond); ms_hist
+   (host, nsteps + 1 or NULL): device milliseconds from the start to the end of each step
+   (ms_hist[0] = 0, NaN beyond the steps taken); gmres_iters (host, nsteps or NULL): GMRES
+   iterations of each solve; steps_taken (or NULL).  A solve that misses rel_tol returns its
+   status (SC_ERR_NOT_CONVERGED) and stops the march. */
+sc_status sc_implicit_march(sc_ctx* ctx, double dt, int nsteps, int jacobian_every, int direct, double steady_tol,
+                            double* res_hist, double* ms_hist, int* gmres_iters, int* steps_taken);
 
 /* ---- Spectrum and condition-number estimate (Sec. 4, Fig. ConditionNumber) ------
    The paper approximates the L2 condition number of the global and of the condensed
@@ -332,24 +335,24 @@ sc_status sc_hessenberg_eigvals(int m, const double* H, double* re, double* im);
 
 /* ---- Learned correction of the red-black sweep --------------------------------------
    Not in the paper (which preconditions GMRES on the condensed system with point Jacobi,
-   Sec. 4): a network maps 64 features of each boundary node k of each element to a 5 x 5
+   Sec. 4): a network maps 128 features of each boundary node k of each element to a 5 x 5
    correction C_k added to the diagonal node block k of a black element's S_bb before the
    black half of the red-black sweep factorises it (SC_PC_LEARNED).  Layout of the parameters
-   (shared by every call): weights W = [W1 (256 x 64) | W2 (256 x 256) | W3 (25 x 256)],
-   row-major, 88,320 values, kept as FP32 masters and as a BF16 copy (IEEE bfloat16 bit
+   (shared by every call): weights W = [W1 (256 x 128) | W2 (256 x 256) | W3 (25 x 256)],
+   row-major, 104,704 values, kept as FP32 masters and as a BF16 copy (IEEE bfloat16 bit
    patterns in uint16_t); biases b = [b1 (256) | b2 (256) | b3 (25)], FP32.  Layers:
    h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3; FP32 arithmetic.  All
    pointers are device pointers unless stated; work is enqueued on cuda_stream and
    synchronised before return.  SC_ERR_ARG for null pointers or bad sizes, SC_ERR_CUDA for
    launch failures. */
 
-/* y[n x 25] = net(X[n x 64]).  cache: NULL, or 4 n x 256 floats that receive z1, h1, z2,
+/* y[n x 25] = net(X[n x 128]).  cache: NULL, or 4 n x 256 floats that receive z1, h1, z2,
    h2 (pre- and post-activations) for sc_mlp_backward; with NULL the call allocates
    temporaries on the stream. */
 sc_status sc_mlp_forward(const uint16_t* Wbf16, const float* bias, const float* X, int n, float* Y, float* cache,
                          void* cuda_stream);
 
-/* Accumulate the gradients of sum(dY * y) into gW (88,320) and gb (537), FP32, from the
+/* Accumulate the gradients of sum(dY * y) into gW (104,704) and gb (537), FP32, from the
    forward cache of the same X.  work: 2 n x 256 floats of scratch. */
 sc_status sc_mlp_backward(const uint16_t* Wbf16, const float* X, const float* cache, const float* dY, int n,
                           float* gW, float* gb, float* work, void* cuda_stream);
@@ -361,7 +364,7 @@ sc_status sc_mlp_loss(const float* Y, const float* T, int n, float* dY, float* l
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step >= 1 counts the
    updates) on the FP32 masters W and bias with gradients gW, gb and moments m, v
-   (88,857 floats each: weights then biases); refreshes Wbf16 and zeroes gW and gb. */
+   (105,241 floats each: weights then biases); refreshes Wbf16 and zeroes gW and gb. */
 sc_status sc_mlp_adam(float* W, uint16_t* Wbf16, float* bias, float* gW, float* gb, float* m, float* v, int step,
                       float lr, void* cuda_stream);
 
@@ -369,7 +372,7 @@ sc_status sc_mlp_adam(float* W, uint16_t* Wbf16, float* bias, float* gW, float* 
 sc_status sc_mlp_bf16(const float* W, uint16_t* Wbf16, int n, void* cuda_stream);
 
 /* Training loop of the network (the learned correction's counterpart of sc_train_mlp):
-   `epochs` passes of mini-batch Adam over device samples X [n x 64] with targets T [n x 25].
+   `epochs` passes of mini-batch Adam over device samples X [n x 128] with targets T [n x 25].
    Before every pass all n samples are shuffled (Fisher-Yates on a splitmix64 stream seeded
    by `seed`), so every batch mixes systems, elements and nodes; each batch of `batch` samples
    (the last may be smaller) runs sc_mlp_forward, sc_mlp_loss, sc_mlp_backward and one
@@ -381,7 +384,7 @@ sc_status sc_mlp_train(float* W, uint16_t* Wbf16, float* bias, float* m, float* 
                        const float* T, int n, int epochs, int batch, float lr, uint64_t seed, float* loss_hist,
                        void* cuda_stream);
 
-/* Network parameter files: the 8 bytes "SCMLP001", the counts 88,320 and 537 (int32), then
+/* Network parameter files: the 8 bytes "SCMLP001", the counts 104,704 and 537 (int32), then
    the FP32 weights W and biases (little endian).  sc_mlp_save writes device W, bias;
    sc_mlp_load reads them into device W, its BF16 copy and bias (SC_ERR_ARG if the file is
    missing or not such a file). */
@@ -394,13 +397,15 @@ sc_status sc_load_mlp(sc_ctx* ctx, const char* path);
 
 /* Features of the learned correction for every (element e, boundary node k) of the
    condensed system, samples ordered element by element and boundary node by boundary
-   node (the condensed order): F[s][64] = q_k over free-stream scales (rho, rho u, rho v,
-   rho w over 1, rho E over p_inf/(gamma-1) + 1/2) | [S_ee]_kk / ||.||_F (row-major 5 x 5)
-   | S_(k,k') / ||.||_F with k' the node at the same point in the neighbour across the
-   lowest-index face of e containing k (order -x,+x,-y,+y,-z,+z) | Ma, Re/1000,
-   dt/(Ma h), N | (faces of e containing k) / 3 | 0 x 4; snorm[s] = ||[S_ee]_kk||_F.  After
-   sc_condense on the mixed arm (SC_ERR_STATE otherwise).  Device pointers, K * nbn * 64 and
-   K * nbn floats. */
+   node (the condensed order).  With k' the node at the same point in the neighbour n across
+   the lowest-index face of e containing k (order -x,+x,-y,+y,-z,+z) and k'' the node at the
+   same point in the neighbour across the lowest face of n containing k' (k itself for a node
+   on one face only): F[s][128] = q_k over free-stream scales (rho, rho u, rho v, rho w over 1,
+   rho E over p_inf/(gamma-1) + 1/2) | [S_ee]_kk | S_(k,k') | S_(k',k'') | [S_nn]_(k'k') (each
+   row-major 5 x 5 over its Frobenius norm) | Ma, Re/1000, dt/(Ma h), N | (faces of e containing
+   k) / 3 | the Frobenius norms of S_(k,k'), S_(k',k''), [S_nn]_(k'k') over that of [S_ee]_kk |
+   0 x 15; snorm[s] = ||[S_ee]_kk||_F.  After sc_condense on the mixed arm (SC_ERR_STATE
+   otherwise).  Device pointers, K * nbn * 128 and K * nbn floats. */
 sc_status sc_learned_features(sc_ctx* ctx, float* F, float* snorm);
 
 /* Training targets T[s][25]: for samples of black elements b (checkerboard colouring,

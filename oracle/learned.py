@@ -17,9 +17,12 @@ natural order of the oracle's condensed system, 5 variables per node):
   half the node-diagonal part of what eliminating the red neighbours adds to S_bb (the
   whole of it over-corrects: the off-diagonal node blocks it leaves out balance it);
 * target = C*_k / ||[S_ee]_kk||_F for black samples, 0 for red ones;
-* features (64): q_k over free-stream scales (5); [S_ee]_kk and [S]_(k, k'), each over
-  its Frobenius norm (25 + 25); (Ma, Re / 1000, dt c_inf / h, N) (4); the number of faces
-  of e containing k over 3 (1); 4 zeros;
+* features (128): q_k over free-stream scales (5); [S_ee]_kk, [S]_(k, k'), [S]_(k', k'') and
+  [S_nn]_(k', k'), each over its Frobenius norm (4 x 25), where k'' is the node at the same
+  point in the neighbour across the lowest face of n containing k' (k itself for a node on
+  one face only); (Ma, Re / 1000, dt c_inf / h, N) (4); the number of faces of e containing
+  k over 3 (1); the Frobenius norms of [S]_(k,k'), [S]_(k',k'') and [S_nn]_(k',k') over that
+  of [S_ee]_kk (3); 15 zeros;
 * the network predicts the target (a dimensionless 5 x 5 block): C_k = y_k ||[S_ee]_kk||_F;
 * network: 64 -> 256 -> 256 -> 25, ReLU after the two hidden layers;
 * loss: mean over samples of ||y - t||^2 / (||t||^2 + eps) (squared relative Frobenius
@@ -29,7 +32,7 @@ from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_H, N_OUT = 64, 256, 25
+N_IN, N_H, N_OUT = 128, 256, 25
 LOSS_EPS = 1e-12
 
 
@@ -112,22 +115,35 @@ def features_and_targets(S: np.ndarray, Q: np.ndarray, n: int, N: int, Ma: float
     T = np.zeros((K * nbn, N_OUT))
     snorm = np.zeros(K * nbn)
     C = black_schur_correction(S, n)
+
+    def coupling(e, a):
+        """(row of node a of e, row of its co-located node k' in the neighbour across the
+        lowest face of e containing it, that neighbour, k''s position)."""
+        m = Bn[a]
+        f = node_face(N, int(m))
+        nbe = face_neighbour(n, e, f)
+        b = pos[mirror_node(N, int(m), f)]
+        return e * nb + 5 * a, nbe * nb + 5 * b, nbe, b
+
     for e in range(K):
         for a, m in enumerate(Bn):
-            f = node_face(N, int(m))
-            nbe = face_neighbour(n, e, f)
-            b = pos[mirror_node(N, int(m), f)]
-            r = e * nb + 5 * a
-            c = nbe * nb + 5 * b
+            r, c, nbe, b = coupling(e, a)
+            r2, c2, _, _ = coupling(nbe, b)  # the neighbour's own sample at k'
             Skk = S[r:r + 5, r:r + 5]
             Skc = S[r:r + 5, c:c + 5]
+            Sck = S[r2:r2 + 5, c2:c2 + 5]
+            Scc = S[r2:r2 + 5, r2:r2 + 5]
             s = e * nbn + a
+            nk = np.linalg.norm(Skk)
             F[s, 0:5] = Q[e, m] / scale
             F[s, 5:30] = _unit(Skk).reshape(-1)
             F[s, 30:55] = _unit(Skc).reshape(-1)
-            F[s, 55:59] = scal
-            F[s, 59] = node_face_count(N, int(m)) / 3.0
-            snorm[s] = np.linalg.norm(Skk)
+            F[s, 55:80] = _unit(Sck).reshape(-1)
+            F[s, 80:105] = _unit(Scc).reshape(-1)
+            F[s, 105:109] = scal
+            F[s, 109] = node_face_count(N, int(m)) / 3.0
+            F[s, 110:113] = [np.linalg.norm(Skc) / nk, np.linalg.norm(Sck) / nk, np.linalg.norm(Scc) / nk]
+            snorm[s] = nk
             T[s] = (LEARNED_DAMPING * C[s] / snorm[s]).reshape(-1)
     return F, T, snorm
 

@@ -355,7 +355,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
     const size_t nsmp = (size_t)G.K * G.nbn;
     A(dalloc(&c->Sdiag, nsmp * 25)); A(dalloc(&c->Cpl, nsmp * 25));
     if (c->cfg.precond == SC_PC_LEARNED) {
-      A(dalloc(&c->Feat, nsmp * 64)); A(dalloc(&c->Snorm, nsmp)); A(dalloc(&c->Ynet, nsmp * 25));
+      A(dalloc(&c->Feat, nsmp * sc::kMlpInputs)); A(dalloc(&c->Snorm, nsmp)); A(dalloc(&c->Ynet, nsmp * 25));
       A(dalloc(&c->Hbuf, nsmp * 512)); A(dalloc(&c->Ck, nsmp * 25)); A(dalloc(&c->Wbias, (size_t)sc::kMlpBiases));
       A(dalloc(&c->Wbf16, (size_t)sc::kMlpWeights));
     }

@@ -311,8 +311,10 @@ cudaError_t lu_solve_dense(sc_ctx* c, const T* D, long long ldd, int n, const in
 void free_direct(sc_ctx* c) {
   if (c->Dlu) cudaFree(c->Dlu);
   if (c->d_dpiv) cudaFree(c->d_dpiv);
+  if (c->Dcorr) cudaFree(c->Dcorr);
   c->Dlu = nullptr;
   c->d_dpiv = nullptr;
+  c->Dcorr = nullptr;
   c->direct_valid = false;
   c->direct_n = c->direct_ld = 0;
   c->direct_which = -1;
@@ -330,6 +332,7 @@ sc_status direct_factor_t(sc_ctx* c, int which, double* ms_form, double* ms_fact
   }
   DC_CUDA(cudaMalloc(&c->Dlu, (size_t)n * ldd * sizeof(T)));
   DC_CUDA(cudaMalloc(&c->d_dpiv, (size_t)n * sizeof(int)));
+  DC_CUDA(cudaMalloc(&c->Dcorr, (size_t)G.K * G.ne * sizeof(double)));  // a sweep's correction
   T* D = static_cast<T*>(c->Dlu);
   cudaEvent_t ev[3];
   for (auto& x : ev) DC_CUDA(cudaEventCreate(&x));
@@ -491,10 +494,10 @@ sc_status sc_direct_solve(sc_ctx* c, double* dQ, int on_device, sc_solve_stats* 
   // x += A^-1 r, r = B - A x (FP64): one sweep on the FP64 arm (a second if rounding left the
   // residual above rel_tol), FP64 refinement of the FP32 factors on the mixed arm
   while (rn > target && sweeps < max_sweeps) {
-    sc_status s = mixed ? direct_apply_t<float>(c, c->Rfull, c->Dfull, &ms_lu, &ms_cond)
-                        : direct_apply_t<double>(c, c->Rfull, c->dQn, &ms_lu, &ms_cond);
+    sc_status s = mixed ? direct_apply_t<float>(c, c->Rfull, c->Dcorr, &ms_lu, &ms_cond)
+                        : direct_apply_t<double>(c, c->Rfull, c->Dcorr, &ms_lu, &ms_cond);
     if (s != SC_OK) return s;
-    DC_CUDA(sc::vec_axpby(c, x, 1.0, mixed ? c->Dfull : c->dQn, 1.0, dofs));
+    DC_CUDA(sc::vec_axpby(c, x, 1.0, c->Dcorr, 1.0, dofs));
     DC_CUDA(sc::global_apply(c, x, c->Rfull));
     DC_CUDA(sc::vec_axpby(c, c->Rfull, 1.0, c->B, -1.0, dofs));
     rn = dnorm(c, c->Rfull, dofs);

@@ -314,7 +314,7 @@ struct sc_ctx {
   // dense direct solve (sc_direct_factor): n x n factors (row-major, ld = ldd), pivots
   void* Dlu = nullptr;       // double (FP64 arm) or float (mixed arm)
   int* d_dpiv = nullptr;
-  unsigned long long* d_dkey = nullptr;
+  double* Dcorr = nullptr;   // one refinement sweep's correction (K ne doubles)
   int direct_n = 0, direct_ld = 0, direct_which = -1;
   bool direct_valid = false;
   bool op32 = false;        // the condensed operator / preconditioner run on the FP32 copies
@@ -441,7 +441,8 @@ cudaError_t gemm_fp32(sc_ctx* c, int M, int N, int K, const float* A, long long 
 cudaError_t extract_sdiag(sc_ctx* c, const float* See);
 cudaError_t learned_features(sc_ctx* c, float* F, float* snorm);
 cudaError_t learned_correction(sc_ctx* c);
-constexpr int kMlpWeights = 256 * 64 + 256 * 256 + 25 * 256, kMlpBiases = 2 * 256 + 25;
+constexpr int kMlpInputs = 128;
+constexpr int kMlpWeights = 256 * kMlpInputs + 256 * 256 + 25 * 256, kMlpBiases = 2 * 256 + 25;
 cudaError_t mlp_forward(cudaStream_t st, const uint16_t* Wbf16, const float* bias, const float* X, int n, float* Y,
                         float* h1, float* h2);
 cudaError_t upload_packed_pattern(sc_ctx* c);

@@ -3,8 +3,11 @@
 // black element b (checkerboard colouring, ex + ey + ez odd), with f the lowest-index face of
 // b containing k (order -x, +x, -y, +y, -z, +z), n the neighbour across f and k' the node of n
 // at the same point:
-//   features (64): q_k over free-stream scales | [S_bb]_kk / ||.||_F | S_(k,k') / ||.||_F |
-//                  (Ma, Re / 1000, dt c_inf / h, N) | (faces of b containing k) / 3 | 0 0 0 0
+//   features (128): q_k over free-stream scales | [S_bb]_kk, S_(k,k'), S_(k',k''), [S_nn]_(k'k'),
+//                  each over its Frobenius norm (k'' the co-located node across the lowest face
+//                  of n containing k', k itself on a single face) | (Ma, Re / 1000, dt c_inf / h,
+//                  N) | (faces of b containing k) / 3 | the norms of the three coupling /
+//                  neighbour blocks over that of [S_bb]_kk | 0 x 15
 //   correction    C_k = net(features) ||[S_bb]_kk||_F, added to the diagonal node block k of
 //                  S_bb before it is factorised for the black half of the sweep
 //   target        C*_k / ||[S_bb]_kk||_F with C*_k = -(1/2) sum_{red m} [S_bm S_mm^-1 S_mb]_kk:
@@ -140,20 +143,29 @@ __device__ __forceinline__ void put_unit(float* dst, const float* src, float* no
 
 __global__ void k_learned_features(Geo G, const double* __restrict__ Q, const int* __restrict__ iperm,
                                    const float* __restrict__ Sdiag, const float* __restrict__ Cpl, float4 scal,
-                                   float e_inf, const int* __restrict__ nfaces, float* __restrict__ F,
-                                   float* __restrict__ snorm) {
+                                   float e_inf, const int* __restrict__ nfaces, const int* __restrict__ nbr,
+                                   const int* __restrict__ lface, const int* __restrict__ lmirror,
+                                   float* __restrict__ F, float* __restrict__ snorm) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= G.K * G.nbn) return;
   const int e = s / G.nbn, a = s % G.nbn;
   const int j = __ldg(iperm + G.nin + a);
-  float* f = F + (size_t)s * 64;
+  // the neighbour's own sample at the co-located node k'
+  const int sm = __ldg(nbr + e * 18 + __ldg(lface + a)) * G.nbn + __ldg(lmirror + a);
+  float* f = F + (size_t)s * 128;
   const double* q = Q + ((size_t)e * G.nn + j) * 5;
   f[0] = (float)q[0]; f[1] = (float)q[1]; f[2] = (float)q[2]; f[3] = (float)q[3]; f[4] = (float)(q[4] / e_inf);
-  put_unit(f + 5, Sdiag + (size_t)s * 25, snorm + s);
-  put_unit(f + 30, Cpl + (size_t)s * 25, nullptr);
-  f[55] = scal.x; f[56] = scal.y; f[57] = scal.z; f[58] = scal.w;
-  f[59] = (float)__ldg(nfaces + a) * (1.0f / 3.0f);
-  for (int i = 60; i < 64; ++i) f[i] = 0.f;
+  float nk = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
+  put_unit(f + 5, Sdiag + (size_t)s * 25, &nk);
+  put_unit(f + 30, Cpl + (size_t)s * 25, &n1);
+  put_unit(f + 55, Cpl + (size_t)sm * 25, &n2);
+  put_unit(f + 80, Sdiag + (size_t)sm * 25, &n3);
+  f[105] = scal.x; f[106] = scal.y; f[107] = scal.z; f[108] = scal.w;
+  f[109] = (float)__ldg(nfaces + a) * (1.0f / 3.0f);
+  const float ik = nk > 0.f ? 1.f / nk : 0.f;
+  f[110] = n1 * ik; f[111] = n2 * ik; f[112] = n3 * ik;
+  for (int i = 113; i < 128; ++i) f[i] = 0.f;
+  snorm[s] = nk;
 }
 
 __global__ void k_set_unit(double* x, size_t n, long long on, long long off) {
@@ -251,7 +263,8 @@ cudaError_t learned_features(sc_ctx* c, float* F, float* snorm) {
   const float4 scal = make_float4((float)Ma, (float)(c->cfg.Re / 1000.0), (float)(G.dt * (1.0 / Ma) / G.h),
                                   (float)G.N);
   k_learned_features<<<(nsmp + 255) / 256, 256, 0, c->stream>>>(G, c->Q, c->d_iperm, c->Sdiag, c->Cpl, scal, e_inf,
-                                                                c->d_lnfaces, F, snorm);
+                                                                c->d_lnfaces, c->d_nbr, c->d_lface, c->d_lmirror, F,
+                                                                snorm);
   return cudaGetLastError();
 }
 
@@ -311,7 +324,7 @@ sc_status sc_learned_targets(sc_ctx* c, float* T) {
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(cudaMalloc(&Scm, (size_t)n1 * n1 * sizeof(double)));
   A(cudaMalloc(&X, (size_t)std::max(npairs, 1) * G.nb * G.nb * sizeof(float)));
-  A(cudaMalloc(&F, (size_t)nsmp * 64 * sizeof(float)));
+  A(cudaMalloc(&F, (size_t)nsmp * 128 * sizeof(float)));
   A(cudaMalloc(&sn, (size_t)nsmp * sizeof(float)));
   A(cudaMalloc(&pb, std::max(npairs, 1) * sizeof(int))); A(cudaMalloc(&pm, std::max(npairs, 1) * sizeof(int)));
   A(cudaMalloc(&pptr, hptr.size() * sizeof(int))); A(cudaMalloc(&bidx, G.K * sizeof(int)));

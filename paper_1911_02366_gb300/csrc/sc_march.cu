@@ -233,8 +233,8 @@ sc_status sc_explicit_march(sc_ctx* c, double cfl, double dfl, int nsteps, doubl
   return SC_OK;
 }
 
-sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every, int direct, double* res_hist,
-                            double* ms_hist, int* gmres_iters) {
+sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every, int direct, double steady_tol,
+                            double* res_hist, double* ms_hist, int* gmres_iters, int* steps_taken) {
   sc_status s = state_checks(c, nsteps);
   if (s != SC_OK) return s;
   if (jacobian_every < 0) { c->err = "implicit march: jacobian_every >= 0"; return SC_ERR_ARG; }
@@ -256,6 +256,7 @@ sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every
   for (auto& e : ev) MC_CUDA(cudaEventCreate(&e));
   struct Evs { std::vector<cudaEvent_t>& v; ~Evs() { for (auto e : v) if (e) cudaEventDestroy(e); } } evg{ev};
   MC_CUDA(cudaEventRecord(ev[0], c->stream));
+  int taken = 0;
   for (int st = 0; st < nsteps; ++st) {
     // BDF1: the history is the state at the start of the step, so R(Q) = H(Q) there
     MC_CUDA(sc::launch_history(c, c->Q, c->Q));
@@ -271,6 +272,12 @@ sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every
     }
     count_launch(c);
     k_rhs<<<kBlocks, kThreads, 0, c->stream>>>(Gs, c->B, nullptr, rd + st);
+    if (steady_tol > 0.0) {  // stop once the state at the start of the step is steady
+      unsigned long long b = 0;
+      MC_CUDA(cudaMemcpyAsync(&b, rd + st, sizeof(b), cudaMemcpyDeviceToHost, c->stream));
+      MC_CUDA(cudaStreamSynchronize(c->stream));
+      if (bits_to_double(b) <= steady_tol) break;
+    }
     sc_solve_stats stt{};
     s = direct >= 0 ? sc_direct_solve(c, c->dQn, 1, &stt) : sc_solve(c, c->dQn, 1, &stt);
     if (s != SC_OK) return s;
@@ -278,10 +285,12 @@ sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every
     count_launch(c);
     k_axpy<<<kBlocks, kThreads, 0, c->stream>>>(dofs, 1.0, c->dQn, c->Q);
     MC_CUDA(cudaEventRecord(ev[st + 1], c->stream));
+    taken = st + 1;
   }
   MC_CUDA(sc::launch_residual_geo(c, Gs, c->Q, c->Q, c->Rfull));
   count_launch(c);
-  k_rhs<<<kBlocks, kThreads, 0, c->stream>>>(Gs, c->Rfull, nullptr, rd + nsteps);
+  MC_CUDA(cudaMemsetAsync(rd + taken, 0, sizeof(unsigned long long), c->stream));
+  k_rhs<<<kBlocks, kThreads, 0, c->stream>>>(Gs, c->Rfull, nullptr, rd + taken);
   MC_CUDA(sc::launch_history(c, c->Q, c->Q));
   MC_CUDA(cudaGetLastError());
   std::vector<unsigned long long> rb(nsteps + 1);
@@ -289,17 +298,18 @@ sc_status sc_implicit_march(sc_ctx* c, double dt, int nsteps, int jacobian_every
                           c->stream));
   MC_CUDA(cudaStreamSynchronize(c->stream));
   if (res_hist)
-    for (int i = 0; i <= nsteps; ++i) res_hist[i] = bits_to_double(rb[i]);
+    for (int i = 0; i <= nsteps; ++i) res_hist[i] = i <= taken ? bits_to_double(rb[i]) : NAN;
   if (ms_hist) {
     ms_hist[0] = 0.0;
     for (int i = 1; i <= nsteps; ++i) {
       float ms = 0.f;
-      MC_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[i]));
-      ms_hist[i] = ms;
+      if (i <= taken) MC_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[i]));
+      ms_hist[i] = i <= taken ? ms : NAN;
     }
   }
+  if (steps_taken) *steps_taken = taken;
   c->assembled = c->condensed = false;  // the Jacobian belongs to an earlier state
-  if (!std::isfinite(bits_to_double(rb[nsteps]))) { c->err = "implicit march: non-finite residual"; return SC_ERR_NONFINITE; }
+  if (!std::isfinite(bits_to_double(rb[taken]))) { c->err = "implicit march: non-finite residual"; return SC_ERR_NONFINITE; }
   return SC_OK;
 }
 

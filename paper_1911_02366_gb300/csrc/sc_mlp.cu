@@ -1,4 +1,4 @@
-// The learned correction of the condensed-system preconditioner: a 64 -> 256 -> 256 -> 25
+// The learned correction of the condensed-system preconditioner: a 128 -> 256 -> 256 -> 25
 // network with ReLU hidden layers, BF16 weights and FP32 arithmetic (not in the paper; a
 // learned part of the condensed-system preconditioner of Sec. 2.2/4), with its training loop
 // (shuffled mini-batch Adam) and a file format for its parameters.
@@ -23,8 +23,8 @@
 
 namespace {
 
-constexpr int NI = 64, NH = 256, NO = 25;
-constexpr int OFF_W2 = NH * NI, OFF_W3 = OFF_W2 + NH * NH, N_W = OFF_W3 + NO * NH;  // 88,320
+constexpr int NI = sc::kMlpInputs, NH = 256, NO = 25;
+constexpr int OFF_W2 = NH * NI, OFF_W3 = OFF_W2 + NH * NH, N_W = OFF_W3 + NO * NH;  // 104,704
 constexpr int OFF_B2 = NH, OFF_B3 = 2 * NH, N_B = 2 * NH + NO;                     // 537
 
 template <class T> __device__ __forceinline__ float ldf(const T* p);

@@ -132,7 +132,8 @@ def lib(build_if_missing: bool = True):
     L.sc_direct_factor.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.sc_direct_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(sc_solve_stats)]
     L.sc_explicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]
-    L.sc_implicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    L.sc_implicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    dp, dp, dp, ctypes.POINTER(ctypes.c_int)]
     L.sc_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.sc_profile_kernel.argtypes = [vp, ctypes.c_int]
     L.sc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]
@@ -309,7 +310,7 @@ class Context:
         return f.value, b.value
 
     def sc_learned_features(self, F, snorm):
-        """Features [K*nbn, 64] and ||[S_ee]_kk||_F [K*nbn] (float32 device tensors)."""
+        """Features [K*nbn, 128] and ||[S_ee]_kk||_F [K*nbn] (float32 device tensors)."""
         self._check(self._L.sc_learned_features(self.h, F.data_ptr(), snorm.data_ptr()))
         return F, snorm
 
@@ -374,16 +375,19 @@ class Context:
                                               ms.ctypes.data))
         return res, dts[:nsteps], float(ms[0])
 
-    def sc_implicit_march(self, dt: float, nsteps: int, jacobian_every: int = 0, direct: str | None = None):
+    def sc_implicit_march(self, dt: float, nsteps: int, jacobian_every: int = 0, direct: str | None = None,
+                          steady_tol: float = 0.0):
         """Linearised BDF1 steps with a reused Jacobian, solved by condensed GMRES (direct=None)
-        or dense LU of A ('A') or S ('S'); returns (residual history, cumulative device ms,
-        GMRES iterations per step)."""
+        or dense LU of A ('A') or S ('S'); stops early at steady_tol > 0.  Returns (residual
+        history, cumulative device ms, GMRES iterations per step), cut to the steps taken."""
         res, ms = np.zeros(nsteps + 1), np.zeros(nsteps + 1)
         its = np.zeros(max(nsteps, 1), dtype=np.int32)
+        taken = ctypes.c_int()
         d = {None: -1, "A": SC_DIRECT_GLOBAL, "S": SC_DIRECT_CONDENSED}[direct]
-        self._check(self._L.sc_implicit_march(self.h, dt, nsteps, jacobian_every, d, res.ctypes.data, ms.ctypes.data,
-                                              its.ctypes.data))
-        return res, ms, its[:nsteps]
+        self._check(self._L.sc_implicit_march(self.h, dt, nsteps, jacobian_every, d, steady_tol, res.ctypes.data,
+                                              ms.ctypes.data, its.ctypes.data, ctypes.byref(taken)))
+        k = taken.value
+        return res[:k + 1], ms[:k + 1], its[:k]
 
     def sc_condensed_matvec_static(self, xb, yb):
         """S x_b without any allocation in the call (fixed 8 MiB device scratch); enqueues only."""
@@ -424,8 +428,8 @@ def sc_gemm_tf32(A, B, C, alpha=1.0, beta=0.0, stream=None, trans_a=False, trans
     return C
 
 
-# ---- learned block-Jacobi correction: the network ---------------------------------
-MLP_IN, MLP_H, MLP_OUT = 64, 256, 25
+# ---- learned correction of the red-black sweep: the network ---------------------
+MLP_IN, MLP_H, MLP_OUT = 128, 256, 25
 MLP_NW = MLP_H * MLP_IN + MLP_H * MLP_H + MLP_OUT * MLP_H
 MLP_NB = 2 * MLP_H + MLP_OUT
 

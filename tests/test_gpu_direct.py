@@ -44,13 +44,14 @@ def test_direct_solve_matches_oracle_global_solve(which, arm, tc, n, N):
 
 
 def test_direct_factor_of_the_cfl50_4x4x4_N3_system():
-    """The 4^3, N = 3, CFL-50 system that stalls restarted GMRES: a direct condensed solve on
-    the mixed arm reaches the oracle's solution to 1e-8 after FP64 refinement."""
+    """The 4^3, N = 3, CFL-50 system that stalls restarted GMRES: a direct condensed solve
+    (FP64 dense LU of S, 17,920 rows) reaches the oracle's solution to 1e-10.  (FP32 factors
+    are not enough at this conditioning: their refinement diverges, and the solve reports it.)"""
     from paper_1911_02366_gb300 import sc
     n, N = 4, 3
     Q, dt = I.tgv_state(n, N, cfl=50.0, seed=0)
     p = O.Params(n=n, N=N, dt=dt)
-    ctx = gpu_context(precision=sc.SC_PREC_MIXED, rel_tol=1e-11, max_refine=40)
+    ctx = gpu_context(rel_tol=1e-12)
     ctx.sc_set_mesh(n, TWO_PI, N)
     ctx.sc_set_timestep(dt, 1)
     ctx.sc_set_state(Q, Q)
@@ -62,7 +63,7 @@ def test_direct_factor_of_the_cfl50_4x4x4_N3_system():
     A = O.jacobian(p, Q)
     B = -O.residual(p, Q).reshape(-1)
     x = O.global_solve_dense(A, B)
-    assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < 1e-8, st
+    assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < 1e-10, st
 
 
 @pytest.mark.parametrize("direct", ["A", "S"])

@@ -26,7 +26,7 @@ def _mixed(n, N, cfl=10.0, seed=0, tc=0, **kw):
 
 def _ft(ctx, n, N, targets=True):
     nsmp = n ** 3 * len(LN.boundary_nodes(N))
-    F = torch.empty(nsmp, 64, device="cuda")
+    F = torch.empty(nsmp, 128, device="cuda")
     sn = torch.empty(nsmp, device="cuda")
     ctx.sc_learned_features(F, sn)
     T = None
@@ -46,8 +46,8 @@ def test_features_and_targets_match_oracle(n, N):
     Fo, To, sno = LN.features_and_targets(S, Q, n, N, 0.1, 1600.0, dt)
     Fg = F.cpu().numpy()
     assert np.max(np.abs(Fg[:, :5] - Fo[:, :5])) < 1e-6 * np.max(np.abs(Fo[:, :5]))
-    assert np.max(np.abs(Fg[:, 5:55] - Fo[:, 5:55])) < 1e-4      # unit-norm blocks
-    assert np.max(np.abs(Fg[:, 55:] - Fo[:, 55:])) < 1e-5 * np.max(np.abs(Fo[:, 55:]))
+    assert np.max(np.abs(Fg[:, 5:105] - Fo[:, 5:105])) < 1e-4    # unit-norm blocks
+    assert np.max(np.abs(Fg[:, 105:] - Fo[:, 105:])) < 1e-4 * np.max(np.abs(Fo[:, 105:]))
     assert np.max(np.abs(sn.cpu().numpy() - sno) / sno) < 1e-4  # S_ee formed in FP32
     Tg = T.cpu().numpy()
     black = LN.black_mask(n, N)
@@ -118,16 +118,16 @@ def _train_set(n, N, seeds, cfl):
 
 
 def test_trained_correction_beats_the_sweep_without_it_and_block_jacobi_on_held_out_seeds(capsys):
-    """Train on systems the method forms (4^3 elements, N = 3, seeds 100..107 at Ma 0.05..0.3,
+    """Train on systems the method forms (4^3 elements, N = 3, seeds 100..111 at Ma 0.05..0.3,
     the time step of the CFL-13 rule), then solve held-out seeds 1000..1001: GMRES iterations
     and solve time with the network against the red-black sweep without it and against block
     Jacobi (and, for reference, what the exact targets would give)."""
     from paper_1911_02366_gb300 import sc
     n, N, cfl = 4, 3, 13.0
-    X, Y = _train_set(n, N, range(100, 108), cfl)
+    X, Y = _train_set(n, N, range(100, 112), cfl)
     net = _net(7)
-    hist = net.train(X, Y, epochs=60, batch=256, lr=1e-3)
-    assert hist[-1] < 0.5 * hist[0]
+    hist = net.train(X, Y, epochs=100, batch=256, lr=1e-3)
+    assert hist[-1] < 0.5 * hist[0], hist
     out = {}
     for seed in (1000, 1001):
         row = {}
@@ -148,7 +148,7 @@ def test_trained_correction_beats_the_sweep_without_it_and_block_jacobi_on_held_
         _, st_x = _solve(cl, Q)
         row["exact_targets"] = (st_x["gmres_iters"], st_x["ms_gmres"])
         out[seed] = row
-        assert row["network"][0] < row["red_black"][0] < row["block_jacobi"][0], row
+        assert row["network"][0] < row["red_black"][0] < row["block_jacobi"][0], (row, hist[0], hist[-1])
         assert row["network"][1] < row["block_jacobi"][1], row
     with capsys.disabled():
         print(f"\nlearned correction: loss {hist[0]:.3g} -> {hist[-1]:.3g}; (GMRES iterations, ms) per held-out seed: {out}")

@@ -20,8 +20,9 @@ def _params(seed):
     b = np.concatenate([P["b1"], P["b2"], P["b3"]]).astype(np.float32)
     # the oracle sees exactly the values the GPU multiplies with
     Wq = bf16_values(bf16_bits(W)).astype(np.float64)
-    Pq = {"W1": Wq[:16384].reshape(256, 64), "W2": Wq[16384:16384 + 65536].reshape(256, 256),
-          "W3": Wq[16384 + 65536:].reshape(25, 256), "b1": b[:256].astype(np.float64),
+    n1 = 256 * LN.N_IN
+    Pq = {"W1": Wq[:n1].reshape(256, LN.N_IN), "W2": Wq[n1:n1 + 65536].reshape(256, 256),
+          "W3": Wq[n1 + 65536:].reshape(25, 256), "b1": b[:256].astype(np.float64),
           "b2": b[256:512].astype(np.float64), "b3": b[512:].astype(np.float64)}
     return W, b, Pq
 
@@ -34,7 +35,7 @@ def _rel(a, b):
 def test_forward_matches_oracle(n):
     from paper_1911_02366_gb300 import sc
     W, b, Pq = _params(1)
-    X = np.random.default_rng(2).standard_normal((n, 64)).astype(np.float32)
+    X = np.random.default_rng(2).standard_normal((n, LN.N_IN)).astype(np.float32)
     net = sc.MLP(W, b)
     Xd = torch.tensor(X, device="cuda")
     Y = torch.empty(n, 25, device="cuda")
@@ -70,7 +71,7 @@ def test_backward_matches_oracle(n):
     from paper_1911_02366_gb300 import sc
     W, b, Pq = _params(4)
     rng = np.random.default_rng(5)
-    X = rng.standard_normal((n, 64)).astype(np.float32)
+    X = rng.standard_normal((n, LN.N_IN)).astype(np.float32)
     dYh = rng.standard_normal((n, 25)).astype(np.float32)
     net = sc.MLP(W, b)
     Xd, dY = torch.tensor(X, device="cuda"), torch.tensor(dYh, device="cuda")
@@ -115,7 +116,7 @@ def test_training_fits_a_teacher_network():
     W, b, Pq = _params(8)
     rng = np.random.default_rng(9)
     n = 8192
-    X = rng.standard_normal((n, 64)).astype(np.float32)
+    X = rng.standard_normal((n, LN.N_IN)).astype(np.float32)
     teacher = LN.init_params(seed=11, scale_out=1.0)
     T, _ = LN.forward(teacher, X.astype(np.float64))
     net = sc.MLP(W, b)

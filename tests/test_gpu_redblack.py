@@ -48,13 +48,16 @@ def test_red_black_apply_satisfies_the_sweep_equations_with_oracle_S(arm, n, N):
         sl = slice(e * nb, (e + 1) * nb)
         r[sl] = S[sl, sl] @ z[sl] - v[sl] + (t[sl] if col[e] == 1 else 0.0)
     scale = np.max(np.sum(np.abs(S), axis=1)) * np.max(np.abs(z)) + np.max(np.abs(v))
-    tol = 1e-13 if arm == "fp64" else 2e-6
+    # the level the element factors themselves reach (S_ee is formed with the explicit interior
+    # inverse): the red rows, plain block Jacobi, show it as well as the black ones
+    tol = 1e-7 if arm == "fp64" else 2e-5
     re = np.abs(r).reshape(K, nb).max(axis=1) / scale
     worst = int(np.argmax(np.abs(r)))
     diag = {"red_max": float(re[col == 0].max()), "black_max": float(re[col == 1].max()),
             "worst_elem": worst // nb, "worst_row": worst % nb, "worst_colour": int(col[worst // nb]),
             "z_at_worst_elem": float(np.max(np.abs(z[(worst // nb) * nb:(worst // nb + 1) * nb])))}
     assert np.max(np.abs(r)) <= tol * scale, diag
+    assert diag["black_max"] <= 10 * max(diag["red_max"], tol * 1e-3), diag  # no worse than block Jacobi rows
     # the oracle's sweep agrees to the block conditioning (FP64) and the black part is not
     # block Jacobi (the sweep reaches across the colours)
     ref = O.red_black_apply(S, n, v)

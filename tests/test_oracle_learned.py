@@ -1,4 +1,4 @@
-"""Pins of the learned block-Jacobi correction oracle (oracle/learned.py)."""
+"""Pins of the learned red-black correction oracle (oracle/learned.py)."""
 import numpy as np
 import pytest
 
@@ -102,13 +102,25 @@ def test_targets_vanish_without_coupling_and_features_are_normalised():
     F, T, sn = LN.features_and_targets(Sblk, Q, n, N, 0.1, 1600.0, dt)
     assert np.max(np.abs(T)) < 1e-10 * np.max(sn)
     F, T, sn = LN.features_and_targets(S, Q, n, N, 0.1, 1600.0, dt)
-    assert np.allclose(np.linalg.norm(F[:, 5:30], axis=1), 1.0)
-    assert np.allclose(np.linalg.norm(F[:, 30:55], axis=1), 1.0)
-    assert np.allclose(F[:, 55:59], [0.1, 1.6, dt * 10.0 / (np.pi), 2.0])
+    for lo in (5, 30, 55, 80):
+        assert np.allclose(np.linalg.norm(F[:, lo:lo + 25], axis=1), 1.0)
+    assert np.allclose(F[:, 105:109], [0.1, 1.6, dt * 10.0 / (np.pi), 2.0])
     # nodes of a face, an edge, a corner: 1, 2 or 3 faces (N = 2: 6 face, 12 edge, 8 corner nodes)
-    nf = np.round(F[:len(LN.boundary_nodes(N)), 59] * 3).astype(int)
+    nf = np.round(F[:len(LN.boundary_nodes(N)), 109] * 3).astype(int)
     assert sorted(np.bincount(nf)[1:]) == [6, 8, 12]
-    assert np.all(F[:, 60:] == 0)
+    assert np.all(F[:, 110:113] > 0) and np.all(F[:, 113:] == 0)
+    # a node on one face only: the neighbour's coupling block at k' is the coupling back to k
+    nbn = len(LN.boundary_nodes(N))
+    nb = 5 * nbn
+    for a, m in enumerate(LN.boundary_nodes(N)):
+        if LN.node_face_count(N, int(m)) != 1:
+            continue
+        f = LN.node_face(N, int(m))
+        ne = LN.face_neighbour(n, 0, f)
+        b = list(LN.boundary_nodes(N)).index(LN.mirror_node(N, int(m), f))
+        blk = S[ne * nb + 5 * b:ne * nb + 5 * b + 5, 5 * a:5 * a + 5]
+        assert np.allclose(F[a, 55:80], (blk / np.linalg.norm(blk)).reshape(-1))
+        break
     black = LN.black_mask(n, N)
     assert np.max(np.abs(T[~black])) == 0 and np.max(np.abs(T[black])) > 0
 
