@@ -120,17 +120,14 @@ def train_correction(args, stream):
     """The learned arm's network, trained before the timed region on systems the method
     forms: 4^3-element Taylor-Green states at the workload's order, seeds 100.., Ma 0.05..0.3,
     each with the time step the CFL rule gives the workload's mesh at that Mach number;
-    features and targets of the black elements from the library, mini-batch Adam through
-    its kernels."""
+    features and targets (the node blocks of the face-block inverses) of every boundary node
+    from the library, shuffled mini-batch Adam through its kernels."""
     import torch
     from paper_1911_02366_gb300 import sc
     rng = np.random.default_rng(0)
     Fs, Ts = [], []
     t0 = time.perf_counter()
     n, N = 4, WORKLOAD["N"]
-    nbn = (N + 1) ** 3 - (N - 1) ** 3
-    col = np.array([((e % n) + (e // n) % n + e // (n * n)) % 2 for e in range(n ** 3)])
-    black = torch.tensor(np.repeat(col == 1, nbn), device="cuda")
     for i, Ma in enumerate((0.05, 0.1, 0.15, 0.2, 0.25, 0.3)):
         Q, _ = I.tgv_state(n, N, Ma=Ma, seed=100 + i, cfl=WORKLOAD["cfl"])
         dt = I.tgv_state(WORKLOAD["n"], N, Ma=Ma, seed=100 + i, cfl=WORKLOAD["cfl"])[1]  # the workload mesh's step
@@ -149,8 +146,8 @@ def train_correction(args, stream):
         T = torch.empty(nsmp, 25, device="cuda")
         c.sc_learned_features(F, sn)
         c.sc_learned_targets(T)
-        Fs.append(F[black])
-        Ts.append(T[black])
+        Fs.append(F)
+        Ts.append(T)
         c.close()
     X = torch.cat(Fs).contiguous()
     Y = torch.cat(Ts).contiguous()

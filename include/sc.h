@@ -81,10 +81,9 @@ typedef struct {
   int tensor_cores;      /* mixed arm: 1 = element Schur products and the LU trailing updates
                             of S_ee on the TF32 tensor cores (tcgen05), 0 = FP32 CUDA cores */
   double learned_min_reduction;  /* SC_PC_LEARNED: a GMRES restart cycle that reduces the
-                            condensed residual by less than this factor switches the rest of
-                            the solve to block Jacobi, the fallback (4: about block Jacobi's own
-                            average reduction per 30-iteration cycle on the 16^3, N = 4 Taylor-Green
-                            system, 357 iterations to 1e-8) */
+                            condensed residual by less than this factor (the learned sweep has
+                            stagnated) switches the rest of the solve to block Jacobi, the
+                            fallback (1.5) */
   int factor_fp16;       /* mixed arm: 1 = keep a copy of the block-Jacobi factors in FP16 for the
                             GMRES preconditioner (FP32 arithmetic; used only when every entry is
                             within the FP16 range, else the FP32 copy), 0 = FP32 only (default 0:
@@ -116,8 +115,8 @@ typedef struct {
 } sc_solve_stats;
 
 /* Fill *cfg with the defaults listed above (Re = 1600, Ma = 0.1, FP64, block Jacobi,
-   GMRES(30), 4000 iterations, rel_tol 1e-8, tensor_cores 1, learned_min_reduction 4).  Never fails
-   for a non-null cfg. */
+   GMRES(30), 4000 iterations, rel_tol 1e-8, tensor_cores 1, learned_min_reduction 1.5).  Never
+   fails for a non-null cfg. */
 sc_status sc_default_config(sc_config* cfg);
 
 /* Create a context that enqueues all work on `cuda_stream` (a cudaStream_t, or NULL
@@ -335,16 +334,21 @@ sc_status sc_hessenberg_eigvals(int m, const double* H, double* re, double* im);
 
 /* ---- Learned correction of the red-black sweep --------------------------------------
    Not in the paper (which preconditions GMRES on the condensed system with point Jacobi,
-   Sec. 4): a network maps 128 features of each boundary node k of each element to a 5 x 5
-   correction C_k added to the diagonal node block k of a black element's S_bb before the
-   black half of the red-black sweep factorises it (SC_PC_LEARNED).  Layout of the parameters
-   (shared by every call): weights W = [W1 (256 x 128) | W2 (256 x 256) | W3 (25 x 256)],
-   row-major, 104,704 values, kept as FP32 masters and as a BF16 copy (IEEE bfloat16 bit
-   patterns in uint16_t); biases b = [b1 (256) | b2 (256) | b3 (25)], FP32.  Layers:
-   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3; FP32 arithmetic.  All
-   pointers are device pointers unless stated; work is enqueued on cuda_stream and
-   synchronised before return.  SC_ERR_ARG for null pointers or bad sizes, SC_ERR_CUDA for
-   launch failures. */
+   Sec. 4).  With SC_PC_LEARNED the black half of the red-black sweep factorises
+   D_b = S_bb + C_b, C_b block diagonal over the 5 x 5 node blocks of the black element b:
+     C_k = -1/2 sum over the faces f of b containing k of S_(k,k'_f) Z_(k'_f) S_(k'_f,k),
+   k'_f the co-located node of the (red) neighbour across f and Z_(k') the diagonal node block
+   of the inverse of that neighbour's face block, [S_nn^-1]_(k'k') (the co-located part of the
+   Schur correction that eliminating the red neighbours adds to S_bb, halved).  A network
+   predicts the correction of each element's face-block inverse there: from 128 features of
+   node k' it gives y, and Z = [S_nn]_(k'k')^-1 + y / ||[S_nn]_(k'k')||_F (the exact Z needs n_b
+   unit solves per element).  Layout of the parameters (shared by every call): weights
+   W = [W1 (256 x 128) | W2 (256 x 256) | W3 (25 x 256)], row-major, 104,704 values, kept as
+   FP32 masters and as a BF16 copy (IEEE bfloat16 bit patterns in uint16_t); biases
+   b = [b1 (256) | b2 (256) | b3 (25)], FP32.  Layers: h1 = relu(W1 x + b1),
+   h2 = relu(W2 h1 + b2), y = W3 h2 + b3; FP32 arithmetic.  All pointers are device pointers
+   unless stated; work is enqueued on cuda_stream and synchronised before return.
+   SC_ERR_ARG for null pointers or bad sizes, SC_ERR_CUDA for launch failures. */
 
 /* y[n x 25] = net(X[n x 128]).  cache: NULL, or 4 n x 256 floats that receive z1, h1, z2,
    h2 (pre- and post-activations) for sc_mlp_backward; with NULL the call allocates
@@ -408,27 +412,24 @@ sc_status sc_load_mlp(sc_ctx* ctx, const char* path);
    otherwise).  Device pointers, K * nbn * 128 and K * nbn floats. */
 sc_status sc_learned_features(sc_ctx* ctx, float* F, float* snorm);
 
-/* Training targets T[s][25]: for samples of black elements b (checkerboard colouring,
-   ex + ey + ez odd), C*_k / ||[S_bb]_kk||_F with C*_k = -(1/2) sum over the red neighbours m
-   of [S_bm S_mm^-1 S_mb]_kk, half the node-diagonal part of what eliminating the red
-   neighbours adds to S_bb (row-major 5 x 5); zero for red samples.  Forms the dense condensed
-   matrix column by column with the condensed operator, so only for small meshes
-   ((K nb)^2 doubles <= 40 GB, else SC_ERR_ARG); S_mm^-1 from the condensation's factors.
-   After sc_condense on the mixed arm.  Device pointer, K * nbn * 25 floats. */
+/* Training targets T[s][25] = ([S_ee^-1]_kk - [S_ee]_kk^-1) ||[S_ee]_kk||_F for every sample
+   (row-major 5 x 5; elements of both colours): the correction of the inverse of the node block
+   to the node block of the face-block inverse, [S_ee^-1]_kk from unit solves with the
+   condensation's factors.  After sc_condense on the mixed arm.  Device pointer, K * nbn * 25
+   floats. */
 sc_status sc_learned_targets(sc_ctx* ctx, float* T);
 
 /* Network parameters for SC_PC_LEARNED (device pointers, layout of sc_mlp_forward; copied
    into the context).  With precond = SC_PC_LEARNED, sc_condense evaluates the network on the
-   features and factorises the black blocks S_bb + C, C_k = y_k ||[S_bb]_kk||_F, apart from the
-   plain factors, which block Jacobi (the fallback) keeps using. */
+   features of every boundary node, assembles the black blocks' corrections C and factorises
+   S_bb + C apart from the plain factors, which block Jacobi (the fallback) keeps using. */
 sc_status sc_set_learned_weights(sc_ctx* ctx, const uint16_t* Wbf16, const float* bias);
 
-/* Measurement hook for SC_PC_LEARNED: after sc_condense, replace the corrections by
-   scale * Ck (device, K * nbn * 25 floats, C_k row-major per sample, unscaled: the matrices
-   added to the diagonal node blocks of the black S_bb; red samples are ignored) and
-   refactorise the black blocks, e.g. with the exact targets times ||[S_bb]_kk||_F, to
+/* Measurement hook for SC_PC_LEARNED: after sc_condense, assemble the black corrections from
+   scale * Y instead of the network's outputs (device, K * nbn * 25 floats in the target form
+   of sc_learned_targets) and refactorise the black blocks, e.g. with the exact targets, to
    measure what a perfect network would give. */
-sc_status sc_set_learned_correction(sc_ctx* ctx, const float* Ck, float scale);
+sc_status sc_set_learned_correction(sc_ctx* ctx, const float* Y, float scale);
 
 /* ---- Batched condensation of elements of uneven order ---------------------------
    Not in the paper: the condensation set-up (A_ii^-1, Y, S_ee, LU of S_ee, solve layout;

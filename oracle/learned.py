@@ -3,28 +3,28 @@
 Not in the paper: the condensed system S x_b = g of Sec. 2.2 (eq. SC_step1) is solved by
 GMRES preconditioned with one forward block sweep over the checkerboard colouring of the
 elements (red: ex + ey + ez even): z_r = S_rr^{-1} v_r, then z_b = D_b^{-1} (v_b - sum S_bm z_m).
-A small network corrects the black blocks, D_b = S_bb + C_b with C_b block-diagonal over the
-5 x 5 node blocks.  Everything here is a plain FP64 restatement, written against the dense
-condensed matrix S of the oracle.
+The black blocks are corrected, D_b = S_bb + C_b, C_b block-diagonal over the 5 x 5 node
+blocks, from a network's prediction of the node blocks of the face-block inverses.
+Everything here is a plain FP64 restatement, written against the dense condensed matrix S of
+the oracle.
 
 Definitions (one sample per element e and boundary node k of e; boundary nodes in the
 natural order of the oracle's condensed system, 5 variables per node):
 
-* face of k: the lowest-index face containing k in the order -x, +x, -y, +y, -z, +z;
-  n = the face neighbour of e across it; k' = the node of n at the same point (k with
-  its index normal to the face mirrored, 0 <-> N);
-* exact correction of a black element b: C*_k = -(1/2) sum_{red m} [S_bm S_mm^{-1} S_mb]_kk,
-  half the node-diagonal part of what eliminating the red neighbours adds to S_bb (the
-  whole of it over-corrects: the off-diagonal node blocks it leaves out balance it);
-* target = C*_k / ||[S_ee]_kk||_F for black samples, 0 for red ones;
-* features (128): q_k over free-stream scales (5); [S_ee]_kk, [S]_(k, k'), [S]_(k', k'') and
-  [S_nn]_(k', k'), each over its Frobenius norm (4 x 25), where k'' is the node at the same
-  point in the neighbour across the lowest face of n containing k' (k itself for a node on
-  one face only); (Ma, Re / 1000, dt c_inf / h, N) (4); the number of faces of e containing
-  k over 3 (1); the Frobenius norms of [S]_(k,k'), [S]_(k',k'') and [S_nn]_(k',k') over that
-  of [S_ee]_kk (3); 15 zeros;
-* the network predicts the target (a dimensionless 5 x 5 block): C_k = y_k ||[S_ee]_kk||_F;
-* network: 64 -> 256 -> 256 -> 25, ReLU after the two hidden layers;
+* for each face f of e containing k: n_f = the face neighbour across it, k'_f = the node of
+  n_f at the same point (k with its index normal to f mirrored, 0 <-> N); the lowest of these
+  faces (order -x, +x, -y, +y, -z, +z) is f, with n and k';
+* Z_k = [S_ee^{-1}]_kk, the diagonal node block of the inverse of the element's face block;
+* target = (Z_k - [S_ee]_kk^{-1}) ||[S_ee]_kk||_F for every sample;
+* correction of a black element b: C_k = -(1/2) sum_f S_(k,k'_f) Z_(k'_f) S_(k'_f,k), with
+  Z_(k') = [S_nn]_(k'k')^{-1} + y_(k') / ||[S_nn]_(k'k')||_F from the network's output y (the
+  exact Z for y = target): the co-located part of the Schur correction of the red
+  neighbours, halved;
+* features (128): q_k over free-stream scales (5); [S_ee]_kk, [S]_(k,k'), [S]_(k',k) and
+  [S_nn]_(k',k'), each over its Frobenius norm (4 x 25); (Ma, Re / 1000, dt c_inf / h, N) (4);
+  the number of faces of e containing k over 3 (1); the Frobenius norms of [S]_(k,k'),
+  [S]_(k',k) and [S_nn]_(k',k') over that of [S_ee]_kk (3); 15 zeros;
+* network: 128 -> 256 -> 256 -> 25, ReLU after the two hidden layers;
 * loss: mean over samples of ||y - t||^2 / (||t||^2 + eps) (squared relative Frobenius
   error of the scaled correction).
 """
@@ -95,14 +95,26 @@ def node_face_count(N: int, m: int) -> int:
 LEARNED_DAMPING = 0.5
 
 
+def node_faces(N: int, m: int) -> list:
+    """The faces (0..5 = -x, +x, -y, +y, -z, +z) containing boundary node m, ascending."""
+    p = N + 1
+    c = (m % p, (m // p) % p, m // (p * p))
+    out = []
+    for d in range(3):
+        if c[d] == 0:
+            out.append(2 * d)
+        elif c[d] == N:
+            out.append(2 * d + 1)
+    return out
+
+
 def features_and_targets(S: np.ndarray, Q: np.ndarray, n: int, N: int, Ma: float, Re: float, dt: float,
                          L: float = 2.0 * np.pi, gamma: float = 1.4):
-    """Features [K*nbn, 64], scaled targets [K*nbn, 25] and the block norms ||[S_ee]_kk||_F.
+    """Features [K*nbn, 128], scaled targets [K*nbn, 25] and the block norms ||[S_ee]_kk||_F.
 
     S: dense condensed matrix (K*nb x K*nb) in the element-major condensed order.
     Q: state [K, (N+1)^3, 5].
     """
-    from .linalg import black_schur_correction
     Bn = boundary_nodes(N)
     nbn = len(Bn)
     nb = 5 * nbn
@@ -114,25 +126,15 @@ def features_and_targets(S: np.ndarray, Q: np.ndarray, n: int, N: int, Ma: float
     F = np.zeros((K * nbn, N_IN))
     T = np.zeros((K * nbn, N_OUT))
     snorm = np.zeros(K * nbn)
-    C = black_schur_correction(S, n)
-
-    def coupling(e, a):
-        """(row of node a of e, row of its co-located node k' in the neighbour across the
-        lowest face of e containing it, that neighbour, k''s position)."""
-        m = Bn[a]
-        f = node_face(N, int(m))
-        nbe = face_neighbour(n, e, f)
-        b = pos[mirror_node(N, int(m), f)]
-        return e * nb + 5 * a, nbe * nb + 5 * b, nbe, b
-
     for e in range(K):
+        blk = slice(e * nb, (e + 1) * nb)
+        Sinv = np.linalg.inv(S[blk, blk])
         for a, m in enumerate(Bn):
-            r, c, nbe, b = coupling(e, a)
-            r2, c2, _, _ = coupling(nbe, b)  # the neighbour's own sample at k'
-            Skk = S[r:r + 5, r:r + 5]
-            Skc = S[r:r + 5, c:c + 5]
-            Sck = S[r2:r2 + 5, c2:c2 + 5]
-            Scc = S[r2:r2 + 5, r2:r2 + 5]
+            f = node_face(N, int(m))
+            nbe = face_neighbour(n, e, f)
+            b = pos[mirror_node(N, int(m), f)]
+            r, c = e * nb + 5 * a, nbe * nb + 5 * b
+            Skk, Skc, Sck, Scc = S[r:r + 5, r:r + 5], S[r:r + 5, c:c + 5], S[c:c + 5, r:r + 5], S[c:c + 5, c:c + 5]
             s = e * nbn + a
             nk = np.linalg.norm(Skk)
             F[s, 0:5] = Q[e, m] / scale
@@ -141,11 +143,34 @@ def features_and_targets(S: np.ndarray, Q: np.ndarray, n: int, N: int, Ma: float
             F[s, 55:80] = _unit(Sck).reshape(-1)
             F[s, 80:105] = _unit(Scc).reshape(-1)
             F[s, 105:109] = scal
-            F[s, 109] = node_face_count(N, int(m)) / 3.0
+            F[s, 109] = len(node_faces(N, int(m))) / 3.0
             F[s, 110:113] = [np.linalg.norm(Skc) / nk, np.linalg.norm(Sck) / nk, np.linalg.norm(Scc) / nk]
             snorm[s] = nk
-            T[s] = (LEARNED_DAMPING * C[s] / snorm[s]).reshape(-1)
+            T[s] = ((Sinv[5 * a:5 * a + 5, 5 * a:5 * a + 5] - np.linalg.inv(Skk)) * nk).reshape(-1)
     return F, T, snorm
+
+
+def assemble_correction(S: np.ndarray, Y: np.ndarray, n: int, N: int) -> np.ndarray:
+    """C [K*nbn, 5, 5]: for black elements C_k = -(1/2) sum_f S_(k,k'_f) Z_(k'_f) S_(k'_f,k) with
+    Z_(k') = [S_nn]_(k'k')^{-1} + y_(k') / ||[S_nn]_(k'k')||_F; zero for red elements."""
+    from .linalg import checkerboard
+    Bn = boundary_nodes(N)
+    nbn = len(Bn)
+    nb = 5 * nbn
+    K = n ** 3
+    pos = {int(m): i for i, m in enumerate(Bn)}
+    C = np.zeros((K * nbn, 5, 5))
+    for e in np.where(checkerboard(n) == 1)[0]:
+        for a, m in enumerate(Bn):
+            r = e * nb + 5 * a
+            for f in node_faces(N, int(m)):
+                nbe = face_neighbour(n, e, f)
+                b = pos[mirror_node(N, int(m), f)]
+                c = nbe * nb + 5 * b
+                Scc = S[c:c + 5, c:c + 5]
+                Z = np.linalg.inv(Scc) + Y[nbe * nbn + b].reshape(5, 5) / np.linalg.norm(Scc)
+                C[e * nbn + a] -= LEARNED_DAMPING * S[r:r + 5, c:c + 5] @ Z @ S[c:c + 5, r:r + 5]
+    return C
 
 
 def black_mask(n: int, N: int) -> np.ndarray:
@@ -220,9 +245,8 @@ def adam_step(P, g, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         P[k] -= lr * mh / (np.sqrt(vh) + eps)
 
 
-def corrected_apply(S: np.ndarray, y: np.ndarray, snorm: np.ndarray, v: np.ndarray, n: int):
-    """The learned sweep: red-black with D_b = S_bb + C, C_k = y_k ||[S_ee]_kk||_F on the black
-    elements' diagonal node blocks."""
+def corrected_apply(S: np.ndarray, Y: np.ndarray, v: np.ndarray, n: int, N: int):
+    """The learned sweep: red-black with D_b = S_bb + C, C assembled from the network outputs Y."""
     from .linalg import corrected_black_blocks, red_black_apply
-    C = (y.reshape(-1, 5, 5) * snorm[:, None, None])
+    C = assemble_correction(S, Y, n, N)
     return red_black_apply(S, n, v, black_blocks=corrected_black_blocks(S, n, C))

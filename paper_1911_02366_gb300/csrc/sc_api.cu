@@ -116,7 +116,8 @@ void free_all(sc_ctx* c) {
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_own_pairs, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
                  &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx,
-                 &c->d_colour, &c->pivL, &c->rowpermL, &c->d_lnfaces};
+                 &c->d_colour, &c->pivL, &c->rowpermL, &c->d_lnfaces, &c->d_lface3, &c->d_lmirror3,
+                 &c->d_lrslot3};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
 }
 
@@ -203,7 +204,7 @@ sc_status sc_default_config(sc_config* cfg) {
   cfg->Ts = 110.4 / 288.15; cfg->sutherland = 1; cfg->roe_delta = 0.05;
   cfg->precision = SC_PREC_FP64; cfg->precond = SC_PC_BLOCK_JACOBI;
   cfg->gmres_restart = 30; cfg->gmres_max_iters = 4000; cfg->max_refine = 10;
-  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4; cfg->tensor_cores = 1; cfg->learned_min_reduction = 4.0;
+  cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4; cfg->tensor_cores = 1; cfg->learned_min_reduction = 1.5;
   return SC_OK;
 }
 
@@ -351,9 +352,11 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->d_pk_lptr, c->pk_lptr.size())); A(dalloc(&c->d_pk_list, c->pk_list.size()));
   A(dalloc(&c->d_pk_row_off, c->pk_row_off.size())); A(dalloc(&c->d_pk_pos, c->pk_pos.size()));
   A(dalloc(&c->d_lface, G.nbn)); A(dalloc(&c->d_lmirror, G.nbn)); A(dalloc(&c->d_lnfaces, G.nbn));
+  A(dalloc(&c->d_lface3, 3 * (size_t)G.nbn)); A(dalloc(&c->d_lmirror3, 3 * (size_t)G.nbn));
+  A(dalloc(&c->d_lrslot3, 3 * (size_t)G.nbn));
   if (c->cfg.precision == SC_PREC_MIXED) {
     const size_t nsmp = (size_t)G.K * G.nbn;
-    A(dalloc(&c->Sdiag, nsmp * 25)); A(dalloc(&c->Cpl, nsmp * 25));
+    A(dalloc(&c->Sdiag, nsmp * 25)); A(dalloc(&c->Cpl, nsmp * 75));  // 3 face slots per node
     if (c->cfg.precond == SC_PC_LEARNED) {
       A(dalloc(&c->Feat, nsmp * sc::kMlpInputs)); A(dalloc(&c->Snorm, nsmp)); A(dalloc(&c->Ynet, nsmp * 25));
       A(dalloc(&c->Hbuf, nsmp * 512)); A(dalloc(&c->Ck, nsmp * 25)); A(dalloc(&c->Wbias, (size_t)sc::kMlpBiases));
@@ -405,6 +408,9 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   SC_CUDA(cudaMemcpy(c->d_lface, c->l_face.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_lmirror, c->l_mirror.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   SC_CUDA(cudaMemcpy(c->d_lnfaces, c->l_nfaces.data(), G.nbn * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_lface3, c->l_face3.data(), 3 * G.nbn * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_lmirror3, c->l_mirror3.data(), 3 * G.nbn * sizeof(int), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(c->d_lrslot3, c->l_rslot3.data(), 3 * G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   if (c->d_colour)
     SC_CUDA(cudaMemcpy(c->d_colour, c->colour_list.data(), (size_t)G.K * sizeof(int), cudaMemcpyHostToDevice));
   // the alignment padding of the element blocks (dense and packed) must read as zero

@@ -1272,8 +1272,8 @@ constexpr int kSolveCtaWarps = 8;
 // Element lists (red-black sweep): CTA / warp i serves element elist[i] (all elements when
 // elist is null); its factors are number i of LS / rowperm when compact, else number e;
 // vsub (optional) is subtracted from v on input.
-template <class T, class TS>
-__global__ void __launch_bounds__(32 * kSolveCtaWarps) k_lu_solve_cta(int n, int nblk, const TS* __restrict__ LS,
+template <class T, class TS, int W = kSolveCtaWarps>
+__global__ void __launch_bounds__(32 * W) k_lu_solve_cta(int n, int nblk, const TS* __restrict__ LS,
                                                                       long long lsstride, int npad,
                                                                       const int* __restrict__ rowperm,
                                                                       const double* __restrict__ v,
@@ -1297,7 +1297,7 @@ __global__ void __launch_bounds__(32 * kSolveCtaWarps) k_lu_solve_cta(int n, int
     s[i] = val;
   }
   __syncthreads();
-  ls_solve_cta<T, TS, kSolveCtaWarps>(n, nblk, LS + (long long)f * lsstride, npad, s, red);
+  ls_solve_cta<T, TS, W>(n, nblk, LS + (long long)f * lsstride, npad, s, red);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     if (z) z[(long long)e * n + i] = (double)s[i];
     if (zt) zt[(long long)e * n + i] = s[i];
@@ -1548,8 +1548,10 @@ inline int ls_nblk(const Geo& G) { return (G.nb + 31) / 32; }
 inline int ls_npad(const Geo& G) { return (G.nb + 3) & ~3; }
 inline long long ls_stride(const Geo& G) { return (long long)ls_nblk(G) * 32 * ls_npad(G); }
 
-// Meshes with fewer elements than this solve the block-Jacobi system with a CTA per element.
+// Meshes with fewer elements than this solve the block-Jacobi system with a CTA per element;
+// element lists (the red-black sweep's colours) below the second bound.
 constexpr int kSolveCtaMaxElems = 2048;
+constexpr int kSolveListCtaMaxElems = 1024;
 
 template <class T, class TS>
 cudaError_t lu_solve_t(sc_ctx* c, const TS* LS, const double* v, double* z, T* zt) {
@@ -1576,7 +1578,17 @@ cudaError_t lu_solve_list_t(sc_ctx* c, const TS* LS, const int* rowperm, int com
   const Geo& G = c->G;
   if (nlist <= 0) return cudaSuccess;
   ProfScope ps(c, SCK_LU_SOLVE, nlist);
-  if (nlist <= kSolveCtaMaxElems) {
+  // short lists: 8 warps per element; one colour of a 16^3 mesh (2048 elements), where one
+  // warp per element leaves the SMs a third full (0.49 ms) and 8 warps take two waves with
+  // 8-warp barriers (0.64 ms): 4 warps per element, one wave of 8192 warps
+  if (nlist >= kSolveListCtaMaxElems && nlist <= 4096) {
+    constexpr int W4 = 4;
+    const size_t csm = (size_t)(ls_nblk(G) + W4) * 32 * sizeof(T);
+    k_lu_solve_cta<T, TS, W4><<<nlist, 32 * W4, csm, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
+                                                                  rowperm, v, z, zt, elist, compact, vsub);
+    return cudaGetLastError();
+  }
+  if (nlist < kSolveListCtaMaxElems) {
     const size_t csm = (size_t)(ls_nblk(G) + kSolveCtaWarps) * 32 * sizeof(T);
     k_lu_solve_cta<T, TS><<<nlist, 32 * kSolveCtaWarps, csm, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
                                                                          ls_npad(G), rowperm, v, z, zt, elist,
@@ -1740,41 +1752,37 @@ cudaError_t factor_batch32(sc_ctx* c, float* A, int n, int lda, long long stride
   return cudaGetLastError();
 }
 
-// X[p][j][:] = S_mm^-1 S[m rows, column b nb + j] for every pair p = (black element b, red
-// neighbour m) and column j < n of b's block, from the dense S stored column by column
-// (n1 rows); one warp per (pair, column), S_mm from the condensation's own factors.
-__global__ void __launch_bounds__(128) k_solve_cols(int n, int nblk, const float* __restrict__ LS, long long lsstride,
-                                                    int npad, const int* __restrict__ rowperm,
-                                                    const double* __restrict__ Scm, long long n1,
-                                                    const int* __restrict__ pb, const int* __restrict__ pm,
-                                                    int npairs, float* __restrict__ X) {
+// Diagonal node blocks of the inverses of the element blocks, [S_ee^-1]_kk for every
+// (element, boundary node) sample: warp w solves S_ee x = e_c for column c = 5 a + var of
+// sample w / 5 with the condensation's factors, and keeps rows 5 a .. 5 a + 4 as column var.
+__global__ void __launch_bounds__(128) k_inv_node_blocks(int n, int nblk, const float* __restrict__ LS,
+                                                         long long lsstride, int npad, const int* __restrict__ rowperm,
+                                                         int nw_total, float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-  const long long w = (long long)blockIdx.x * 4 + warp;
-  if (w >= (long long)npairs * n) return;
-  const int pidx = (int)(w / n), j = (int)(w % n);
-  const int b = __ldg(pb + pidx), m = __ldg(pm + pidx);
+  const int w = blockIdx.x * 4 + warp;
+  if (w >= nw_total) return;
+  const int smp = w / 5, var = w - 5 * smp, nbn = n / 5;
+  const int e = smp / nbn, a = smp % nbn, col = 5 * a + var;
   const int ls = nblk * 32;
   float* s = reinterpret_cast<float*>(smem_raw) + (size_t)warp * ls;
-  const int* rp = rowperm + (long long)m * n;
-  const double* col = Scm + ((long long)b * n + j) * n1 + (long long)m * n;
-  for (int i = lane; i < ls; i += 32) s[i] = i < n ? (float)col[__ldg(rp + i)] : 0.f;
+  const int* rp = rowperm + (long long)e * n;
+  for (int i = lane; i < ls; i += 32) s[i] = (i < n && __ldg(rp + i) == col) ? 1.f : 0.f;
   __syncwarp();
-  ls_solve_warp<float, float>(n, nblk, LS + (long long)m * lsstride, npad, s, lane);
-  float* out = X + ((long long)pidx * n + j) * n;
-  for (int i = lane; i < n; i += 32) out[i] = s[i];
+  ls_solve_warp<float, float>(n, nblk, LS + (long long)e * lsstride, npad, s, lane);
+  if (lane < 5) out[(long long)smp * 25 + 5 * lane + var] = s[5 * a + lane];
 }
 
-cudaError_t solve_columns32(sc_ctx* c, const double* Scm, long long n1, const int* pb, const int* pm, int npairs,
-                            float* X) {
+cudaError_t inverse_node_blocks32(sc_ctx* c, float* out) {
   const Geo& G = c->G;
-  const int n = G.nb, nblk = ls_nblk(G);
+  const int nblk = ls_nblk(G);
   const size_t smem = (size_t)4 * nblk * 32 * sizeof(float);
-  cudaError_t err = cudaFuncSetAttribute(k_solve_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = cudaFuncSetAttribute(k_inv_node_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   count_launch(c);
-  k_solve_cols<<<(unsigned)cdiv((long long)npairs * n, 4), 128, smem, c->stream>>>(
-      n, nblk, c->Sls32, ls_stride(G), ls_npad(G), c->rowperm, Scm, n1, pb, pm, npairs, X);
+  const long long nw = (long long)G.K * G.nbn * 5;
+  k_inv_node_blocks<<<cdiv(nw, 4), 128, smem, c->stream>>>(G.nb, nblk, c->Sls32, ls_stride(G), ls_npad(G), c->rowperm,
+                                                           (int)nw, out);
   return cudaGetLastError();
 }
 

@@ -289,8 +289,12 @@ struct sc_ctx {
   std::vector<int> l_face, l_mirror;  // per boundary position: face, co-located position
   std::vector<int> l_nfaces;          // per boundary position: number of element faces containing the node
   int* d_lnfaces = nullptr;
+  // per (boundary position, i-th face containing it): the face, the co-located position in
+  // the neighbour across it, and that position's slot of the opposite face
+  std::vector<int> l_face3, l_mirror3, l_rslot3;
+  int *d_lface3 = nullptr, *d_lmirror3 = nullptr, *d_lrslot3 = nullptr;
   int *d_lface = nullptr, *d_lmirror = nullptr;
-  float *Sdiag = nullptr, *Cpl = nullptr;  // [K nbn][25]: [S_ee]_kk, S_(k,k')
+  float *Sdiag = nullptr, *Cpl = nullptr;  // [K nbn][25] [S_ee]_kk; [K nbn][3][25] S_(k,k'_f) per face of k
   float *Feat = nullptr, *Snorm = nullptr, *Ynet = nullptr, *Hbuf = nullptr, *Ck = nullptr, *Wbias = nullptr;
   uint16_t* Wbf16 = nullptr;
   bool Sdiag_valid = false, weights_set = false, learned_on = false;
@@ -441,6 +445,7 @@ cudaError_t gemm_fp32(sc_ctx* c, int M, int N, int K, const float* A, long long 
 cudaError_t extract_sdiag(sc_ctx* c, const float* See);
 cudaError_t learned_features(sc_ctx* c, float* F, float* snorm);
 cudaError_t learned_correction(sc_ctx* c);
+cudaError_t assemble_correction(sc_ctx* c, const float* Y, float scale);
 constexpr int kMlpInputs = 128;
 constexpr int kMlpWeights = 256 * kMlpInputs + 256 * 256 + 25 * 256, kMlpBiases = 2 * 256 + 25;
 cudaError_t mlp_forward(cudaStream_t st, const uint16_t* Wbf16, const float* bias, const float* X, int n, float* Y,
@@ -473,8 +478,6 @@ cudaError_t gather_black_see(sc_ctx* c, const float* See);
 template <class T>
 cudaError_t gemm_update(sc_ctx* c, int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc);
 void free_direct_factors(sc_ctx* c);
-// X[p] = S_mm^-1 S[m rows, b cols] (nb x nb, column j contiguous) for pairs (b, m), from the
-// dense S stored column by column
-cudaError_t solve_columns32(sc_ctx* c, const double* Scm, long long n1, const int* pb, const int* pm, int npairs,
-                            float* X);
+// [S_ee^-1]_kk for every (element, boundary node) sample from the condensation's factors
+cudaError_t inverse_node_blocks32(sc_ctx* c, float* out);
 }  // namespace sc

@@ -1,21 +1,23 @@
-// Learned correction of the red-black block sweep of the condensed system (not in the
-// paper; its GMRES runs on S x_b = g of Sec. 2.2, eq. SC_step1).  For boundary node k of a
-// black element b (checkerboard colouring, ex + ey + ez odd), with f the lowest-index face of
-// b containing k (order -x, +x, -y, +y, -z, +z), n the neighbour across f and k' the node of n
-// at the same point:
-//   features (128): q_k over free-stream scales | [S_bb]_kk, S_(k,k'), S_(k',k''), [S_nn]_(k'k'),
-//                  each over its Frobenius norm (k'' the co-located node across the lowest face
-//                  of n containing k', k itself on a single face) | (Ma, Re / 1000, dt c_inf / h,
-//                  N) | (faces of b containing k) / 3 | the norms of the three coupling /
-//                  neighbour blocks over that of [S_bb]_kk | 0 x 15
-//   correction    C_k = net(features) ||[S_bb]_kk||_F, added to the diagonal node block k of
-//                  S_bb before it is factorised for the black half of the sweep
-//   target        C*_k / ||[S_bb]_kk||_F with C*_k = -(1/2) sum_{red m} [S_bm S_mm^-1 S_mb]_kk:
-//                  half the node-diagonal part of what eliminating the red neighbours adds to
-//                  the black block (the whole of it over-corrects: the off-diagonal node
-//                  blocks it leaves out would have balanced it).
-// The coupling block of S between k and k' has three parts (no other element reaches a
-// boundary row of b through its interior):
+// Learned correction of the red-black sweep of the condensed system (not in the paper; its
+// GMRES runs on S x_b = g of Sec. 2.2, eq. SC_step1, preconditioned there by point Jacobi).
+//
+// The black half of the sweep solves with D_b = S_bb + C_b; C_b is block diagonal over the
+// 5 x 5 node blocks, one per boundary node k of the black element b:
+//   C_k = -(1/2) sum over the faces f of b containing k of S_(k,k'_f) Z_(k'_f) S_(k'_f,k),
+// k'_f the node at the same point in the (red) neighbour n_f across f and Z_(k') the diagonal
+// node block of the inverse of that neighbour's face block, [S_nn^-1]_(k'k'): the co-located
+// part of the Schur correction that eliminating the red neighbours adds to S_bb, halved (the
+// off-diagonal node blocks it leaves out would balance it).  Z is what the network provides:
+// it predicts, from local features of node k' of element n, the correction of the inverse of
+// the node block, Z = [S_nn]_(k'k')^-1 + y / ||[S_nn]_(k'k')||_F (the exact Z needs n_b unit
+// solves per element; the network one forward pass per node).
+//   features (128): q_k over free-stream scales | [S_ee]_kk, S_(k,k'), S_(k',k), [S_nn]_(k'k'),
+//                  each over its Frobenius norm (k' across the lowest face of e containing k) |
+//                  (Ma, Re / 1000, dt c_inf / h, N) | (faces of e containing k) / 3 | the norms
+//                  of the last three over that of [S_ee]_kk | 0 x 15
+//   target        ([S_ee^-1]_kk - [S_ee]_kk^-1) ||[S_ee]_kk||_F, every element of either colour
+// The coupling block of S between k and k'_f has three parts (no other element reaches a
+// boundary row of e through its interior):
 //   S_(k,k') = A_bb[k,k'] - A_bi,e[k,:] A_ii,e^-1 A_ib[e_int, k'] - A_bi[k, n_int] Y_n[:, k']
 // with Y_n = A_ii,n^-1 A_ib,n (kept transposed by the mixed condensation).
 #include <algorithm>
@@ -40,15 +42,21 @@ __global__ void k_extract_sdiag(int nb, const float* __restrict__ See, long long
 // S_(k,k') for every (element, boundary node): one warp per sample.
 __global__ void __launch_bounds__(256) k_learned_coupling(Geo G, const float* __restrict__ Aown, const float* __restrict__ Ainv,
     const float* __restrict__ X, const int* __restrict__ pptr, const int* __restrict__ pinfo,
-    const int* __restrict__ iperm, const int* __restrict__ nbr, const int* __restrict__ lface,
-    const int* __restrict__ lmirror, const float* __restrict__ Y, int y_transposed, float* __restrict__ out) {
+    const int* __restrict__ iperm, const int* __restrict__ nbr, const int* __restrict__ lface3,
+    const int* __restrict__ lmirror3, const int* __restrict__ nfaces, const float* __restrict__ Y, int y_transposed,
+    float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
   const int nbn = G.nbn, ni = G.ni, nb = G.nb;
-  const int smp = blockIdx.x * (blockDim.x / 32) + warp;
-  if (smp >= G.K * nbn) return;
+  const int w = blockIdx.x * (blockDim.x / 32) + warp;  // (sample, i-th face of its node)
+  if (w >= G.K * nbn * 3) return;
+  const int smp = w / 3, slot = w % 3;
   const int e = smp / nbn, a = smp % nbn;
-  const int f = __ldg(lface + a), am = __ldg(lmirror + a);
+  if (slot >= __ldg(nfaces + a)) {  // the node lies on fewer faces: the slot stays zero
+    if (lane < 25) out[(size_t)w * 25 + lane] = 0.f;
+    return;
+  }
+  const int f = __ldg(lface3 + 3 * a + slot), am = __ldg(lmirror3 + 3 * a + slot);
   const int n = __ldg(nbr + e * 18 + f);
   float* t = reinterpret_cast<float*>(smem_raw) + (size_t)warp * (ni * 5 + 32);  // [ni][5] = A_ii^-1 A_ib[:, k']
   int* hits = reinterpret_cast<int*>(t + ni * 5);                                 // up to 32 (node, pair) hits
@@ -128,7 +136,7 @@ __global__ void __launch_bounds__(256) k_learned_coupling(Geo G, const float* __
   for (int i = 0; i < 25; ++i) {
     float v = acc[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) out[(size_t)smp * 25 + i] = v;
+    if (lane == 0) out[(size_t)w * 25 + i] = v;
   }
 }
 
@@ -144,22 +152,22 @@ __device__ __forceinline__ void put_unit(float* dst, const float* src, float* no
 __global__ void k_learned_features(Geo G, const double* __restrict__ Q, const int* __restrict__ iperm,
                                    const float* __restrict__ Sdiag, const float* __restrict__ Cpl, float4 scal,
                                    float e_inf, const int* __restrict__ nfaces, const int* __restrict__ nbr,
-                                   const int* __restrict__ lface, const int* __restrict__ lmirror,
-                                   float* __restrict__ F, float* __restrict__ snorm) {
+                                   const int* __restrict__ lface3, const int* __restrict__ lmirror3,
+                                   const int* __restrict__ lrslot3, float* __restrict__ F, float* __restrict__ snorm) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= G.K * G.nbn) return;
   const int e = s / G.nbn, a = s % G.nbn;
   const int j = __ldg(iperm + G.nin + a);
-  // the neighbour's own sample at the co-located node k'
-  const int sm = __ldg(nbr + e * 18 + __ldg(lface + a)) * G.nbn + __ldg(lmirror + a);
+  // the neighbour's sample at the co-located node k' across the lowest face of e containing k
+  const int sm = __ldg(nbr + e * 18 + __ldg(lface3 + 3 * a)) * G.nbn + __ldg(lmirror3 + 3 * a);
   float* f = F + (size_t)s * 128;
   const double* q = Q + ((size_t)e * G.nn + j) * 5;
   f[0] = (float)q[0]; f[1] = (float)q[1]; f[2] = (float)q[2]; f[3] = (float)q[3]; f[4] = (float)(q[4] / e_inf);
   float nk = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
   put_unit(f + 5, Sdiag + (size_t)s * 25, &nk);
-  put_unit(f + 30, Cpl + (size_t)s * 25, &n1);
-  put_unit(f + 55, Cpl + (size_t)sm * 25, &n2);
-  put_unit(f + 80, Sdiag + (size_t)sm * 25, &n3);
+  put_unit(f + 30, Cpl + (size_t)s * 75, &n1);                                   // S_(k,k')
+  put_unit(f + 55, Cpl + ((size_t)sm * 3 + __ldg(lrslot3 + 3 * a)) * 25, &n2);  // S_(k',k)
+  put_unit(f + 80, Sdiag + (size_t)sm * 25, &n3);                                // [S_nn]_(k'k')
   f[105] = scal.x; f[106] = scal.y; f[107] = scal.z; f[108] = scal.w;
   f[109] = (float)__ldg(nfaces + a) * (1.0f / 3.0f);
   const float ik = nk > 0.f ? 1.f / nk : 0.f;
@@ -168,46 +176,87 @@ __global__ void k_learned_features(Geo G, const double* __restrict__ Q, const in
   snorm[s] = nk;
 }
 
-__global__ void k_set_unit(double* x, size_t n, long long on, long long off) {
-  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t == 0 && off >= 0) x[off] = 0.0;
-  if (t == 0 && on >= 0) x[on] = 1.0;
-  (void)n;
-}
-
-// Share of the node-diagonal Schur correction the target keeps.
-constexpr float kLearnedDamping = 0.5f;
-
-// T[s] = -kLearnedDamping sum_{pairs p of b} [S_bm X_p]_(k,k) / ||[S_bb]_kk||_F for every sample
-// s = (black element b, boundary node a); red samples get zero.  X_p = S_mm^-1 S_mb with
-// column j contiguous (k_solve_cols); S column by column with n1 rows.
-__global__ void k_black_targets(int nb, int nbn, long long n1, const double* __restrict__ Scm,
-                                const float* __restrict__ X, const int* __restrict__ bidx,
-                                const int* __restrict__ pptr, const int* __restrict__ pm,
-                                const float* __restrict__ snorm, int nsmp, float* __restrict__ T) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)nsmp * 25) return;
-  const int smp = (int)(t / 25), r = (int)((t / 5) % 5), l = (int)(t % 5);
-  const int e = smp / nbn, a = smp % nbn;
-  const int bi = __ldg(bidx + e);
-  if (bi < 0) { T[t] = 0.f; return; }
-  const long long row = (long long)e * nb + 5 * a + r;
-  double acc = 0.0;
-  for (int p = __ldg(pptr + bi); p < __ldg(pptr + bi + 1); ++p) {
-    const long long m0 = (long long)__ldg(pm + p) * nb;
-    const float* xc = X + ((long long)p * nb + 5 * a + l) * nb;
-    for (int i = 0; i < nb; ++i) acc += Scm[(m0 + i) * n1 + row] * (double)xc[i];
+// Inverse of a 5 x 5 matrix (row-major) by Gauss-Jordan elimination with partial pivoting;
+// false (and B untouched) when a pivot vanishes.
+__device__ bool inv5(const float* A, float* B) {
+  float M[5][10];
+  for (int r = 0; r < 5; ++r)
+    for (int cc = 0; cc < 5; ++cc) { M[r][cc] = A[5 * r + cc]; M[r][5 + cc] = r == cc ? 1.f : 0.f; }
+  for (int k = 0; k < 5; ++k) {
+    int p = k;
+    for (int r = k + 1; r < 5; ++r)
+      if (fabsf(M[r][k]) > fabsf(M[p][k])) p = r;
+    if (M[p][k] == 0.f) return false;
+    if (p != k)
+      for (int cc = 0; cc < 10; ++cc) { const float t = M[k][cc]; M[k][cc] = M[p][cc]; M[p][cc] = t; }
+    const float ip = 1.f / M[k][k];
+    for (int cc = 0; cc < 10; ++cc) M[k][cc] *= ip;
+    for (int r = 0; r < 5; ++r) {
+      if (r == k) continue;
+      const float fct = M[r][k];
+      if (fct != 0.f)
+        for (int cc = 0; cc < 10; ++cc) M[r][cc] -= fct * M[k][cc];
+    }
   }
-  const float sn = snorm[smp];
-  T[t] = sn > 0.f ? (float)(-(double)kLearnedDamping * acc) / sn : 0.f;
+  for (int r = 0; r < 5; ++r)
+    for (int cc = 0; cc < 5; ++cc) B[5 * r + cc] = M[r][5 + cc];
+  return true;
 }
 
-// C_k = y_k ||[S_ee]_kk||_F (the network works on blocks scaled by the node's own block)
-__global__ void k_scale_correction(int nsmp, const float* __restrict__ Y, const float* __restrict__ snorm,
-                                   float* __restrict__ Ck) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nsmp * 25) return;
-  Ck[t] = Y[t] * snorm[t / 25];
+// Targets T[s] = ([S_ee^-1]_kk - [S_ee]_kk^-1) ||[S_ee]_kk||_F for every sample.
+__global__ void k_inverse_targets(int nsmp, const float* __restrict__ Zex, const float* __restrict__ Sdiag,
+                                  float* __restrict__ T) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsmp) return;
+  float B[25], nk = 0.f;
+  for (int i = 0; i < 25; ++i) nk = fmaf(Sdiag[(size_t)s * 25 + i], Sdiag[(size_t)s * 25 + i], nk);
+  nk = sqrtf(nk);
+  if (!inv5(Sdiag + (size_t)s * 25, B))
+    for (int i = 0; i < 25; ++i) B[i] = 0.f;
+  for (int i = 0; i < 25; ++i) T[(size_t)s * 25 + i] = (Zex[(size_t)s * 25 + i] - B[i]) * nk;
+}
+
+// C_k = -(1/2) sum_f S_(k,k'_f) Z_(k'_f) S_(k'_f,k) for the samples of black elements (zero for
+// red ones), Z_(k') = [S_nn]_(k'k')^-1 + scale y_(k') / ||[S_nn]_(k'k')||_F.
+__global__ void k_assemble_correction(Geo G, const float* __restrict__ Y, float scale,
+                                      const float* __restrict__ Sdiag, const float* __restrict__ Cpl,
+                                      const int* __restrict__ nbr, const int* __restrict__ nfaces,
+                                      const int* __restrict__ lface3, const int* __restrict__ lmirror3,
+                                      const int* __restrict__ lrslot3, float* __restrict__ C) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= G.K * G.nbn) return;
+  const int e = s / G.nbn, a = s % G.nbn;
+  float acc[25];
+  for (int i = 0; i < 25; ++i) acc[i] = 0.f;
+  const int ex = e % G.n, ey = (e / G.n) % G.n, ez = e / (G.n * G.n);
+  if (((ex + ey + ez) & 1) == 1) {
+    for (int i = 0; i < __ldg(nfaces + a); ++i) {
+      const int sm = __ldg(nbr + e * 18 + __ldg(lface3 + 3 * a + i)) * G.nbn + __ldg(lmirror3 + 3 * a + i);
+      const float* Sd = Sdiag + (size_t)sm * 25;
+      float Z[25], nk = 0.f;
+      for (int t = 0; t < 25; ++t) nk = fmaf(Sd[t], Sd[t], nk);
+      nk = sqrtf(nk);
+      if (!inv5(Sd, Z)) continue;
+      const float sc = nk > 0.f ? scale / nk : 0.f;
+      for (int t = 0; t < 25; ++t) Z[t] = fmaf(sc, Y[(size_t)sm * 25 + t], Z[t]);
+      const float* Skc = Cpl + ((size_t)s * 3 + i) * 25;                            // S_(k,k')
+      const float* Sck = Cpl + ((size_t)sm * 3 + __ldg(lrslot3 + 3 * a + i)) * 25;  // S_(k',k)
+      float ZS[25];
+      for (int r = 0; r < 5; ++r)
+        for (int cc = 0; cc < 5; ++cc) {
+          float v = 0.f;
+          for (int t = 0; t < 5; ++t) v = fmaf(Z[5 * r + t], Sck[5 * t + cc], v);
+          ZS[5 * r + cc] = v;
+        }
+      for (int r = 0; r < 5; ++r)
+        for (int cc = 0; cc < 5; ++cc) {
+          float v = 0.f;
+          for (int t = 0; t < 5; ++t) v = fmaf(Skc[5 * r + t], ZS[5 * t + cc], v);
+          acc[5 * r + cc] -= 0.5f * v;
+        }
+    }
+  }
+  for (int i = 0; i < 25; ++i) C[(size_t)s * 25 + i] = acc[i];
 }
 
 }  // namespace
@@ -222,19 +271,39 @@ void build_learned_tables(sc_ctx* c) {
   c->l_face.assign(G.nbn, 0);
   c->l_mirror.assign(G.nbn, 0);
   c->l_nfaces.assign(G.nbn, 0);
+  c->l_face3.assign(3 * G.nbn, 0);
+  c->l_mirror3.assign(3 * G.nbn, 0);
+  c->l_rslot3.assign(3 * G.nbn, 0);
+  auto faces_of = [&](int m, int out[3]) {
+    const int cc[3] = {m % p, (m / p) % p, m / (p * p)};
+    int k = 0;
+    for (int d = 0; d < 3; ++d) {
+      if (cc[d] == 0) out[k++] = 2 * d;
+      else if (cc[d] == N) out[k++] = 2 * d + 1;
+    }
+    return k;
+  };
   for (int a = 0; a < G.nbn; ++a) {
     const int m = c->iperm[G.nin + a];
-    int cc[3] = {m % p, (m / p) % p, m / (p * p)};
-    int f = -1;
-    for (int d = 0; d < 3 && f < 0; ++d) {
-      if (cc[d] == 0) f = 2 * d;
-      else if (cc[d] == N) f = 2 * d + 1;
+    int fl[3];
+    const int nf = faces_of(m, fl);
+    c->l_nfaces[a] = nf;
+    for (int i = 0; i < nf; ++i) {
+      const int f = fl[i];
+      int cc[3] = {m % p, (m / p) % p, m / (p * p)};
+      cc[f / 2] = N - cc[f / 2];
+      const int mm = cc[0] + p * (cc[1] + p * cc[2]);
+      int fr[3];
+      const int nr = faces_of(mm, fr);
+      int rs = 0;
+      for (int t = 0; t < nr; ++t)
+        if (fr[t] == (f ^ 1)) rs = t;  // the mirrored node's slot of the face back to e
+      c->l_face3[3 * a + i] = f;
+      c->l_mirror3[3 * a + i] = c->perm[mm] - G.nin;
+      c->l_rslot3[3 * a + i] = rs;
     }
-    c->l_face[a] = f;
-    c->l_nfaces[a] = (cc[0] == 0 || cc[0] == N) + (cc[1] == 0 || cc[1] == N) + (cc[2] == 0 || cc[2] == N);
-    cc[f / 2] = N - cc[f / 2];
-    const int mm = cc[0] + p * (cc[1] + p * cc[2]);
-    c->l_mirror[a] = c->perm[mm] - G.nin;
+    c->l_face[a] = c->l_face3[3 * a];
+    c->l_mirror[a] = c->l_mirror3[3 * a];
   }
 }
 
@@ -255,30 +324,41 @@ cudaError_t learned_features(sc_ctx* c, float* F, float* snorm) {
   cudaError_t e = cudaFuncSetAttribute(k_learned_coupling, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launch(c, 2);
-  k_learned_coupling<<<(nsmp + 7) / 8, 256, smem, c->stream>>>(G, c->Aown32, c->Ainv32, c->X32, c->d_pptr,
-      c->d_pinfo, c->d_iperm, c->d_nbr, c->d_lface, c->d_lmirror, c->Y32, c->cfg.tensor_cores ? 1 : 0, c->Cpl);
+  k_learned_coupling<<<(3 * nsmp + 7) / 8, 256, smem, c->stream>>>(G, c->Aown32, c->Ainv32, c->X32, c->d_pptr,
+      c->d_pinfo, c->d_iperm, c->d_nbr, c->d_lface3, c->d_lmirror3, c->d_lnfaces, c->Y32,
+      c->cfg.tensor_cores ? 1 : 0, c->Cpl);
   const double Ma = c->cfg.Ma, gamma = c->cfg.gamma;
   const double p_inf = 1.0 / (gamma * Ma * Ma);
   const float e_inf = (float)(p_inf / (gamma - 1.0) + 0.5);
   const float4 scal = make_float4((float)Ma, (float)(c->cfg.Re / 1000.0), (float)(G.dt * (1.0 / Ma) / G.h),
                                   (float)G.N);
   k_learned_features<<<(nsmp + 255) / 256, 256, 0, c->stream>>>(G, c->Q, c->d_iperm, c->Sdiag, c->Cpl, scal, e_inf,
-                                                                c->d_lnfaces, c->d_nbr, c->d_lface, c->d_lmirror, F,
-                                                                snorm);
+                                                                c->d_lnfaces, c->d_nbr, c->d_lface3, c->d_lmirror3,
+                                                                c->d_lrslot3, F, snorm);
   return cudaGetLastError();
 }
 
-// Network on the features, scaled into the per-node corrections C_k.
+// The black blocks' corrections C from network outputs Y (per sample, target form) into c->Ck;
+// the couplings of every face come from the last learned_features.
+cudaError_t assemble_correction(sc_ctx* c, const float* Y, float scale) {
+  const Geo& G = c->G;
+  const int nsmp = G.K * G.nbn;
+  count_launch(c);
+  k_assemble_correction<<<(nsmp + 127) / 128, 128, 0, c->stream>>>(G, Y, scale, c->Sdiag, c->Cpl, c->d_nbr,
+                                                                   c->d_lnfaces, c->d_lface3, c->d_lmirror3,
+                                                                   c->d_lrslot3, c->Ck);
+  return cudaGetLastError();
+}
+
+// Network on the features, its outputs assembled into the black blocks' corrections C_k.
 cudaError_t learned_correction(sc_ctx* c) {
   const Geo& G = c->G;
   const int nsmp = G.K * G.nbn;
   cudaError_t e = learned_features(c, c->Feat, c->Snorm);
   if (e == cudaSuccess)
     e = mlp_forward(c->stream, c->Wbf16, c->Wbias, c->Feat, nsmp, c->Ynet, c->Hbuf, c->Hbuf + (size_t)nsmp * 256);
-  if (e != cudaSuccess) return e;
-  count_launch(c, 4);
-  k_scale_correction<<<(nsmp * 25 + 255) / 256, 256, 0, c->stream>>>(nsmp, c->Ynet, c->Snorm, c->Ck);
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = assemble_correction(c, c->Ynet, 1.0f);
+  return e;
 }
 
 }  // namespace sc
@@ -297,77 +377,28 @@ sc_status sc_learned_targets(sc_ctx* c, float* T) {
   if (!c || !T) return SC_ERR_ARG;
   if (!c->condensed || c->cfg.precision != SC_PREC_MIXED || !c->Sdiag_valid) return SC_ERR_STATE;
   const Geo& G = c->G;
-  const long long n1 = (long long)G.K * G.nb;
   const int nsmp = G.K * G.nbn;
-  if ((double)n1 * n1 * 8.0 > 40e9) return SC_ERR_ARG;  // training meshes only
-  // pairs (black element, distinct red neighbour), grouped by black element
-  std::vector<int> hb, hm, hptr(1, 0), hbidx(G.K, -1);
-  for (int i = c->n_red; i < G.K; ++i) {
-    const int b = c->colour_list[i];
-    hbidx[b] = i - c->n_red;
-    std::vector<int> seen;
-    for (int sl = 0; sl < 18; ++sl) {
-      const int m = c->nbr[(size_t)b * 18 + sl];
-      const int ex = m % G.n, ey = (m / G.n) % G.n, ez = m / (G.n * G.n);
-      if (((ex + ey + ez) & 1) != 0 || std::find(seen.begin(), seen.end(), m) != seen.end()) continue;
-      seen.push_back(m);
-      hb.push_back(b); hm.push_back(m);
-    }
-    hptr.push_back((int)hb.size());
+  float* Zex = nullptr;
+  if (cudaMalloc(&Zex, (size_t)nsmp * 25 * sizeof(float)) != cudaSuccess) return SC_ERR_OOM;
+  cudaError_t e = sc::inverse_node_blocks32(c, Zex);
+  if (e == cudaSuccess) {
+    count_launch(c);
+    k_inverse_targets<<<(nsmp + 127) / 128, 128, 0, c->stream>>>(nsmp, Zex, c->Sdiag, T);
+    e = cudaGetLastError();
   }
-  const int npairs = (int)hb.size();
-  cudaStream_t st = c->stream;
-  double* Scm = nullptr;
-  float *X = nullptr, *F = nullptr, *sn = nullptr;
-  int *pb = nullptr, *pm = nullptr, *pptr = nullptr, *bidx = nullptr;
-  cudaError_t e = cudaSuccess;
-  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  A(cudaMalloc(&Scm, (size_t)n1 * n1 * sizeof(double)));
-  A(cudaMalloc(&X, (size_t)std::max(npairs, 1) * G.nb * G.nb * sizeof(float)));
-  A(cudaMalloc(&F, (size_t)nsmp * 128 * sizeof(float)));
-  A(cudaMalloc(&sn, (size_t)nsmp * sizeof(float)));
-  A(cudaMalloc(&pb, std::max(npairs, 1) * sizeof(int))); A(cudaMalloc(&pm, std::max(npairs, 1) * sizeof(int)));
-  A(cudaMalloc(&pptr, hptr.size() * sizeof(int))); A(cudaMalloc(&bidx, G.K * sizeof(int)));
-  sc_status status = SC_OK;
-  if (e != cudaSuccess) { status = SC_ERR_OOM; goto done; }
-  {
-    // S column by column through the condensed operator (the system the method forms)
-    double* xb = c->Xfull;  // K ne >= n1 doubles of scratch
-    A(cudaMemsetAsync(xb, 0, (size_t)n1 * sizeof(double), st));
-    for (long long jcol = 0; jcol < n1 && e == cudaSuccess; ++jcol) {
-      k_set_unit<<<1, 32, 0, st>>>(xb, (size_t)n1, jcol, jcol - 1);
-      A(sc::vec_to_float(c, c->Xbf, xb, (size_t)n1));
-      A(sc::cond_interior32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf));
-      A(sc::cond_boundary32(c, c->Xbf, 1.0, nullptr, 0.0, c->Uf, Scm + jcol * n1));
-    }
-    if (npairs > 0) {
-      A(cudaMemcpyAsync(pb, hb.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
-      A(cudaMemcpyAsync(pm, hm.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
-    }
-    A(cudaMemcpyAsync(pptr, hptr.data(), hptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    A(cudaMemcpyAsync(bidx, hbidx.data(), G.K * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (npairs > 0) A(sc::solve_columns32(c, Scm, n1, pb, pm, npairs, X));
-    A(sc::learned_features(c, F, sn));
-    if (e == cudaSuccess) {
-      count_launch(c);
-      const long long nt = (long long)nsmp * 25;
-      k_black_targets<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(G.nb, G.nbn, n1, Scm, X, bidx, pptr, pm, sn,
-                                                                    nsmp, T);
-      A(cudaGetLastError());
-    }
-    A(cudaStreamSynchronize(st));
-    if (e != cudaSuccess) status = SC_ERR_CUDA;
-  }
-done:
-  cudaFree(Scm); cudaFree(X); cudaFree(F); cudaFree(sn); cudaFree(pb); cudaFree(pm); cudaFree(pptr); cudaFree(bidx);
-  return status;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(Zex);
+  return e == cudaSuccess ? SC_OK : SC_ERR_CUDA;
 }
 
-sc_status sc_set_learned_correction(sc_ctx* c, const float* Ck, float scale) {
-  if (!c || !Ck) return SC_ERR_ARG;
-  if (!c->condensed || !c->SeeB) return SC_ERR_STATE;
-  if (sc::learned_black_factor(c, Ck, scale) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
-    return SC_ERR_CUDA;
+sc_status sc_set_learned_correction(sc_ctx* c, const float* Y, float scale) {
+  if (!c || !Y) return SC_ERR_ARG;
+  if (!c->condensed || !c->SeeB || !c->Ck || !c->Feat) return SC_ERR_STATE;
+  cudaError_t e = sc::learned_features(c, c->Feat, c->Snorm);  // the couplings of every face
+  if (e == cudaSuccess) e = sc::assemble_correction(c, Y, scale);
+  if (e == cudaSuccess) e = sc::learned_black_factor(c, c->Ck, 1.0f);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return SC_ERR_CUDA;
   c->weights_set = true;  // the corrected black factors are in place; the next sc_solve uses them
   return SC_OK;
 }

@@ -50,9 +50,7 @@ def test_features_and_targets_match_oracle(n, N):
     assert np.max(np.abs(Fg[:, 105:] - Fo[:, 105:])) < 1e-4 * np.max(np.abs(Fo[:, 105:]))
     assert np.max(np.abs(sn.cpu().numpy() - sno) / sno) < 1e-4  # S_ee formed in FP32
     Tg = T.cpu().numpy()
-    black = LN.black_mask(n, N)
-    assert np.max(np.abs(Tg[~black])) == 0.0
-    assert np.max(np.abs(Tg - To)) < 2e-3 * np.max(np.abs(To))
+    assert np.max(np.abs(Tg - To)) < 2e-3 * np.max(np.abs(To))  # FP32 factors
 
 
 def _net(seed, zero_out=False):
@@ -71,18 +69,21 @@ def _solve(ctx, Q):
     return dQ, st
 
 
-def test_zero_correction_reproduces_the_red_black_sweep():
+def test_zero_correction_weights_give_the_closed_form_correction():
+    """A network whose output is zero sets Z to the inverses of the neighbours' node blocks:
+    the closed-form co-located correction, applied (iterations differ from the plain sweep)
+    and converged."""
     from paper_1911_02366_gb300 import sc
     n, N = 4, 2
     Q, dt, p, crb = _mixed(n, N, precond=sc.SC_PC_RED_BLACK)
     crb.sc_condense()
     _, st_rb = _solve(crb, Q)
-    Q, dt, p, cl = _mixed(n, N, precond=sc.SC_PC_LEARNED, learned_min_reduction=1.0)
+    Q, dt, p, cl = _mixed(n, N, precond=sc.SC_PC_LEARNED)
     cl.sc_set_learned_weights(_net(1, zero_out=True))
     cl.sc_condense()
     _, st = _solve(cl, Q)
-    assert st["rel_residual"] < 1e-8
-    assert st["gmres_iters"] == st_rb["gmres_iters"] and st["learned_fallbacks"] == 0
+    assert st["rel_residual"] < 1e-8 and st["learned_fallbacks"] == 0
+    assert st["gmres_iters"] != st_rb["gmres_iters"]
 
 
 def test_learned_solve_matches_oracle_global_solve():
@@ -101,7 +102,6 @@ def test_learned_solve_matches_oracle_global_solve():
 def _train_set(n, N, seeds, cfl):
     from paper_1911_02366_gb300 import sc
     Fs, Ts = [], []
-    black = torch.tensor(LN.black_mask(n, N), device="cuda")
     for i, seed in enumerate(seeds):
         Ma = [0.05, 0.1, 0.15, 0.2, 0.25, 0.3][i % 6]
         Q, dt = I.tgv_state(n, N, Ma=Ma, cfl=cfl, seed=seed)
@@ -112,8 +112,8 @@ def _train_set(n, N, seeds, cfl):
         ctx.sc_assemble()
         ctx.sc_condense()
         F, T, _ = _ft(ctx, n, N)
-        Fs.append(F[black])
-        Ts.append(T[black])
+        Fs.append(F)
+        Ts.append(T)
     return torch.cat(Fs).contiguous(), torch.cat(Ts).contiguous()
 
 
@@ -144,7 +144,7 @@ def test_trained_correction_beats_the_sweep_without_it_and_block_jacobi_on_held_
         row["network"] = (st_l["gmres_iters"], st_l["ms_gmres"])
         # what a perfect network would give: the exact targets
         F, T, sn = _ft(cl, n, N)
-        cl.sc_set_learned_correction((T * sn[:, None]).contiguous(), 1.0)
+        cl.sc_set_learned_correction(T, 1.0)
         _, st_x = _solve(cl, Q)
         row["exact_targets"] = (st_x["gmres_iters"], st_x["ms_gmres"])
         out[seed] = row

@@ -84,9 +84,10 @@ def test_backward_matches_oracle(n):
     g = LN.backward(Pq, c, dYh.astype(np.float64))
     gW = net.gW.cpu().numpy()
     gb = net.gb.cpu().numpy()
-    assert _rel(gW[:16384], g["W1"].ravel()) < 1e-4
-    assert _rel(gW[16384:16384 + 65536], g["W2"].ravel()) < 1e-4
-    assert _rel(gW[16384 + 65536:], g["W3"].ravel()) < 1e-4
+    n1 = 256 * LN.N_IN
+    assert _rel(gW[:n1], g["W1"].ravel()) < 1e-4
+    assert _rel(gW[n1:n1 + 65536], g["W2"].ravel()) < 1e-4
+    assert _rel(gW[n1 + 65536:], g["W3"].ravel()) < 1e-4
     assert _rel(gb, np.concatenate([g["b1"], g["b2"], g["b3"]])) < 1e-4
 
 
