@@ -1578,16 +1578,9 @@ cudaError_t lu_solve_list_t(sc_ctx* c, const TS* LS, const int* rowperm, int com
   const Geo& G = c->G;
   if (nlist <= 0) return cudaSuccess;
   ProfScope ps(c, SCK_LU_SOLVE, nlist);
-  // short lists: 8 warps per element; one colour of a 16^3 mesh (2048 elements), where one
-  // warp per element leaves the SMs a third full (0.49 ms) and 8 warps take two waves with
-  // 8-warp barriers (0.64 ms): 4 warps per element, one wave of 8192 warps
-  if (nlist >= kSolveListCtaMaxElems && nlist <= 4096) {
-    constexpr int W4 = 4;
-    const size_t csm = (size_t)(ls_nblk(G) + W4) * 32 * sizeof(T);
-    k_lu_solve_cta<T, TS, W4><<<nlist, 32 * W4, csm, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
-                                                                  rowperm, v, z, zt, elist, compact, vsub);
-    return cudaGetLastError();
-  }
+  // lists of 1024 elements or more keep one warp per element: at 2048 elements (one colour of
+  // 16^3) it takes 0.49 ms per launch against 0.57 ms with 4 and 0.64 ms with 8 warps per
+  // element (CTA kernel)
   if (nlist < kSolveListCtaMaxElems) {
     const size_t csm = (size_t)(ls_nblk(G) + kSolveCtaWarps) * 32 * sizeof(T);
     k_lu_solve_cta<T, TS><<<nlist, 32 * kSolveCtaWarps, csm, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
