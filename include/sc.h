@@ -59,8 +59,20 @@ enum { SC_PREC_FP64 = 0, SC_PREC_MIXED = 1 };
      in block Jacobi.
    SC_PC_LEARNED (mixed arm): the red-black sweep with the black blocks corrected by a
      network, z_b = (S_bb + C_b)^-1 (...), C_b the per-node 5 x 5 corrections of the network
-     (see the learned correction below); block Jacobi is its fallback. */
-enum { SC_PC_BLOCK_JACOBI = 0, SC_PC_NONE = 1, SC_PC_LEARNED = 2, SC_PC_RED_BLACK = 3 };
+     (see the learned correction below); block Jacobi is its fallback.
+   SC_PC_RB_SCHUR (mixed arm): the red-black sweep with each black block replaced by its
+     block of the black Schur complement, D_b = S_bb + C_b,
+       C_b[k,l] = -sum over the faces f of b containing k and l of
+                  S_(k,k'_f) [S_mm^-1]_(k'_f,l'_f) S_(l'_f,l),
+     m the red neighbour across f and k'_f the node of m at the same point as k: the
+     eliminated red neighbour's whole face block of its inverse, through the co-located
+     couplings.  The forward sweep's preconditioned operator has the spectrum of D^-1 times
+     the black Schur complement, so this D takes the red couplings out of the black blocks
+     (on the Taylor-Green systems about 0.7 times the sweep's iterations).  sc_condense forms
+     the red blocks' inverses (n_b solves per red element with their factors; n_red n_b^2
+     floats of device memory) and factorises the corrected black blocks; if that
+     factorisation meets a singular block the plain sweep runs. */
+enum { SC_PC_BLOCK_JACOBI = 0, SC_PC_NONE = 1, SC_PC_LEARNED = 2, SC_PC_RED_BLACK = 3, SC_PC_RB_SCHUR = 4 };
 
 /* Physics and solver settings (App. B parameters; solver choices of this library). */
 typedef struct {
@@ -72,7 +84,8 @@ typedef struct {
   int sutherland;        /* 1: Sutherland viscosity law, 0: mu = 1 */
   double roe_delta;      /* Harten entropy-fix width as a fraction of the Roe sound speed (0.05) */
   int precision;         /* SC_PREC_FP64 or SC_PREC_MIXED */
-  int precond;           /* SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED or SC_PC_RED_BLACK */
+  int precond;           /* SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED, SC_PC_RED_BLACK or
+                            SC_PC_RB_SCHUR */
   int gmres_restart;     /* Krylov dimension per cycle (e.g. 30) */
   int gmres_max_iters;   /* total iteration cap */
   int max_refine;        /* mixed arm: cap on FP64 refinement sweeps */

@@ -52,12 +52,15 @@ def face_schur_correction(S: np.ndarray, n: int, N: int) -> dict:
     nb = S.shape[0] // K
     blk = lambda e: slice(e * nb, (e + 1) * nb)
     nodes, mirror = face_node_lists(N)
+    col = checkerboard(n)
     inv = {}
     out = {}
-    for b in np.where(checkerboard(n) == 1)[0]:
+    for b in np.where(col == 1)[0]:
         C = np.zeros((nb, nb))
         for f in range(6):
             m = LN.face_neighbour(n, int(b), f)
+            if col[m] == 1:  # odd n: the periodic wrap joins two black elements; no red to eliminate
+                continue
             if m not in inv:
                 inv[m] = np.linalg.inv(S[blk(m), blk(m)])
             Sbm, Smb = S[blk(b), blk(m)], S[blk(m), blk(b)]

@@ -97,7 +97,8 @@ void free_all(sc_ctx* c) {
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
                    &c->Apk32, &c->Sls32, &c->Sdiag, &c->Cpl, &c->Feat, &c->Snorm, &c->Ynet, &c->Hbuf,
-                   &c->Ck, &c->Wbias, &c->ExIb, &c->ExBi, &c->ExY, &c->ExW, &c->Zrb, &c->SeeB, &c->SeeL, &c->SlsL};
+                   &c->Ck, &c->Wbias, &c->ExIb, &c->ExBi, &c->ExY, &c->ExW, &c->Zrb, &c->SeeB, &c->SeeL, &c->SlsL,
+                   &c->Zinv};
   for (auto p : fps) { if (*p) cudaFree(*p); *p = nullptr; }
   if (c->Dfull) cudaFree(c->Dfull);
   c->Dfull = nullptr;
@@ -117,7 +118,7 @@ void free_all(sc_ctx* c) {
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
                  &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx,
                  &c->d_colour, &c->pivL, &c->rowpermL, &c->d_lnfaces, &c->d_lface3, &c->d_lmirror3,
-                 &c->d_lrslot3};
+                 &c->d_lrslot3, &c->d_redidx, &c->d_face_tab};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
 }
 
@@ -214,6 +215,7 @@ sc_status sc_create(const sc_config* cfg, void* cuda_stream, sc_ctx** out) {
       !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->gamma > 1) || !(cfg->Pr > 0))
     return SC_ERR_ARG;
   if (cfg->precision != SC_PREC_FP64 && cfg->precision != SC_PREC_MIXED) return SC_ERR_ARG;
+  if (cfg->precond < SC_PC_BLOCK_JACOBI || cfg->precond > SC_PC_RB_SCHUR) return SC_ERR_ARG;
   if (cfg->outer_krylov < 0 || cfg->outer_krylov > cfg->gmres_restart || cfg->inner_iters < 0) return SC_ERR_ARG;
   sc_ctx* c = new sc_ctx();
   c->cfg = *cfg;
@@ -245,6 +247,8 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
     return fail(c, SC_ERR_ARG, "explicit Schur blocks: N <= 4 (W_e holds (n_b + 30 (N+1)^2)^2 values per element)");
   if (c->cfg.precond == SC_PC_LEARNED && c->cfg.precision != SC_PREC_MIXED)
     return fail(c, SC_ERR_ARG, "the learned correction runs on the mixed arm's FP32 blocks");
+  if (c->cfg.precond == SC_PC_RB_SCHUR && c->cfg.precision != SC_PREC_MIXED)
+    return fail(c, SC_ERR_ARG, "the Schur-corrected sweep runs on the mixed arm's FP32 blocks");
   if (c->cfg.explicit_schur && (c->cfg.precision != SC_PREC_MIXED || n < 3))
     return fail(c, SC_ERR_ARG, "explicit Schur blocks: mixed arm on meshes with n >= 3 (distinct neighbours)");
   cudaStreamSynchronize(c->stream);
@@ -311,6 +315,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   sc::build_packed_pattern(c);
   sc::build_learned_tables(c);
   sc::build_colours(c);
+  sc::build_face_tables(c);
   if (c->cfg.explicit_schur) sc::build_explicit_tables(c);
   const size_t nodes = (size_t)G.K * G.nn, dofs = nodes * 5;
   const size_t n1 = (size_t)G.K * G.nb;
@@ -342,7 +347,8 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->Gb, n1)); A(dalloc(&c->Rb, n1)); A(dalloc(&c->Tb, n1));
   A(dalloc(&c->Ui, (size_t)G.K * G.ni)); A(dalloc(&c->Hd, 3 * (size_t)(m + 2) + 16));
   A(dalloc(&c->partial, 152 * (size_t)(m + 2)));
-  A(dalloc(&c->d_status, 2));  // [0] first bad element / error code, [1] FP16 range overflow
+  A(dalloc(&c->d_status, 3));  // [0] first bad element / error code, [1] FP16 range overflow,
+                                // [2] first singular corrected black block
   A(dalloc(&c->d_nbr, c->nbr.size())); A(dalloc(&c->d_perm, G.nn)); A(dalloc(&c->d_iperm, G.nn));
   A(dalloc(&c->d_own_pairs, c->own_pairs.size()));
   A(dalloc(&c->gj_scale, (size_t)G.K * G.ni));
@@ -372,12 +378,17 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   } else {
     A(dalloc(&c->Apk, (size_t)G.K * c->pk_stride)); A(dalloc(&c->Sls, sc::solve_layout_elems(G)));
   }
-  const bool sweep = c->cfg.precond == SC_PC_RED_BLACK || c->cfg.precond == SC_PC_LEARNED;
+  const bool sweep = c->cfg.precond == SC_PC_RED_BLACK || c->cfg.precond == SC_PC_LEARNED ||
+                     c->cfg.precond == SC_PC_RB_SCHUR;
   if (sweep) {
     A(dalloc(&c->d_colour, (size_t)G.K)); A(dalloc(&c->Trb, n1));
     if (c->cfg.precision == SC_PREC_MIXED) A(dalloc(&c->Zrb, n1));
   }
-  if (c->cfg.precond == SC_PC_LEARNED) {
+  if (c->cfg.precond == SC_PC_RB_SCHUR) {
+    A(dalloc(&c->Zinv, (size_t)c->n_red * G.nb * G.nb));
+    A(dalloc(&c->d_redidx, (size_t)G.K)); A(dalloc(&c->d_face_tab, c->face_tab.size()));
+  }
+  if (c->cfg.precond == SC_PC_LEARNED || c->cfg.precond == SC_PC_RB_SCHUR) {
     const size_t nbk = (size_t)c->n_black;
     A(dalloc(&c->SeeB, nbk * G.nb * G.lds)); A(dalloc(&c->SeeL, nbk * G.nb * G.lds));
     A(dalloc(&c->SlsL, nbk * (size_t)sc::solve_layout_stride(G)));
@@ -413,6 +424,10 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   SC_CUDA(cudaMemcpy(c->d_lrslot3, c->l_rslot3.data(), 3 * G.nbn * sizeof(int), cudaMemcpyHostToDevice));
   if (c->d_colour)
     SC_CUDA(cudaMemcpy(c->d_colour, c->colour_list.data(), (size_t)G.K * sizeof(int), cudaMemcpyHostToDevice));
+  if (c->d_redidx) {
+    SC_CUDA(cudaMemcpy(c->d_redidx, c->red_index.data(), (size_t)G.K * sizeof(int), cudaMemcpyHostToDevice));
+    SC_CUDA(cudaMemcpy(c->d_face_tab, c->face_tab.data(), c->face_tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   // the alignment padding of the element blocks (dense and packed) must read as zero
   if (c->Apk) SC_CUDA(cudaMemset(c->Apk, 0, (size_t)G.K * c->pk_stride * sizeof(double)));
   if (c->Apk32) SC_CUDA(cudaMemset(c->Apk32, 0, (size_t)G.K * c->pk_stride * sizeof(float)));
@@ -494,16 +509,20 @@ sc_status sc_condense(sc_ctx* c) {
   const int zero = 0;
   SC_CUDA(cudaMemcpyAsync(c->d_status + 1, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   SC_CUDA(sc::launch_condense(c));
+  SC_CUDA(cudaMemsetAsync(c->d_status + 2, 0xff, sizeof(int), c->stream));  // -1: no singular black block
   if (c->cfg.precond == SC_PC_LEARNED) {  // network -> C_k -> factors of the corrected black blocks
     SC_CUDA(sc::learned_correction(c));
     SC_CUDA(sc::learned_black_factor(c, c->Ck, 1.0f));
   }
+  if (c->cfg.precond == SC_PC_RB_SCHUR) SC_CUDA(sc::schur_black_factor(c));
   if (c->cfg.explicit_schur) SC_CUDA(sc::explicit_build(c));
-  int bad = -1, ovf = 0;
+  int bad = -1, ovf = 0, bad_black = -1;
   SC_CUDA(cudaMemcpyAsync(&bad, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   SC_CUDA(cudaMemcpyAsync(&ovf, c->d_status + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SC_CUDA(cudaMemcpyAsync(&bad_black, c->d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
   if (s != SC_OK) return s;
+  if (bad_black >= 0) c->blackL_valid = false;  // a corrected black block is singular: plain sweep
   if (bad == SC_TC_TIMEOUT) return fail(c, SC_ERR_CUDA, "tensor-core wait timed out in the condensation");
   if (bad == SC_EXPLICIT_PATTERN)
     return fail(c, SC_ERR_STATE, "an interior row couples outside the extended boundary set");

@@ -1779,4 +1779,148 @@ cudaError_t inverse_node_blocks32(sc_ctx* c, float* out) {
   return cudaGetLastError();
 }
 
+
+// ls_solve_warp for R right-hand sides at once (s: R vectors of nblk * 32 entries, stride
+// ls, zero beyond n): every factor entry the warp loads serves all R columns.
+template <int R>
+__device__ __forceinline__ void ls_solve_warp_multi(int n, int nblk, const float* __restrict__ Le, int npad,
+                                                    float* s, int ls, int lane) {
+  const int nq = npad / 4;
+  for (int b = 0; b < nblk; ++b) {  // forward: x_b = L_bb^-1 v_b - M_b x_{<b}
+    const int i0 = 32 * b, Rw = i0 + lane;
+    const bool live = Rw < n;
+    const float* row = Le + (long long)b * 32 * npad + 4 * lane;
+    float a[R], d[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = 0.f;
+    if (live) {
+#pragma unroll 2
+      for (int q = 0; q < i0 / 4; ++q) {
+        Quad<float, float> m;
+        m.load(row + (long long)q * 128);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float4 x = *reinterpret_cast<const float4*>(s + r * ls + 4 * q);
+          a[r] = fmaf(m.v[0], x.x, a[r]);
+          a[r] = fmaf(m.v[1], x.y, a[r]);
+          a[r] = fmaf(m.v[2], x.z, a[r]);
+          a[r] = fmaf(m.v[3], x.w, a[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[r] = s[r * ls + Rw];
+    const int qd = min(i0 / 4 + 8, nq);
+    for (int q = i0 / 4; q < qd; ++q) {
+      if (live && 4 * q < Rw) {  // strictly lower part: columns < Rw
+        Quad<float, float> m;
+        m.load(row + (long long)q * 128);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j < Rw) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) d[r] = fmaf(m.v[j], s[r * ls + 4 * q + j], d[r]);
+          }
+      }
+    }
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[r * ls + Rw] = d[r] - a[r];
+    }
+    __syncwarp();
+  }
+  for (int b = nblk - 1; b >= 0; --b) {  // backward: z_b = U_bb^-1 x_b - N_b z_{>b}
+    const int i0 = 32 * b, Rw = i0 + lane;
+    const bool live = Rw < n;
+    const float* row = Le + (long long)b * 32 * npad + 4 * lane;
+    float a[R], d[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = d[r] = 0.f;
+    const int qd = min(i0 / 4 + 8, nq);
+    for (int q = i0 / 4; q < qd; ++q) {
+      if (live && 4 * q + 3 >= Rw) {  // upper part: columns >= Rw
+        Quad<float, float> m;
+        m.load(row + (long long)q * 128);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j >= Rw) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) d[r] = fmaf(m.v[j], s[r * ls + 4 * q + j], d[r]);
+          }
+      }
+    }
+    if (live) {
+#pragma unroll 2
+      for (int q = i0 / 4 + 8; q < nq; ++q) {
+        Quad<float, float> m;
+        m.load(row + (long long)q * 128);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float4 x = *reinterpret_cast<const float4*>(s + r * ls + 4 * q);
+          a[r] = fmaf(m.v[0], x.x, a[r]);
+          a[r] = fmaf(m.v[1], x.y, a[r]);
+          a[r] = fmaf(m.v[2], x.z, a[r]);
+          a[r] = fmaf(m.v[3], x.w, a[r]);
+        }
+      }
+    }
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[r * ls + Rw] = d[r] - a[r];
+    }
+    __syncwarp();
+  }
+}
+
+namespace {
+
+constexpr int kInvCols = 8;  // right-hand sides per warp in k_inv_columns
+
+// Explicit inverses of the element blocks listed: warp w solves S_ee X = I[:, c0 .. c0 + 7]
+// for element list[w / ngrp], c0 = 8 (w % ngrp), with the condensation's factors, and writes
+// the columns contiguously: out[(i n + c) n + r] = (S_ee^-1)[r][c], i the list index.
+__global__ void __launch_bounds__(128) k_inv_columns(int n, int nblk, const float* __restrict__ LS, long long lsstride,
+                                                     int npad, const int* __restrict__ rowperm,
+                                                     const int* __restrict__ list, int nlist, float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int ngrp = (n + kInvCols - 1) / kInvCols;
+  const long long w = (long long)blockIdx.x * 4 + warp;
+  if (w >= (long long)nlist * ngrp) return;
+  const int li = (int)(w / ngrp), c0 = (int)(w % ngrp) * kInvCols;
+  const int e = __ldg(list + li);
+  const int ls = nblk * 32;
+  float* s = reinterpret_cast<float*>(smem_raw) + (size_t)warp * kInvCols * ls;
+  const int* rp = rowperm + (long long)e * n;
+  for (int i = lane; i < ls; i += 32) {
+    const int pi = i < n ? __ldg(rp + i) : -1;
+#pragma unroll
+    for (int r = 0; r < kInvCols; ++r) s[r * ls + i] = pi == c0 + r ? 1.f : 0.f;
+  }
+  __syncwarp();
+  ls_solve_warp_multi<kInvCols>(n, nblk, LS + (long long)e * lsstride, npad, s, ls, lane);
+  for (int r = 0; r < kInvCols && c0 + r < n; ++r) {
+    float* o = out + ((long long)li * n + c0 + r) * n;
+    for (int i = lane; i < n; i += 32) o[i] = s[r * ls + i];
+  }
+}
+
+}  // namespace
+
+cudaError_t inverse_columns32(sc_ctx* c, const int* list, int nlist, float* out) {
+  const Geo& G = c->G;
+  if (nlist == 0) return cudaSuccess;
+  const int nblk = ls_nblk(G);
+  const size_t smem = (size_t)4 * kInvCols * nblk * 32 * sizeof(float);
+  cudaError_t err = cudaFuncSetAttribute(k_inv_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  count_launch(c);
+  const long long nw = (long long)nlist * cdiv(G.nb, kInvCols);
+  k_inv_columns<<<(unsigned)cdiv(nw, 4), 128, smem, c->stream>>>(G.nb, nblk, c->Sls32, ls_stride(G), ls_npad(G),
+                                                                 c->rowperm, list, nlist, out);
+  return cudaGetLastError();
+}
+
 }  // namespace sc

@@ -315,6 +315,13 @@ struct sc_ctx {
   float *SeeB = nullptr, *SeeL = nullptr, *SlsL = nullptr;
   int *pivL = nullptr, *rowpermL = nullptr;
   bool blackL_valid = false;  // SlsL holds the factors of the corrected black blocks
+  // Schur-corrected sweep (SC_PC_RB_SCHUR): the red blocks' inverses, column-major per red
+  // element (Zinv[r][j][i] = (S_rr^-1)[i][j], r the red list index), red index of every
+  // element (-1 for black), and per face f the (N+1)^2 boundary nodes on f with the slot of f
+  // in each node's face list: face_tab[(2 f) P2 + t] = node, face_tab[(2 f + 1) P2 + t] = slot
+  float* Zinv = nullptr;
+  std::vector<int> red_index, face_tab;
+  int *d_redidx = nullptr, *d_face_tab = nullptr;
   // dense direct solve (sc_direct_factor): n x n factors (row-major, ld = ldd), pivots
   void* Dlu = nullptr;       // double (FP64 arm) or float (mixed arm)
   int* d_dpiv = nullptr;
@@ -474,6 +481,10 @@ bool rb_active(const sc_ctx* c);
 cudaError_t precond_rb(sc_ctx* c, const double* v, double* z);
 cudaError_t precond_rb32(sc_ctx* c, const double* v, double* z, float* zf);
 cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale);
+cudaError_t learned_couplings(sc_ctx* c);
+void build_face_tables(sc_ctx* c);
+cudaError_t schur_black_factor(sc_ctx* c);
+cudaError_t inverse_columns32(sc_ctx* c, const int* list, int nlist, float* out);
 cudaError_t gather_black_see(sc_ctx* c, const float* See);
 template <class T>
 cudaError_t gemm_update(sc_ctx* c, int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc);

@@ -316,17 +316,27 @@ cudaError_t extract_sdiag(sc_ctx* c, const float* See) {
   return cudaGetLastError();
 }
 
-// Features of every (element, boundary node) of the current condensed system.
-cudaError_t learned_features(sc_ctx* c, float* F, float* snorm) {
+// Couplings S_(k,k'_f) of every (element, boundary node, face of the node) into Cpl.
+cudaError_t learned_couplings(sc_ctx* c) {
   const Geo& G = c->G;
   const int nsmp = G.K * G.nbn;
   const size_t smem = (size_t)8 * (G.ni * 5 + 32) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_learned_coupling, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  count_launch(c, 2);
+  count_launch(c);
   k_learned_coupling<<<(3 * nsmp + 7) / 8, 256, smem, c->stream>>>(G, c->Aown32, c->Ainv32, c->X32, c->d_pptr,
       c->d_pinfo, c->d_iperm, c->d_nbr, c->d_lface3, c->d_lmirror3, c->d_lnfaces, c->Y32,
       c->cfg.tensor_cores ? 1 : 0, c->Cpl);
+  return cudaGetLastError();
+}
+
+// Features of every (element, boundary node) of the current condensed system.
+cudaError_t learned_features(sc_ctx* c, float* F, float* snorm) {
+  const Geo& G = c->G;
+  const int nsmp = G.K * G.nbn;
+  cudaError_t e = learned_couplings(c);
+  if (e != cudaSuccess) return e;
+  count_launch(c);
   const double Ma = c->cfg.Ma, gamma = c->cfg.gamma;
   const double p_inf = 1.0 / (gamma * Ma * Ma);
   const float e_inf = (float)(p_inf / (gamma - 1.0) + 0.5);

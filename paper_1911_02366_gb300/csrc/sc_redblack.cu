@@ -8,15 +8,18 @@
 // colour).  One application z = P v of the preconditioner is one forward block sweep:
 //   z_r = S_rr^-1 v_r                          for every red element r,
 //   z_b = D_b^-1 (v_b - sum_{red n} S_bn z_n)  for every black element b,
-// with D_b = S_bb (SC_PC_RED_BLACK) or S_bb + C_b (SC_PC_LEARNED).  The couplings
+// with D_b = S_bb (SC_PC_RED_BLACK) or S_bb + C_b (SC_PC_LEARNED, SC_PC_RB_SCHUR).  The couplings
 // sum S_bn z_n are the black rows of S z for z zero on the black elements, which the
 // implicit operator passes give: the interior pass over every element, then the boundary
 // pass over the black elements only.
 //
-// C_b approximates the node-diagonal 5 x 5 blocks of the Schur correction that eliminating
-// the red face neighbours would add to the black block, -sum_n [S_bn S_nn^-1 S_nb]_kk: a
-// network predicts it from local features (the block-ILU view of the sweep: with this
-// correction the black blocks carry what the red elements do to them).
+// Eliminating the red unknowns leaves the black Schur complement
+// Sigma = S_bb - S_br S_rr^-1 S_rb, and the sweep's preconditioned operator has the spectrum
+// of D^-1 Sigma (plus ones): the best block-diagonal D is the block diagonal of Sigma.
+// SC_PC_RB_SCHUR forms it through the co-located couplings of each shared face,
+//   C_b[k,l] = -sum_f S_(k,k'_f) [S_mm^-1]_(k'_f,l'_f) S_(l'_f,l)      (k, l on face f of b),
+// from the red neighbour's explicit inverse; SC_PC_LEARNED keeps the node-diagonal blocks
+// of a correction assembled from the network's inverse node blocks.
 #include "sc_internal.cuh"
 
 namespace {
@@ -46,6 +49,70 @@ __global__ void k_add_node_blocks(int nbn, int lds, int nlist, const int* __rest
       scale * Ck[((long long)e * nbn + a) * 25 + 5 * r + l];
 }
 
+// D_i -= sum over the faces f of black element b = list[i], over the node pairs (k, l) on f:
+// S_(k,k') [S_mm^-1]_(k',l') S_(l',l), m the neighbour across f (skipped when it is black, on
+// meshes with an odd n), k', l' the nodes of m at the points of k, l.  Cpl holds S_(k,k'_f) per
+// (sample, face slot); Zinv the red inverses column-major.  One CTA per black element, faces
+// in turn (the pairs of one face write distinct entries; an edge node's pairs meet again on
+// its other faces).
+__global__ void __launch_bounds__(256) k_face_schur(Geo G, const int* __restrict__ list, const int* __restrict__ redidx,
+                                                    const float* __restrict__ Zinv, const float* __restrict__ Cpl,
+                                                    const int* __restrict__ nbr, const int* __restrict__ ftab,
+                                                    const int* __restrict__ lmirror3, const int* __restrict__ lrslot3,
+                                                    float* __restrict__ SeeL) {
+  const int i = blockIdx.x, b = __ldg(list + i);
+  const int P2 = (G.N + 1) * (G.N + 1), nb = G.nb, nbn = G.nbn;
+  float* D = SeeL + (long long)i * nb * G.lds;
+  for (int f = 0; f < 6; ++f) {
+    const int m = __ldg(nbr + (long long)b * 18 + f);
+    const int ri = __ldg(redidx + m);
+    if (ri >= 0) {
+      const float* Z = Zinv + (long long)ri * nb * nb;
+      const int* fa = ftab + 2 * f * P2;
+      const int* fs = fa + P2;
+      for (int p = threadIdx.x; p < P2 * P2; p += blockDim.x) {
+        const int ia = p % P2, ib = p / P2;
+        const int a = __ldg(fa + ia), sa = __ldg(fs + ia), bb = __ldg(fa + ib), sb = __ldg(fs + ib);
+        const int am = __ldg(lmirror3 + 3 * a + sa), bm = __ldg(lmirror3 + 3 * bb + sb);
+        const float* Skc = Cpl + ((long long)(b * nbn + a) * 3 + sa) * 25;                           // S_(k,k')
+        const float* Sck = Cpl + ((long long)(m * nbn + bm) * 3 + __ldg(lrslot3 + 3 * bb + sb)) * 25;  // S_(l',l)
+        float T[25];  // [S_mm^-1]_(k',l') S_(l',l)
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int cc = 0; cc < 5; ++cc) T[5 * r + cc] = 0.f;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+          const float* zc = Z + (long long)(5 * bm + t) * nb + 5 * am;  // column 5 l' + t, rows of k'
+          float zr[5], sr[5];
+#pragma unroll
+          for (int r = 0; r < 5; ++r) zr[r] = __ldg(zc + r);
+#pragma unroll
+          for (int cc = 0; cc < 5; ++cc) sr[cc] = __ldg(Sck + 5 * t + cc);
+#pragma unroll
+          for (int r = 0; r < 5; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 5; ++cc) T[5 * r + cc] = fmaf(zr[r], sr[cc], T[5 * r + cc]);
+        }
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+          float u[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int t = 0; t < 5; ++t) {
+            const float k = __ldg(Skc + 5 * r + t);
+#pragma unroll
+            for (int cc = 0; cc < 5; ++cc) u[cc] = fmaf(k, T[5 * t + cc], u[cc]);
+          }
+          float* drow = D + (long long)(5 * a + r) * G.lds + 5 * bb;
+#pragma unroll
+          for (int cc = 0; cc < 5; ++cc) drow[cc] -= u[cc];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 namespace sc {
@@ -62,11 +129,31 @@ void build_colours(sc_ctx* c) {
   c->n_red = 0;
   for (int e = 0; e < G.K; ++e) c->n_red += ((e % n + (e / n) % n + e / (n * n)) & 1) == 0;
   c->n_black = G.K - c->n_red;
+  c->red_index.assign(G.K, -1);
+  for (int i = 0; i < c->n_red; ++i) c->red_index[c->colour_list[i]] = i;
+}
+
+// face_tab: per face f the boundary nodes on f (condensed order) and the slot of f in each
+// node's face list (the learned tables l_face3 hold the faces of every boundary node).
+void build_face_tables(sc_ctx* c) {
+  const Geo& G = c->G;
+  const int P2 = (G.N + 1) * (G.N + 1);
+  c->face_tab.assign(12 * (size_t)P2, 0);
+  for (int f = 0; f < 6; ++f) {
+    int t = 0;
+    for (int a = 0; a < G.nbn; ++a)
+      for (int i = 0; i < c->l_nfaces[a]; ++i)
+        if (c->l_face3[3 * a + i] == f && t < P2) {  // (N+1)^2 boundary nodes on every face
+          c->face_tab[2 * f * P2 + t] = a;
+          c->face_tab[(2 * f + 1) * P2 + t] = i;
+          ++t;
+        }
+  }
 }
 
 bool rb_active(const sc_ctx* c) {
   if (!c->d_colour) return false;
-  if (c->cfg.precond == SC_PC_RED_BLACK) return true;
+  if (c->cfg.precond == SC_PC_RED_BLACK || c->cfg.precond == SC_PC_RB_SCHUR) return true;
   return c->cfg.precond == SC_PC_LEARNED && c->learned_on && c->blackL_valid;
 }
 
@@ -89,14 +176,15 @@ cudaError_t precond_rb32(sc_ctx* c, const double* v, double* z, float* zf) {
   const Geo& G = c->G;
   const size_t n1 = (size_t)G.K * G.nb;
   float* zt = zf ? zf : c->Zrb;
-  const bool learned = c->cfg.precond == SC_PC_LEARNED && c->learned_on && c->blackL_valid;
+  const bool corrected = c->blackL_valid && ((c->cfg.precond == SC_PC_LEARNED && c->learned_on) ||
+                                             c->cfg.precond == SC_PC_RB_SCHUR);
   const int* black = c->d_colour + c->n_red;
   cudaError_t e = cudaMemsetAsync(zt, 0, n1 * sizeof(float), c->stream);
   if (e == cudaSuccess) e = lu_solve_list32(c, c->Sls32, c->rowperm, 0, c->d_colour, c->n_red, v, nullptr, z, zt);
   if (e == cudaSuccess) e = cond_interior32(c, zt, 1.0, nullptr, 0.0, c->Uf);
   if (e == cudaSuccess) e = cond_boundary_pk_list<float>(c, c->Apk32, c->X32, zt, c->Uf, c->Trb, black, c->n_black);
   if (e == cudaSuccess) {
-    if (learned)
+    if (corrected)
       e = lu_solve_list32(c, c->SlsL, c->rowpermL, 1, black, c->n_black, v, c->Trb, z, zt);
     else
       e = lu_solve_list32(c, c->Sls32, c->rowperm, 0, black, c->n_black, v, c->Trb, z, zt);
@@ -113,9 +201,10 @@ cudaError_t gather_black_see(sc_ctx* c, const float* See) {
   return cudaGetLastError();
 }
 
-// Corrected black blocks S_bb + scale C (C per sample, K nbn x 25; null: no correction),
-// factorised into the compact black solve layout.
-cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale) {
+// Corrected black blocks S_bb + scale C (C per sample, K nbn x 25; null: no correction), plus
+// the face-block Schur correction when face_schur is set (couplings in Cpl and the red
+// inverses in Zinv already formed), factorised into the compact black solve layout.
+static cudaError_t black_factor(sc_ctx* c, const float* Ck, float scale, bool face_schur) {
   const Geo& G = c->G;
   c->blackL_valid = false;
   if (!c->SeeB || c->n_black == 0) return cudaSuccess;
@@ -123,6 +212,13 @@ cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale) {
   cudaError_t e = cudaMemcpyAsync(c->SeeL, c->SeeB, (size_t)c->n_black * per * sizeof(float),
                                   cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return e;
+  if (face_schur) {
+    count_launch(c);
+    k_face_schur<<<c->n_black, 256, 0, c->stream>>>(G, c->d_colour + c->n_red, c->d_redidx, c->Zinv, c->Cpl, c->d_nbr,
+                                                    c->d_face_tab, c->d_lmirror3, c->d_lrslot3, c->SeeL);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (Ck) {
     const long long nt = (long long)c->n_black * G.nbn * 25;
     count_launch(c);
@@ -132,8 +228,22 @@ cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale) {
     if (e != cudaSuccess) return e;
   }
   e = factor_batch32(c, c->SeeL, G.nb, G.lds, (long long)per, c->n_black, c->pivL, c->rowpermL, c->SlsL,
-                     c->d_status);
+                     c->d_status + 2);
   if (e == cudaSuccess) c->blackL_valid = true;
+  return e;
+}
+
+cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale) { return black_factor(c, Ck, scale, false); }
+
+// SC_PC_RB_SCHUR after the condensation: couplings, red inverses, corrected black factors.
+cudaError_t schur_black_factor(sc_ctx* c) {
+  if (!c->Zinv || !c->SeeB || c->n_black == 0) {
+    c->blackL_valid = false;
+    return cudaSuccess;
+  }
+  cudaError_t e = learned_couplings(c);
+  if (e == cudaSuccess) e = inverse_columns32(c, c->d_colour, c->n_red, c->Zinv);
+  if (e == cudaSuccess) e = black_factor(c, nullptr, 0.f, true);
   return e;
 }
 

@@ -16,7 +16,7 @@ from . import build as _build
 SC_OK, SC_ERR_ARG, SC_ERR_CUDA, SC_ERR_OOM, SC_ERR_STATE = 0, 1, 2, 3, 4
 SC_ERR_SINGULAR_BLOCK, SC_ERR_NONFINITE, SC_ERR_NOT_CONVERGED = 5, 6, 7
 SC_PREC_FP64, SC_PREC_MIXED = 0, 1
-SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED, SC_PC_RED_BLACK = 0, 1, 2, 3
+SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED, SC_PC_RED_BLACK, SC_PC_RB_SCHUR = 0, 1, 2, 3, 4
 SC_DIRECT_GLOBAL, SC_DIRECT_CONDENSED = 0, 1
 
 _lib = None

@@ -54,7 +54,7 @@ def test_create_rejects_invalid_configs_before_any_cuda_call():
     from paper_1911_02366_gb300 import sc
     bad = [dict(gmres_restart=0), dict(gmres_restart=401), dict(gmres_max_iters=0), dict(rel_tol=0.0),
            dict(Re=0.0), dict(Ma=-1.0), dict(gamma=1.0), dict(Pr=0.0), dict(precision=7),
-           dict(outer_krylov=31), dict(outer_krylov=-1), dict(inner_iters=-1)]
+           dict(outer_krylov=31), dict(outer_krylov=-1), dict(inner_iters=-1), dict(precond=-1), dict(precond=5)]
     L = sc.lib()
     for kw in bad:
         cfg = sc.default_config(**kw)
