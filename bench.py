@@ -349,7 +349,6 @@ def fp64_reference_arm(args, W, Q, dt, stream, dQ_mixed):
 # captures summarised in profiles/, taken on the 8^3-element case and scaled x8 to the
 # 16^3 mesh (traffic grows with the element count); None once a kernel has changed.
 TRAFFIC = {
-    ("mixed", 2): 8 * (509.318144e6 + 3.564288e6),  # k_lu_solve<float>, profiles/mixed_iteration_kernels_tgv_8x8x8_N4.md
     ("fp64", 2): 8 * (1.002096e9 + 3.80032e6),  # k_lu_solve<double>, profiles/fp64_iteration_kernels_tgv_8x8x8_N4.md
 }
 
@@ -762,7 +761,7 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=8, help="learned arm: training epochs (untimed)")
     ap.add_argument("--operator", choices=["implicit", "explicit"], default="implicit",
                     help="mixed arm: condensed operator applied implicitly or from explicit W_e blocks")
-    ap.add_argument("--precond", choices=["bj", "rb", "rbs"], default="bj",
+    ap.add_argument("--precond", choices=["bj", "rb", "rbs"], default="rbs",
                     help="condensed preconditioner: block Jacobi, the red-black block Gauss-Seidel sweep, or the "
                          "sweep with Schur-corrected black blocks (mixed arm; the FP64 arm takes the plain sweep)")
     ap.add_argument("--restart", type=int, default=30)

@@ -1354,24 +1354,26 @@ namespace sc {
 
 // Blocked LU of the S_ee blocks with the trailing updates A22 -= L21 U12 as batched TF32
 // tensor-core GEMMs (mixed arm): per panel one k_lu_panel launch and one GEMM.
-cudaError_t lu_blocked_tf32(sc_ctx* c, float* See) {
+// Blocked LU with partial pivoting of `batch` n_b x n_b blocks (row stride lds, block stride
+// n_b lds): panels of PW columns, TF32 tensor-core trailing updates; pivots in piv, the first
+// singular block's index in *status.
+static cudaError_t lu_blocked_tf32_batch(sc_ctx* c, float* See, int K, int* piv, int* status) {
   const Geo& G = c->G;
-  const int nb = G.nb, K = G.K, lds = G.lds;
+  const int nb = G.nb, lds = G.lds;
   const long long sS = (long long)nb * lds;
   const size_t smem = (size_t)nb * (PW + 1) * sizeof(float);
   const bool reg = nb <= LPR_ROWS, reg2 = !reg && nb <= LPR2_ROWS;
   cudaError_t err = cudaFuncSetAttribute(k_lu_panel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  ProfScope ps(c, SCK_LU);  // one measured span over all panels
   for (int k0 = 0; k0 < nb; k0 += PW) {
     const int bw = min(PW, nb - k0), rest = nb - k0 - bw;
     if (k0 > 0) count_launch(c);
     if (reg)
-      k_lu_panel_reg<<<K, 256, 0, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
+      k_lu_panel_reg<<<K, 256, 0, c->stream>>>(nb, k0, See, sS, lds, piv, status);
     else if (reg2)
-      k_lu_panel_reg2<<<K, 32 * LPR2_W, 0, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
+      k_lu_panel_reg2<<<K, 32 * LPR2_W, 0, c->stream>>>(nb, k0, See, sS, lds, piv, status);
     else
-      k_lu_panel<float><<<K, 256, smem, c->stream>>>(nb, k0, See, sS, lds, c->piv, c->d_status);
+      k_lu_panel<float><<<K, 256, smem, c->stream>>>(nb, k0, See, sS, lds, piv, status);
     if (rest > 0) {
       count_launch(c);
       err = gemm_tf32(c->stream, rest, rest, bw, -1.0f, See + (size_t)(k0 + bw) * lds + k0, sS, lds, false,
@@ -1381,6 +1383,11 @@ cudaError_t lu_blocked_tf32(sc_ctx* c, float* See) {
     }
   }
   return cudaGetLastError();
+}
+
+cudaError_t lu_blocked_tf32(sc_ctx* c, float* See) {
+  ProfScope ps(c, SCK_LU);  // one measured span over all panels
+  return lu_blocked_tf32_batch(c, See, c->G.K, c->piv, c->d_status);
 }
 
 // A_ii^-1 of blocks with n_i > 136 (FP32) or too large for a shared-memory copy (FP64):
@@ -1729,11 +1736,18 @@ long long solve_layout_stride(const Geo& G) { return ls_stride(G); }
 // then the gather permutation and the partitioned-inverse solve layout LS.
 cudaError_t factor_batch32(sc_ctx* c, float* A, int n, int lda, long long stride, int batch, int* piv, int* rowperm,
                            float* LS, int* status) {
-  const size_t smem = (size_t)n * (PW + 1) * sizeof(float);
-  cudaError_t err = cudaFuncSetAttribute(k_lu<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  count_launch(c, 4);
-  k_lu<float><<<batch, 256, smem, c->stream>>>(n, A, stride, lda, piv, status);
+  cudaError_t err;
+  if (c->cfg.tensor_cores && n == c->G.nb && lda == c->G.lds && stride == (long long)n * lda) {
+    err = lu_blocked_tf32_batch(c, A, batch, piv, status);  // element-block sized: TF32 trailing updates
+    if (err != cudaSuccess) return err;
+    count_launch(c, 3);
+  } else {
+    const size_t smem = (size_t)n * (PW + 1) * sizeof(float);
+    err = cudaFuncSetAttribute(k_lu<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    count_launch(c, 4);
+    k_lu<float><<<batch, 256, smem, c->stream>>>(n, A, stride, lda, piv, status);
+  }
   k_piv_to_perm<<<cdiv(batch, 128), 128, 0, c->stream>>>(n, piv, rowperm, batch);
   const size_t dsm = (size_t)8 * 2 * 32 * 33 * sizeof(float);
   err = cudaFuncSetAttribute(k_diag_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
@@ -1782,11 +1796,12 @@ cudaError_t inverse_node_blocks32(sc_ctx* c, float* out) {
 
 // ls_solve_warp for R right-hand sides at once (s: R vectors of nblk * 32 entries, stride
 // ls, zero beyond n): every factor entry the warp loads serves all R columns.
+// The forward pass starts at block row b0: the right-hand sides are zero above row 32 b0.
 template <int R>
 __device__ __forceinline__ void ls_solve_warp_multi(int n, int nblk, const float* __restrict__ Le, int npad,
-                                                    float* s, int ls, int lane) {
+                                                    float* s, int ls, int lane, int b0) {
   const int nq = npad / 4;
-  for (int b = 0; b < nblk; ++b) {  // forward: x_b = L_bb^-1 v_b - M_b x_{<b}
+  for (int b = b0; b < nblk; ++b) {  // forward: x_b = L_bb^-1 v_b - M_b x_{<b}
     const int i0 = 32 * b, Rw = i0 + lane;
     const bool live = Rw < n;
     const float* row = Le + (long long)b * 32 * npad + 4 * lane;
@@ -1795,7 +1810,7 @@ __device__ __forceinline__ void ls_solve_warp_multi(int n, int nblk, const float
     for (int r = 0; r < R; ++r) a[r] = 0.f;
     if (live) {
 #pragma unroll 2
-      for (int q = 0; q < i0 / 4; ++q) {
+      for (int q = 8 * b0; q < i0 / 4; ++q) {
         Quad<float, float> m;
         m.load(row + (long long)q * 128);
 #pragma unroll
@@ -1894,13 +1909,16 @@ __global__ void __launch_bounds__(128) k_inv_columns(int n, int nblk, const floa
   const int ls = nblk * 32;
   float* s = reinterpret_cast<float*>(smem_raw) + (size_t)warp * kInvCols * ls;
   const int* rp = rowperm + (long long)e * n;
+  int first = n;  // the lowest row holding a one: the forward pass starts at its block
   for (int i = lane; i < ls; i += 32) {
     const int pi = i < n ? __ldg(rp + i) : -1;
+    if (pi >= c0 && pi < c0 + kInvCols) first = min(first, i);
 #pragma unroll
     for (int r = 0; r < kInvCols; ++r) s[r * ls + i] = pi == c0 + r ? 1.f : 0.f;
   }
+  first = __reduce_min_sync(0xffffffffu, first);
   __syncwarp();
-  ls_solve_warp_multi<kInvCols>(n, nblk, LS + (long long)e * lsstride, npad, s, ls, lane);
+  ls_solve_warp_multi<kInvCols>(n, nblk, LS + (long long)e * lsstride, npad, s, ls, lane, min(first, n - 1) / 32);
   for (int r = 0; r < kInvCols && c0 + r < n; ++r) {
     float* o = out + ((long long)li * n + c0 + r) * n;
     for (int i = lane; i < n; i += 32) o[i] = s[r * ls + i];
