@@ -177,6 +177,8 @@ def run_ours(args, world, rank, local):
     if args.arm == "learned":
         net, train_info = train_correction(args, stream)
         extra = dict(precond=sc.SC_PC_LEARNED)
+        if args.learned_min_reduction is not None:
+            extra["learned_min_reduction"] = args.learned_min_reduction
     elif args.precond == "rb":
         extra = dict(precond=sc.SC_PC_RED_BLACK)
     elif args.precond == "rbs":
@@ -348,9 +350,7 @@ def fp64_reference_arm(args, W, Q, dt, stream, dQ_mixed):
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
 # captures summarised in profiles/, taken on the 8^3-element case and scaled x8 to the
 # 16^3 mesh (traffic grows with the element count); None once a kernel has changed.
-TRAFFIC = {
-    ("fp64", 2): 8 * (1.002096e9 + 3.80032e6),  # k_lu_solve<double>, profiles/fp64_iteration_kernels_tgv_8x8x8_N4.md
-}
+TRAFFIC = {}
 
 
 def cpu_sample(seed=0):
@@ -759,6 +759,8 @@ def main():
     ap.add_argument("--newton-tol", type=float, default=1e-6, help="timesteps arm: ||R|| / ||R_0|| per step")
     ap.add_argument("--max-newton", type=int, default=8, help="timesteps arm: Newton updates per step")
     ap.add_argument("--train-epochs", type=int, default=8, help="learned arm: training epochs (untimed)")
+    ap.add_argument("--learned-min-reduction", type=float, default=None,
+                    help="learned arm: restart-cycle reduction below which the solve falls back to block Jacobi")
     ap.add_argument("--operator", choices=["implicit", "explicit"], default="implicit",
                     help="mixed arm: condensed operator applied implicitly or from explicit W_e blocks")
     ap.add_argument("--precond", choices=["bj", "rb", "rbs"], default="rbs",

@@ -93,10 +93,10 @@ typedef struct {
   double inner_tol;      /* mixed arm: relative tolerance of each inner condensed solve */
   int tensor_cores;      /* mixed arm: 1 = element Schur products and the LU trailing updates
                             of S_ee on the TF32 tensor cores (tcgen05), 0 = FP32 CUDA cores */
-  double learned_min_reduction;  /* SC_PC_LEARNED: a GMRES restart cycle that reduces the
-                            condensed residual by less than this factor (the learned sweep has
-                            stagnated) switches the rest of the solve to block Jacobi, the
-                            fallback (1.5) */
+  double learned_min_reduction;  /* SC_PC_LEARNED: a full GMRES restart cycle (all
+                            gmres_restart iterations) that reduces the condensed residual by less
+                            than this factor (the learned sweep has stagnated) switches the rest
+                            of the solve to block Jacobi, the fallback (1.5) */
   int factor_fp16;       /* mixed arm: 1 = keep a copy of the block-Jacobi factors in FP16 for the
                             GMRES preconditioner (FP32 arithmetic; used only when every entry is
                             within the FP16 range, else the FP32 copy), 0 = FP32 only (default 0:

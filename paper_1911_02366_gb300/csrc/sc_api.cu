@@ -795,9 +795,10 @@ sc_status gmres_condensed(sc_ctx* c, double abs_tol, int max_iters, int* iters_o
     resid = beta;
     if (!std::isfinite(beta)) return fail(c, SC_ERR_NONFINITE, "non-finite condensed residual");
     if (beta <= abs_tol) ok = true;
-    // learned correction: a restart cycle that reduces the residual by less than the
-    // configured factor hands the rest of the solve to plain block Jacobi
-    if (!ok && c->learned_on && beta_cycle < c->cfg.learned_min_reduction * beta) {
+    // learned correction: a full restart cycle that reduces the residual by less than the
+    // configured factor hands the rest of the solve to plain block Jacobi (a cycle cut short
+    // by the Givens estimate reaching the tolerance is no measure of the preconditioner)
+    if (!ok && c->learned_on && k == m && beta_cycle < c->cfg.learned_min_reduction * beta) {
       c->learned_on = false;
       c->learned_fallbacks++;
     }

@@ -1183,6 +1183,126 @@ __device__ __forceinline__ void ls_solve_warp(int n, int nblk, const TS* __restr
 // to fill the GPU one warp each: in every block row the W warps share the off-diagonal
 // 4-column groups (strided), their partial dot products meet in shared memory, and warp
 // 0 adds the diagonal block's part and writes the row.  Two CTA barriers per block row.
+// ls_solve_warp with loads issued ahead of the dependence on s: each block row's diagonal
+// block quads are loaded before its long dot product, and the first 8 quads of the next
+// row's long part before the row's result is written.  The factor entries do not depend on
+// the solution, so a warp keeps more loads in flight across the short, serial stretch at
+// each block row; for launches with few warps per SM (one colour of the red-black sweep).
+template <class T, class TS>
+__device__ __forceinline__ void ls_solve_warp_pf(int n, int nblk, const TS* __restrict__ Le, int npad, T* s, int lane) {
+  const int nq = npad / 4;
+  Quad<T, TS> pre[8];
+  bool have_pre = false;
+  for (int b = 0; b < nblk; ++b) {  // forward: x_b = L_bb^-1 v_b - M_b x_{<b}
+    const int i0 = 32 * b, R = i0 + lane;
+    const bool live = R < n;
+    const TS* row = Le + (long long)b * 32 * npad + 4 * lane;
+    const int q0 = i0 / 4, qd = min(q0 + 8, nq);
+    Quad<T, TS> dg[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (live && q0 + t < qd && 4 * (q0 + t) < R) dg[t].load(row + (long long)(q0 + t) * 128);
+    T a0 = T(0), a1 = T(0);
+    if (live) {
+      int q = 0;
+      if (have_pre) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          a0 = fma(pre[t].v[0], s[4 * t], a0);
+          a1 = fma(pre[t].v[1], s[4 * t + 1], a1);
+          a0 = fma(pre[t].v[2], s[4 * t + 2], a0);
+          a1 = fma(pre[t].v[3], s[4 * t + 3], a1);
+        }
+        q = 8;
+      }
+#pragma unroll 8
+      for (; q < q0; ++q) {
+        Quad<T, TS> m;
+        m.load(row + (long long)q * 128);
+        a0 = fma(m.v[0], s[4 * q], a0);
+        a1 = fma(m.v[1], s[4 * q + 1], a1);
+        a0 = fma(m.v[2], s[4 * q + 2], a0);
+        a1 = fma(m.v[3], s[4 * q + 3], a1);
+      }
+    }
+    T d = s[R];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int q = q0 + t;
+      if (live && q < qd && 4 * q < R) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j < R) d = fma(dg[t].v[j], s[4 * q + j], d);
+      }
+    }
+    // the next row's first 8 quads (columns 0..31: its long part starts there)
+    have_pre = b + 1 < nblk && 32 * (b + 1) + lane < n;
+    if (have_pre) {
+      const TS* nrow = row + (long long)32 * npad;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) pre[t].load(nrow + (long long)t * 128);
+    }
+    __syncwarp();
+    if (live) s[R] = d - (a0 + a1);
+    __syncwarp();
+  }
+  have_pre = false;
+  for (int b = nblk - 1; b >= 0; --b) {  // backward: z_b = U_bb^-1 x_b - N_b z_{>b}
+    const int i0 = 32 * b, R = i0 + lane;
+    const bool live = R < n;
+    const TS* row = Le + (long long)b * 32 * npad + 4 * lane;
+    const int q0 = i0 / 4, qd = min(q0 + 8, nq);
+    Quad<T, TS> dg[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (live && q0 + t < qd && 4 * (q0 + t) + 3 >= R) dg[t].load(row + (long long)(q0 + t) * 128);
+    T a0 = T(0), a1 = T(0);
+    if (live) {
+      int q = q0 + 8;
+      if (have_pre) {  // the row's last 8 quads, loaded during the previous block row
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int qq = nq - 8 + t;
+          a0 = fma(pre[t].v[0], s[4 * qq], a0);
+          a1 = fma(pre[t].v[1], s[4 * qq + 1], a1);
+          a0 = fma(pre[t].v[2], s[4 * qq + 2], a0);
+          a1 = fma(pre[t].v[3], s[4 * qq + 3], a1);
+        }
+      }
+      const int qend = have_pre ? nq - 8 : nq;
+#pragma unroll 8
+      for (; q < qend; ++q) {
+        Quad<T, TS> m;
+        m.load(row + (long long)q * 128);
+        a0 = fma(m.v[0], s[4 * q], a0);
+        a1 = fma(m.v[1], s[4 * q + 1], a1);
+        a0 = fma(m.v[2], s[4 * q + 2], a0);
+        a1 = fma(m.v[3], s[4 * q + 3], a1);
+      }
+    }
+    T d = T(0);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int q = q0 + t;
+      if (live && q < qd && 4 * q + 3 >= R) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j >= R) d = fma(dg[t].v[j], s[4 * q + j], d);
+      }
+    }
+    // the previous row's last 8 quads (its long part, [q0 of this row, nq), holds at least 8)
+    have_pre = b >= 1 && 32 * (b - 1) + lane < n && nq - 8 >= (32 * (b - 1)) / 4 + 8;
+    if (have_pre) {
+      const TS* prow = row - (long long)32 * npad;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) pre[t].load(prow + (long long)(nq - 8 + t) * 128);
+    }
+    __syncwarp();
+    if (live) s[R] = d - (a0 + a1);
+    __syncwarp();
+  }
+}
+
 template <class T, class TS, int W>
 __device__ __forceinline__ void ls_solve_cta(int n, int nblk, const TS* __restrict__ Le, int npad, T* s, T* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1307,7 +1427,7 @@ __global__ void __launch_bounds__(32 * W) k_lu_solve_cta(int n, int nblk, const 
 // z = (P^T L U)^-1 v, one warp per element (4 per CTA); the running vector (v, then x,
 // then z) sits in shared memory.  Arithmetic in the factor precision T; v in double,
 // outputs z (double) and / or zt (T).
-template <class T, class TS>
+template <class T, class TS, bool PF = false>
 __global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const TS* __restrict__ LS, long long lsstride,
                                                   int npad, const int* __restrict__ rowperm,
                                                   const double* __restrict__ v, double* __restrict__ z,
@@ -1333,7 +1453,10 @@ __global__ void __launch_bounds__(128) k_lu_solve(int n, int nblk, const TS* __r
     s[i] = val;
   }
   __syncwarp();
-  ls_solve_warp<T, TS>(n, nblk, LS + (long long)f * lsstride, npad, s, lane);
+  if constexpr (PF)
+    ls_solve_warp_pf<T, TS>(n, nblk, LS + (long long)f * lsstride, npad, s, lane);
+  else
+    ls_solve_warp<T, TS>(n, nblk, LS + (long long)f * lsstride, npad, s, lane);
   for (int i = lane; i < n; i += 32) {
     const T val = s[i];
     if (z) z[(long long)e * n + i] = (double)val;
@@ -1596,8 +1719,11 @@ cudaError_t lu_solve_list_t(sc_ctx* c, const TS* LS, const int* rowperm, int com
     return cudaGetLastError();
   }
   const size_t smem = (size_t)4 * ls_nblk(G) * 32 * sizeof(T);
-  k_lu_solve<T, TS><<<cdiv(nlist, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G), ls_npad(G),
-                                                              rowperm, v, z, zt, nlist, elist, compact, vsub);
+  // FP32 factors: loads issued ahead (128 registers, 4 CTAs per SM hold one colour of 16^3)
+  constexpr bool pf = std::is_same<T, float>::value && std::is_same<TS, float>::value;
+  k_lu_solve<T, TS, pf><<<cdiv(nlist, 4), 128, smem, c->stream>>>(G.nb, ls_nblk(G), LS, ls_stride(G),
+                                                                  ls_npad(G), rowperm, v, z, zt, nlist, elist,
+                                                                  compact, vsub);
   return cudaGetLastError();
 }
 
