@@ -211,7 +211,10 @@ def run_ours(args, world, rank, local):
         step()
     torch.cuda.synchronize()
 
-    dominant = sc.SC_KERNEL_EXPLICIT_APPLY if args.operator == "explicit" else sc.SC_KERNEL_LU_SOLVE
+    dominant = {"lu_solve": sc.SC_KERNEL_LU_SOLVE, "cond_boundary": sc.SC_KERNEL_COND_BOUNDARY,
+                "cond_interior": sc.SC_KERNEL_COND_INTERIOR}[args.roofline_kernel]
+    if args.operator == "explicit":
+        dominant = sc.SC_KERNEL_EXPLICIT_APPLY
     ctx.sc_profile_kernel(dominant)
     sampler = ClockSampler(local) if rank == 0 else None
     l0 = ctx.sc_launch_count()
@@ -267,7 +270,8 @@ def run_ours(args, world, rank, local):
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = (TRAFFIC.get((args.arm, dominant)) * per_launch / K_all
                        if (W["n"], W["N"]) == (16, 4) and TRAFFIC.get((args.arm, dominant)) else None)
-    roof["kernel"] = {sc.SC_KERNEL_LU_SOLVE: "k_lu_solve", sc.SC_KERNEL_COND_BOUNDARY: "k_cond_boundary",
+    roof["kernel"] = {sc.SC_KERNEL_LU_SOLVE: "k_lu_solve", sc.SC_KERNEL_COND_BOUNDARY: "k_cond_boundary_pk",
+                      sc.SC_KERNEL_COND_INTERIOR: "k_cond_interior_pk",
                       sc.SC_KERNEL_EXPLICIT_APPLY: "k_explicit_w"}[dominant]
     roof["launches_timed"] = n_prof
     roof["avg_launch_ms"] = avg_ms
@@ -766,6 +770,8 @@ def main():
     ap.add_argument("--precond", choices=["bj", "rb", "rbs"], default="rbs",
                     help="condensed preconditioner: block Jacobi, the red-black block Gauss-Seidel sweep, or the "
                          "sweep with Schur-corrected black blocks (mixed arm; the FP64 arm takes the plain sweep)")
+    ap.add_argument("--roofline-kernel", choices=["lu_solve", "cond_boundary", "cond_interior"], default="lu_solve",
+                    help="the kernel whose launches the roofline object times (the step's largest share)")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)

@@ -355,7 +355,8 @@ sc_status sc_hessenberg_eigvals(int m, const double* H, double* re, double* im);
    Schur correction that eliminating the red neighbours adds to S_bb, halved).  A network
    predicts the correction of each element's face-block inverse there: from 128 features of
    node k' it gives y, and Z = [S_nn]_(k'k')^-1 + y / ||[S_nn]_(k'k')||_F (the exact Z needs n_b
-   unit solves per element).  Layout of the parameters (shared by every call): weights
+   unit solves per element); sc_condense applies the output at half weight, y/2 (shrunk
+   towards the closed form: the corrected black blocks amplify the network's errors).  Layout of the parameters (shared by every call): weights
    W = [W1 (256 x 128) | W2 (256 x 256) | W3 (25 x 256)], row-major, 104,704 values, kept as
    FP32 masters and as a BF16 copy (IEEE bfloat16 bit patterns in uint16_t); biases
    b = [b1 (256) | b2 (256) | b3 (25)], FP32.  Layers: h1 = relu(W1 x + b1),
@@ -434,7 +435,8 @@ sc_status sc_learned_targets(sc_ctx* ctx, float* T);
 
 /* Network parameters for SC_PC_LEARNED (device pointers, layout of sc_mlp_forward; copied
    into the context).  With precond = SC_PC_LEARNED, sc_condense evaluates the network on the
-   features of every boundary node, assembles the black blocks' corrections C and factorises
+   features of every boundary node, assembles the black blocks' corrections C from half its
+   outputs and factorises
    S_bb + C apart from the plain factors, which block Jacobi (the fallback) keeps using. */
 sc_status sc_set_learned_weights(sc_ctx* ctx, const uint16_t* Wbf16, const float* bias);
 

@@ -335,9 +335,11 @@ __global__ void k_vec_to_float(float* __restrict__ y, const double* __restrict__
     y[t] = (float)x[t];
 }
 
+// y = a x + b y; with b = 0 y is not read (it may hold anything, NaN included, e.g. a fresh
+// Krylov basis vector in memory another context used before).
 __global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    y[t] = a * x[t] + b * y[t];
+    y[t] = b == 0.0 ? a * x[t] : a * x[t] + b * y[t];
 }
 
 constexpr int kDotBlocks = 608;  // 4 x 152 SMs

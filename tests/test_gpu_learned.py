@@ -99,6 +99,43 @@ def test_learned_solve_matches_oracle_global_solve():
     assert np.linalg.norm(dQ - x) / np.linalg.norm(x) < 1e-9
 
 
+@pytest.mark.parametrize("n,N", [(4, 2), (2, 3)])
+def test_learned_apply_satisfies_the_oracle_corrected_blocks(n, N):
+    """One application of the learned sweep with given network outputs Y (here half the
+    oracle's exact targets) against the oracle's corrected black blocks
+    D_b = S_bb + C_b(Y) (oracle/learned.py): S_rr z_r = v_r, D_b z_b = v_b - sum_m S_bm z_m,
+    checked as a backward error (the GPU assembles C from its FP32 blocks and couplings)."""
+    from paper_1911_02366_gb300 import sc
+    Q, dt, p, ctx = _mixed(n, N, precond=sc.SC_PC_LEARNED)
+    ctx.sc_set_learned_weights(_net(3))
+    ctx.sc_condense()
+    S = O.condensed_operator(O.jacobian(p, Q), n, N).dense_S()
+    _, To, _ = LN.features_and_targets(S, Q, n, N, 0.1, 1600.0, dt)
+    ctx.sc_set_learned_correction(torch.tensor(To, dtype=torch.float32, device="cuda").contiguous(), 0.5)
+    D = O.corrected_black_blocks(S, n, LN.assemble_correction(S, 0.5 * To, n, N))
+    K = n ** 3
+    nb = S.shape[0] // K
+    v = np.random.default_rng(5).standard_normal(S.shape[0])
+    zt = torch.zeros(S.shape[0], dtype=torch.float64, device="cuda")
+    ctx.sc_precond_apply(torch.tensor(v, device="cuda"), zt)
+    z = zt.cpu().numpy()
+    col = O.checkerboard(n)
+    t = S @ np.where(np.repeat(col == 0, nb), z, 0.0)
+    r = np.empty_like(v)
+    for e in range(K):
+        sl = slice(e * nb, (e + 1) * nb)
+        M = D[e] if col[e] == 1 else S[sl, sl]
+        r[sl] = M @ z[sl] - v[sl] + (t[sl] if col[e] == 1 else 0.0)
+    scale = np.max(np.sum(np.abs(S), axis=1)) * np.max(np.abs(z)) + np.max(np.abs(v))
+    re = np.abs(r).reshape(K, nb).max(axis=1) / scale
+    diag = {"red_max": float(re[col == 0].max()), "black_max": float(re[col == 1].max())}
+    assert diag["red_max"] <= 2e-5 and diag["black_max"] <= 1e-4, diag
+    # against the uncorrected black blocks the residual is much larger: the correction is applied
+    r0 = np.concatenate([S[e * nb:(e + 1) * nb, e * nb:(e + 1) * nb] @ z[e * nb:(e + 1) * nb] - v[e * nb:(e + 1) * nb]
+                         + t[e * nb:(e + 1) * nb] for e in range(K) if col[e] == 1])
+    assert np.max(np.abs(r0)) > 20 * diag["black_max"] * scale, diag
+
+
 def _train_set(n, N, seeds, cfl):
     from paper_1911_02366_gb300 import sc
     Fs, Ts = [], []
@@ -124,8 +161,9 @@ def test_trained_correction_beats_block_jacobi_on_held_out_seeds(capsys):
     without a correction, and, for reference, with the closed form (zero network output) and
     the exact targets.  The node-diagonal correction's own headroom is small (exact targets:
     about 12 % fewer iterations than the plain sweep) and the network, whose relative error
-    stays near 0.25 whatever the training set, lands close to the plain sweep: the test asserts
-    the gain over block Jacobi and that the network costs at most 10 % over the plain sweep."""
+    stays near 0.25 whatever the training set and which the solver applies at half weight,
+    lands close to the plain sweep: the test asserts the gain over block Jacobi and that the
+    network costs at most 10 % over the plain sweep."""
     from paper_1911_02366_gb300 import sc
     n, N, cfl = 4, 3, 13.0
     X, Y = _train_set(n, N, range(100, 112), cfl)
