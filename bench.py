@@ -116,7 +116,7 @@ def gather_max(world, x):
     return float(t.item())
 
 
-def train_correction(args, stream):
+def train_correction(args, stream, cfl=None):
     """The learned arm's network, trained before the timed region on systems the method
     forms on the workload's own mesh and order (its element size and time step set the local
     physics the features see): Taylor-Green states of seeds 100.. (the timed system is seed 0)
@@ -129,9 +129,10 @@ def train_correction(args, stream):
     Fs, Ts = [], []
     t0 = time.perf_counter()
     n, N = WORKLOAD["n"], WORKLOAD["N"]
+    cfl = WORKLOAD["cfl"] if cfl is None else cfl
     mach = (0.05, 0.1, 0.2)
     for i, Ma in enumerate(mach):
-        Q, dt = I.tgv_state(n, N, Ma=Ma, seed=100 + i, cfl=WORKLOAD["cfl"])
+        Q, dt = I.tgv_state(n, N, Ma=Ma, seed=100 + i, cfl=cfl)
         c = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Ma=Ma, Re=WORKLOAD["Re"],
                        precond=sc.SC_PC_RED_BLACK)
         c.sc_set_mesh(n, 2 * math.pi, N)
@@ -269,7 +270,8 @@ def run_ours(args, world, rank, local):
                 "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = (TRAFFIC.get((args.arm, dominant)) * per_launch / K_all
-                       if (W["n"], W["N"]) == (16, 4) and TRAFFIC.get((args.arm, dominant)) else None)
+                       if (W["n"], W["N"]) == (16, 4) and args.precond in ("rb", "rbs") and args.arm == "mixed"
+                       and TRAFFIC.get((args.arm, dominant)) else None)
     roof["kernel"] = {sc.SC_KERNEL_LU_SOLVE: "k_lu_solve", sc.SC_KERNEL_COND_BOUNDARY: "k_cond_boundary_pk",
                       sc.SC_KERNEL_COND_INTERIOR: "k_cond_interior_pk",
                       sc.SC_KERNEL_EXPLICIT_APPLY: "k_explicit_w"}[dominant]
@@ -351,10 +353,15 @@ def fp64_reference_arm(args, W, Q, dt, stream, dQ_mixed):
             "solution_rel_diff_mixed_vs_fp64": diff}
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# captures summarised in profiles/, taken on the 8^3-element case and scaled x8 to the
-# 16^3 mesh (traffic grows with the element count); None once a kernel has changed.
-TRAFFIC = {}
+# DRAM traffic per launch over all elements (dram__bytes_read.sum + dram__bytes_write.sum)
+# from the one-pass ncu capture of the bench workload summarised in profiles/; None for the
+# kernels changed since.
+TRAFFIC = {
+    # k_lu_solve<float, float, 1> on one colour (2048 elements) of the 16^3, N = 4 workload:
+    # 2,043,262,464 + 93,952 bytes; x2 for a launch over all 4096 elements
+    # (profiles/dram_traffic_tgv_16x16x16_N4_rb_schur.md)
+    ("mixed", 2): 2 * (2043262464 + 93952),
+}
 
 
 def cpu_sample(seed=0):
@@ -540,11 +547,16 @@ def run_timesteps(args, world, rank, local):
     Q, dt = I.tgv_state(W["n"], W["N"], Ma=W["Ma"], seed=W["seed"], cfl=args.cfl)
     dofs = Q.size
     stream = torch.cuda.current_stream()
+    pc = {"bj": sc.SC_PC_BLOCK_JACOBI, "rb": sc.SC_PC_RED_BLACK, "rbs": sc.SC_PC_RB_SCHUR,
+          "learned": sc.SC_PC_LEARNED}[args.ts_precond]
+    net, train_info = (train_correction(args, stream, cfl=args.cfl) if pc == sc.SC_PC_LEARNED else (None, None))
     ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
-                     outer_krylov=args.outer_krylov, inner_iters=args.inner_iters)
+                     outer_krylov=args.outer_krylov, inner_iters=args.inner_iters, precond=pc)
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
+    if net is not None:
+        ctx.sc_set_learned_weights(net)
     Qs = torch.tensor(Q.reshape(-1), device="cuda")
     Qsm1 = None
     sampler = ClockSampler(local) if rank == 0 else None
@@ -553,16 +565,21 @@ def run_timesteps(args, world, rank, local):
     start = torch.cuda.Event(enable_timing=True); end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
     steps = []
+    failure = None
     for s in range(args.time_steps):
         bdf = 1 if Qsm1 is None else 2
         ctx.sc_set_timestep(dt, bdf)
         ctx.sc_set_state(Qs, Qs, Qsm1)  # Newton starts from the last level
-        it, nrel, st = ctx.sc_newton_step(max_newton=args.max_newton, newton_tol=args.newton_tol)
+        try:
+            it, nrel, st = ctx.sc_newton_step(max_newton=args.max_newton, newton_tol=args.newton_tol)
+        except sc.SCError as ex:  # recorded with the steps done so far; the line says it did not finish
+            failure = {"step": s, "bdf": bdf, "error": str(ex)}
+            break
         Qn = torch.empty_like(Qs)
         ctx.sc_get_state(Qn)
         Qsm1, Qs = Qs, Qn
         steps.append({"bdf": bdf, "newton": it, "newton_rel": nrel, "last_gmres_iters": st["gmres_iters"],
-                      "last_rel_residual": st["rel_residual"]})
+                      "last_rel_residual": st["rel_residual"], "last_learned_fallbacks": st["learned_fallbacks"]})
     end.record(stream)
     torch.cuda.synchronize()
     launches = ctx.sc_launch_count() - l0
@@ -571,17 +588,19 @@ def run_timesteps(args, world, rank, local):
     ctx.close()
     return {
         "metric": "implicit time steps: DOF x steps / s (Newton on each step, condensed mixed-precision solves)",
-        "value": world * dofs * args.time_steps / (total_ms * 1e-3), "unit": "DOF*steps/s", "n_gpus": world,
-        "steps": args.time_steps, "warmup": 0, "ms_per_step": total_ms / args.time_steps, "higher_is_better": True,
+        "value": world * dofs * len(steps) / (total_ms * 1e-3), "unit": "DOF*steps/s", "n_gpus": world,
+        "steps": args.time_steps, "warmup": 0, "ms_per_step": total_ms / max(len(steps), 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded Taylor-Green state, 1e-3 perturbation)",
         "config": {"workload": f"tgv_{W['n']}x{W['n']}x{W['n']}_N{W['N']}_bdf2_cfl{args.cfl:g}",
                    "elements": W["n"] ** 3, "order": W["N"], "dof": dofs, "cfl": args.cfl, "dt": dt,
                    "newton_tol": args.newton_tol, "linear_rel_tol": REL_TOL, "arm": "timesteps",
                    "outer": f"fgmres({args.outer_krylov})" if args.outer_krylov else "refinement sweeps",
-                   "inner_iters_cap": args.inner_iters or None,
+                   "inner_iters_cap": args.inner_iters or None, "precond": args.ts_precond,
                    "gmres_restart": args.restart, "parallelism": f"replicas x{world}"},
+        "training": train_info,
         "time_steps": steps, "newton_total": sum(x["newton"] for x in steps),
+        "completed_steps": len(steps), "failure": failure,
         "gpu_launches": launches, "clocks": clocks,
     }
 
@@ -760,6 +779,8 @@ def main():
     ap.add_argument("--max-implicit-steps", type=int, default=400)
     ap.add_argument("--time-steps", type=int, default=10, help="timesteps arm: BDF2 steps")
     ap.add_argument("--cfl", type=float, default=100.0, help="timesteps arm: CFL of the time step")
+    ap.add_argument("--ts-precond", choices=["bj", "rb", "rbs", "learned"], default="rb",
+                    help="timesteps arm: preconditioner of the condensed GMRES (learned: trained first, untimed)")
     ap.add_argument("--newton-tol", type=float, default=1e-6, help="timesteps arm: ||R|| / ||R_0|| per step")
     ap.add_argument("--max-newton", type=int, default=8, help="timesteps arm: Newton updates per step")
     ap.add_argument("--train-epochs", type=int, default=8, help="learned arm: training epochs (untimed)")

@@ -116,7 +116,7 @@ void free_all(sc_ctx* c) {
   c->Sdiag_valid = c->weights_set = c->learned_on = false;
   int** ips[] = {&c->d_nbr, &c->d_perm, &c->d_iperm, &c->d_own_pairs, &c->d_prow, &c->d_pslot, &c->d_pcol, &c->d_pptr,
                  &c->d_pinfo, &c->piv, &c->rowperm, &c->d_status, &c->d_pk_lptr, &c->d_pk_list,
-                 &c->d_pk_row_off, &c->d_pk_pos, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx,
+                 &c->d_pk_row_off, &c->d_pk_pos, &c->d_pk_nint, &c->d_lface, &c->d_lmirror, &c->d_ex_nbpos, &c->d_ex_face_idx,
                  &c->d_colour, &c->pivL, &c->rowpermL, &c->d_lnfaces, &c->d_lface3, &c->d_lmirror3,
                  &c->d_lrslot3, &c->d_redidx, &c->d_face_tab};
   for (auto p : ips) { if (*p) cudaFree(*p); *p = nullptr; }
@@ -357,6 +357,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->d_pptr, G.nn + 1)); A(dalloc(&c->d_pinfo, np));
   A(dalloc(&c->d_pk_lptr, c->pk_lptr.size())); A(dalloc(&c->d_pk_list, c->pk_list.size()));
   A(dalloc(&c->d_pk_row_off, c->pk_row_off.size())); A(dalloc(&c->d_pk_pos, c->pk_pos.size()));
+  A(dalloc(&c->d_pk_nint, c->pk_nint.size()));
   A(dalloc(&c->d_lface, G.nbn)); A(dalloc(&c->d_lmirror, G.nbn)); A(dalloc(&c->d_lnfaces, G.nbn));
   A(dalloc(&c->d_lface3, 3 * (size_t)G.nbn)); A(dalloc(&c->d_lmirror3, 3 * (size_t)G.nbn));
   A(dalloc(&c->d_lrslot3, 3 * (size_t)G.nbn));

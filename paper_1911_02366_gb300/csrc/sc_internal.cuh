@@ -275,8 +275,10 @@ struct sc_ctx {
   double* dQn = nullptr;    // Newton update of sc_newton_step
   // pattern-packed own blocks of the condensed operator (A_ib rows, [A_bi A_bb] rows)
   std::vector<int> pk_lptr, pk_list, pk_pos, pk_row_off;
+  std::vector<int> pk_nint;  // per node slot: packed entries of its rows in interior columns (listed first)
   long long pk_stride = 0, pk_nnz_int = 0, pk_nnz_bnd = 0;
   int *d_pk_lptr = nullptr, *d_pk_list = nullptr, *d_pk_row_off = nullptr, *d_pk_pos = nullptr;
+  int* d_pk_nint = nullptr;
   double* Apk = nullptr;   // FP64 arm
   float* Apk32 = nullptr;  // mixed arm
   // S_ee factors with partitioned inverses in the block-Jacobi solve layout
@@ -461,7 +463,9 @@ cudaError_t upload_packed_pattern(sc_ctx* c);
 cudaError_t pack_own(sc_ctx* c);
 template <class T>
 cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* X, const T* Ainv, const T* xb, double beta,
-                             const double* Bfull, double alpha, T* u);
+                             const double* Bfull, double alpha, T* u, int black_zero);
+cudaError_t cond_interior_sweep(sc_ctx* c, const double* xb, double* u);
+cudaError_t cond_interior_sweep32(sc_ctx* c, const float* xb, float* u);
 template <class T>
 cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* X, const T* xb, double delta, const double* Bfull,
                              double gamma_, const T* u, double* y);

@@ -358,7 +358,7 @@ cudaError_t cond_interior_t(sc_ctx* c, const T* Aown, const T* Apk, const T* X, 
   if (G.ni == 0) return cudaSuccess;
   if (Apk) {
     ProfScope ps(c, SCK_COND_INTERIOR);
-    return cond_interior_pk<T>(c, Apk, X, Ainv, xb, beta, Bfull, alpha, u);
+    return cond_interior_pk<T>(c, Apk, X, Ainv, xb, beta, Bfull, alpha, u, 0);
   }
   if (xb) {
     count_launch(c);
@@ -410,6 +410,20 @@ cudaError_t cond_boundary(sc_ctx* c, const double* xb, double delta, const doubl
 cudaError_t cond_interior32(sc_ctx* c, const float* xb, double beta, const double* Bfull, double alpha, float* u) {
   return cond_interior_t<float>(c, c->Aown32, c->packed ? c->Apk32 : nullptr, c->X32, c->Ainv32, c->Cross32, xb, beta,
                                 Bfull, alpha, u);
+}
+
+// Interior pass of the red-black sweep: u = A_ii^-1 (A_ib x_b) with x_b zero on the black
+// elements, whose own part is then skipped (packed blocks; otherwise the general pass).
+cudaError_t cond_interior_sweep(sc_ctx* c, const double* xb, double* u) {
+  if (!c->packed || c->G.ni == 0) return cond_interior(c, xb, 1.0, nullptr, 0.0, u);
+  ProfScope ps(c, SCK_COND_INTERIOR);
+  return cond_interior_pk<double>(c, c->Apk, c->X, c->Ainv, xb, 1.0, nullptr, 0.0, u, 1);
+}
+
+cudaError_t cond_interior_sweep32(sc_ctx* c, const float* xb, float* u) {
+  if (!c->packed || c->G.ni == 0) return cond_interior32(c, xb, 1.0, nullptr, 0.0, u);
+  ProfScope ps(c, SCK_COND_INTERIOR);
+  return cond_interior_pk<float>(c, c->Apk32, c->X32, c->Ainv32, xb, 1.0, nullptr, 0.0, u, 1);
 }
 
 cudaError_t cond_boundary32(sc_ctx* c, const float* xb, double delta, const double* Bfull, double gamma_,

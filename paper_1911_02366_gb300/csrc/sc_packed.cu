@@ -136,9 +136,13 @@ __global__ void __launch_bounds__(256, PkOcc<T>::v) k_cond_interior_pk(Geo G, co
     const int* __restrict__ row_off, const int* __restrict__ lptr, const int* __restrict__ list,
     const T* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
     const int* __restrict__ pinfo, const T* __restrict__ Ainv, const int* __restrict__ iperm,
-    const T* __restrict__ xb, double beta, const double* __restrict__ Bfull, double alpha, T* __restrict__ u) {
+    const T* __restrict__ xb, double beta, const double* __restrict__ Bfull, double alpha, T* __restrict__ u,
+    int black_zero) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int e = blockIdx.x, ni = G.ni, nb = G.nb, lda = G.lda, ldi = G.ldi;
+  // black_zero: x_b is zero on the black elements (the red-black sweep), so their own A_ib x_b
+  // part is skipped and only the neighbour couplings feed their interior solve
+  const bool own = !(black_zero && ((e % G.n + (e / G.n) % G.n + e / (G.n * G.n)) & 1));
   T* v = reinterpret_cast<T*>(smem_raw);  // lda: x_e at the boundary columns
   T* t = v + lda;                         // ldi: right-hand side of the interior solve
   __shared__ int nbr_s[18];
@@ -157,8 +161,10 @@ __global__ void __launch_bounds__(256, PkOcc<T>::v) k_cond_interior_pk(Geo G, co
     const int j = __ldg(iperm + p);
     T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (xb) {
-      const int l0 = __ldg(lptr + p), n = 5 * (__ldg(lptr + p + 1) - l0);
-      own_node5(Pe + __ldg(row_off + 5 * p), (n + 3) & ~3, n, list + l0, v, lane, acc);
+      if (own) {
+        const int l0 = __ldg(lptr + p), n = 5 * (__ldg(lptr + p + 1) - l0);
+        own_node5(Pe + __ldg(row_off + 5 * p), (n + 3) & ~3, n, list + l0, v, lane, acc);
+      }
       const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
       cross_node5(X + ((size_t)e * 5 * G.NP + q0) * 5, ks, 5 * (q1 - q0), pinfo + q0, nbr_s, nb, ni, xb, T(1),
                   (const T*)nullptr, T(0), lane, acc);
@@ -208,7 +214,7 @@ __global__ void __launch_bounds__(256, PkOcc<T>::v) k_cond_boundary_pk(Geo G, co
     const T* __restrict__ X, const int* __restrict__ nbr, const int* __restrict__ pptr,
     const int* __restrict__ pinfo, const int* __restrict__ iperm, const T* __restrict__ xb, double delta,
     const double* __restrict__ Bfull, double gamma_, const T* __restrict__ u, double* __restrict__ y,
-    const int* __restrict__ elist) {
+    const int* __restrict__ elist, const int* __restrict__ nint) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // CTA i serves element elist[i] (one colour of the red-black sweep), or element i
   const int e = elist ? __ldg(elist + blockIdx.x) : blockIdx.x, ni = G.ni, nb = G.nb, lda = G.lda, cb0 = G.cb0;
@@ -232,7 +238,8 @@ __global__ void __launch_bounds__(256, PkOcc<T>::v) k_cond_boundary_pk(Geo G, co
     T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (need) {
       const int l0 = __ldg(lptr + p), n = 5 * (__ldg(lptr + p + 1) - l0);
-      own_node5(Pe + __ldg(row_off + 5 * p), (n + 3) & ~3, n, list + l0, v, lane, acc);
+      // with nint: the element's own boundary values are zero, only the interior columns count
+      own_node5(Pe + __ldg(row_off + 5 * p), (n + 3) & ~3, nint ? __ldg(nint + p) : n, list + l0, v, lane, acc);
       const int q0 = __ldg(pptr + j), q1 = __ldg(pptr + j + 1);
       cross_node5(X + ((size_t)e * 5 * G.NP + q0) * 5, ks, 5 * (q1 - q0), pinfo + q0, nbr_s, nb, ni, xb, dT, u,
                   T(-1), lane, acc);
@@ -274,6 +281,9 @@ void build_packed_pattern(sc_ctx* c) {
     }
     c->pk_lptr[p + 1] = c->pk_lptr[p] + len;
   }
+  c->pk_nint.assign(nn, 0);
+  for (int p = 0; p < nn; ++p)
+    for (int i = c->pk_lptr[p]; i < c->pk_lptr[p + 1]; ++i) c->pk_nint[p] += c->pk_list[i] < G.ni ? 5 : 0;
   c->pk_row_off.assign(G.ne + 1, 0);
   c->pk_nnz_int = c->pk_nnz_bnd = 0;
   for (int r = 0; r < G.ne; ++r) {
@@ -293,6 +303,8 @@ cudaError_t upload_packed_pattern(sc_ctx* c) {
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->d_pk_pos, c->pk_pos.data(), c->pk_pos.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_pk_nint, c->pk_nint.data(), c->pk_nint.size() * sizeof(int), cudaMemcpyHostToDevice);
   return e;
 }
 
@@ -312,12 +324,12 @@ cudaError_t pack_own(sc_ctx* c) {
 
 template <class T>
 cudaError_t cond_interior_pk(sc_ctx* c, const T* Apk, const T* X, const T* Ainv, const T* xb, double beta,
-                             const double* Bfull, double alpha, T* u) {
+                             const double* Bfull, double alpha, T* u, int black_zero) {
   const Geo& G = c->G;
   const size_t smem = (size_t)(G.lda + G.ldi) * sizeof(T);
   k_cond_interior_pk<T><<<G.K, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
                                                        c->d_pk_list, X, c->d_nbr, c->d_pptr, c->d_pinfo, Ainv,
-                                                       c->d_iperm, xb, beta, Bfull, alpha, u);
+                                                       c->d_iperm, xb, beta, Bfull, alpha, u, black_zero);
   return cudaGetLastError();
 }
 
@@ -328,11 +340,13 @@ cudaError_t cond_boundary_pk(sc_ctx* c, const T* Apk, const T* X, const T* xb, d
   const size_t smem = (size_t)G.lda * sizeof(T);
   k_cond_boundary_pk<T><<<G.K, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
                                                        c->d_pk_list, X, c->d_nbr, c->d_pptr, c->d_pinfo, c->d_iperm,
-                                                       xb, delta, Bfull, gamma_, u, y, nullptr);
+                                                       xb, delta, Bfull, gamma_, u, y, nullptr, nullptr);
   return cudaGetLastError();
 }
 
-// y_e = (A_bb x_b)_e - (A_bi u)_e for the elements of a list only (rows of one colour).
+// y_e = (A_bb x_b)_e - (A_bi u)_e for the elements of a list only (rows of one colour), whose
+// own boundary values in x_b are zero (the black elements in the red-black sweep): their packed
+// rows are read in the interior columns only (a quarter of the own-block bytes at N = 4).
 template <class T>
 cudaError_t cond_boundary_pk_list(sc_ctx* c, const T* Apk, const T* X, const T* xb, const T* u, double* y,
                                   const int* elist, int nlist) {
@@ -343,7 +357,7 @@ cudaError_t cond_boundary_pk_list(sc_ctx* c, const T* Apk, const T* X, const T* 
   k_cond_boundary_pk<T><<<nlist, 256, smem, c->stream>>>(G, Apk, c->pk_stride, c->d_pk_row_off, c->d_pk_lptr,
                                                          c->d_pk_list, X, c->d_nbr, c->d_pptr, c->d_pinfo,
                                                          c->d_iperm, xb, 1.0, nullptr, 0.0, G.ni ? u : nullptr, y,
-                                                         elist);
+                                                         elist, c->d_pk_nint);
   return cudaGetLastError();
 }
 template cudaError_t cond_boundary_pk_list<float>(sc_ctx*, const float*, const float*, const float*, const float*,
@@ -352,9 +366,9 @@ template cudaError_t cond_boundary_pk_list<double>(sc_ctx*, const double*, const
                                                    const double*, double*, const int*, int);
 
 template cudaError_t cond_interior_pk<float>(sc_ctx*, const float*, const float*, const float*, const float*, double,
-                                             const double*, double, float*);
+                                             const double*, double, float*, int);
 template cudaError_t cond_interior_pk<double>(sc_ctx*, const double*, const double*, const double*, const double*,
-                                              double, const double*, double, double*);
+                                              double, const double*, double, double*, int);
 template cudaError_t cond_boundary_pk<float>(sc_ctx*, const float*, const float*, const float*, double, const double*,
                                              double, const float*, double*);
 template cudaError_t cond_boundary_pk<double>(sc_ctx*, const double*, const double*, const double*, double,

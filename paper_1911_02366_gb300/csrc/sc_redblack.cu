@@ -163,7 +163,7 @@ cudaError_t precond_rb(sc_ctx* c, const double* v, double* z) {
   const size_t n1 = (size_t)G.K * G.nb;
   cudaError_t e = cudaMemsetAsync(z, 0, n1 * sizeof(double), c->stream);
   if (e == cudaSuccess) e = lu_solve_list(c, c->Sls, c->rowperm, 0, c->d_colour, c->n_red, v, nullptr, z);
-  if (e == cudaSuccess) e = cond_interior(c, z, 1.0, nullptr, 0.0, c->Ui);
+  if (e == cudaSuccess) e = cond_interior_sweep(c, z, c->Ui);
   if (e == cudaSuccess)
     e = cond_boundary_pk_list<double>(c, c->Apk, c->X, z, c->Ui, c->Trb, c->d_colour + c->n_red, c->n_black);
   if (e == cudaSuccess)
@@ -181,7 +181,7 @@ cudaError_t precond_rb32(sc_ctx* c, const double* v, double* z, float* zf) {
   const int* black = c->d_colour + c->n_red;
   cudaError_t e = cudaMemsetAsync(zt, 0, n1 * sizeof(float), c->stream);
   if (e == cudaSuccess) e = lu_solve_list32(c, c->Sls32, c->rowperm, 0, c->d_colour, c->n_red, v, nullptr, z, zt);
-  if (e == cudaSuccess) e = cond_interior32(c, zt, 1.0, nullptr, 0.0, c->Uf);
+  if (e == cudaSuccess) e = cond_interior_sweep32(c, zt, c->Uf);
   if (e == cudaSuccess) e = cond_boundary_pk_list<float>(c, c->Apk32, c->X32, zt, c->Uf, c->Trb, black, c->n_black);
   if (e == cudaSuccess) {
     if (corrected)
