@@ -15,6 +15,7 @@
 //     time-out raises an error status instead of spinning;
 //   * the four warps read their 32 TMEM lanes (rows) with tcgen05.ld and write
 //     C = alpha * acc + beta * C.
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -201,6 +202,8 @@ struct Stager {
 };
 
 constexpr int TC_TMEM_COLS = 256;
+// TMEM columns of a 128 x BN accumulator: a power of two of at least 32
+constexpr uint32_t tmem_cols_for(int bn) { return bn <= 32 ? 32u : bn <= 64 ? 64u : bn <= 128 ? 128u : 256u; }
 constexpr int TC_EG = 4;  // 8-column chunks per epilogue group
 template <int BN>
 constexpr size_t tc_stage_bytes() {
@@ -217,6 +220,7 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(int M, int N, int K, float al
                                                    const float* const* __restrict__ Ap,
                                                    const float* const* __restrict__ Bp, float* const* __restrict__ Cp) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= TC_TMEM_COLS, "M = 128 needs N % 16 == 0 and N <= 256");
+  constexpr uint32_t kTmemCols = tmem_cols_for(BN);
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr size_t kA = (size_t)(TC_BM / 8) * TC_SBO, kStage = tc_stage_bytes<BN>();
   __shared__ __align__(8) uint64_t mbar[2];
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(int M, int N, int K, float al
   const float* Ab = TA ? A + m0 : A + (long long)m0 * lda;
   const float* Bb = TB ? B + (long long)n0 * ldb : B + n0;
   const int mrows = min(TC_BM, M - m0), nrows = min(BN, N - n0);
-  if (warp == 0) tmem_alloc(&tmem_base_s, TC_TMEM_COLS);
+  if (warp == 0) tmem_alloc(&tmem_base_s, kTmemCols);
   if (tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
@@ -373,7 +377,7 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(int M, int N, int K, float al
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
   if (s_err && tid == 0) atomicCAS(status, -1, SC_TC_TIMEOUT);
 }
 
@@ -382,9 +386,14 @@ cudaError_t launch_tf32(cudaStream_t stream, int M, int N, int K, float alpha, c
                         const float* B, long long sB, int ldb, float beta, float* C, long long sC, int ldc, int batch,
                         int flags, int* status, const float* const* Ap = nullptr, const float* const* Bp = nullptr,
                         float* const* Cp = nullptr) {
-  constexpr size_t smem = 2 * tc_stage_bytes<BN>();
-  // two CTAs per SM: 2 x 256 TMEM columns fill the 512 of an SM
-  static_assert(2 * (smem + 1024) <= 228 * 1024, "two CTAs per SM must fit");
+  constexpr size_t smem2 = 2 * tc_stage_bytes<BN>();
+  static_assert(2 * (smem2 + 1024) <= 228 * 1024, "two CTAs per SM must fit");
+  // K within one 32-wide chunk (the LU trailing updates): one staging buffer.  The request
+  // is padded so that no more CTAs share an SM than its 512 TMEM columns hold, and none
+  // waits in tcgen05.alloc.
+  constexpr int kMaxCtas = 512 / (int)tmem_cols_for(BN);
+  constexpr size_t kSmemSM = 228 * 1024, kMinSmem = kSmemSM / (kMaxCtas + 1) - 1024 + 16;
+  const size_t smem = std::max(K <= TC_BK ? tc_stage_bytes<BN>() : smem2, kMinSmem);
   cudaError_t e = cudaFuncSetAttribute(k_gemm_tf32<BN, TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((N + BN - 1) / BN, (M + TC_BM - 1) / TC_BM, batch);
@@ -432,6 +441,9 @@ cudaError_t gemm_tf32(cudaStream_t stream, int M, int N, int K, float alpha, con
   if (N <= 64)
     return launch_tf32_t<64>(stream, M, N, K, alpha, A, sA, lda, ta, B, sB, ldb, tb, beta, C, sC, ldc, batch, flags,
                              status);
+  if (K <= TC_BK)  // rank-32 updates: 128-wide tiles, one staging buffer, four CTAs per SM
+    return launch_tf32_t<128>(stream, M, N, K, alpha, A, sA, lda, ta, B, sB, ldb, tb, beta, C, sC, ldc, batch, flags,
+                              status);
   if (N <= 144)
     return launch_tf32_t<144>(stream, M, N, K, alpha, A, sA, lda, ta, B, sB, ldb, tb, beta, C, sC, ldc, batch, flags,
                               status);
