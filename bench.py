@@ -188,7 +188,8 @@ def run_ours(args, world, rank, local):
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
                      outer_krylov=args.outer_krylov if args.arm != "fp64" else 0, inner_iters=args.inner_iters,
-                     explicit_schur=1 if args.operator == "explicit" else 0, **extra)
+                     explicit_schur=1 if args.operator == "explicit" else 0,
+                     interior_fp64=args.interior_fp64 if args.arm != "fp64" else 0, **extra)
 
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
     if args.arm == "learned":
@@ -553,7 +554,8 @@ def run_timesteps(args, world, rank, local):
     ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
-                     outer_krylov=args.outer_krylov, inner_iters=args.inner_iters, precond=pc)
+                     outer_krylov=args.outer_krylov, inner_iters=args.inner_iters, precond=pc,
+                     interior_fp64=args.interior_fp64)
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
     if net is not None:
         ctx.sc_set_learned_weights(net)
@@ -597,6 +599,7 @@ def run_timesteps(args, world, rank, local):
                    "newton_tol": args.newton_tol, "linear_rel_tol": REL_TOL, "arm": "timesteps",
                    "outer": f"fgmres({args.outer_krylov})" if args.outer_krylov else "refinement sweeps",
                    "inner_iters_cap": args.inner_iters or None, "precond": args.ts_precond,
+                   "interior_fp64": bool(args.interior_fp64),
                    "gmres_restart": args.restart, "parallelism": f"replicas x{world}"},
         "training": train_info,
         "time_steps": steps, "newton_total": sum(x["newton"] for x in steps),
@@ -793,6 +796,8 @@ def main():
                          "sweep with Schur-corrected black blocks (mixed arm; the FP64 arm takes the plain sweep)")
     ap.add_argument("--roofline-kernel", choices=["lu_solve", "cond_boundary", "cond_interior"], default="lu_solve",
                     help="the kernel whose launches the roofline object times (the step's largest share)")
+    ap.add_argument("--interior-fp64", type=int, choices=[0, 1], default=0,
+                    help="mixed arms, N >= 5: A_ii^-1 by FP64 Gauss-Jordan, rounded to FP32 for the operator")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)

@@ -113,6 +113,10 @@ typedef struct {
                             too inexact for the conditioning */
   int inner_iters;       /* mixed arm: cap on the GMRES iterations of one inner condensed solve
                             (0 = no cap; the inner tolerance alone ends it) */
+  int interior_fp64;     /* mixed arm, n_i > 136 (N >= 5): 1 = A_ii^-1 by FP64 blocked Gauss-Jordan
+                            on the FP64 own blocks, rounded to FP32 for the operator (FP32 rounding
+                            instead of the ~3e-5 of the FP32 inverse at N = 6; costs the FP64 pipe
+                            and n_i^2 doubles per element); 0 = FP32 Gauss-Jordan (default) */
 } sc_config;
 
 /* Per-solve statistics filled by sc_solve. */
@@ -449,7 +453,8 @@ sc_status sc_set_learned_correction(sc_ctx* ctx, const float* Y, float scale);
 /* ---- Batched condensation of elements of uneven order ---------------------------
    Not in the paper: the condensation set-up (A_ii^-1, Y, S_ee, LU of S_ee, solve layout;
    Sec. 2.2 eq. StaticCondBlock) of several assembled systems, each of one order N (mixed
-   arm, block Jacobi, tensor cores, FP32 factors, implicit operator, one shared stream), run
+   arm, block Jacobi, tensor cores, FP32 factors and interior inverses, implicit operator, one
+   shared stream), run
    together: the per-element steps as grouped launches over all elements of all orders, the
    TF32 products per order through tables of block addresses.  After sc_batch_condense each
    system is condensed exactly as by its own sc_condense and is solved with sc_solve. */

@@ -216,6 +216,7 @@ sc_status sc_create(const sc_config* cfg, void* cuda_stream, sc_ctx** out) {
     return SC_ERR_ARG;
   if (cfg->precision != SC_PREC_FP64 && cfg->precision != SC_PREC_MIXED) return SC_ERR_ARG;
   if (cfg->precond < SC_PC_BLOCK_JACOBI || cfg->precond > SC_PC_RB_SCHUR) return SC_ERR_ARG;
+  if (cfg->interior_fp64 != 0 && cfg->interior_fp64 != 1) return SC_ERR_ARG;
   if (cfg->outer_krylov < 0 || cfg->outer_krylov > cfg->gmres_restart || cfg->inner_iters < 0) return SC_ERR_ARG;
   sc_ctx* c = new sc_ctx();
   c->cfg = *cfg;
@@ -331,6 +332,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   if (c->cfg.precision == SC_PREC_MIXED) {
     A(dalloc(&c->Aown32, (size_t)G.K * own_stride(G))); A(dalloc(&c->X32, (size_t)G.K * G.NP * 25));
     A(dalloc(&c->Ainv32, (size_t)G.K * G.ni * G.ldi)); A(dalloc(&c->Y32, (size_t)G.K * G.nb * G.ldi));  // Y^T (nb x ldi) on the tensor-core path
+    if (c->cfg.interior_fp64 && G.ni > sc::kGjRegRows) A(dalloc(&c->Ainv, (size_t)G.K * G.ni * G.ldi));  // FP64 A_ii^-1
     A(dalloc(&c->See32, (size_t)G.K * G.nb * G.lds)); A(dalloc(&c->Dfull, dofs));
     A(dalloc(&c->Zf, n1)); A(dalloc(&c->Xbf, n1)); A(dalloc(&c->Uf, (size_t)G.K * G.ni));
     A(dalloc(&c->Cross32, n1 + (size_t)G.K * G.ni));

@@ -149,7 +149,8 @@ sc_status sc_batch_create(sc_ctx* const* ctxs, int nctx, sc_batch** out) {
   for (int i = 0; i < nctx; ++i) {
     sc_ctx* c = ctxs[i];
     if (!c || !c->has_mesh || c->cfg.precision != SC_PREC_MIXED || c->cfg.precond != SC_PC_BLOCK_JACOBI ||
-        c->cfg.explicit_schur || !c->cfg.tensor_cores || c->cfg.factor_fp16 || c->stream != b->stream) {
+        c->cfg.explicit_schur || !c->cfg.tensor_cores || c->cfg.factor_fp16 || c->cfg.interior_fp64 ||
+        c->stream != b->stream) {
       delete b;
       return SC_ERR_ARG;
     }

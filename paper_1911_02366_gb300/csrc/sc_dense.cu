@@ -107,6 +107,7 @@ __device__ void gj_inv_body(int n, const T* __restrict__ Ae, int lda, T* __restr
 // the Jacobian's rows span three orders of magnitude, and unscaled FP32 Gauss-Jordan loses
 // about two digits against an LU-based inverse on these blocks.
 constexpr int GJR_R = 17, GJR_C = 5, GJR_N = 8 * GJR_R, GJR_LDS = GJR_N + 1;
+static_assert(GJR_N == sc::kGjRegRows, "register Gauss-Jordan bound");
 // dynamic shared memory the one-CTA Gauss-Jordan may take (227 KB less its static part)
 constexpr size_t kGjSmemMax = 227 * 1024 - 64;
 
@@ -1547,13 +1548,13 @@ cudaError_t gj_blocked(sc_ctx* c, const T* Aown, long long sA, int lda, T* Ainv,
 // trailing updates run on the TF32 tensor cores and Y is kept transposed (nb x ldi), the
 // K-major operand layout of the second product.
 template <class T>
-cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc) {
+cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc, bool have_inv = false) {
   const Geo& G = c->G;
   const int ni = G.ni, nb = G.nb, K = G.K, lda = G.lda, cb0 = G.cb0, ldi = G.ldi, lds = G.lds;
   const long long sA = (long long)own_stride(G);
   cudaError_t err;
   if (ni > 0) {
-    bool done = false;
+    bool done = have_inv;  // A_ii^-1 already in Ainv
     if constexpr (std::is_same<T, float>::value) {
       if (ni <= GJR_N) {
         const size_t smem = (size_t)GJR_N * GJR_LDS * sizeof(float);
@@ -1668,7 +1669,16 @@ cudaError_t launch_condense(sc_ctx* c) {
     count_launch(c);
     const size_t nx = (size_t)G.K * G.NP * 25;
     k_to_float<<<608, 256, 0, c->stream>>>(c->X, c->X32, nx);
-    return condense_t<float>(c, c->Aown32, c->Ainv32, c->Y32, c->See32, c->cfg.tensor_cores != 0);
+    bool have_inv = false;
+    if (c->cfg.interior_fp64 && c->Ainv && G.ni > GJR_N) {
+      // A_ii^-1 in FP64 from the FP64 own blocks, rounded to FP32 for the operator
+      cudaError_t e = gj_blocked<double>(c, c->Aown, (long long)own_stride(G), G.lda, c->Ainv, G.ldi);
+      if (e != cudaSuccess) return e;
+      count_launch(c);
+      k_to_float<<<608, 256, 0, c->stream>>>(c->Ainv, c->Ainv32, (size_t)G.K * G.ni * G.ldi);
+      have_inv = true;
+    }
+    return condense_t<float>(c, c->Aown32, c->Ainv32, c->Y32, c->See32, c->cfg.tensor_cores != 0, have_inv);
   }
   return condense_t<double>(c, c->Aown, c->Ainv, c->Ytmp, c->See, false);
 }

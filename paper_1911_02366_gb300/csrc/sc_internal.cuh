@@ -455,6 +455,8 @@ cudaError_t extract_sdiag(sc_ctx* c, const float* See);
 cudaError_t learned_features(sc_ctx* c, float* F, float* snorm);
 cudaError_t learned_correction(sc_ctx* c);
 cudaError_t assemble_correction(sc_ctx* c, const float* Y, float scale);
+// FP32 interior inverses up to this n_i run register-resident (k_gj_inv_reg); larger ones blocked
+constexpr int kGjRegRows = 136;
 constexpr int kMlpInputs = 128;
 constexpr int kMlpWeights = 256 * kMlpInputs + 256 * 256 + 25 * 256, kMlpBiases = 2 * 256 + 25;
 cudaError_t mlp_forward(cudaStream_t st, const uint16_t* Wbf16, const float* bias, const float* X, int n, float* Y,

@@ -36,7 +36,7 @@ class sc_config(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("rel_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("tensor_cores", ctypes.c_int), ("learned_min_reduction", ctypes.c_double),
                 ("factor_fp16", ctypes.c_int), ("explicit_schur", ctypes.c_int),
-                ("outer_krylov", ctypes.c_int), ("inner_iters", ctypes.c_int)]
+                ("outer_krylov", ctypes.c_int), ("inner_iters", ctypes.c_int), ("interior_fp64", ctypes.c_int)]
 
 
 class sc_solve_stats(ctypes.Structure):

@@ -186,6 +186,30 @@ def test_mixed_condensed_operator_is_fp32_close(n, N):
     assert rel(yb.cpu().numpy(), S @ xb) < 1e-4
 
 
+@pytest.mark.parametrize("n,N", [(1, 5), (1, 6)])
+def test_fp64_interior_inverse_brings_the_mixed_operator_closer_to_the_oracle(n, N):
+    """N = 5, 6 (n_i = 320, 625): the mixed condensed operator with A_ii^-1 from the FP64
+    Gauss-Jordan rounded to FP32 (interior_fp64 = 1) against the FP32 equilibrated
+    Gauss-Jordan, both against the oracle's dense FP64 S (Sec. 2.2, eq. SC_step1)."""
+    from paper_1911_02366_gb300 import sc
+    rels = {}
+    S = None
+    for f64 in (0, 1):
+        Q, dt, p, ctx = case(n, N, precision=sc.SC_PREC_MIXED, interior_fp64=f64)
+        ctx.sc_set_state(Q, Q)
+        ctx.sc_assemble()
+        ctx.sc_condense()
+        if S is None:
+            S = O.condensed_operator(O.jacobian(p, Q), n, N).dense_S()
+        xb = np.random.default_rng(9).standard_normal(S.shape[0])
+        yb = torch.zeros(S.shape[0], dtype=torch.float64, device="cuda")
+        ctx.sc_condensed_matvec(torch.tensor(xb, device="cuda"), yb)
+        torch.cuda.synchronize()
+        rels[f64] = rel(yb.cpu().numpy(), S @ xb)
+    print(f"\nN = {N}: mixed operator relative error, FP32 inverse {rels[0]:.3g}, FP64 inverse {rels[1]:.3g}")
+    assert rels[1] < 0.5 * rels[0], rels
+
+
 @pytest.mark.parametrize("n,N", [(2, 4), (3, 3)])
 def test_tensor_core_preconditioner_keeps_iteration_count(n, N):
     """The block-Jacobi factors from the TF32 products and blocked LU precondition as well
