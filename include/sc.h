@@ -508,6 +508,26 @@ sc_status sc_profile_elements(const sc_ctx* ctx, long long* elements);
    once); per element, divide by K. */
 sc_status sc_kernel_work(const sc_ctx* ctx, int kernel_id, double* flops, double* bytes);
 
+/* ---- Element partitions of a sharded run (host only; no GPU work, no context) ----
+   Not in the paper.  The condensation is element-local (Sec. 2.2), so a run on several GPUs
+   gives each rank whole elements; one application of the implicit condensed operator then
+   needs two halo exchanges: the boundary values x_b of the face and edge neighbours of the
+   owned elements (before the interior pass) and the interior values u of their face
+   neighbours (before the boundary pass).  This build runs one GPU per process (replicas);
+   these calls give the layout a sharded run would use. */
+
+/* part[e] (K = n^3 ints, caller-owned) = the rank of element e = ex + n (ey + n ez): slabs of
+   whole z-planes, rank r owning planes [r n / nparts, (r + 1) n / nparts).  SC_ERR_ARG unless
+   1 <= nparts <= n <= 32. */
+sc_status sc_partition_slabs(int n, int nparts, int* part);
+
+/* For rank `rank` of the partition part[K]: counts[0..2] = the numbers of owned elements,
+   of elements whose boundary values the owned rows need (halo_b: face and edge neighbours
+   not owned) and of elements whose interior values they need (halo_u: face neighbours not
+   owned); owned, halo_b, halo_u (each K ints, caller-owned) receive those element indices in
+   ascending order.  SC_ERR_ARG for null pointers or a bad n. */
+sc_status sc_partition_halo(int n, const int* part, int rank, int* counts, int* owned, int* halo_b, int* halo_u);
+
 #ifdef __cplusplus
 }
 #endif

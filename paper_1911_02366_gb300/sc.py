@@ -60,7 +60,7 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_batch_condense", "sc_batch_tiles", "sc_batch_destroy", "sc_spectrum_estimate",
            "sc_hessenberg_eigvals", "sc_steady_residual", "sc_explicit_march", "sc_implicit_march",
            "sc_precond_apply", "sc_profile_elements", "sc_mlp_bf16", "sc_mlp_train", "sc_mlp_save", "sc_mlp_load", "sc_load_mlp",
-           "sc_direct_factor", "sc_direct_solve"]
+           "sc_direct_factor", "sc_direct_solve", "sc_partition_slabs", "sc_partition_halo"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -131,6 +131,8 @@ def lib(build_if_missing: bool = True):
     L.sc_load_mlp.argtypes = [vp, ctypes.c_char_p]
     L.sc_direct_factor.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.sc_direct_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(sc_solve_stats)]
+    L.sc_partition_slabs.argtypes = [ctypes.c_int, ctypes.c_int, vp]
+    L.sc_partition_halo.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp]
     L.sc_explicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp]
     L.sc_implicit_march.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     dp, dp, dp, ctypes.POINTER(ctypes.c_int)]
@@ -407,6 +409,29 @@ def sc_hessenberg_eigvals(H: np.ndarray) -> np.ndarray:
     if s != SC_OK:
         raise SCError(s, "Hessenberg QR failed")
     return re + 1j * im
+
+
+def sc_partition_slabs(n: int, nparts: int) -> np.ndarray:
+    """Rank of every element of the n^3 mesh: slabs of whole z-planes (host only)."""
+    part = np.zeros(n ** 3, dtype=np.int32)
+    s = lib().sc_partition_slabs(n, nparts, part.ctypes.data)
+    if s != SC_OK:
+        raise SCError(s, "partition: need 1 <= nparts <= n <= 32")
+    return part
+
+
+def sc_partition_halo(n: int, part: np.ndarray, rank: int):
+    """(owned, halo_b, halo_u) element indices of one rank (host only): the owned elements,
+    the elements whose boundary values and whose interior values the owned rows need."""
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    K = n ** 3
+    counts = np.zeros(3, dtype=np.int32)
+    owned, hb, hu = (np.zeros(K, dtype=np.int32) for _ in range(3))
+    s = lib().sc_partition_halo(n, part.ctypes.data, rank, counts.ctypes.data, owned.ctypes.data, hb.ctypes.data,
+                                hu.ctypes.data)
+    if s != SC_OK:
+        raise SCError(s, "partition halo: bad arguments")
+    return owned[:counts[0]].copy(), hb[:counts[1]].copy(), hu[:counts[2]].copy()
 
 
 def sc_gemm_tf32(A, B, C, alpha=1.0, beta=0.0, stream=None, trans_a=False, trans_b=False):
