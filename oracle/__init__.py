@@ -50,7 +50,7 @@ class _Params(ctypes.Structure):
         ("Re", ctypes.c_double), ("Ma", ctypes.c_double), ("Ts", ctypes.c_double),
         ("sutherland", ctypes.c_int), ("model", ctypes.c_int), ("viscous", ctypes.c_int),
         ("adv", ctypes.c_double * 3), ("nu", ctypes.c_double), ("roe_delta", ctypes.c_double),
-        ("with_time", ctypes.c_int),
+        ("with_time", ctypes.c_int), ("adv_flux", ctypes.c_int),
     ]
 
 
@@ -74,6 +74,7 @@ class Params:
     nu: float = 0.0
     roe_delta: float = 0.05
     with_time: bool = True
+    adv_flux: int = 0       # 0 Roe (entropy fix), 1 local Lax-Friedrichs
 
     @property
     def K(self) -> int:
@@ -94,6 +95,7 @@ class Params:
         p.sutherland, p.model, p.viscous = int(self.sutherland), self.model, int(self.viscous)
         p.adv = (ctypes.c_double * 3)(*self.adv)
         p.nu, p.roe_delta, p.with_time = self.nu, self.roe_delta, int(self.with_time)
+        p.adv_flux = int(self.adv_flux)
         return p
 
 

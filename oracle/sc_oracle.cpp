@@ -27,7 +27,10 @@
 //   * Sutherland mu = (1+S)/(T+S) T^(3/2), S = T_suth / T_inf (App. B);
 //   * Roe flux with Roe averages and Harten's entropy fix on every wave,
 //     |lambda| -> (lambda^2 + delta^2)/(2 delta) for |lambda| < delta,
-//     delta = roe_delta * c_roe (the paper names Roe without details).
+//     delta = roe_delta * c_roe (the paper names Roe without details);
+//   * or (adv_flux = 1) the Lax-Friedrichs flux of the paper's experiment (Sec. 4), read as
+//     the local one: fhat = (f(q+) + f(q-)) . n / 2 - lambda (q- - q+) / 2 with
+//     lambda = max over the two states of |u . n| + c.
 
 #include <cmath>
 #include <cstdint>
@@ -98,6 +101,7 @@ struct or_params {
   double nu;        // diffusivity of model 1
   double roe_delta; // entropy-fix width as a fraction of the Roe sound speed
   int with_time;    // 0 drops the time term (spatial operator H only)
+  int adv_flux;     // 0: Roe with entropy fix; 1: local Lax-Friedrichs (the paper's experiment, Sec. 4)
 };
 }
 
@@ -276,6 +280,16 @@ void num_flux_adv(const or_params& P, const T* qL, const T* qR, int d, int s, T*
   T uR[3] = {qR[1] / rR, qR[2] / rR, qR[3] / rR};
   T pL = (g - 1.0) * (qL[4] - 0.5 * rL * (uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2]));
   T pR = (g - 1.0) * (qR[4] - 0.5 * rR * (uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2]));
+  if (P.adv_flux == 1) {
+    // local Lax-Friedrichs: the central flux minus half the larger of the two states' fastest
+    // wave speeds |u.n| + c times the jump
+    T sL = sqrt(g * pL / rL), sR = sqrt(g * pR / rR);
+    T wL = (val(uL[d]) >= 0 ? uL[d] : -uL[d]) + sL;
+    T wR = (val(uR[d]) >= 0 ? uR[d] : -uR[d]) + sR;
+    T lam = val(wL) >= val(wR) ? wL : wR;
+    for (int k = 0; k < NV; ++k) fh[k] = 0.5 * (double)s * (fL[k] + fR[k]) - 0.5 * lam * (qR[k] - qL[k]);
+    return;
+  }
   T HL = (qL[4] + pL) / rL, HR = (qR[4] + pR) / rR;
   T sL = sqrt(rL), sR = sqrt(rR);
   T den = sL + sR;

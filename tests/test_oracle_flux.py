@@ -65,3 +65,46 @@ def test_roe_dissipation_sign():
     qR = cons(1.0, 0, 0, 0, 70.0)
     f = O.num_flux(P, qL, qR, 0, +1)
     assert f[0] > 0
+
+
+PLF = O.Params(n=1, N=1, adv_flux=1)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_lax_friedrichs_consistency_and_conservation(d):
+    # equal states give the physical flux; swapping the sides and the normal negates the flux
+    q = cons(1.1, 0.3, -0.2, 0.4, 50.0)
+    for s in (-1, 1):
+        fa, _ = O.phys_flux(PLF, q, np.zeros(15), d)
+        np.testing.assert_allclose(O.num_flux(PLF, q, q, d, s), s * fa, rtol=1e-14, atol=1e-12)
+    qL, qR = cons(1.0, 0.2, 0.1, -0.3, 40.0), cons(1.2, -0.1, 0.4, 0.2, 45.0)
+    for s in (-1, 1):
+        np.testing.assert_allclose(O.num_flux(PLF, qL, qR, d, s), -O.num_flux(PLF, qR, qL, d, -s),
+                                   rtol=1e-14, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_lax_friedrichs_contact_at_rest(d):
+    # fluid at rest, equal pressure, a density jump: the central part carries only the
+    # pressure, and the dissipation is the fastest sound speed sqrt(gamma p / rho_min) times
+    # half the jump of the conserved state (energy unchanged: same pressure, no motion)
+    p, rL, rR = 30.0, 1.0, 2.0
+    qL, qR = cons(rL, 0, 0, 0, p), cons(rR, 0, 0, 0, p)
+    lam = np.sqrt(GAMMA * p / rL)
+    fh = O.num_flux(PLF, qL, qR, d, +1)
+    expect = np.zeros(5)
+    expect[1 + d] = p
+    expect[0] = -0.5 * lam * (rR - rL)
+    np.testing.assert_allclose(fh, expect, rtol=1e-13, atol=1e-12)
+
+
+def test_lax_friedrichs_dissipates_more_than_roe_across_a_shear_layer():
+    # a pure shear jump (same rho, p, normal velocity): Roe damps it with |u.n| only, LF with
+    # |u.n| + c, so the LF flux differs from the central flux by more
+    qL, qR = cons(1.0, 0.1, 0.5, 0.0, 40.0), cons(1.0, 0.1, -0.5, 0.0, 40.0)
+    fL, _ = O.phys_flux(P, qL, np.zeros(15), 0)
+    fR, _ = O.phys_flux(P, qR, np.zeros(15), 0)
+    central = 0.5 * (fL + fR)
+    d_roe = np.linalg.norm(O.num_flux(P, qL, qR, 0, 1) - central)
+    d_lf = np.linalg.norm(O.num_flux(PLF, qL, qR, 0, 1) - central)
+    assert d_lf > 5 * d_roe > 0

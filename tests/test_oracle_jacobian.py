@@ -146,3 +146,24 @@ def test_own_block_couples_only_nodes_sharing_a_gl_index(n, N):
         assert not (nz & ~share).any()
         seen |= nz
     assert (seen == share).all()
+
+
+def test_lax_friedrichs_jacobian_matches_central_differences():
+    # |u . n| and the larger of the two wave speeds are not differentiable where u . n = 0
+    # or where the two sides tie: the Taylor-Green velocity vanishes on whole grid planes, so
+    # a mean flow is added (same pressure) to keep the faces away from those kinks
+    n, N = 3, 2
+    Q, dt = I.tgv_state(n, N, eps=1e-2)
+    Q = Q.copy()
+    rho = Q[..., 0]
+    v = Q[..., 1:4] / rho[..., None]
+    U = np.array([0.6, 0.45, 0.35])
+    Q[..., 4] += 0.5 * rho * (np.sum((v + U) ** 2, axis=-1) - np.sum(v ** 2, axis=-1))
+    Q[..., 1:4] += rho[..., None] * U
+    p = O.Params(n=n, N=N, dt=dt, adv_flux=1)
+    A = O.jacobian(p, Q)
+    x = np.random.default_rng(3).standard_normal(Q.shape)
+    y = (A @ x.reshape(-1)).reshape(Q.shape)
+    h = 1e-5
+    fd = (O.residual(p, Q + h * x, Q) - O.residual(p, Q - h * x, Q)) / (2 * h)
+    assert np.abs(y - fd).max() / np.abs(y).max() < 1e-8

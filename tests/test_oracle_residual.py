@@ -165,3 +165,17 @@ def test_euler_smooth_state():
 
     errs = _errors(st, div, [3, 5, 7, 9], viscous=False)
     assert errs[-1] < 1e-4 and all(errs[i + 1] < 0.1 * errs[i] for i in range(3)), errs
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_lax_friedrichs_free_stream_and_conservation(N):
+    Q = I.uniform_state(3, N, vel=(1.0, 0.3, -0.2))
+    R = O.residual(O.Params(n=3, N=N, with_time=False, adv_flux=1), Q)
+    assert np.abs(R).max() < 1e-11 * np.abs(Q).max()
+    Q, dt = I.tgv_state(3, N, eps=1e-2)
+    R = O.residual(O.Params(n=3, N=N, dt=dt, with_time=False, adv_flux=1), Q)
+    tot = R.reshape(-1, 5).sum(0)
+    assert np.all(np.abs(tot) < 1e-12 * np.abs(R).max() * R.shape[0] ** 0.5)
+    # and the residual is not Roe's
+    R_roe = O.residual(O.Params(n=3, N=N, dt=dt, with_time=False), Q)
+    assert np.abs(R - R_roe).max() > 1e-6 * np.abs(R).max()
