@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 
 import sc_inputs as I  # noqa: E402
 
-WORKLOAD = dict(name="tgv_16x16x16_N4_cfl50", n=16, N=4, Ma=0.1, Re=1600.0, cfl=50.0, seed=0)
+WORKLOAD = dict(name="tgv_16x16x16_N4_cfl50", n=16, N=4, Ma=0.1, Re=1600.0, cfl=50.0, seed=0, adv_flux=0)
 METRIC = "linear-solve DOF/s at rel. residual 1e-8: condensed GPU forms vs plain FP64"
 REL_TOL = 1e-8
 # Peaks: HBM and bf16 from MEASURED_PEAKS.json; FP64 and FP32 FMA rates derived from
@@ -134,6 +134,7 @@ def train_correction(args, stream, cfl=None):
     for i, Ma in enumerate(mach):
         Q, dt = I.tgv_state(n, N, Ma=Ma, seed=100 + i, cfl=cfl)
         c = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Ma=Ma, Re=WORKLOAD["Re"],
+                       adv_flux=WORKLOAD["adv_flux"],
                        precond=sc.SC_PC_RED_BLACK)
         c.sc_set_mesh(n, 2 * math.pi, N)
         c.sc_set_timestep(dt, 1)
@@ -184,7 +185,7 @@ def run_ours(args, world, rank, local):
         extra = dict(precond=sc.SC_PC_RED_BLACK)
     elif args.precond == "rbs":
         extra = dict(precond=sc.SC_PC_RB_SCHUR if precision == sc.SC_PREC_MIXED else sc.SC_PC_RED_BLACK)
-    ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"],
+    ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"], adv_flux=W["adv_flux"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
                      outer_krylov=args.outer_krylov if args.arm != "fp64" else 0, inner_iters=args.inner_iters,
@@ -326,6 +327,7 @@ def fp64_reference_arm(args, W, Q, dt, stream, dQ_mixed):
     import torch
     from paper_1911_02366_gb300 import sc
     ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_FP64, Re=W["Re"], Ma=W["Ma"],
+                     adv_flux=W["adv_flux"],
                      gmres_restart=30, gmres_max_iters=args.max_iters, rel_tol=REL_TOL)
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
     ctx.sc_set_timestep(dt, 1)
@@ -382,7 +384,7 @@ def run_oracle(steps: int):
     import oracle as O
     n_s, L, Q, dt = cpu_sample()
     W = WORKLOAD
-    p = O.Params(n=n_s, N=W["N"], dt=dt, L=L, Re=W["Re"], Ma=W["Ma"])
+    p = O.Params(n=n_s, N=W["N"], dt=dt, L=L, Re=W["Re"], Ma=W["Ma"], adv_flux=W["adv_flux"])
     A = O.jacobian(p, Q)
     B = -O.residual(p, Q).reshape(-1)
     times, iters = [], []
@@ -416,6 +418,7 @@ def run_batched(args, world, rank, local):
     for n, N in BATCH_ORDERS:
         Q, dt = I.tgv_state(n, N, Ma=W["Ma"], seed=W["seed"], cfl=BATCH_CFL)
         c = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
+                       adv_flux=W["adv_flux"],
                        gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                        inner_tol=args.inner_tol, max_refine=20)
         c.sc_set_mesh(n, 2 * math.pi, N)
@@ -552,6 +555,7 @@ def run_timesteps(args, world, rank, local):
           "learned": sc.SC_PC_LEARNED}[args.ts_precond]
     net, train_info = (train_correction(args, stream, cfl=args.cfl) if pc == sc.SC_PC_LEARNED else (None, None))
     ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
+                     adv_flux=W["adv_flux"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
                      outer_krylov=args.outer_krylov, inner_iters=args.inner_iters, precond=pc,
@@ -798,6 +802,8 @@ def main():
                     help="the kernel whose launches the roofline object times (the step's largest share)")
     ap.add_argument("--interior-fp64", type=int, choices=[0, 1], default=0,
                     help="mixed arms, N >= 5: A_ii^-1 by FP64 Gauss-Jordan, rounded to FP32 for the operator")
+    ap.add_argument("--adv-flux", choices=["roe", "lf"], default="roe",
+                    help="advective numerical flux: Roe (default) or local Lax-Friedrichs (the paper's experiment)")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
@@ -813,6 +819,8 @@ def main():
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 arm beside the mixed line")
     args = ap.parse_args()
     world, rank, local = dist_setup()
+    if args.adv_flux == "lf":
+        WORKLOAD.update(adv_flux=1, name=WORKLOAD["name"] + "_lf")
     if args.n or args.order:
         n = args.n or WORKLOAD["n"]; N = args.order or WORKLOAD["N"]
         WORKLOAD.update(n=n, N=N, name=f"tgv_{n}x{n}x{n}_N{N}_cfl{int(WORKLOAD['cfl'])}")

@@ -48,6 +48,7 @@ typedef enum {
 } sc_status;
 
 enum { SC_PREC_FP64 = 0, SC_PREC_MIXED = 1 };
+enum { SC_FLUX_ROE = 0, SC_FLUX_LF = 1 };
 /* Preconditioners of the condensed GMRES (the paper uses point Jacobi, Sec. 4):
    SC_PC_BLOCK_JACOBI: z_e = S_ee^-1 v_e per element.
    SC_PC_RED_BLACK: one forward block Gauss-Seidel sweep over the checkerboard colouring of
@@ -117,6 +118,10 @@ typedef struct {
                             on the FP64 own blocks, rounded to FP32 for the operator (FP32 rounding
                             instead of the ~3e-5 of the FP32 inverse at N = 6; costs the FP64 pipe
                             and n_i^2 doubles per element); 0 = FP32 Gauss-Jordan (default) */
+  int adv_flux;          /* advective numerical flux: SC_FLUX_ROE (Roe with Harten's entropy fix,
+                            width roe_delta; default) or SC_FLUX_LF (local Lax-Friedrichs, the
+                            paper's experiment, Sec. 4: central flux minus half the larger
+                            |u . n| + c of the two states times the jump) */
 } sc_config;
 
 /* Per-solve statistics filled by sc_solve. */

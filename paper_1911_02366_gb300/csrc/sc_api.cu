@@ -217,6 +217,7 @@ sc_status sc_create(const sc_config* cfg, void* cuda_stream, sc_ctx** out) {
   if (cfg->precision != SC_PREC_FP64 && cfg->precision != SC_PREC_MIXED) return SC_ERR_ARG;
   if (cfg->precond < SC_PC_BLOCK_JACOBI || cfg->precond > SC_PC_RB_SCHUR) return SC_ERR_ARG;
   if (cfg->interior_fp64 != 0 && cfg->interior_fp64 != 1) return SC_ERR_ARG;
+  if (cfg->adv_flux != SC_FLUX_ROE && cfg->adv_flux != SC_FLUX_LF) return SC_ERR_ARG;
   if (cfg->outer_krylov < 0 || cfg->outer_krylov > cfg->gmres_restart || cfg->inner_iters < 0) return SC_ERR_ARG;
   sc_ctx* c = new sc_ctx();
   c->cfg = *cfg;
@@ -270,7 +271,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   diff_matrix(c->xi, G.D);
   G.inv_hw = 1.0 / (G.h * w[N]);
   G.gamma = c->cfg.gamma; G.Pr = c->cfg.Pr; G.Re = c->cfg.Re; G.Ma = c->cfg.Ma; G.Ts = c->cfg.Ts;
-  G.roe_delta = c->cfg.roe_delta; G.sutherland = c->cfg.sutherland;
+  G.roe_delta = c->cfg.roe_delta; G.sutherland = c->cfg.sutherland; G.adv_flux = c->cfg.adv_flux;
   G.dt = 1.0; G.c0 = 1.0;
   // node permutation: interior nodes first, then boundary nodes, each in natural order
   const int p = G.p;

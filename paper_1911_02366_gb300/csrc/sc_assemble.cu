@@ -125,7 +125,7 @@ __global__ void k_resid(Geo G, const double* __restrict__ Q, const double* __res
     load_node(Q, grad, t, qa, ga);
     load_node(Q, grad, tn, qb, gb);
     double fr[5], fva[5], fvb[5];
-    flux_roe(G, qa, qb, d, s, fr);
+    flux_adv(G, qa, qb, d, s, fr);
     flux_viscous(G, qa, ga, d, fva);
     flux_viscous(G, qb, gb, d, fvb);
     const double Sf = G.Jf * Wj / G.w[c[d]];
@@ -182,7 +182,7 @@ __global__ void k_nodejac(Geo G, const double* __restrict__ Q, const double* __r
   if (t < G.K * G.nn) nodejac_body(G, Q, grad, t, NJ);
 }
 
-// Roe flux derivatives at every face node of every element: RJ[e][f][comp][fidx],
+// Numerical-flux (Roe or Lax-Friedrichs) derivatives at every face node of every element: RJ[e][f][comp][fidx],
 // comp < 25: d fhat/d q+, comp >= 25: d fhat/d q-; fidx = a + p*b over the in-face
 // coordinates ((d+1)%3, (d+2)%3).
 SC_HD void roejac_body(const Geo& G, const double* Q, const int* nbr, int t, double* RJ) {
@@ -200,7 +200,7 @@ SC_HD void roejac_body(const Geo& G, const double* Q, const int* nbr, int t, dou
     D5 a[5], b[5], fh[5];
     for (int k = 0; k < 5; ++k) { a[k] = D5(qa[k]); b[k] = D5(qb[k]); }
     for (int k = 0; k < 5; ++k) (side == 0 ? a : b)[k].d[k] = 1.0;
-    flux_roe(G, a, b, d, s, fh);
+    flux_adv(G, a, b, d, s, fh);
     for (int k = 0; k < 5; ++k)
       for (int l = 0; l < 5; ++l) out[(size_t)(side * 25 + k * 5 + l) * pp] = fh[k].d[l];
   }

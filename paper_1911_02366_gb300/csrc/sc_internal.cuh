@@ -25,6 +25,7 @@ struct Geo {
   double h, Jf, dx, inv_hw;  // element size, (h/2)^2, 2/h, 1/(h w_N)
   double dt, c0;          // time step, BDF leading coefficient (1 or 3/2)
   double gamma, Pr, Re, Ma, Ts, roe_delta;
+  int adv_flux;  // 0 Roe, 1 local Lax-Friedrichs
   int sutherland;
   double D[SC_MAXP][SC_MAXP];  // D[a][b] = l_b'(xi_a)
   double w[SC_MAXP];           // Gauss-Lobatto weights
@@ -228,6 +229,34 @@ SC_HD inline void flux_roe(const Geo& G, const T qa[5], const T qb[5], int d, in
   diss[1 + d] = diss[1 + d] + (ap - am) * cm * sd;
   diss[4] = (am + ap) * Hm + (ap - am) * cm * un + a0 * (0.5 * we * vsq + rhom * umjt);
   for (int k = 0; k < 5; ++k) fh[k] = 0.5 * sd * (fa[k] + fb[k]) - 0.5 * diss[k];
+}
+
+// Local Lax-Friedrichs flux (the paper's experiment, Sec. 4): the central flux minus half the
+// larger of the two states' fastest wave speeds |u . e_d| + c times the jump, n = s e_d.
+template <class T>
+SC_HD inline void flux_lf(const Geo& G, const T qa[5], const T qb[5], int d, int s, T fh[5]) {
+  const double gm1 = G.gamma - 1.0;
+  T fa[5], fb[5];
+  flux_inviscid(G, qa, d, fa);
+  flux_inviscid(G, qb, d, fb);
+  const T ira = recip(qa[0]), irb = recip(qb[0]);
+  const T uad = qa[1 + d] * ira, ubd = qb[1 + d] * irb;
+  const T pa = gm1 * (qa[4] - 0.5 * (qa[1] * qa[1] + qa[2] * qa[2] + qa[3] * qa[3]) * ira);
+  const T pb = gm1 * (qb[4] - 0.5 * (qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]) * irb);
+  const T wa = (vval(uad) >= 0.0 ? uad : -uad) + dsqrt(G.gamma * pa * ira);
+  const T wb = (vval(ubd) >= 0.0 ? ubd : -ubd) + dsqrt(G.gamma * pb * irb);
+  const T lam = vval(wa) >= vval(wb) ? wa : wb;
+  const double sd = (double)s;
+  for (int k = 0; k < 5; ++k) fh[k] = 0.5 * sd * (fa[k] + fb[k]) - 0.5 * lam * (qb[k] - qa[k]);
+}
+
+// The configured advective numerical flux (Geo::adv_flux: 0 Roe, 1 Lax-Friedrichs).
+template <class T>
+SC_HD inline void flux_adv(const Geo& G, const T qa[5], const T qb[5], int d, int s, T fh[5]) {
+  if (G.adv_flux == 1)
+    flux_lf(G, qa, qb, d, s, fh);
+  else
+    flux_roe(G, qa, qb, d, s, fh);
 }
 
 // ------------------------------------------------------------------ host context

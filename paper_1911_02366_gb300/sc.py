@@ -17,6 +17,7 @@ SC_OK, SC_ERR_ARG, SC_ERR_CUDA, SC_ERR_OOM, SC_ERR_STATE = 0, 1, 2, 3, 4
 SC_ERR_SINGULAR_BLOCK, SC_ERR_NONFINITE, SC_ERR_NOT_CONVERGED = 5, 6, 7
 SC_PREC_FP64, SC_PREC_MIXED = 0, 1
 SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED, SC_PC_RED_BLACK, SC_PC_RB_SCHUR = 0, 1, 2, 3, 4
+SC_FLUX_ROE, SC_FLUX_LF = 0, 1
 SC_DIRECT_GLOBAL, SC_DIRECT_CONDENSED = 0, 1
 
 _lib = None
@@ -36,7 +37,8 @@ class sc_config(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("rel_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("tensor_cores", ctypes.c_int), ("learned_min_reduction", ctypes.c_double),
                 ("factor_fp16", ctypes.c_int), ("explicit_schur", ctypes.c_int),
-                ("outer_krylov", ctypes.c_int), ("inner_iters", ctypes.c_int), ("interior_fp64", ctypes.c_int)]
+                ("outer_krylov", ctypes.c_int), ("inner_iters", ctypes.c_int), ("interior_fp64", ctypes.c_int),
+                ("adv_flux", ctypes.c_int)]
 
 
 class sc_solve_stats(ctypes.Structure):

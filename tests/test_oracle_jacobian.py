@@ -167,3 +167,21 @@ def test_lax_friedrichs_jacobian_matches_central_differences():
     h = 1e-5
     fd = (O.residual(p, Q + h * x, Q) - O.residual(p, Q - h * x, Q)) / (2 * h)
     assert np.abs(y - fd).max() / np.abs(y).max() < 1e-8
+
+
+def test_lax_friedrichs_keeps_the_jacobian_pattern_and_the_exact_condensation():
+    # the flux pair only changes values: the same face-node couplings, so the same pattern,
+    # and the condensed solve still equals the global one
+    n, N = 2, 2
+    Q, dt = I.tgv_state(n, N, eps=1e-2)
+    A_roe = O.jacobian(O.Params(n=n, N=N, dt=dt), Q).tocsr()
+    p = O.Params(n=n, N=N, dt=dt, adv_flux=1)
+    A_lf = O.jacobian(p, Q).tocsr()
+    # node-pair (5 x 5 block) pattern: the scalar lambda of Lax-Friedrichs fills entries inside
+    # blocks where Roe's dissipation has zeros, but couples no new pair of nodes
+    pat = lambda A: set(zip(*(i // 5 for i in A.nonzero())))
+    assert pat(A_lf) == pat(A_roe)
+    B = -O.residual(p, Q).reshape(-1)
+    x = O.global_solve(A_lf, B)
+    xc, _ = O.condensed_solve(A_lf, B, n, N, method="direct")
+    assert np.linalg.norm(xc - x) <= 1e-10 * np.linalg.norm(x)
