@@ -279,16 +279,34 @@ __global__ void k_scatter(Geo G, const int* __restrict__ iperm, const double* __
 
 // Partial dot products <V[i], w> over a slice of the vectors: grid (chunks, nvec);
 // partial[i * gridDim.x + chunk].
+// Partial dot products w . v_i over the chunk of block x, one vector per block row y.  With
+// vec2 (n even, both pointers 16-byte aligned) the loads are double2, two chains per thread.
 __global__ void __launch_bounds__(256) k_multidot_partial(const double* __restrict__ V, size_t n,
                                                           const double* __restrict__ w,
-                                                          double* __restrict__ partial) {
+                                                          double* __restrict__ partial, int vec2) {
   __shared__ double red[8];
   const int i = blockIdx.y;
   const double* v = V + (size_t)i * n;
-  double s = 0.0;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    s = fma(v[t], w[t], s);
-  s = warp_sum(s);
+  double s = 0.0, s2 = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if (vec2) {
+    const double2* v2 = reinterpret_cast<const double2*>(v);
+    const double2* w2 = reinterpret_cast<const double2*>(w);
+    const size_t n2 = n / 2;
+    size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (; t + stride < n2; t += 2 * stride) {
+      const double2 a = __ldg(v2 + t), b = __ldg(w2 + t), c = __ldg(v2 + t + stride), d = __ldg(w2 + t + stride);
+      s = fma(a.x, b.x, s); s2 = fma(a.y, b.y, s2);
+      s = fma(c.x, d.x, s); s2 = fma(c.y, d.y, s2);
+    }
+    if (t < n2) {
+      const double2 a = __ldg(v2 + t), b = __ldg(w2 + t);
+      s = fma(a.x, b.x, s); s2 = fma(a.y, b.y, s2);
+    }
+  } else {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += stride) s = fma(v[t], w[t], s);
+  }
+  s = warp_sum(s + s2);
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -314,9 +332,43 @@ __global__ void k_multidot_final(const double* __restrict__ partial, int nchunks
   }
 }
 
-__global__ void k_vec_update(double* __restrict__ w, const double* __restrict__ V, int nvec, size_t n,
-                             const double* __restrict__ coef, double sign) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+// w -= or += sum_i coef[i] v_i (sign); with vec2 (n even, pointers 16-byte aligned) double2
+// accesses and the vectors taken four at a time into independent accumulators.
+__global__ void __launch_bounds__(256) k_vec_update(double* __restrict__ w, const double* __restrict__ V, int nvec,
+                                                    size_t n, const double* __restrict__ coef, double sign,
+                                                    int vec2) {
+  __shared__ double cs[64];
+  for (int i = threadIdx.x; i < nvec && i < 64; i += blockDim.x) cs[i] = coef[i];
+  __syncthreads();
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if (vec2 && nvec <= 64) {
+    const size_t n2 = n / 2;
+    double2* w2 = reinterpret_cast<double2*>(w);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n2; t += stride) {
+      double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
+      int i = 0;
+      for (; i + 4 <= nvec; i += 4) {
+        const double2 v0 = __ldg(reinterpret_cast<const double2*>(V + (size_t)i * n) + t);
+        const double2 v1 = __ldg(reinterpret_cast<const double2*>(V + (size_t)(i + 1) * n) + t);
+        const double2 v2 = __ldg(reinterpret_cast<const double2*>(V + (size_t)(i + 2) * n) + t);
+        const double2 v3 = __ldg(reinterpret_cast<const double2*>(V + (size_t)(i + 3) * n) + t);
+        a0.x = fma(cs[i], v0.x, a0.x); a0.y = fma(cs[i], v0.y, a0.y);
+        a1.x = fma(cs[i + 1], v1.x, a1.x); a1.y = fma(cs[i + 1], v1.y, a1.y);
+        a2.x = fma(cs[i + 2], v2.x, a2.x); a2.y = fma(cs[i + 2], v2.y, a2.y);
+        a3.x = fma(cs[i + 3], v3.x, a3.x); a3.y = fma(cs[i + 3], v3.y, a3.y);
+      }
+      for (; i < nvec; ++i) {
+        const double2 v0 = __ldg(reinterpret_cast<const double2*>(V + (size_t)i * n) + t);
+        a0.x = fma(cs[i], v0.x, a0.x); a0.y = fma(cs[i], v0.y, a0.y);
+      }
+      double2 o = w2[t];
+      o.x = fma(sign, (a0.x + a1.x) + (a2.x + a3.x), o.x);
+      o.y = fma(sign, (a0.y + a1.y) + (a2.y + a3.y), o.y);
+      w2[t] = o;
+    }
+    return;
+  }
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += stride) {
     double s = 0.0;
     for (int i = 0; i < nvec; ++i) s = fma(coef[i], V[(size_t)i * n + t], s);
     w[t] = fma(sign, s, w[t]);
@@ -461,7 +513,8 @@ cudaError_t multidot(sc_ctx* c, const double* V, int nvec, size_t n, const doubl
   if (nvec < 1 || nvec > c->restart_alloc + 1) return cudaErrorInvalidValue;
   const int chunks = kDotChunks;
   count_launch(c, 2);
-  k_multidot_partial<<<dim3(chunks, nvec), 256, 0, c->stream>>>(V, n, w, c->partial);
+  const int vec2 = n % 2 == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  k_multidot_partial<<<dim3(chunks, nvec), 256, 0, c->stream>>>(V, n, w, c->partial, vec2);
   k_multidot_final<<<nvec, 256, 0, c->stream>>>(c->partial, chunks, nvec, out_dev);
   return cudaGetLastError();
 }
@@ -469,7 +522,8 @@ cudaError_t multidot(sc_ctx* c, const double* V, int nvec, size_t n, const doubl
 cudaError_t vec_update(sc_ctx* c, double* w, const double* V, int nvec, size_t n, const double* coef_dev,
                        double sign) {
   count_launch(c);
-  k_vec_update<<<kDotBlocks, 256, 0, c->stream>>>(w, V, nvec, n, coef_dev, sign);
+  const int vec2 = n % 2 == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  k_vec_update<<<kDotBlocks, 256, 0, c->stream>>>(w, V, nvec, n, coef_dev, sign, vec2);
   return cudaGetLastError();
 }
 
