@@ -394,7 +394,9 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   }
   if (c->cfg.precond == SC_PC_LEARNED || c->cfg.precond == SC_PC_RB_SCHUR) {
     const size_t nbk = (size_t)c->n_black;
-    A(dalloc(&c->SeeB, nbk * G.nb * G.lds)); A(dalloc(&c->SeeL, nbk * G.nb * G.lds));
+    // SeeL also stages the red blocks for their factorisation (SC_PC_RB_SCHUR; n_red = n_black + 1 for odd K)
+    A(dalloc(&c->SeeB, nbk * G.nb * G.lds));
+    A(dalloc(&c->SeeL, (size_t)std::max(c->n_red, c->n_black) * G.nb * G.lds));
     A(dalloc(&c->SlsL, nbk * (size_t)sc::solve_layout_stride(G)));
     A(dalloc(&c->pivL, nbk * G.nb)); A(dalloc(&c->rowpermL, nbk * G.nb));
   }
@@ -526,15 +528,29 @@ sc_status sc_condense(sc_ctx* c) {
   SC_CUDA(cudaMemcpyAsync(&bad_black, c->d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   sc_status s = check(c);
   if (s != SC_OK) return s;
-  if (bad_black >= 0) c->blackL_valid = false;  // a corrected black block is singular: plain sweep
   if (bad == SC_TC_TIMEOUT) return fail(c, SC_ERR_CUDA, "tensor-core wait timed out in the condensation");
   if (bad == SC_EXPLICIT_PATTERN)
     return fail(c, SC_ERR_STATE, "an interior row couples outside the extended boundary set");
   if (bad == SC_PACK_VIOLATION)
     return fail(c, SC_ERR_STATE, "own-block entry outside the packed node pattern is nonzero");
-  if (bad >= 0) return fail(c, SC_ERR_SINGULAR_BLOCK, "singular element block in element " + std::to_string(bad));
+  if (bad >= 0) {  // with compact red factors the index is the red list's
+    const int el = c->red_compact && bad < (int)c->colour_list.size() ? c->colour_list[bad] : bad;
+    return fail(c, SC_ERR_SINGULAR_BLOCK, "singular element block in element " + std::to_string(el));
+  }
+  if (bad_black >= 0) {  // a corrected black block is singular: the plain sweep
+    c->blackL_valid = false;
+    if (c->red_compact) {  // its black factors too come from SlsL (the red ones are compact)
+      SC_CUDA(cudaMemsetAsync(c->d_status + 2, 0xff, sizeof(int), c->stream));
+      SC_CUDA(sc::plain_black_factor(c));
+      SC_CUDA(cudaMemcpyAsync(&bad_black, c->d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      s = check(c);
+      if (s != SC_OK) return s;
+      if (bad_black >= 0) return fail(c, SC_ERR_SINGULAR_BLOCK, "singular black element block");
+      c->blackL_valid = true;
+    }
+  }
   // FP16 factors for the block-Jacobi solve only when every entry fits the FP16 range
-  c->ls16_ok = c->Sls16 != nullptr && ovf == 0 && c->cfg.precond != SC_PC_NONE;
+  c->ls16_ok = c->Sls16 != nullptr && ovf == 0 && c->cfg.precond != SC_PC_NONE && !c->red_compact;
   c->condensed = true;
   return SC_OK;
 }

@@ -1624,9 +1624,18 @@ cudaError_t condense_t(sc_ctx* c, T* Aown, T* Ainv, T* Y, T* See, bool tc, bool 
     err = gather_black_see(c, See);  // uncorrected black blocks for the learned correction
     if (err != cudaSuccess) return err;
   }
+  c->red_compact = false;
   if (c->cfg.precond != SC_PC_NONE) {
     bool done = false;
     if constexpr (std::is_same<T, float>::value) {
+      if (tc && c->cfg.precond == SC_PC_RB_SCHUR && c->SeeL) {
+        // the Schur-corrected sweep factorises only the red blocks here; the black ones are
+        // factorised once, after their correction
+        err = red_factor32(c, See);
+        if (err != cudaSuccess) return err;
+        c->red_compact = true;
+        return cudaGetLastError();
+      }
       if (tc) {
         err = lu_blocked_tf32(c, See);
         if (err != cudaSuccess) return err;
@@ -2027,21 +2036,24 @@ __device__ __forceinline__ void ls_solve_warp_multi(int n, int nblk, const float
 
 namespace {
 
-constexpr int kInvCols = 8;  // right-hand sides per warp in k_inv_columns
+constexpr int kInvCols = 4;   // right-hand sides per warp in k_inv_columns
+constexpr int kInvWarps = 4;  // warps per CTA
 
-// Explicit inverses of the element blocks listed: warp w solves S_ee X = I[:, c0 .. c0 + 7]
-// for element list[w / ngrp], c0 = 8 (w % ngrp), with the condensation's factors, and writes
+// Explicit inverses of the element blocks listed: warp w solves S_ee X = I[:, c0 .. c0 + R - 1]
+// (R = kInvCols) for element list[w / ngrp], c0 = R (w % ngrp), with the condensation's factors, and writes
 // the columns contiguously: out[(i n + c) n + r] = (S_ee^-1)[r][c], i the list index.
-__global__ void __launch_bounds__(128) k_inv_columns(int n, int nblk, const float* __restrict__ LS, long long lsstride,
-                                                     int npad, const int* __restrict__ rowperm,
-                                                     const int* __restrict__ list, int nlist, float* __restrict__ out) {
+__global__ void __launch_bounds__(32 * kInvWarps) k_inv_columns(int n, int nblk, const float* __restrict__ LS,
+                                                               long long lsstride, int npad,
+                                                               const int* __restrict__ rowperm,
+                                                               const int* __restrict__ list, int nlist,
+                                                               float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
   const int ngrp = (n + kInvCols - 1) / kInvCols;
-  const long long w = (long long)blockIdx.x * 4 + warp;
+  const long long w = (long long)blockIdx.x * kInvWarps + warp;
   if (w >= (long long)nlist * ngrp) return;
   const int li = (int)(w / ngrp), c0 = (int)(w % ngrp) * kInvCols;
-  const int e = __ldg(list + li);
+  const int e = list ? __ldg(list + li) : li;  // no list: entries in list order (compact factors)
   const int ls = nblk * 32;
   float* s = reinterpret_cast<float*>(smem_raw) + (size_t)warp * kInvCols * ls;
   const int* rp = rowperm + (long long)e * n;
@@ -2067,12 +2079,12 @@ cudaError_t inverse_columns32(sc_ctx* c, const int* list, int nlist, float* out)
   const Geo& G = c->G;
   if (nlist == 0) return cudaSuccess;
   const int nblk = ls_nblk(G);
-  const size_t smem = (size_t)4 * kInvCols * nblk * 32 * sizeof(float);
+  const size_t smem = (size_t)kInvWarps * kInvCols * nblk * 32 * sizeof(float);
   cudaError_t err = cudaFuncSetAttribute(k_inv_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   count_launch(c);
   const long long nw = (long long)nlist * cdiv(G.nb, kInvCols);
-  k_inv_columns<<<(unsigned)cdiv(nw, 4), 128, smem, c->stream>>>(G.nb, nblk, c->Sls32, ls_stride(G), ls_npad(G),
+  k_inv_columns<<<(unsigned)cdiv(nw, kInvWarps), 32 * kInvWarps, smem, c->stream>>>(G.nb, nblk, c->Sls32, ls_stride(G), ls_npad(G),
                                                                  c->rowperm, list, nlist, out);
   return cudaGetLastError();
 }

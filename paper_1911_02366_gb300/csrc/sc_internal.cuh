@@ -346,6 +346,8 @@ struct sc_ctx {
   float *SeeB = nullptr, *SeeL = nullptr, *SlsL = nullptr;
   int *pivL = nullptr, *rowpermL = nullptr;
   bool blackL_valid = false;  // SlsL holds the factors of the corrected black blocks
+  bool red_compact = false;   // SC_PC_RB_SCHUR: Sls32 / rowperm hold only the red blocks' factors,
+                              // entry i for the i-th red element (the black ones are in SlsL)
   // Schur-corrected sweep (SC_PC_RB_SCHUR): the red blocks' inverses, column-major per red
   // element (Zinv[r][j][i] = (S_rr^-1)[i][j], r the red list index), red index of every
   // element (-1 for black), and per face f the (N+1)^2 boundary nodes on f with the slot of f
@@ -519,6 +521,8 @@ cudaError_t learned_black_factor(sc_ctx* c, const float* Ck, float scale);
 cudaError_t learned_couplings(sc_ctx* c);
 void build_face_tables(sc_ctx* c);
 cudaError_t schur_black_factor(sc_ctx* c);
+cudaError_t red_factor32(sc_ctx* c, const float* See);
+cudaError_t plain_black_factor(sc_ctx* c);
 cudaError_t inverse_columns32(sc_ctx* c, const int* list, int nlist, float* out);
 cudaError_t gather_black_see(sc_ctx* c, const float* See);
 template <class T>

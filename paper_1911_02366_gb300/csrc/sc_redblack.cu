@@ -180,7 +180,8 @@ cudaError_t precond_rb32(sc_ctx* c, const double* v, double* z, float* zf) {
                                              c->cfg.precond == SC_PC_RB_SCHUR);
   const int* black = c->d_colour + c->n_red;
   cudaError_t e = cudaMemsetAsync(zt, 0, n1 * sizeof(float), c->stream);
-  if (e == cudaSuccess) e = lu_solve_list32(c, c->Sls32, c->rowperm, 0, c->d_colour, c->n_red, v, nullptr, z, zt);
+  if (e == cudaSuccess)
+    e = lu_solve_list32(c, c->Sls32, c->rowperm, c->red_compact ? 1 : 0, c->d_colour, c->n_red, v, nullptr, z, zt);
   if (e == cudaSuccess) e = cond_interior_sweep32(c, zt, c->Uf);
   if (e == cudaSuccess) e = cond_boundary_pk_list<float>(c, c->Apk32, c->X32, zt, c->Uf, c->Trb, black, c->n_black);
   if (e == cudaSuccess) {
@@ -242,9 +243,28 @@ cudaError_t schur_black_factor(sc_ctx* c) {
     return cudaSuccess;
   }
   cudaError_t e = learned_couplings(c);
-  if (e == cudaSuccess) e = inverse_columns32(c, c->d_colour, c->n_red, c->Zinv);
+  if (e == cudaSuccess) e = inverse_columns32(c, c->red_compact ? nullptr : c->d_colour, c->n_red, c->Zinv);
   if (e == cudaSuccess) e = black_factor(c, nullptr, 0.f, true);
   return e;
 }
+
+// The red blocks alone (SC_PC_RB_SCHUR): gathered into SeeL (free until the black correction)
+// and factorised into the first n_red entries of the solve layout and of rowperm.
+cudaError_t red_factor32(sc_ctx* c, const float* See) {
+  const Geo& G = c->G;
+  if (c->n_red == 0) return cudaSuccess;
+  count_launch(c);
+  k_gather_blocks<<<dim3(64, c->n_red), 256, 0, c->stream>>>(G.nb, G.lds, See, c->d_colour, c->SeeL);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t per = (size_t)G.nb * G.lds;
+  return factor_batch32(c, c->SeeL, G.nb, G.lds, (long long)per, c->n_red, c->piv, c->rowperm, c->Sls32,
+                        c->d_status);
+}
+
+// The plain black blocks into SlsL: the Schur-corrected sweep's fallback when a corrected
+// block is singular (its red factors are compact, so the plain sweep takes its black factors
+// from here as well).
+cudaError_t plain_black_factor(sc_ctx* c) { return black_factor(c, nullptr, 0.f, false); }
 
 }  // namespace sc
