@@ -51,6 +51,7 @@ class _Params(ctypes.Structure):
         ("sutherland", ctypes.c_int), ("model", ctypes.c_int), ("viscous", ctypes.c_int),
         ("adv", ctypes.c_double * 3), ("nu", ctypes.c_double), ("roe_delta", ctypes.c_double),
         ("with_time", ctypes.c_int), ("adv_flux", ctypes.c_int),
+        ("visc_flux", ctypes.c_int), ("ip_penalty", ctypes.c_double),
     ]
 
 
@@ -75,6 +76,8 @@ class Params:
     roe_delta: float = 0.05
     with_time: bool = True
     adv_flux: int = 0       # 0 Roe (entropy fix), 1 local Lax-Friedrichs
+    visc_flux: int = 0      # 0 BR1, 1 symmetric interior penalty (compact)
+    ip_penalty: float = 1.0  # C_IP in sigma = C_IP (N+1)^2 nu_ref / h
 
     @property
     def K(self) -> int:
@@ -96,6 +99,7 @@ class Params:
         p.adv = (ctypes.c_double * 3)(*self.adv)
         p.nu, p.roe_delta, p.with_time = self.nu, self.roe_delta, int(self.with_time)
         p.adv_flux = int(self.adv_flux)
+        p.visc_flux, p.ip_penalty = int(self.visc_flux), float(self.ip_penalty)
         return p
 
 
@@ -253,7 +257,7 @@ def residual_mixed(p: Params, orders, Q, Qs=None, Qsm1=None, force_mortar: bool 
     R = np.zeros((mixed_nodes(o), 5))
     if lib().or_residual_mixed(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), _dp(Qs), _dp(Qsm1),
                                _dp(R)) != 0:
-        raise ValueError("orders must lie in 1..7")
+        raise ValueError("orders must lie in 1..7, with the BR1 viscous flux")
     return R
 
 
@@ -263,7 +267,7 @@ def jvp_mixed(p: Params, orders, Q, x, force_mortar: bool = False) -> np.ndarray
     Q = _f64(Q); x = _f64(x)
     y = np.zeros((mixed_nodes(o), 5))
     if lib().or_jvp_mixed(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), _dp(x), _dp(y)) != 0:
-        raise ValueError("orders must lie in 1..7")
+        raise ValueError("orders must lie in 1..7, with the BR1 viscous flux")
     return y
 
 
@@ -274,7 +278,7 @@ def jacobian_mixed(p: Params, orders, Q, force_mortar: bool = False) -> np.ndarr
     dofs = mixed_nodes(o) * 5
     A = np.zeros((dofs, dofs))
     if lib().or_jacobian_mixed(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), _dp(A)) != 0:
-        raise ValueError("orders must lie in 1..7")
+        raise ValueError("orders must lie in 1..7, with the BR1 viscous flux")
     return A
 
 
@@ -291,7 +295,7 @@ def jacobian_mixed_sparse(p: Params, orders, Q, force_mortar: bool = False):
         nnz = lib().or_jacobian_mixed_coo(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), cap,
                                           _ip(rows), _ip(cols), _dp(vals))
         if nnz < 0:
-            raise ValueError("orders must lie in 1..7")
+            raise ValueError("orders must lie in 1..7, with the BR1 viscous flux")
         if nnz <= cap:
             break
         cap = int(nnz)
@@ -312,7 +316,7 @@ def jacobian_mixed_element_rows(p: Params, orders, Q, e: int, force_mortar: bool
     cnt = lib().or_jacobian_mixed_elem_rows(ctypes.byref(p.c()), _ip(o), int(force_mortar), _dp(Q), int(e),
                                             _ip(elems), _dp(blocks))
     if cnt < 0:
-        raise ValueError("orders must lie in 1..7")
+        raise ValueError("orders must lie in 1..7, with the BR1 viscous flux")
     out, off = {}, 0
     for i in range(cnt):
         c = int(elems[i])

@@ -30,7 +30,14 @@
 //     delta = roe_delta * c_roe (the paper names Roe without details);
 //   * or (adv_flux = 1) the Lax-Friedrichs flux of the paper's experiment (Sec. 4), read as
 //     the local one: fhat = (f(q+) + f(q-)) . n / 2 - lambda (q- - q+) / 2 with
-//     lambda = max over the two states of |u . n| + c.
+//     lambda = max over the two states of |u . n| + c;
+//   * or (visc_flux = 1) the symmetric interior-penalty viscous flux of the paper's
+//     experiment (Sec. 4), read inside the paper's mixed form: the volume term keeps the
+//     lifted gradient with qhat = (q+ + q-)/2, and the face flux becomes the compact
+//     f^nu_hat . n = (f^nu(q+, grad q+) + f^nu(q-, grad q-)) . n / 2 + sigma (q- - q+) with
+//     the elements' own (unlifted) gradients, sigma = C_IP (N+1)^2 nu_ref / h on all five
+//     variables.  For linear diffusion this is the SIPG bilinear form with Gauss-Lobatto
+//     quadrature: the lifted volume gradient supplies the symmetrising term.
 
 #include <cmath>
 #include <cstdint>
@@ -102,6 +109,8 @@ struct or_params {
   double roe_delta; // entropy-fix width as a fraction of the Roe sound speed
   int with_time;    // 0 drops the time term (spatial operator H only)
   int adv_flux;     // 0: Roe with entropy fix; 1: local Lax-Friedrichs (the paper's experiment, Sec. 4)
+  int visc_flux;    // 0: BR1 (non-compact); 1: symmetric interior penalty (compact, Sec. 4)
+  double ip_penalty;  // C_IP of the interior-penalty coefficient sigma = C_IP (N+1)^2 nu_ref / h
 };
 }
 
@@ -392,6 +401,47 @@ void trace(const Disc& D, const A& acc, int e, int d, int s, int fb, int fc, T* 
   }
 }
 
+// Gradient of the element's own polynomial (no lifting) at the same face point:
+// out[a*NV + k] = d/dx_a sum_n q_n phi_n(x).  This is the local gradient that a compact
+// viscous flux takes on each side of a face (Sec. 2.1, compact fluxes).
+template <class T, class A>
+void trace_grad(const Disc& D, const A& acc, int e, int d, int s, int fb, int fc, T* out) {
+  const Basis& B = D.B;
+  const std::vector<double>& edge = (s > 0) ? B.eR : B.eL;
+  const int xf = (s > 0) ? D.N : 0;  // xi = +-1 is the Gauss-Lobatto node 0 or N
+  for (int x = 0; x < 3 * NV; ++x) out[x] = T(0.0);
+  int db = (d + 1) % 3, dc = (d + 2) % 3;
+  for (int a = 0; a < D.p; ++a)
+    for (int b = 0; b < D.p; ++b)
+      for (int cc = 0; cc < D.p; ++cc) {
+        // phi = l_a(xi_d) l_b(xi_db) l_cc(xi_dc) evaluated / differentiated at the point
+        double v_d = edge[a], dv_d = B.dell[a * D.p + xf];
+        double v_b = (b == fb) ? 1.0 : 0.0, dv_b = B.dell[b * D.p + fb];
+        double v_c = (cc == fc) ? 1.0 : 0.0, dv_c = B.dell[cc * D.p + fc];
+        double gd[3];
+        gd[d] = D.dx * dv_d * v_b * v_c;
+        gd[db] = D.dx * v_d * dv_b * v_c;
+        gd[dc] = D.dx * v_d * v_b * dv_c;
+        if (gd[0] == 0.0 && gd[1] == 0.0 && gd[2] == 0.0) continue;
+        int c[3]; c[d] = a; c[db] = b; c[dc] = cc;
+        int m = D.node(c[0], c[1], c[2]);
+        for (int k = 0; k < NV; ++k) {
+          T qm = acc.get(e, m, k);
+          for (int x = 0; x < 3; ++x)
+            if (gd[x] != 0.0) out[x * NV + k] += gd[x] * qm;
+        }
+      }
+}
+
+// Interior-penalty coefficient (reading of the unstated constant): sigma = C_IP (N+1)^2
+// nu_ref / h with nu_ref the reference diffusivity, 1/Re for Navier-Stokes (mu = 1 at the
+// free-stream temperature) and nu for the advection-diffusion model.
+double ip_sigma(const or_params& P, int N, double h) {
+  if (!P.viscous) return 0.0;
+  const double nu_ref = (P.model == 1) ? P.nu : 1.0 / P.Re;
+  return P.ip_penalty * (N + 1.0) * (N + 1.0) * nu_ref / h;
+}
+
 // Weak-form lifting (eq. DGSEMsystem:2): g[m][a][k] for every node m of element e.
 template <class T, class A>
 void lifting(const Disc& D, const A& acc, int e, T* g /* nn*3*NV */) {
@@ -504,24 +554,33 @@ void elem_residual(const Disc& D, const A& acc, int e, const G& gsrc,
         T qp[NV], qm[NV];
         trace(D, acc, e, d, s, fb, fc, qp);
         trace(D, acc, nb, d, -s, fb, fc, qm);
-        // lifted gradients are nodal polynomials too; trace them the same way
         T gpl[3 * NV], gmi[3 * NV];
-        for (int x = 0; x < 3 * NV; ++x) { gpl[x] = T(0.0); gmi[x] = T(0.0); }
-        const T* gn = gsrc(nb);
-        for (int a = 0; a < p; ++a) {
-          int c[3]; c[db] = fb; c[dc] = fc; c[d] = a;
-          int m = D.node(c[0], c[1], c[2]);
-          if (edge[a] != 0.0)
-            for (int x = 0; x < 3 * NV; ++x) gpl[x] += edge[a] * g[(size_t)m * 3 * NV + x];
-          if (edgeo[a] != 0.0)
-            for (int x = 0; x < 3 * NV; ++x) gmi[x] += edgeo[a] * gn[(size_t)m * 3 * NV + x];
+        double sigma = 0.0;
+        if (D.P.visc_flux == 1) {
+          // interior penalty: the average of the viscous fluxes at the local gradients of
+          // both sides, minus sigma times the jump of q (penalising q+ - q-)
+          trace_grad(D, acc, e, d, s, fb, fc, gpl);
+          trace_grad(D, acc, nb, d, -s, fb, fc, gmi);
+          sigma = ip_sigma(D.P, D.N, D.h);
+        } else {
+          // BR1: lifted gradients are nodal polynomials too; trace them the same way
+          for (int x = 0; x < 3 * NV; ++x) { gpl[x] = T(0.0); gmi[x] = T(0.0); }
+          const T* gn = gsrc(nb);
+          for (int a = 0; a < p; ++a) {
+            int c[3]; c[db] = fb; c[dc] = fc; c[d] = a;
+            int m = D.node(c[0], c[1], c[2]);
+            if (edge[a] != 0.0)
+              for (int x = 0; x < 3 * NV; ++x) gpl[x] += edge[a] * g[(size_t)m * 3 * NV + x];
+            if (edgeo[a] != 0.0)
+              for (int x = 0; x < 3 * NV; ++x) gmi[x] += edgeo[a] * gn[(size_t)m * 3 * NV + x];
+          }
         }
         T fa[NV], fvp[NV], fvm[NV];
         num_flux_adv(D.P, qp, qm, d, s, fa);
         visc_flux(D.P, qp, gpl, d, fvp);
         visc_flux(D.P, qm, gmi, d, fvm);
         for (int k = 0; k < NV; ++k) {
-          T fhat = fa[k] - 0.5 * (double)s * (fvp[k] + fvm[k]);
+          T fhat = fa[k] - 0.5 * (double)s * (fvp[k] + fvm[k]) + sigma * (qp[k] - qm[k]);
           r[k] += (D.Jf * wf * phin) * fhat;
         }
       }
@@ -1055,7 +1114,10 @@ void mresidual(const MDisc& D, const Mortar1D& Mo, const A& acc, const double* Q
   for (int e = 0; e < D.K; ++e) melem_residual<T>(D, Mo, acc, e, G, Qs, Qsm1, R + (size_t)D.off[e] * NV);
 }
 
+// Meshes of mixed order take BR1 only: the interior-penalty flux is defined here on
+// conforming faces.
 bool orders_ok(const or_params* P, const int* orders) {
+  if (P->visc_flux != 0) return false;
   const int K = P->n * P->n * P->n;
   for (int e = 0; e < K; ++e)
     if (orders[e] < 1 || orders[e] > 7) return false;
