@@ -31,7 +31,8 @@ if ROOT not in sys.path:
 
 import sc_inputs as I  # noqa: E402
 
-WORKLOAD = dict(name="tgv_16x16x16_N4_cfl50", n=16, N=4, Ma=0.1, Re=1600.0, cfl=50.0, seed=0, adv_flux=0)
+WORKLOAD = dict(name="tgv_16x16x16_N4_cfl50", n=16, N=4, Ma=0.1, Re=1600.0, cfl=50.0, seed=0, adv_flux=0,
+                visc_flux=0)
 METRIC = "linear-solve DOF/s at rel. residual 1e-8: condensed GPU forms vs plain FP64"
 REL_TOL = 1e-8
 # Peaks: HBM and bf16 from MEASURED_PEAKS.json; FP64 and FP32 FMA rates derived from
@@ -134,7 +135,7 @@ def train_correction(args, stream, cfl=None):
     for i, Ma in enumerate(mach):
         Q, dt = I.tgv_state(n, N, Ma=Ma, seed=100 + i, cfl=cfl)
         c = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Ma=Ma, Re=WORKLOAD["Re"],
-                       adv_flux=WORKLOAD["adv_flux"],
+                       adv_flux=WORKLOAD["adv_flux"], visc_flux=WORKLOAD["visc_flux"],
                        precond=sc.SC_PC_RED_BLACK)
         c.sc_set_mesh(n, 2 * math.pi, N)
         c.sc_set_timestep(dt, 1)
@@ -185,7 +186,8 @@ def run_ours(args, world, rank, local):
         extra = dict(precond=sc.SC_PC_RED_BLACK)
     elif args.precond == "rbs":
         extra = dict(precond=sc.SC_PC_RB_SCHUR if precision == sc.SC_PREC_MIXED else sc.SC_PC_RED_BLACK)
-    ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"], adv_flux=W["adv_flux"],
+    ctx = sc.Context(stream=stream.cuda_stream, precision=precision, Re=W["Re"], Ma=W["Ma"],
+                     adv_flux=W["adv_flux"], visc_flux=W["visc_flux"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
                      outer_krylov=args.outer_krylov if args.arm != "fp64" else 0, inner_iters=args.inner_iters,
@@ -292,6 +294,8 @@ def run_ours(args, world, rank, local):
         "data": "synthetic (seeded Taylor-Green state, 1e-3 perturbation)",
         "config": {"workload": W["name"], "elements": W["n"] ** 3, "order": W["N"], "dof": dofs, "cfl": W["cfl"],
                    "Ma": W["Ma"], "Re": W["Re"], "arm": args.arm, "gmres_restart": args.restart,
+                   "fluxes": ("lax-friedrichs" if W["adv_flux"] else "roe") + " + "
+                   + ("sipg" if W["visc_flux"] else "br1"),
                    "inner_tol": args.inner_tol if args.arm != "fp64" else None,
                    "outer": (f"fgmres({args.outer_krylov})" if args.outer_krylov else "refinement sweeps")
                    if args.arm != "fp64" else None,
@@ -327,7 +331,7 @@ def fp64_reference_arm(args, W, Q, dt, stream, dQ_mixed):
     import torch
     from paper_1911_02366_gb300 import sc
     ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_FP64, Re=W["Re"], Ma=W["Ma"],
-                     adv_flux=W["adv_flux"],
+                     adv_flux=W["adv_flux"], visc_flux=W["visc_flux"],
                      gmres_restart=30, gmres_max_iters=args.max_iters, rel_tol=REL_TOL)
     ctx.sc_set_mesh(W["n"], 2 * math.pi, W["N"])
     ctx.sc_set_timestep(dt, 1)
@@ -384,7 +388,8 @@ def run_oracle(steps: int):
     import oracle as O
     n_s, L, Q, dt = cpu_sample()
     W = WORKLOAD
-    p = O.Params(n=n_s, N=W["N"], dt=dt, L=L, Re=W["Re"], Ma=W["Ma"], adv_flux=W["adv_flux"])
+    p = O.Params(n=n_s, N=W["N"], dt=dt, L=L, Re=W["Re"], Ma=W["Ma"], adv_flux=W["adv_flux"],
+                 visc_flux=W["visc_flux"])
     A = O.jacobian(p, Q)
     B = -O.residual(p, Q).reshape(-1)
     times, iters = [], []
@@ -418,7 +423,7 @@ def run_batched(args, world, rank, local):
     for n, N in BATCH_ORDERS:
         Q, dt = I.tgv_state(n, N, Ma=W["Ma"], seed=W["seed"], cfl=BATCH_CFL)
         c = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
-                       adv_flux=W["adv_flux"],
+                       adv_flux=W["adv_flux"], visc_flux=W["visc_flux"],
                        gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                        inner_tol=args.inner_tol, max_refine=20)
         c.sc_set_mesh(n, 2 * math.pi, N)
@@ -555,7 +560,7 @@ def run_timesteps(args, world, rank, local):
           "learned": sc.SC_PC_LEARNED}[args.ts_precond]
     net, train_info = (train_correction(args, stream, cfl=args.cfl) if pc == sc.SC_PC_LEARNED else (None, None))
     ctx = sc.Context(stream=stream.cuda_stream, precision=sc.SC_PREC_MIXED, Re=W["Re"], Ma=W["Ma"],
-                     adv_flux=W["adv_flux"],
+                     adv_flux=W["adv_flux"], visc_flux=W["visc_flux"],
                      gmres_restart=args.restart, gmres_max_iters=args.max_iters, rel_tol=REL_TOL,
                      inner_tol=args.inner_tol, max_refine=20, tensor_cores=args.tensor_cores,
                      outer_krylov=args.outer_krylov, inner_iters=args.inner_iters, precond=pc,
@@ -804,6 +809,9 @@ def main():
                     help="mixed arms, N >= 5: A_ii^-1 by FP64 Gauss-Jordan, rounded to FP32 for the operator")
     ap.add_argument("--adv-flux", choices=["roe", "lf"], default="roe",
                     help="advective numerical flux: Roe (default) or local Lax-Friedrichs (the paper's experiment)")
+    ap.add_argument("--visc-flux", choices=["br1", "sipg"], default="br1",
+                    help="viscous numerical flux: BR1 (default) or the symmetric interior penalty (the "
+                         "paper's experiment; compact)")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--max-iters", type=int, default=4000)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
@@ -819,11 +827,13 @@ def main():
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain FP64 arm beside the mixed line")
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    if args.adv_flux == "lf":
-        WORKLOAD.update(adv_flux=1, name=WORKLOAD["name"] + "_lf")
     if args.n or args.order:
         n = args.n or WORKLOAD["n"]; N = args.order or WORKLOAD["N"]
         WORKLOAD.update(n=n, N=N, name=f"tgv_{n}x{n}x{n}_N{N}_cfl{int(WORKLOAD['cfl'])}")
+    if args.adv_flux == "lf":
+        WORKLOAD.update(adv_flux=1, name=WORKLOAD["name"] + "_lf")
+    if args.visc_flux == "sipg":
+        WORKLOAD.update(visc_flux=1, name=WORKLOAD["name"] + "_sipg")
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")

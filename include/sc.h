@@ -49,6 +49,7 @@ typedef enum {
 
 enum { SC_PREC_FP64 = 0, SC_PREC_MIXED = 1 };
 enum { SC_FLUX_ROE = 0, SC_FLUX_LF = 1 };
+enum { SC_VISC_BR1 = 0, SC_VISC_SIPG = 1 };
 /* Preconditioners of the condensed GMRES (the paper uses point Jacobi, Sec. 4):
    SC_PC_BLOCK_JACOBI: z_e = S_ee^-1 v_e per element.
    SC_PC_RED_BLACK: one forward block Gauss-Seidel sweep over the checkerboard colouring of
@@ -122,6 +123,15 @@ typedef struct {
                             width roe_delta; default) or SC_FLUX_LF (local Lax-Friedrichs, the
                             paper's experiment, Sec. 4: central flux minus half the larger
                             |u . n| + c of the two states times the jump) */
+  int visc_flux;         /* viscous numerical flux (Sec. 2.1; the paper's experiment, Sec. 4, uses the
+                            symmetric interior penalty): SC_VISC_BR1 (Bassi-Rebay 1: the average of
+                            f^nu at the lifted gradients of both sides; default) or SC_VISC_SIPG
+                            (compact: the average of f^nu at each side's own unlifted gradient plus
+                            sigma (q- - q+), sigma = ip_penalty (N+1)^2 / (h Re), on all five
+                            variables; the volume term keeps the lifted gradient with qhat = {{q}}).
+                            SIPG couples an element to its six face neighbours only: the edge
+                            couplings of BR1 are exact zeros */
+  double ip_penalty;     /* C_IP of the interior-penalty coefficient (> 0; default 1) */
 } sc_config;
 
 /* Per-solve statistics filled by sc_solve. */

@@ -93,7 +93,7 @@ void free_all(sc_ctx* c) {
   double** dps[] = {&c->Q, &c->Qh, &c->grad, &c->F, &c->B, &c->NJ, &c->RJ, &c->Aown, &c->X, &c->Ainv,
                     &c->Ytmp, &c->See, &c->V, &c->Wv, &c->Zv, &c->Xb, &c->Gb, &c->Rb, &c->Ui, &c->Tb,
                     &c->Hd, &c->partial, &c->Xfull, &c->Rfull, &c->Cross, &c->Apk, &c->Sls, &c->dQn,
-                    &c->OV, &c->OZ};
+                    &c->OV, &c->OZ, &c->gloc, &c->NJL};
   for (auto p : dps) { if (*p) cudaFree(*p); *p = nullptr; }
   float** fps[] = {&c->Aown32, &c->X32, &c->Ainv32, &c->Y32, &c->See32, &c->Zf, &c->Xbf, &c->Uf, &c->Cross32,
                    &c->Apk32, &c->Sls32, &c->Sdiag, &c->Cpl, &c->Feat, &c->Snorm, &c->Ynet, &c->Hbuf,
@@ -203,6 +203,7 @@ sc_status sc_default_config(sc_config* cfg) {
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->gamma = 1.4; cfg->Pr = 0.72; cfg->Re = 1600.0; cfg->Ma = 0.1;
   cfg->Ts = 110.4 / 288.15; cfg->sutherland = 1; cfg->roe_delta = 0.05;
+  cfg->visc_flux = SC_VISC_BR1; cfg->ip_penalty = 1.0;
   cfg->precision = SC_PREC_FP64; cfg->precond = SC_PC_BLOCK_JACOBI;
   cfg->gmres_restart = 30; cfg->gmres_max_iters = 4000; cfg->max_refine = 10;
   cfg->rel_tol = 1e-8; cfg->inner_tol = 1e-4; cfg->tensor_cores = 1; cfg->learned_min_reduction = 1.5;
@@ -218,6 +219,8 @@ sc_status sc_create(const sc_config* cfg, void* cuda_stream, sc_ctx** out) {
   if (cfg->precond < SC_PC_BLOCK_JACOBI || cfg->precond > SC_PC_RB_SCHUR) return SC_ERR_ARG;
   if (cfg->interior_fp64 != 0 && cfg->interior_fp64 != 1) return SC_ERR_ARG;
   if (cfg->adv_flux != SC_FLUX_ROE && cfg->adv_flux != SC_FLUX_LF) return SC_ERR_ARG;
+  if (cfg->visc_flux != SC_VISC_BR1 && cfg->visc_flux != SC_VISC_SIPG) return SC_ERR_ARG;
+  if (!(cfg->ip_penalty > 0.0) || !std::isfinite(cfg->ip_penalty)) return SC_ERR_ARG;
   if (cfg->outer_krylov < 0 || cfg->outer_krylov > cfg->gmres_restart || cfg->inner_iters < 0) return SC_ERR_ARG;
   sc_ctx* c = new sc_ctx();
   c->cfg = *cfg;
@@ -272,6 +275,8 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   G.inv_hw = 1.0 / (G.h * w[N]);
   G.gamma = c->cfg.gamma; G.Pr = c->cfg.Pr; G.Re = c->cfg.Re; G.Ma = c->cfg.Ma; G.Ts = c->cfg.Ts;
   G.roe_delta = c->cfg.roe_delta; G.sutherland = c->cfg.sutherland; G.adv_flux = c->cfg.adv_flux;
+  G.visc_flux = c->cfg.visc_flux;
+  G.sigma = (G.visc_flux == SC_VISC_SIPG) ? c->cfg.ip_penalty * (N + 1.0) * (N + 1.0) / (G.h * G.Re) : 0.0;
   G.dt = 1.0; G.c0 = 1.0;
   // node permutation: interior nodes first, then boundary nodes, each in natural order
   const int p = G.p;
@@ -329,6 +334,7 @@ sc_status sc_set_mesh(sc_ctx* c, int n, double L, int N) {
   A(dalloc(&c->Xfull, dofs)); A(dalloc(&c->Rfull, dofs)); A(dalloc(&c->dQn, dofs));
   A(dalloc(&c->grad, nodes * 15)); A(dalloc(&c->F, nodes * 15));
   A(dalloc(&c->NJ, nodes * 375)); A(dalloc(&c->RJ, (size_t)G.K * 6 * 50 * G.p * G.p));
+  if (G.visc_flux == SC_VISC_SIPG) { A(dalloc(&c->gloc, nodes * 15)); A(dalloc(&c->NJL, nodes * 375)); }
   A(dalloc(&c->Aown, (size_t)G.K * own_stride(G))); A(dalloc(&c->X, (size_t)G.K * G.NP * 25));
   if (c->cfg.precision == SC_PREC_MIXED) {
     A(dalloc(&c->Aown32, (size_t)G.K * own_stride(G))); A(dalloc(&c->X32, (size_t)G.K * G.NP * 25));

@@ -7,7 +7,12 @@
 //   R_j = c0 J W_j (q_j - q_hist)/dt + Jf W_j sum_a sum_b D[j_a][b] F_a(m_b)
 //         + sum_{faces f of j} Jf W^f_j [ fhat_f(j) - s_f F_{d_f}(j) ]
 // with F = f^a - f^nu, fhat = Roe(q+, q-) - (1/2) s (f^nu_d(+) + f^nu_d(-)), J = (h/2)^3,
-// Jf = (h/2)^2, W_j the tensor GL weight.
+// Jf = (h/2)^2, W_j the tensor GL weight.  With the symmetric interior penalty (the paper's
+// experiment, Sec. 4) the face flux takes f^nu at each side's own unlifted gradient
+// Dq = (2/h) sum_b D[m_a][b] q(...) instead of the lifted one and adds sigma (q+ - q-); the
+// volume flux F keeps the lifted gradient (qhat = {{q}}), which supplies the symmetrising
+// term.  The unlifted gradients depend on their own element only, so the edge-neighbour
+// couplings of BR1 vanish.
 //
 // Jacobian (Sec. 2.1.1-2.1.2, eqs. AdvImpDG, DiffImpDGouter, GradDGImp): the point flux
 // Jacobians dF_d/dq, df^nu_d/dq and df^nu_d/dg_a, and the Roe derivatives, are
@@ -39,7 +44,7 @@ __global__ void k_history(Geo G, const double* __restrict__ Qs, const double* __
 }
 
 // Lifted gradients, one thread per node.
-SC_HD void lift_body(const Geo& G, const double* Q, const int* nbr, int t, double* grad) {
+SC_HD void lift_body(const Geo& G, const double* Q, const int* nbr, int t, double* grad, int lifted) {
   const int e = t / G.nn, m = t % G.nn, p = G.p, N = G.N;
   int c[3]; node_coords(m, p, c);
   const double* qe = Q + (size_t)e * G.nn * 5;
@@ -53,7 +58,7 @@ SC_HD void lift_body(const Geo& G, const double* Q, const int* nbr, int t, doubl
       const double* qb = qe + (size_t)node_index(cc, p) * 5;
       for (int k = 0; k < 5; ++k) acc[k] = fma(Dab, qb[k], acc[k]);
     }
-    if (c[a] == N || c[a] == 0) {
+    if (lifted && (c[a] == N || c[a] == 0)) {
       const int s = (c[a] == N) ? 1 : -1;
       const int nb = nbr[e * 18 + face_slot(a, s)];
       int cn[3] = {c[0], c[1], c[2]}; cn[a] = N - c[a];
@@ -65,10 +70,11 @@ SC_HD void lift_body(const Geo& G, const double* Q, const int* nbr, int t, doubl
   }
 }
 
+// lifted = 1: the BR1 lifted gradient g; 0: the element's own gradient Dq.
 __global__ void k_lift(Geo G, const double* __restrict__ Q, const int* __restrict__ nbr,
-                       double* __restrict__ grad) {
+                       double* __restrict__ grad, int lifted) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < G.K * G.nn) lift_body(G, Q, nbr, t, grad);
+  if (t < G.K * G.nn) lift_body(G, Q, nbr, t, grad, lifted);
 }
 
 SC_HD inline void load_node(const double* __restrict__ Q, const double* __restrict__ grad,
@@ -94,8 +100,9 @@ __global__ void k_flux(Geo G, const double* __restrict__ Q, const double* __rest
 }
 
 // Residual rows; writes B = -R.  One thread per node.
+// gface: the gradients the face flux takes (lifted for BR1, unlifted for the interior penalty).
 __global__ void k_resid(Geo G, const double* __restrict__ Q, const double* __restrict__ Qh,
-                        const double* __restrict__ grad, const double* __restrict__ F,
+                        const double* __restrict__ gface, const double* __restrict__ F,
                         const int* __restrict__ nbr, double* __restrict__ Bout) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= G.K * G.nn) return;
@@ -122,15 +129,16 @@ __global__ void k_resid(Geo G, const double* __restrict__ Q, const double* __res
     int cn[3] = {c[0], c[1], c[2]}; cn[d] = N - c[d];
     const size_t tn = (size_t)nb * G.nn + node_index(cn, p);
     double qa[5], ga[3][5], qb[5], gb[3][5];
-    load_node(Q, grad, t, qa, ga);
-    load_node(Q, grad, tn, qb, gb);
+    load_node(Q, gface, t, qa, ga);
+    load_node(Q, gface, tn, qb, gb);
     double fr[5], fva[5], fvb[5];
     flux_adv(G, qa, qb, d, s, fr);
     flux_viscous(G, qa, ga, d, fva);
     flux_viscous(G, qb, gb, d, fvb);
     const double Sf = G.Jf * Wj / G.w[c[d]];
     for (int k = 0; k < 5; ++k) {
-      const double fhat = fr[k] - 0.5 * s * (fva[k] + fvb[k]);
+      double fhat = fr[k] - 0.5 * s * (fva[k] + fvb[k]);
+      if (G.visc_flux == 1) fhat = fma(G.sigma, qa[k] - qb[k], fhat);
       r[k] = fma(Sf, fhat - s * F[(size_t)t * 15 + d * 5 + k], r[k]);
     }
   }
@@ -245,11 +253,15 @@ SC_HD inline double wprod(const Geo& G, const int c[3]) { return G.w[c[0]] * G.w
     }                                                      \
   } while (0)
 
-// Own element block: rows j, columns r (both in element e).
-SC_HD void own_entry(const Geo& G, const double* NJ, const double* RJ, const int* nbr, int e, int j, int r,
-                     double acc[25]) {
+// Own element block: rows j, columns r (both in element e).  NJL: the point-flux Jacobians at
+// the unlifted gradients (interior penalty only; null with BR1).
+template <bool IP>
+SC_HD void own_entry(const Geo& G, const double* NJ, const double* NJL, const double* RJ, const int* nbr, int e,
+                     int j, int r, double acc[25]) {
   const int nn = G.nn, p = G.p, N = G.N;
   ElemView V{NJ + (size_t)e * NJC * nn, nn};
+  constexpr bool ip = IP;
+  ElemView VL{ip ? NJL + (size_t)e * NJC * nn : nullptr, nn};
   const int pp = p * p;
   {
     int cj[3], cr[3];
@@ -308,7 +320,27 @@ SC_HD void own_entry(const Geo& G, const double* NJ, const double* RJ, const int
           if (cj[df] != 0 && cj[df] != N) continue;
           const int sf = (cj[df] == N) ? 1 : -1;
           const double Sf = G.Jf * Wj / G.w[cj[df]];
-          if (ndiff == 0) {
+          if constexpr (ip) {
+            // fhat - s F_d(j): the strong-form term -s F_d(j) keeps the lifted gradient at j
+            // (full weight), the face average -s/2 f^nu(q_j, Dq_j) takes the unlifted one
+            // (Dq_a(j) = dx D[j_a][r_a] q_r along the a-line), and sigma (q_j - q_jm) adds
+            // sigma on the diagonal
+            if (ndiff == 0) {
+              const int f = face_slot(df, sf);
+              const int fidx = cj[(df + 1) % 3] + p * cj[(df + 2) % 3];
+              const double* rj = RJ + ((size_t)e * 6 + f) * 50 * pp + fidx;
+              ACC25(Sf, rj[(size_t)kl * pp] - sf * V.Fq(df, j, kl) - 0.5 * sf * VL.fvq(df, j, kl)
+                            + (kl % 6 == 0 ? G.sigma : 0.0));
+              for (int a = 0; a < 3; ++a) {
+                ACC25(Sf * sf * lift_own(G, cj, cj, a, true), V.fvg(df, a, j, kl));
+                ACC25(-0.5 * Sf * sf * G.dx * G.D[cj[a]][cj[a]], VL.fvg(df, a, j, kl));
+              }
+            } else {
+              const int a = dc[0];
+              ACC25(Sf * sf * lift_own(G, cj, cr, a, false), V.fvg(df, a, j, kl));
+              ACC25(-0.5 * Sf * sf * G.dx * G.D[cj[a]][cr[a]], VL.fvg(df, a, j, kl));
+            }
+          } else if (ndiff == 0) {
             const int f = face_slot(df, sf);
             const int fidx = cj[(df + 1) % 3] + p * cj[(df + 2) % 3];
             const double* rj = RJ + ((size_t)e * 6 + f) * 50 * pp + fidx;
@@ -332,7 +364,9 @@ SC_HD void own_entry(const Geo& G, const double* NJ, const double* RJ, const int
 
 // Pairs sharing no GL index are structurally zero: they are not in the pair list and keep the
 // zeros written when the mesh was set.
+template <bool IP>
 __global__ void __launch_bounds__(256, 3) k_asm_own(Geo G, const double* __restrict__ NJ,
+                                                 const double* __restrict__ NJL,
                                                  const double* __restrict__ RJ,
                                                  const int* __restrict__ nbr, const int* __restrict__ iperm,
                                                  const int* __restrict__ pairs, int npairs,
@@ -343,7 +377,7 @@ __global__ void __launch_bounds__(256, 3) k_asm_own(Geo G, const double* __restr
     const int code = pairs[t];
     const int pj = code >> 16, pr = code & 0xffff;
     double acc[25];
-    own_entry(G, NJ, RJ, nbr, e, iperm[pj], iperm[pr], acc);
+    own_entry<IP>(G, NJ, NJL, RJ, nbr, e, iperm[pj], iperm[pr], acc);
     double* out = Aown + (size_t)e * own_stride(G) + (size_t)(5 * pj) * lda + own_col(G, pr, 0);
     for (int k = 0; k < 5; ++k)
       for (int l = 0; l < 5; ++l) out[(size_t)k * lda + l] = acc[k * 5 + l];
@@ -351,12 +385,16 @@ __global__ void __launch_bounds__(256, 3) k_asm_own(Geo G, const double* __restr
 }
 
 // Neighbour couplings: X[e][pair][5x5] = dR_{e, row}/dq_{nbr(e, slot), col}.
-SC_HD void cross_entry(const Geo& G, const double* NJ, const double* RJ, const int* nbr, int e, int j, int slot,
-                       int r, double acc[25]) {
+// With the interior penalty (NJL non-null) the neighbour enters the face rows through its
+// state and its unlifted gradient only, and the edge slots stay zero.
+template <bool IP>
+SC_HD void cross_entry(const Geo& G, const double* NJ, const double* NJL, const double* RJ, const int* nbr, int e,
+                       int j, int slot, int r, double acc[25]) {
   const int nn = G.nn, p = G.p, N = G.N, pp = p * p;
   int cj[3], cr[3];
   node_coords(j, p, cj); node_coords(r, p, cr);
   ElemView V{NJ + (size_t)e * NJC * nn, nn};
+  constexpr bool ip = IP;
 #pragma unroll
   for (int kl = 0; kl < 25; ++kl) acc[kl] = 0.0;
   const double Wj = wprod(G, cj);
@@ -365,6 +403,7 @@ SC_HD void cross_entry(const Geo& G, const double* NJ, const double* RJ, const i
     const int jend = sf > 0 ? N : 0, nend = N - jend;
     const int nb = nbr[e * 18 + slot];
     ElemView Vn{NJ + (size_t)nb * NJC * nn, nn};
+    ElemView VnL{ip ? NJL + (size_t)nb * NJC * nn : nullptr, nn};
     // (V) volume rows through e's own lifted gradient at the face node m co-located with r
     if (cr[df] == nend) {
       int cm[3] = {cr[0], cr[1], cr[2]}; cm[df] = jend;
@@ -383,25 +422,39 @@ SC_HD void cross_entry(const Geo& G, const double* NJ, const double* RJ, const i
       if (r == jm) {
         const int fidx = cj[(df + 1) % 3] + p * cj[(df + 2) % 3];
         const double* rj = RJ + ((size_t)e * 6 + slot) * 50 * pp + fidx;
-        ACC25(Sf, rj[(size_t)(25 + kl) * pp] - 0.5 * sf * Vn.fvq(df, jm, kl));   // (S1)
-        for (int d2 = 0; d2 < 3; ++d2) {                                         // (S2)
+        if (ip)                                                                  // (S1)
+          ACC25(Sf, rj[(size_t)(25 + kl) * pp] - 0.5 * sf * VnL.fvq(df, jm, kl) - (kl % 6 == 0 ? G.sigma : 0.0));
+        else
+          ACC25(Sf, rj[(size_t)(25 + kl) * pp] - 0.5 * sf * Vn.fvq(df, jm, kl));
+        // (S2) e's lifted gradient at j reaches across the face: in every face term of j,
+        // at half weight (BR1 average) or at the full weight of -s F_d(j) (interior penalty)
+        const double w2 = ip ? 1.0 : 0.5;
+        for (int d2 = 0; d2 < 3; ++d2) {
           if (cj[d2] != 0 && cj[d2] != N) continue;
           const int s2 = (cj[d2] == N) ? 1 : -1;
           const double Sf2 = G.Jf * Wj / G.w[cj[d2]];
-          ACC25(Sf2 * 0.5 * s2 * sf * G.inv_hw, V.fvg(d2, df, j, kl));
+          ACC25(Sf2 * w2 * s2 * sf * G.inv_hw, V.fvg(d2, df, j, kl));
         }
       }
-      // (S3) neighbour's own lifting at jm, along its grid lines through jm
+      // (S3) the neighbour's gradient at jm (lifted, or unlifted with the interior penalty),
+      // along its grid lines through jm
       int nd = 0, dd = -1;
       for (int a = 0; a < 3; ++a) if (cn[a] != cr[a]) { ++nd; dd = a; }
-      if (nd == 0) {
+      if (ip) {
+        if (nd == 0) {
+          for (int a = 0; a < 3; ++a)
+            ACC25(-0.5 * sf * Sf * G.dx * G.D[cn[a]][cn[a]], VnL.fvg(df, a, jm, kl));
+        } else if (nd == 1) {
+          ACC25(-0.5 * sf * Sf * G.dx * G.D[cn[dd]][cr[dd]], VnL.fvg(df, dd, jm, kl));
+        }
+      } else if (nd == 0) {
         for (int a = 0; a < 3; ++a)
           ACC25(-0.5 * sf * Sf * lift_own(G, cn, cn, a, true), Vn.fvg(df, a, jm, kl));
       } else if (nd == 1) {
         ACC25(-0.5 * sf * Sf * lift_own(G, cn, cr, dd, false), Vn.fvg(df, dd, jm, kl));
       }
     }
-  } else {
+  } else if (!ip) {
     const int q = slot - 6, pi = q / 4;
     const int d1 = pi == 2 ? 1 : 0, d2 = pi == 0 ? 1 : 2;
     const int s1 = (q & 2) ? 1 : -1, s2 = (q & 1) ? 1 : -1;
@@ -422,7 +475,9 @@ SC_HD void cross_entry(const Geo& G, const double* NJ, const double* RJ, const i
   }
 }
 
-__global__ void k_asm_cross(Geo G, const double* __restrict__ NJ, const double* __restrict__ RJ,
+template <bool IP>
+__global__ void k_asm_cross(Geo G, const double* __restrict__ NJ, const double* __restrict__ NJL,
+                            const double* __restrict__ RJ,
                             const int* __restrict__ nbr, const int* __restrict__ prow,
                             const int* __restrict__ pslot, const int* __restrict__ pcol,
                             double* __restrict__ X) {
@@ -430,7 +485,7 @@ __global__ void k_asm_cross(Geo G, const double* __restrict__ NJ, const double* 
   if (t >= (size_t)G.K * G.NP) return;
   const int e = (int)(t / G.NP), pr = (int)(t % G.NP);
   double acc[25];
-  cross_entry(G, NJ, RJ, nbr, e, prow[pr], pslot[pr], pcol[pr], acc);
+  cross_entry<IP>(G, NJ, NJL, RJ, nbr, e, prow[pr], pslot[pr], pcol[pr], acc);
   // layout X[e][k][pair][l]: the couplings of one row variable are contiguous
   for (int k = 0; k < 5; ++k)
     for (int l = 0; l < 5; ++l) X[(((size_t)e * 5 + k) * G.NP + pr) * 5 + l] = acc[k * 5 + l];
@@ -444,10 +499,12 @@ namespace sc {
 
 cudaError_t launch_residual_geo(sc_ctx* c, const Geo& G, const double* Q, const double* Qh, double* out) {
   const size_t nodes = (size_t)G.K * G.nn;
-  count_launch(c, 3);
-  k_lift<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, c->d_nbr, c->grad);
+  const bool ip = G.visc_flux == 1;
+  count_launch(c, ip ? 4 : 3);
+  k_lift<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, c->d_nbr, c->grad, 1);
+  if (ip) k_lift<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, c->d_nbr, c->gloc, 0);
   k_flux<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, c->grad, c->F);
-  k_resid<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, Qh, c->grad, c->F, c->d_nbr, out);
+  k_resid<<<blocks_for(nodes, 128), 128, 0, c->stream>>>(G, Q, Qh, ip ? c->gloc : c->grad, c->F, c->d_nbr, out);
   return cudaGetLastError();
 }
 
@@ -463,18 +520,29 @@ cudaError_t launch_history(sc_ctx* c, const double* Qs, const double* Qsm1) {
 cudaError_t launch_assembly(sc_ctx* c) {
   const Geo& G = c->G;
   const size_t nodes = (size_t)G.K * G.nn;
-  count_launch(c, 3);
+  const bool ip = G.visc_flux == 1;
+  count_launch(c, ip ? 4 : 3);
   k_nodejac<<<blocks_for(nodes, 64), 64, 0, c->stream>>>(G, c->Q, c->grad, c->NJ);
+  // the unlifted gradients are those of the last residual evaluation of this state
+  if (ip) k_nodejac<<<blocks_for(nodes, 64), 64, 0, c->stream>>>(G, c->Q, c->gloc, c->NJL);
   const size_t fn = (size_t)G.K * 6 * G.p * G.p;
   k_roejac<<<blocks_for(fn, 64), 64, 0, c->stream>>>(G, c->Q, c->d_nbr, c->RJ);
   {
     ProfScope ps(c, SCK_ASM_OWN);
-    k_asm_own<<<G.K, 256, 0, c->stream>>>(G, c->NJ, c->RJ, c->d_nbr, c->d_iperm, c->d_own_pairs,
-                                          (int)c->own_pairs.size(), c->Aown);
+    if (ip)
+      k_asm_own<true><<<G.K, 256, 0, c->stream>>>(G, c->NJ, c->NJL, c->RJ, c->d_nbr, c->d_iperm, c->d_own_pairs,
+                                                  (int)c->own_pairs.size(), c->Aown);
+    else
+      k_asm_own<false><<<G.K, 256, 0, c->stream>>>(G, c->NJ, nullptr, c->RJ, c->d_nbr, c->d_iperm, c->d_own_pairs,
+                                                   (int)c->own_pairs.size(), c->Aown);
   }
   const size_t np = (size_t)G.K * G.NP;
-  k_asm_cross<<<blocks_for(np, 128), 128, 0, c->stream>>>(G, c->NJ, c->RJ, c->d_nbr, c->d_prow, c->d_pslot,
-                                                          c->d_pcol, c->X);
+  if (ip)
+    k_asm_cross<true><<<blocks_for(np, 128), 128, 0, c->stream>>>(G, c->NJ, c->NJL, c->RJ, c->d_nbr, c->d_prow,
+                                                                  c->d_pslot, c->d_pcol, c->X);
+  else
+    k_asm_cross<false><<<blocks_for(np, 128), 128, 0, c->stream>>>(G, c->NJ, nullptr, c->RJ, c->d_nbr, c->d_prow,
+                                                                   c->d_pslot, c->d_pcol, c->X);
   return cudaGetLastError();
 }
 

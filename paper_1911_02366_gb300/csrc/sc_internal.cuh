@@ -26,6 +26,8 @@ struct Geo {
   double dt, c0;          // time step, BDF leading coefficient (1 or 3/2)
   double gamma, Pr, Re, Ma, Ts, roe_delta;
   int adv_flux;  // 0 Roe, 1 local Lax-Friedrichs
+  int visc_flux;  // 0 BR1 (lifted gradients at the faces), 1 symmetric interior penalty
+  double sigma;   // interior-penalty coefficient C_IP (N+1)^2 / (h Re) (0 with BR1)
   int sutherland;
   double D[SC_MAXP][SC_MAXP];  // D[a][b] = l_b'(xi_a)
   double w[SC_MAXP];           // Gauss-Lobatto weights
@@ -285,6 +287,9 @@ struct sc_ctx {
   // device memory
   double *Q = nullptr, *Qh = nullptr, *grad = nullptr, *F = nullptr, *B = nullptr;
   double *NJ = nullptr, *RJ = nullptr, *Aown = nullptr, *X = nullptr;
+  // interior penalty only: the elements' own (unlifted) gradients and the point-flux
+  // Jacobians at them, same layouts as grad and NJ
+  double *gloc = nullptr, *NJL = nullptr;
   int *d_nbr = nullptr, *d_perm = nullptr, *d_iperm = nullptr, *d_own_pairs = nullptr;
   double* gj_scale = nullptr;      // [K][n_i] row scaling of the blocked Gauss-Jordan (T-typed)
   double *OV = nullptr, *OZ = nullptr;  // outer FGMRES: Arnoldi basis (m+1 global vectors), preconditioned (m)

@@ -18,6 +18,7 @@ SC_ERR_SINGULAR_BLOCK, SC_ERR_NONFINITE, SC_ERR_NOT_CONVERGED = 5, 6, 7
 SC_PREC_FP64, SC_PREC_MIXED = 0, 1
 SC_PC_BLOCK_JACOBI, SC_PC_NONE, SC_PC_LEARNED, SC_PC_RED_BLACK, SC_PC_RB_SCHUR = 0, 1, 2, 3, 4
 SC_FLUX_ROE, SC_FLUX_LF = 0, 1
+SC_VISC_BR1, SC_VISC_SIPG = 0, 1
 SC_DIRECT_GLOBAL, SC_DIRECT_CONDENSED = 0, 1
 
 _lib = None
@@ -38,7 +39,7 @@ class sc_config(ctypes.Structure):
                 ("tensor_cores", ctypes.c_int), ("learned_min_reduction", ctypes.c_double),
                 ("factor_fp16", ctypes.c_int), ("explicit_schur", ctypes.c_int),
                 ("outer_krylov", ctypes.c_int), ("inner_iters", ctypes.c_int), ("interior_fp64", ctypes.c_int),
-                ("adv_flux", ctypes.c_int)]
+                ("adv_flux", ctypes.c_int), ("visc_flux", ctypes.c_int), ("ip_penalty", ctypes.c_double)]
 
 
 class sc_solve_stats(ctypes.Structure):

@@ -46,6 +46,7 @@ def test_default_config_values():
     assert (cfg.precision, cfg.precond, cfg.tensor_cores) == (sc.SC_PREC_FP64, sc.SC_PC_BLOCK_JACOBI, 1)
     assert (cfg.outer_krylov, cfg.inner_iters, cfg.factor_fp16, cfg.explicit_schur) == (0, 0, 0, 0)
     assert cfg.interior_fp64 == 0 and cfg.adv_flux == sc.SC_FLUX_ROE
+    assert (cfg.visc_flux, cfg.ip_penalty) == (sc.SC_VISC_BR1, 1.0)
     assert (cfg.gamma, cfg.Pr, cfg.Re, cfg.Ma) == (1.4, 0.72, 1600.0, 0.1)
 
 
@@ -56,7 +57,9 @@ def test_create_rejects_invalid_configs_before_any_cuda_call():
     bad = [dict(gmres_restart=0), dict(gmres_restart=401), dict(gmres_max_iters=0), dict(rel_tol=0.0),
            dict(Re=0.0), dict(Ma=-1.0), dict(gamma=1.0), dict(Pr=0.0), dict(precision=7),
            dict(outer_krylov=31), dict(outer_krylov=-1), dict(inner_iters=-1), dict(precond=-1), dict(precond=5),
-           dict(interior_fp64=2), dict(adv_flux=2)]
+           dict(interior_fp64=2), dict(adv_flux=2), dict(visc_flux=2), dict(visc_flux=-1),
+           dict(visc_flux=1, ip_penalty=0.0), dict(visc_flux=1, ip_penalty=-1.0),
+           dict(visc_flux=1, ip_penalty=float("nan")), dict(ip_penalty=float("inf"))]
     L = sc.lib()
     for kw in bad:
         cfg = sc.default_config(**kw)
