@@ -495,6 +495,53 @@ sc_status sc_batch_tiles(const sc_batch* batch, int c, int* ni, int* bn_y, int* 
 
 void sc_batch_destroy(sc_batch* batch);
 
+/* ---- One mesh of mixed polynomial order ------------------------------------------
+   A periodic n^3 mesh of side L whose element e = ex + n (ey + n ez) has its own order
+   orders[e] in 2..6 (the paper treats one order per mesh; this is its uneven-order case).
+   A face between two orders is a mortar: the traces of both sides (state and lifted
+   gradient) are interpolated to the Gauss-Lobatto nodes of the larger order, qhat (BR1)
+   and fhat (Roe or local Lax-Friedrichs, cfg->adv_flux) are formed there point by point,
+   and each side takes their L2 projection onto its own face polynomials (Gauss rule of
+   M + 1 points).  force_mortar = 1 routes faces between equal orders through the mortar
+   too.  States are ragged: element by element, (N_e+1)^3 nodes of 5 variables in natural
+   node order (i fastest), flat doubles.
+   Only the mixed arm: cfg->precision = SC_PREC_MIXED, cfg->precond SC_PC_BLOCK_JACOBI or
+   SC_PC_NONE, cfg->visc_flux = SC_VISC_BR1; SC_ERR_ARG otherwise, or for n outside [2, 32],
+   an order outside 2..6 or L <= 0.  The context keeps cuda_stream; every call is
+   synchronous and reports errors as the calls above do (message: sc_mixed_last_error). */
+typedef struct sc_mixed sc_mixed;
+sc_status sc_mixed_create(const sc_config* cfg, void* cuda_stream, int n, double L, const int* orders,
+                          int force_mortar, sc_mixed** out);
+void sc_mixed_destroy(sc_mixed* m);
+const char* sc_mixed_last_error(const sc_mixed* m);
+/* Totals of the ragged layouts: nodes, boundary dofs, interior dofs. */
+sc_status sc_mixed_sizes(const sc_mixed* m, long long* nodes, long long* nb_total, long long* ni_total);
+/* Newton state Q, history Qs (and Qsm1 for BDF2), time step dt > 0, bdf 1 or 2; host
+   pointers, or device pointers when on_device = 1. */
+sc_status sc_mixed_set_state(sc_mixed* m, const double* Q, const double* Qs, const double* Qsm1, double dt, int bdf,
+                             int on_device);
+/* R(Q) of eq. NeqtonEq (time term included), ragged layout. */
+sc_status sc_mixed_residual(sc_mixed* m, double* R, int on_device);
+/* y = (dR/dQ)(Q) x by forward-mode dual numbers in FP64 (eq. NewtonLinSys1, exact to rounding). */
+sc_status sc_mixed_jvp(sc_mixed* m, const double* x, double* y, int on_device);
+/* dR_e/dQ_e of element e in FP64, natural node order, 5 (N_e+1)^3 square, row-major, into
+   the host array block. */
+sc_status sc_mixed_own_block(sc_mixed* m, int e, double* block);
+/* Static condensation set-up (Sec. 2.2): element blocks in FP32 by five-direction duals,
+   then A_ii^-1 (Gauss-Jordan), S_ee = A_bb - A_bi A_ii^-1 A_ib (TF32 tensor cores) and the
+   blocked LU of S_ee, grouped over all elements of all orders.  SC_ERR_SINGULAR_BLOCK if a
+   block is singular. */
+sc_status sc_mixed_condense(sc_mixed* m);
+/* Solve A dQ = -R(Q) (after sc_mixed_condense): FP64 iterative refinement of the global
+   system to cfg->rel_tol (at most cfg->max_refine sweeps); each sweep solves the condensed
+   system of the current residual by right-preconditioned GMRES(gmres_restart) to
+   cfg->inner_tol, with S applied through two FP32 Jacobian-vector products and the FP32
+   A_ii^-1, and back-substitutes the interior values.  SC_ERR_NOT_CONVERGED (dQ still
+   written) if rel_tol is not reached. */
+sc_status sc_mixed_solve(sc_mixed* m, double* dQ, int on_device, sc_solve_stats* stats);
+/* Kernel launches made by the context so far. */
+long long sc_mixed_launch_count(const sc_mixed* m);
+
 /* ---- Measurement hooks (not part of the method; used by the benchmark) ---------- */
 
 /* Kernel ids for sc_profile_kernel / sc_kernel_work. */

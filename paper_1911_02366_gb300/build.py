@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsc.so")
-SOURCES = ["sc_api.cu", "sc_assemble.cu", "sc_dense.cu", "sc_krylov.cu", "sc_tc.cu", "sc_packed.cu", "sc_mlp.cu", "sc_learned.cu", "sc_explicit.cu", "sc_batch.cu", "sc_march.cu", "sc_redblack.cu", "sc_direct.cu", "sc_partition.cu"]
+SOURCES = ["sc_api.cu", "sc_assemble.cu", "sc_dense.cu", "sc_krylov.cu", "sc_tc.cu", "sc_packed.cu", "sc_mlp.cu", "sc_learned.cu", "sc_explicit.cu", "sc_batch.cu", "sc_march.cu", "sc_redblack.cu", "sc_direct.cu", "sc_partition.cu", "sc_mixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

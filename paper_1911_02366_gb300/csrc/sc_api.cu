@@ -196,6 +196,13 @@ double dnorm2(sc_ctx* c, const double* v, size_t n, double* hd_slot) {
 
 }  // namespace
 
+namespace sc {
+void gl_basis(int N, std::vector<double>& x, std::vector<double>& w, double D[SC_MAXP][SC_MAXP]) {
+  gauss_lobatto(N, x, w);
+  diff_matrix(x, D);
+}
+}  // namespace sc
+
 extern "C" {
 
 sc_status sc_default_config(sc_config* cfg) {

@@ -430,6 +430,8 @@ constexpr int SC_PACK_VIOLATION = (1 << 30) + 1;
 constexpr int SC_EXPLICIT_PATTERN = (1 << 30) + 2;
 
 namespace sc {
+// Gauss-Lobatto nodes x, weights w and differentiation matrix D[a][b] = l_b'(x_a) of order N.
+void gl_basis(int N, std::vector<double>& x, std::vector<double>& w, double D[SC_MAXP][SC_MAXP]);
 cudaError_t launch_residual(sc_ctx* c);
 // -R(Q) with the geometry G (c0 = 0 gives -H(Q), the spatial operator alone) into out;
 // uses c->grad and c->F as scratch.

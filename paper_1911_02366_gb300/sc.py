@@ -63,7 +63,10 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_batch_condense", "sc_batch_tiles", "sc_batch_destroy", "sc_spectrum_estimate",
            "sc_hessenberg_eigvals", "sc_steady_residual", "sc_explicit_march", "sc_implicit_march",
            "sc_precond_apply", "sc_profile_elements", "sc_mlp_bf16", "sc_mlp_train", "sc_mlp_save", "sc_mlp_load", "sc_load_mlp",
-           "sc_direct_factor", "sc_direct_solve", "sc_partition_slabs", "sc_partition_halo"]
+           "sc_direct_factor", "sc_direct_solve", "sc_partition_slabs", "sc_partition_halo",
+           "sc_mixed_create", "sc_mixed_destroy", "sc_mixed_last_error", "sc_mixed_sizes", "sc_mixed_set_state",
+           "sc_mixed_residual", "sc_mixed_jvp", "sc_mixed_own_block", "sc_mixed_condense", "sc_mixed_solve",
+           "sc_mixed_launch_count"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -86,6 +89,18 @@ def lib(build_if_missing: bool = True):
     L = ctypes.CDLL(_build.LIB)
     vp, dp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)
     L.sc_default_config.argtypes = [ctypes.POINTER(sc_config)]
+    L.sc_mixed_create.argtypes = [ctypes.POINTER(sc_config), vp, ctypes.c_int, ctypes.c_double, ip, ctypes.c_int,
+                                  ctypes.POINTER(vp)]
+    L.sc_mixed_destroy.argtypes = [vp]; L.sc_mixed_destroy.restype = None
+    L.sc_mixed_last_error.argtypes = [vp]; L.sc_mixed_last_error.restype = ctypes.c_char_p
+    L.sc_mixed_sizes.argtypes = [vp] + [ctypes.POINTER(ctypes.c_longlong)] * 3
+    L.sc_mixed_set_state.argtypes = [vp, dp, dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    L.sc_mixed_residual.argtypes = [vp, dp, ctypes.c_int]
+    L.sc_mixed_jvp.argtypes = [vp, dp, dp, ctypes.c_int]
+    L.sc_mixed_own_block.argtypes = [vp, ctypes.c_int, dp]
+    L.sc_mixed_condense.argtypes = [vp]
+    L.sc_mixed_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(sc_solve_stats)]
+    L.sc_mixed_launch_count.argtypes = [vp]; L.sc_mixed_launch_count.restype = ctypes.c_longlong
     L.sc_create.argtypes = [ctypes.POINTER(sc_config), vp, ctypes.POINTER(vp)]
     L.sc_destroy.argtypes = [vp]; L.sc_destroy.restype = None
     L.sc_last_error.argtypes = [vp]; L.sc_last_error.restype = ctypes.c_char_p
@@ -171,6 +186,87 @@ def default_config(**kw) -> sc_config:
     for k, v in kw.items():
         setattr(cfg, k, v)
     return cfg
+
+
+class MixedContext:
+    """One periodic mesh of mixed polynomial order (wraps sc_mixed_create / sc_mixed_destroy).
+    States are flat ragged arrays [sum_e (N_e+1)^3 * 5] (numpy on the host or torch on the
+    device)."""
+
+    def __init__(self, n: int, orders, L: float = 2 * np.pi, force_mortar: bool = False,
+                 cfg: sc_config | None = None, stream: int | None = None, **kw):
+        self._L = lib()
+        kw.setdefault("precision", SC_PREC_MIXED)
+        self.cfg = cfg if cfg is not None else default_config(**kw)
+        self.orders = np.ascontiguousarray(orders, dtype=np.int32)
+        if self.orders.shape != (n ** 3,):
+            raise ValueError("one order per element")
+        h = ctypes.c_void_p()
+        st = self._L.sc_mixed_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), int(n), float(L),
+                                     self.orders.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(force_mortar),
+                                     ctypes.byref(h))
+        if st != SC_OK:
+            raise SCError(st, "sc_mixed_create rejected the arguments")
+        self.h = h
+
+    def _check(self, status):
+        if status != SC_OK:
+            raise SCError(status, self._L.sc_mixed_last_error(self.h).decode() if self.h else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.sc_mixed_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sizes(self):
+        v = [ctypes.c_longlong() for _ in range(3)]
+        self._check(self._L.sc_mixed_sizes(self.h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def set_state(self, Q, Qs=None, Qsm1=None, dt: float = 1.0, bdf: int = 1):
+        Qs = Q if Qs is None else Qs
+        (pq, dq), (ps, ds), (pm, dm) = _ptr(Q), _ptr(Qs), _ptr(Qsm1)
+        if ds != dq or (Qsm1 is not None and dm != dq):
+            raise ValueError("all state arrays must live on the same side")
+        self._check(self._L.sc_mixed_set_state(self.h, pq, ps, pm, float(dt), int(bdf), dq))
+
+    def residual(self, R):
+        p, dev = _ptr(R)
+        self._check(self._L.sc_mixed_residual(self.h, p, dev))
+        return R
+
+    def jvp(self, x, y):
+        (px, dx), (py, dy) = _ptr(x), _ptr(y)
+        if dx != dy:
+            raise ValueError("x and y must live on the same side")
+        self._check(self._L.sc_mixed_jvp(self.h, px, py, dx))
+        return y
+
+    def own_block(self, e: int) -> np.ndarray:
+        ne = 5 * (int(self.orders[e]) + 1) ** 3
+        out = np.zeros((ne, ne))
+        self._check(self._L.sc_mixed_own_block(self.h, int(e), out.ctypes.data))
+        return out
+
+    def condense(self):
+        self._check(self._L.sc_mixed_condense(self.h))
+
+    def solve(self, dQ, raise_on_not_converged: bool = True):
+        st = sc_solve_stats()
+        p, dev = _ptr(dQ)
+        s = self._L.sc_mixed_solve(self.h, p, dev, ctypes.byref(st))
+        if s != SC_OK and not (s == SC_ERR_NOT_CONVERGED and not raise_on_not_converged):
+            self._check(s)
+        return st.as_dict() | {"status": s}
+
+    def launch_count(self) -> int:
+        return int(self._L.sc_mixed_launch_count(self.h))
 
 
 class Context:

@@ -84,3 +84,21 @@ def test_hessenberg_eigenvalues_match_numpy():
     # a matrix with a known real spectrum and one with an exact zero subdiagonal
     H = np.diag([5.0, -3.0, 1e-3, 2.0]) + np.diag([1.0, 0.0, 1.0], -1)
     assert np.allclose(np.sort_complex(sc.sc_hessenberg_eigvals(H)), np.sort_complex(np.linalg.eigvals(H)))
+
+
+def test_mixed_mesh_create_rejects_invalid_arguments_before_any_cuda_call():
+    import ctypes
+    import numpy as np
+    from paper_1911_02366_gb300 import sc
+    L = sc.lib()
+    good = np.full(8, 3, np.int32)
+    cases = [(dict(), 2, np.full(8, 7, np.int32)), (dict(), 2, np.full(8, 1, np.int32)),
+             (dict(), 1, np.full(1, 3, np.int32)), (dict(precision=sc.SC_PREC_FP64), 2, good),
+             (dict(visc_flux=sc.SC_VISC_SIPG), 2, good), (dict(precond=sc.SC_PC_RED_BLACK), 2, good),
+             (dict(gmres_restart=0), 2, good)]
+    for kw, n, orders in cases:
+        cfg = sc.default_config(**{"precision": sc.SC_PREC_MIXED, **kw})
+        h = ctypes.c_void_p()
+        st = L.sc_mixed_create(ctypes.byref(cfg), None, n, 6.28, orders.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               0, ctypes.byref(h))
+        assert st == sc.SC_ERR_ARG and not h.value, (kw, n)
