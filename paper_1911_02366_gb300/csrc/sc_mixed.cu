@@ -250,21 +250,26 @@ struct PfQhat {
 };
 struct PfFhat {
   Geo Gp;
+  // The viscous fluxes take the face direction as a compile-time constant: the variant with
+  // a run-time direction, inlined here, gave wrong dual parts.
+  template <int D, class T>
+  __device__ void visc(const T* qa, const T* qb, const T (*ga)[5], const T (*gb)[5], T* v) const {
+    T fva[5], fvb[5];
+    flux_viscous(Gp, qa, ga, D, fva);
+    flux_viscous(Gp, qb, gb, D, fvb);
+    for (int k = 0; k < 5; ++k) v[k] = fva[k] + fvb[k];
+  }
   template <class T>
   __device__ void operator()(const T* a, const T* b, int d, int s, T* out) const {
-    // the viscous fluxes of all three directions with compile-time indices (the variant
-    // with a run-time direction gave wrong dual parts when inlined here)
-    T fa[5], qa[5], qb[5], ga[3][5], gb[3][5], fva[3][5], fvb[3][5];
+    T fa[5], qa[5], qb[5], ga[3][5], gb[3][5], v[5];
     for (int k = 0; k < 5; ++k) { qa[k] = a[k]; qb[k] = b[k]; }
     for (int x = 0; x < 3; ++x)
       for (int k = 0; k < 5; ++k) { ga[x][k] = a[5 + 5 * x + k]; gb[x][k] = b[5 + 5 * x + k]; }
     flux_adv(Gp, qa, qb, d, s, fa);
-    flux_viscous_all(Gp, qa, ga, fva);
-    flux_viscous_all(Gp, qb, gb, fvb);
-    for (int k = 0; k < 5; ++k) {
-      const T v = d == 0 ? fva[0][k] + fvb[0][k] : (d == 1 ? fva[1][k] + fvb[1][k] : fva[2][k] + fvb[2][k]);
-      out[k] = fa[k] - 0.5 * (double)s * v;
-    }
+    if (d == 0) visc<0>(qa, qb, ga, gb, v);
+    else if (d == 1) visc<1>(qa, qb, ga, gb, v);
+    else visc<2>(qa, qb, ga, gb, v);
+    for (int k = 0; k < 5; ++k) out[k] = fa[k] - 0.5 * (double)s * v[k];
   }
 };
 
@@ -471,9 +476,8 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
       };
       face_eval<T5, 5>(M, e, f, ld, PfQhat{}, sbuf, stmp, dst);
     }
-    if (r < 0) continue;
     // the neighbours' qhat on the faces through the seed (their lifted gradients move too)
-    for (int f = 0; f < 6; ++f) {
+    for (int f = 0; f < 6 && r >= 0; ++f) {
       if (!on_face(f)) continue;
       const int d = f >> 1, s = (f & 1) ? 1 : -1, nb = nbr_of(f), fo = 2 * d + (s < 0);
       auto ld = [&](int side, int x, int k) -> T5 {
@@ -483,9 +487,19 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
       };
       face_eval<T5, 5>(M, nb, fo, ld, PfQhat{}, sbuf, stmp, S + L.qhn + f * 49 * 5);
     }
-    // lifted gradient and point fluxes of e
+    // lifted gradient and point fluxes of e; only nodes on a grid line through the seed or
+    // on a face through it move (their derivative parts are cleared again after the seed)
+    auto moves = [&](const int c[3]) {
+      if (r < 0) return true;
+      const int same = (c[0] == cr[0]) + (c[1] == cr[1]) + (c[2] == cr[2]);
+      if (same >= 2) return true;
+      for (int d = 0; d < 3; ++d)
+        if ((c[d] == 0 || c[d] == N) && c[d] == cr[d]) return true;
+      return false;
+    };
     for (int m = threadIdx.x; m < nn; m += blockDim.x) {
       const int c[3] = {m % p, (m / p) % p, m / pp};
+      if (!moves(c)) continue;
       T5 qm[5];
       for (int k = 0; k < 5; ++k) qm[k] = qown(m, k);
       T5 g[3][5];
@@ -501,7 +515,7 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
         if (c[a] == 0 || c[a] == N) {
           const int s = c[a] == N ? 1 : -1, f = 2 * a + (s > 0);
           const int x = c[(a + 2) % 3] * p + c[(a + 1) % 3];
-          const T5* qh = S + L.qh + (f * pp + x) * 5;
+          const T5* qh = S + (r < 0 ? L.qh0 : L.qh) + (f * pp + x) * 5;
           const double coef = s / w[c[a]];
           for (int k = 0; k < 5; ++k) acc[k] = acc[k] + coef * (qh[k] - qm[k]);
         }
@@ -516,6 +530,8 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
         for (int k = 0; k < 5; ++k) S[L.fe + m * 15 + d * 5 + k] = fa[k] - fv[d][k];
       }
     }
+    __syncthreads();
+    if (r < 0) continue;  // the unseeded gradients and fluxes of every node are in place
     // the neighbours' gradients at their face nodes on the shared faces: the FP64 values
     // plus, on the faces through the seed, the move of their lifting term
     for (int f = 0; f < 6; ++f) {
@@ -584,6 +600,14 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
           else { row = 5 * pj + k; col = pr < nin ? 5 * pr + l : cb0 + 5 * (pr - nin) + l; }
           out[row * lda + col] = rr[k].d[l];
         }
+    }
+    __syncthreads();
+    // back to the unseeded gradients and fluxes (their values do not depend on the seed)
+    for (int m = threadIdx.x; m < nn; m += blockDim.x) {
+      const int c[3] = {m % p, (m / p) % p, m / pp};
+      if (!moves(c)) continue;
+      for (int x = 0; x < 15; ++x)
+        for (int i = 0; i < 5; ++i) { S[L.ge + m * 15 + x].d[i] = R(0); S[L.fe + m * 15 + x].d[i] = R(0); }
     }
     __syncthreads();
   }
