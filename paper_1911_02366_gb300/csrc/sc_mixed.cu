@@ -147,7 +147,7 @@ SC_HD inline int mx_node(const int c[3], int p) { return c[0] + p * (c[1] + p * 
 // One face f of element e, evaluated by all threads of the CTA: the values of both sides
 // at their face nodes (ld(side, x, comp), x = fc * p + fb along ((d+1)%3, (d+2)%3)) are
 // interpolated to the mortar points (or used as they are on a conforming face), the point
-// function pf(own, other, out[5]) runs there, and the result is projected back onto e's
+// function pf(point, own, other, d, s, out[5]) runs there, and the result is projected back onto e's
 // face nodes: out[x * 5 + k], x < p_e^2.  sbuf and stmp hold 64 * NC values each.
 template <class T, int NC, class LD, class PF>
 __device__ void face_eval(const MxMesh& M, int e, int f, const LD& ld, const PF& pf, T* sbuf, T* stmp, T* out) {
@@ -197,7 +197,7 @@ __device__ void face_eval(const MxMesh& M, int e, int f, const LD& ld, const PF&
     __syncthreads();
   }
   T fp[5];
-  if (t < pt * pt) pf(va, vb, d, s, fp);
+  if (t < pt * pt) pf(t, va, vb, d, s, fp);
   if (!mortar) {
     if (t < pe * pe)
       for (int k = 0; k < 5; ++k) out[t * 5 + k] = fp[k];
@@ -244,7 +244,7 @@ SC_HD inline int face_node(int N, int d, int s, int x) {
 // fhat = Roe / Lax-Friedrichs(q+, q-) - (1/2) s (f^nu(q+, g+) + f^nu(q-, g-)).
 struct PfQhat {
   template <class T>
-  __device__ void operator()(const T* a, const T* b, int, int, T* out) const {
+  __device__ void operator()(int, const T* a, const T* b, int, int, T* out) const {
     for (int k = 0; k < 5; ++k) out[k] = 0.5 * (a[k] + b[k]);
   }
 };
@@ -260,7 +260,7 @@ struct PfFhat {
     for (int k = 0; k < 5; ++k) v[k] = fva[k] + fvb[k];
   }
   template <class T>
-  __device__ void operator()(const T* a, const T* b, int d, int s, T* out) const {
+  __device__ void operator()(int, const T* a, const T* b, int d, int s, T* out) const {
     T fa[5], qa[5], qb[5], ga[3][5], gb[3][5], v[5];
     for (int k = 0; k < 5; ++k) { qa[k] = a[k]; qb[k] = b[k]; }
     for (int x = 0; x < 3; ++x)
@@ -410,12 +410,64 @@ __global__ void __launch_bounds__(128) k_mx_resid(MxMesh M, const double* __rest
 // (QH), the neighbour's qhat on each shared face (QHN, <= 49 nodes), the lifted gradient
 // (GE) and point fluxes (FE) of the element, the neighbour's gradients on each shared face
 // (GN) and the face fluxes (FH).
+// JF: per face and point, the derivatives of fhat with respect to the own side's 20 inputs
+// (q, lifted gradient) and the neighbour's 15 gradient inputs, 175 reals (in T5 units: 6 reals each).
+constexpr int kFaceJac = 175;
 struct OwnScratch {
-  int qh0, qh, qhn, ge, fe, gn, fh, total;
+  int qh0, qh, qhn, ge, fe, gn, fh, jf, total;
   SC_HD OwnScratch(int N) {
     const int p = N + 1, nn = p * p * p, pf = 6 * p * p * 5;
     qh0 = 0; qh = qh0 + pf; qhn = qh + pf; ge = qhn + 6 * 49 * 5; fe = ge + nn * 15; gn = fe + nn * 15;
-    fh = gn + 6 * 49 * 15; total = fh + pf;
+    fh = gn + 6 * 49 * 15; jf = fh + pf; total = jf + (6 * 49 * kFaceJac + 5) / 6;
+  }
+};
+
+// Point function of the unseeded pass: the face-flux Jacobians at every point (seven passes of
+// five directions: the own 20 inputs, then the neighbour's 15 gradient inputs); no output.
+template <class R>
+struct PfJac {
+  Geo Gp; R* J;  // J[point][175] of one face
+  template <class T>
+  __device__ void operator()(int t, const T* a, const T* b, int d, int s, T* out) const {
+    R* Jt = J + t * kFaceJac;
+    for (int pass = 0; pass < 7; ++pass) {
+      T qa[20], qb[20], o[5];
+      for (int c = 0; c < 20; ++c) { qa[c] = T((double)a[c].v); qb[c] = T((double)b[c].v); }
+      for (int i = 0; i < 5; ++i) {
+        const int dir = pass * 5 + i;
+        if (dir < 20) qa[dir].d[i] = R(1);
+        else qb[5 + dir - 20].d[i] = R(1);
+      }
+      PfFhat{Gp}(t, qa, qb, d, s, o);
+      for (int k = 0; k < 5; ++k)
+        for (int i = 0; i < 5; ++i) {
+          const int dir = pass * 5 + i;
+          if (dir < 20) Jt[k * 20 + dir] = o[k].d[i];
+          else Jt[100 + k * 15 + dir - 20] = o[k].d[i];
+        }
+    }
+    for (int k = 0; k < 5; ++k) out[k] = T(0.0);
+  }
+};
+
+// Point function of a seed: the dual parts of fhat from those of the inputs through the
+// Jacobians of the unseeded pass (values are not needed: the rows take dual parts only).
+template <class R>
+struct PfLin {
+  const R* J;
+  template <class T>
+  __device__ void operator()(int t, const T* a, const T* b, int, int, T* out) const {
+    const R* Jt = J + t * kFaceJac;
+    for (int k = 0; k < 5; ++k) {
+      T o;
+      for (int i = 0; i < 5; ++i) {
+        R acc = R(0);
+        for (int c = 0; c < 20; ++c) acc += Jt[k * 20 + c] * a[c].d[i];
+        for (int c = 0; c < 15; ++c) acc += Jt[100 + k * 15 + c] * b[5 + c].d[i];
+        o.d[i] = acc;
+      }
+      out[k] = o;
+    }
   }
 };
 
@@ -530,8 +582,6 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
         for (int k = 0; k < 5; ++k) S[L.fe + m * 15 + d * 5 + k] = fa[k] - fv[d][k];
       }
     }
-    __syncthreads();
-    if (r < 0) continue;  // the unseeded gradients and fluxes of every node are in place
     // the neighbours' gradients at their face nodes on the shared faces: the FP64 values
     // plus, on the faces through the seed, the move of their lifting term
     for (int f = 0; f < 6; ++f) {
@@ -551,7 +601,9 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
       }
     }
     __syncthreads();
-    // face fluxes of e
+    R* Jf = reinterpret_cast<R*>(S + L.jf);
+    // face fluxes of e: at r = -1 the Jacobians of every face point, then per seed their
+    // products with the moved inputs
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1, s = (f & 1) ? 1 : -1, nb = nbr_of(f);
       auto ld = [&](int side, int x, int k) -> T5 {
@@ -565,8 +617,10 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
         }
         return S[L.gn + (f * 49 + x) * 15 + (k - 5)];
       };
-      face_eval<T5, 20>(M, e, f, ld, PfFhat{Gp}, sbuf, stmp, S + L.fh + f * pp * 5);
+      if (r < 0) face_eval<T5, 20>(M, e, f, ld, PfJac<R>{Gp, Jf + f * 49 * kFaceJac}, sbuf, stmp, S + L.fh + f * pp * 5);
+      else face_eval<T5, 20>(M, e, f, ld, PfLin<R>{Jf + f * 49 * kFaceJac}, sbuf, stmp, S + L.fh + f * pp * 5);
     }
+    if (r < 0) continue;  // unseeded gradients, fluxes and face Jacobians are in place
     // rows of e: the column block of the seed
     for (int j = threadIdx.x; j < nn; j += blockDim.x) {
       const int c[3] = {j % p, (j / p) % p, j / pp};
