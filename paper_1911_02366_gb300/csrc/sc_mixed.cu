@@ -822,6 +822,8 @@ struct MxClass {  // the elements of one order
   float *Aown32 = nullptr, *Ainv32 = nullptr, *Y32 = nullptr, *See32 = nullptr, *Sls32 = nullptr, *dsc = nullptr;
   int *piv = nullptr, *rowperm = nullptr;
   sc_ctx* view = nullptr;  // sizes and stream for the shared block-solve kernels
+  cudaStream_t st = nullptr;       // the class's own stream (the class passes run concurrently)
+  cudaEvent_t done = nullptr;
   int bn_y = 144, bn_s = 144, bn_t = 144;
   size_t off_y = 0, off_s = 0;
   std::vector<size_t> off_t;
@@ -860,6 +862,7 @@ struct sc_mixed {
   float** d_own_out = nullptr;
   int* d_elist = nullptr;
   sc_ctx* aux = nullptr;  // Krylov workspace of the shared vector kernels
+  cudaEvent_t fork = nullptr;
   long long launches = 0;
 };
 
@@ -1028,13 +1031,16 @@ sc_status sc_mixed_create(const sc_config* cfg, void* cuda_stream, int n, double
     A(mx_alloc(&c.Y32, k * c.nb * c.ldi)); A(mx_alloc(&c.See32, k * c.nb * c.lds));
     A(mx_alloc(&c.Sls32, k * c.ls)); A(mx_alloc(&c.dsc, k * c.ni));
     A(mx_alloc(&c.piv, k * c.nb)); A(mx_alloc(&c.rowperm, k * c.nb));
+    A(cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking));
+    A(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
     c.view = new sc_ctx();
-    c.view->G = Gc; c.view->stream = m->stream; c.view->cfg = *cfg;
+    c.view->G = Gc; c.view->stream = c.st; c.view->cfg = *cfg;
     c.view->rowperm = c.rowperm;
     m->max_ni = std::max(m->max_ni, c.ni);
     m->max_nb = std::max(m->max_nb, c.nb);
   }
   A(mx_alloc(&m->d_status, 1));
+  A(cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming));
   if (e == cudaSuccess) {
     for (MxClass& c : m->cls)
       for (int i = 0; i < c.count; ++i) {
@@ -1114,8 +1120,11 @@ void sc_mixed_destroy(sc_mixed* m) {
   for (MxClass& c : m->cls) {
     void* cs[] = {c.Aown32, c.Ainv32, c.Y32, c.See32, c.Sls32, c.dsc, c.piv, c.rowperm};
     for (void* p : cs) if (p) cudaFree(p);
+    if (c.st) cudaStreamDestroy(c.st);
+    if (c.done) cudaEventDestroy(c.done);
     delete c.view;
   }
+  if (m->fork) cudaEventDestroy(m->fork);
   if (m->aux) {
     if (m->aux->partial) cudaFree(m->aux->partial);
     if (m->aux->Hd) cudaFree(m->aux->Hd);
@@ -1240,14 +1249,28 @@ cudaError_t mx_condense_blocks(sc_mixed* m) {
 }
 
 // u = A_ii^-1 (x - xsub) over all classes (interior vectors, slot order).
-cudaError_t mx_ainv(sc_mixed* m, const double* x, const double* xsub, double* u) {
-  for (const MxClass& c : m->cls) {
-    const long long o = m->ioff[c.slot0];
-    if (c.ni == 0) continue;
-    k_mx_ainv<<<c.count, 256, 0, m->stream>>>(c.ni, c.ldi, c.Ainv32, x + o, xsub ? xsub + o : nullptr, u + o);
-    m->launches += 1;
+// The classes' passes run on the classes' streams, forked from and joined back into the
+// context's stream.
+template <class F>
+cudaError_t mx_per_class(sc_mixed* m, F&& launch) {
+  cudaError_t e = cudaEventRecord(m->fork, m->stream);
+  for (MxClass& c : m->cls) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.st, m->fork, 0);
+    if (e == cudaSuccess) e = launch(c);
+    if (e == cudaSuccess) e = cudaEventRecord(c.done, c.st);
   }
-  return cudaGetLastError();
+  for (MxClass& c : m->cls)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m->stream, c.done, 0);
+  return e;
+}
+
+cudaError_t mx_ainv(sc_mixed* m, const double* x, const double* xsub, double* u) {
+  return mx_per_class(m, [&](MxClass& c) {
+    const long long o = m->ioff[c.slot0];
+    k_mx_ainv<<<c.count, 256, 0, c.st>>>(c.ni, c.ldi, c.Ainv32, x + o, xsub ? xsub + o : nullptr, u + o);
+    m->launches += 1;
+    return cudaGetLastError();
+  });
 }
 
 // y = S x with two FP32 Jacobian-vector products (x, y boundary vectors).
@@ -1270,13 +1293,11 @@ cudaError_t mx_apply_S(sc_mixed* m, const double* x, double* y) {
 cudaError_t mx_precond(sc_mixed* m, const double* v, double* z) {
   if (m->cfg.precond == SC_PC_NONE)
     return cudaMemcpyAsync(z, v, (size_t)m->nbt * sizeof(double), cudaMemcpyDeviceToDevice, m->stream);
-  for (MxClass& c : m->cls) {
+  return mx_per_class(m, [&](MxClass& c) {
     const long long o = m->boff[c.slot0];
-    cudaError_t e = sc::lu_solve_list32(c.view, c.Sls32, c.rowperm, 0, nullptr, c.count, v + o, nullptr, z + o, nullptr);
     m->launches += 1;
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+    return sc::lu_solve_list32(c.view, c.Sls32, c.rowperm, 0, nullptr, c.count, v + o, nullptr, z + o, nullptr);
+  });
 }
 
 double mx_norm(sc_mixed* m, const double* v, size_t n) {
