@@ -515,11 +515,7 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
     // qhat of e's faces (r = -1: the unseeded values)
     for (int f = 0; f < 6; ++f) {
       T5* dst = S + (r < 0 ? L.qh0 : L.qh) + f * pp * 5;
-      if (r >= 0 && !on_face(f)) {
-        for (int x = threadIdx.x; x < pp * 5; x += blockDim.x) dst[x] = S[L.qh0 + f * pp * 5 + x];
-        __syncthreads();
-        continue;
-      }
+      if (r >= 0 && !on_face(f)) continue;  // the lifting reads the unseeded qhat of this face
       const int d = f >> 1, s = (f & 1) ? 1 : -1, nb = nbr_of(f);
       auto ld = [&](int side, int x, int k) -> T5 {
         if (side == 0) return qown(face_node(N, d, s, x), k);
@@ -567,7 +563,7 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
         if (c[a] == 0 || c[a] == N) {
           const int s = c[a] == N ? 1 : -1, f = 2 * a + (s > 0);
           const int x = c[(a + 2) % 3] * p + c[(a + 1) % 3];
-          const T5* qh = S + (r < 0 ? L.qh0 : L.qh) + (f * pp + x) * 5;
+          const T5* qh = S + (on_face(f) ? L.qh : L.qh0) + (f * pp + x) * 5;
           const double coef = s / w[c[a]];
           for (int k = 0; k < 5; ++k) acc[k] = acc[k] + coef * (qh[k] - qm[k]);
         }
@@ -587,6 +583,7 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1, s = (f & 1) ? 1 : -1, nb = nbr_of(f), Nn = M.ord[nb], pn = Nn + 1;
       const bool moved = on_face(f);
+      if (r >= 0 && !moved) continue;  // only the general face path (faces through the seed) reads these
       const double coef = M.dx * (double)(-s) / M.tab->w[Nn][0];
       for (int x = threadIdx.x; x < pn * pn; x += blockDim.x) {
         const size_t node = (size_t)M.off[nb] + face_node(Nn, d, -s, x);
@@ -606,6 +603,70 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
     // products with the moved inputs
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1, s = (f & 1) ? 1 : -1, nb = nbr_of(f);
+      if (r >= 0 && !on_face(f)) {
+        // a face away from the seed: the state on it does not move, nor does the neighbour's
+        // gradient; the lifted gradient moves at the face nodes the seed moves (the one on
+        // its grid line along d, and the rows on faces through the seed), so fhat moves by
+        // J_g times their interpolated moves
+        const int Nn = M.ord[nb], pe = p;
+        const bool mortar = N != Nn || M.force_mortar;
+        const int Mo = N > Nn ? N : Nn, pm = Mo + 1, npt = mortar ? pm * pm : pe * pe;
+        const R* J = Jf + f * 49 * kFaceJac;
+        T5* out5 = S + L.fh + f * pp * 5;
+        const double* Im = &M.tab->I[N][Mo][0][0];
+        for (int t = threadIdx.x; t < npt; t += blockDim.x) {
+          R dg[15][5];
+          for (int c = 0; c < 15; ++c)
+            for (int i = 0; i < 5; ++i) dg[c][i] = R(0);
+          bool any = false;
+          for (int x = 0; x < pe * pe; ++x) {
+            const int m = face_node(N, d, s, x);
+            const int cm[3] = {m % p, (m / p) % p, m / pp};
+            if (!moves(cm)) continue;
+            const double wgt = mortar ? Im[(t / pm) * 8 + x / pe] * Im[(t % pm) * 8 + x % pe] : (t == x ? 1.0 : 0.0);
+            if (wgt == 0.0) continue;
+            any = true;
+            const T5* g = S + L.ge + m * 15;
+            for (int c = 0; c < 15; ++c)
+              for (int i = 0; i < 5; ++i) dg[c][i] += R(wgt) * g[c].d[i];
+          }
+          const R* Jt = J + t * kFaceJac;
+          for (int k = 0; k < 5; ++k) {
+            T5 o;
+            if (any)
+              for (int i = 0; i < 5; ++i) {
+                R acc = R(0);
+                for (int c = 0; c < 15; ++c) acc += Jt[k * 20 + 5 + c] * dg[c][i];
+                o.d[i] = acc;
+              }
+            if (mortar) sbuf[t * 5 + k] = o;
+            else out5[t * 5 + k] = o;
+          }
+        }
+        __syncthreads();
+        if (mortar) {  // projection onto e's face nodes, as in face_eval
+          const double* Pm = &M.tab->P[Mo][N][0][0];
+          for (int x = threadIdx.x; x < pe * pm; x += blockDim.x) {
+            const int i = x / pm, b = x % pm;
+            for (int k = 0; k < 5; ++k) {
+              T5 acc;
+              for (int a = 0; a < pm; ++a) acc = acc + Pm[i * 8 + a] * sbuf[(a * pm + b) * 5 + k];
+              stmp[x * 5 + k] = acc;
+            }
+          }
+          __syncthreads();
+          for (int x = threadIdx.x; x < pe * pe; x += blockDim.x) {
+            const int i = x / pe, j = x % pe;
+            for (int k = 0; k < 5; ++k) {
+              T5 acc;
+              for (int b = 0; b < pm; ++b) acc = acc + Pm[j * 8 + b] * stmp[(i * pm + b) * 5 + k];
+              out5[x * 5 + k] = acc;
+            }
+          }
+          __syncthreads();
+        }
+        continue;
+      }
       auto ld = [&](int side, int x, int k) -> T5 {
         if (side == 0) {
           const int m = face_node(N, d, s, x);
