@@ -93,3 +93,25 @@ def test_mixed_condensed_solve_matches_oracle_global_solve_bdf2_on_device():
     B = -O.residual_mixed(p, orders, Q.reshape(-1, 5), Qs.reshape(-1, 5), Qsm1.reshape(-1, 5)).reshape(-1)
     x = O.global_solve(A, B)
     assert np.linalg.norm(dQ.cpu().numpy() - x) / np.linalg.norm(x) < 1e-8
+
+
+def test_mixed_full_size_mesh_of_the_benchmark():
+    # the 12^3 mesh of orders drawn from 2..6 (seed 1) that bench.py --arm mixedmesh times, in
+    # its launch configuration: residual against the oracle's, sampled element blocks against
+    # the oracle's element rows, and the solve to 1e-8 checked through the oracle's product
+    from paper_1911_02366_gb300 import sc
+    n = 12
+    orders = I.order_draw(1, n ** 3)
+    Q, p, ctx = _case(n, orders, cfl=10.0, rel_tol=1e-8, inner_tol=1e-4, max_refine=20)
+    Q2 = Q.reshape(-1, 5)
+    R = ctx.residual(np.zeros_like(Q))
+    assert rel(R, O.residual_mixed(p, orders, Q2).reshape(-1)) < 1e-12
+    for e in (int(np.argmax(orders)), int(np.argmin(orders)), 1000):
+        ref = O.jacobian_mixed_element_rows(p, orders, Q2, e)[e]
+        assert np.abs(ctx.own_block(e) - ref).max() <= 1e-11 * np.abs(ref).max(), e
+    ctx.condense()
+    dQ = np.zeros_like(Q)
+    st = ctx.solve(dQ)
+    B = -R
+    AdQ = O.jvp_mixed(p, orders, Q2, dQ.reshape(-1, 5)).reshape(-1)
+    assert np.linalg.norm(B - AdQ) / np.linalg.norm(B) < 1.01e-8, st
