@@ -17,7 +17,7 @@ def _case(n, orders, force_mortar=False, cfl=10.0, seed=0, **cfg):
     from paper_1911_02366_gb300 import sc
     Q, dt = I.tgv_state_mixed(n, orders, cfl=cfl, eps=1e-2, seed=seed)
     Q = np.ascontiguousarray(Q.reshape(-1))
-    p = O.Params(n=n, N=int(max(orders)), dt=dt)
+    p = O.Params(n=n, N=int(max(orders)), dt=dt, adv_flux=cfg.get("adv_flux", 0))
     ctx = sc.MixedContext(n, orders, TWO_PI, force_mortar=force_mortar,
                           stream=torch.cuda.current_stream().cuda_stream, **cfg)
     ctx.set_state(Q, Q, dt=dt)
@@ -115,3 +115,20 @@ def test_mixed_full_size_mesh_of_the_benchmark():
     B = -R
     AdQ = O.jvp_mixed(p, orders, Q2, dQ.reshape(-1, 5)).reshape(-1)
     assert np.linalg.norm(B - AdQ) / np.linalg.norm(B) < 1.01e-8, st
+
+
+def test_mixed_lax_friedrichs_residual_products_and_blocks_match_oracle():
+    from paper_1911_02366_gb300 import sc
+    n = 2
+    orders = _orders(n, "draw")
+    Q, p, ctx = _case(n, orders, adv_flux=sc.SC_FLUX_LF)
+    assert p.adv_flux == 1
+    R = ctx.residual(np.zeros_like(Q))
+    assert rel(R, O.residual_mixed(p, orders, Q.reshape(-1, 5)).reshape(-1)) < 1e-12
+    assert rel(R, O.residual_mixed(O.Params(**{**p.__dict__, "adv_flux": 0}), orders, Q.reshape(-1, 5)).reshape(-1)) > 1e-8
+    x = np.random.default_rng(6).standard_normal(Q.size)
+    y = ctx.jvp(x, np.zeros_like(x))
+    assert rel(y, O.jvp_mixed(p, orders, Q.reshape(-1, 5), x.reshape(-1, 5)).reshape(-1)) < 1e-12
+    e = int(np.argmax(orders))
+    ref = O.jacobian_mixed_element_rows(p, orders, Q.reshape(-1, 5), e)[e]
+    assert np.abs(ctx.own_block(e) - ref).max() <= 1e-11 * np.abs(ref).max()
