@@ -541,6 +541,13 @@ sc_status sc_mixed_condense(sc_mixed* m);
 sc_status sc_mixed_solve(sc_mixed* m, double* dQ, int on_device, sc_solve_stats* stats);
 /* Kernel launches made by the context so far. */
 long long sc_mixed_launch_count(const sc_mixed* m);
+/* Measurement hook (not part of the method): with on = 1, every block-Jacobi application of
+   the following solves is bracketed by events (the counter restarts).  profile_read
+   synchronises and returns the number of applications, their total device time and the
+   bytes one application moves by its algorithm (FP32 factors n_b x lds, row permutation,
+   FP64 right-hand side in and result out, summed over the elements). */
+sc_status sc_mixed_profile(sc_mixed* m, int on);
+sc_status sc_mixed_profile_read(sc_mixed* m, int* count, double* ms_total, double* bytes_each);
 
 /* ---- Measurement hooks (not part of the method; used by the benchmark) ---------- */
 

@@ -924,6 +924,10 @@ struct sc_mixed {
   int* d_elist = nullptr;
   sc_ctx* aux = nullptr;  // Krylov workspace of the shared vector kernels
   cudaEvent_t fork = nullptr;
+  // measurement hook: events around every block-Jacobi application
+  bool prof = false;
+  int prof_used = 0;
+  std::vector<cudaEvent_t> prof_ev;
   long long launches = 0;
 };
 
@@ -1186,6 +1190,7 @@ void sc_mixed_destroy(sc_mixed* m) {
     delete c.view;
   }
   if (m->fork) cudaEventDestroy(m->fork);
+  for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
   if (m->aux) {
     if (m->aux->partial) cudaFree(m->aux->partial);
     if (m->aux->Hd) cudaFree(m->aux->Hd);
@@ -1354,11 +1359,21 @@ cudaError_t mx_apply_S(sc_mixed* m, const double* x, double* y) {
 cudaError_t mx_precond(sc_mixed* m, const double* v, double* z) {
   if (m->cfg.precond == SC_PC_NONE)
     return cudaMemcpyAsync(z, v, (size_t)m->nbt * sizeof(double), cudaMemcpyDeviceToDevice, m->stream);
-  return mx_per_class(m, [&](MxClass& c) {
+  if (m->prof) {
+    while ((int)m->prof_ev.size() < 2 * (m->prof_used + 1)) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) return cudaErrorMemoryAllocation;
+      m->prof_ev.push_back(ev);
+    }
+    cudaEventRecord(m->prof_ev[2 * m->prof_used], m->stream);
+  }
+  cudaError_t e = mx_per_class(m, [&](MxClass& c) {
     const long long o = m->boff[c.slot0];
     m->launches += 1;
     return sc::lu_solve_list32(c.view, c.Sls32, c.rowperm, 0, nullptr, c.count, v + o, nullptr, z + o, nullptr);
   });
+  if (m->prof) cudaEventRecord(m->prof_ev[2 * m->prof_used++ + 1], m->stream);
+  return e;
 }
 
 double mx_norm(sc_mixed* m, const double* v, size_t n) {
@@ -1534,5 +1549,29 @@ sc_status sc_mixed_solve(sc_mixed* m, double* dQ, int on_device, sc_solve_stats*
 }
 
 long long sc_mixed_launch_count(const sc_mixed* m) { return m ? m->launches + (m->aux ? m->aux->launches : 0) : 0; }
+
+sc_status sc_mixed_profile(sc_mixed* m, int on) {
+  if (!m) return SC_ERR_ARG;
+  m->prof = on != 0;
+  m->prof_used = 0;
+  return SC_OK;
+}
+
+sc_status sc_mixed_profile_read(sc_mixed* m, int* count, double* ms_total, double* bytes_each) {
+  if (!m || !count || !ms_total || !bytes_each) return SC_ERR_ARG;
+  MX_CUDA(cudaStreamSynchronize(m->stream));
+  double ms = 0.0;
+  for (int i = 0; i < m->prof_used; ++i) {
+    float t = 0.f;
+    MX_CUDA(cudaEventElapsedTime(&t, m->prof_ev[2 * i], m->prof_ev[2 * i + 1]));
+    ms += t;
+  }
+  double b = 0.0;  // per application: the FP32 factors, the row permutation, v in and z out
+  for (const MxClass& c : m->cls) b += (double)c.count * (4.0 * c.nb * c.lds + 4.0 * c.nb + 16.0 * c.nb);
+  *count = m->prof_used;
+  *ms_total = ms;
+  *bytes_each = b;
+  return SC_OK;
+}
 
 }  // extern "C"

@@ -66,7 +66,7 @@ EXPORTS = ["sc_default_config", "sc_create", "sc_destroy", "sc_last_error", "sc_
            "sc_direct_factor", "sc_direct_solve", "sc_partition_slabs", "sc_partition_halo",
            "sc_mixed_create", "sc_mixed_destroy", "sc_mixed_last_error", "sc_mixed_sizes", "sc_mixed_set_state",
            "sc_mixed_residual", "sc_mixed_jvp", "sc_mixed_own_block", "sc_mixed_condense", "sc_mixed_solve",
-           "sc_mixed_launch_count"]
+           "sc_mixed_launch_count", "sc_mixed_profile", "sc_mixed_profile_read"]
 
 SC_KERNEL_COND_INTERIOR, SC_KERNEL_COND_BOUNDARY, SC_KERNEL_LU_SOLVE, SC_KERNEL_LU = 0, 1, 2, 3
 SC_KERNEL_SCHUR_GEMM, SC_KERNEL_GJ_INV, SC_KERNEL_ASSEMBLE_OWN, SC_KERNEL_GLOBAL_APPLY = 4, 5, 6, 7
@@ -101,6 +101,8 @@ def lib(build_if_missing: bool = True):
     L.sc_mixed_condense.argtypes = [vp]
     L.sc_mixed_solve.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(sc_solve_stats)]
     L.sc_mixed_launch_count.argtypes = [vp]; L.sc_mixed_launch_count.restype = ctypes.c_longlong
+    L.sc_mixed_profile.argtypes = [vp, ctypes.c_int]
+    L.sc_mixed_profile_read.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.sc_create.argtypes = [ctypes.POINTER(sc_config), vp, ctypes.POINTER(vp)]
     L.sc_destroy.argtypes = [vp]; L.sc_destroy.restype = None
     L.sc_last_error.argtypes = [vp]; L.sc_last_error.restype = ctypes.c_char_p
@@ -267,6 +269,15 @@ class MixedContext:
 
     def launch_count(self) -> int:
         return int(self._L.sc_mixed_launch_count(self.h))
+
+    def profile(self, on: bool):
+        self._check(self._L.sc_mixed_profile(self.h, int(on)))
+
+    def profile_read(self):
+        """(block-Jacobi applications, their total device ms, algorithmic bytes of one)."""
+        n, ms, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.sc_mixed_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
+        return n.value, ms.value, b.value
 
 
 class Context:
