@@ -6,6 +6,8 @@ import os
 import re
 import subprocess
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -102,3 +104,15 @@ def test_mixed_mesh_create_rejects_invalid_arguments_before_any_cuda_call():
         st = L.sc_mixed_create(ctypes.byref(cfg), None, n, 6.28, orders.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                0, ctypes.byref(h))
         assert st == sc.SC_ERR_ARG and not h.value, (kw, n)
+
+
+def test_mixed_context_binding_checks_its_arguments_without_a_gpu():
+    import numpy as np
+    from paper_1911_02366_gb300 import sc
+    with pytest.raises(ValueError):
+        sc.MixedContext(2, np.full(7, 3))          # one order per element
+    with pytest.raises(sc.SCError) as ei:
+        sc.MixedContext(2, np.full(8, 9))          # orders outside 2..6
+    assert ei.value.status == sc.SC_ERR_ARG
+    with pytest.raises(sc.SCError):
+        sc.MixedContext(2, np.full(8, 3), visc_flux=sc.SC_VISC_SIPG)
