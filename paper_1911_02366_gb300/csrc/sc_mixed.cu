@@ -682,31 +682,44 @@ __global__ void __launch_bounds__(128) k_mx_own(MxMesh M, Geo Gp, const double* 
       else face_eval<T5, 20>(M, e, f, ld, PfLin<R>{Jf + f * 49 * kFaceJac}, sbuf, stmp, S + L.fh + f * pp * 5);
     }
     if (r < 0) continue;  // unseeded gradients, fluxes and face Jacobians are in place
-    // rows of e: the column block of the seed
+    // rows of e: the column block of the seed.  Only moved nodes carry a flux derivative, so
+    // a row reads the fluxes of the moved nodes on its grid lines; rows with no moved node
+    // on them and no face keep the zeros already in the block
     for (int j = threadIdx.x; j < nn; j += blockDim.x) {
       const int c[3] = {j % p, (j / p) % p, j / pp};
       const double Wj = w[c[0]] * w[c[1]] * w[c[2]];
       T5 rr[5];
-      if (j == r)
+      bool any = false;
+      if (j == r) {
         for (int k = 0; k < 5; ++k) rr[k].d[k] = R(M.c0 * M.J * Wj / M.dt);
+        any = true;
+      }
       for (int d = 0; d < 3; ++d) {
         int cc[3] = {c[0], c[1], c[2]};
         for (int b = 0; b < p; ++b) {
           cc[d] = b;
+          if (!moves(cc)) continue;
+          any = true;
           const double coef = M.Jf * Wj * D[c[d] * 8 + b];
           const T5* Fm = S + L.fe + mx_node(cc, p) * 15 + d * 5;
           for (int k = 0; k < 5; ++k) rr[k] = rr[k] + coef * Fm[k];
         }
       }
+      const bool jm = moves(c);
       for (int d = 0; d < 3; ++d) {
         if (c[d] != 0 && c[d] != N) continue;
+        any = true;
         const int s = c[d] == N ? 1 : -1, f = 2 * d + (s > 0);
         const int x = c[(d + 2) % 3] * p + c[(d + 1) % 3];
         const T5* fh = S + L.fh + (f * pp + x) * 5;
-        const T5* Fj = S + L.fe + j * 15 + d * 5;
         const double Sf = M.Jf * Wj / w[c[d]];
-        for (int k = 0; k < 5; ++k) rr[k] = rr[k] + Sf * (fh[k] - (double)s * Fj[k]);
+        for (int k = 0; k < 5; ++k) rr[k] = rr[k] + Sf * fh[k];
+        if (jm) {
+          const T5* Fj = S + L.fe + j * 15 + d * 5;
+          for (int k = 0; k < 5; ++k) rr[k] = rr[k] - (Sf * (double)s) * Fj[k];
+        }
       }
+      if (!any) continue;
       const int pj = perm[j], pr = perm[r];
       for (int k = 0; k < 5; ++k)
         for (int l = 0; l < 5; ++l) {
