@@ -245,3 +245,17 @@ def test_mixed_element_rows_equal_the_sparse_jacobian():
         for c, blk in rows.items():
             ref = A[off[e]:off[e + 1], off[c]:off[c + 1]].toarray()
             assert np.abs(blk - ref).max() <= 1e-14 * np.abs(A.data).max(), (e, c)
+
+
+def test_lax_friedrichs_across_mortars_keeps_free_stream_and_conservation():
+    # the paper's advective flux on mixed-order meshes: the same two invariants as Roe's
+    n = 3
+    orders = I.order_draw(1, n ** 3)
+    U = I.uniform_state_mixed(n, orders)
+    p = O.Params(n=n, N=int(orders.max()), with_time=False, adv_flux=1)
+    assert np.abs(O.residual_mixed(p, orders, U)).max() < 1e-11 * np.abs(U).max()
+    Q, _ = I.tgv_state_mixed(n, orders, eps=1e-2)
+    R = O.residual_mixed(p, orders, Q)
+    assert np.abs(R.sum(axis=0)).max() < 1e-10 * np.abs(R).max()
+    roe = O.residual_mixed(O.Params(**{**p.__dict__, "adv_flux": 0}), orders, Q)
+    assert np.abs(R - roe).max() > 1e-8 * np.abs(R).max()
